@@ -1,0 +1,170 @@
+"""Seeded synthetic inputs for filter-bank correlation workloads.
+
+This module holds random-number recipes only -- none of the correlation
+arithmetic -- so that both the GPU tests and the CPU oracle can be fed the
+same arrays.  Every array is drawn in FP64 with ``numpy.random.default_rng``
+and cast to FP32; draw order is x, then w, then g.
+
+Shapes follow the paper's Table "Performance of RTCG auto-tuning on 3D
+filter-bank convolutions" (input H x W x D, bank N x fh x fw x D): the
+256x256x8 / 64x9x9x8 workload below is that table's first row.  The paper's
+inputs came from natural-image model layers that are not available, so
+uniform and Gaussian draws of the same shapes stand in for them.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import List, Optional, Tuple
+
+import numpy as np
+
+
+def uniform(rng, shape, lo=0.0, hi=1.0) -> np.ndarray:
+    return rng.uniform(lo, hi, size=shape).astype(np.float32)
+
+
+def normal(rng, shape, var=1.0) -> np.ndarray:
+    return (rng.standard_normal(size=shape) * np.sqrt(var)).astype(np.float32)
+
+
+def zero_mean_unit_norm_bank(rng, N, fh, fw, D) -> np.ndarray:
+    """N(0,1) filters, then per filter: subtract the mean and divide by the L2
+    norm over (fh, fw, D), in FP64, then cast to FP32."""
+    w = rng.standard_normal(size=(N, fh, fw, D))
+    w = w - w.mean(axis=(1, 2, 3), keepdims=True)
+    w = w / np.sqrt((w * w).sum(axis=(1, 2, 3), keepdims=True))
+    return w.astype(np.float32)
+
+
+def integer_array(rng, shape, lo=-4, hi=4) -> np.ndarray:
+    """Integers in [lo, hi] stored as FP32 (exact in FP32 and BF16)."""
+    return rng.integers(lo, hi + 1, size=shape).astype(np.float32)
+
+
+@dataclass
+class Workload:
+    name: str
+    x: np.ndarray                       # [H, W, D] float32
+    w: np.ndarray                       # [N, fh, fw, D] float32
+    g: Optional[np.ndarray] = None      # [H', W', N] float32 upstream gradient
+    clamp: Optional[Tuple[float, float]] = None
+    modes: Tuple[str, ...] = ("f32",)
+
+    @property
+    def out_shape(self):
+        H, W, _ = self.x.shape
+        N, fh, fw, _ = self.w.shape
+        return (H - fh + 1, W - fw + 1, N)
+
+    @property
+    def flops(self) -> int:
+        """Algorithmic FLOPs: 2 per multiply-add, 2*H'*W'*N*fh*fw*D."""
+        Ho, Wo, N = self.out_shape
+        _, fh, fw, D = self.w.shape
+        return 2 * Ho * Wo * N * fh * fw * D
+
+
+def workload_small_f32(seed: int = 1) -> Workload:
+    """128x128x8 U[0,1) input, 16 zero-mean unit-norm 9x9x8 filters, no epilogue."""
+    rng = np.random.default_rng(seed)
+    x = uniform(rng, (128, 128, 8))
+    w = zero_mean_unit_norm_bank(rng, 16, 9, 9, 8)
+    return Workload("fp32_128x128x8_16x9x9x8", x, w)
+
+
+def workload_paper_row1_clamp(seed: int = 2) -> Workload:
+    """256x256x8 U[0,1) input, 64 zero-mean unit-norm 9x9x8 filters, clamp [0, 1]."""
+    rng = np.random.default_rng(seed)
+    x = uniform(rng, (256, 256, 8))
+    w = zero_mean_unit_norm_bank(rng, 64, 9, 9, 8)
+    return Workload("fp32clamp_256x256x8_64x9x9x8", x, w, clamp=(0.0, 1.0))
+
+
+def workload_precision(seed: int = 3) -> Workload:
+    """512x512x32 U[-1,1) input, 256 filters 5x5x32 drawn N(0, variance 1/800)."""
+    rng = np.random.default_rng(seed)
+    x = uniform(rng, (512, 512, 32), -1.0, 1.0)
+    w = normal(rng, (256, 5, 5, 32), var=1.0 / 800.0)
+    return Workload("precision_512x512x32_256x5x5x32", x, w, modes=("f32", "bf16", "bf16x3"))
+
+
+def workload_differentiation(seed: int = 5) -> Workload:
+    """256x256x16 U[0,1) input, 64 filters 7x7x16 N(0, 1/784), upstream g N(0,1)."""
+    rng = np.random.default_rng(seed)
+    x = uniform(rng, (256, 256, 16))
+    w = normal(rng, (64, 7, 7, 16), var=1.0 / 784.0)
+    g = normal(rng, (250, 250, 64))
+    return Workload("fwdbwd_256x256x16_64x7x7x16", x, w, g=g)
+
+
+def workload_finite_difference(seed: int = 55) -> Workload:
+    """12x12x2 input, 3 filters 3x3x2, g 10x10x3 -- the finite-difference case."""
+    rng = np.random.default_rng(seed)
+    x = uniform(rng, (12, 12, 2))
+    w = normal(rng, (3, 3, 3, 2), var=1.0 / 18.0)
+    g = normal(rng, (10, 10, 3))
+    return Workload("fd_12x12x2_3x3x3x2", x, w, g=g)
+
+
+BATCH_HW = tuple(range(64, 513, 32))
+BATCH_D = (4, 8, 16, 32)
+BATCH_N = (16, 32, 64, 128)
+BATCH_F = (3, 5, 7, 9, 11)
+
+
+@dataclass
+class BatchWorkload:
+    name: str
+    items: List[Workload] = field(default_factory=list)
+
+    @property
+    def flops(self) -> int:
+        return sum(it.flops for it in self.items)
+
+
+def batch_shapes(seed: int = 4, count: int = 64):
+    """Shapes only (H, W, D, N, f) of the uneven batch, drawn in the same order
+    as ``workload_batch`` so that both agree for the same seed."""
+    return [(s[0], s[1], s[2], s[3], s[4]) for s in _batch_draw(seed, count, arrays=False)]
+
+
+def _batch_draw(seed, count, arrays=True):
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(count):
+        H = int(rng.choice(BATCH_HW))
+        W = int(rng.choice(BATCH_HW))
+        D = int(rng.choice(BATCH_D))
+        N = int(rng.choice(BATCH_N))
+        f = int(rng.choice(BATCH_F))
+        # the arrays are always drawn so that the shapes of later images do not
+        # depend on whether arrays are requested
+        x = uniform(rng, (H, W, D))
+        w = normal(rng, (N, f, f, D))
+        out.append((H, W, D, N, f, x if arrays else None, w if arrays else None))
+    return out
+
+
+def workload_batch(seed: int = 4, count: int = 64) -> BatchWorkload:
+    """64 images: H, W uniform over {64, 96, ..., 512}; D over {4, 8, 16, 32};
+    N over {16, 32, 64, 128}; f = fh = fw over {3, 5, 7, 9, 11}; each image
+    U[0,1) with its own N(0,1) bank."""
+    items = []
+    for k, (H, W, D, N, f, x, w) in enumerate(_batch_draw(seed, count)):
+        items.append(Workload(f"img{k}_{H}x{W}x{D}_{N}x{f}x{f}x{D}", x, w))
+    return BatchWorkload("batch64_uneven", items)
+
+
+def random_case(seed, H, W, D, N, fh, fw, kind="real", with_g=False) -> Workload:
+    """A small case for parity tests.  ``kind`` = "real" (U[-1,1) input and
+    N(0,1) filters) or "int" (integers in [-4, 4])."""
+    rng = np.random.default_rng(seed)
+    if kind == "int":
+        x = integer_array(rng, (H, W, D))
+        w = integer_array(rng, (N, fh, fw, D))
+        g = integer_array(rng, (H - fh + 1, W - fw + 1, N)) if with_g else None
+    else:
+        x = uniform(rng, (H, W, D), -1.0, 1.0)
+        w = normal(rng, (N, fh, fw, D))
+        g = normal(rng, (H - fh + 1, W - fw + 1, N)) if with_g else None
+    return Workload(f"case_{H}x{W}x{D}_{N}x{fh}x{fw}_{kind}_s{seed}", x, w, g=g)
