@@ -1,0 +1,179 @@
+/*
+ * fbcorr.h -- C ABI of the GB300 (sm_103a) filter-bank correlation library.
+ *
+ * The operation is the 3D filter-bank correlation that the paper's vision
+ * case study (Sec. 6.2, "Computational Visual Neuroscience") identifies as the
+ * bottleneck of its models and auto-tunes with run-time code generation
+ * (Table "Performance of RTCG auto-tuning on 3D filter-bank convolutions"):
+ * an H x W x D input stack correlated 'valid' against a bank of N filters of
+ * fh x fw x D, giving an H' x W' x N output (H' = H-fh+1, W' = W-fw+1):
+ *
+ *     y[p][q][n] = epi( sum_{i<fh} sum_{j<fw} sum_{d<D} x[p+i][q+j][d] * w[n][i][j][d] )
+ *
+ * with an optional fused elementwise epilogue epi (a static non-linearity,
+ * Sec. 6.2).  The backward pass gives the gradients of a scalar loss L with
+ * respect to x and w from g = dL/dy.
+ *
+ * Conventions (all calls):
+ *  - Tensors are FP32, row-major with the last index fastest, contiguous and
+ *    16-byte aligned, in DEVICE memory owned by the caller:
+ *      x [H][W][D], w [N][fh][fw][D], y / g [H'][W'][N], dx [H][W][D], dw like w.
+ *  - Every call returns a status and never aborts or exits.  Argument and
+ *    shape errors are detected before any work is enqueued.  A CUDA error is
+ *    reported as FBCORR_ERR_CUDA; fbcorr_last_error() gives the detail
+ *    (a thread-local message, valid until the next call on that thread).
+ *  - forward / backward / forward_batched are stream-ordered, never
+ *    synchronise the host, and allocate no memory: scratch space is the
+ *    caller's workspace (size from the *_workspace_size queries).
+ *  - Kernels are specialised per (fh, fw, D, tile) at plan time by run-time
+ *    code generation (NVRTC, cached on disk) -- the paper's RTCG approach
+ *    (Sec. 3, Sec. 6.2) -- with a prebuilt generic "default" kernel when
+ *    code generation is unavailable.  There is no CPU fallback.
+ */
+#ifndef FBCORR_H
+#define FBCORR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same type as cudaStream_t; NULL is the legacy default stream. */
+typedef struct CUstream_st* fbcorr_stream_t;
+
+typedef struct fbcorr_plan* fbcorr_plan_t;
+typedef struct fbcorr_batch_plan* fbcorr_batch_plan_t;
+
+typedef enum {
+    FBCORR_OK = 0,
+    FBCORR_ERR_INVALID_ARG = 1,  /* null pointer, bad enum, bad count          */
+    FBCORR_ERR_SHAPE = 2,        /* non-positive dim, fh > H, depth mismatch,  */
+                                 /* index arithmetic that would overflow int32 */
+    FBCORR_ERR_UNSUPPORTED = 3,  /* valid request this build cannot run        */
+    FBCORR_ERR_ALIGNMENT = 4,    /* a tensor pointer is not 16-byte aligned    */
+    FBCORR_ERR_WORKSPACE = 5,    /* workspace missing or smaller than required */
+    FBCORR_ERR_CUDA = 6,         /* a CUDA runtime call or a launch failed     */
+    FBCORR_ERR_NVRTC = 7,        /* run-time compilation of a variant failed   */
+    FBCORR_ERR_OOM = 8,          /* host or plan-time device allocation failed */
+    FBCORR_ERR_TIMEOUT = 9,      /* a kernel gave up a bounded wait            */
+    FBCORR_ERR_INTERNAL = 10
+} fbcorr_status_t;
+
+/* Arithmetic of the forward pass; tensors are FP32 in every mode.
+ *  F32    : FP32 products, FP32 accumulation (CUDA cores).
+ *  BF16   : x and w rounded to BF16 (round-to-nearest-even), BF16 x BF16
+ *           products with FP32 accumulation on the tcgen05 tensor cores.
+ *  BF16X3 : "split BF16": v = hi + lo with hi = bf16(v), lo = bf16(v - hi);
+ *           y accumulates hi*hi + hi*lo + lo*hi in FP32 on the tensor cores,
+ *           recovering close to FP32 accuracy.
+ * The backward pass always runs in F32. */
+typedef enum { FBCORR_F32 = 0, FBCORR_BF16 = 1, FBCORR_BF16X3 = 2 } fbcorr_dtype_t;
+
+typedef enum { FBCORR_EPI_NONE = 0, FBCORR_EPI_CLAMP = 1 } fbcorr_epilogue_kind_t;
+
+/* Fused epilogue applied to the FP32 accumulator before the store.
+ * CLAMP: y = fminf(fmaxf(acc, lo), hi), lo <= hi.  Its gradient passes g only
+ * where lo < y < hi strictly. */
+typedef struct {
+    int kind;   /* fbcorr_epilogue_kind_t */
+    float lo, hi;
+} fbcorr_epilogue_t;
+
+/* ---- single-image plans ------------------------------------------------- */
+
+/* Validate the shapes, pick (and on first use compile) the kernel variants for
+ * the current CUDA device, and return a plan.  in_shape = {H, W, D},
+ * filt_shape = {N, fh, fw, D}.  The chosen variant comes from, in order:
+ * FBCORR_VARIANT, the on-disk tuning cache, a measurement run when
+ * FBCORR_AUTOTUNE=1 (or force), and otherwise a built-in heuristic.
+ * The plan owns its compiled modules and device bookkeeping, released by
+ * fbcorr_plan_destroy. */
+fbcorr_status_t fbcorr_plan_create(fbcorr_plan_t* out, const int64_t in_shape[3],
+                                   const int64_t filt_shape[4], fbcorr_dtype_t dtype,
+                                   fbcorr_epilogue_t epilogue);
+fbcorr_status_t fbcorr_plan_destroy(fbcorr_plan_t plan);
+
+/* out = {H', W', N}. */
+fbcorr_status_t fbcorr_plan_out_shape(fbcorr_plan_t plan, int64_t out[3]);
+
+/* Bytes of device workspace that forward and backward need (either pointer
+ * may be NULL).  Zero means the call accepts ws = NULL. */
+fbcorr_status_t fbcorr_plan_workspace_size(fbcorr_plan_t plan, size_t* fwd_bytes,
+                                           size_t* bwd_bytes);
+
+/* y = epi(corr(x, w)).  x, w, y: device pointers as above; ws: device
+ * workspace of at least the forward size (NULL allowed when it is zero).
+ * y must not alias x, w or ws. */
+fbcorr_status_t fbcorr_forward(fbcorr_plan_t plan, const float* x, const float* w, float* y,
+                               void* ws, size_t ws_bytes, fbcorr_stream_t stream);
+
+/* Gradients of L from g = dL/dy (shape of y):
+ *   dx[p][q][d]    = sum_{n,i,j} g~[p-i][q-j][n] * w[n][i][j][d]   (zero outside the output)
+ *   dw[n][i][j][d] = sum_{p,q}   g~[p][q][n]     * x[p+i][q+j][d]
+ * with g~ = g, or g masked to lo < y < hi when the plan's epilogue is CLAMP
+ * (then y_or_null must be the forward output; otherwise it is ignored).
+ * Either dx_or_null or dw_or_null may be NULL to skip that gradient.  The
+ * dw reduction is deterministic (fixed order, no atomics).  Always F32. */
+fbcorr_status_t fbcorr_backward(fbcorr_plan_t plan, const float* x, const float* w,
+                                const float* g, const float* y_or_null, float* dx_or_null,
+                                float* dw_or_null, void* ws, size_t ws_bytes,
+                                fbcorr_stream_t stream);
+
+/* Measure the candidate variants for this plan's shape on `stream` (CUDA
+ * events, the paper's coarse grid search of Sec. 6.2), keep the fastest, and
+ * record it in the tuning cache.  Synchronises the stream; not capturable. */
+fbcorr_status_t fbcorr_autotune(fbcorr_plan_t plan, fbcorr_stream_t stream);
+
+/* Force the forward variant: "default" (the prebuilt generic kernel),
+ * "heuristic", "tuned", or an explicit spec as printed by fbcorr_plan_info. */
+fbcorr_status_t fbcorr_plan_set_variant(fbcorr_plan_t plan, const char* spec);
+
+/* A one-line JSON description of the plan and its chosen variants, written
+ * into buf (NUL-terminated, truncated to cap bytes). */
+fbcorr_status_t fbcorr_plan_info(fbcorr_plan_t plan, char* buf, size_t cap);
+
+/* FBCORR_OK, or FBCORR_ERR_TIMEOUT once a kernel of this plan has given up a
+ * bounded wait (read from host-mapped memory; no synchronisation).  Clears
+ * the flag when `clear` is non-zero. */
+fbcorr_status_t fbcorr_plan_device_status(fbcorr_plan_t plan, int clear);
+
+/* ---- batches of uneven images ------------------------------------------- */
+
+/* A plan for n independent problems, image k with in_shapes[k] = {H, W, D}
+ * and its own bank filt_shapes[k] = {N, fh, fw, D}, all run by ONE persistent
+ * kernel launch (replayed from a CUDA graph) over a largest-first tile list. */
+fbcorr_status_t fbcorr_batch_plan_create(fbcorr_batch_plan_t* out, int n,
+                                         const int64_t (*in_shapes)[3],
+                                         const int64_t (*filt_shapes)[4], fbcorr_dtype_t dtype,
+                                         fbcorr_epilogue_t epilogue);
+fbcorr_status_t fbcorr_batch_plan_destroy(fbcorr_batch_plan_t plan);
+fbcorr_status_t fbcorr_batch_plan_workspace_size(fbcorr_batch_plan_t plan, size_t* bytes);
+fbcorr_status_t fbcorr_batch_plan_info(fbcorr_batch_plan_t plan, char* buf, size_t cap);
+
+/* x[k], w[k], y[k]: HOST arrays of n DEVICE pointers (image k's tensors). */
+fbcorr_status_t fbcorr_forward_batched(fbcorr_batch_plan_t plan, const float* const* x,
+                                       const float* const* w, float* const* y, void* ws,
+                                       size_t ws_bytes, fbcorr_stream_t stream);
+
+/* ---- diagnostics -------------------------------------------------------- */
+
+const char* fbcorr_status_string(fbcorr_status_t status);
+const char* fbcorr_last_error(void);
+/* Library version string, e.g. "fbcorr 0.1 sm_103a". */
+const char* fbcorr_version(void);
+
+/* Generate and compile (NVRTC, sm_103a) -- without loading or running -- the
+ * forward, dL/dx and dL/dw kernels that a plan of this shape would use, with
+ * the forward tile `spec` ("heuristic" or a "direct:..." spec).  Needs no GPU.
+ * On failure the NVRTC log is written into log (NUL-terminated, cap bytes). */
+fbcorr_status_t fbcorr_rtcg_check(const int64_t in_shape[3], const int64_t filt_shape[4],
+                                  fbcorr_epilogue_t epilogue, const char* spec, char* log,
+                                  size_t cap);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FBCORR_H */

@@ -1,0 +1,625 @@
+// api.cu -- the C ABI of libfbcorr: plan creation, variant selection,
+// forward / backward dispatch and the auto-tuner.
+//
+// Control flow mirrors the paper's RTCG loop (Sec. 3.1, Sec. 6.2): a plan
+// fixes the problem shape, code is generated and compiled for exactly that
+// shape (NVRTC, cached), candidates are timed when tuning is requested and the
+// winner is remembered per GPU and shape; the per-call path is then a single
+// prepared launch.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <sstream>
+
+#include "internal.h"
+
+namespace fbc {
+const char* last_error_message();
+}
+
+using namespace fbc;
+
+namespace {
+
+// Host mirrors of the NVRTC kernels' by-value argument structs (rtcg_direct.cuh).
+struct DirectArgsK {
+    const float* x;
+    const float* m;
+    const float* w;
+    float* y;
+    int in_h, in_w, out_h, out_w, nf;
+    int pad_y, pad_x;
+    float lo, hi;
+};
+struct DwArgsK {
+    const float* x;
+    const float* g;
+    const float* m;
+    float* part;
+    int H, W, Ho, Wo, N;
+    int rows_per_chunk;
+    float lo, hi;
+};
+
+const int64_t kMaxElems = (int64_t)1 << 31;
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+DirectProblem fwd_problem(const fbcorr_plan* p) {
+    DirectProblem pr;
+    pr.in_h = (int)p->H;
+    pr.in_w = (int)p->W;
+    pr.c = (int)p->D;
+    pr.out_h = (int)p->Ho;
+    pr.out_w = (int)p->Wo;
+    pr.nf = (int)p->N;
+    pr.fh = (int)p->fh;
+    pr.fw = (int)p->fw;
+    pr.pad_y = 0;
+    pr.pad_x = 0;
+    pr.flip = 0;
+    pr.epi = p->epi.kind == FBCORR_EPI_CLAMP ? 1 : 0;
+    pr.mask = 0;
+    return pr;
+}
+
+DirectProblem dx_problem(const fbcorr_plan* p) {
+    DirectProblem pr;
+    pr.in_h = (int)p->Ho;
+    pr.in_w = (int)p->Wo;
+    pr.c = (int)p->N;
+    pr.out_h = (int)p->H;
+    pr.out_w = (int)p->W;
+    pr.nf = (int)p->D;
+    pr.fh = (int)p->fh;
+    pr.fw = (int)p->fw;
+    pr.pad_y = (int)p->fh - 1;
+    pr.pad_x = (int)p->fw - 1;
+    pr.flip = 1;
+    pr.epi = 0;
+    pr.mask = p->epi.kind == FBCORR_EPI_CLAMP ? 1 : 0;
+    return pr;
+}
+
+std::string kname_for(const char* base, const DirectProblem& pr, const DirectTile& t) {
+    char b[160];
+    snprintf(b, sizeof b, "%s_f%dx%d_c%d_t%d_%d_%d_%d_fl%d_e%d_m%d", base, pr.fh, pr.fw, pr.c, t.tr,
+             t.tf, t.wr, t.wf, pr.flip, pr.epi, pr.mask);
+    return b;
+}
+
+size_t smem_limit(const DeviceInfo& dev) {
+    return std::min<size_t>(dev.smem_optin ? dev.smem_optin : 227 * 1024, 200 * 1024);
+}
+
+fbcorr_status_t build_direct(const DirectProblem& pr, const DirectTile& t, Kernel* k) {
+    const std::string name = kname_for("fbc_direct", pr, t);
+    const std::string src = direct_kernel_source(pr, t, name);
+    return rtcg_kernel(src, name, direct_smem_bytes(t, pr.fh, pr.fw, pr.c), t.threads(), k);
+}
+
+dim3 direct_grid(const DirectProblem& pr, const DirectTile& t) {
+    return dim3((unsigned)((pr.out_w + 31) / 32), (unsigned)((pr.out_h + t.bh() - 1) / t.bh()),
+                (unsigned)((pr.nf + t.bn() - 1) / t.bn()));
+}
+
+fbcorr_status_t run_direct(const Kernel& k, const DirectProblem& pr, const DirectTile& t,
+                           const float* x, const float* m, const float* w, float* y, float lo,
+                           float hi, cudaStream_t s) {
+    DirectArgsK a{x, m, w, y, pr.in_h, pr.in_w, pr.out_h, pr.out_w, pr.nf, pr.pad_y, pr.pad_x, lo, hi};
+    void* args[] = {&a};
+    return launch(k, direct_grid(pr, t), args, s);
+}
+
+fbcorr_status_t run_default(const DirectProblem& pr, const float* x, const float* m,
+                            const float* w, float* y, float lo, float hi, cudaStream_t s) {
+    DirectArgsRT a{x, m, w, y, pr.in_h, pr.in_w, pr.c, pr.out_h, pr.out_w, pr.nf, pr.fh, pr.fw,
+                   pr.pad_y, pr.pad_x, pr.flip, pr.epi, pr.mask, lo, hi};
+    FBC_CUDA(launch_default_direct(a, s));
+    return FBCORR_OK;
+}
+
+const char* kind_name(VarKind k) {
+    switch (k) {
+        case VarKind::Default: return "default";
+        case VarKind::Direct: return "direct";
+        case VarKind::Tensor: return "tcgen05";
+    }
+    return "?";
+}
+
+std::string shape_key(const fbcorr_plan* p, const char* what) {
+    std::ostringstream o;
+    o << what << "|x" << p->H << "x" << p->W << "x" << p->D << "|w" << p->N << "x" << p->fh << "x"
+      << p->fw << "|dt" << (int)p->dtype << "|epi" << p->epi.kind;
+    return o.str();
+}
+
+// Select the forward variant of an F32 plan from a spec string.
+fbcorr_status_t set_fwd_spec(fbcorr_plan* p, const std::string& spec, const char* source) {
+    if (spec == "default") {
+        p->fwd_kind = VarKind::Default;
+        p->fwd_kernel = Kernel{};
+        p->fwd_source = source;
+        return FBCORR_OK;
+    }
+    DirectTile t;
+    if (!parse_direct_spec(spec, &t))
+        return set_error(FBCORR_ERR_INVALID_ARG, "unknown variant spec '%s'", spec.c_str());
+    const DirectProblem pr = fwd_problem(p);
+    if (direct_smem_bytes(t, pr.fh, pr.fw, pr.c) > smem_limit(p->dev))
+        return set_error(FBCORR_ERR_UNSUPPORTED, "variant %s needs too much shared memory",
+                         spec.c_str());
+    Kernel k;
+    FBC_TRY(build_direct(pr, t, &k));
+    p->fwd_kind = VarKind::Direct;
+    p->fwd_tile = t;
+    p->fwd_kernel = k;
+    p->fwd_source = source;
+    return FBCORR_OK;
+}
+
+fbcorr_status_t choose_fwd_f32(fbcorr_plan* p) {
+    const std::string env = env_str("FBCORR_VARIANT", "");
+    if (!env.empty()) {
+        fbcorr_status_t s = set_fwd_spec(p, env, "env");
+        if (s == FBCORR_OK) return s;
+        logf("FBCORR_VARIANT=%s not usable (%s); continuing", env.c_str(), last_error_message());
+    }
+    std::string cached;
+    if (tune_lookup(tune_key(p->dev, shape_key(p, "fwd")), &cached)) {
+        if (set_fwd_spec(p, cached, "cache") == FBCORR_OK) return FBCORR_OK;
+        logf("tune-cache entry '%s' not usable; ignoring it", cached.c_str());
+    }
+    const DirectProblem pr = fwd_problem(p);
+    const DirectTile t = direct_heuristic(pr, smem_limit(p->dev), p->dev.sm_count);
+    fbcorr_status_t s = set_fwd_spec(p, direct_tile_spec(t), "heuristic");
+    if (s == FBCORR_ERR_NVRTC) {
+        logf("code generation failed, falling back to the prebuilt default kernel: %s",
+             last_error_message());
+        return set_fwd_spec(p, "default", "fallback");
+    }
+    return s;
+}
+
+fbcorr_status_t prepare_backward(fbcorr_plan* p) {
+    if (p->bwd_ready) return FBCORR_OK;
+    const DirectProblem pr = dx_problem(p);
+    const DirectTile t = direct_heuristic(pr, smem_limit(p->dev), p->dev.sm_count);
+    Kernel k;
+    fbcorr_status_t s = build_direct(pr, t, &k);
+    if (s == FBCORR_OK) {
+        p->dx_kind = VarKind::Direct;
+        p->dx_tile = t;
+        p->dx_kernel = k;
+    } else if (s == FBCORR_ERR_NVRTC) {
+        p->dx_kind = VarKind::Default;
+    } else {
+        return s;
+    }
+    const int mask = p->epi.kind == FBCORR_EPI_CLAMP ? 1 : 0;
+    char name[128];
+    snprintf(name, sizeof name, "fbc_dw_f%dx%d_c%d_n%d_m%d", (int)p->fh, (int)p->fw, (int)p->D,
+             p->dw_tn, mask);
+    s = rtcg_kernel(dw_kernel_source((int)p->fh, (int)p->fw, (int)p->D, p->dw_tn, mask, name), name,
+                    0, 128, &p->dw_kernel);
+    if (s == FBCORR_OK)
+        p->dw_kind = VarKind::Direct;
+    else if (s == FBCORR_ERR_NVRTC)
+        p->dw_kind = VarKind::Default;
+    else
+        return s;
+    p->bwd_ready = true;
+    return FBCORR_OK;
+}
+
+void plan_dw_chunks(fbcorr_plan* p) {
+    // enough CTAs for two waves of the partial-sum kernel, deterministic in the shape
+    const long pairs = ((p->N + p->dw_tn - 1) / p->dw_tn) * p->D;
+    const long zgroups = (pairs + 127) / 128;
+    long want = (2L * std::max(1, p->dev.sm_count) + p->fh * zgroups - 1) / (p->fh * zgroups);
+    want = std::max(1L, std::min<long>(want, std::min<long>(p->Ho, 128)));
+    p->dw_rows_per_chunk = (int)((p->Ho + want - 1) / want);
+    p->dw_chunks = (int)((p->Ho + p->dw_rows_per_chunk - 1) / p->dw_rows_per_chunk);
+    p->ws_bwd = (size_t)p->dw_chunks * p->N * p->fh * p->fw * p->D * sizeof(float);
+}
+
+fbcorr_status_t validate_shapes(const int64_t* in, const int64_t* fs, fbcorr_dtype_t dtype,
+                                const fbcorr_epilogue_t& epi) {
+    if (!in || !fs) return set_error(FBCORR_ERR_INVALID_ARG, "null shape array");
+    if (dtype != FBCORR_F32 && dtype != FBCORR_BF16 && dtype != FBCORR_BF16X3)
+        return set_error(FBCORR_ERR_INVALID_ARG, "unknown dtype %d", (int)dtype);
+    if (epi.kind != FBCORR_EPI_NONE && epi.kind != FBCORR_EPI_CLAMP)
+        return set_error(FBCORR_ERR_INVALID_ARG, "unknown epilogue kind %d", epi.kind);
+    if (epi.kind == FBCORR_EPI_CLAMP && !(epi.lo <= epi.hi))
+        return set_error(FBCORR_ERR_INVALID_ARG, "clamp needs lo <= hi (got %g, %g)", epi.lo, epi.hi);
+    const int64_t H = in[0], W = in[1], D = in[2], N = fs[0], fh = fs[1], fw = fs[2], Dw = fs[3];
+    if (H <= 0 || W <= 0 || D <= 0 || N <= 0 || fh <= 0 || fw <= 0 || Dw <= 0)
+        return set_error(FBCORR_ERR_SHAPE, "every dimension must be positive");
+    if (Dw != D) return set_error(FBCORR_ERR_SHAPE, "filter depth %lld != input depth %lld",
+                                  (long long)Dw, (long long)D);
+    if (fh > H || fw > W)
+        return set_error(FBCORR_ERR_SHAPE, "filter %lldx%lld larger than input %lldx%lld",
+                         (long long)fh, (long long)fw, (long long)H, (long long)W);
+    const int64_t Ho = H - fh + 1, Wo = W - fw + 1;
+    if (H > (1 << 20) || W > (1 << 20) || D > 4096 || N > 65535 || fh > 64 || fw > 64 ||
+        H * W * D >= kMaxElems || Ho * Wo * N >= kMaxElems || N * fh * fw * D >= kMaxElems)
+        return set_error(FBCORR_ERR_SHAPE, "shape exceeds the supported index range");
+    return FBCORR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fbcorr_status_t fbcorr_plan_create(fbcorr_plan_t* out, const int64_t in_shape[3],
+                                   const int64_t filt_shape[4], fbcorr_dtype_t dtype,
+                                   fbcorr_epilogue_t epilogue) {
+    clear_error();
+    if (!out) return set_error(FBCORR_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    FBC_TRY(validate_shapes(in_shape, filt_shape, dtype, epilogue));
+    DeviceInfo dev;
+    FBC_TRY(device_info(&dev));
+    if (dev.cc_major != 10 || dev.cc_minor != 3)
+        return set_error(FBCORR_ERR_UNSUPPORTED,
+                         "libfbcorr is built for sm_103a (GB300); device %d is %s (cc %d.%d)",
+                         dev.device, dev.name, dev.cc_major, dev.cc_minor);
+    fbcorr_plan* p = new (std::nothrow) fbcorr_plan();
+    if (!p) return set_error(FBCORR_ERR_OOM, "host allocation failed");
+    p->H = in_shape[0];
+    p->W = in_shape[1];
+    p->D = in_shape[2];
+    p->N = filt_shape[0];
+    p->fh = filt_shape[1];
+    p->fw = filt_shape[2];
+    p->Ho = p->H - p->fh + 1;
+    p->Wo = p->W - p->fw + 1;
+    p->dtype = dtype;
+    p->epi = epilogue;
+    if (p->epi.kind == FBCORR_EPI_NONE) p->epi.lo = p->epi.hi = 0.f;
+    p->dev = dev;
+
+    fbcorr_status_t s = FBCORR_OK;
+    if (cudaHostAlloc((void**)&p->err_host, sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer((void**)&p->err_dev, p->err_host, 0) != cudaSuccess) {
+        cudaGetLastError();
+        s = set_error(FBCORR_ERR_OOM, "mapped host allocation for the error word failed");
+    } else {
+        *p->err_host = 0;
+    }
+    if (s == FBCORR_OK) {
+        if (dtype == FBCORR_F32) {
+            s = choose_fwd_f32(p);
+        } else {
+            p->fwd_kind = VarKind::Tensor;
+            p->fwd_source = "fixed";
+            s = tc_plan_create(&p->tc, (int)p->H, (int)p->W, (int)p->D, (int)p->N, (int)p->fh,
+                               (int)p->fw, dtype == FBCORR_BF16X3 ? 1 : 0,
+                               p->epi.kind == FBCORR_EPI_CLAMP ? 1 : 0, p->epi.lo, p->epi.hi, dev);
+            if (s == FBCORR_OK) p->ws_fwd = tc_workspace_bytes(p->tc);
+        }
+    }
+    if (s == FBCORR_OK) plan_dw_chunks(p);
+    if (s != FBCORR_OK) {
+        fbcorr_plan_destroy(p);
+        return s;
+    }
+    const std::string at = env_str("FBCORR_AUTOTUNE", "0");
+    if (dtype == FBCORR_F32 && (at == "force" || (at == "1" && p->fwd_source == "heuristic"))) {
+        s = fbcorr_autotune(p, nullptr);
+        if (s != FBCORR_OK) {
+            fbcorr_plan_destroy(p);
+            return s;
+        }
+    }
+    logf("plan %lldx%lldx%lld * %lldx%lldx%lldx%lld dtype=%d: fwd=%s (%s)", (long long)p->H,
+         (long long)p->W, (long long)p->D, (long long)p->N, (long long)p->fh, (long long)p->fw,
+         (long long)p->D, (int)dtype, kind_name(p->fwd_kind), p->fwd_source.c_str());
+    *out = p;
+    return FBCORR_OK;
+}
+
+fbcorr_status_t fbcorr_plan_destroy(fbcorr_plan_t p) {
+    clear_error();
+    if (!p) return FBCORR_OK;
+    if (p->tc) tc_plan_destroy(p->tc);
+    if (p->err_host) cudaFreeHost(p->err_host);
+    delete p;
+    return FBCORR_OK;
+}
+
+fbcorr_status_t fbcorr_plan_out_shape(fbcorr_plan_t p, int64_t out[3]) {
+    clear_error();
+    if (!p || !out) return set_error(FBCORR_ERR_INVALID_ARG, "NULL argument");
+    out[0] = p->Ho;
+    out[1] = p->Wo;
+    out[2] = p->N;
+    return FBCORR_OK;
+}
+
+fbcorr_status_t fbcorr_plan_workspace_size(fbcorr_plan_t p, size_t* fwd, size_t* bwd) {
+    clear_error();
+    if (!p) return set_error(FBCORR_ERR_INVALID_ARG, "NULL plan");
+    if (fwd) *fwd = p->ws_fwd;
+    if (bwd) *bwd = p->ws_bwd;
+    return FBCORR_OK;
+}
+
+fbcorr_status_t fbcorr_forward(fbcorr_plan_t p, const float* x, const float* w, float* y, void* ws,
+                               size_t ws_bytes, fbcorr_stream_t stream) {
+    clear_error();
+    if (!p || !x || !w || !y) return set_error(FBCORR_ERR_INVALID_ARG, "NULL argument");
+    if (!aligned16(x) || !aligned16(w) || !aligned16(y))
+        return set_error(FBCORR_ERR_ALIGNMENT, "x, w and y must be 16-byte aligned");
+    if (p->ws_fwd > 0 && (!ws || ws_bytes < p->ws_fwd || !aligned16(ws)))
+        return set_error(FBCORR_ERR_WORKSPACE, "forward needs %zu bytes of aligned workspace (got %zu)",
+                         p->ws_fwd, ws ? ws_bytes : (size_t)0);
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (p->fwd_kind) {
+        case VarKind::Direct:
+            return run_direct(p->fwd_kernel, fwd_problem(p), p->fwd_tile, x, nullptr, w, y,
+                              p->epi.lo, p->epi.hi, s);
+        case VarKind::Default:
+            return run_default(fwd_problem(p), x, nullptr, w, y, p->epi.lo, p->epi.hi, s);
+        case VarKind::Tensor:
+            return tc_forward(p->tc, x, w, y, ws, p->err_dev, s);
+    }
+    return set_error(FBCORR_ERR_INTERNAL, "bad variant kind");
+}
+
+fbcorr_status_t fbcorr_backward(fbcorr_plan_t p, const float* x, const float* w, const float* g,
+                                const float* y, float* dx, float* dw, void* ws, size_t ws_bytes,
+                                fbcorr_stream_t stream) {
+    clear_error();
+    if (!p || !g) return set_error(FBCORR_ERR_INVALID_ARG, "NULL plan or gradient");
+    if (dw && !x) return set_error(FBCORR_ERR_INVALID_ARG, "dw needs x");
+    if (dx && !w) return set_error(FBCORR_ERR_INVALID_ARG, "dx needs w");
+    const bool clamp = p->epi.kind == FBCORR_EPI_CLAMP;
+    if (clamp && !y) return set_error(FBCORR_ERR_INVALID_ARG, "a clamp epilogue needs y for its mask");
+    const void* ptrs[] = {x, w, g, clamp ? y : nullptr, dx, dw};
+    for (const void* q : ptrs)
+        if (q && !aligned16(q)) return set_error(FBCORR_ERR_ALIGNMENT, "tensors must be 16-byte aligned");
+    if (!dx && !dw) return FBCORR_OK;
+    if (dw && (!ws || ws_bytes < p->ws_bwd || !aligned16(ws)))
+        return set_error(FBCORR_ERR_WORKSPACE, "backward needs %zu bytes of aligned workspace (got %zu)",
+                         p->ws_bwd, ws ? ws_bytes : (size_t)0);
+    FBC_TRY(prepare_backward(p));
+    cudaStream_t s = (cudaStream_t)stream;
+    const float* m = clamp ? y : nullptr;
+    if (dx) {
+        const DirectProblem pr = dx_problem(p);
+        if (p->dx_kind == VarKind::Direct)
+            FBC_TRY(run_direct(p->dx_kernel, pr, p->dx_tile, g, m, w, dx, p->epi.lo, p->epi.hi, s));
+        else
+            FBC_TRY(run_default(pr, g, m, w, dx, p->epi.lo, p->epi.hi, s));
+    }
+    if (dw) {
+        float* part = (float*)ws;
+        if (p->dw_kind == VarKind::Direct) {
+            DwArgsK a{x, g, m ? m : g, part, (int)p->H, (int)p->W, (int)p->Ho, (int)p->Wo, (int)p->N,
+                      p->dw_rows_per_chunk, p->epi.lo, p->epi.hi};
+            void* args[] = {&a};
+            const long pairs = ((p->N + p->dw_tn - 1) / p->dw_tn) * p->D;
+            dim3 grid((unsigned)p->dw_chunks, (unsigned)p->fh, (unsigned)((pairs + 127) / 128));
+            FBC_TRY(launch(p->dw_kernel, grid, args, s));
+        } else {
+            FBC_CUDA(launch_default_dw(x, g, m ? m : g, part, (int)p->H, (int)p->W, (int)p->D,
+                                       (int)p->Ho, (int)p->Wo, (int)p->N, (int)p->fh, (int)p->fw,
+                                       p->dw_chunks, p->dw_rows_per_chunk, clamp ? 1 : 0, p->epi.lo,
+                                       p->epi.hi, s));
+        }
+        FBC_CUDA(launch_dw_reduce(part, dw, p->dw_chunks, (long long)p->N * p->fh * p->fw * p->D, s));
+    }
+    return FBCORR_OK;
+}
+
+fbcorr_status_t fbcorr_plan_set_variant(fbcorr_plan_t p, const char* spec) {
+    clear_error();
+    if (!p || !spec) return set_error(FBCORR_ERR_INVALID_ARG, "NULL argument");
+    if (p->dtype != FBCORR_F32)
+        return set_error(FBCORR_ERR_UNSUPPORTED, "tensor-core plans have a single variant");
+    const std::string s = spec;
+    if (s == "heuristic") {
+        const DirectTile t = direct_heuristic(fwd_problem(p), smem_limit(p->dev), p->dev.sm_count);
+        return set_fwd_spec(p, direct_tile_spec(t), "heuristic");
+    }
+    if (s == "tuned") return fbcorr_autotune(p, nullptr);
+    return set_fwd_spec(p, s, "forced");
+}
+
+fbcorr_status_t fbcorr_autotune(fbcorr_plan_t p, fbcorr_stream_t stream) {
+    clear_error();
+    if (!p) return set_error(FBCORR_ERR_INVALID_ARG, "NULL plan");
+    if (p->dtype != FBCORR_F32) return FBCORR_OK;   // one tensor-core variant per plan
+    cudaStream_t s = (cudaStream_t)stream;
+    const DirectProblem pr = fwd_problem(p);
+    // Candidate set: the analytic model's ranking, top K plus the default kernel.
+    std::vector<DirectTile> cands = direct_candidates(pr, smem_limit(p->dev));
+    const DirectTile h = direct_heuristic(pr, smem_limit(p->dev), p->dev.sm_count);
+    int topk = atoi(env_str("FBCORR_TUNE_TOPK", "12").c_str());
+    if (topk < 1) topk = 1;
+    // order: heuristic first, then by a cheap proxy (larger register blocks first)
+    std::stable_sort(cands.begin(), cands.end(), [](const DirectTile& a, const DirectTile& b) {
+        return a.tr * a.tf * 100 + a.threads() > b.tr * b.tf * 100 + b.threads();
+    });
+    std::vector<std::string> specs = {direct_tile_spec(h)};
+    for (auto& t : cands) {
+        const std::string sp = direct_tile_spec(t);
+        if ((int)specs.size() >= topk) break;
+        if (std::find(specs.begin(), specs.end(), sp) == specs.end()) specs.push_back(sp);
+    }
+    specs.push_back("default");
+
+    float *x = nullptr, *w = nullptr, *y = nullptr;
+    const size_t xb = (size_t)p->H * p->W * p->D * 4, wb = (size_t)p->N * p->fh * p->fw * p->D * 4,
+                 yb = (size_t)p->Ho * p->Wo * p->N * 4;
+    FBC_CUDA(cudaMalloc(&x, xb));
+    if (cudaMalloc(&w, wb) != cudaSuccess || cudaMalloc(&y, yb) != cudaSuccess) {
+        cudaFree(x);
+        cudaFree(w);
+        return set_error(FBCORR_ERR_OOM, "autotune buffers");
+    }
+    cudaMemsetAsync(x, 0, xb, s);
+    cudaMemsetAsync(w, 0, wb, s);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    std::string best_spec;
+    float best_ms = 1e30f;
+    std::ostringstream report;
+    const VarKind old_kind = p->fwd_kind;
+    const DirectTile old_tile = p->fwd_tile;
+    const Kernel old_kernel = p->fwd_kernel;
+    const std::string old_source = p->fwd_source;
+    fbcorr_status_t status = FBCORR_OK;
+    for (const auto& sp : specs) {
+        if (set_fwd_spec(p, sp, "tuning") != FBCORR_OK) continue;
+        std::vector<float> ms_list;
+        bool ok = true;
+        for (int r = 0; r < 2 && ok; ++r)
+            ok = fbcorr_forward(p, x, w, y, nullptr, 0, stream) == FBCORR_OK;
+        for (int r = 0; r < 7 && ok; ++r) {
+            cudaEventRecord(e0, s);
+            ok = fbcorr_forward(p, x, w, y, nullptr, 0, stream) == FBCORR_OK;
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) ok = false;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms_list.push_back(ms);
+        }
+        if (!ok) {
+            status = set_error(FBCORR_ERR_CUDA, "autotune run of %s failed", sp.c_str());
+            break;
+        }
+        std::sort(ms_list.begin(), ms_list.end());
+        const float med = ms_list[ms_list.size() / 2];
+        report << sp << "=" << med << "ms;";
+        logf("autotune %s: %.4f ms", sp.c_str(), med);
+        if (med < best_ms) {
+            best_ms = med;
+            best_spec = sp;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(x);
+    cudaFree(w);
+    cudaFree(y);
+    if (status != FBCORR_OK || best_spec.empty()) {
+        p->fwd_kind = old_kind;
+        p->fwd_tile = old_tile;
+        p->fwd_kernel = old_kernel;
+        p->fwd_source = old_source;
+        return status != FBCORR_OK ? status : set_error(FBCORR_ERR_INTERNAL, "no variant ran");
+    }
+    FBC_TRY(set_fwd_spec(p, best_spec, "tuned"));
+    tune_store(tune_key(p->dev, shape_key(p, "fwd")), best_spec);
+    logf("autotune picked %s (%.4f ms); %s", best_spec.c_str(), best_ms, report.str().c_str());
+    return FBCORR_OK;
+}
+
+fbcorr_status_t fbcorr_plan_info(fbcorr_plan_t p, char* buf, size_t cap) {
+    clear_error();
+    if (!p || !buf || cap == 0) return set_error(FBCORR_ERR_INVALID_ARG, "NULL argument");
+    std::ostringstream o;
+    o << "{\"in\":[" << p->H << "," << p->W << "," << p->D << "],\"filt\":[" << p->N << "," << p->fh
+      << "," << p->fw << "," << p->D << "],\"out\":[" << p->Ho << "," << p->Wo << "," << p->N
+      << "],\"dtype\":" << (int)p->dtype << ",\"epilogue\":" << p->epi.kind << ",\"fwd\":{\"kind\":\""
+      << kind_name(p->fwd_kind) << "\",\"source\":\"" << p->fwd_source << "\"";
+    if (p->fwd_kind == VarKind::Direct) {
+        o << ",\"spec\":\"" << direct_tile_spec(p->fwd_tile) << "\",\"smem\":" << p->fwd_kernel.smem
+          << ",\"threads\":" << p->fwd_kernel.threads << ",\"kernel\":\"" << p->fwd_kernel.name << "\"";
+    } else if (p->fwd_kind == VarKind::Default) {
+        o << ",\"spec\":\"default\"";
+    } else if (p->tc) {
+        o << ",\"spec\":\"" << tc_describe(p->tc) << "\"";
+    }
+    o << "},\"bwd_ready\":" << (p->bwd_ready ? 1 : 0);
+    if (p->bwd_ready) {
+        o << ",\"dx\":{\"kind\":\"" << kind_name(p->dx_kind) << "\"";
+        if (p->dx_kind == VarKind::Direct) o << ",\"spec\":\"" << direct_tile_spec(p->dx_tile) << "\"";
+        o << "},\"dw\":{\"kind\":\"" << kind_name(p->dw_kind) << "\",\"chunks\":" << p->dw_chunks
+          << ",\"rows_per_chunk\":" << p->dw_rows_per_chunk << "}";
+    }
+    o << ",\"ws_fwd\":" << p->ws_fwd << ",\"ws_bwd\":" << p->ws_bwd << ",\"sm_count\":"
+      << p->dev.sm_count << "}";
+    const std::string s = o.str();
+    snprintf(buf, cap, "%s", s.c_str());
+    return FBCORR_OK;
+}
+
+fbcorr_status_t fbcorr_plan_device_status(fbcorr_plan_t p, int clear) {
+    clear_error();
+    if (!p) return set_error(FBCORR_ERR_INVALID_ARG, "NULL plan");
+    const int v = p->err_host ? *(volatile int*)p->err_host : 0;
+    if (clear && p->err_host) *(volatile int*)p->err_host = 0;
+    if (v != 0) return set_error(FBCORR_ERR_TIMEOUT, "a kernel gave up a bounded wait (code %d)", v);
+    return FBCORR_OK;
+}
+
+const char* fbcorr_status_string(fbcorr_status_t s) {
+    switch (s) {
+        case FBCORR_OK: return "FBCORR_OK";
+        case FBCORR_ERR_INVALID_ARG: return "FBCORR_ERR_INVALID_ARG";
+        case FBCORR_ERR_SHAPE: return "FBCORR_ERR_SHAPE";
+        case FBCORR_ERR_UNSUPPORTED: return "FBCORR_ERR_UNSUPPORTED";
+        case FBCORR_ERR_ALIGNMENT: return "FBCORR_ERR_ALIGNMENT";
+        case FBCORR_ERR_WORKSPACE: return "FBCORR_ERR_WORKSPACE";
+        case FBCORR_ERR_CUDA: return "FBCORR_ERR_CUDA";
+        case FBCORR_ERR_NVRTC: return "FBCORR_ERR_NVRTC";
+        case FBCORR_ERR_OOM: return "FBCORR_ERR_OOM";
+        case FBCORR_ERR_TIMEOUT: return "FBCORR_ERR_TIMEOUT";
+        case FBCORR_ERR_INTERNAL: return "FBCORR_ERR_INTERNAL";
+    }
+    return "FBCORR_ERR_UNKNOWN";
+}
+
+const char* fbcorr_last_error(void) { return last_error_message(); }
+
+const char* fbcorr_version(void) { return "fbcorr 0.1 sm_103a"; }
+
+fbcorr_status_t fbcorr_rtcg_check(const int64_t in_shape[3], const int64_t filt_shape[4],
+                                  fbcorr_epilogue_t epilogue, const char* spec, char* log,
+                                  size_t cap) {
+    clear_error();
+    if (log && cap) log[0] = '\0';
+    FBC_TRY(validate_shapes(in_shape, filt_shape, FBCORR_F32, epilogue));
+    fbcorr_plan tmp;
+    tmp.H = in_shape[0];
+    tmp.W = in_shape[1];
+    tmp.D = in_shape[2];
+    tmp.N = filt_shape[0];
+    tmp.fh = filt_shape[1];
+    tmp.fw = filt_shape[2];
+    tmp.Ho = tmp.H - tmp.fh + 1;
+    tmp.Wo = tmp.W - tmp.fw + 1;
+    tmp.epi = epilogue;
+    const size_t lim = 200 * 1024;
+    const DirectProblem fp = fwd_problem(&tmp), bp = dx_problem(&tmp);
+    DirectTile t;
+    const std::string sp = spec ? spec : "heuristic";
+    if (sp == "heuristic")
+        t = direct_heuristic(fp, lim, 148);
+    else if (!parse_direct_spec(sp, &t))
+        return set_error(FBCORR_ERR_INVALID_ARG, "unknown variant spec '%s'", sp.c_str());
+    const DirectTile tb = direct_heuristic(bp, lim, 148);
+    const int mask = epilogue.kind == FBCORR_EPI_CLAMP ? 1 : 0;
+    const std::string srcs[3] = {
+        direct_kernel_source(fp, t, kname_for("fbc_direct", fp, t)),
+        direct_kernel_source(bp, tb, kname_for("fbc_direct", bp, tb)),
+        dw_kernel_source((int)tmp.fh, (int)tmp.fw, (int)tmp.D, 4, mask, "fbc_dw_check")};
+    for (const auto& src : srcs) {
+        std::string lg;
+        fbcorr_status_t s = rtcg_compile_only(src, &lg);
+        if (s != FBCORR_OK) {
+            if (log && cap) snprintf(log, cap, "%s", lg.c_str());
+            return s;
+        }
+    }
+    return FBCORR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,161 @@
+// internal.h -- shared declarations of the libfbcorr host code (not installed).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "fbcorr.h"
+
+namespace fbc {
+
+// ---- errors -----------------------------------------------------------------
+fbcorr_status_t set_error(fbcorr_status_t s, const char* fmt, ...);
+void clear_error();
+
+#define FBC_CUDA(call)                                                                      \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return ::fbc::set_error(FBCORR_ERR_CUDA, "%s failed: %s (%s:%d)", #call,         \
+                                    cudaGetErrorString(e_), __FILE__, __LINE__);            \
+    } while (0)
+
+#define FBC_TRY(expr)                                                                       \
+    do {                                                                                    \
+        fbcorr_status_t s_ = (expr);                                                        \
+        if (s_ != FBCORR_OK) return s_;                                                     \
+    } while (0)
+
+// ---- environment knobs -------------------------------------------------------
+std::string env_str(const char* name, const char* dflt = "");
+bool log_enabled();
+void logf(const char* fmt, ...);
+bool fault_injected(const char* what);   // FBCORR_FAULT contains `what`
+std::string cache_dir();                  // FBCORR_CACHE_DIR or ~/.cache/fbcorr
+
+// ---- device facts ------------------------------------------------------------
+struct DeviceInfo {
+    int device = -1;
+    int sm_count = 0;
+    int cc_major = 0, cc_minor = 0;
+    size_t smem_optin = 0;
+    int driver_version = 0;
+    char name[256] = {0};
+};
+fbcorr_status_t device_info(DeviceInfo* out);
+
+// ---- run-time code generation (NVRTC -> cubin -> driver module) --------------
+struct Kernel {
+    CUfunction fn = nullptr;
+    int threads = 0;
+    size_t smem = 0;
+    std::string name;
+};
+
+// Compile `src` (with `name` as the extern "C" kernel) for sm_103a, using the
+// on-disk cubin cache, load it into the current context and return a handle.
+fbcorr_status_t rtcg_kernel(const std::string& src, const std::string& name, size_t smem,
+                            int threads, Kernel* out);
+// Compile only (no GPU needed); returns the NVRTC log on failure.
+fbcorr_status_t rtcg_compile_only(const std::string& src, std::string* log);
+fbcorr_status_t launch(const Kernel& k, dim3 grid, void** args, cudaStream_t stream);
+const char* rtcg_header_source();   // contents of rtcg_direct.cuh
+
+// ---- variants ------------------------------------------------------------------
+enum class VarKind { Default = 0, Direct = 1, Tensor = 2 };
+
+struct DirectTile {
+    int tr = 8, tf = 8, wr = 1, wf = 2;
+    int bh() const { return tr * wr; }
+    int bn() const { return tf * wf; }
+    int threads() const { return 32 * wr * wf; }
+};
+size_t direct_smem_bytes(const DirectTile& t, int fh, int fw, int c);
+std::string direct_tile_spec(const DirectTile& t);
+bool parse_direct_spec(const std::string& s, DirectTile* t);
+
+// A direct-correlation problem in kernel terms (forward or dL/dx).
+struct DirectProblem {
+    int in_h, in_w, c;        // input extents and channels
+    int out_h, out_w, nf;     // output extents and channels
+    int fh, fw;
+    int pad_y, pad_x;
+    int flip, epi, mask;
+};
+std::string direct_kernel_source(const DirectProblem& pr, const DirectTile& t,
+                                 const std::string& kname);
+std::vector<DirectTile> direct_candidates(const DirectProblem& pr, size_t smem_limit);
+DirectTile direct_heuristic(const DirectProblem& pr, size_t smem_limit, int sm_count);
+
+struct DwTile {
+    int tn = 4, threads = 128, chunks = 0;   // chunks = 0: choose from the SM count
+};
+std::string dw_kernel_source(int fh, int fw, int c, int tn, int mask, const std::string& kname);
+
+// prebuilt (nvcc) kernels, launchers defined in default_kernels.cu
+struct DirectArgsRT {
+    const float* x;
+    const float* m;
+    const float* w;
+    float* y;
+    int in_h, in_w, c, out_h, out_w, nf, fh, fw, pad_y, pad_x, flip, epi, mask;
+    float lo, hi;
+};
+cudaError_t launch_default_direct(const DirectArgsRT& a, cudaStream_t s);
+cudaError_t launch_default_dw(const float* x, const float* g, const float* m, float* part,
+                              int H, int W, int C, int Ho, int Wo, int N, int fh, int fw,
+                              int chunks, int rows_per_chunk, int mask, float lo, float hi,
+                              cudaStream_t s);
+cudaError_t launch_dw_reduce(const float* part, float* dw, int S, long long E, cudaStream_t s);
+
+// ---- tensor-core path (tc_kernel.cu) -----------------------------------------------
+struct TcPlan;   // opaque
+fbcorr_status_t tc_plan_create(TcPlan** out, int H, int W, int D, int N, int fh, int fw,
+                               int split, int epi, float lo, float hi, const DeviceInfo& dev);
+void tc_plan_destroy(TcPlan* p);
+size_t tc_workspace_bytes(const TcPlan* p);
+fbcorr_status_t tc_forward(TcPlan* p, const float* x, const float* w, float* y, void* ws,
+                           int* err_word, cudaStream_t s);
+std::string tc_describe(const TcPlan* p);
+
+// ---- tune cache ----------------------------------------------------------------------
+std::string tune_key(const DeviceInfo& dev, const std::string& what);
+bool tune_lookup(const std::string& key, std::string* value);
+void tune_store(const std::string& key, const std::string& value);
+
+}  // namespace fbc
+
+// ---- the plan object ------------------------------------------------------------------
+struct fbcorr_plan {
+    int64_t H = 0, W = 0, D = 0, N = 0, fh = 0, fw = 0, Ho = 0, Wo = 0;
+    fbcorr_dtype_t dtype = FBCORR_F32;
+    fbcorr_epilogue_t epi{0, 0.f, 0.f};
+    fbc::DeviceInfo dev;
+
+    // forward
+    fbc::VarKind fwd_kind = fbc::VarKind::Direct;
+    fbc::DirectTile fwd_tile;
+    fbc::Kernel fwd_kernel;
+    std::string fwd_source;        // "heuristic", "tuned", "cache", "env", "forced"
+    fbc::TcPlan* tc = nullptr;
+
+    // backward (F32 always)
+    bool bwd_ready = false;
+    fbc::VarKind dx_kind = fbc::VarKind::Direct;
+    fbc::DirectTile dx_tile;
+    fbc::Kernel dx_kernel;
+    fbc::VarKind dw_kind = fbc::VarKind::Direct;
+    fbc::Kernel dw_kernel;
+    int dw_tn = 4, dw_chunks = 1, dw_rows_per_chunk = 1;
+
+    size_t ws_fwd = 0, ws_bwd = 0;
+
+    // bounded-wait failure flag in host-mapped memory
+    int* err_host = nullptr;
+    int* err_dev = nullptr;
+};

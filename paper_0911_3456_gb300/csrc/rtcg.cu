@@ -1,0 +1,271 @@
+// rtcg.cu -- run-time code generation: NVRTC compile for sm_103a, an on-disk
+// cubin cache, and module loading through the CUDA driver API.
+//
+// The paper builds its kernels from source strings at run time and caches the
+// binaries in a "semi-permanent" compiler cache keyed on the hardware/software
+// environment, recompiling only when that changes (Sec. 4, Fig. 2).  Here the
+// cache key is a hash of the full source, the NVRTC options, the NVRTC
+// version and the target architecture; the file is written atomically
+// (temporary file + rename) so that concurrent processes never read a torn
+// binary.  Driver entry points are resolved through the runtime, so the
+// library does not link libcuda and still loads on machines without a GPU.
+#include <nvrtc.h>
+#include <sys/stat.h>
+#include <unistd.h>
+
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+
+#include "internal.h"
+
+namespace fbc {
+
+namespace {
+
+struct DriverApi {
+    bool ok = false;
+    CUresult (*moduleLoadData)(CUmodule*, const void*) = nullptr;
+    CUresult (*moduleGetFunction)(CUfunction*, CUmodule, const char*) = nullptr;
+    CUresult (*funcSetAttribute)(CUfunction, CUfunction_attribute, int) = nullptr;
+    CUresult (*launchKernel)(CUfunction, unsigned, unsigned, unsigned, unsigned, unsigned,
+                             unsigned, unsigned, CUstream, void**, void**) = nullptr;
+    CUresult (*ctxGetCurrent)(CUcontext*) = nullptr;
+    CUresult (*getErrorString)(CUresult, const char**) = nullptr;
+};
+
+std::mutex g_mu;
+DriverApi g_drv;
+
+template <typename F>
+bool resolve(const char* sym, F* fp) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion(sym, &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !p)
+        return false;
+    *fp = reinterpret_cast<F>(p);
+    return true;
+}
+
+fbcorr_status_t driver_api(DriverApi** out) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_drv.ok) {
+        DriverApi d;
+        bool ok = resolve("cuModuleLoadData", &d.moduleLoadData) &&
+                  resolve("cuModuleGetFunction", &d.moduleGetFunction) &&
+                  resolve("cuFuncSetAttribute", &d.funcSetAttribute) &&
+                  resolve("cuLaunchKernel", &d.launchKernel) &&
+                  resolve("cuCtxGetCurrent", &d.ctxGetCurrent) &&
+                  resolve("cuGetErrorString", &d.getErrorString);
+        if (!ok) return set_error(FBCORR_ERR_CUDA, "could not resolve CUDA driver entry points");
+        d.ok = true;
+        g_drv = d;
+    }
+    *out = &g_drv;
+    return FBCORR_OK;
+}
+
+const char* cu_err(CUresult r) {
+    const char* s = "unknown driver error";
+    if (g_drv.getErrorString) g_drv.getErrorString(r, &s);
+    return s;
+}
+
+uint64_t fnv1a(const std::string& s, uint64_t h = 1469598103934665603ull) {
+    for (unsigned char c : s) {
+        h ^= c;
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+const char* kArch = "sm_103a";
+
+std::vector<std::string> nvrtc_options() {
+    return {"--gpu-architecture=sm_103a", "-std=c++17", "-lineinfo", "-DFBC_NVRTC=1"};
+}
+
+std::string nvrtc_version_string() {
+    int maj = 0, min = 0;
+    nvrtcVersion(&maj, &min);
+    char b[32];
+    snprintf(b, sizeof b, "%d.%d", maj, min);
+    return b;
+}
+
+fbcorr_status_t compile(const std::string& src, std::vector<char>* cubin, std::string* log) {
+    if (fault_injected("nvrtc"))
+        return set_error(FBCORR_ERR_NVRTC, "NVRTC compilation disabled by FBCORR_FAULT=nvrtc");
+    nvrtcProgram prog;
+    nvrtcResult r = nvrtcCreateProgram(&prog, src.c_str(), "fbcorr_rtcg.cu", 0, nullptr, nullptr);
+    if (r != NVRTC_SUCCESS)
+        return set_error(FBCORR_ERR_NVRTC, "nvrtcCreateProgram: %s", nvrtcGetErrorString(r));
+    std::vector<std::string> opts = nvrtc_options();
+    std::vector<const char*> copts;
+    for (auto& o : opts) copts.push_back(o.c_str());
+    r = nvrtcCompileProgram(prog, (int)copts.size(), copts.data());
+    size_t logsz = 0;
+    nvrtcGetProgramLogSize(prog, &logsz);
+    std::string lg(logsz, '\0');
+    if (logsz) nvrtcGetProgramLog(prog, &lg[0]);
+    if (log) *log = lg;
+    if (r != NVRTC_SUCCESS) {
+        nvrtcDestroyProgram(&prog);
+        return set_error(FBCORR_ERR_NVRTC, "NVRTC compile failed: %s\n%.2000s",
+                         nvrtcGetErrorString(r), lg.c_str());
+    }
+    size_t n = 0;
+    if (nvrtcGetCUBINSize(prog, &n) != NVRTC_SUCCESS || n == 0) {
+        nvrtcDestroyProgram(&prog);
+        return set_error(FBCORR_ERR_NVRTC, "NVRTC produced no cubin");
+    }
+    cubin->resize(n);
+    nvrtcGetCUBIN(prog, cubin->data());
+    nvrtcDestroyProgram(&prog);
+    return FBCORR_OK;
+}
+
+bool read_file(const std::string& path, std::vector<char>* out) {
+    FILE* f = fopen(path.c_str(), "rb");
+    if (!f) return false;
+    fseek(f, 0, SEEK_END);
+    long n = ftell(f);
+    fseek(f, 0, SEEK_SET);
+    if (n <= 0) {
+        fclose(f);
+        return false;
+    }
+    out->resize((size_t)n);
+    bool ok = fread(out->data(), 1, (size_t)n, f) == (size_t)n;
+    fclose(f);
+    return ok;
+}
+
+void mkdirs(const std::string& dir) {
+    std::string cur;
+    for (size_t i = 0; i < dir.size(); ++i) {
+        cur += dir[i];
+        if (dir[i] == '/' && cur.size() > 1) mkdir(cur.c_str(), 0755);
+    }
+    mkdir(dir.c_str(), 0755);
+}
+
+void write_file_atomic(const std::string& path, const std::vector<char>& data) {
+    std::string tmp = path + ".tmp" + std::to_string((long)getpid());
+    FILE* f = fopen(tmp.c_str(), "wb");
+    if (!f) return;
+    bool ok = fwrite(data.data(), 1, data.size(), f) == data.size();
+    ok = (fclose(f) == 0) && ok;
+    if (ok)
+        rename(tmp.c_str(), path.c_str());
+    else
+        unlink(tmp.c_str());
+}
+
+struct ModKey {
+    CUcontext ctx;
+    uint64_t hash;
+    bool operator<(const ModKey& o) const {
+        return ctx != o.ctx ? ctx < o.ctx : hash < o.hash;
+    }
+};
+std::map<ModKey, CUmodule> g_modules;   // loaded once per context, kept for the process
+
+}  // namespace
+
+// FBCORR_DUMP_DIR: write every generated source there (for offline ptxas -v checks).
+void dump_source(const std::string& src, const std::string& name) {
+    const std::string dir = env_str("FBCORR_DUMP_DIR", "");
+    if (dir.empty()) return;
+    mkdirs(dir);
+    FILE* f = fopen((dir + "/" + name + ".cu").c_str(), "w");
+    if (!f) return;
+    fwrite(src.data(), 1, src.size(), f);
+    fclose(f);
+}
+
+fbcorr_status_t rtcg_compile_only(const std::string& src, std::string* log) {
+    std::vector<char> cubin;
+    dump_source(src, "check_" + std::to_string(fnv1a(src) & 0xffffff));
+    return compile(src, &cubin, log);
+}
+
+fbcorr_status_t rtcg_kernel(const std::string& src, const std::string& name, size_t smem,
+                            int threads, Kernel* out) {
+    DriverApi* drv = nullptr;
+    FBC_TRY(driver_api(&drv));
+    FBC_CUDA(cudaFree(nullptr));   // make the primary context current
+    CUcontext ctx = nullptr;
+    if (drv->ctxGetCurrent(&ctx) != CUDA_SUCCESS || !ctx)
+        return set_error(FBCORR_ERR_CUDA, "no current CUDA context");
+
+    std::string keysrc = src + "\n//" + kArch + " nvrtc " + nvrtc_version_string();
+    for (auto& o : nvrtc_options()) keysrc += " " + o;
+    const uint64_t h = fnv1a(keysrc);
+
+    CUmodule mod = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        auto it = g_modules.find(ModKey{ctx, h});
+        if (it != g_modules.end()) mod = it->second;
+    }
+    if (!mod) {
+        char hb[32];
+        snprintf(hb, sizeof hb, "%016llx", (unsigned long long)h);
+        const std::string dir = cache_dir();
+        const std::string path = dir + "/rtcg-" + hb + ".cubin";
+        std::vector<char> cubin;
+        bool cached = !fault_injected("nocache") && read_file(path, &cubin);
+        if (!cached) {
+            dump_source(src, name);
+            FBC_TRY(compile(src, &cubin, nullptr));
+            mkdirs(dir);
+            write_file_atomic(path, cubin);
+            logf("rtcg: compiled %s (%zu bytes) -> %s", name.c_str(), cubin.size(), path.c_str());
+        } else {
+            logf("rtcg: cache hit %s for %s", path.c_str(), name.c_str());
+        }
+        CUresult r = drv->moduleLoadData(&mod, cubin.data());
+        if (r != CUDA_SUCCESS && cached) {
+            // stale or corrupt cache entry: rebuild it once
+            FBC_TRY(compile(src, &cubin, nullptr));
+            write_file_atomic(path, cubin);
+            r = drv->moduleLoadData(&mod, cubin.data());
+        }
+        if (r != CUDA_SUCCESS)
+            return set_error(FBCORR_ERR_CUDA, "cuModuleLoadData(%s): %s", name.c_str(), cu_err(r));
+        std::lock_guard<std::mutex> lk(g_mu);
+        g_modules[ModKey{ctx, h}] = mod;
+    }
+    CUfunction fn = nullptr;
+    CUresult r = drv->moduleGetFunction(&fn, mod, name.c_str());
+    if (r != CUDA_SUCCESS)
+        return set_error(FBCORR_ERR_CUDA, "cuModuleGetFunction(%s): %s", name.c_str(), cu_err(r));
+    if (smem > 48 * 1024) {
+        r = drv->funcSetAttribute(fn, CU_FUNC_ATTRIBUTE_MAX_DYNAMIC_SHARED_SIZE_BYTES, (int)smem);
+        if (r != CUDA_SUCCESS)
+            return set_error(FBCORR_ERR_CUDA, "cuFuncSetAttribute(smem=%zu): %s", smem, cu_err(r));
+    }
+    out->fn = fn;
+    out->threads = threads;
+    out->smem = smem;
+    out->name = name;
+    return FBCORR_OK;
+}
+
+fbcorr_status_t launch(const Kernel& k, dim3 grid, void** args, cudaStream_t stream) {
+    DriverApi* drv = nullptr;
+    FBC_TRY(driver_api(&drv));
+    if (!k.fn) return set_error(FBCORR_ERR_INTERNAL, "launch of an unloaded kernel");
+    CUresult r = drv->launchKernel(k.fn, grid.x, grid.y, grid.z, (unsigned)k.threads, 1, 1,
+                                   (unsigned)k.smem, (CUstream)stream, args, nullptr);
+    if (r != CUDA_SUCCESS)
+        return set_error(FBCORR_ERR_CUDA, "cuLaunchKernel(%s grid=%u,%u,%u block=%d smem=%zu): %s",
+                         k.name.c_str(), grid.x, grid.y, grid.z, k.threads, k.smem, cu_err(r));
+    return FBCORR_OK;
+}
+
+}  // namespace fbc

@@ -1,0 +1,320 @@
+// rtcg_direct.cuh -- kernel templates compiled at plan time by NVRTC for sm_103a.
+//
+// This file is embedded as a string into libfbcorr and compiled with the
+// filter size, depth and tile of one plan baked in as template arguments --
+// the "hardcoding" specialisation that the paper obtains from run-time code
+// generation (Sec. 3.2, Sec. 6.2): fixed loop trip counts, fully unrolled
+// inner loops, register blocking chosen per shape by the auto-tuner.
+// It is self-contained: NVRTC compiles it without any system header.
+//
+// Operation (Sec. 6.2, Table "Performance of RTCG auto-tuning on 3D
+// filter-bank convolutions"), all tensors FP32 with the last index fastest:
+//   forward:  y[p][q][n] = epi( sum_{i,j,c} x[p+i][q+j][c] * w[n][i][j][c] )
+//   dL/dx:    the same correlation run over the zero-padded upstream gradient
+//             g~ with the flipped, transposed bank  w'[d][i][j][n] =
+//             w[n][fh-1-i][fw-1-j][d]  (FLIP = 1, pad = (fh-1, fw-1));
+//   dL/dw:    dw[n][i][j][c] = sum_{p,q} g~[p][q][n] * x[p+i][q+j][c], as
+//             per-chunk partial sums followed by a fixed-order pairwise
+//             reduction (deterministic, no atomics).
+
+typedef unsigned int fbc_u32;
+
+struct FbcDirectArgs {
+    const float* __restrict__ x;   // input  [in_h][in_w][C]
+    const float* __restrict__ m;   // clamp-mask source, same shape as x (FLIP with MASK only)
+    const float* __restrict__ w;   // bank in its original [N][fh][fw][D] layout
+    float* __restrict__ y;         // output [out_h][out_w][nf]
+    int in_h, in_w, out_h, out_w, nf;
+    int pad_y, pad_x;              // output (p, q) reads input (p - pad_y + i, q - pad_x + j)
+    float lo, hi;                  // clamp bounds (EPI) or mask bounds (MASK)
+};
+
+template <int V>
+struct FbcOdd { static constexpr int value = (V % 2 == 1) ? V : V + 1; };
+
+// One CTA computes an output block of BH = TR*WR rows x 32 columns x BN = TF*WF
+// output channels.  Lane l of a warp owns output column q0 + l; warp (wr, wf)
+// owns rows wr*TR .. +TR and channels wf*TF .. +TF, so each thread holds a
+// TR x TF accumulator block.  The input halo is staged in shared memory as
+// [row][channel][column] (odd column pitch: conflict-free column reads), the
+// CTA's slice of the bank as [i][j][channel][BN+4] so that a warp's TF filter
+// values are one broadcast float4 read per 4 filters.  For a fixed (j, c) a
+// thread loads TR+FH-1 input values once and reuses them for all FH filter
+// rows: TR*TF*FH FMAs per TR+FH-1 scalar and FH*TF/4 vector shared loads.
+template <int FH, int FW, int C, int TR, int TF, int WR, int WF, int FLIP, int EPI, int MASK>
+struct FbcDirect {
+    static constexpr int BW = 32;
+    static constexpr int BH = TR * WR;
+    static constexpr int BN = TF * WF;
+    static constexpr int NT = 32 * WR * WF;
+    static constexpr int HR = BH + FH - 1;
+    static constexpr int HC = BW + FW - 1;
+    static constexpr int COLP = FbcOdd<HC>::value;
+    static constexpr int BNP = BN + 4;
+    static constexpr int XS = ((HR * C * COLP + 3) / 4) * 4;    // floats, 16-byte multiple
+    static constexpr int WS = FH * FW * C * BNP;
+    static constexpr int SMEM_BYTES = (XS + WS) * 4;
+    static_assert(TF % 4 == 0, "TF must be a multiple of 4");
+
+    static __device__ __forceinline__ float mask_val(float v, float mv, float lo, float hi) {
+        return (mv > lo && mv < hi) ? v : 0.0f;
+    }
+
+    static __device__ __forceinline__ void run(const FbcDirectArgs& a, float* smem,
+                                               int tile_x, int tile_y, int tile_f) {
+        const int tid = threadIdx.x;
+        const int lane = tid & 31;
+        const int warp = tid >> 5;
+        const int wr = warp % WR;
+        const int wf = warp / WR;
+        const int q0 = tile_x * BW;
+        const int p0 = tile_y * BH;
+        const int f0 = tile_f * BN;
+        float* xs = smem;
+        float* ws = smem + XS;
+
+        // ---- stage the input halo: rows p0-pad_y .. +HR, columns q0-pad_x .. +HC
+        if (C % 4 == 0) {
+            constexpr int C4 = C / 4;
+            for (int e = tid; e < HR * HC * C4; e += NT) {
+                const int c4 = e % C4;
+                const int t = e / C4;
+                const int col = t % HC;
+                const int row = t / HC;
+                const int gy = p0 - a.pad_y + row;
+                const int gx = q0 - a.pad_x + col;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (gy >= 0 && gy < a.in_h && gx >= 0 && gx < a.in_w) {
+                    const long long off = ((long long)gy * a.in_w + gx) * C + c4 * 4;
+                    v = __ldg(reinterpret_cast<const float4*>(a.x + off));
+                    if (MASK) {
+                        const float4 mv = __ldg(reinterpret_cast<const float4*>(a.m + off));
+                        v.x = mask_val(v.x, mv.x, a.lo, a.hi);
+                        v.y = mask_val(v.y, mv.y, a.lo, a.hi);
+                        v.z = mask_val(v.z, mv.z, a.lo, a.hi);
+                        v.w = mask_val(v.w, mv.w, a.lo, a.hi);
+                    }
+                }
+                float* dst = xs + (row * C + c4 * 4) * COLP + col;
+                dst[0] = v.x;
+                dst[COLP] = v.y;
+                dst[2 * COLP] = v.z;
+                dst[3 * COLP] = v.w;
+            }
+        } else {
+            for (int e = tid; e < HR * HC * C; e += NT) {
+                const int c = e % C;
+                const int t = e / C;
+                const int col = t % HC;
+                const int row = t / HC;
+                const int gy = p0 - a.pad_y + row;
+                const int gx = q0 - a.pad_x + col;
+                float v = 0.f;
+                if (gy >= 0 && gy < a.in_h && gx >= 0 && gx < a.in_w) {
+                    const long long off = ((long long)gy * a.in_w + gx) * C + c;
+                    v = __ldg(a.x + off);
+                    if (MASK) v = mask_val(v, __ldg(a.m + off), a.lo, a.hi);
+                }
+                xs[(row * C + c) * COLP + col] = v;
+            }
+        }
+
+        // ---- stage this CTA's BN output channels of the bank as [i][j][c][BNP]
+        if (!FLIP) {
+            // forward: ws[i][j][c][f] = w[f0+f][i][j][c]; global reads along c
+            for (int e = tid; e < BN * FH * FW * C; e += NT) {
+                const int c = e % C;
+                int t = e / C;
+                const int j = t % FW;
+                t /= FW;
+                const int i = t % FH;
+                const int f = t / FH;
+                const int n = f0 + f;
+                const float v = (n < a.nf) ? __ldg(a.w + (((long long)n * FH + i) * FW + j) * C + c) : 0.f;
+                ws[((i * FW + j) * C + c) * BNP + f] = v;
+            }
+        } else {
+            // dL/dx: output channel f is the bank's depth index, input channel c
+            // its filter index: ws[i][j][c][f] = w[c][FH-1-i][FW-1-j][f0+f];
+            // global reads along f
+            for (int e = tid; e < BN * FH * FW * C; e += NT) {
+                const int f = e % BN;
+                int t = e / BN;
+                const int j = t % FW;
+                t /= FW;
+                const int i = t % FH;
+                const int c = t / FH;
+                const int n = f0 + f;
+                const float v = (n < a.nf)
+                    ? __ldg(a.w + (((long long)c * FH + (FH - 1 - i)) * FW + (FW - 1 - j)) * a.nf + n)
+                    : 0.f;
+                ws[((i * FW + j) * C + c) * BNP + f] = v;
+            }
+        }
+        __syncthreads();
+
+        // ---- register-blocked FMA loop
+        float acc[TR][TF];
+#pragma unroll
+        for (int r = 0; r < TR; ++r)
+#pragma unroll
+            for (int f = 0; f < TF; ++f) acc[r][f] = 0.f;
+
+        const float* xb = xs + (wr * TR) * C * COLP + lane;
+        const float* wb = ws + wf * TF;
+#pragma unroll 1
+        for (int j = 0; j < FW; ++j) {
+#pragma unroll 2
+            for (int c = 0; c < C; ++c) {
+                float xv[TR + FH - 1];
+#pragma unroll
+                for (int k = 0; k < TR + FH - 1; ++k) xv[k] = xb[(k * C + c) * COLP + j];
+#pragma unroll
+                for (int i = 0; i < FH; ++i) {
+                    float wv[TF];
+                    const float4* wp = reinterpret_cast<const float4*>(wb + ((i * FW + j) * C + c) * BNP);
+#pragma unroll
+                    for (int f4 = 0; f4 < TF / 4; ++f4) {
+                        const float4 t4 = wp[f4];
+                        wv[4 * f4 + 0] = t4.x;
+                        wv[4 * f4 + 1] = t4.y;
+                        wv[4 * f4 + 2] = t4.z;
+                        wv[4 * f4 + 3] = t4.w;
+                    }
+#pragma unroll
+                    for (int r = 0; r < TR; ++r)
+#pragma unroll
+                        for (int f = 0; f < TF; ++f) acc[r][f] = fmaf(xv[r + i], wv[f], acc[r][f]);
+                }
+            }
+        }
+
+        // ---- epilogue: optional clamp, then store
+        const int q = q0 + lane;
+        const int nb = f0 + wf * TF;
+        const bool vec = ((a.nf & 3) == 0) && (nb + TF <= a.nf);
+#pragma unroll
+        for (int r = 0; r < TR; ++r) {
+            const int p = p0 + wr * TR + r;
+            if (p >= a.out_h || q >= a.out_w) continue;
+            float* yp = a.y + ((long long)p * a.out_w + q) * a.nf + nb;
+            float v[TF];
+#pragma unroll
+            for (int f = 0; f < TF; ++f) {
+                v[f] = acc[r][f];
+                if (EPI == 1) v[f] = fminf(fmaxf(v[f], a.lo), a.hi);
+            }
+            if (vec) {
+#pragma unroll
+                for (int f4 = 0; f4 < TF / 4; ++f4)
+                    reinterpret_cast<float4*>(yp)[f4] =
+                        make_float4(v[4 * f4], v[4 * f4 + 1], v[4 * f4 + 2], v[4 * f4 + 3]);
+            } else {
+#pragma unroll
+                for (int f = 0; f < TF; ++f)
+                    if (nb + f < a.nf) yp[f] = v[f];
+            }
+        }
+    }
+};
+
+// ---- dL/dw partial sums -----------------------------------------------------
+// Grid: x = chunk of output rows, y = filter row i, z = group of NT (n-group, c)
+// pairs.  Thread (ng, c) accumulates dw[ng*TN .. +TN][i][0..FW)[c] over its
+// chunk, one output row at a time into a row partial that is then added to the
+// chunk total (two-level summation).  Along q the FW input values x[p+i][q+j][c]
+// live in a register window rotated by a compile-time index (unroll by FW).
+struct FbcDwArgs {
+    const float* __restrict__ x;   // [H][W][C]
+    const float* __restrict__ g;   // [Ho][Wo][N]
+    const float* __restrict__ m;   // forward output y for the clamp mask, or unused
+    float* __restrict__ part;      // [S][N][FH][FW][C]
+    int H, W, Ho, Wo, N;
+    int rows_per_chunk;
+    float lo, hi;
+};
+
+template <int FH, int FW, int C, int TN, int MASK>
+struct FbcDw {
+    static __device__ __forceinline__ void run(const FbcDwArgs& a, int chunk, int i, int pair) {
+        const int ngroups = (a.N + TN - 1) / TN;
+        if (pair >= ngroups * C) return;
+        const int c = pair % C;
+        const int n0 = (pair / C) * TN;
+        const int pb = chunk * a.rows_per_chunk;
+        int pe = pb + a.rows_per_chunk;
+        if (pe > a.Ho) pe = a.Ho;
+
+        float tot[TN][FW];
+#pragma unroll
+        for (int t = 0; t < TN; ++t)
+#pragma unroll
+            for (int k = 0; k < FW; ++k) tot[t][k] = 0.f;
+
+        const bool vec = (TN == 4) && ((a.N & 3) == 0) && (n0 + 4 <= a.N);
+        for (int p = pb; p < pe; ++p) {
+            float ra[TN][FW];
+#pragma unroll
+            for (int t = 0; t < TN; ++t)
+#pragma unroll
+                for (int k = 0; k < FW; ++k) ra[t][k] = 0.f;
+            const float* xr = a.x + ((long long)(p + i) * a.W) * C + c;
+            const float* gr = a.g + ((long long)p * a.Wo) * a.N + n0;
+            const float* mr = a.m + ((long long)p * a.Wo) * a.N + n0;
+            float win[FW];
+#pragma unroll
+            for (int k = 0; k < FW - 1; ++k) win[k] = __ldg(xr + k * C);
+            for (int q = 0; q < a.Wo; q += FW) {
+#pragma unroll
+                for (int s = 0; s < FW; ++s) {
+                    const int qq = q + s;
+                    if (qq < a.Wo) {
+                        win[(s + FW - 1) % FW] = __ldg(xr + (long long)(qq + FW - 1) * C);
+                        float gv[TN];
+                        if (vec) {
+                            const float4 t4 = __ldg(reinterpret_cast<const float4*>(gr + (long long)qq * a.N));
+                            gv[0] = t4.x; gv[1 % TN] = t4.y; gv[2 % TN] = t4.z; gv[3 % TN] = t4.w;
+                            if (MASK) {
+                                const float4 m4 = __ldg(reinterpret_cast<const float4*>(mr + (long long)qq * a.N));
+                                gv[0] = (m4.x > a.lo && m4.x < a.hi) ? gv[0] : 0.f;
+                                gv[1 % TN] = (m4.y > a.lo && m4.y < a.hi) ? gv[1 % TN] : 0.f;
+                                gv[2 % TN] = (m4.z > a.lo && m4.z < a.hi) ? gv[2 % TN] : 0.f;
+                                gv[3 % TN] = (m4.w > a.lo && m4.w < a.hi) ? gv[3 % TN] : 0.f;
+                            }
+                        } else {
+#pragma unroll
+                            for (int t = 0; t < TN; ++t) {
+                                float v = 0.f;
+                                if (n0 + t < a.N) {
+                                    v = __ldg(gr + (long long)qq * a.N + t);
+                                    if (MASK) {
+                                        const float mv = __ldg(mr + (long long)qq * a.N + t);
+                                        v = (mv > a.lo && mv < a.hi) ? v : 0.f;
+                                    }
+                                }
+                                gv[t] = v;
+                            }
+                        }
+#pragma unroll
+                        for (int t = 0; t < TN; ++t)
+#pragma unroll
+                            for (int k = 0; k < FW; ++k)
+                                ra[t][k] = fmaf(gv[t], win[(s + k) % FW], ra[t][k]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < TN; ++t)
+#pragma unroll
+                for (int k = 0; k < FW; ++k) tot[t][k] += ra[t][k];
+        }
+        // part[chunk][n][i][j][c]
+#pragma unroll
+        for (int t = 0; t < TN; ++t) {
+            if (n0 + t >= a.N) continue;
+#pragma unroll
+            for (int k = 0; k < FW; ++k)
+                a.part[((((long long)chunk * a.N + n0 + t) * FH + i) * FW + k) * C + c] = tot[t][k];
+        }
+    }
+};

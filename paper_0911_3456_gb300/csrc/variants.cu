@@ -1,0 +1,143 @@
+// variants.cu -- the space of generated kernel variants and the source text
+// handed to NVRTC for each of them.
+//
+// The paper's auto-tuner searches "unique combinations of loop unrolling
+// depth, register spilling, block/grid dimensions, thread work size, shared
+// memory padding" (Sec. 6.2).  On sm_103a the corresponding knobs of the
+// direct FP32 kernel are the thread work size TR x TF (output rows x output
+// channels per thread, i.e. the register block), the CTA shape WR x WF warps,
+// and -- fixed per plan -- the filter size and depth that NVRTC unrolls.
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <sstream>
+
+#include "internal.h"
+
+namespace fbc {
+
+#include "_embedded_src.inc"   // kRtcgDirectSrc: the text of rtcg_direct.cuh
+
+const char* rtcg_header_source() { return kRtcgDirectSrc; }
+
+size_t direct_smem_bytes(const DirectTile& t, int fh, int fw, int c) {
+    const long bh = t.tr * t.wr, bn = t.tf * t.wf;
+    const long hr = bh + fh - 1, hc = 32 + fw - 1;
+    const long colp = (hc % 2 == 1) ? hc : hc + 1;
+    const long bnp = bn + 4;
+    const long xs = ((hr * c * colp + 3) / 4) * 4;
+    const long ws = (long)fh * fw * c * bnp;
+    return (size_t)(xs + ws) * 4;
+}
+
+std::string direct_tile_spec(const DirectTile& t) {
+    char b[96];
+    snprintf(b, sizeof b, "direct:tr=%d,tf=%d,wr=%d,wf=%d", t.tr, t.tf, t.wr, t.wf);
+    return b;
+}
+
+bool parse_direct_spec(const std::string& s, DirectTile* t) {
+    DirectTile d;
+    if (sscanf(s.c_str(), "direct:tr=%d,tf=%d,wr=%d,wf=%d", &d.tr, &d.tf, &d.wr, &d.wf) != 4)
+        return false;
+    if (d.tr < 1 || d.tr > 16 || (d.tf != 4 && d.tf != 8 && d.tf != 12 && d.tf != 16) ||
+        d.wr < 1 || d.wf < 1 || d.threads() > 1024)
+        return false;
+    *t = d;
+    return true;
+}
+
+std::string direct_kernel_source(const DirectProblem& pr, const DirectTile& t,
+                                 const std::string& kname) {
+    std::ostringstream o;
+    o << rtcg_header_source() << "\n";
+    o << "typedef FbcDirect<" << pr.fh << "," << pr.fw << "," << pr.c << "," << t.tr << ","
+      << t.tf << "," << t.wr << "," << t.wf << "," << pr.flip << "," << pr.epi << "," << pr.mask
+      << "> FbcThis;\n";
+    o << "static_assert(FbcThis::SMEM_BYTES == " << direct_smem_bytes(t, pr.fh, pr.fw, pr.c)
+      << ", \"host and device disagree on the shared-memory size\");\n";
+    o << "extern \"C\" __global__ void __launch_bounds__(" << t.threads() << ") " << kname
+      << "(FbcDirectArgs a) {\n"
+      << "  extern __shared__ __align__(16) float fbc_smem[];\n"
+      << "  FbcThis::run(a, fbc_smem, blockIdx.x, blockIdx.y, blockIdx.z);\n"
+      << "}\n";
+    return o.str();
+}
+
+std::string dw_kernel_source(int fh, int fw, int c, int tn, int mask, const std::string& kname) {
+    std::ostringstream o;
+    o << rtcg_header_source() << "\n";
+    o << "extern \"C\" __global__ void __launch_bounds__(128) " << kname << "(FbcDwArgs a) {\n"
+      << "  FbcDw<" << fh << "," << fw << "," << c << "," << tn << "," << mask
+      << ">::run(a, blockIdx.x, blockIdx.y, blockIdx.z * blockDim.x + threadIdx.x);\n"
+      << "}\n";
+    return o.str();
+}
+
+namespace {
+int ceil_div(long a, long b) { return (int)((a + b - 1) / b); }
+}  // namespace
+
+std::vector<DirectTile> direct_candidates(const DirectProblem& pr, size_t smem_limit) {
+    std::vector<DirectTile> out;
+    const int trs[] = {2, 4, 8};
+    const int tfs[] = {4, 8};
+    const int wrs[] = {1, 2, 4};
+    const int wfs[] = {1, 2, 4};
+    const int nf4 = ((pr.nf + 3) / 4) * 4;
+    for (int tr : trs)
+        for (int tf : tfs)
+            for (int wr : wrs)
+                for (int wf : wfs) {
+                    DirectTile t{tr, tf, wr, wf};
+                    if (t.threads() > 512) continue;
+                    if (tf > nf4) continue;                       // no all-padding channels
+                    if (t.bn() > nf4 && wf > 1) continue;
+                    if (tr * tf > 64) continue;                   // register block
+                    if (tr + pr.fh - 1 > 40) continue;            // input window registers
+                    if (t.bh() > ((pr.out_h + 1) / 2) * 2 + 8 && wr > 1) continue;
+                    if (direct_smem_bytes(t, pr.fh, pr.fw, pr.c) > smem_limit) continue;
+                    out.push_back(t);
+                }
+    return out;
+}
+
+DirectTile direct_heuristic(const DirectProblem& pr, size_t smem_limit, int sm_count) {
+    // A small analytic model: tile edge waste x wave quantisation x inner-loop
+    // issue efficiency x latency hiding (resident warps).  The auto-tuner
+    // replaces it with measurements.
+    auto cands = direct_candidates(pr, smem_limit);
+    DirectTile best{4, 4, 1, 1};
+    double best_score = -1.0;
+    const size_t smem_per_sm = 228 * 1024;
+    for (const auto& t : cands) {
+        const int gx = ceil_div(pr.out_w, 32), gy = ceil_div(pr.out_h, t.bh()),
+                  gz = ceil_div(pr.nf, t.bn());
+        const double useful = (double)pr.out_w * pr.out_h * pr.nf;
+        const double computed = (double)gx * 32 * gy * t.bh() * gz * t.bn();
+        const double e_tile = useful / computed;
+        const size_t smem = direct_smem_bytes(t, pr.fh, pr.fw, pr.c) + 1024;
+        const int regs = t.tr * t.tf + t.tr + pr.fh + t.tf + 28;
+        int res = (int)(smem_per_sm / smem);
+        res = std::min(res, 2048 / t.threads());
+        res = std::min(res, 65536 / (t.threads() * std::min(255, regs)));
+        if (res < 1) continue;
+        const long ctas = (long)gx * gy * gz;
+        const long slots = (long)res * sm_count;
+        const long waves = (ctas + slots - 1) / slots;
+        const double wave_eff = (double)ctas / (double)(waves * slots);
+        const double loads = (t.tr + pr.fh - 1) + pr.fh * t.tf / 4.0 + 2.0;
+        const double fmas = (double)t.tr * t.tf * pr.fh;
+        const double e_issue = fmas / (fmas + loads);
+        const int warps = std::min<long>(res, (ctas + sm_count - 1) / sm_count) * t.threads() / 32;
+        const double occ = std::min(1.0, warps / 12.0);
+        const double score = e_tile * wave_eff * e_issue * (0.5 + 0.5 * occ);
+        if (score > best_score) {
+            best_score = score;
+            best = t;
+        }
+    }
+    return best;
+}
+
+}  // namespace fbc

@@ -1,0 +1,139 @@
+"""CPU-only checks of the C ABI: the library loads, exports every symbol that
+include/fbcorr.h declares, validates arguments before touching a GPU, and its
+generated kernel sources compile for sm_103a (NVRTC needs no GPU)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_0911_3456_gb300 import _capi as C
+from paper_0911_3456_gb300 import build as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return C.load()
+
+
+def header_functions():
+    text = open(os.path.join(ROOT, "include", "fbcorr.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(fbcorr_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(lib):
+    names = header_functions()
+    assert len(names) >= 19
+    out = subprocess.run(["nm", "-D", "--defined-only", C.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (fbcorr_\w+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    for n in names:
+        assert hasattr(lib, n)
+    # the binding declares the same names
+    assert set(C.PROTOTYPES) == set(names)
+
+
+def test_version_and_status_strings(lib):
+    assert b"sm_103a" in lib.fbcorr_version()
+    for code, name in C.STATUS_NAMES.items():
+        assert lib.fbcorr_status_string(code).decode() == name
+
+
+def _create(lib, ins, fs, dtype=0, clamp=None):
+    h = ctypes.c_void_p()
+    st = lib.fbcorr_plan_create(ctypes.byref(h), C.I64_3(*ins), C.I64_4(*fs), dtype, C.epilogue(clamp))
+    return st, h
+
+
+@pytest.mark.parametrize("ins,fs,expect", [
+    ((8, 8, 2), (1, 9, 3, 2), 2),          # fh > H
+    ((8, 8, 2), (1, 3, 3, 4), 2),          # depth mismatch
+    ((0, 8, 2), (1, 3, 3, 2), 2),          # zero dim
+    ((8, 8, 2), (-1, 3, 3, 2), 2),         # negative dim
+    ((70000, 70000, 1), (1, 1, 1, 1), 2),  # int32 overflow of H*W*D
+    ((8, 8, 2), (1, 3, 3, 2), 2),          # placeholder replaced below
+])
+def test_plan_create_rejects_bad_shapes(lib, ins, fs, expect):
+    if ins == (8, 8, 2) and fs == (1, 3, 3, 2):
+        st, _ = _create(lib, ins, fs, dtype=7)
+        assert st == 1  # bad dtype
+        return
+    st, h = _create(lib, ins, fs)
+    assert st == expect, C.last_error()
+    assert not h.value
+
+
+def test_plan_create_rejects_bad_epilogue(lib):
+    st, _ = _create(lib, (8, 8, 2), (1, 3, 3, 2), clamp=(1.0, 0.0))
+    assert st == 1
+    h = ctypes.c_void_p()
+    st = lib.fbcorr_plan_create(ctypes.byref(h), C.I64_3(8, 8, 2), C.I64_4(1, 3, 3, 2), 0,
+                                C.Epilogue(5, 0.0, 1.0))
+    assert st == 1
+    assert lib.fbcorr_plan_create(None, C.I64_3(8, 8, 2), C.I64_4(1, 3, 3, 2), 0, C.epilogue()) == 1
+
+
+def test_null_plan_calls_fail_cleanly(lib):
+    assert lib.fbcorr_forward(None, None, None, None, None, 0, None) == 1
+    assert lib.fbcorr_backward(None, None, None, None, None, None, None, None, 0, None) == 1
+    assert lib.fbcorr_plan_out_shape(None, C.I64_3()) == 1
+    assert lib.fbcorr_plan_destroy(None) == 0
+    assert lib.fbcorr_autotune(None, None) == 1
+
+
+def test_valid_plan_without_gpu_reports_cuda_error(lib):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    st, h = _create(lib, (16, 16, 4), (2, 3, 3, 4))
+    assert st == 6 and "cuda" in C.last_error().lower() or st == 6
+
+
+SHAPES = [
+    ((128, 128, 8), (16, 9, 9, 8), None),
+    ((256, 256, 8), (64, 9, 9, 8), (0.0, 1.0)),
+    ((512, 512, 32), (256, 5, 5, 32), None),
+    ((256, 256, 16), (64, 7, 7, 16), None),
+    ((12, 12, 2), (3, 3, 3, 2), None),
+    ((37, 45, 3), (5, 4, 2, 3), (-0.5, 0.5)),   # odd everything, fh != fw
+    ((64, 64, 4), (16, 11, 11, 4), None),
+    ((512, 512, 4), (32, 13, 13, 4), None),      # the paper's second table row
+    ((128, 96, 8), (4, 8, 8, 8), None),          # even filter size
+]
+
+
+@pytest.mark.parametrize("ins,fs,clamp", SHAPES)
+def test_generated_sources_compile(lib, ins, fs, clamp):
+    log = ctypes.create_string_buffer(1 << 16)
+    st = lib.fbcorr_rtcg_check(C.I64_3(*ins), C.I64_4(*fs), C.epilogue(clamp), b"heuristic", log,
+                               len(log))
+    assert st == 0, C.last_error() + log.value.decode()
+
+
+@pytest.mark.parametrize("spec", [b"direct:tr=8,tf=8,wr=1,wf=2", b"direct:tr=2,tf=4,wr=4,wf=1",
+                                  b"direct:tr=4,tf=8,wr=2,wf=4"])
+def test_explicit_tile_specs_compile(lib, spec):
+    log = ctypes.create_string_buffer(1 << 16)
+    st = lib.fbcorr_rtcg_check(C.I64_3(64, 80, 8), C.I64_4(24, 5, 3, 8), C.epilogue((0, 1)), spec,
+                               log, len(log))
+    assert st == 0, C.last_error() + log.value.decode()
+    st = lib.fbcorr_rtcg_check(C.I64_3(64, 80, 8), C.I64_4(24, 5, 3, 8), C.epilogue(), b"direct:bogus",
+                               log, len(log))
+    assert st == 1
+
+
+def test_nvrtc_fault_injection_reports_nvrtc_error():
+    """FBCORR_FAULT=nvrtc makes code generation fail; the status says so."""
+    code = ("import ctypes\nfrom paper_0911_3456_gb300 import _capi as C\nlib=C.load()\n"
+            "log=ctypes.create_string_buffer(4096)\n"
+            "print(lib.fbcorr_rtcg_check(C.I64_3(16,16,4), C.I64_4(2,3,3,4), C.epilogue(), b'heuristic', log, 4096))\n")
+    env = dict(os.environ, FBCORR_FAULT="nvrtc")
+    r = subprocess.run(["python", "-c", code], capture_output=True, text=True, env=env, cwd=ROOT)
+    assert r.stdout.strip().splitlines()[-1] == "7", r.stderr
