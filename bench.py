@@ -1,0 +1,486 @@
+#!/usr/bin/env python
+"""Benchmark of GB300 filter-bank correlation (one JSON line on stdout).
+
+Headline workload: the precision configuration -- a 512x512x32 U[-1,1) input
+correlated 'valid' against 256 filters of 5x5x32 drawn N(0, 1/800), giving a
+508x508x256 output -- computed in split-BF16 (hi*hi + hi*lo + lo*hi on the
+tcgen05 tensor cores, FP32 accumulation), reported next to the FP32 direct
+kernel and plain BF16 on the same inputs.  One step = one forward call (BF16
+split pre-pass + correlation kernel), inputs resident in HBM; the working set
+(34 MB in, 264 MB out) exceeds the 129 MB L2, so no flush is needed between
+steps.  GFLOP/s count 2*H'*W'*N*fh*fw*D per step (algorithmic FLOPs).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun (N > 1) every rank runs an independent replica (no collective
+on the data path); rank 0 prints the line with the max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "filter-bank correlation GFLOP/s and % of roofline, split-BF16 vs FP32 at <=1e-5 rel err"
+UNIT = "GFLOP/s"
+HEADLINE_MODE = "bf16x3"
+
+
+# ----------------------------------------------------------------------------- helpers
+def load_peaks(sm_count: int) -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    src = "measured"
+    try:
+        with open(path) as f:
+            pk = json.load(f)
+    except Exception:
+        pk = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+              "sm_max_mhz": 2070.0}
+        src = "fallback"
+    mhz = float(pk.get("sm_max_mhz", 2070.0))
+    return {
+        "source": src,
+        "hbm_gbs": float(pk["hbm_gbs"]),
+        "bf16_tflops": float(pk["bf16_tflops"]),
+        "bf16_tflops_sustained": float(pk.get("bf16_tflops_sustained", pk["bf16_tflops"])),
+        "sm_max_mhz": mhz,
+        # FP32 FMA peak: SMs x 128 FP32 lanes x 2 FLOP x max SM clock
+        "fp32_tflops": sm_count * 128 * 2 * mhz * 1e6 / 1e12,
+    }
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled while the timed loop runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="fbc_clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        power = [num(r[3]) for r in rows if num(r[3]) is not None]
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(power) if power else None}
+
+
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v: float, world: int) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def time_loop(torch, fn, steps, warmup, world, flush=None):
+    """W warm-up calls, then K timed calls bracketed by barrier + synchronize.
+    Returns milliseconds per step (max over ranks).  With `flush`, every step is
+    timed by its own event pair and L2 is flushed between steps outside them."""
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    if flush is None:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+    else:
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        for a, b in evs:
+            flush()
+            a.record(stream)
+            fn()
+            b.record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in evs) / steps
+    barrier(world)
+    return max_over_ranks(ms, world)
+
+
+def make_flush(torch):
+    buf = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def flush():
+        buf.zero_()
+    return flush
+
+
+def workload_by_name(name):
+    from paper_0911_3456_gb300 import inputs
+    if name == "precision":
+        return inputs.workload_precision()
+    if name == "precision384":
+        # the same recipe at 384x384x32 (output 148 MB, still above the L2 size),
+        # used for detailed profiler captures
+        rng = np.random.default_rng(3)
+        x = inputs.uniform(rng, (384, 384, 32), -1.0, 1.0)
+        w = inputs.normal(rng, (256, 5, 5, 32), var=1.0 / 800.0)
+        return inputs.Workload("precision_384x384x32_256x5x5x32", x, w)
+    raise ValueError(name)
+
+
+# ----------------------------------------------------------------------------- CPU oracle leg
+def oracle_rows_sample(wl, rows, r0=None):
+    """The oracle on `rows` consecutive output rows of the workload (a bounded
+    sample); returns (rows start, FP64 output slab, seconds, cores)."""
+    import oracle
+    Ho = wl.out_shape[0]
+    fh = wl.w.shape[1]
+    if r0 is None:
+        r0 = (Ho - rows) // 2
+    slab = wl.x[r0:r0 + rows + fh - 1]
+    t = time.perf_counter()
+    y = oracle.fwd(slab, wl.w)
+    dt = time.perf_counter() - t
+    return r0, y, dt, oracle.max_threads()
+
+
+def cpu_baseline(wl, target_s=12.0):
+    """Time the oracle on a sample of output rows sized for about target_s."""
+    import oracle
+    Ho, Wo, N = wl.out_shape
+    _, fh, fw, D = wl.w.shape
+    row_flops = 2 * Wo * N * fh * fw * D
+    _, _, dt1, cores = oracle_rows_sample(wl, 1)
+    rows = max(1, min(Ho, int(target_s / max(dt1, 1e-6))))
+    r0, y, dt, cores = oracle_rows_sample(wl, rows)
+    gflops = rows * row_flops / dt / 1e9
+    return {"value": gflops, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{rows} consecutive output rows (from row {r0}) of {Ho}: "
+                      f"{rows * Wo * N} outputs, FP64 nested loops, OpenMP over rows",
+            "seconds": dt}, (r0, y)
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    """The oracle timed as the reference arm on the headline workload."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_0911_3456_gb300 import inputs
+    wl = inputs.workload_precision()
+    Ho, Wo, N = wl.out_shape
+    _, fh, fw, D = wl.w.shape
+    per_point = 2 * fh * fw * D
+    rng = np.random.default_rng(0)
+    # calibrate points per second, then size each step so K + W steps take ~90 s
+    idx = np.stack([rng.integers(0, Ho, 20000), rng.integers(0, Wo, 20000), rng.integers(0, N, 20000)], 1)
+    t = time.perf_counter()
+    oracle.fwd_points(wl.x, wl.w, idx)
+    rate = 20000 / max(time.perf_counter() - t, 1e-6)
+    budget = 90.0 / (args.steps + args.warmup)
+    npts = int(max(256, min(2_000_000, rate * budget)))
+    idx = np.stack([rng.integers(0, Ho, npts), rng.integers(0, Wo, npts), rng.integers(0, N, npts)], 1)
+    for _ in range(args.warmup):
+        oracle.fwd_points(wl.x, wl.w, idx)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.fwd_points(wl.x, wl.w, idx)
+    dt = (time.perf_counter() - t) / args.steps
+    value = npts * per_point / dt / 1e9
+    cores = oracle.max_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": wl.name, "sample_points_per_step": npts},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{npts} random output elements of {Ho}x{Wo}x{N} per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- our arm
+def sampled_error(y_gpu_rows, ref_rows, scale=None):
+    d = np.abs(y_gpu_rows.astype(np.float64) - ref_rows).max()
+    s = np.abs(ref_rows).max() if scale is None else scale
+    return float(d / s)
+
+
+def run_ours(args):
+    import torch
+    from paper_0911_3456_gb300 import inputs
+    from paper_0911_3456_gb300.api import Plan, BatchPlan
+
+    world, rank, local = dist_setup()
+    props = torch.cuda.get_device_properties(local)
+    peaks = load_peaks(props.multi_processor_count)
+    wl = workload_by_name(args.workload)
+    flops = wl.flops
+    x = torch.from_numpy(wl.x).cuda()
+    w = torch.from_numpy(wl.w).cuda()
+
+    mode = args.mode
+    plans = {}
+    for m in dict.fromkeys([mode, "f32", "bf16", "bf16x3"]):
+        if args.quick and m != mode:
+            continue
+        try:
+            p = Plan(wl.x.shape, wl.w.shape, m)
+            if not args.no_tune:
+                p.autotune()
+            plans[m] = p
+        except Exception as e:   # a mode this build cannot run is reported, not hidden
+            if m == mode:
+                raise
+            plans[m] = e
+    plan = plans[mode]
+    y = torch.empty(plan.out_shape, device="cuda")
+
+    # ---- headline: device-resident inputs, K back-to-back steps
+    plan.profile(args.steps)
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms = time_loop(torch, lambda: plan.forward(x, w, y), args.steps, args.warmup, world)
+    clk = clocks.stop()
+    kern_ms = plan.profile_read()
+    plan.profile(0)
+    kern_avg = float(np.mean(kern_ms)) if kern_ms else None
+    value = world * flops / (ms * 1e-3) / 1e9
+    info = plan.info()
+    launches_per_step = int(info["fwd"].get("launches", 1))
+
+    # roofline of the dominant kernel (the correlation kernel)
+    if mode == "f32":
+        peak = peaks["fp32_tflops"]
+        roof = {"bound": "alu", "peak": peak, "unit": "TFLOP/s",
+                "peak_note": "FP32 FMA: SMs x 128 lanes x 2 x max SM clock"}
+    else:
+        peak = peaks["bf16_tflops_sustained"] if args.steps * ms > 1000 else peaks["bf16_tflops"]
+        roof = {"bound": "tensor", "peak": peak, "unit": "TFLOP/s",
+                "peak_note": f"cuBLAS bf16 {'sustained' if args.steps * ms > 1000 else 'burst'}, "
+                             f"{peaks['source']}"}
+    achieved = flops / (kern_avg * 1e-3) / 1e12 if kern_avg else None
+    roof.update({"achieved": achieved, "frac": (achieved / peak) if achieved else None,
+                 "traffic": None, "kernel_ms": kern_avg,
+                 "algorithmic_flops_per_launch": flops})
+    if mode == "bf16x3" and achieved:
+        roof["tensor_issued_tflops"] = 3 * achieved
+
+    # ---- e2e through the public API with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.from_numpy(wl.x).pin_memory()
+        wh = torch.from_numpy(wl.w).pin_memory()
+        yh = torch.empty(plan.out_shape, dtype=torch.float32).pin_memory()
+        xd = torch.empty_like(x)
+        wd = torch.empty_like(w)
+
+        def e2e_step():
+            xd.copy_(xh, non_blocking=True)
+            wd.copy_(wh, non_blocking=True)
+            plan.forward(xd, wd, y)
+            yh.copy_(y, non_blocking=True)
+
+        k_e2e = max(3, min(args.steps, 100))
+        ms_e2e = time_loop(torch, e2e_step, k_e2e, max(3, args.warmup), world)
+        e2e = {"value": world * flops / (ms_e2e * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms_e2e,
+               "steps": k_e2e, "h2d_bytes_per_step": int(wl.x.nbytes + wl.w.nbytes),
+               "d2h_bytes_per_step": int(np.prod(plan.out_shape) * 4)}
+
+    detail = {"headline_plan": info}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        # CPU oracle on a bounded sample; the same sample gives the error of every mode
+        cpu, (r0, ref) = cpu_baseline(wl, target_s=args.cpu_seconds)
+        rows = ref.shape[0]
+        errs = {}
+        for m, p in plans.items():
+            if isinstance(p, Exception):
+                errs[m] = f"unavailable: {p}"
+                continue
+            yy = p.forward(x, w)
+            torch.cuda.synchronize()
+            errs[m] = sampled_error(yy[r0:r0 + rows].cpu().numpy(), ref)
+        detail["max_rel_err_vs_fp64_oracle"] = errs
+        detail["error_sample"] = cpu["sample"]
+
+    # ---- the same workload in the other modes (kernel + step times)
+    if not args.quick:
+        modes = {}
+        for m, p in plans.items():
+            if isinstance(p, Exception):
+                modes[m] = {"unavailable": str(p)}
+                continue
+            p.profile(50)
+            ms_m = time_loop(torch, lambda p=p: p.forward(x, w, y), 50, 3, world)
+            km = p.profile_read()
+            p.profile(0)
+            k_avg = float(np.mean(km)) if km else None
+            pk = peaks["fp32_tflops"] if m == "f32" else peaks["bf16_tflops"]
+            modes[m] = {"gflops": flops / (ms_m * 1e-3) / 1e9, "ms_per_step": ms_m,
+                        "kernel_ms": k_avg,
+                        "kernel_frac_of_peak": (flops / (k_avg * 1e-3) / 1e12 / pk) if k_avg else None,
+                        "peak_tflops": pk, "spec": p.info()["fwd"].get("spec")}
+        detail["modes_same_workload"] = modes
+        if "f32" in modes and mode in modes and "gflops" in modes.get("f32", {}):
+            detail["speedup_vs_fp32_direct"] = modes[mode]["gflops"] / modes["f32"]["gflops"]
+        detail.update(secondary(torch, args, world, peaks))
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": mode, "data": "synthetic",
+            "config": {"workload": wl.name, "input": list(wl.x.shape), "bank": list(wl.w.shape),
+                       "output": list(plan.out_shape), "mode": mode, "flops_per_step": flops,
+                       "l2": "no flush: 34 MB input + 264 MB output per step exceed the 129 MB L2",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roof, "clocks": clk, "gpu_launches": launches_per_step * args.steps,
+            "e2e": e2e, "cpu_baseline": cpu, "peaks": peaks, "detail": detail,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def secondary(torch, args, world, peaks):
+    """Other workloads of the method, each timed with an L2 flush between steps."""
+    from paper_0911_3456_gb300 import inputs
+    from paper_0911_3456_gb300.api import Plan
+    flush = make_flush(torch)
+    out = {}
+    for name, wl in (("small_128x128x8_16x9x9x8", inputs.workload_small_f32()),
+                     ("paper_row1_256x256x8_64x9x9x8_clamp", inputs.workload_paper_row1_clamp())):
+        x = torch.from_numpy(wl.x).cuda()
+        w = torch.from_numpy(wl.w).cuda()
+        p = Plan(wl.x.shape, wl.w.shape, "f32", wl.clamp)
+        y = torch.empty(p.out_shape, device="cuda")
+        p.set_variant("default")
+        ms_def = time_loop(torch, lambda: p.forward(x, w, y), 30, 3, world, flush)
+        p.autotune()
+        ms_tuned = time_loop(torch, lambda: p.forward(x, w, y), 30, 3, world, flush)
+        out[name] = {"default_gflops": wl.flops / ms_def / 1e6, "tuned_gflops": wl.flops / ms_tuned / 1e6,
+                     "boost_percent": 100.0 * (ms_def / ms_tuned - 1.0),
+                     "tuned_frac_of_fp32_peak": wl.flops / ms_tuned / 1e9 / peaks["fp32_tflops"],
+                     "tuned_spec": p.info()["fwd"].get("spec")}
+    wl = inputs.workload_differentiation()
+    x = torch.from_numpy(wl.x).cuda()
+    w = torch.from_numpy(wl.w).cuda()
+    g = torch.from_numpy(wl.g).cuda()
+    p = Plan(wl.x.shape, wl.w.shape, "f32")
+    p.autotune()
+    y = torch.empty(p.out_shape, device="cuda")
+
+    def fb():
+        p.forward(x, w, y)
+        p.backward(x, w, g)
+    ms_f = time_loop(torch, lambda: p.forward(x, w, y), 30, 3, world, flush)
+    ms_fb = time_loop(torch, fb, 30, 3, world, flush)
+    out["fwdbwd_256x256x16_64x7x7x16"] = {
+        "fwd_gflops": wl.flops / ms_f / 1e6, "fwd_bwd_gflops": 3 * wl.flops / ms_fb / 1e6,
+        "ms_fwd": ms_f, "ms_fwd_bwd": ms_fb,
+        "fwd_bwd_frac_of_fp32_peak": 3 * wl.flops / ms_fb / 1e9 / peaks["fp32_tflops"]}
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--mode", choices=["f32", "bf16", "bf16x3"], default=HEADLINE_MODE)
+    ap.add_argument("--quick", action="store_true", help="headline only")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--workload", choices=["precision", "precision384"], default="precision")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -139,6 +139,18 @@ fbcorr_status_t fbcorr_plan_info(fbcorr_plan_t plan, char* buf, size_t cap);
  * the flag when `clear` is non-zero. */
 fbcorr_status_t fbcorr_plan_device_status(fbcorr_plan_t plan, int clear);
 
+/* Timing service (the paper's auto-tuning relies on the runtime's timers,
+ * Sec. 4): when capacity > 0, every later forward call of this plan records a
+ * pair of CUDA events on its stream around its main kernel (the correlation
+ * kernel itself, not the BF16 split pre-pass), for up to `capacity` calls.
+ * capacity = 0 switches recording off. */
+fbcorr_status_t fbcorr_plan_profile(fbcorr_plan_t plan, int capacity);
+
+/* Milliseconds of each recorded main-kernel launch, oldest first, into ms
+ * (up to cap values); *n receives the count.  Waits for the recorded events,
+ * then clears the record. */
+fbcorr_status_t fbcorr_plan_profile_read(fbcorr_plan_t plan, float* ms, int cap, int* n);
+
 /* ---- batches of uneven images ------------------------------------------- */
 
 /* A plan for n independent problems, image k with in_shapes[k] = {H, W, D}

@@ -59,6 +59,9 @@ PROTOTYPES = {
     "fbcorr_plan_set_variant": (_st, [_vp, ctypes.c_char_p]),
     "fbcorr_plan_info": (_st, [_vp, ctypes.c_char_p, _sz]),
     "fbcorr_plan_device_status": (_st, [_vp, ctypes.c_int]),
+    "fbcorr_plan_profile": (_st, [_vp, ctypes.c_int]),
+    "fbcorr_plan_profile_read": (_st, [_vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_int)]),
     "fbcorr_batch_plan_create": (_st, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
                                        ctypes.POINTER(ctypes.c_int64), ctypes.c_int, Epilogue]),
     "fbcorr_batch_plan_destroy": (_st, [_vp]),

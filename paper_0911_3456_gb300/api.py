@@ -138,6 +138,18 @@ class Plan:
         C.call("fbcorr_plan_info", self._h, buf, len(buf))
         return json.loads(buf.value.decode())
 
+    def profile(self, capacity: int) -> None:
+        """Record events around the main kernel of the next `capacity` forward calls."""
+        C.call("fbcorr_plan_profile", self._h, int(capacity))
+
+    def profile_read(self):
+        """Milliseconds of each recorded main-kernel launch (waits for them)."""
+        cap = 1 << 16
+        buf = (ctypes.c_float * cap)()
+        n = ctypes.c_int()
+        C.call("fbcorr_plan_profile_read", self._h, buf, cap, ctypes.byref(n))
+        return [buf[i] for i in range(n.value)]
+
     def device_status(self, clear: bool = False) -> int:
         """0, or the FBCORR_ERR_TIMEOUT status once a kernel gave up a bounded wait."""
         return int(C.load().fbcorr_plan_device_status(self._h, 1 if clear else 0))

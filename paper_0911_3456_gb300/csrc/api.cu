@@ -299,7 +299,18 @@ fbcorr_status_t fbcorr_plan_create(fbcorr_plan_t* out, const int64_t in_shape[3]
             s = tc_plan_create(&p->tc, (int)p->H, (int)p->W, (int)p->D, (int)p->N, (int)p->fh,
                                (int)p->fw, dtype == FBCORR_BF16X3 ? 1 : 0,
                                p->epi.kind == FBCORR_EPI_CLAMP ? 1 : 0, p->epi.lo, p->epi.hi, dev);
-            if (s == FBCORR_OK) p->ws_fwd = tc_workspace_bytes(p->tc);
+            if (s == FBCORR_OK) {
+                p->ws_fwd = tc_workspace_bytes(p->tc);
+                p->fwd_source = "heuristic";
+                std::string spec = env_str("FBCORR_VARIANT", "");
+                if (!spec.empty() && tc_set_spec(p->tc, spec) == FBCORR_OK) {
+                    p->fwd_source = "env";
+                } else if (tune_lookup(tune_key(p->dev, shape_key(p, "fwd")), &spec) &&
+                           tc_set_spec(p->tc, spec) == FBCORR_OK) {
+                    p->fwd_source = "cache";
+                }
+                clear_error();
+            }
         }
     }
     if (s == FBCORR_OK) plan_dw_chunks(p);
@@ -308,7 +319,7 @@ fbcorr_status_t fbcorr_plan_create(fbcorr_plan_t* out, const int64_t in_shape[3]
         return s;
     }
     const std::string at = env_str("FBCORR_AUTOTUNE", "0");
-    if (dtype == FBCORR_F32 && (at == "force" || (at == "1" && p->fwd_source == "heuristic"))) {
+    if (at == "force" || (at == "1" && p->fwd_source == "heuristic")) {
         s = fbcorr_autotune(p, nullptr);
         if (s != FBCORR_OK) {
             fbcorr_plan_destroy(p);
@@ -322,9 +333,49 @@ fbcorr_status_t fbcorr_plan_create(fbcorr_plan_t* out, const int64_t in_shape[3]
     return FBCORR_OK;
 }
 
+fbcorr_status_t fbcorr_plan_profile(fbcorr_plan_t p, int capacity) {
+    clear_error();
+    if (!p || capacity < 0) return set_error(FBCORR_ERR_INVALID_ARG, "bad argument");
+    for (auto e : p->prof_start) cudaEventDestroy(e);
+    for (auto e : p->prof_stop) cudaEventDestroy(e);
+    p->prof_start.clear();
+    p->prof_stop.clear();
+    p->prof_count = 0;
+    for (int k = 0; k < capacity; ++k) {
+        cudaEvent_t a, b;
+        FBC_CUDA(cudaEventCreate(&a));
+        if (cudaEventCreate(&b) != cudaSuccess) {
+            cudaEventDestroy(a);
+            return set_error(FBCORR_ERR_CUDA, "cudaEventCreate failed");
+        }
+        p->prof_start.push_back(a);
+        p->prof_stop.push_back(b);
+    }
+    return FBCORR_OK;
+}
+
+fbcorr_status_t fbcorr_plan_profile_read(fbcorr_plan_t p, float* ms, int cap, int* n) {
+    clear_error();
+    if (!p || !n || (cap > 0 && !ms)) return set_error(FBCORR_ERR_INVALID_ARG, "bad argument");
+    const int cnt = std::min(p->prof_count, cap);
+    for (int k = 0; k < cnt; ++k) {
+        FBC_CUDA(cudaEventSynchronize(p->prof_stop[k]));
+        FBC_CUDA(cudaEventElapsedTime(&ms[k], p->prof_start[k], p->prof_stop[k]));
+    }
+    *n = cnt;
+    p->prof_count = 0;
+    return FBCORR_OK;
+}
+
+int plan_launches_per_forward(const fbcorr_plan* p) {
+    return p->fwd_kind == VarKind::Tensor ? tc_launches(p->tc) : 1;
+}
+
 fbcorr_status_t fbcorr_plan_destroy(fbcorr_plan_t p) {
     clear_error();
     if (!p) return FBCORR_OK;
+    for (auto e : p->prof_start) cudaEventDestroy(e);
+    for (auto e : p->prof_stop) cudaEventDestroy(e);
     if (p->tc) tc_plan_destroy(p->tc);
     if (p->err_host) cudaFreeHost(p->err_host);
     delete p;
@@ -358,14 +409,27 @@ fbcorr_status_t fbcorr_forward(fbcorr_plan_t p, const float* x, const float* w, 
         return set_error(FBCORR_ERR_WORKSPACE, "forward needs %zu bytes of aligned workspace (got %zu)",
                          p->ws_fwd, ws ? ws_bytes : (size_t)0);
     cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (p->prof_count < (int)p->prof_start.size()) {
+        e0 = p->prof_start[p->prof_count];
+        e1 = p->prof_stop[p->prof_count];
+        ++p->prof_count;
+    }
+    fbcorr_status_t st = FBCORR_OK;
     switch (p->fwd_kind) {
         case VarKind::Direct:
-            return run_direct(p->fwd_kernel, fwd_problem(p), p->fwd_tile, x, nullptr, w, y,
-                              p->epi.lo, p->epi.hi, s);
+            if (e0) FBC_CUDA(cudaEventRecord(e0, s));
+            st = run_direct(p->fwd_kernel, fwd_problem(p), p->fwd_tile, x, nullptr, w, y,
+                            p->epi.lo, p->epi.hi, s);
+            if (e1 && st == FBCORR_OK) FBC_CUDA(cudaEventRecord(e1, s));
+            return st;
         case VarKind::Default:
-            return run_default(fwd_problem(p), x, nullptr, w, y, p->epi.lo, p->epi.hi, s);
+            if (e0) FBC_CUDA(cudaEventRecord(e0, s));
+            st = run_default(fwd_problem(p), x, nullptr, w, y, p->epi.lo, p->epi.hi, s);
+            if (e1 && st == FBCORR_OK) FBC_CUDA(cudaEventRecord(e1, s));
+            return st;
         case VarKind::Tensor:
-            return tc_forward(p->tc, x, w, y, ws, p->err_dev, s);
+            return tc_forward(p->tc, x, w, y, ws, p->err_dev, s, e0, e1);
     }
     return set_error(FBCORR_ERR_INTERNAL, "bad variant kind");
 }
@@ -419,9 +483,17 @@ fbcorr_status_t fbcorr_backward(fbcorr_plan_t p, const float* x, const float* w,
 fbcorr_status_t fbcorr_plan_set_variant(fbcorr_plan_t p, const char* spec) {
     clear_error();
     if (!p || !spec) return set_error(FBCORR_ERR_INVALID_ARG, "NULL argument");
-    if (p->dtype != FBCORR_F32)
-        return set_error(FBCORR_ERR_UNSUPPORTED, "tensor-core plans have a single variant");
     const std::string s = spec;
+    if (p->dtype != FBCORR_F32) {
+        if (s == "tuned") return fbcorr_autotune(p, nullptr);
+        if (s == "heuristic") {
+            FBC_TRY(tc_set_spec(p->tc, tc_candidates(p->tc).front()));
+        } else {
+            FBC_TRY(tc_set_spec(p->tc, s));
+        }
+        p->fwd_source = s == "heuristic" ? "heuristic" : "forced";
+        return FBCORR_OK;
+    }
     if (s == "heuristic") {
         const DirectTile t = direct_heuristic(fwd_problem(p), smem_limit(p->dev), p->dev.sm_count);
         return set_fwd_spec(p, direct_tile_spec(t), "heuristic");
@@ -430,11 +502,13 @@ fbcorr_status_t fbcorr_plan_set_variant(fbcorr_plan_t p, const char* spec) {
     return set_fwd_spec(p, s, "forced");
 }
 
+static fbcorr_status_t autotune_tc(fbcorr_plan_t p, fbcorr_stream_t stream);
+
 fbcorr_status_t fbcorr_autotune(fbcorr_plan_t p, fbcorr_stream_t stream) {
     clear_error();
     if (!p) return set_error(FBCORR_ERR_INVALID_ARG, "NULL plan");
-    if (p->dtype != FBCORR_F32) return FBCORR_OK;   // one tensor-core variant per plan
     cudaStream_t s = (cudaStream_t)stream;
+    if (p->dtype != FBCORR_F32) return autotune_tc(p, stream);
     const DirectProblem pr = fwd_problem(p);
     // Candidate set: the analytic model's ranking, top K plus the default kernel.
     std::vector<DirectTile> cands = direct_candidates(pr, smem_limit(p->dev));
@@ -521,6 +595,70 @@ fbcorr_status_t fbcorr_autotune(fbcorr_plan_t p, fbcorr_stream_t stream) {
     return FBCORR_OK;
 }
 
+// Time every feasible tensor-core configuration (ring depths, filter-tile
+// width) and keep the fastest -- the same measured grid search as for the
+// generated FP32 kernels.
+static fbcorr_status_t autotune_tc(fbcorr_plan_t p, fbcorr_stream_t stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    const std::vector<std::string> specs = tc_candidates(p->tc);
+    const std::string old = tc_spec(p->tc);
+    float *x = nullptr, *w = nullptr, *y = nullptr;
+    void* ws = nullptr;
+    const size_t xb = (size_t)p->H * p->W * p->D * 4, wb = (size_t)p->N * p->fh * p->fw * p->D * 4,
+                 yb = (size_t)p->Ho * p->Wo * p->N * 4;
+    if (cudaMalloc(&x, xb) != cudaSuccess || cudaMalloc(&w, wb) != cudaSuccess ||
+        cudaMalloc(&y, yb) != cudaSuccess || cudaMalloc(&ws, p->ws_fwd) != cudaSuccess) {
+        cudaFree(x); cudaFree(w); cudaFree(y); cudaFree(ws);
+        cudaGetLastError();
+        return set_error(FBCORR_ERR_OOM, "autotune buffers");
+    }
+    cudaMemsetAsync(x, 0, xb, s);
+    cudaMemsetAsync(w, 0, wb, s);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    std::string best;
+    float best_ms = 1e30f;
+    fbcorr_status_t status = FBCORR_OK;
+    for (const auto& sp : specs) {
+        if (tc_set_spec(p->tc, sp) != FBCORR_OK) continue;
+        std::vector<float> ms;
+        bool ok = true;
+        for (int r = 0; r < 2 && ok; ++r) ok = fbcorr_forward(p, x, w, y, ws, p->ws_fwd, stream) == FBCORR_OK;
+        for (int r = 0; r < 5 && ok; ++r) {
+            cudaEventRecord(e0, s);
+            ok = fbcorr_forward(p, x, w, y, ws, p->ws_fwd, stream) == FBCORR_OK;
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) ok = false;
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            ms.push_back(t);
+        }
+        if (!ok || fbcorr_plan_device_status(p, 0) != FBCORR_OK) {
+            status = set_error(FBCORR_ERR_CUDA, "autotune run of %s failed", sp.c_str());
+            break;
+        }
+        std::sort(ms.begin(), ms.end());
+        logf("autotune %s: %.4f ms", sp.c_str(), ms[ms.size() / 2]);
+        if (ms[ms.size() / 2] < best_ms) {
+            best_ms = ms[ms.size() / 2];
+            best = sp;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(x); cudaFree(w); cudaFree(y); cudaFree(ws);
+    if (status != FBCORR_OK || best.empty()) {
+        tc_set_spec(p->tc, old);
+        return status != FBCORR_OK ? status : set_error(FBCORR_ERR_INTERNAL, "no variant ran");
+    }
+    FBC_TRY(tc_set_spec(p->tc, best));
+    p->fwd_source = "tuned";
+    tune_store(tune_key(p->dev, shape_key(p, "fwd")), best);
+    logf("autotune picked %s (%.4f ms)", best.c_str(), best_ms);
+    return FBCORR_OK;
+}
+
 fbcorr_status_t fbcorr_plan_info(fbcorr_plan_t p, char* buf, size_t cap) {
     clear_error();
     if (!p || !buf || cap == 0) return set_error(FBCORR_ERR_INVALID_ARG, "NULL argument");
@@ -535,9 +673,9 @@ fbcorr_status_t fbcorr_plan_info(fbcorr_plan_t p, char* buf, size_t cap) {
     } else if (p->fwd_kind == VarKind::Default) {
         o << ",\"spec\":\"default\"";
     } else if (p->tc) {
-        o << ",\"spec\":\"" << tc_describe(p->tc) << "\"";
+        o << ",\"spec\":\"" << tc_spec(p->tc) << "\",\"detail\":" << tc_describe(p->tc);
     }
-    o << "},\"bwd_ready\":" << (p->bwd_ready ? 1 : 0);
+    o << ",\"launches\":" << plan_launches_per_forward(p) << "},\"bwd_ready\":" << (p->bwd_ready ? 1 : 0);
     if (p->bwd_ready) {
         o << ",\"dx\":{\"kind\":\"" << kind_name(p->dx_kind) << "\"";
         if (p->dx_kind == VarKind::Direct) o << ",\"spec\":\"" << direct_tile_spec(p->dx_tile) << "\"";

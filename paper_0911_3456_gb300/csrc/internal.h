@@ -119,9 +119,14 @@ fbcorr_status_t tc_plan_create(TcPlan** out, int H, int W, int D, int N, int fh,
                                int split, int epi, float lo, float hi, const DeviceInfo& dev);
 void tc_plan_destroy(TcPlan* p);
 size_t tc_workspace_bytes(const TcPlan* p);
+// ev_start / ev_stop (may be null): recorded around the main GEMM kernel.
 fbcorr_status_t tc_forward(TcPlan* p, const float* x, const float* w, float* y, void* ws,
-                           int* err_word, cudaStream_t s);
-std::string tc_describe(const TcPlan* p);
+                           int* err_word, cudaStream_t s, cudaEvent_t ev_start, cudaEvent_t ev_stop);
+int tc_launches(const TcPlan* p);
+std::string tc_describe(const TcPlan* p);           // JSON object
+std::string tc_spec(const TcPlan* p);               // "tcgen05:na=..,nb=..,nt=.."
+std::vector<std::string> tc_candidates(TcPlan* p);  // feasible specs, default first
+fbcorr_status_t tc_set_spec(TcPlan* p, const std::string& spec);
 
 // ---- tune cache ----------------------------------------------------------------------
 std::string tune_key(const DeviceInfo& dev, const std::string& what);
@@ -158,4 +163,8 @@ struct fbcorr_plan {
     // bounded-wait failure flag in host-mapped memory
     int* err_host = nullptr;
     int* err_dev = nullptr;
+
+    // timing service: events around the main forward kernel
+    std::vector<cudaEvent_t> prof_start, prof_stop;
+    int prof_count = 0;
 };

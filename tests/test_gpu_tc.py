@@ -1,0 +1,163 @@
+"""GPU parity of the tcgen05 tensor-core path (BF16 and split-BF16) against the
+FP64 oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+from helpers import dev, host, normwise_rel, torch_cuda
+from paper_0911_3456_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"bf16": 1e-2, "bf16x3": 1e-5}
+
+
+def gamma(mode, K):
+    """Elementwise bound factor: |y - y_exact| <= gamma * sum_k |x_k w_k|.
+    BF16: each operand rounded (unit roundoff 2^-8) -> 2*2^-8 + 2^-16 per product.
+    Split BF16: v = hi + lo + e with |e| <= 2^-16 |v|; the dropped lo*lo term is
+    <= 2^-16 |xw| -> about 3.05 * 2^-16 per product.  Plus FP32 accumulation:
+    one rounding of at most 2 ulp (2^-22) per MMA into the accumulator, K/16
+    (BF16) or 3K/16 (split) MMAs."""
+    n_mma = (K + 15) // 16 * (3 if mode == "bf16x3" else 1)
+    per_term = (2 * 2.0 ** -8 + 2.0 ** -16) if mode == "bf16" else 3.05 * 2.0 ** -16
+    return per_term + n_mma * 2.0 ** -22
+
+
+def assert_within_bound(y, x, w, mode, clamp=None):
+    ref = oracle.fwd(x, w, epilogue=clamp)
+    absref = oracle.fwd(np.abs(x), np.abs(w))
+    K = w.shape[1] * w.shape[2] * w.shape[3]
+    bound = gamma(mode, K) * absref
+    excess = np.abs(y - ref) - bound
+    assert excess.max() <= 0, (mode, float(excess.max()), float(normwise_rel(y, ref)))
+
+SHAPES = [
+    # H, W, D, N, fh, fw: ragged tiles, N not a multiple of 16, N > 256 (two
+    # filter tiles), D below / above 16, fh != fw, 1x1 filters
+    (20, 150, 16, 16, 3, 3),
+    (37, 45, 3, 5, 4, 2),
+    (40, 200, 32, 64, 5, 5),
+    (33, 97, 8, 20, 3, 5),
+    (25, 140, 16, 300, 2, 3),
+    (18, 260, 48, 40, 7, 7),
+    (30, 131, 64, 256, 1, 1),
+    (9, 9, 4, 3, 9, 9),
+]
+
+
+def _plan(torch, mode, x, w, clamp=None):
+    from paper_0911_3456_gb300.api import Plan
+    return Plan(x.shape, w.shape, mode, clamp)
+
+
+@pytest.mark.parametrize("mode", ["bf16", "bf16x3"])
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(map(str, s)))
+def test_tc_matches_oracle(mode, shape):
+    torch = torch_cuda()
+    wl = inputs.random_case(1300, *shape)
+    p = _plan(torch, mode, wl.x, wl.w)
+    y = host(p.forward(dev(wl.x, torch), dev(wl.w, torch)))
+    torch.cuda.synchronize()
+    assert p.device_status() == 0
+    assert_within_bound(y, wl.x, wl.w, mode)
+    if mode == "bf16":
+        assert normwise_rel(y, oracle.fwd(wl.x, wl.w)) <= TOL[mode]
+
+
+@pytest.mark.parametrize("mode", ["bf16", "bf16x3"])
+@pytest.mark.parametrize("shape", SHAPES[:6], ids=lambda s: "x".join(map(str, s)))
+def test_tc_integer_bit_exact(mode, shape):
+    """Integers in [-4, 4] are exact in BF16 and every partial sum is an exact
+    FP32 integer: both modes must reproduce the oracle bit for bit."""
+    torch = torch_cuda()
+    wl = inputs.random_case(1400, *shape, kind="int")
+    p = _plan(torch, mode, wl.x, wl.w)
+    y = host(p.forward(dev(wl.x, torch), dev(wl.w, torch)))
+    assert np.array_equal(y, oracle.fwd(wl.x, wl.w))
+
+
+@pytest.mark.parametrize("mode", ["bf16", "bf16x3"])
+def test_tc_clamp(mode):
+    torch = torch_cuda()
+    wl = inputs.random_case(1500, 40, 133, 16, 48, 3, 3)
+    clamp = (-0.5, 0.5)
+    p = _plan(torch, mode, wl.x, wl.w, clamp)
+    y = host(p.forward(dev(wl.x, torch), dev(wl.w, torch)))
+    assert_within_bound(y, wl.x, wl.w, mode, clamp)   # the clamp is 1-Lipschitz
+    assert y.min() >= -0.5 and y.max() <= 0.5
+
+
+def test_tc_delta_filters_bit_exact():
+    """Unit-impulse filters copy shifted input windows; with BF16-representable
+    inputs both modes are exact."""
+    torch = torch_cuda()
+    rng = np.random.default_rng(4)
+    H, W, D, fh, fw = 20, 150, 16, 3, 4
+    x = rng.integers(-64, 64, (H, W, D)).astype(np.float32) / 8.0
+    taps = [(i, j, d) for i in range(fh) for j in range(fw) for d in (0, 5, 15)]
+    w = np.zeros((len(taps), fh, fw, D), np.float32)
+    for n, (i, j, d) in enumerate(taps):
+        w[n, i, j, d] = 1.0
+    Ho, Wo = H - fh + 1, W - fw + 1
+    for mode in ("bf16", "bf16x3"):
+        y = host(_plan(torch, mode, x, w).forward(dev(x, torch), dev(w, torch)))
+        for n, (i, j, d) in enumerate(taps):
+            assert np.array_equal(y[:, :, n], x[i:i + Ho, j:j + Wo, d].astype(np.float64)), (mode, i, j, d)
+
+
+def test_tc_deterministic_and_guard_bands():
+    torch = torch_cuda()
+    wl = inputs.random_case(1600, 30, 170, 32, 96, 5, 5)
+    p = _plan(torch, "bf16x3", wl.x, wl.w)
+    x, w = dev(wl.x, torch), dev(wl.w, torch)
+    n = int(np.prod(p.out_shape))
+    buf = torch.full((n + 4096,), 7.0, device="cuda")
+    y = buf[2048:2048 + n].view(p.out_shape)
+    p.forward(x, w, y=y)
+    a = y.clone()
+    p.forward(x, w, y=y)
+    torch.cuda.synchronize()
+    assert torch.equal(a, y)
+    assert torch.all(buf[:2048] == 7.0) and torch.all(buf[2048 + n:] == 7.0)
+
+
+def test_precision_config_full_size():
+    """512x512x32 U[-1,1) input, 256 filters 5x5x32 N(0, 1/800): split-BF16 at
+    <= 1e-5 and BF16 at <= 1e-2 (normwise) on output rows spanning the image
+    (first, last, and a band in the middle), plus random points."""
+    torch = torch_cuda()
+    wl = inputs.workload_precision()
+    x, w = dev(wl.x, torch), dev(wl.w, torch)
+    rows = [0, 1, 250, 251, 252, 506, 507]
+    Ho, Wo, N = wl.out_shape
+    rng = np.random.default_rng(12)
+    idx = np.stack([rng.integers(0, Ho, 4000), rng.integers(0, Wo, 4000), rng.integers(0, N, 4000)], 1)
+    ref_pts = oracle.fwd_points(wl.x, wl.w, idx)
+    errs = {}
+    for mode in ("bf16", "bf16x3"):
+        p = _plan(torch, mode, wl.x, wl.w)
+        y = host(p.forward(x, w))
+        assert p.device_status() == 0
+        e = 0.0
+        for r in rows:
+            ref = oracle.fwd(wl.x[r:r + 5], wl.w)[0]
+            e = max(e, np.abs(y[r] - ref).max() / np.abs(ref).max())
+        e = max(e, np.abs(y[tuple(idx.T)] - ref_pts).max() / np.abs(ref_pts).max())
+        errs[mode] = e
+        assert e <= TOL[mode], (mode, e)
+    print("precision config errors:", errs)
+
+
+def test_split_beats_bf16_and_approaches_fp32():
+    """On zero-mean, unit-norm filters (the paper's first table row, 256x256x8
+    with 64 filters 9x9x8) split-BF16 stays within 1e-5 normwise while plain
+    BF16 does not reach it."""
+    torch = torch_cuda()
+    wl = inputs.workload_paper_row1_clamp()
+    x, w = dev(wl.x, torch), dev(wl.w, torch)
+    ref = oracle.fwd(wl.x, wl.w)
+    e = {}
+    for mode in ("bf16", "bf16x3"):
+        e[mode] = normwise_rel(host(_plan(torch, mode, wl.x, wl.w).forward(x, w)), ref)
+    assert e["bf16x3"] <= 1e-5 < e["bf16"] <= 1e-2, e
