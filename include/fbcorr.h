@@ -151,6 +151,25 @@ fbcorr_status_t fbcorr_plan_profile(fbcorr_plan_t plan, int capacity);
  * then clears the record. */
 fbcorr_status_t fbcorr_plan_profile_read(fbcorr_plan_t plan, float* ms, int cap, int* n);
 
+/* Forward without any device allocation.  The paper has no counterpart: this
+ * is for callers that cannot allocate device memory when they run the
+ * correlation (no cudaMalloc after start-up in a real-time loop, a plugin host
+ * whose allocator belongs to another runtime, a process that budgets all
+ * device memory at initialisation).  It runs the same kernels as
+ * fbcorr_forward, but the scratch that tensor-core plans need (the BF16 copies
+ * of x and w) lives in one 48 MiB array built into the library, which every
+ * GPU that loads the library keeps until the process exits.  Plans whose
+ * forward workspace (fbcorr_plan_workspace_size) exceeds 48 MiB are rejected
+ * with FBCORR_ERR_WORKSPACE; FP32 plans need no scratch.  The first call on a
+ * device looks up the array's device address, so make that first call before
+ * any stream capture.  All calls on a device share the one array: calls whose
+ * GPU work may overlap (different streams, or different threads without
+ * ordering) race on it; order them on one stream.  The array keeps the last
+ * call's contents; every call rewrites all the scratch it reads first.
+ * Calls no cudaMalloc, cudaFree or other allocating routine. */
+fbcorr_status_t fbcorr_forward_noalloc(fbcorr_plan_t plan, const float* x, const float* w,
+                                       float* y, fbcorr_stream_t stream);
+
 /* ---- batches of uneven images ------------------------------------------- */
 
 /* A plan for n independent problems, image k with in_shapes[k] = {H, W, D}

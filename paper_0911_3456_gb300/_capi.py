@@ -59,6 +59,7 @@ PROTOTYPES = {
     "fbcorr_plan_set_variant": (_st, [_vp, ctypes.c_char_p]),
     "fbcorr_plan_info": (_st, [_vp, ctypes.c_char_p, _sz]),
     "fbcorr_plan_device_status": (_st, [_vp, ctypes.c_int]),
+    "fbcorr_forward_noalloc": (_st, [_vp, _vp, _vp, _vp, _vp]),
     "fbcorr_plan_profile": (_st, [_vp, ctypes.c_int]),
     "fbcorr_plan_profile_read": (_st, [_vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_int)]),
