@@ -203,6 +203,13 @@ fbcorr_status_t fbcorr_rtcg_check(const int64_t in_shape[3], const int64_t filt_
                                   fbcorr_epilogue_t epilogue, const char* spec, char* log,
                                   size_t cap);
 
+/* The same offline check for a batch plan: generate and compile (without
+ * loading) the single persistent kernel that fbcorr_batch_plan_create would
+ * build for these n images.  Needs no GPU. */
+fbcorr_status_t fbcorr_batch_rtcg_check(int n, const int64_t (*in_shapes)[3],
+                                        const int64_t (*filt_shapes)[4], fbcorr_epilogue_t epilogue,
+                                        char* log, size_t cap);
+
 #ifdef __cplusplus
 }
 #endif

@@ -74,6 +74,8 @@ PROTOTYPES = {
     "fbcorr_last_error": (ctypes.c_char_p, []),
     "fbcorr_version": (ctypes.c_char_p, []),
     "fbcorr_rtcg_check": (_st, [I64_3, I64_4, Epilogue, ctypes.c_char_p, ctypes.c_char_p, _sz]),
+    "fbcorr_batch_rtcg_check": (_st, [ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
+                                      ctypes.POINTER(ctypes.c_int64), Epilogue, ctypes.c_char_p, _sz]),
 }
 
 _lib = None

@@ -85,8 +85,8 @@ DirectProblem dx_problem(const fbcorr_plan* p) {
 
 std::string kname_for(const char* base, const DirectProblem& pr, const DirectTile& t) {
     char b[160];
-    snprintf(b, sizeof b, "%s_f%dx%d_c%d_t%d_%d_%d_%d_fl%d_e%d_m%d", base, pr.fh, pr.fw, pr.c, t.tr,
-             t.tf, t.wr, t.wf, pr.flip, pr.epi, pr.mask);
+    snprintf(b, sizeof b, "%s_f%dx%d_c%d_t%d_%d_%d_%d_cc%d_fl%d_e%d_m%d", base, pr.fh, pr.fw, pr.c,
+             t.tr, t.tf, t.wr, t.wf, t.chunk(pr.c), pr.flip, pr.epi, pr.mask);
     return b;
 }
 
@@ -226,8 +226,10 @@ void plan_dw_chunks(fbcorr_plan* p) {
     p->ws_bwd = (size_t)p->dw_chunks * p->N * p->fh * p->fw * p->D * sizeof(float);
 }
 
-fbcorr_status_t validate_shapes(const int64_t* in, const int64_t* fs, fbcorr_dtype_t dtype,
-                                const fbcorr_epilogue_t& epi) {
+}  // namespace
+
+fbcorr_status_t fbc::validate_shapes(const int64_t* in, const int64_t* fs, fbcorr_dtype_t dtype,
+                                     const fbcorr_epilogue_t& epi) {
     if (!in || !fs) return set_error(FBCORR_ERR_INVALID_ARG, "null shape array");
     if (dtype != FBCORR_F32 && dtype != FBCORR_BF16 && dtype != FBCORR_BF16X3)
         return set_error(FBCORR_ERR_INVALID_ARG, "unknown dtype %d", (int)dtype);
@@ -250,6 +252,7 @@ fbcorr_status_t validate_shapes(const int64_t* in, const int64_t* fs, fbcorr_dty
     return FBCORR_OK;
 }
 
+namespace {
 }  // namespace
 
 extern "C" {

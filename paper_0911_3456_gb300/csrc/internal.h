@@ -64,6 +64,12 @@ fbcorr_status_t rtcg_kernel(const std::string& src, const std::string& name, siz
 // Compile only (no GPU needed); returns the NVRTC log on failure.
 fbcorr_status_t rtcg_compile_only(const std::string& src, std::string* log);
 fbcorr_status_t launch(const Kernel& k, dim3 grid, void** args, cudaStream_t stream);
+// CUDA-graph kernel nodes for NVRTC kernels (driver API under the hood).
+fbcorr_status_t graph_add_kernel(cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps,
+                                 const Kernel& k, dim3 grid, void** args, cudaGraphNode_t* out);
+fbcorr_status_t graph_set_kernel(cudaGraphExec_t e, cudaGraphNode_t n, const Kernel& k, dim3 grid,
+                                 void** args);
+fbcorr_status_t kernel_occupancy(const Kernel& k, int* blocks_per_sm);
 const char* rtcg_header_source();   // contents of rtcg_direct.cuh
 
 // ---- variants ------------------------------------------------------------------
@@ -71,6 +77,8 @@ enum class VarKind { Default = 0, Direct = 1, Tensor = 2 };
 
 struct DirectTile {
     int tr = 8, tf = 8, wr = 1, wf = 2;
+    int cc = 0;   // input channels staged per chunk; 0 = the whole depth
+    int chunk(int c) const { return (cc > 0 && cc < c) ? cc : c; }
     int bh() const { return tr * wr; }
     int bn() const { return tf * wf; }
     int threads() const { return 32 * wr * wf; }
@@ -89,8 +97,12 @@ struct DirectProblem {
 };
 std::string direct_kernel_source(const DirectProblem& pr, const DirectTile& t,
                                  const std::string& kname);
-std::vector<DirectTile> direct_candidates(const DirectProblem& pr, size_t smem_limit);
-DirectTile direct_heuristic(const DirectProblem& pr, size_t smem_limit, int sm_count);
+// threads > 0 restricts the candidates to one CTA size (the batched kernel).
+// max_block bounds the per-thread accumulator block TR*TF (register pressure).
+std::vector<DirectTile> direct_candidates(const DirectProblem& pr, size_t smem_limit,
+                                          int threads = 0, int max_block = 64);
+DirectTile direct_heuristic(const DirectProblem& pr, size_t smem_limit, int sm_count,
+                            int threads = 0, int max_block = 64);
 
 struct DwTile {
     int tn = 4, threads = 128, chunks = 0;   // chunks = 0: choose from the SM count
@@ -127,6 +139,10 @@ std::string tc_describe(const TcPlan* p);           // JSON object
 std::string tc_spec(const TcPlan* p);               // "tcgen05:na=..,nb=..,nt=.."
 std::vector<std::string> tc_candidates(TcPlan* p);  // feasible specs, default first
 fbcorr_status_t tc_set_spec(TcPlan* p, const std::string& spec);
+
+// ---- argument validation (api.cu) -------------------------------------------------------
+fbcorr_status_t validate_shapes(const int64_t* in, const int64_t* fs, fbcorr_dtype_t dtype,
+                                const fbcorr_epilogue_t& epi);
 
 // ---- tune cache ----------------------------------------------------------------------
 std::string tune_key(const DeviceInfo& dev, const std::string& what);

@@ -34,6 +34,11 @@ struct DriverApi {
                              unsigned, unsigned, CUstream, void**, void**) = nullptr;
     CUresult (*ctxGetCurrent)(CUcontext*) = nullptr;
     CUresult (*getErrorString)(CUresult, const char**) = nullptr;
+    CUresult (*graphAddKernelNode)(CUgraphNode*, CUgraph, const CUgraphNode*, size_t,
+                                   const CUDA_KERNEL_NODE_PARAMS*) = nullptr;
+    CUresult (*graphExecKernelNodeSetParams)(CUgraphExec, CUgraphNode,
+                                             const CUDA_KERNEL_NODE_PARAMS*) = nullptr;
+    CUresult (*occupancy)(int*, CUfunction, int, size_t) = nullptr;
 };
 
 std::mutex g_mu;
@@ -59,7 +64,10 @@ fbcorr_status_t driver_api(DriverApi** out) {
                   resolve("cuFuncSetAttribute", &d.funcSetAttribute) &&
                   resolve("cuLaunchKernel", &d.launchKernel) &&
                   resolve("cuCtxGetCurrent", &d.ctxGetCurrent) &&
-                  resolve("cuGetErrorString", &d.getErrorString);
+                  resolve("cuGetErrorString", &d.getErrorString) &&
+                  resolve("cuGraphAddKernelNode", &d.graphAddKernelNode) &&
+                  resolve("cuGraphExecKernelNodeSetParams", &d.graphExecKernelNodeSetParams) &&
+                  resolve("cuOccupancyMaxActiveBlocksPerMultiprocessor", &d.occupancy);
         if (!ok) return set_error(FBCORR_ERR_CUDA, "could not resolve CUDA driver entry points");
         d.ok = true;
         g_drv = d;
@@ -265,6 +273,58 @@ fbcorr_status_t launch(const Kernel& k, dim3 grid, void** args, cudaStream_t str
     if (r != CUDA_SUCCESS)
         return set_error(FBCORR_ERR_CUDA, "cuLaunchKernel(%s grid=%u,%u,%u block=%d smem=%zu): %s",
                          k.name.c_str(), grid.x, grid.y, grid.z, k.threads, k.smem, cu_err(r));
+    return FBCORR_OK;
+}
+
+namespace {
+CUDA_KERNEL_NODE_PARAMS node_params(const Kernel& k, dim3 grid, void** args) {
+    CUDA_KERNEL_NODE_PARAMS np;
+    memset(&np, 0, sizeof np);
+    np.func = k.fn;
+    np.gridDimX = grid.x;
+    np.gridDimY = grid.y;
+    np.gridDimZ = grid.z;
+    np.blockDimX = (unsigned)k.threads;
+    np.blockDimY = 1;
+    np.blockDimZ = 1;
+    np.sharedMemBytes = (unsigned)k.smem;
+    np.kernelParams = args;
+    np.extra = nullptr;
+    return np;
+}
+}  // namespace
+
+fbcorr_status_t graph_add_kernel(cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps,
+                                 const Kernel& k, dim3 grid, void** args, cudaGraphNode_t* out) {
+    DriverApi* drv = nullptr;
+    FBC_TRY(driver_api(&drv));
+    const CUDA_KERNEL_NODE_PARAMS np = node_params(k, grid, args);
+    CUresult r = drv->graphAddKernelNode((CUgraphNode*)out, (CUgraph)g, (const CUgraphNode*)deps,
+                                         ndeps, &np);
+    if (r != CUDA_SUCCESS)
+        return set_error(FBCORR_ERR_CUDA, "cuGraphAddKernelNode(%s): %s", k.name.c_str(), cu_err(r));
+    return FBCORR_OK;
+}
+
+fbcorr_status_t graph_set_kernel(cudaGraphExec_t e, cudaGraphNode_t n, const Kernel& k, dim3 grid,
+                                 void** args) {
+    DriverApi* drv = nullptr;
+    FBC_TRY(driver_api(&drv));
+    const CUDA_KERNEL_NODE_PARAMS np = node_params(k, grid, args);
+    CUresult r = drv->graphExecKernelNodeSetParams((CUgraphExec)e, (CUgraphNode)n, &np);
+    if (r != CUDA_SUCCESS)
+        return set_error(FBCORR_ERR_CUDA, "cuGraphExecKernelNodeSetParams(%s): %s", k.name.c_str(),
+                         cu_err(r));
+    return FBCORR_OK;
+}
+
+fbcorr_status_t kernel_occupancy(const Kernel& k, int* blocks_per_sm) {
+    DriverApi* drv = nullptr;
+    FBC_TRY(driver_api(&drv));
+    CUresult r = drv->occupancy(blocks_per_sm, k.fn, k.threads, k.smem);
+    if (r != CUDA_SUCCESS)
+        return set_error(FBCORR_ERR_CUDA, "cuOccupancyMaxActiveBlocksPerMultiprocessor(%s): %s",
+                         k.name.c_str(), cu_err(r));
     return FBCORR_OK;
 }
 

@@ -35,13 +35,17 @@ struct FbcOdd { static constexpr int value = (V % 2 == 1) ? V : V + 1; };
 // One CTA computes an output block of BH = TR*WR rows x 32 columns x BN = TF*WF
 // output channels.  Lane l of a warp owns output column q0 + l; warp (wr, wf)
 // owns rows wr*TR .. +TR and channels wf*TF .. +TF, so each thread holds a
-// TR x TF accumulator block.  The input halo is staged in shared memory as
-// [row][channel][column] (odd column pitch: conflict-free column reads), the
-// CTA's slice of the bank as [i][j][channel][BN+4] so that a warp's TF filter
-// values are one broadcast float4 read per 4 filters.  For a fixed (j, c) a
-// thread loads TR+FH-1 input values once and reuses them for all FH filter
-// rows: TR*TF*FH FMAs per TR+FH-1 scalar and FH*TF/4 vector shared loads.
-template <int FH, int FW, int C, int TR, int TF, int WR, int WF, int FLIP, int EPI, int MASK>
+// TR x TF accumulator block.  The input depth is processed in chunks of CC
+// channels: per chunk the input halo is staged in shared memory as
+// [row][channel][column] (odd column pitch: conflict-free column reads) and
+// the CTA's slice of the bank as [i][j][channel][BN+4], so that a warp's TF
+// filter values are one broadcast float4 read per 4 filters.  For a fixed
+// (j, c) a thread loads TR+FH-1 input values once and reuses them for all FH
+// filter rows: TR*TF*FH FMAs per TR+FH-1 scalar and FH*TF/4 vector shared loads.
+// Chunking bounds shared memory by CC instead of the full depth C, so large
+// filters (11x11x32) and deep inputs (the 64-channel gradient of dL/dx) keep
+// several CTAs resident per SM.
+template <int FH, int FW, int C, int TR, int TF, int WR, int WF, int FLIP, int EPI, int MASK, int CC>
 struct FbcDirect {
     static constexpr int BW = 32;
     static constexpr int BH = TR * WR;
@@ -51,13 +55,100 @@ struct FbcDirect {
     static constexpr int HC = BW + FW - 1;
     static constexpr int COLP = FbcOdd<HC>::value;
     static constexpr int BNP = BN + 4;
-    static constexpr int XS = ((HR * C * COLP + 3) / 4) * 4;    // floats, 16-byte multiple
-    static constexpr int WS = FH * FW * C * BNP;
+    static constexpr int NCHUNK = (C + CC - 1) / CC;
+    static constexpr int XS = ((HR * CC * COLP + 3) / 4) * 4;   // floats, 16-byte multiple
+    static constexpr int WS = FH * FW * CC * BNP;
     static constexpr int SMEM_BYTES = (XS + WS) * 4;
     static_assert(TF % 4 == 0, "TF must be a multiple of 4");
 
     static __device__ __forceinline__ float mask_val(float v, float mv, float lo, float hi) {
         return (mv > lo && mv < hi) ? v : 0.0f;
+    }
+
+    // Stage input channels [c0, c0+CC) of the halo and the matching bank slice.
+    static __device__ __forceinline__ void stage(const FbcDirectArgs& a, float* xs, float* ws, int c0,
+                                                 int p0, int q0, int f0) {
+        const int tid = threadIdx.x;
+        if (C % 4 == 0 && CC % 4 == 0) {
+            constexpr int C4 = CC / 4;
+            for (int e = tid; e < HR * HC * C4; e += NT) {
+                const int c4 = e % C4;
+                const int t = e / C4;
+                const int col = t % HC;
+                const int row = t / HC;
+                const int gy = p0 - a.pad_y + row;
+                const int gx = q0 - a.pad_x + col;
+                const int c = c0 + c4 * 4;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (gy >= 0 && gy < a.in_h && gx >= 0 && gx < a.in_w && c < C) {
+                    const long long off = ((long long)gy * a.in_w + gx) * C + c;
+                    v = __ldg(reinterpret_cast<const float4*>(a.x + off));
+                    if (MASK) {
+                        const float4 mv = __ldg(reinterpret_cast<const float4*>(a.m + off));
+                        v.x = mask_val(v.x, mv.x, a.lo, a.hi);
+                        v.y = mask_val(v.y, mv.y, a.lo, a.hi);
+                        v.z = mask_val(v.z, mv.z, a.lo, a.hi);
+                        v.w = mask_val(v.w, mv.w, a.lo, a.hi);
+                    }
+                }
+                float* dst = xs + (row * CC + c4 * 4) * COLP + col;
+                dst[0] = v.x;
+                dst[COLP] = v.y;
+                dst[2 * COLP] = v.z;
+                dst[3 * COLP] = v.w;
+            }
+        } else {
+            for (int e = tid; e < HR * HC * CC; e += NT) {
+                const int cl = e % CC;
+                const int t = e / CC;
+                const int col = t % HC;
+                const int row = t / HC;
+                const int gy = p0 - a.pad_y + row;
+                const int gx = q0 - a.pad_x + col;
+                const int c = c0 + cl;
+                float v = 0.f;
+                if (gy >= 0 && gy < a.in_h && gx >= 0 && gx < a.in_w && c < C) {
+                    const long long off = ((long long)gy * a.in_w + gx) * C + c;
+                    v = __ldg(a.x + off);
+                    if (MASK) v = mask_val(v, __ldg(a.m + off), a.lo, a.hi);
+                }
+                xs[(row * CC + cl) * COLP + col] = v;
+            }
+        }
+        if (!FLIP) {
+            // forward: ws[i][j][cl][f] = w[f0+f][i][j][c0+cl]; global reads along c
+            for (int e = tid; e < BN * FH * FW * CC; e += NT) {
+                const int cl = e % CC;
+                int t = e / CC;
+                const int j = t % FW;
+                t /= FW;
+                const int i = t % FH;
+                const int f = t / FH;
+                const int n = f0 + f;
+                const int c = c0 + cl;
+                const float v = (n < a.nf && c < C)
+                    ? __ldg(a.w + (((long long)n * FH + i) * FW + j) * C + c) : 0.f;
+                ws[((i * FW + j) * CC + cl) * BNP + f] = v;
+            }
+        } else {
+            // dL/dx: output channel f is the bank's depth index, input channel c
+            // its filter index: ws[i][j][cl][f] = w[c0+cl][FH-1-i][FW-1-j][f0+f];
+            // global reads along f
+            for (int e = tid; e < BN * FH * FW * CC; e += NT) {
+                const int f = e % BN;
+                int t = e / BN;
+                const int j = t % FW;
+                t /= FW;
+                const int i = t % FH;
+                const int cl = t / FH;
+                const int n = f0 + f;
+                const int c = c0 + cl;
+                const float v = (n < a.nf && c < C)
+                    ? __ldg(a.w + (((long long)c * FH + (FH - 1 - i)) * FW + (FW - 1 - j)) * a.nf + n)
+                    : 0.f;
+                ws[((i * FW + j) * CC + cl) * BNP + f] = v;
+            }
+        }
     }
 
     static __device__ __forceinline__ void run(const FbcDirectArgs& a, float* smem,
@@ -73,118 +164,43 @@ struct FbcDirect {
         float* xs = smem;
         float* ws = smem + XS;
 
-        // ---- stage the input halo: rows p0-pad_y .. +HR, columns q0-pad_x .. +HC
-        if (C % 4 == 0) {
-            constexpr int C4 = C / 4;
-            for (int e = tid; e < HR * HC * C4; e += NT) {
-                const int c4 = e % C4;
-                const int t = e / C4;
-                const int col = t % HC;
-                const int row = t / HC;
-                const int gy = p0 - a.pad_y + row;
-                const int gx = q0 - a.pad_x + col;
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (gy >= 0 && gy < a.in_h && gx >= 0 && gx < a.in_w) {
-                    const long long off = ((long long)gy * a.in_w + gx) * C + c4 * 4;
-                    v = __ldg(reinterpret_cast<const float4*>(a.x + off));
-                    if (MASK) {
-                        const float4 mv = __ldg(reinterpret_cast<const float4*>(a.m + off));
-                        v.x = mask_val(v.x, mv.x, a.lo, a.hi);
-                        v.y = mask_val(v.y, mv.y, a.lo, a.hi);
-                        v.z = mask_val(v.z, mv.z, a.lo, a.hi);
-                        v.w = mask_val(v.w, mv.w, a.lo, a.hi);
-                    }
-                }
-                float* dst = xs + (row * C + c4 * 4) * COLP + col;
-                dst[0] = v.x;
-                dst[COLP] = v.y;
-                dst[2 * COLP] = v.z;
-                dst[3 * COLP] = v.w;
-            }
-        } else {
-            for (int e = tid; e < HR * HC * C; e += NT) {
-                const int c = e % C;
-                const int t = e / C;
-                const int col = t % HC;
-                const int row = t / HC;
-                const int gy = p0 - a.pad_y + row;
-                const int gx = q0 - a.pad_x + col;
-                float v = 0.f;
-                if (gy >= 0 && gy < a.in_h && gx >= 0 && gx < a.in_w) {
-                    const long long off = ((long long)gy * a.in_w + gx) * C + c;
-                    v = __ldg(a.x + off);
-                    if (MASK) v = mask_val(v, __ldg(a.m + off), a.lo, a.hi);
-                }
-                xs[(row * C + c) * COLP + col] = v;
-            }
-        }
-
-        // ---- stage this CTA's BN output channels of the bank as [i][j][c][BNP]
-        if (!FLIP) {
-            // forward: ws[i][j][c][f] = w[f0+f][i][j][c]; global reads along c
-            for (int e = tid; e < BN * FH * FW * C; e += NT) {
-                const int c = e % C;
-                int t = e / C;
-                const int j = t % FW;
-                t /= FW;
-                const int i = t % FH;
-                const int f = t / FH;
-                const int n = f0 + f;
-                const float v = (n < a.nf) ? __ldg(a.w + (((long long)n * FH + i) * FW + j) * C + c) : 0.f;
-                ws[((i * FW + j) * C + c) * BNP + f] = v;
-            }
-        } else {
-            // dL/dx: output channel f is the bank's depth index, input channel c
-            // its filter index: ws[i][j][c][f] = w[c][FH-1-i][FW-1-j][f0+f];
-            // global reads along f
-            for (int e = tid; e < BN * FH * FW * C; e += NT) {
-                const int f = e % BN;
-                int t = e / BN;
-                const int j = t % FW;
-                t /= FW;
-                const int i = t % FH;
-                const int c = t / FH;
-                const int n = f0 + f;
-                const float v = (n < a.nf)
-                    ? __ldg(a.w + (((long long)c * FH + (FH - 1 - i)) * FW + (FW - 1 - j)) * a.nf + n)
-                    : 0.f;
-                ws[((i * FW + j) * C + c) * BNP + f] = v;
-            }
-        }
-        __syncthreads();
-
-        // ---- register-blocked FMA loop
         float acc[TR][TF];
 #pragma unroll
         for (int r = 0; r < TR; ++r)
 #pragma unroll
             for (int f = 0; f < TF; ++f) acc[r][f] = 0.f;
 
-        const float* xb = xs + (wr * TR) * C * COLP + lane;
+        const float* xb = xs + (wr * TR) * CC * COLP + lane;
         const float* wb = ws + wf * TF;
 #pragma unroll 1
-        for (int j = 0; j < FW; ++j) {
+        for (int ch = 0; ch < NCHUNK; ++ch) {
+            if (ch > 0) __syncthreads();   // every thread is done reading the previous chunk
+            stage(a, xs, ws, ch * CC, p0, q0, f0);
+            __syncthreads();
+#pragma unroll 1
+            for (int j = 0; j < FW; ++j) {
 #pragma unroll 2
-            for (int c = 0; c < C; ++c) {
-                float xv[TR + FH - 1];
+                for (int c = 0; c < CC; ++c) {
+                    float xv[TR + FH - 1];
 #pragma unroll
-                for (int k = 0; k < TR + FH - 1; ++k) xv[k] = xb[(k * C + c) * COLP + j];
+                    for (int k = 0; k < TR + FH - 1; ++k) xv[k] = xb[(k * CC + c) * COLP + j];
 #pragma unroll
-                for (int i = 0; i < FH; ++i) {
-                    float wv[TF];
-                    const float4* wp = reinterpret_cast<const float4*>(wb + ((i * FW + j) * C + c) * BNP);
+                    for (int i = 0; i < FH; ++i) {
+                        float wv[TF];
+                        const float4* wp = reinterpret_cast<const float4*>(wb + ((i * FW + j) * CC + c) * BNP);
 #pragma unroll
-                    for (int f4 = 0; f4 < TF / 4; ++f4) {
-                        const float4 t4 = wp[f4];
-                        wv[4 * f4 + 0] = t4.x;
-                        wv[4 * f4 + 1] = t4.y;
-                        wv[4 * f4 + 2] = t4.z;
-                        wv[4 * f4 + 3] = t4.w;
+                        for (int f4 = 0; f4 < TF / 4; ++f4) {
+                            const float4 t4 = wp[f4];
+                            wv[4 * f4 + 0] = t4.x;
+                            wv[4 * f4 + 1] = t4.y;
+                            wv[4 * f4 + 2] = t4.z;
+                            wv[4 * f4 + 3] = t4.w;
+                        }
+#pragma unroll
+                        for (int r = 0; r < TR; ++r)
+#pragma unroll
+                            for (int f = 0; f < TF; ++f) acc[r][f] = fmaf(xv[r + i], wv[f], acc[r][f]);
                     }
-#pragma unroll
-                    for (int r = 0; r < TR; ++r)
-#pragma unroll
-                        for (int f = 0; f < TF; ++f) acc[r][f] = fmaf(xv[r + i], wv[f], acc[r][f]);
                 }
             }
         }
@@ -318,3 +334,37 @@ struct FbcDw {
         }
     }
 };
+
+// ---- batched persistent forward ----------------------------------------------
+// One launch serves many images, each with its own shape and bank.  Work items
+// (image, tile_x, tile_y, tile_f) are sorted largest-first on the host and
+// handed out through an atomic counter; the generated kernel switches on the
+// image's variant (filter size, depth, tile) and runs that variant's FbcDirect
+// tile.  Per-image pointers are kernel parameters; shapes live in `meta`.
+struct FbcBatchPtrs {
+    const float* x;
+    const float* w;
+    float* y;
+};
+
+template <int NIMG>
+struct FbcBatchArgs {
+    const int4* __restrict__ work;   // nwork items
+    const int* __restrict__ meta;    // per image: in_h, in_w, out_h, out_w, nf, variant
+    int* counter;                    // zeroed before every launch
+    int nwork;
+    float lo, hi;
+    int pad_;
+    FbcBatchPtrs img[NIMG];
+};
+
+__device__ __forceinline__ bool fbc_batch_next(int* counter, int nwork, int* s_item, int4* wk,
+                                               const int4* __restrict__ work) {
+    if (threadIdx.x == 0) *s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int item = *s_item;
+    __syncthreads();
+    if (item >= nwork) return false;
+    *wk = work[item];
+    return true;
+}

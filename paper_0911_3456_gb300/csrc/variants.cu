@@ -21,27 +21,30 @@ namespace fbc {
 const char* rtcg_header_source() { return kRtcgDirectSrc; }
 
 size_t direct_smem_bytes(const DirectTile& t, int fh, int fw, int c) {
+    const long cc = t.chunk(c);
     const long bh = t.tr * t.wr, bn = t.tf * t.wf;
     const long hr = bh + fh - 1, hc = 32 + fw - 1;
     const long colp = (hc % 2 == 1) ? hc : hc + 1;
     const long bnp = bn + 4;
-    const long xs = ((hr * c * colp + 3) / 4) * 4;
-    const long ws = (long)fh * fw * c * bnp;
+    const long xs = ((hr * cc * colp + 3) / 4) * 4;
+    const long ws = (long)fh * fw * cc * bnp;
     return (size_t)(xs + ws) * 4;
 }
 
 std::string direct_tile_spec(const DirectTile& t) {
-    char b[96];
-    snprintf(b, sizeof b, "direct:tr=%d,tf=%d,wr=%d,wf=%d", t.tr, t.tf, t.wr, t.wf);
+    char b[112];
+    snprintf(b, sizeof b, "direct:tr=%d,tf=%d,wr=%d,wf=%d,cc=%d", t.tr, t.tf, t.wr, t.wf, t.cc);
     return b;
 }
 
 bool parse_direct_spec(const std::string& s, DirectTile* t) {
     DirectTile d;
-    if (sscanf(s.c_str(), "direct:tr=%d,tf=%d,wr=%d,wf=%d", &d.tr, &d.tf, &d.wr, &d.wf) != 4)
-        return false;
+    const int n = sscanf(s.c_str(), "direct:tr=%d,tf=%d,wr=%d,wf=%d,cc=%d", &d.tr, &d.tf, &d.wr,
+                         &d.wf, &d.cc);
+    if (n != 4 && n != 5) return false;
+    if (n == 4) d.cc = 0;
     if (d.tr < 1 || d.tr > 16 || (d.tf != 4 && d.tf != 8 && d.tf != 12 && d.tf != 16) ||
-        d.wr < 1 || d.wf < 1 || d.threads() > 1024)
+        d.wr < 1 || d.wf < 1 || d.threads() > 1024 || d.cc < 0 || d.cc > 4096)
         return false;
     *t = d;
     return true;
@@ -53,7 +56,7 @@ std::string direct_kernel_source(const DirectProblem& pr, const DirectTile& t,
     o << rtcg_header_source() << "\n";
     o << "typedef FbcDirect<" << pr.fh << "," << pr.fw << "," << pr.c << "," << t.tr << ","
       << t.tf << "," << t.wr << "," << t.wf << "," << pr.flip << "," << pr.epi << "," << pr.mask
-      << "> FbcThis;\n";
+      << "," << t.chunk(pr.c) << "> FbcThis;\n";
     o << "static_assert(FbcThis::SMEM_BYTES == " << direct_smem_bytes(t, pr.fh, pr.fw, pr.c)
       << ", \"host and device disagree on the shared-memory size\");\n";
     o << "extern \"C\" __global__ void __launch_bounds__(" << t.threads() << ") " << kname
@@ -78,36 +81,45 @@ namespace {
 int ceil_div(long a, long b) { return (int)((a + b - 1) / b); }
 }  // namespace
 
-std::vector<DirectTile> direct_candidates(const DirectProblem& pr, size_t smem_limit) {
+std::vector<DirectTile> direct_candidates(const DirectProblem& pr, size_t smem_limit, int threads,
+                                          int max_block) {
     std::vector<DirectTile> out;
     const int trs[] = {2, 4, 8};
     const int tfs[] = {4, 8};
-    const int wrs[] = {1, 2, 4};
-    const int wfs[] = {1, 2, 4};
+    const int wrs[] = {1, 2, 4, 8};
+    const int wfs[] = {1, 2, 4, 8};
     const int nf4 = ((pr.nf + 3) / 4) * 4;
+    // channel chunks: the whole depth, or 16 / 8 / 4 channels per stage
+    std::vector<int> ccs = {0};
+    for (int cc : {16, 8, 4})
+        if (cc < pr.c) ccs.push_back(cc);
     for (int tr : trs)
         for (int tf : tfs)
             for (int wr : wrs)
-                for (int wf : wfs) {
-                    DirectTile t{tr, tf, wr, wf};
-                    if (t.threads() > 512) continue;
-                    if (tf > nf4) continue;                       // no all-padding channels
-                    if (t.bn() > nf4 && wf > 1) continue;
-                    if (tr * tf > 64) continue;                   // register block
-                    if (tr + pr.fh - 1 > 40) continue;            // input window registers
-                    if (t.bh() > ((pr.out_h + 1) / 2) * 2 + 8 && wr > 1) continue;
-                    if (direct_smem_bytes(t, pr.fh, pr.fw, pr.c) > smem_limit) continue;
-                    out.push_back(t);
-                }
+                for (int wf : wfs)
+                    for (int cc : ccs) {
+                        DirectTile t{tr, tf, wr, wf, cc};
+                        if (t.threads() > 512) continue;
+                        if (threads > 0 && t.threads() != threads) continue;
+                        if (tf > nf4) continue;                       // no all-padding channels
+                        if (t.bn() > nf4 && wf > 1) continue;
+                        if (tr * tf > max_block) continue;            // register block
+                        if (tr + pr.fh - 1 > 40) continue;            // input window registers
+                        if (t.bh() > ((pr.out_h + 1) / 2) * 2 + 8 && wr > 1) continue;
+                        if (direct_smem_bytes(t, pr.fh, pr.fw, pr.c) > smem_limit) continue;
+                        out.push_back(t);
+                    }
     return out;
 }
 
-DirectTile direct_heuristic(const DirectProblem& pr, size_t smem_limit, int sm_count) {
+DirectTile direct_heuristic(const DirectProblem& pr, size_t smem_limit, int sm_count, int threads,
+                            int max_block) {
     // A small analytic model: tile edge waste x wave quantisation x inner-loop
     // issue efficiency x latency hiding (resident warps).  The auto-tuner
     // replaces it with measurements.
-    auto cands = direct_candidates(pr, smem_limit);
-    DirectTile best{4, 4, 1, 1};
+    auto cands = direct_candidates(pr, smem_limit, threads, max_block);
+    DirectTile best{4, 4, 1, 1, 0};
+    if (threads == 256) best = DirectTile{4, 4, 2, 4, 4};
     double best_score = -1.0;
     const size_t smem_per_sm = 228 * 1024;
     for (const auto& t : cands) {
@@ -128,7 +140,12 @@ DirectTile direct_heuristic(const DirectProblem& pr, size_t smem_limit, int sm_c
         const double wave_eff = (double)ctas / (double)(waves * slots);
         const double loads = (t.tr + pr.fh - 1) + pr.fh * t.tf / 4.0 + 2.0;
         const double fmas = (double)t.tr * t.tf * pr.fh;
-        const double e_issue = fmas / (fmas + loads);
+        // staging: elements copied per thread per chunk vs FMAs per chunk
+        const int cc = t.chunk(pr.c);
+        const double staged = ((double)(t.bh() + pr.fh - 1) * (32 + pr.fw - 1) * cc +
+                               (double)pr.fh * pr.fw * cc * t.bn()) / t.threads();
+        const double fma_chunk = fmas * pr.fw * cc;
+        const double e_issue = fma_chunk / (fma_chunk + loads * pr.fw * cc + 6.0 * staged + 400.0);
         const int warps = std::min<long>(res, (ctas + sm_count - 1) / sm_count) * t.threads() / 32;
         const double occ = std::min(1.0, warps / 12.0);
         const double score = e_tile * wave_eff * e_issue * (0.5 + 0.5 * occ);

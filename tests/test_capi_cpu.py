@@ -137,3 +137,16 @@ def test_nvrtc_fault_injection_reports_nvrtc_error():
     env = dict(os.environ, FBCORR_FAULT="nvrtc")
     r = subprocess.run(["python", "-c", code], capture_output=True, text=True, env=env, cwd=ROOT)
     assert r.stdout.strip().splitlines()[-1] == "7", r.stderr
+
+
+def test_batch_kernel_source_compiles(lib):
+    """The single persistent kernel of a batch plan (several filter sizes and
+    depths in one switch) compiles for sm_103a."""
+    shapes = [(40, 70, 8, 16, 3, 3), (33, 45, 4, 32, 5, 5), (20, 150, 32, 64, 11, 11),
+              (17, 19, 3, 5, 2, 4)]
+    n = len(shapes)
+    ins = (ctypes.c_int64 * (3 * n))(*[v for (H, W, D, N, fh, fw) in shapes for v in (H, W, D)])
+    fls = (ctypes.c_int64 * (4 * n))(*[v for (H, W, D, N, fh, fw) in shapes for v in (N, fh, fw, D)])
+    log = ctypes.create_string_buffer(1 << 16)
+    st = lib.fbcorr_batch_rtcg_check(n, ins, fls, C.epilogue((0.0, 1.0)), log, len(log))
+    assert st == 0, C.last_error() + log.value.decode()

@@ -91,8 +91,9 @@ def test_default_variant_matches_oracle():
     assert np.abs(y - oracle.fwd(wl.x, wl.w, epilogue=(-1.0, 1.0))).max() <= TOL_F32 * scale
 
 
-@pytest.mark.parametrize("spec", ["direct:tr=8,tf=8,wr=1,wf=2", "direct:tr=2,tf=4,wr=4,wf=1",
-                                  "direct:tr=4,tf=8,wr=2,wf=4", "direct:tr=8,tf=4,wr=2,wf=1"])
+@pytest.mark.parametrize("spec", ["direct:tr=8,tf=8,wr=1,wf=2,cc=0", "direct:tr=2,tf=4,wr=4,wf=1,cc=0",
+                                  "direct:tr=4,tf=8,wr=2,wf=4,cc=4", "direct:tr=8,tf=4,wr=2,wf=1,cc=0",
+                                  "direct:tr=4,tf=4,wr=2,wf=4,cc=4", "direct:tr=2,tf=8,wr=8,wf=1,cc=0"])
 def test_every_tile_shape_matches_oracle(spec):
     torch = torch_cuda()
     wl = inputs.random_case(500, 51, 77, 8, 27, 5, 4)
@@ -173,3 +174,12 @@ def test_bad_pointer_alignment_rejected():
     st = C.load().fbcorr_forward(p.handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(w.data_ptr()),
                                  ctypes.c_void_p(y.data_ptr()), None, 0, None)
     assert st == 4
+
+
+@pytest.mark.parametrize("D,cc", [(6, 4), (12, 8), (10, 4), (3, 4)])
+def test_ragged_channel_chunks(D, cc):
+    """Depth not a multiple of the channel chunk: the last chunk is zero-padded."""
+    torch = torch_cuda()
+    wl = inputs.random_case(510 + D, 41, 70, D, 12, 3, 5)
+    y, p = _run(torch, wl.x, wl.w, spec=f"direct:tr=4,tf=4,wr=2,wf=2,cc={cc}")
+    assert normwise_rel(y, oracle.fwd(wl.x, wl.w)) <= TOL_F32
