@@ -197,7 +197,18 @@ def workload_by_name(name):
         x = inputs.uniform(rng, (384, 384, 32), -1.0, 1.0)
         w = inputs.normal(rng, (256, 5, 5, 32), var=1.0 / 800.0)
         return inputs.Workload("precision_384x384x32_256x5x5x32", x, w)
+    if name == "paper_row1":
+        return inputs.workload_paper_row1_clamp()
     raise ValueError(name)
+
+
+def l2_note(wl, out_shape):
+    inb = wl.x.nbytes + wl.w.nbytes
+    outb = int(np.prod(out_shape)) * 4
+    if inb + outb > 129e6:
+        return (f"no flush: {inb / 1e6:.0f} MB in + {outb / 1e6:.0f} MB out per step exceed the "
+                f"129 MB L2")
+    return f"working set {(inb + outb) / 1e6:.0f} MB fits in L2; back-to-back steps reuse it"
 
 
 # ----------------------------------------------------------------------------- CPU oracle leg
@@ -301,7 +312,7 @@ def run_ours(args):
         if args.quick and m != mode:
             continue
         try:
-            p = Plan(wl.x.shape, wl.w.shape, m)
+            p = Plan(wl.x.shape, wl.w.shape, m, wl.clamp)
             if not args.no_tune:
                 p.autotune()
             plans[m] = p
@@ -409,7 +420,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": mode, "data": "synthetic",
             "config": {"workload": wl.name, "input": list(wl.x.shape), "bank": list(wl.w.shape),
                        "output": list(plan.out_shape), "mode": mode, "flops_per_step": flops,
-                       "l2": "no flush: 34 MB input + 264 MB output per step exceed the 129 MB L2",
+                       "l2": l2_note(wl, plan.out_shape),
                        "parallelism": f"replicas x{world}"},
             "roofline": roof, "clocks": clk, "gpu_launches": launches_per_step * args.steps,
             "e2e": e2e, "cpu_baseline": cpu, "peaks": peaks, "detail": detail,
@@ -453,11 +464,32 @@ def secondary(torch, args, world, peaks):
         p.forward(x, w, y)
         p.backward(x, w, g)
     ms_f = time_loop(torch, lambda: p.forward(x, w, y), 30, 3, world, flush)
+    ms_dx = time_loop(torch, lambda: p.backward(x, w, g, need_dw=False), 30, 3, world, flush)
+    ms_dw = time_loop(torch, lambda: p.backward(x, w, g, need_dx=False), 30, 3, world, flush)
     ms_fb = time_loop(torch, fb, 30, 3, world, flush)
+    fp = peaks["fp32_tflops"]
     out["fwdbwd_256x256x16_64x7x7x16"] = {
-        "fwd_gflops": wl.flops / ms_f / 1e6, "fwd_bwd_gflops": 3 * wl.flops / ms_fb / 1e6,
-        "ms_fwd": ms_f, "ms_fwd_bwd": ms_fb,
-        "fwd_bwd_frac_of_fp32_peak": 3 * wl.flops / ms_fb / 1e9 / peaks["fp32_tflops"]}
+        "fwd_gflops": wl.flops / ms_f / 1e6, "dx_gflops": wl.flops / ms_dx / 1e6,
+        "dw_gflops": wl.flops / ms_dw / 1e6, "fwd_bwd_gflops": 3 * wl.flops / ms_fb / 1e6,
+        "ms_fwd": ms_f, "ms_dx": ms_dx, "ms_dw": ms_dw, "ms_fwd_bwd": ms_fb,
+        "fwd_bwd_frac_of_fp32_peak": 3 * wl.flops / ms_fb / 1e9 / fp,
+        "plan": p.info()}
+    # the 64-image uneven batch: one persistent launch replayed from a CUDA graph
+    from paper_0911_3456_gb300.api import BatchPlan
+    bw = inputs.workload_batch()
+    t0 = time.perf_counter()
+    bp = BatchPlan([it.x.shape for it in bw.items], [it.w.shape for it in bw.items])
+    t_plan = time.perf_counter() - t0
+    xs = [torch.from_numpy(it.x).cuda() for it in bw.items]
+    wss = [torch.from_numpy(it.w).cuda() for it in bw.items]
+    ys = [torch.empty(it.out_shape, device="cuda") for it in bw.items]
+    ms_b = time_loop(torch, lambda: bp.forward(xs, wss, ys), 20, 3, world, flush)
+    binfo = bp.info()
+    out["batch64_uneven"] = {
+        "gflops": bw.flops / ms_b / 1e6, "ms": ms_b, "flops": bw.flops,
+        "frac_of_fp32_peak": bw.flops / ms_b / 1e9 / fp, "launches_per_step": binfo["launches"],
+        "work_items": binfo["work_items"], "grid": binfo["grid"], "variants": len(binfo["variants"]),
+        "plan_seconds": t_plan}
     return out
 
 
@@ -473,7 +505,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--workload", choices=["precision", "precision384"], default="precision")
+    ap.add_argument("--workload", choices=["precision", "precision384", "paper_row1"],
+                    default="precision")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -187,9 +187,19 @@ fbcorr_status_t choose_fwd_f32(fbcorr_plan* p) {
 fbcorr_status_t prepare_backward(fbcorr_plan* p) {
     if (p->bwd_ready) return FBCORR_OK;
     const DirectProblem pr = dx_problem(p);
-    const DirectTile t = direct_heuristic(pr, smem_limit(p->dev), p->dev.sm_count);
+    DirectTile t = direct_heuristic(pr, smem_limit(p->dev), p->dev.sm_count);
+    std::string cached;
+    bool use_default = false;
+    if (tune_lookup(tune_key(p->dev, shape_key(p, "dx")), &cached)) {
+        DirectTile ct;
+        if (cached == "default")
+            use_default = true;
+        else if (parse_direct_spec(cached, &ct) &&
+                 direct_smem_bytes(ct, pr.fh, pr.fw, pr.c) <= smem_limit(p->dev))
+            t = ct;
+    }
     Kernel k;
-    fbcorr_status_t s = build_direct(pr, t, &k);
+    fbcorr_status_t s = use_default ? FBCORR_ERR_NVRTC : build_direct(pr, t, &k);
     if (s == FBCORR_OK) {
         p->dx_kind = VarKind::Direct;
         p->dx_tile = t;
@@ -216,11 +226,12 @@ fbcorr_status_t prepare_backward(fbcorr_plan* p) {
 }
 
 void plan_dw_chunks(fbcorr_plan* p) {
-    // enough CTAs for two waves of the partial-sum kernel, deterministic in the shape
+    // enough 128-thread CTAs to keep about 12 resident per SM (the partial-sum
+    // kernel is latency-bound), deterministic in the shape
     const long pairs = ((p->N + p->dw_tn - 1) / p->dw_tn) * p->D;
     const long zgroups = (pairs + 127) / 128;
-    long want = (2L * std::max(1, p->dev.sm_count) + p->fh * zgroups - 1) / (p->fh * zgroups);
-    want = std::max(1L, std::min<long>(want, std::min<long>(p->Ho, 128)));
+    long want = (12L * std::max(1, p->dev.sm_count) + p->fh * zgroups - 1) / (p->fh * zgroups);
+    want = std::max(1L, std::min<long>(want, std::min<long>(p->Ho, 256)));
     p->dw_rows_per_chunk = (int)((p->Ho + want - 1) / want);
     p->dw_chunks = (int)((p->Ho + p->dw_rows_per_chunk - 1) / p->dw_rows_per_chunk);
     p->ws_bwd = (size_t)p->dw_chunks * p->N * p->fh * p->fw * p->D * sizeof(float);
@@ -507,60 +518,54 @@ fbcorr_status_t fbcorr_plan_set_variant(fbcorr_plan_t p, const char* spec) {
 
 static fbcorr_status_t autotune_tc(fbcorr_plan_t p, fbcorr_stream_t stream);
 
-fbcorr_status_t fbcorr_autotune(fbcorr_plan_t p, fbcorr_stream_t stream) {
-    clear_error();
-    if (!p) return set_error(FBCORR_ERR_INVALID_ARG, "NULL plan");
-    cudaStream_t s = (cudaStream_t)stream;
-    if (p->dtype != FBCORR_F32) return autotune_tc(p, stream);
-    const DirectProblem pr = fwd_problem(p);
-    // Candidate set: the analytic model's ranking, top K plus the default kernel.
-    std::vector<DirectTile> cands = direct_candidates(pr, smem_limit(p->dev));
-    const DirectTile h = direct_heuristic(pr, smem_limit(p->dev), p->dev.sm_count);
+// Time the top candidates of one direct-correlation problem (forward or dL/dx)
+// and the prebuilt default kernel on zero-filled buffers; returns the fastest.
+static fbcorr_status_t tune_direct(fbcorr_plan_t p, const DirectProblem& pr, cudaStream_t s,
+                                   const char* what, std::string* best_spec, float* best_ms_out) {
+    std::vector<DirectTile> ranked = direct_ranked(pr, smem_limit(p->dev), p->dev.sm_count);
     int topk = atoi(env_str("FBCORR_TUNE_TOPK", "12").c_str());
     if (topk < 1) topk = 1;
-    // order: heuristic first, then by a cheap proxy (larger register blocks first)
-    std::stable_sort(cands.begin(), cands.end(), [](const DirectTile& a, const DirectTile& b) {
-        return a.tr * a.tf * 100 + a.threads() > b.tr * b.tf * 100 + b.threads();
-    });
-    std::vector<std::string> specs = {direct_tile_spec(h)};
-    for (auto& t : cands) {
-        const std::string sp = direct_tile_spec(t);
+    std::vector<std::string> specs;
+    for (auto& t : ranked) {
         if ((int)specs.size() >= topk) break;
-        if (std::find(specs.begin(), specs.end(), sp) == specs.end()) specs.push_back(sp);
+        specs.push_back(direct_tile_spec(t));
     }
     specs.push_back("default");
-
-    float *x = nullptr, *w = nullptr, *y = nullptr;
-    const size_t xb = (size_t)p->H * p->W * p->D * 4, wb = (size_t)p->N * p->fh * p->fw * p->D * 4,
-                 yb = (size_t)p->Ho * p->Wo * p->N * 4;
-    FBC_CUDA(cudaMalloc(&x, xb));
-    if (cudaMalloc(&w, wb) != cudaSuccess || cudaMalloc(&y, yb) != cudaSuccess) {
-        cudaFree(x);
-        cudaFree(w);
+    const size_t xb = (size_t)pr.in_h * pr.in_w * pr.c * 4;
+    const size_t wb = (size_t)pr.nf * pr.fh * pr.fw * pr.c * 4;
+    const size_t yb = (size_t)pr.out_h * pr.out_w * pr.nf * 4;
+    float *x = nullptr, *w = nullptr, *y = nullptr, *m = nullptr;
+    if (cudaMalloc(&x, xb) != cudaSuccess || cudaMalloc(&w, wb) != cudaSuccess ||
+        cudaMalloc(&y, yb) != cudaSuccess || (pr.mask && cudaMalloc(&m, xb) != cudaSuccess)) {
+        cudaFree(x); cudaFree(w); cudaFree(y); cudaFree(m);
+        cudaGetLastError();
         return set_error(FBCORR_ERR_OOM, "autotune buffers");
     }
     cudaMemsetAsync(x, 0, xb, s);
     cudaMemsetAsync(w, 0, wb, s);
+    if (m) cudaMemsetAsync(m, 0, xb, s);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    std::string best_spec;
     float best_ms = 1e30f;
-    std::ostringstream report;
-    const VarKind old_kind = p->fwd_kind;
-    const DirectTile old_tile = p->fwd_tile;
-    const Kernel old_kernel = p->fwd_kernel;
-    const std::string old_source = p->fwd_source;
     fbcorr_status_t status = FBCORR_OK;
     for (const auto& sp : specs) {
-        if (set_fwd_spec(p, sp, "tuning") != FBCORR_OK) continue;
+        Kernel k;
+        DirectTile t;
+        const bool dflt = sp == "default";
+        if (!dflt) {
+            if (!parse_direct_spec(sp, &t) || build_direct(pr, t, &k) != FBCORR_OK) continue;
+        }
+        auto run = [&]() {
+            return dflt ? run_default(pr, x, m, w, y, 0.f, 1.f, s)
+                        : run_direct(k, pr, t, x, m, w, y, 0.f, 1.f, s);
+        };
         std::vector<float> ms_list;
         bool ok = true;
-        for (int r = 0; r < 2 && ok; ++r)
-            ok = fbcorr_forward(p, x, w, y, nullptr, 0, stream) == FBCORR_OK;
+        for (int r = 0; r < 2 && ok; ++r) ok = run() == FBCORR_OK;
         for (int r = 0; r < 7 && ok; ++r) {
             cudaEventRecord(e0, s);
-            ok = fbcorr_forward(p, x, w, y, nullptr, 0, stream) == FBCORR_OK;
+            ok = run() == FBCORR_OK;
             cudaEventRecord(e1, s);
             if (cudaEventSynchronize(e1) != cudaSuccess) ok = false;
             float ms = 0.f;
@@ -568,33 +573,44 @@ fbcorr_status_t fbcorr_autotune(fbcorr_plan_t p, fbcorr_stream_t stream) {
             ms_list.push_back(ms);
         }
         if (!ok) {
-            status = set_error(FBCORR_ERR_CUDA, "autotune run of %s failed", sp.c_str());
+            status = set_error(FBCORR_ERR_CUDA, "autotune run of %s (%s) failed", sp.c_str(), what);
             break;
         }
         std::sort(ms_list.begin(), ms_list.end());
         const float med = ms_list[ms_list.size() / 2];
-        report << sp << "=" << med << "ms;";
-        logf("autotune %s: %.4f ms", sp.c_str(), med);
+        logf("autotune %s %s: %.4f ms", what, sp.c_str(), med);
         if (med < best_ms) {
             best_ms = med;
-            best_spec = sp;
+            *best_spec = sp;
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    cudaFree(x);
-    cudaFree(w);
-    cudaFree(y);
-    if (status != FBCORR_OK || best_spec.empty()) {
-        p->fwd_kind = old_kind;
-        p->fwd_tile = old_tile;
-        p->fwd_kernel = old_kernel;
-        p->fwd_source = old_source;
-        return status != FBCORR_OK ? status : set_error(FBCORR_ERR_INTERNAL, "no variant ran");
-    }
-    FBC_TRY(set_fwd_spec(p, best_spec, "tuned"));
-    tune_store(tune_key(p->dev, shape_key(p, "fwd")), best_spec);
-    logf("autotune picked %s (%.4f ms); %s", best_spec.c_str(), best_ms, report.str().c_str());
+    cudaFree(x); cudaFree(w); cudaFree(y); cudaFree(m);
+    if (status != FBCORR_OK) return status;
+    if (best_spec->empty()) return set_error(FBCORR_ERR_INTERNAL, "no %s variant ran", what);
+    if (best_ms_out) *best_ms_out = best_ms;
+    return FBCORR_OK;
+}
+
+fbcorr_status_t fbcorr_autotune(fbcorr_plan_t p, fbcorr_stream_t stream) {
+    clear_error();
+    if (!p) return set_error(FBCORR_ERR_INVALID_ARG, "NULL plan");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (p->dtype != FBCORR_F32) return autotune_tc(p, stream);
+    // forward
+    std::string best;
+    float ms = 0.f;
+    FBC_TRY(tune_direct(p, fwd_problem(p), s, "fwd", &best, &ms));
+    FBC_TRY(set_fwd_spec(p, best, "tuned"));
+    tune_store(tune_key(p->dev, shape_key(p, "fwd")), best);
+    logf("autotune fwd picked %s (%.4f ms)", best.c_str(), ms);
+    // dL/dx: the same generated kernel family on the flipped problem
+    std::string best_dx;
+    FBC_TRY(tune_direct(p, dx_problem(p), s, "dx", &best_dx, &ms));
+    tune_store(tune_key(p->dev, shape_key(p, "dx")), best_dx);
+    logf("autotune dx picked %s (%.4f ms)", best_dx.c_str(), ms);
+    p->bwd_ready = false;   // rebuilt from the cache entry on the next backward call
     return FBCORR_OK;
 }
 

@@ -103,6 +103,9 @@ std::vector<DirectTile> direct_candidates(const DirectProblem& pr, size_t smem_l
                                           int threads = 0, int max_block = 64);
 DirectTile direct_heuristic(const DirectProblem& pr, size_t smem_limit, int sm_count,
                             int threads = 0, int max_block = 64);
+// candidates ordered by the analytic model, best first
+std::vector<DirectTile> direct_ranked(const DirectProblem& pr, size_t smem_limit, int sm_count,
+                                      int threads = 0, int max_block = 64);
 
 struct DwTile {
     int tn = 4, threads = 128, chunks = 0;   // chunks = 0: choose from the SM count

@@ -215,7 +215,8 @@ fbcorr_status_t rtcg_kernel(const std::string& src, const std::string& name, siz
     const uint64_t h = fnv1a(keysrc);
 
     CUmodule mod = nullptr;
-    {
+    const bool nocache = fault_injected("nocache");   // testing knob: bypass both caches
+    if (!nocache) {
         std::lock_guard<std::mutex> lk(g_mu);
         auto it = g_modules.find(ModKey{ctx, h});
         if (it != g_modules.end()) mod = it->second;
@@ -226,7 +227,7 @@ fbcorr_status_t rtcg_kernel(const std::string& src, const std::string& name, siz
         const std::string dir = cache_dir();
         const std::string path = dir + "/rtcg-" + hb + ".cubin";
         std::vector<char> cubin;
-        bool cached = !fault_injected("nocache") && read_file(path, &cubin);
+        bool cached = !nocache && read_file(path, &cubin);
         if (!cached) {
             dump_source(src, name);
             FBC_TRY(compile(src, &cubin, nullptr));

@@ -112,49 +112,60 @@ std::vector<DirectTile> direct_candidates(const DirectProblem& pr, size_t smem_l
     return out;
 }
 
+// A small analytic model: tile edge waste x wave quantisation x inner-loop
+// issue efficiency (including the per-chunk staging) x latency hiding
+// (resident warps).  The auto-tuner replaces it with measurements; it also
+// orders the candidates the tuner measures first.
+static double direct_score(const DirectProblem& pr, const DirectTile& t, int sm_count) {
+    const size_t smem_per_sm = 228 * 1024;
+    const int gx = ceil_div(pr.out_w, 32), gy = ceil_div(pr.out_h, t.bh()), gz = ceil_div(pr.nf, t.bn());
+    const double useful = (double)pr.out_w * pr.out_h * pr.nf;
+    const double computed = (double)gx * 32 * gy * t.bh() * gz * t.bn();
+    const double e_tile = useful / computed;
+    const size_t smem = direct_smem_bytes(t, pr.fh, pr.fw, pr.c) + 1024;
+    const int regs = t.tr * t.tf + t.tr + pr.fh + t.tf + 28;
+    int res = (int)(smem_per_sm / smem);
+    res = std::min(res, 2048 / t.threads());
+    res = std::min(res, 65536 / (t.threads() * std::min(255, regs)));
+    if (res < 1) return -1.0;
+    const long ctas = (long)gx * gy * gz;
+    const long slots = (long)res * sm_count;
+    const long waves = (ctas + slots - 1) / slots;
+    const double wave_eff = (double)ctas / (double)(waves * slots);
+    const double loads = (t.tr + pr.fh - 1) + pr.fh * t.tf / 4.0 + 2.0;
+    const double fmas = (double)t.tr * t.tf * pr.fh;
+    const int cc = t.chunk(pr.c);
+    const double staged = ((double)(t.bh() + pr.fh - 1) * (32 + pr.fw - 1) * cc +
+                           (double)pr.fh * pr.fw * cc * t.bn()) / t.threads();
+    const double fma_chunk = fmas * pr.fw * cc;
+    const double e_issue = fma_chunk / (fma_chunk + loads * pr.fw * cc + 6.0 * staged + 400.0);
+    const int warps = std::min<long>(res, (ctas + sm_count - 1) / sm_count) * t.threads() / 32;
+    const double occ = std::min(1.0, warps / 12.0);
+    return e_tile * wave_eff * e_issue * (0.5 + 0.5 * occ);
+}
+
+std::vector<DirectTile> direct_ranked(const DirectProblem& pr, size_t smem_limit, int sm_count,
+                                      int threads, int max_block) {
+    auto cands = direct_candidates(pr, smem_limit, threads, max_block);
+    std::vector<std::pair<double, DirectTile>> scored;
+    for (const auto& t : cands) {
+        const double sc = direct_score(pr, t, sm_count);
+        if (sc > 0) scored.push_back({sc, t});
+    }
+    std::stable_sort(scored.begin(), scored.end(),
+                     [](const std::pair<double, DirectTile>& a, const std::pair<double, DirectTile>& b) {
+                         return a.first > b.first;
+                     });
+    std::vector<DirectTile> out;
+    for (auto& st : scored) out.push_back(st.second);
+    return out;
+}
+
 DirectTile direct_heuristic(const DirectProblem& pr, size_t smem_limit, int sm_count, int threads,
                             int max_block) {
-    // A small analytic model: tile edge waste x wave quantisation x inner-loop
-    // issue efficiency x latency hiding (resident warps).  The auto-tuner
-    // replaces it with measurements.
-    auto cands = direct_candidates(pr, smem_limit, threads, max_block);
-    DirectTile best{4, 4, 1, 1, 0};
-    if (threads == 256) best = DirectTile{4, 4, 2, 4, 4};
-    double best_score = -1.0;
-    const size_t smem_per_sm = 228 * 1024;
-    for (const auto& t : cands) {
-        const int gx = ceil_div(pr.out_w, 32), gy = ceil_div(pr.out_h, t.bh()),
-                  gz = ceil_div(pr.nf, t.bn());
-        const double useful = (double)pr.out_w * pr.out_h * pr.nf;
-        const double computed = (double)gx * 32 * gy * t.bh() * gz * t.bn();
-        const double e_tile = useful / computed;
-        const size_t smem = direct_smem_bytes(t, pr.fh, pr.fw, pr.c) + 1024;
-        const int regs = t.tr * t.tf + t.tr + pr.fh + t.tf + 28;
-        int res = (int)(smem_per_sm / smem);
-        res = std::min(res, 2048 / t.threads());
-        res = std::min(res, 65536 / (t.threads() * std::min(255, regs)));
-        if (res < 1) continue;
-        const long ctas = (long)gx * gy * gz;
-        const long slots = (long)res * sm_count;
-        const long waves = (ctas + slots - 1) / slots;
-        const double wave_eff = (double)ctas / (double)(waves * slots);
-        const double loads = (t.tr + pr.fh - 1) + pr.fh * t.tf / 4.0 + 2.0;
-        const double fmas = (double)t.tr * t.tf * pr.fh;
-        // staging: elements copied per thread per chunk vs FMAs per chunk
-        const int cc = t.chunk(pr.c);
-        const double staged = ((double)(t.bh() + pr.fh - 1) * (32 + pr.fw - 1) * cc +
-                               (double)pr.fh * pr.fw * cc * t.bn()) / t.threads();
-        const double fma_chunk = fmas * pr.fw * cc;
-        const double e_issue = fma_chunk / (fma_chunk + loads * pr.fw * cc + 6.0 * staged + 400.0);
-        const int warps = std::min<long>(res, (ctas + sm_count - 1) / sm_count) * t.threads() / 32;
-        const double occ = std::min(1.0, warps / 12.0);
-        const double score = e_tile * wave_eff * e_issue * (0.5 + 0.5 * occ);
-        if (score > best_score) {
-            best_score = score;
-            best = t;
-        }
-    }
-    return best;
+    auto r = direct_ranked(pr, smem_limit, sm_count, threads, max_block);
+    if (!r.empty()) return r.front();
+    return threads == 256 ? DirectTile{4, 4, 2, 4, 4} : DirectTile{4, 4, 1, 1, 4};
 }
 
 }  // namespace fbc
