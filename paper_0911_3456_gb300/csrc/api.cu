@@ -210,27 +210,37 @@ fbcorr_status_t prepare_backward(fbcorr_plan* p) {
         return s;
     }
     const int mask = p->epi.kind == FBCORR_EPI_CLAMP ? 1 : 0;
-    char name[128];
-    snprintf(name, sizeof name, "fbc_dw_f%dx%d_c%d_n%d_m%d", (int)p->fh, (int)p->fw, (int)p->D,
-             p->dw_tn, mask);
-    s = rtcg_kernel(dw_kernel_source((int)p->fh, (int)p->fw, (int)p->D, p->dw_tn, mask, name), name,
-                    0, 128, &p->dw_kernel);
-    if (s == FBCORR_OK)
-        p->dw_kind = VarKind::Direct;
-    else if (s == FBCORR_ERR_NVRTC)
-        p->dw_kind = VarKind::Default;
-    else
-        return s;
+    if (p->D > 256) {
+        p->dw_kind = VarKind::Default;   // one thread per channel does not fit a CTA
+    } else {
+        char name[160];
+        snprintf(name, sizeof name, "fbc_dw_f%dx%d_c%d_n%d_g%d_q%d_m%d", (int)p->fh, (int)p->fw,
+                 (int)p->D, p->dw_tn, p->dw_ng, p->dw_qb, mask);
+        s = rtcg_kernel(dw_kernel_source((int)p->fh, (int)p->fw, (int)p->D, p->dw_tn, p->dw_ng,
+                                         p->dw_qb, mask, name),
+                        name, dw_smem_bytes((int)p->fw, (int)p->D, p->dw_tn, p->dw_ng, p->dw_qb),
+                        (int)p->D * p->dw_ng, &p->dw_kernel);
+        if (s == FBCORR_OK)
+            p->dw_kind = VarKind::Direct;
+        else if (s == FBCORR_ERR_NVRTC)
+            p->dw_kind = VarKind::Default;
+        else
+            return s;
+    }
     p->bwd_ready = true;
     return FBCORR_OK;
 }
 
 void plan_dw_chunks(fbcorr_plan* p) {
-    // enough 128-thread CTAs to keep about 12 resident per SM (the partial-sum
-    // kernel is latency-bound), deterministic in the shape
-    const long pairs = ((p->N + p->dw_tn - 1) / p->dw_tn) * p->D;
-    const long zgroups = (pairs + 127) / 128;
-    long want = (12L * std::max(1, p->dev.sm_count) + p->fh * zgroups - 1) / (p->fh * zgroups);
+    // CTA = NG filter groups x D channels (about 256 threads); enough row chunks
+    // for about 4 resident CTAs per SM over two waves; deterministic in the shape
+    p->dw_tn = 4;
+    const long ngroups_needed = (p->N + p->dw_tn - 1) / p->dw_tn;
+    p->dw_ng = (int)std::max(1L, std::min<long>(256 / std::max<int64_t>(1, p->D), ngroups_needed));
+    p->dw_qb = 64;
+    p->dw_nblocks = (int)((p->N + (long)p->dw_tn * p->dw_ng - 1) / ((long)p->dw_tn * p->dw_ng));
+    long want = (4L * std::max(1, p->dev.sm_count) + p->fh * p->dw_nblocks - 1) /
+                (p->fh * p->dw_nblocks);
     want = std::max(1L, std::min<long>(want, std::min<long>(p->Ho, 256)));
     p->dw_rows_per_chunk = (int)((p->Ho + want - 1) / want);
     p->dw_chunks = (int)((p->Ho + p->dw_rows_per_chunk - 1) / p->dw_rows_per_chunk);
@@ -480,8 +490,7 @@ fbcorr_status_t fbcorr_backward(fbcorr_plan_t p, const float* x, const float* w,
             DwArgsK a{x, g, m ? m : g, part, (int)p->H, (int)p->W, (int)p->Ho, (int)p->Wo, (int)p->N,
                       p->dw_rows_per_chunk, p->epi.lo, p->epi.hi};
             void* args[] = {&a};
-            const long pairs = ((p->N + p->dw_tn - 1) / p->dw_tn) * p->D;
-            dim3 grid((unsigned)p->dw_chunks, (unsigned)p->fh, (unsigned)((pairs + 127) / 128));
+            dim3 grid((unsigned)p->dw_chunks, (unsigned)p->fh, (unsigned)p->dw_nblocks);
             FBC_TRY(launch(p->dw_kernel, grid, args, s));
         } else {
             FBC_CUDA(launch_default_dw(x, g, m ? m : g, part, (int)p->H, (int)p->W, (int)p->D,
@@ -698,7 +707,8 @@ fbcorr_status_t fbcorr_plan_info(fbcorr_plan_t p, char* buf, size_t cap) {
     if (p->bwd_ready) {
         o << ",\"dx\":{\"kind\":\"" << kind_name(p->dx_kind) << "\"";
         if (p->dx_kind == VarKind::Direct) o << ",\"spec\":\"" << direct_tile_spec(p->dx_tile) << "\"";
-        o << "},\"dw\":{\"kind\":\"" << kind_name(p->dw_kind) << "\",\"chunks\":" << p->dw_chunks
+        o << "},\"dw\":{\"kind\":\"" << kind_name(p->dw_kind) << "\",\"threads\":" << p->D * p->dw_ng
+          << ",\"filters_per_cta\":" << p->dw_tn * p->dw_ng << ",\"chunks\":" << p->dw_chunks
           << ",\"rows_per_chunk\":" << p->dw_rows_per_chunk << "}";
     }
     o << ",\"ws_fwd\":" << p->ws_fwd << ",\"ws_bwd\":" << p->ws_bwd << ",\"sm_count\":"
@@ -767,7 +777,9 @@ fbcorr_status_t fbcorr_rtcg_check(const int64_t in_shape[3], const int64_t filt_
     const std::string srcs[3] = {
         direct_kernel_source(fp, t, kname_for("fbc_direct", fp, t)),
         direct_kernel_source(bp, tb, kname_for("fbc_direct", bp, tb)),
-        dw_kernel_source((int)tmp.fh, (int)tmp.fw, (int)tmp.D, 4, mask, "fbc_dw_check")};
+        dw_kernel_source((int)tmp.fh, (int)tmp.fw, (int)tmp.D, 4,
+                         (int)std::max<int64_t>(1, std::min<int64_t>(256 / tmp.D, (tmp.N + 3) / 4)), 64,
+                         mask, "fbc_dw_check")};
     for (const auto& src : srcs) {
         std::string lg;
         fbcorr_status_t s = rtcg_compile_only(src, &lg);

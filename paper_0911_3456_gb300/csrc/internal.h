@@ -107,10 +107,11 @@ DirectTile direct_heuristic(const DirectProblem& pr, size_t smem_limit, int sm_c
 std::vector<DirectTile> direct_ranked(const DirectProblem& pr, size_t smem_limit, int sm_count,
                                       int threads = 0, int max_block = 64);
 
-struct DwTile {
-    int tn = 4, threads = 128, chunks = 0;   // chunks = 0: choose from the SM count
-};
-std::string dw_kernel_source(int fh, int fw, int c, int tn, int mask, const std::string& kname);
+// dL/dw partial-sum kernel: TN filters x fw taps per thread, NG filter groups of
+// C threads per CTA, rows walked in blocks of QB columns staged in shared memory.
+size_t dw_smem_bytes(int fw, int c, int tn, int ng, int qb);
+std::string dw_kernel_source(int fh, int fw, int c, int tn, int ng, int qb, int mask,
+                             const std::string& kname);
 
 // prebuilt (nvcc) kernels, launchers defined in default_kernels.cu
 struct DirectArgsRT {
@@ -175,7 +176,8 @@ struct fbcorr_plan {
     fbc::Kernel dx_kernel;
     fbc::VarKind dw_kind = fbc::VarKind::Direct;
     fbc::Kernel dw_kernel;
-    int dw_tn = 4, dw_chunks = 1, dw_rows_per_chunk = 1;
+    int dw_tn = 4, dw_ng = 1, dw_qb = 64, dw_nblocks = 1;
+    int dw_chunks = 1, dw_rows_per_chunk = 1;
 
     size_t ws_fwd = 0, ws_bwd = 0;
 

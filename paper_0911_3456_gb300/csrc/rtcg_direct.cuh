@@ -235,11 +235,17 @@ struct FbcDirect {
 };
 
 // ---- dL/dw partial sums -----------------------------------------------------
-// Grid: x = chunk of output rows, y = filter row i, z = group of NT (n-group, c)
-// pairs.  Thread (ng, c) accumulates dw[ng*TN .. +TN][i][0..FW)[c] over its
-// chunk, one output row at a time into a row partial that is then added to the
-// chunk total (two-level summation).  Along q the FW input values x[p+i][q+j][c]
-// live in a register window rotated by a compile-time index (unroll by FW).
+// Grid: x = chunk of output rows, y = filter row i, z = block of NBLK = TN*NG
+// filters.  Thread (ng, c) = (tid / C, tid % C) accumulates
+// dw[n0 + ng*TN .. +TN][i][0..FW)[c] over its chunk.  For each output row p the
+// CTA walks the row in blocks of QB columns: it stages g~[p][q0..q0+QB)[n-block]
+// and the input row segment x[p+i][q0..q0+QB+FW-1)[0..C) in shared memory with
+// coalesced loads (zero beyond the row end), then every thread slides an FW-wide
+// register window x[p+i][q+j][c] along q (one shared load per column, rotated
+// by a compile-time index) and adds TN x FW outer-product terms.  Sums run one
+// output row at a time into a row partial that is then added to the chunk total
+// (two-level summation); the chunk totals go to part[chunk] for a fixed-order
+// pairwise reduction by a second kernel.
 struct FbcDwArgs {
     const float* __restrict__ x;   // [H][W][C]
     const float* __restrict__ g;   // [Ho][Wo][N]
@@ -250,13 +256,22 @@ struct FbcDwArgs {
     float lo, hi;
 };
 
-template <int FH, int FW, int C, int TN, int MASK>
+template <int FH, int FW, int C, int TN, int NG, int QB, int MASK>
 struct FbcDw {
-    static __device__ __forceinline__ void run(const FbcDwArgs& a, int chunk, int i, int pair) {
-        const int ngroups = (a.N + TN - 1) / TN;
-        if (pair >= ngroups * C) return;
-        const int c = pair % C;
-        const int n0 = (pair / C) * TN;
+    static constexpr int NT = C * NG;
+    static constexpr int NBLK = TN * NG;
+    static constexpr int GS = QB * NBLK;
+    static constexpr int XS = (QB + FW - 1) * C;
+    static constexpr int SMEM_BYTES = (GS + XS) * 4;
+
+    static __device__ __forceinline__ void run(const FbcDwArgs& a, float* smem, int chunk, int i,
+                                               int nblk) {
+        const int tid = threadIdx.x;
+        const int ng = tid / C;
+        const int c = tid - ng * C;
+        const int n0 = nblk * NBLK;
+        float* gs = smem;
+        float* xs = smem + GS;
         const int pb = chunk * a.rows_per_chunk;
         int pe = pb + a.rows_per_chunk;
         if (pe > a.Ho) pe = a.Ho;
@@ -267,57 +282,63 @@ struct FbcDw {
 #pragma unroll
             for (int k = 0; k < FW; ++k) tot[t][k] = 0.f;
 
-        const bool vec = (TN == 4) && ((a.N & 3) == 0) && (n0 + 4 <= a.N);
         for (int p = pb; p < pe; ++p) {
             float ra[TN][FW];
 #pragma unroll
             for (int t = 0; t < TN; ++t)
 #pragma unroll
                 for (int k = 0; k < FW; ++k) ra[t][k] = 0.f;
-            const float* xr = a.x + ((long long)(p + i) * a.W) * C + c;
-            const float* gr = a.g + ((long long)p * a.Wo) * a.N + n0;
-            const float* mr = a.m + ((long long)p * a.Wo) * a.N + n0;
-            float win[FW];
+            const long long grow = (long long)p * a.Wo;
+            const long long xrow = (long long)(p + i) * a.W;
+            for (int q0 = 0; q0 < a.Wo; q0 += QB) {
+                const int nq = min(QB, a.Wo - q0);
+                for (int e = tid; e < GS; e += NT) {
+                    const int qq = e / NBLK;
+                    const int nl = e - qq * NBLK;
+                    const int n = n0 + nl;
+                    float v = 0.f;
+                    if (qq < nq && n < a.N) {
+                        const long long off = (grow + q0 + qq) * a.N + n;
+                        v = __ldg(a.g + off);
+                        if (MASK) {
+                            const float mv = __ldg(a.m + off);
+                            v = (mv > a.lo && mv < a.hi) ? v : 0.f;
+                        }
+                    }
+                    gs[e] = v;
+                }
+                for (int e = tid; e < XS; e += NT) {
+                    const int k = e / C;
+                    const int cc = e - k * C;
+                    const int col = q0 + k;
+                    xs[e] = (k < nq + FW - 1 && col < a.W) ? __ldg(a.x + (xrow + col) * C + cc) : 0.f;
+                }
+                __syncthreads();
+                if (ng * TN < NBLK) {
+                    float win[FW];
 #pragma unroll
-            for (int k = 0; k < FW - 1; ++k) win[k] = __ldg(xr + k * C);
-            for (int q = 0; q < a.Wo; q += FW) {
+                    for (int k = 0; k < FW - 1; ++k) win[k] = xs[k * C + c];
+                    const float* gp = gs + ng * TN;
+#pragma unroll 1
+                    for (int qb = 0; qb < QB; qb += FW) {
 #pragma unroll
-                for (int s = 0; s < FW; ++s) {
-                    const int qq = q + s;
-                    if (qq < a.Wo) {
-                        win[(s + FW - 1) % FW] = __ldg(xr + (long long)(qq + FW - 1) * C);
-                        float gv[TN];
-                        if (vec) {
-                            const float4 t4 = __ldg(reinterpret_cast<const float4*>(gr + (long long)qq * a.N));
-                            gv[0] = t4.x; gv[1 % TN] = t4.y; gv[2 % TN] = t4.z; gv[3 % TN] = t4.w;
-                            if (MASK) {
-                                const float4 m4 = __ldg(reinterpret_cast<const float4*>(mr + (long long)qq * a.N));
-                                gv[0] = (m4.x > a.lo && m4.x < a.hi) ? gv[0] : 0.f;
-                                gv[1 % TN] = (m4.y > a.lo && m4.y < a.hi) ? gv[1 % TN] : 0.f;
-                                gv[2 % TN] = (m4.z > a.lo && m4.z < a.hi) ? gv[2 % TN] : 0.f;
-                                gv[3 % TN] = (m4.w > a.lo && m4.w < a.hi) ? gv[3 % TN] : 0.f;
-                            }
-                        } else {
+                        for (int s = 0; s < FW; ++s) {
+                            const int qq = qb + s;
+                            if (qq < QB) {
+                                win[(s + FW - 1) % FW] = xs[(qq + FW - 1) * C + c];
+                                float gv[TN];
 #pragma unroll
-                            for (int t = 0; t < TN; ++t) {
-                                float v = 0.f;
-                                if (n0 + t < a.N) {
-                                    v = __ldg(gr + (long long)qq * a.N + t);
-                                    if (MASK) {
-                                        const float mv = __ldg(mr + (long long)qq * a.N + t);
-                                        v = (mv > a.lo && mv < a.hi) ? v : 0.f;
-                                    }
-                                }
-                                gv[t] = v;
+                                for (int t = 0; t < TN; ++t) gv[t] = gp[qq * NBLK + t];
+#pragma unroll
+                                for (int t = 0; t < TN; ++t)
+#pragma unroll
+                                    for (int k = 0; k < FW; ++k)
+                                        ra[t][k] = fmaf(gv[t], win[(s + k) % FW], ra[t][k]);
                             }
                         }
-#pragma unroll
-                        for (int t = 0; t < TN; ++t)
-#pragma unroll
-                            for (int k = 0; k < FW; ++k)
-                                ra[t][k] = fmaf(gv[t], win[(s + k) % FW], ra[t][k]);
                     }
                 }
+                __syncthreads();
             }
 #pragma unroll
             for (int t = 0; t < TN; ++t)
@@ -327,10 +348,11 @@ struct FbcDw {
         // part[chunk][n][i][j][c]
 #pragma unroll
         for (int t = 0; t < TN; ++t) {
-            if (n0 + t >= a.N) continue;
+            const int n = n0 + ng * TN + t;
+            if (n >= a.N) continue;
 #pragma unroll
             for (int k = 0; k < FW; ++k)
-                a.part[((((long long)chunk * a.N + n0 + t) * FH + i) * FW + k) * C + c] = tot[t][k];
+                a.part[((((long long)chunk * a.N + n) * FH + i) * FW + k) * C + c] = tot[t][k];
         }
     }
 };

@@ -470,24 +470,29 @@ __device__ __forceinline__ void split8(const float (&v)[8], uint4* hi_out, uint4
 
 __global__ void __launch_bounds__(256) fbc_tc_split(const __grid_constant__ SplitParams S) {
     if ((long long)blockIdx.x < S.xblocks) {
-        const long long idx = (long long)blockIdx.x * 256 + threadIdx.x;   // (c, pix), pix fastest
-        if (idx >= (long long)S.nc * S.npix_pad) return;
-        const int c = (int)(idx / S.npix_pad);
-        const long long pix = idx - (long long)c * S.npix_pad;
-        float v[8];
-        if (pix < S.npix && (S.D & 7) == 0 && c * 8 + 8 <= S.D) {
-            const float4* src = reinterpret_cast<const float4*>(S.x + pix * S.D + c * 8);
-            const float4 a = __ldg(src), b = __ldg(src + 1);
-            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-            v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
-        } else {
+        // one thread per pixel: contiguous reads of its D channels, and for
+        // every chunk plane a 16-byte store that is contiguous across the warp
+        const long long pix = (long long)blockIdx.x * 256 + threadIdx.x;
+        if (pix >= S.npix_pad) return;
+        const bool inside = pix < S.npix;
+        const float* src = S.x + pix * S.D;
+        for (int c = 0; c < S.nc; ++c) {
+            float v[8];
+            if (inside && (S.D & 7) == 0 && c * 8 + 8 <= S.D) {
+                const float4* s4 = reinterpret_cast<const float4*>(src + c * 8);
+                const float4 a = __ldg(s4), b = __ldg(s4 + 1);
+                v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+                v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+            } else {
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const int d = c * 8 + k;
-                v[k] = (pix < S.npix && d < S.D) ? __ldg(S.x + pix * S.D + d) : 0.f;
+                for (int k = 0; k < 8; ++k) {
+                    const int d = c * 8 + k;
+                    v[k] = (inside && d < S.D) ? __ldg(src + d) : 0.f;
+                }
             }
+            const long long idx = (long long)c * S.npix_pad + pix;
+            split8(v, reinterpret_cast<uint4*>(S.xhi) + idx, reinterpret_cast<uint4*>(S.xlo) + idx, S.split);
         }
-        split8(v, reinterpret_cast<uint4*>(S.xhi) + idx, reinterpret_cast<uint4*>(S.xlo) + idx, S.split);
     } else {
         const long long idx = ((long long)blockIdx.x - S.xblocks) * 256 + threadIdx.x;
         const int taps = S.fh * S.fw;
@@ -611,7 +616,7 @@ bool tc_layout(TcPlan* p, const TcConfig& c, bool commit) {
     sp.npix_pad = k.npix_pad;
     sp.D = p->D; sp.nc = nc; sp.N = p->N; sp.fh = p->fh; sp.fw = p->fw; sp.nt = nt; sp.ntn = ntn;
     sp.split = p->split;
-    sp.xblocks = ((long long)nc * k.npix_pad + 255) / 256;
+    sp.xblocks = (k.npix_pad + 255) / 256;
     const long long wblocks = ((long long)ntn * p->fh * p->fw * nc * nt + 255) / 256;
     p->split_blocks = (int)(sp.xblocks + wblocks);
     p->grid = std::min(mtiles * ntn, std::max(1, p->sm_count));

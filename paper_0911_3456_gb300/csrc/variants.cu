@@ -67,12 +67,22 @@ std::string direct_kernel_source(const DirectProblem& pr, const DirectTile& t,
     return o.str();
 }
 
-std::string dw_kernel_source(int fh, int fw, int c, int tn, int mask, const std::string& kname) {
+size_t dw_smem_bytes(int fw, int c, int tn, int ng, int qb) {
+    return (size_t)(qb * tn * ng + (qb + fw - 1) * c) * 4;
+}
+
+std::string dw_kernel_source(int fh, int fw, int c, int tn, int ng, int qb, int mask,
+                             const std::string& kname) {
     std::ostringstream o;
     o << rtcg_header_source() << "\n";
-    o << "extern \"C\" __global__ void __launch_bounds__(128) " << kname << "(FbcDwArgs a) {\n"
-      << "  FbcDw<" << fh << "," << fw << "," << c << "," << tn << "," << mask
-      << ">::run(a, blockIdx.x, blockIdx.y, blockIdx.z * blockDim.x + threadIdx.x);\n"
+    o << "typedef FbcDw<" << fh << "," << fw << "," << c << "," << tn << "," << ng << "," << qb << ","
+      << mask << "> FbcDwThis;\n";
+    o << "static_assert(FbcDwThis::SMEM_BYTES == " << dw_smem_bytes(fw, c, tn, ng, qb)
+      << ", \"host and device disagree on the shared-memory size\");\n";
+    o << "extern \"C\" __global__ void __launch_bounds__(" << c * ng << ") " << kname
+      << "(FbcDwArgs a) {\n"
+      << "  extern __shared__ __align__(16) float fbc_smem[];\n"
+      << "  FbcDwThis::run(a, fbc_smem, blockIdx.x, blockIdx.y, blockIdx.z);\n"
       << "}\n";
     return o.str();
 }
