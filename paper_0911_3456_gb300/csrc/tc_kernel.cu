@@ -10,13 +10,14 @@
 // serves all fw taps of that row: tap j is the same slab started j rows later.
 //
 // Data path per CTA (persistent, one per SM, 192 threads):
-//   warp 0     : producer -- cp.async.bulk (1D TMA) of A slabs and per-tap B
-//                slices into multi-stage rings, mbarrier complete_tx;
+//   warp 0     : producer -- cp.async.bulk (1D TMA) of A slabs and B slices of
+//                `bt` consecutive taps into multi-stage rings, mbarrier complete_tx;
 //   warp 1     : allocates 512 TMEM columns and issues tcgen05.mma
 //                (M=128, N<=256, K=16, kind::f16 BF16 inputs, FP32 accumulate)
 //                into one of two accumulators; tcgen05.commit frees ring
 //                slots and hands finished accumulators to the epilogue;
-//   warps 2..5 : epilogue -- tcgen05.ld 32x32b, optional clamp, transpose
+//   warps 2..5 : epilogue, one warp per TMEM lane quarter -- tcgen05.ld 32x32b,
+//                optional clamp, transpose
 //                through shared memory, coalesced float4 streaming stores;
 //                overlaps the MMAs of the next tile (double-buffered TMEM).
 // Operands use the no-swizzle K-major canonical layout: a core matrix is 8
@@ -45,12 +46,13 @@ namespace fbc {
 
 namespace {
 
-constexpr int kThreads = 192;
+constexpr int kEpiWarps = 4;      // one epilogue warp per TMEM lane quarter (4 or 8)
+constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr int kTileM = 128;
 constexpr int kAccCols = 256;     // TMEM columns reserved per accumulator
 constexpr int kTmemCols = 512;
 constexpr int kStgPitch = 36;     // floats per staged row (16-byte aligned, conflict-free)
-constexpr int kStgBytes = 4 * 32 * kStgPitch * 4;
+constexpr int kStgBytes = kEpiWarps * 32 * kStgPitch * 4;
 constexpr size_t kSmemMax = 227 * 1024 - 1024;   // leave room for static shared memory
 
 enum : int { kErrWaitA = 1, kErrWaitB = 2, kErrWaitAcc = 3, kErrWaitEmpty = 4 };
@@ -69,8 +71,9 @@ struct TcParams {
     int lp;               // pixels per chunk plane of an A slot
     int split;
     int na, nb;
+    int bt;               // filter taps per B stage (one wait + one commit per stage)
     uint32_t a_slot, b_stage;   // bytes per A slot / B stage (hi [+ lo])
-    uint32_t a_tx, b_tx;        // bytes actually copied per A slot / B stage
+    uint32_t a_tx, b_tx;        // bytes copied per A slot / per filter tap of a B stage
     uint32_t a_off, b_off, stg_off, bar_off;
     int epi;
     float lo, hi;
@@ -194,12 +197,38 @@ __device__ __noinline__ void wait_drain(uint32_t bar, uint32_t parity, const TcP
         if (globaltimer() - t0 > P.wait_ns) return;
 }
 
+// All MMAs of one filter tap: K = 16 per instruction over the NC/2 pairs of
+// chunk planes; split mode adds hi*lo and lo*hi before hi*hi.
+template <int NC, int SPLIT>
+__device__ __forceinline__ void issue_tap(uint32_t d_tmem, uint64_t ad, uint64_t bd, uint64_t ak,
+                                          uint64_t bk, uint64_t alo, uint64_t blo, uint32_t idesc,
+                                          uint32_t& accumulate) {
+#pragma unroll
+    for (int kk = 0; kk < NC / 2; ++kk) {
+        const uint64_t a = ad + kk * ak;
+        const uint64_t b = bd + kk * bk;
+        if (SPLIT) {
+            // small terms first, then hi*hi
+            umma_bf16(d_tmem, a, b + blo, idesc, accumulate);
+            umma_bf16(d_tmem, a + alo, b, idesc, 1);
+            umma_bf16(d_tmem, a, b, idesc, 1);
+        } else {
+            umma_bf16(d_tmem, a, b, idesc, accumulate);
+        }
+        accumulate = 1;
+    }
+}
+
 // ---------------------------------------------------------------- the kernel
 // NC = 16-byte chunk planes per pixel (D rounded up to 16, / 8); SPLIT = 3-product mode.
 // Both are compile-time so that the single MMA-issuing thread runs a short,
 // fully unrolled instruction chain per tap: ring indices advance incrementally
 // and descriptors are advanced by adding to their start-address field.
-template <int NC, int SPLIT>
+// LF selects the shape of the issuing loop: 0 = one iteration per tap with the
+// stage wait / release as branches, 1 = one iteration per B stage with an inner
+// tap loop.  Both issue the same MMAs; which schedules better depends on the
+// taps per stage, so the auto-tuner measures both.
+template <int NC, int SPLIT, int LF>
 __global__ void __launch_bounds__(kThreads, 1) fbc_tc_corr(const __grid_constant__ TcParams P) {
     extern __shared__ __align__(1024) uint8_t smem[];
     __shared__ int s_abort;
@@ -227,7 +256,7 @@ __global__ void __launch_bounds__(kThreads, 1) fbc_tc_corr(const __grid_constant
         }
         for (int s = 0; s < 2; ++s) {
             mbar_init(acc_full0 + 8u * s, 1);
-            mbar_init(acc_empty0 + 8u * s, 4);
+            mbar_init(acc_empty0 + 8u * s, kEpiWarps);
         }
         mbar_init(drain_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -282,17 +311,21 @@ __global__ void __launch_bounds__(kThreads, 1) fbc_tc_corr(const __grid_constant
                     xrow_lo += (long long)P.W * 16;
                     ++a_it;
                     if (++as == P.na) { as = 0; aph ^= 1; }
-                    for (int j = 0; j < P.fw; ++j) {
+                    for (int j0 = 0; j0 < P.fw; j0 += P.bt) {
+                        // taps j0 .. j0+tcnt-1 of this filter row are contiguous in the
+                        // operand layout: one copy per half for the whole stage
+                        const int tcnt = min(P.bt, P.fw - j0);
                         if (!(ok = wait_bar(b_empty0 + 8u * bs, bph ^ 1, P, abort_flag, kErrWaitEmpty))) break;
                         const uint32_t bfull = b_full0 + 8u * bs;
-                        mbar_expect_tx(bfull, P.b_tx);
+                        const uint32_t bytes = (uint32_t)tcnt * b_half;
+                        mbar_expect_tx(bfull, SPLIT ? 2u * bytes : bytes);
                         if ((int)b_it != P.drop_b) {
                             const uint32_t bdst = sbase + P.b_off + bs * P.b_stage;
-                            bulk_g2s(bdst, wtap_hi, b_half, bfull);
-                            if (SPLIT) bulk_g2s(bdst + b_half, wtap_lo, b_half, bfull);
+                            bulk_g2s(bdst, wtap_hi, bytes, bfull);
+                            if (SPLIT) bulk_g2s(bdst + (uint32_t)P.bt * b_half, wtap_lo, bytes, bfull);
                         }
-                        wtap_hi += tap_bytes;
-                        wtap_lo += tap_bytes;
+                        wtap_hi += tcnt * tap_bytes;
+                        wtap_lo += tcnt * tap_bytes;
                         ++b_it;
                         if (++bs == P.nb) { bs = 0; bph ^= 1; }
                     }
@@ -320,7 +353,8 @@ __global__ void __launch_bounds__(kThreads, 1) fbc_tc_corr(const __grid_constant
             const uint64_t bdesc0 = smem_desc(sbase + P.b_off, bplane, 128);
             const uint64_t a_step = P.a_slot >> 4, b_step = P.b_stage >> 4;
             const uint64_t ak = (2 * plane) >> 4, bk = (2 * bplane) >> 4;
-            const uint64_t alo = a_half >> 4, blo = b_half >> 4;
+            const uint64_t alo = a_half >> 4, blo = ((uint64_t)P.bt * b_half) >> 4;
+            const uint64_t btap = b_half >> 4;   // next tap inside a stage
             int as = 0, bs = 0;
             uint32_t aph = 0, bph = 0, acc_it = 0;
             uint64_t adesc = adesc0, bdesc = bdesc0;
@@ -335,26 +369,34 @@ __global__ void __launch_bounds__(kThreads, 1) fbc_tc_corr(const __grid_constant
                 uint32_t accumulate = 0;
                 for (int i = 0; i < P.fh && ok; ++i) {
                     if (!(ok = wait_bar(a_full0 + 8u * as, aph, P, abort_flag, kErrWaitA))) break;
-                    for (int j = 0; j < P.fw; ++j) {
-                        if (!(ok = wait_bar(b_full0 + 8u * bs, bph, P, abort_flag, kErrWaitB))) break;
-                        const uint64_t ad = adesc + (uint64_t)j;   // tap j: slab shifted by j rows
-#pragma unroll
-                        for (int kk = 0; kk < NC / 2; ++kk) {
-                            const uint64_t a = ad + kk * ak;
-                            const uint64_t b = bdesc + kk * bk;
-                            if (SPLIT) {
-                                // small terms first, then hi*hi
-                                umma_bf16(d_tmem, a, b + blo, idesc, accumulate);
-                                umma_bf16(d_tmem, a + alo, b, idesc, 1);
-                                umma_bf16(d_tmem, a, b, idesc, 1);
-                            } else {
-                                umma_bf16(d_tmem, a, b, idesc, accumulate);
+                    if (LF == 0) {
+                        // one iteration per tap; a B stage holds bt consecutive taps:
+                        // wait for it at its first tap, release it after its last
+                        int t = 0;
+                        for (int j = 0; j < P.fw; ++j) {
+                            if (t == 0 && !(ok = wait_bar(b_full0 + 8u * bs, bph, P, abort_flag, kErrWaitB)))
+                                break;
+                            issue_tap<NC, SPLIT>(d_tmem, adesc + (uint64_t)j, bdesc + (uint64_t)t * btap, ak, bk,
+                                                 alo, blo, idesc, accumulate);
+                            issued = true;
+                            if (++t == P.bt || j == P.fw - 1) {
+                                umma_commit(b_empty0 + 8u * bs);
+                                if (++bs == P.nb) { bs = 0; bph ^= 1; bdesc = bdesc0; } else { bdesc += b_step; }
+                                t = 0;
                             }
-                            accumulate = 1;
                         }
-                        issued = true;
-                        umma_commit(b_empty0 + 8u * bs);
-                        if (++bs == P.nb) { bs = 0; bph ^= 1; bdesc = bdesc0; } else { bdesc += b_step; }
+                    } else {
+                        // one iteration per B stage, inner loop over its taps
+                        for (int j0 = 0; j0 < P.fw; j0 += P.bt) {
+                            const int tcnt = min(P.bt, P.fw - j0);
+                            if (!(ok = wait_bar(b_full0 + 8u * bs, bph, P, abort_flag, kErrWaitB))) break;
+                            for (int t = 0; t < tcnt; ++t)
+                                issue_tap<NC, SPLIT>(d_tmem, adesc + (uint64_t)(j0 + t), bdesc + (uint64_t)t * btap,
+                                                     ak, bk, alo, blo, idesc, accumulate);
+                            issued = true;
+                            umma_commit(b_empty0 + 8u * bs);
+                            if (++bs == P.nb) { bs = 0; bph ^= 1; bdesc = bdesc0; } else { bdesc += b_step; }
+                        }
                     }
                     if (!ok) break;
                     umma_commit(a_empty0 + 8u * as);
@@ -373,6 +415,7 @@ __global__ void __launch_bounds__(kThreads, 1) fbc_tc_corr(const __grid_constant
         // ------------------------------------------------------------ epilogue
         const int ew = warp - 2;         // staging buffer
         const int lq = warp & 3;         // TMEM lane quarter this warp may access
+        const int part = ew >> 2;        // with 8 epilogue warps: even / odd chunks of this quarter
         float* stg = reinterpret_cast<float*>(smem + P.stg_off) + ew * 32 * kStgPitch;
         uint32_t acc_it = 0;
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -392,7 +435,7 @@ __global__ void __launch_bounds__(kThreads, 1) fbc_tc_corr(const __grid_constant
                 obase[it] = (p < P.Ho && q < P.Wo) ? (p * P.Wo + q) * P.N : -1;
             }
             const int ncol = (P.nt + 31) / 32;   // a 16-wide tile still loads one 32-column chunk
-            for (int cc = 0; cc < ncol; ++cc) {
+            for (int cc = part; cc < ncol; cc += kEpiWarps / 4) {
                 uint32_t r[32];
                 tmem_ld32(tmem + ((uint32_t)(lq * 32) << 16) + (uint32_t)(acc * kAccCols + cc * 32), r);
                 float4* srow = reinterpret_cast<float4*>(stg + lane * kStgPitch);
@@ -409,12 +452,15 @@ __global__ void __launch_bounds__(kThreads, 1) fbc_tc_corr(const __grid_constant
                     srow[k] = v;
                 }
                 __syncwarp();
+                // columns past this tile's last filter (nt is a multiple of 16, the
+                // chunk 32 wide) hold no result: stop at the tile end as well as N
+                const int nend = min(P.N, (nti + 1) * P.nt);
                 const int n0 = nti * P.nt + cc * 32 + (lane & 7) * 4;
-                const bool vec = ((P.N & 3) == 0) && (n0 + 4 <= P.N);
+                const bool vec = ((P.N & 3) == 0) && (n0 + 4 <= nend);
 #pragma unroll
                 for (int it = 0; it < 8; ++it) {
                     const int row = it * 4 + (lane >> 3);
-                    if (obase[it] < 0 || n0 >= P.N) continue;
+                    if (obase[it] < 0 || n0 >= nend) continue;
                     const float4 v = *reinterpret_cast<const float4*>(stg + row * kStgPitch + (lane & 7) * 4);
                     float* dst = P.y + (long long)obase[it] + n0;
                     if (vec) {
@@ -422,7 +468,7 @@ __global__ void __launch_bounds__(kThreads, 1) fbc_tc_corr(const __grid_constant
                     } else {
                         const float vv[4] = {v.x, v.y, v.z, v.w};
                         for (int e = 0; e < 4; ++e)
-                            if (n0 + e < P.N) dst[e] = vv[e];
+                            if (n0 + e < nend) dst[e] = vv[e];
                     }
                 }
                 __syncwarp();
@@ -476,22 +522,34 @@ __global__ void __launch_bounds__(256) fbc_tc_split(const __grid_constant__ Spli
         if (pix >= S.npix_pad) return;
         const bool inside = pix < S.npix;
         const float* src = S.x + pix * S.D;
-        for (int c = 0; c < S.nc; ++c) {
-            float v[8];
-            if (inside && (S.D & 7) == 0 && c * 8 + 8 <= S.D) {
-                const float4* s4 = reinterpret_cast<const float4*>(src + c * 8);
-                const float4 a = __ldg(s4), b = __ldg(s4 + 1);
-                v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-                v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
-            } else {
+        // all loads first (up to 8 planes, 64 registers), then convert and store,
+        // so the loads of one pixel are in flight together
+        float v[8][8];
+        const bool vec = inside && (S.D & 7) == 0;
 #pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const int d = c * 8 + k;
-                    v[k] = (inside && d < S.D) ? __ldg(src + d) : 0.f;
+        for (int c = 0; c < 8; ++c) {
+            if (c < S.nc) {
+                if (vec && c * 8 + 8 <= S.D) {
+                    const float4* s4 = reinterpret_cast<const float4*>(src + c * 8);
+                    const float4 a = __ldg(s4), b = __ldg(s4 + 1);
+                    v[c][0] = a.x; v[c][1] = a.y; v[c][2] = a.z; v[c][3] = a.w;
+                    v[c][4] = b.x; v[c][5] = b.y; v[c][6] = b.z; v[c][7] = b.w;
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        const int d = c * 8 + k;
+                        v[c][k] = (inside && d < S.D) ? __ldg(src + d) : 0.f;
+                    }
                 }
             }
-            const long long idx = (long long)c * S.npix_pad + pix;
-            split8(v, reinterpret_cast<uint4*>(S.xhi) + idx, reinterpret_cast<uint4*>(S.xlo) + idx, S.split);
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            if (c < S.nc) {
+                const long long idx = (long long)c * S.npix_pad + pix;
+                split8(v[c], reinterpret_cast<uint4*>(S.xhi) + idx, reinterpret_cast<uint4*>(S.xlo) + idx,
+                       S.split);
+            }
         }
     } else {
         const long long idx = ((long long)blockIdx.x - S.xblocks) * 256 + threadIdx.x;
@@ -520,24 +578,31 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 typedef void (*TcKernelFn)(const TcParams);
 
-TcKernelFn tc_kernel_for(int nc, int split) {
+template <int LF>
+TcKernelFn tc_kernel_lf(int nc, int split) {
     switch (nc * 2 + (split ? 1 : 0)) {
-        case 4: return fbc_tc_corr<2, 0>;
-        case 5: return fbc_tc_corr<2, 1>;
-        case 8: return fbc_tc_corr<4, 0>;
-        case 9: return fbc_tc_corr<4, 1>;
-        case 12: return fbc_tc_corr<6, 0>;
-        case 13: return fbc_tc_corr<6, 1>;
-        case 16: return fbc_tc_corr<8, 0>;
-        case 17: return fbc_tc_corr<8, 1>;
+        case 4: return fbc_tc_corr<2, 0, LF>;
+        case 5: return fbc_tc_corr<2, 1, LF>;
+        case 8: return fbc_tc_corr<4, 0, LF>;
+        case 9: return fbc_tc_corr<4, 1, LF>;
+        case 12: return fbc_tc_corr<6, 0, LF>;
+        case 13: return fbc_tc_corr<6, 1, LF>;
+        case 16: return fbc_tc_corr<8, 0, LF>;
+        case 17: return fbc_tc_corr<8, 1, LF>;
     }
     return nullptr;
+}
+
+TcKernelFn tc_kernel_for(int nc, int split, int lf) {
+    return lf ? tc_kernel_lf<1>(nc, split) : tc_kernel_lf<0>(nc, split);
 }
 
 }  // namespace
 
 struct TcConfig {
     int na = 2, nb = 5, ntmax = 256;   // A slots, B stages, widest filter tile
+    int bt = 1;                        // filter taps per B stage
+    int lf = 0;                        // issuing-loop form (see fbc_tc_corr)
 };
 
 struct TcPlan {
@@ -578,7 +643,8 @@ bool tc_layout(TcPlan* p, const TcConfig& c, bool commit) {
     const int lp = (kTileM + p->fw - 1 + 7) / 8 * 8;
     const int halves = p->split ? 2 : 1;
     const uint32_t a_slot = (uint32_t)align_up((size_t)nc * lp * 16 * halves, 128);
-    const uint32_t b_stage = (uint32_t)align_up((size_t)nc * nt * 16 * halves, 128);
+    if (c.bt < 1 || c.bt > p->fw) return false;
+    const uint32_t b_stage = (uint32_t)align_up((size_t)c.bt * nc * nt * 16 * halves, 128);
     if (c.na < 2 || c.nb < 2) return false;
     const size_t need = (size_t)c.na * a_slot + (size_t)c.nb * b_stage + kStgBytes + 512;
     if (need > kSmemMax) return false;
@@ -589,7 +655,7 @@ bool tc_layout(TcPlan* p, const TcConfig& c, bool commit) {
     k.npix_pad = (long long)align_up((size_t)p->H * p->W + kTileM + p->fw + 8, 8);
     k.W = p->W; k.Ho = Ho; k.Wo = Wo; k.N = p->N;
     k.fh = p->fh; k.fw = p->fw; k.nc = nc; k.nt = nt; k.ntn = ntn; k.mtiles = mtiles;
-    k.lp = lp; k.split = p->split; k.na = c.na; k.nb = c.nb;
+    k.lp = lp; k.split = p->split; k.na = c.na; k.nb = c.nb; k.bt = c.bt;
     k.a_slot = a_slot; k.b_stage = b_stage;
     k.a_tx = (uint32_t)(nc * (kTileM + p->fw - 1) * 16 * halves);
     k.b_tx = (uint32_t)(nc * nt * 16 * halves);
@@ -620,6 +686,7 @@ bool tc_layout(TcPlan* p, const TcConfig& c, bool commit) {
     const long long wblocks = ((long long)ntn * p->fh * p->fw * nc * nt + 255) / 256;
     p->split_blocks = (int)(sp.xblocks + wblocks);
     p->grid = std::min(mtiles * ntn, std::max(1, p->sm_count));
+    p->kfn = tc_kernel_for(nc, p->split, c.lf);
     return true;
 }
 
@@ -631,23 +698,32 @@ size_t tc_ws_need(TcPlan* p, const TcConfig& c) {
 }
 
 std::vector<TcConfig> tc_candidate_configs(TcPlan* p) {
+    // widest filter tile first; within it, taps per stage from the most (fewest
+    // barrier handoffs) down, each with the deepest B ring that fits
     std::vector<TcConfig> out;
     const int widths[] = {256, 128};
     for (int ntmax : widths) {
         if (ntmax == 128 && p->N <= 128) continue;
-        for (int na = 2; na <= 4; ++na) {
-            int best = 0;
-            for (int nb = 2; nb <= 10; ++nb)
-                if (tc_layout(p, TcConfig{na, nb, ntmax}, false)) best = nb;
-            if (best) out.push_back(TcConfig{na, best, ntmax});
-        }
+        for (int bt = std::min(p->fw, 5); bt >= 1; --bt)
+            for (int na = 2; na <= 3; ++na) {
+                int best = 0;
+                for (int nb = 2; nb <= 10; ++nb)
+                    if (tc_layout(p, TcConfig{na, nb, ntmax, bt, 0}, false)) best = nb;
+                if (!best) continue;
+                out.push_back(TcConfig{na, best, ntmax, bt, 0});
+                if (bt > 1) out.push_back(TcConfig{na, best, ntmax, bt, 1});
+            }
     }
     return out;
 }
 
 bool parse_tc_spec(const std::string& s, TcConfig* c) {
     TcConfig t;
-    if (sscanf(s.c_str(), "tcgen05:na=%d,nb=%d,nt=%d", &t.na, &t.nb, &t.ntmax) != 3) return false;
+    const int n = sscanf(s.c_str(), "tcgen05:na=%d,nb=%d,nt=%d,bt=%d,lf=%d", &t.na, &t.nb, &t.ntmax,
+                         &t.bt, &t.lf);
+    if (n == 3) t.bt = 1;
+    if (n <= 4) t.lf = 0;
+    if (n < 3 || t.lf < 0 || t.lf > 1) return false;
     if (t.ntmax != 256 && t.ntmax != 128 && t.ntmax != 64) return false;
     *c = t;
     return true;
@@ -657,7 +733,8 @@ bool parse_tc_spec(const std::string& s, TcConfig* c) {
 
 std::string tc_spec(const TcPlan* p) {
     char b[96];
-    snprintf(b, sizeof b, "tcgen05:na=%d,nb=%d,nt=%d", p->cfg.na, p->cfg.nb, p->cfg.ntmax);
+    snprintf(b, sizeof b, "tcgen05:na=%d,nb=%d,nt=%d,bt=%d,lf=%d", p->cfg.na, p->cfg.nb, p->cfg.ntmax,
+             p->cfg.bt, p->cfg.lf);
     return b;
 }
 
@@ -665,7 +742,7 @@ std::vector<std::string> tc_candidates(TcPlan* p) {
     std::vector<std::string> out;
     for (const auto& c : tc_candidate_configs(p)) {
         char b[96];
-        snprintf(b, sizeof b, "tcgen05:na=%d,nb=%d,nt=%d", c.na, c.nb, c.ntmax);
+        snprintf(b, sizeof b, "tcgen05:na=%d,nb=%d,nt=%d,bt=%d,lf=%d", c.na, c.nb, c.ntmax, c.bt, c.lf);
         out.push_back(b);
     }
     return out;
@@ -693,7 +770,7 @@ fbcorr_status_t tc_plan_create(TcPlan** out, int H, int W, int D, int N, int fh,
     p->sm_count = dev.sm_count;
     const long long wait_ms = atoll(env_str("FBCORR_WAIT_MS", "4000").c_str());
     p->wait_ns = (unsigned long long)std::max(1LL, wait_ms) * 1000000ull;
-    p->drop_b = fault_injected("tcdrop") ? 3 : -1;
+    p->drop_b = fault_injected("tcdrop") ? 0 : -1;   // the first B stage: every CTA has one
     const std::vector<TcConfig> cands = tc_candidate_configs(p);
     if (cands.empty()) {
         delete p;
@@ -703,11 +780,13 @@ fbcorr_status_t tc_plan_create(TcPlan** out, int H, int W, int D, int N, int fh,
     // default: the fewest A slots (2) with the deepest B ring, widest filter tile
     tc_layout(p, cands.front(), true);
     // one attribute for every plan: the largest dynamic shared memory any plan uses
-    p->kfn = tc_kernel_for(p->kp.nc, p->split);
-    cudaError_t e = p->kfn ? cudaFuncSetAttribute((const void*)p->kfn,
-                                                  cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                  (int)kSmemMax)
-                           : cudaErrorInvalidValue;
+    cudaError_t e = cudaSuccess;
+    for (int lf = 0; lf <= 1 && e == cudaSuccess; ++lf) {
+        TcKernelFn f = tc_kernel_for(p->kp.nc, p->split, lf);
+        e = f ? cudaFuncSetAttribute((const void*)f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kSmemMax)
+              : cudaErrorInvalidValue;
+    }
     if (e != cudaSuccess) {
         delete p;
         return set_error(FBCORR_ERR_CUDA, "cudaFuncSetAttribute(tc smem): %s", cudaGetErrorString(e));

@@ -161,3 +161,35 @@ def test_split_beats_bf16_and_approaches_fp32():
     for mode in ("bf16", "bf16x3"):
         e[mode] = normwise_rel(host(_plan(torch, mode, wl.x, wl.w).forward(x, w)), ref)
     assert e["bf16x3"] <= 1e-5 < e["bf16"] <= 1e-2, e
+
+
+@pytest.mark.parametrize("mode", ["bf16", "bf16x3"])
+def test_every_tensor_core_configuration_matches(mode):
+    """Every configuration the auto-tuner may pick (ring depths, filter-tile
+    width, taps per B stage -- including a last stage with fewer taps) gives
+    the same result on integer inputs, bit for bit."""
+    torch = torch_cuda()
+    from paper_0911_3456_gb300 import _capi as C
+    from paper_0911_3456_gb300.api import Plan
+    wl = inputs.random_case(1700, 21, 140, 32, 272, 3, 5, kind="int")
+    ref = oracle.fwd(wl.x, wl.w)
+    p = Plan(wl.x.shape, wl.w.shape, mode)
+    x, w = dev(wl.x, torch), dev(wl.w, torch)
+    specs = set()
+    for na in (2, 3):
+        for nb in (2, 3, 4):
+            for nt in (256, 128):
+                for bt in (1, 2, 3, 5):
+                    for lf in (0, 1):
+                        specs.add(f"tcgen05:na={na},nb={nb},nt={nt},bt={bt},lf={lf}")
+    ran = 0
+    for sp in sorted(specs):
+        try:
+            p.set_variant(sp)
+        except C.FbcorrError:
+            continue              # does not fit this shape's shared memory
+        assert p.info()["fwd"]["spec"] == sp
+        y = host(p.forward(x, w))
+        assert np.array_equal(y, ref), sp
+        ran += 1
+    assert ran >= 16
