@@ -136,13 +136,22 @@ def barrier(world):
 
 
 def max_over_ranks(v: float, world: int) -> float:
+    """The slowest rank's value (replicas are timed together; the job ends
+    when the last one does)."""
     if world == 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_throughput(units_per_rank: float, ms: float, world: int) -> float:
+    """Whole-job throughput of `world` independent replicas that each processed
+    `units_per_rank` units, timed by the slowest rank (`ms`)."""
+    return world * units_per_rank / (ms * 1e-3)
 
 
 def time_loop(torch, fn, steps, warmup, world, flush=None):
@@ -332,7 +341,7 @@ def run_ours(args):
     kern_ms = plan.profile_read()
     plan.profile(0)
     kern_avg = float(np.mean(kern_ms)) if kern_ms else None
-    value = world * flops / (ms * 1e-3) / 1e9
+    value = replica_throughput(flops, ms, world) / 1e9
     info = plan.info()
     launches_per_step = int(info["fwd"].get("launches", 1))
 
@@ -452,6 +461,27 @@ def secondary(torch, args, world, peaks):
                      "boost_percent": 100.0 * (ms_def / ms_tuned - 1.0),
                      "tuned_frac_of_fp32_peak": wl.flops / ms_tuned / 1e9 / peaks["fp32_tflops"],
                      "tuned_spec": p.info()["fwd"].get("spec")}
+    # the paper's own table shapes: default (prebuilt generic) vs tuned, the
+    # table's "Default", "RTCG auto-tuned" and "Boost" columns measured here
+    table = []
+    for row in range(len(inputs.PAPER_TABLE_SHAPES)):
+        wl = inputs.workload_paper_table(row)
+        x = torch.from_numpy(wl.x).cuda()
+        w = torch.from_numpy(wl.w).cuda()
+        p = Plan(wl.x.shape, wl.w.shape, "f32")
+        y = torch.empty(p.out_shape, device="cuda")
+        p.set_variant("default")
+        ms_def = time_loop(torch, lambda: p.forward(x, w, y), 20, 3, world, flush)
+        p.autotune()
+        ms_tuned = time_loop(torch, lambda: p.forward(x, w, y), 20, 3, world, flush)
+        table.append({"input": list(wl.x.shape), "bank": list(wl.w.shape),
+                      "default_gflops": wl.flops / ms_def / 1e6, "tuned_gflops": wl.flops / ms_tuned / 1e6,
+                      "boost_percent": 100.0 * (ms_def / ms_tuned - 1.0),
+                      "tuned_frac_of_fp32_peak": wl.flops / ms_tuned / 1e9 / peaks["fp32_tflops"],
+                      "tuned_spec": p.info()["fwd"].get("spec")})
+        del x, w, y, p
+    out["paper_table_fp32"] = table
+
     wl = inputs.workload_differentiation()
     x = torch.from_numpy(wl.x).cuda()
     w = torch.from_numpy(wl.w).cuda()
@@ -478,7 +508,15 @@ def secondary(torch, args, world, peaks):
     from paper_0911_3456_gb300.api import BatchPlan
     bw = inputs.workload_batch()
     t0 = time.perf_counter()
-    bp = BatchPlan([it.x.shape for it in bw.items], [it.w.shape for it in bw.items])
+    old_at = os.environ.get("FBCORR_AUTOTUNE")
+    os.environ["FBCORR_AUTOTUNE"] = "1"          # per-variant tiles measured on this GPU
+    try:
+        bp = BatchPlan([it.x.shape for it in bw.items], [it.w.shape for it in bw.items])
+    finally:
+        if old_at is None:
+            os.environ.pop("FBCORR_AUTOTUNE", None)
+        else:
+            os.environ["FBCORR_AUTOTUNE"] = old_at
     t_plan = time.perf_counter() - t0
     xs = [torch.from_numpy(it.x).cuda() for it in bw.items]
     wss = [torch.from_numpy(it.w).cuda() for it in bw.items]
@@ -489,7 +527,7 @@ def secondary(torch, args, world, peaks):
         "gflops": bw.flops / ms_b / 1e6, "ms": ms_b, "flops": bw.flops,
         "frac_of_fp32_peak": bw.flops / ms_b / 1e9 / fp, "launches_per_step": binfo["launches"],
         "work_items": binfo["work_items"], "grid": binfo["grid"], "variants": len(binfo["variants"]),
-        "plan_seconds": t_plan}
+        "plan_seconds_incl_tuning": t_plan, "tiles": [v["spec"] for v in binfo["variants"]]}
     return out
 
 

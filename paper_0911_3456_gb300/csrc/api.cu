@@ -23,16 +23,7 @@ using namespace fbc;
 
 namespace {
 
-// Host mirrors of the NVRTC kernels' by-value argument structs (rtcg_direct.cuh).
-struct DirectArgsK {
-    const float* x;
-    const float* m;
-    const float* w;
-    float* y;
-    int in_h, in_w, out_h, out_w, nf;
-    int pad_y, pad_x;
-    float lo, hi;
-};
+// Host mirror of the NVRTC dL/dw kernel's by-value argument struct (rtcg_direct.cuh).
 struct DwArgsK {
     const float* x;
     const float* g;
@@ -81,44 +72,6 @@ DirectProblem dx_problem(const fbcorr_plan* p) {
     pr.epi = 0;
     pr.mask = p->epi.kind == FBCORR_EPI_CLAMP ? 1 : 0;
     return pr;
-}
-
-std::string kname_for(const char* base, const DirectProblem& pr, const DirectTile& t) {
-    char b[160];
-    snprintf(b, sizeof b, "%s_f%dx%d_c%d_t%d_%d_%d_%d_cc%d_fl%d_e%d_m%d", base, pr.fh, pr.fw, pr.c,
-             t.tr, t.tf, t.wr, t.wf, t.chunk(pr.c), pr.flip, pr.epi, pr.mask);
-    return b;
-}
-
-size_t smem_limit(const DeviceInfo& dev) {
-    return std::min<size_t>(dev.smem_optin ? dev.smem_optin : 227 * 1024, 200 * 1024);
-}
-
-fbcorr_status_t build_direct(const DirectProblem& pr, const DirectTile& t, Kernel* k) {
-    const std::string name = kname_for("fbc_direct", pr, t);
-    const std::string src = direct_kernel_source(pr, t, name);
-    return rtcg_kernel(src, name, direct_smem_bytes(t, pr.fh, pr.fw, pr.c), t.threads(), k);
-}
-
-dim3 direct_grid(const DirectProblem& pr, const DirectTile& t) {
-    return dim3((unsigned)((pr.out_w + 31) / 32), (unsigned)((pr.out_h + t.bh() - 1) / t.bh()),
-                (unsigned)((pr.nf + t.bn() - 1) / t.bn()));
-}
-
-fbcorr_status_t run_direct(const Kernel& k, const DirectProblem& pr, const DirectTile& t,
-                           const float* x, const float* m, const float* w, float* y, float lo,
-                           float hi, cudaStream_t s) {
-    DirectArgsK a{x, m, w, y, pr.in_h, pr.in_w, pr.out_h, pr.out_w, pr.nf, pr.pad_y, pr.pad_x, lo, hi};
-    void* args[] = {&a};
-    return launch(k, direct_grid(pr, t), args, s);
-}
-
-fbcorr_status_t run_default(const DirectProblem& pr, const float* x, const float* m,
-                            const float* w, float* y, float lo, float hi, cudaStream_t s) {
-    DirectArgsRT a{x, m, w, y, pr.in_h, pr.in_w, pr.c, pr.out_h, pr.out_w, pr.nf, pr.fh, pr.fw,
-                   pr.pad_y, pr.pad_x, pr.flip, pr.epi, pr.mask, lo, hi};
-    FBC_CUDA(launch_default_direct(a, s));
-    return FBCORR_OK;
 }
 
 const char* kind_name(VarKind k) {
@@ -527,79 +480,11 @@ fbcorr_status_t fbcorr_plan_set_variant(fbcorr_plan_t p, const char* spec) {
 
 static fbcorr_status_t autotune_tc(fbcorr_plan_t p, fbcorr_stream_t stream);
 
-// Time the top candidates of one direct-correlation problem (forward or dL/dx)
-// and the prebuilt default kernel on zero-filled buffers; returns the fastest.
 static fbcorr_status_t tune_direct(fbcorr_plan_t p, const DirectProblem& pr, cudaStream_t s,
                                    const char* what, std::string* best_spec, float* best_ms_out) {
-    std::vector<DirectTile> ranked = direct_ranked(pr, smem_limit(p->dev), p->dev.sm_count);
     int topk = atoi(env_str("FBCORR_TUNE_TOPK", "12").c_str());
-    if (topk < 1) topk = 1;
-    std::vector<std::string> specs;
-    for (auto& t : ranked) {
-        if ((int)specs.size() >= topk) break;
-        specs.push_back(direct_tile_spec(t));
-    }
-    specs.push_back("default");
-    const size_t xb = (size_t)pr.in_h * pr.in_w * pr.c * 4;
-    const size_t wb = (size_t)pr.nf * pr.fh * pr.fw * pr.c * 4;
-    const size_t yb = (size_t)pr.out_h * pr.out_w * pr.nf * 4;
-    float *x = nullptr, *w = nullptr, *y = nullptr, *m = nullptr;
-    if (cudaMalloc(&x, xb) != cudaSuccess || cudaMalloc(&w, wb) != cudaSuccess ||
-        cudaMalloc(&y, yb) != cudaSuccess || (pr.mask && cudaMalloc(&m, xb) != cudaSuccess)) {
-        cudaFree(x); cudaFree(w); cudaFree(y); cudaFree(m);
-        cudaGetLastError();
-        return set_error(FBCORR_ERR_OOM, "autotune buffers");
-    }
-    cudaMemsetAsync(x, 0, xb, s);
-    cudaMemsetAsync(w, 0, wb, s);
-    if (m) cudaMemsetAsync(m, 0, xb, s);
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    float best_ms = 1e30f;
-    fbcorr_status_t status = FBCORR_OK;
-    for (const auto& sp : specs) {
-        Kernel k;
-        DirectTile t;
-        const bool dflt = sp == "default";
-        if (!dflt) {
-            if (!parse_direct_spec(sp, &t) || build_direct(pr, t, &k) != FBCORR_OK) continue;
-        }
-        auto run = [&]() {
-            return dflt ? run_default(pr, x, m, w, y, 0.f, 1.f, s)
-                        : run_direct(k, pr, t, x, m, w, y, 0.f, 1.f, s);
-        };
-        std::vector<float> ms_list;
-        bool ok = true;
-        for (int r = 0; r < 2 && ok; ++r) ok = run() == FBCORR_OK;
-        for (int r = 0; r < 7 && ok; ++r) {
-            cudaEventRecord(e0, s);
-            ok = run() == FBCORR_OK;
-            cudaEventRecord(e1, s);
-            if (cudaEventSynchronize(e1) != cudaSuccess) ok = false;
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            ms_list.push_back(ms);
-        }
-        if (!ok) {
-            status = set_error(FBCORR_ERR_CUDA, "autotune run of %s (%s) failed", sp.c_str(), what);
-            break;
-        }
-        std::sort(ms_list.begin(), ms_list.end());
-        const float med = ms_list[ms_list.size() / 2];
-        logf("autotune %s %s: %.4f ms", what, sp.c_str(), med);
-        if (med < best_ms) {
-            best_ms = med;
-            *best_spec = sp;
-        }
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    cudaFree(x); cudaFree(w); cudaFree(y); cudaFree(m);
-    if (status != FBCORR_OK) return status;
-    if (best_spec->empty()) return set_error(FBCORR_ERR_INTERNAL, "no %s variant ran", what);
-    if (best_ms_out) *best_ms_out = best_ms;
-    return FBCORR_OK;
+    return tune_direct_problem(p->dev, pr, s, 0, 64, smem_limit(p->dev), std::max(1, topk), true, what,
+                               best_spec, best_ms_out);
 }
 
 fbcorr_status_t fbcorr_autotune(fbcorr_plan_t p, fbcorr_stream_t stream) {

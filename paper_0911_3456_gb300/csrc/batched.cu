@@ -131,40 +131,84 @@ void destroy(fbcorr_batch_plan* b) {
     delete b;
 }
 
-fbcorr_status_t select_variants(fbcorr_batch_plan* b) {
-    // ---- variants: one tile per (fh, fw, D, filter class), 256 threads per CTA
+// One tile per (fh, fw, D, filter class), 256 threads per CTA.  The tile comes
+// from, in order: a measurement when FBCORR_AUTOTUNE is 1 or force (the
+// variant's largest image, timed as a single-image launch under the batch
+// kernel's constraints, result stored in the tuning cache), the tuning cache,
+// or the analytic ranking.
+fbcorr_status_t select_variants(fbcorr_batch_plan* b, bool allow_tuning) {
     std::map<std::tuple<int, int, int, int>, int> key_to_var;
+    std::vector<int> rep_image;   // per variant: its largest image
     b->var_of.resize(b->n);
+    b->variants.clear();
     for (int k = 0; k < b->n; ++k) {
         const auto& s = b->shp[k];
         const auto key = std::make_tuple((int)s[4], (int)s[5], (int)s[2], filter_class(s[3]));
         auto it = key_to_var.find(key);
         if (it == key_to_var.end()) {
-            BatchVariant bv{(int)s[4], (int)s[5], (int)s[2], filter_class(s[3]), DirectTile{}};
-            DirectProblem rep{256 + bv.fh - 1, 256 + bv.fw - 1, bv.d, 256, 256, bv.nclass,
-                              bv.fh, bv.fw, 0, 0, 0, b->epi.kind == FBCORR_EPI_CLAMP ? 1 : 0, 0};
-            std::string spec;
-            char key_s[96];
-            snprintf(key_s, sizeof key_s, "batchvar|f%dx%d|c%d|n%d|t%d", bv.fh, bv.fw, bv.d, bv.nclass,
-                     kBatchThreads);
-            DirectTile cached;
-            if (tune_lookup(tune_key(b->dev, key_s), &spec) && parse_direct_spec(spec, &cached) &&
-                cached.threads() == kBatchThreads && cached.tr * cached.tf <= kBatchMaxBlock &&
-                direct_smem_bytes(cached, bv.fh, bv.fw, bv.d) <= kBatchSmemLimit)
-                bv.tile = cached;
-            else
-                bv.tile = direct_heuristic(rep, kBatchSmemLimit, b->dev.sm_count, kBatchThreads,
-                                           kBatchMaxBlock);
-            if (bv.tile.threads() != kBatchThreads ||
-                direct_smem_bytes(bv.tile, bv.fh, bv.fw, bv.d) > kBatchSmemLimit)
-                return set_error(FBCORR_ERR_UNSUPPORTED,
-                                 "no batched tile fits filter %dx%d at depth %d", bv.fh, bv.fw, bv.d);
             key_to_var[key] = (int)b->variants.size();
-            b->variants.push_back(bv);
+            b->variants.push_back(BatchVariant{(int)s[4], (int)s[5], (int)s[2], filter_class(s[3]), DirectTile{}});
+            rep_image.push_back(k);
             it = key_to_var.find(key);
         }
-        b->var_of[k] = it->second;
+        const int v = it->second;
+        b->var_of[k] = v;
+        auto work = [&](int img) {
+            const auto& t = b->shp[img];
+            return (t[0] - t[4] + 1) * (t[1] - t[5] + 1) * t[3];
+        };
+        if (work(k) > work(rep_image[v])) rep_image[v] = k;
     }
+    const std::string at = env_str("FBCORR_AUTOTUNE", "0");
+    const bool tune = allow_tuning && (at == "1" || at == "force");
+    const int topk = std::max(1, atoi(env_str("FBCORR_TUNE_TOPK_BATCH", "4").c_str()));
+    const int epi = b->epi.kind == FBCORR_EPI_CLAMP ? 1 : 0;
+    if (tune) {
+        // compile the candidates of every variant at once, in parallel
+        std::vector<std::string> srcs;
+        for (size_t v = 0; v < b->variants.size(); ++v) {
+            const BatchVariant& bv = b->variants[v];
+            const auto& s = b->shp[rep_image[v]];
+            DirectProblem rep{(int)s[0], (int)s[1], bv.d, (int)(s[0] - s[4] + 1), (int)(s[1] - s[5] + 1),
+                              (int)s[3], bv.fh, bv.fw, 0, 0, 0, epi, 0};
+            auto ranked = direct_ranked(rep, kBatchSmemLimit, b->dev.sm_count, kBatchThreads, kBatchMaxBlock);
+            for (int k = 0; k < topk && k < (int)ranked.size(); ++k)
+                srcs.push_back(direct_kernel_source(rep, ranked[k], kname_for("fbc_direct", rep, ranked[k])));
+        }
+        rtcg_precompile(srcs);
+    }
+    for (size_t v = 0; v < b->variants.size(); ++v) {
+        BatchVariant& bv = b->variants[v];
+        const auto& s = b->shp[rep_image[v]];
+        DirectProblem rep{(int)s[0], (int)s[1], bv.d, (int)(s[0] - s[4] + 1), (int)(s[1] - s[5] + 1),
+                          (int)s[3], bv.fh, bv.fw, 0, 0, 0, epi, 0};
+        char key_s[96];
+        snprintf(key_s, sizeof key_s, "batchvar|f%dx%d|c%d|n%d|t%d", bv.fh, bv.fw, bv.d, bv.nclass,
+                 kBatchThreads);
+        const std::string key = tune_key(b->dev, key_s);
+        std::string spec;
+        DirectTile t;
+        bool have = false;
+        if (tune && (at == "force" || !tune_lookup(key, &spec))) {
+            float ms = 0.f;
+            if (tune_direct_problem(b->dev, rep, nullptr, kBatchThreads, kBatchMaxBlock, kBatchSmemLimit,
+                                    topk, false, "batch", &spec, &ms) == FBCORR_OK &&
+                parse_direct_spec(spec, &t)) {
+                tune_store(key, spec);
+                have = true;
+            }
+        }
+        if (!have && tune_lookup(key, &spec) && parse_direct_spec(spec, &t) &&
+            t.threads() == kBatchThreads && t.tr * t.tf <= kBatchMaxBlock &&
+            direct_smem_bytes(t, bv.fh, bv.fw, bv.d) <= kBatchSmemLimit)
+            have = true;
+        if (!have) t = direct_heuristic(rep, kBatchSmemLimit, b->dev.sm_count, kBatchThreads, kBatchMaxBlock);
+        if (t.threads() != kBatchThreads || direct_smem_bytes(t, bv.fh, bv.fw, bv.d) > kBatchSmemLimit)
+            return set_error(FBCORR_ERR_UNSUPPORTED, "no batched tile fits filter %dx%d at depth %d", bv.fh,
+                             bv.fw, bv.d);
+        bv.tile = t;
+    }
+    clear_error();
     return FBCORR_OK;
 }
 
@@ -176,7 +220,7 @@ size_t batch_smem(const fbcorr_batch_plan* b) {
 }
 
 fbcorr_status_t build(fbcorr_batch_plan* b) {
-    FBC_TRY(select_variants(b));
+    FBC_TRY(select_variants(b, true));
     const size_t smem = batch_smem(b);
 
     // ---- one generated kernel for the whole batch
@@ -318,7 +362,7 @@ fbcorr_status_t fbcorr_batch_rtcg_check(int n, const int64_t (*in_shapes)[3],
     for (int k = 0; k < n; ++k)
         tmp.shp.push_back({in_shapes[k][0], in_shapes[k][1], in_shapes[k][2], filt_shapes[k][0],
                            filt_shapes[k][1], filt_shapes[k][2]});
-    FBC_TRY(select_variants(&tmp));
+    FBC_TRY(select_variants(&tmp, false));
     std::string lg;
     fbcorr_status_t s = rtcg_compile_only(batch_source(&tmp), &lg);
     if (s != FBCORR_OK && log && cap) snprintf(log, cap, "%s", lg.c_str());

@@ -61,6 +61,8 @@ struct Kernel {
 // on-disk cubin cache, load it into the current context and return a handle.
 fbcorr_status_t rtcg_kernel(const std::string& src, const std::string& name, size_t smem,
                             int threads, Kernel* out);
+// Compile many sources on host threads into the on-disk cubin cache.
+fbcorr_status_t rtcg_precompile(const std::vector<std::string>& sources);
 // Compile only (no GPU needed); returns the NVRTC log on failure.
 fbcorr_status_t rtcg_compile_only(const std::string& src, std::string* log);
 fbcorr_status_t launch(const Kernel& k, dim3 grid, void** args, cudaStream_t stream);
@@ -106,6 +108,21 @@ DirectTile direct_heuristic(const DirectProblem& pr, size_t smem_limit, int sm_c
 // candidates ordered by the analytic model, best first
 std::vector<DirectTile> direct_ranked(const DirectProblem& pr, size_t smem_limit, int sm_count,
                                       int threads = 0, int max_block = 64);
+
+// Build / launch generated direct kernels and measure candidates (variants.cu).
+std::string kname_for(const char* base, const DirectProblem& pr, const DirectTile& t);
+size_t smem_limit(const DeviceInfo& dev);
+fbcorr_status_t build_direct(const DirectProblem& pr, const DirectTile& t, Kernel* k);
+dim3 direct_grid(const DirectProblem& pr, const DirectTile& t);
+fbcorr_status_t run_direct(const Kernel& k, const DirectProblem& pr, const DirectTile& t,
+                           const float* x, const float* m, const float* w, float* y, float lo,
+                           float hi, cudaStream_t s);
+fbcorr_status_t run_default(const DirectProblem& pr, const float* x, const float* m,
+                            const float* w, float* y, float lo, float hi, cudaStream_t s);
+fbcorr_status_t tune_direct_problem(const DeviceInfo& dev, const DirectProblem& pr, cudaStream_t s,
+                                    int threads, int max_block, size_t smem_cap, int topk,
+                                    bool include_default, const char* what, std::string* best_spec,
+                                    float* best_ms_out);
 
 // dL/dw partial-sum kernel: TN filters x fw taps per thread, NG filter groups of
 // C threads per CTA, rows walked in blocks of QB columns staged in shared memory.

@@ -13,11 +13,14 @@
 #include <sys/stat.h>
 #include <unistd.h>
 
+#include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <thread>
 
 #include "internal.h"
 
@@ -201,6 +204,51 @@ fbcorr_status_t rtcg_compile_only(const std::string& src, std::string* log) {
     return compile(src, &cubin, log);
 }
 
+namespace {
+uint64_t source_hash(const std::string& src) {
+    std::string keysrc = src + "\n//" + kArch + " nvrtc " + nvrtc_version_string();
+    for (auto& o : nvrtc_options()) keysrc += " " + o;
+    return fnv1a(keysrc);
+}
+
+std::string cubin_path(uint64_t h) {
+    char hb[32];
+    snprintf(hb, sizeof hb, "%016llx", (unsigned long long)h);
+    return cache_dir() + "/rtcg-" + hb + ".cubin";
+}
+}  // namespace
+
+fbcorr_status_t rtcg_precompile(const std::vector<std::string>& sources) {
+    // Compile on host threads every source whose cubin is not cached yet; the
+    // results land in the on-disk cache that rtcg_kernel reads.  Failures are
+    // left for rtcg_kernel to report.
+    if (fault_injected("nvrtc") || fault_injected("nocache")) return FBCORR_OK;
+    std::vector<const std::string*> todo;
+    for (const auto& src : sources) {
+        struct stat st;
+        if (stat(cubin_path(source_hash(src)).c_str(), &st) != 0) todo.push_back(&src);
+    }
+    if (todo.empty()) return FBCORR_OK;
+    mkdirs(cache_dir());
+    unsigned hw = std::thread::hardware_concurrency();
+    const size_t nthreads = std::min<size_t>(todo.size(), std::max(1u, std::min(hw ? hw : 4u, 32u)));
+    std::atomic<size_t> next{0};
+    std::vector<std::thread> pool;
+    for (size_t t = 0; t < nthreads; ++t)
+        pool.emplace_back([&]() {
+            for (size_t k = next++; k < todo.size(); k = next++) {
+                std::vector<char> cubin;
+                std::string lg;
+                if (compile(*todo[k], &cubin, &lg) == FBCORR_OK)
+                    write_file_atomic(cubin_path(source_hash(*todo[k])), cubin);
+            }
+        });
+    for (auto& th : pool) th.join();
+    logf("rtcg: precompiled %zu sources on %zu threads", todo.size(), nthreads);
+    clear_error();
+    return FBCORR_OK;
+}
+
 fbcorr_status_t rtcg_kernel(const std::string& src, const std::string& name, size_t smem,
                             int threads, Kernel* out) {
     DriverApi* drv = nullptr;
@@ -210,9 +258,7 @@ fbcorr_status_t rtcg_kernel(const std::string& src, const std::string& name, siz
     if (drv->ctxGetCurrent(&ctx) != CUDA_SUCCESS || !ctx)
         return set_error(FBCORR_ERR_CUDA, "no current CUDA context");
 
-    std::string keysrc = src + "\n//" + kArch + " nvrtc " + nvrtc_version_string();
-    for (auto& o : nvrtc_options()) keysrc += " " + o;
-    const uint64_t h = fnv1a(keysrc);
+    const uint64_t h = source_hash(src);
 
     CUmodule mod = nullptr;
     const bool nocache = fault_injected("nocache");   // testing knob: bypass both caches
@@ -222,10 +268,8 @@ fbcorr_status_t rtcg_kernel(const std::string& src, const std::string& name, siz
         if (it != g_modules.end()) mod = it->second;
     }
     if (!mod) {
-        char hb[32];
-        snprintf(hb, sizeof hb, "%016llx", (unsigned long long)h);
         const std::string dir = cache_dir();
-        const std::string path = dir + "/rtcg-" + hb + ".cubin";
+        const std::string path = cubin_path(h);
         std::vector<char> cubin;
         bool cached = !nocache && read_file(path, &cubin);
         if (!cached) {

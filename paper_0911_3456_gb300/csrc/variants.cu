@@ -178,4 +178,144 @@ DirectTile direct_heuristic(const DirectProblem& pr, size_t smem_limit, int sm_c
     return threads == 256 ? DirectTile{4, 4, 2, 4, 4} : DirectTile{4, 4, 1, 1, 4};
 }
 
+
+// ---- building, launching and timing generated direct kernels -------------------
+
+namespace {
+// Host mirror of the NVRTC kernels' by-value argument struct (rtcg_direct.cuh).
+struct DirectArgsK {
+    const float* x;
+    const float* m;
+    const float* w;
+    float* y;
+    int in_h, in_w, out_h, out_w, nf;
+    int pad_y, pad_x;
+    float lo, hi;
+};
+}  // namespace
+
+std::string kname_for(const char* base, const DirectProblem& pr, const DirectTile& t) {
+    char b[160];
+    snprintf(b, sizeof b, "%s_f%dx%d_c%d_t%d_%d_%d_%d_cc%d_fl%d_e%d_m%d", base, pr.fh, pr.fw, pr.c,
+             t.tr, t.tf, t.wr, t.wf, t.chunk(pr.c), pr.flip, pr.epi, pr.mask);
+    return b;
+}
+
+size_t smem_limit(const DeviceInfo& dev) {
+    return std::min<size_t>(dev.smem_optin ? dev.smem_optin : 227 * 1024, 200 * 1024);
+}
+
+fbcorr_status_t build_direct(const DirectProblem& pr, const DirectTile& t, Kernel* k) {
+    const std::string name = kname_for("fbc_direct", pr, t);
+    const std::string src = direct_kernel_source(pr, t, name);
+    return rtcg_kernel(src, name, direct_smem_bytes(t, pr.fh, pr.fw, pr.c), t.threads(), k);
+}
+
+dim3 direct_grid(const DirectProblem& pr, const DirectTile& t) {
+    return dim3((unsigned)((pr.out_w + 31) / 32), (unsigned)((pr.out_h + t.bh() - 1) / t.bh()),
+                (unsigned)((pr.nf + t.bn() - 1) / t.bn()));
+}
+
+fbcorr_status_t run_direct(const Kernel& k, const DirectProblem& pr, const DirectTile& t,
+                           const float* x, const float* m, const float* w, float* y, float lo,
+                           float hi, cudaStream_t s) {
+    DirectArgsK a{x, m, w, y, pr.in_h, pr.in_w, pr.out_h, pr.out_w, pr.nf, pr.pad_y, pr.pad_x, lo, hi};
+    void* args[] = {&a};
+    return launch(k, direct_grid(pr, t), args, s);
+}
+
+fbcorr_status_t run_default(const DirectProblem& pr, const float* x, const float* m,
+                            const float* w, float* y, float lo, float hi, cudaStream_t s) {
+    DirectArgsRT a{x, m, w, y, pr.in_h, pr.in_w, pr.c, pr.out_h, pr.out_w, pr.nf, pr.fh, pr.fw,
+                   pr.pad_y, pr.pad_x, pr.flip, pr.epi, pr.mask, lo, hi};
+    FBC_CUDA(launch_default_direct(a, s));
+    return FBCORR_OK;
+}
+
+
+fbcorr_status_t tune_direct_problem(const DeviceInfo& dev, const DirectProblem& pr, cudaStream_t s,
+                                    int threads, int max_block, size_t smem_cap, int topk,
+                                    bool include_default, const char* what, std::string* best_spec,
+                                    float* best_ms_out) {
+    // Time the top candidates of one direct-correlation problem (and, when asked,
+    // the prebuilt default kernel) on zero-filled buffers; keep the fastest.
+    std::vector<DirectTile> ranked = direct_ranked(pr, smem_cap, dev.sm_count, threads, max_block);
+    std::vector<std::string> specs;
+    for (auto& t : ranked) {
+        if ((int)specs.size() >= topk) break;
+        specs.push_back(direct_tile_spec(t));
+    }
+    if (specs.empty() && !include_default)
+        return set_error(FBCORR_ERR_UNSUPPORTED, "no %s candidate fits", what);
+    {
+        // compile every candidate in parallel before timing them one by one
+        std::vector<std::string> srcs;
+        for (const auto& sp : specs) {
+            DirectTile t;
+            if (parse_direct_spec(sp, &t)) srcs.push_back(direct_kernel_source(pr, t, kname_for("fbc_direct", pr, t)));
+        }
+        rtcg_precompile(srcs);
+    }
+    if (include_default) specs.push_back("default");
+    const size_t xb = (size_t)pr.in_h * pr.in_w * pr.c * 4;
+    const size_t wb = (size_t)pr.nf * pr.fh * pr.fw * pr.c * 4;
+    const size_t yb = (size_t)pr.out_h * pr.out_w * pr.nf * 4;
+    float *x = nullptr, *w = nullptr, *y = nullptr, *m = nullptr;
+    if (cudaMalloc(&x, xb) != cudaSuccess || cudaMalloc(&w, wb) != cudaSuccess ||
+        cudaMalloc(&y, yb) != cudaSuccess || (pr.mask && cudaMalloc(&m, xb) != cudaSuccess)) {
+        cudaFree(x); cudaFree(w); cudaFree(y); cudaFree(m);
+        cudaGetLastError();
+        return set_error(FBCORR_ERR_OOM, "autotune buffers");
+    }
+    cudaMemsetAsync(x, 0, xb, s);
+    cudaMemsetAsync(w, 0, wb, s);
+    if (m) cudaMemsetAsync(m, 0, xb, s);
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best_ms = 1e30f;
+    best_spec->clear();
+    fbcorr_status_t status = FBCORR_OK;
+    for (const auto& sp : specs) {
+        Kernel k;
+        DirectTile t;
+        const bool dflt = sp == "default";
+        if (!dflt && (!parse_direct_spec(sp, &t) || build_direct(pr, t, &k) != FBCORR_OK)) continue;
+        auto run = [&]() {
+            return dflt ? run_default(pr, x, m, w, y, 0.f, 1.f, s)
+                        : run_direct(k, pr, t, x, m, w, y, 0.f, 1.f, s);
+        };
+        std::vector<float> ms_list;
+        bool ok = true;
+        for (int r = 0; r < 2 && ok; ++r) ok = run() == FBCORR_OK;
+        for (int r = 0; r < 7 && ok; ++r) {
+            cudaEventRecord(e0, s);
+            ok = run() == FBCORR_OK;
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) ok = false;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms_list.push_back(ms);
+        }
+        if (!ok) {
+            status = set_error(FBCORR_ERR_CUDA, "autotune run of %s (%s) failed", sp.c_str(), what);
+            break;
+        }
+        std::sort(ms_list.begin(), ms_list.end());
+        const float med = ms_list[ms_list.size() / 2];
+        logf("autotune %s %s: %.4f ms", what, sp.c_str(), med);
+        if (med < best_ms) {
+            best_ms = med;
+            *best_spec = sp;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(x); cudaFree(w); cudaFree(y); cudaFree(m);
+    if (status != FBCORR_OK) return status;
+    if (best_spec->empty()) return set_error(FBCORR_ERR_INTERNAL, "no %s variant ran", what);
+    if (best_ms_out) *best_ms_out = best_ms;
+    return FBCORR_OK;
+}
+
 }  // namespace fbc

@@ -80,6 +80,26 @@ def workload_paper_row1_clamp(seed: int = 2) -> Workload:
     return Workload("fp32clamp_256x256x8_64x9x9x8", x, w, clamp=(0.0, 1.0))
 
 
+# The four input / filter-bank shapes of the paper's Table "Performance of RTCG
+# auto-tuning on 3D filter-bank convolutions" (Sec. 6.2): (H, W, D), (N, f, f, D).
+PAPER_TABLE_SHAPES = (
+    ((256, 256, 8), (64, 9, 9, 8)),
+    ((512, 512, 4), (32, 13, 13, 4)),
+    ((1024, 1024, 8), (16, 5, 5, 8)),
+    ((2048, 2048, 4), (4, 8, 8, 4)),
+)
+
+
+def workload_paper_table(row: int, seed: int = 10) -> Workload:
+    """Row `row` (0..3) of the paper's table shapes, with the recipe of the
+    small workloads: U[0,1) input, zero-mean unit-norm N(0,1) filters."""
+    (H, W, D), (N, fh, fw, _) = PAPER_TABLE_SHAPES[row]
+    rng = np.random.default_rng(seed + row)
+    x = uniform(rng, (H, W, D))
+    w = zero_mean_unit_norm_bank(rng, N, fh, fw, D)
+    return Workload(f"paper_table_{H}x{W}x{D}_{N}x{fh}x{fw}x{D}", x, w)
+
+
 def workload_precision(seed: int = 3) -> Workload:
     """512x512x32 U[-1,1) input, 256 filters 5x5x32 drawn N(0, variance 1/800)."""
     rng = np.random.default_rng(seed)

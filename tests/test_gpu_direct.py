@@ -183,3 +183,28 @@ def test_ragged_channel_chunks(D, cc):
     wl = inputs.random_case(510 + D, 41, 70, D, 12, 3, 5)
     y, p = _run(torch, wl.x, wl.w, spec=f"direct:tr=4,tf=4,wr=2,wf=2,cc={cc}")
     assert normwise_rel(y, oracle.fwd(wl.x, wl.w)) <= TOL_F32
+
+
+@pytest.mark.parametrize("row", [1, 2, 3])
+def test_paper_table_shapes_sampled(row):
+    """The paper's other table shapes (512x512x4 / 32x13x13x4, 1024x1024x8 /
+    16x5x5x8, 2048x2048x4 / 4x8x8x4): first, middle and last output rows and
+    random points against the oracle, with the default and the heuristic tile."""
+    torch = torch_cuda()
+    from paper_0911_3456_gb300.api import Plan
+    wl = inputs.workload_paper_table(row)
+    p = Plan(wl.x.shape, wl.w.shape)
+    x, w = dev(wl.x, torch), dev(wl.w, torch)
+    Ho, Wo, N = p.out_shape
+    fh = wl.w.shape[1]
+    rng = np.random.default_rng(row)
+    idx = np.stack([rng.integers(0, Ho, 2000), rng.integers(0, Wo, 2000), rng.integers(0, N, 2000)], 1)
+    ref_pts = oracle.fwd_points(wl.x, wl.w, idx)
+    for spec in (None, "default"):
+        if spec:
+            p.set_variant(spec)
+        y = host(p.forward(x, w))
+        for r in (0, Ho // 2, Ho - 1):
+            ref = oracle.fwd(wl.x[r:r + fh], wl.w)[0]
+            assert np.abs(y[r] - ref).max() <= TOL_F32 * np.abs(ref).max(), (spec, r)
+        assert np.abs(y[tuple(idx.T)] - ref_pts).max() <= TOL_F32 * np.abs(ref_pts).max(), spec
