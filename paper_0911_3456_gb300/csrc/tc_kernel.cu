@@ -47,7 +47,8 @@ namespace fbc {
 namespace {
 
 constexpr int kEpiWarps = 4;      // one epilogue warp per TMEM lane quarter (4 or 8)
-constexpr int kThreads = 64 + 32 * kEpiWarps;
+constexpr int kConvWarps = 2;     // FP32 -> BF16 converters of the fused mode
+constexpr int kThreads = 64 + 32 * kEpiWarps + 32 * kConvWarps;
 constexpr int kTileM = 128;
 constexpr int kAccCols = 256;     // TMEM columns reserved per accumulator
 constexpr int kTmemCols = 512;
@@ -78,6 +79,13 @@ struct TcParams {
     int epi;
     float lo, hi;
     int drop_b;           // fault injection: B load index whose copy is skipped (-1: none)
+    // fused conversion of x (fuse = 1): raw FP32 slab rows are staged in nr slots
+    // and turned into the BF16 hi / lo A slots by the converter warps
+    const float* xraw;    // x itself [H*W][D]
+    long long npix;       // H*W
+    int D, fuse, nr;
+    uint32_t raw_slot, raw_off;
+    int alook;            // rows by which the A side runs ahead of the B stages (0 or 1)
 };
 
 // ---------------------------------------------------------------- PTX wrappers
@@ -197,6 +205,18 @@ __device__ __noinline__ void wait_drain(uint32_t bar, uint32_t parity, const TcP
         if (globaltimer() - t0 > P.wait_ns) return;
 }
 
+// hi = bf16_rn(v), lo = bf16_rn(v - hi) for 8 values; v - hi is exact in FP32.
+__device__ __forceinline__ void split8(const float (&v)[8], uint4* hi_out, uint4* lo_out, int split) {
+    __nv_bfloat16 h[8], l[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        h[k] = __float2bfloat16_rn(v[k]);
+        l[k] = __float2bfloat16_rn(v[k] - __bfloat162float(h[k]));
+    }
+    *hi_out = *reinterpret_cast<const uint4*>(h);
+    if (split) *lo_out = *reinterpret_cast<const uint4*>(l);
+}
+
 // All MMAs of one filter tap: K = 16 per instruction over the NC/2 pairs of
 // chunk planes; split mode adds hi*lo and lo*hi before hi*hi.
 template <int NC, int SPLIT>
@@ -244,11 +264,17 @@ __global__ void __launch_bounds__(kThreads, 1) fbc_tc_corr(const __grid_constant
     const uint32_t acc_full0 = b_empty0 + 8u * P.nb;
     const uint32_t acc_empty0 = acc_full0 + 16u;
     const uint32_t drain_bar = acc_empty0 + 16u;
+    const uint32_t raw_full0 = drain_bar + 8u;        // fused mode only: raw_full[nr] raw_empty[nr]
+    const uint32_t raw_empty0 = raw_full0 + 8u * P.nr;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < P.na; ++s) {
-            mbar_init(a_full0 + 8u * s, 1);
+            mbar_init(a_full0 + 8u * s, P.fuse ? kConvWarps : 1);
             mbar_init(a_empty0 + 8u * s, 1);
+        }
+        for (int s = 0; s < P.nr; ++s) {
+            mbar_init(raw_full0 + 8u * s, 1);
+            mbar_init(raw_empty0 + 8u * s, kConvWarps);
         }
         for (int s = 0; s < P.nb; ++s) {
             mbar_init(b_full0 + 8u * s, 1);
@@ -282,54 +308,80 @@ __global__ void __launch_bounds__(kThreads, 1) fbc_tc_corr(const __grid_constant
     if (warp == 0) {
         // ------------------------------------------------------------ producer
         if (lane == 0) {
-            uint32_t a_it = 0, b_it = 0;
-            int as = 0, bs = 0;
-            uint32_t aph = 0, bph = 0;
+            uint32_t a_it = 0, b_it = 0, r_it = 0;
+            int as = 0, bs = 0, rs = 0;
+            uint32_t aph = 0, bph = 0, rph = 0;
             bool ok = true;
             const uint32_t a_copy = (uint32_t)(kTileM + P.fw - 1) * 16u;
-            const long long gplane = P.npix_pad * 16;          // bytes per global x chunk plane
             const long long tap_bytes = (long long)NC * P.nt * 16;
-            for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
-                const int mt = tile % P.mtiles;
-                const int nti = tile / P.mtiles;
-                const uint8_t* xrow_hi = P.xhi + (long long)mt * kTileM * 16;
-                const uint8_t* xrow_lo = P.xlo + (long long)mt * kTileM * 16;
-                const long long woff0 = (long long)nti * P.fh * P.fw * tap_bytes;
-                const uint8_t* wtap_hi = P.whi + woff0;
-                const uint8_t* wtap_lo = P.wlo + woff0;
-                for (int i = 0; i < P.fh && ok; ++i) {
-                    if (!(ok = wait_bar(a_empty0 + 8u * as, aph ^ 1, P, abort_flag, kErrWaitEmpty))) break;
+            // The rows of this CTA's tiles in order: row r = (tile k, filter row i).
+            // The A side of row r (+ alook) is issued before the B stages of row r,
+            // so a slab (or, fused, a raw row and its conversion) is in flight while
+            // the MMAs of the previous row run.
+            const int my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+            const int R = my_tiles * P.fh;
+            auto issue_a = [&](int r) -> bool {
+                const int tile = blockIdx.x + (r / P.fh) * gridDim.x;
+                const int i = r % P.fh;
+                const long long p0 = (long long)(tile % P.mtiles) * kTileM + (long long)i * P.W;
+                if (P.fuse) {
+                    // raw FP32 pixels [p0, p0 + 128 + fw - 1); the part past the end of
+                    // x is zero-filled by the converters
+                    if (!wait_bar(raw_empty0 + 8u * rs, rph ^ 1, P, abort_flag, kErrWaitEmpty)) return false;
+                    const uint32_t rfull = raw_full0 + 8u * rs;
+                    long long valid = P.npix - p0;
+                    valid = valid < 0 ? 0 : (valid > kTileM + P.fw - 1 ? kTileM + P.fw - 1 : valid);
+                    const uint32_t bytes = (uint32_t)(valid * P.D * 4);
+                    mbar_expect_tx(rfull, bytes);
+                    if (bytes) bulk_g2s(sbase + P.raw_off + rs * P.raw_slot, P.xraw + p0 * P.D, bytes, rfull);
+                    ++r_it;
+                    if (++rs == P.nr) { rs = 0; rph ^= 1; }
+                } else {
+                    if (!wait_bar(a_empty0 + 8u * as, aph ^ 1, P, abort_flag, kErrWaitEmpty)) return false;
                     const uint32_t afull = a_full0 + 8u * as;
                     mbar_expect_tx(afull, P.a_tx);
                     const uint32_t dst = sbase + P.a_off + as * P.a_slot;
 #pragma unroll
                     for (int c = 0; c < NC; ++c) {
-                        bulk_g2s(dst + c * plane, xrow_hi + c * gplane, a_copy, afull);
-                        if (SPLIT) bulk_g2s(dst + a_half + c * plane, xrow_lo + c * gplane, a_copy, afull);
+                        const long long src = (c * P.npix_pad + p0) * 16;
+                        bulk_g2s(dst + c * plane, P.xhi + src, a_copy, afull);
+                        if (SPLIT) bulk_g2s(dst + a_half + c * plane, P.xlo + src, a_copy, afull);
                     }
-                    xrow_hi += (long long)P.W * 16;
-                    xrow_lo += (long long)P.W * 16;
                     ++a_it;
                     if (++as == P.na) { as = 0; aph ^= 1; }
-                    for (int j0 = 0; j0 < P.fw; j0 += P.bt) {
-                        // taps j0 .. j0+tcnt-1 of this filter row are contiguous in the
-                        // operand layout: one copy per half for the whole stage
-                        const int tcnt = min(P.bt, P.fw - j0);
-                        if (!(ok = wait_bar(b_empty0 + 8u * bs, bph ^ 1, P, abort_flag, kErrWaitEmpty))) break;
-                        const uint32_t bfull = b_full0 + 8u * bs;
-                        const uint32_t bytes = (uint32_t)tcnt * b_half;
-                        mbar_expect_tx(bfull, SPLIT ? 2u * bytes : bytes);
-                        if ((int)b_it != P.drop_b) {
-                            const uint32_t bdst = sbase + P.b_off + bs * P.b_stage;
-                            bulk_g2s(bdst, wtap_hi, bytes, bfull);
-                            if (SPLIT) bulk_g2s(bdst + (uint32_t)P.bt * b_half, wtap_lo, bytes, bfull);
-                        }
-                        wtap_hi += tcnt * tap_bytes;
-                        wtap_lo += tcnt * tap_bytes;
-                        ++b_it;
-                        if (++bs == P.nb) { bs = 0; bph ^= 1; }
-                    }
                 }
+                return true;
+            };
+            auto issue_b_row = [&](int r) -> bool {
+                const int tile = blockIdx.x + (r / P.fh) * gridDim.x;
+                const int i = r % P.fh;
+                const long long woff = (((long long)(tile / P.mtiles) * P.fh + i) * P.fw) * tap_bytes;
+                const uint8_t* wtap_hi = P.whi + woff;
+                const uint8_t* wtap_lo = P.wlo + woff;
+                for (int j0 = 0; j0 < P.fw; j0 += P.bt) {
+                    // taps j0 .. j0+tcnt-1 of this filter row are contiguous in the
+                    // operand layout: one copy per half for the whole stage
+                    const int tcnt = min(P.bt, P.fw - j0);
+                    if (!wait_bar(b_empty0 + 8u * bs, bph ^ 1, P, abort_flag, kErrWaitEmpty)) return false;
+                    const uint32_t bfull = b_full0 + 8u * bs;
+                    const uint32_t bytes = (uint32_t)tcnt * b_half;
+                    mbar_expect_tx(bfull, SPLIT ? 2u * bytes : bytes);
+                    if ((int)b_it != P.drop_b) {
+                        const uint32_t bdst = sbase + P.b_off + bs * P.b_stage;
+                        bulk_g2s(bdst, wtap_hi, bytes, bfull);
+                        if (SPLIT) bulk_g2s(bdst + (uint32_t)P.bt * b_half, wtap_lo, bytes, bfull);
+                    }
+                    wtap_hi += tcnt * tap_bytes;
+                    wtap_lo += tcnt * tap_bytes;
+                    ++b_it;
+                    if (++bs == P.nb) { bs = 0; bph ^= 1; }
+                }
+                return true;
+            };
+            int next_a = 0;
+            for (int r = 0; r < R && ok; ++r) {
+                while (ok && next_a < R && next_a <= r + P.alook) ok = issue_a(next_a++);
+                if (ok) ok = issue_b_row(r);
             }
             if (!ok) {
                 // wait (bounded) for the copies still in flight into each ring slot
@@ -337,6 +389,8 @@ __global__ void __launch_bounds__(kThreads, 1) fbc_tc_corr(const __grid_constant
                 for (uint32_t k = a0; k < a_it; ++k) wait_drain(a_full0 + 8u * (k % P.na), (k / P.na) & 1, P);
                 const uint32_t b0 = b_it > (uint32_t)P.nb ? b_it - P.nb : 0;
                 for (uint32_t k = b0; k < b_it; ++k) wait_drain(b_full0 + 8u * (k % P.nb), (k / P.nb) & 1, P);
+                const uint32_t r0 = r_it > (uint32_t)P.nr ? r_it - P.nr : 0;
+                for (uint32_t k = r0; k < r_it; ++k) wait_drain(raw_full0 + 8u * (k % P.nr), (k / P.nr) & 1, P);
             }
         }
     } else if (warp == 1) {
@@ -409,6 +463,59 @@ __global__ void __launch_bounds__(kThreads, 1) fbc_tc_corr(const __grid_constant
             if (!ok && issued) {
                 umma_commit(drain_bar);
                 wait_drain(drain_bar, 0, P);
+            }
+        }
+    } else if (warp >= 2 + kEpiWarps) {
+        // ------------------------------------------------------------ converters (fused mode)
+        // FP32 slab row -> BF16 hi (and lo) chunk planes of an A slot.  Generic-proxy
+        // shared-memory writes are made visible to the tensor core's async proxy by
+        // fence.proxy.async before the arrival on a_full.
+        if (P.fuse) {
+            const int ct = threadIdx.x - (2 + kEpiWarps) * 32;
+            constexpr int NCT = kConvWarps * 32;
+            const int L = kTileM + P.fw - 1;
+            int as = 0, rs = 0;
+            uint32_t aph = 0, rph = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+                const int mt = tile % P.mtiles;
+                for (int i = 0; i < P.fh && ok; ++i) {
+                    if (!(ok = wait_bar(raw_full0 + 8u * rs, rph, P, abort_flag, kErrWaitA))) break;
+                    if (!(ok = wait_bar(a_empty0 + 8u * as, aph ^ 1, P, abort_flag, kErrWaitEmpty))) break;
+                    const long long p0 = (long long)mt * kTileM + (long long)i * P.W;
+                    long long vl = P.npix - p0;
+                    const int valid = (int)(vl < 0 ? 0 : (vl > L ? L : vl));
+                    const float* raw = reinterpret_cast<const float*>(smem + P.raw_off + rs * P.raw_slot);
+                    uint8_t* dst = smem + P.a_off + as * P.a_slot;
+                    const bool vec = (P.D & 7) == 0;
+                    for (int item = ct; item < L * NC; item += NCT) {
+                        const int px = item / NC;
+                        const int c = item - px * NC;
+                        float v[8];
+                        if (px < valid && vec && c * 8 + 8 <= P.D) {
+                            const float4* r4 = reinterpret_cast<const float4*>(raw + px * P.D + c * 8);
+                            const float4 a = r4[0], b = r4[1];
+                            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+                            v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+                        } else {
+#pragma unroll
+                            for (int k = 0; k < 8; ++k) {
+                                const int d = c * 8 + k;
+                                v[k] = (px < valid && d < P.D) ? raw[px * P.D + d] : 0.f;
+                            }
+                        }
+                        split8(v, reinterpret_cast<uint4*>(dst + c * plane + px * 16),
+                               reinterpret_cast<uint4*>(dst + a_half + c * plane + px * 16), SPLIT);
+                    }
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    __syncwarp();
+                    if (lane == 0) {
+                        mbar_arrive(a_full0 + 8u * as);
+                        mbar_arrive(raw_empty0 + 8u * rs);
+                    }
+                    if (++as == P.na) { as = 0; aph ^= 1; }
+                    if (++rs == P.nr) { rs = 0; rph ^= 1; }
+                }
             }
         }
     } else {
@@ -503,16 +610,6 @@ struct SplitParams {
     long long xblocks;
 };
 
-__device__ __forceinline__ void split8(const float (&v)[8], uint4* hi_out, uint4* lo_out, int split) {
-    __nv_bfloat16 h[8], l[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        h[k] = __float2bfloat16_rn(v[k]);
-        l[k] = __float2bfloat16_rn(v[k] - __bfloat162float(h[k]));
-    }
-    *hi_out = *reinterpret_cast<const uint4*>(h);
-    if (split) *lo_out = *reinterpret_cast<const uint4*>(l);
-}
 
 __global__ void __launch_bounds__(256) fbc_tc_split(const __grid_constant__ SplitParams S) {
     if ((long long)blockIdx.x < S.xblocks) {
@@ -603,6 +700,7 @@ struct TcConfig {
     int na = 2, nb = 5, ntmax = 256;   // A slots, B stages, widest filter tile
     int bt = 1;                        // filter taps per B stage
     int lf = 0;                        // issuing-loop form (see fbc_tc_corr)
+    int fuse = 0;                      // convert x inside the kernel (no x pre-pass)
 };
 
 struct TcPlan {
@@ -644,9 +742,13 @@ bool tc_layout(TcPlan* p, const TcConfig& c, bool commit) {
     const int halves = p->split ? 2 : 1;
     const uint32_t a_slot = (uint32_t)align_up((size_t)nc * lp * 16 * halves, 128);
     if (c.bt < 1 || c.bt > p->fw) return false;
+    if (c.fuse && (p->D % 4) != 0) return false;   // raw rows are copied in 16-byte units
+    const int L = kTileM + p->fw - 1;
+    const int nr = c.fuse ? 2 : 0;
+    const uint32_t raw_slot = c.fuse ? (uint32_t)align_up((size_t)L * p->D * 4, 128) : 0;
     const uint32_t b_stage = (uint32_t)align_up((size_t)c.bt * nc * nt * 16 * halves, 128);
     if (c.na < 2 || c.nb < 2) return false;
-    const size_t need = (size_t)c.na * a_slot + (size_t)c.nb * b_stage + kStgBytes + 512;
+    const size_t need = (size_t)c.na * a_slot + (size_t)c.nb * b_stage + kStgBytes + (size_t)nr * raw_slot + 512;
     if (need > kSmemMax) return false;
     if (!commit) return true;
     p->cfg = c;
@@ -662,7 +764,16 @@ bool tc_layout(TcPlan* p, const TcConfig& c, bool commit) {
     k.a_off = 0;
     k.b_off = (uint32_t)(c.na * a_slot);
     k.stg_off = (uint32_t)(k.b_off + c.nb * b_stage);
-    k.bar_off = (uint32_t)(k.stg_off + kStgBytes);
+    k.raw_off = (uint32_t)(k.stg_off + kStgBytes);
+    k.raw_slot = raw_slot;
+    k.nr = nr;
+    k.fuse = c.fuse;
+    k.npix = (long long)p->H * p->W;
+    k.D = p->D;
+    // A-side look-ahead needs a free slot beyond the one the MMAs of the previous
+    // row still read: the raw ring (fused), or three A slots
+    k.alook = (c.fuse || c.na >= 3) ? 1 : 0;
+    k.bar_off = (uint32_t)(k.raw_off + (size_t)nr * raw_slot);
     k.epi = p->epi; k.lo = p->lo; k.hi = p->hi;
     k.wait_ns = p->wait_ns;
     k.drop_b = p->drop_b;
@@ -684,6 +795,7 @@ bool tc_layout(TcPlan* p, const TcConfig& c, bool commit) {
     sp.split = p->split;
     sp.xblocks = (k.npix_pad + 255) / 256;
     const long long wblocks = ((long long)ntn * p->fh * p->fw * nc * nt + 255) / 256;
+    if (c.fuse) sp.xblocks = 0;   // x is converted inside the correlation kernel
     p->split_blocks = (int)(sp.xblocks + wblocks);
     p->grid = std::min(mtiles * ntn, std::max(1, p->sm_count));
     p->kfn = tc_kernel_for(nc, p->split, c.lf);
@@ -704,26 +816,28 @@ std::vector<TcConfig> tc_candidate_configs(TcPlan* p) {
     const int widths[] = {256, 128};
     for (int ntmax : widths) {
         if (ntmax == 128 && p->N <= 128) continue;
-        for (int bt = std::min(p->fw, 5); bt >= 1; --bt)
-            for (int na = 2; na <= 3; ++na) {
-                int best = 0;
-                for (int nb = 2; nb <= 10; ++nb)
-                    if (tc_layout(p, TcConfig{na, nb, ntmax, bt, 0}, false)) best = nb;
-                if (!best) continue;
-                out.push_back(TcConfig{na, best, ntmax, bt, 0});
-                if (bt > 1) out.push_back(TcConfig{na, best, ntmax, bt, 1});
-            }
+        for (int fuse = (p->D % 4 == 0) ? 1 : 0; fuse >= 0; --fuse)
+            for (int bt = std::min(p->fw, 5); bt >= 1; --bt)
+                for (int na = 2; na <= 3; ++na) {
+                    int best = 0;
+                    for (int nb = 2; nb <= 10; ++nb)
+                        if (tc_layout(p, TcConfig{na, nb, ntmax, bt, 0, fuse}, false)) best = nb;
+                    if (!best) continue;
+                    out.push_back(TcConfig{na, best, ntmax, bt, 0, fuse});
+                    if (bt > 1) out.push_back(TcConfig{na, best, ntmax, bt, 1, fuse});
+                }
     }
     return out;
 }
 
 bool parse_tc_spec(const std::string& s, TcConfig* c) {
     TcConfig t;
-    const int n = sscanf(s.c_str(), "tcgen05:na=%d,nb=%d,nt=%d,bt=%d,lf=%d", &t.na, &t.nb, &t.ntmax,
-                         &t.bt, &t.lf);
+    const int n = sscanf(s.c_str(), "tcgen05:na=%d,nb=%d,nt=%d,bt=%d,lf=%d,fz=%d", &t.na, &t.nb,
+                         &t.ntmax, &t.bt, &t.lf, &t.fuse);
     if (n == 3) t.bt = 1;
     if (n <= 4) t.lf = 0;
-    if (n < 3 || t.lf < 0 || t.lf > 1) return false;
+    if (n <= 5) t.fuse = 0;
+    if (n < 3 || t.lf < 0 || t.lf > 1 || t.fuse < 0 || t.fuse > 1) return false;
     if (t.ntmax != 256 && t.ntmax != 128 && t.ntmax != 64) return false;
     *c = t;
     return true;
@@ -733,8 +847,8 @@ bool parse_tc_spec(const std::string& s, TcConfig* c) {
 
 std::string tc_spec(const TcPlan* p) {
     char b[96];
-    snprintf(b, sizeof b, "tcgen05:na=%d,nb=%d,nt=%d,bt=%d,lf=%d", p->cfg.na, p->cfg.nb, p->cfg.ntmax,
-             p->cfg.bt, p->cfg.lf);
+    snprintf(b, sizeof b, "tcgen05:na=%d,nb=%d,nt=%d,bt=%d,lf=%d,fz=%d", p->cfg.na, p->cfg.nb,
+             p->cfg.ntmax, p->cfg.bt, p->cfg.lf, p->cfg.fuse);
     return b;
 }
 
@@ -742,7 +856,8 @@ std::vector<std::string> tc_candidates(TcPlan* p) {
     std::vector<std::string> out;
     for (const auto& c : tc_candidate_configs(p)) {
         char b[96];
-        snprintf(b, sizeof b, "tcgen05:na=%d,nb=%d,nt=%d,bt=%d,lf=%d", c.na, c.nb, c.ntmax, c.bt, c.lf);
+        snprintf(b, sizeof b, "tcgen05:na=%d,nb=%d,nt=%d,bt=%d,lf=%d,fz=%d", c.na, c.nb, c.ntmax, c.bt,
+                 c.lf, c.fuse);
         out.push_back(b);
     }
     return out;
@@ -830,6 +945,7 @@ fbcorr_status_t tc_forward(TcPlan* p, const float* x, const float* w, float* y, 
     kp.wlo = sp.wlo;
     kp.y = y;
     kp.err = err_word;
+    kp.xraw = x;
     if (ev_start) FBC_CUDA(cudaEventRecord(ev_start, s));
     void* args[] = {&kp};
     FBC_CUDA(cudaLaunchKernel((const void*)p->kfn, dim3(p->grid), dim3(kThreads), args, p->smem, s));

@@ -181,7 +181,8 @@ def test_every_tensor_core_configuration_matches(mode):
             for nt in (256, 128):
                 for bt in (1, 2, 3, 5):
                     for lf in (0, 1):
-                        specs.add(f"tcgen05:na={na},nb={nb},nt={nt},bt={bt},lf={lf}")
+                        for fz in (0, 1):
+                            specs.add(f"tcgen05:na={na},nb={nb},nt={nt},bt={bt},lf={lf},fz={fz}")
     ran = 0
     for sp in sorted(specs):
         try:
@@ -192,4 +193,23 @@ def test_every_tensor_core_configuration_matches(mode):
         y = host(p.forward(x, w))
         assert np.array_equal(y, ref), sp
         ran += 1
-    assert ran >= 16
+    assert ran >= 32
+
+
+@pytest.mark.parametrize("mode", ["bf16", "bf16x3"])
+@pytest.mark.parametrize("shape", [(20, 150, 16, 16, 3, 3), (37, 45, 4, 20, 4, 2), (18, 260, 48, 40, 7, 7),
+                                   (9, 9, 12, 3, 9, 9)], ids=lambda s: "x".join(map(str, s)))
+def test_fused_conversion_matches_prepass(mode, shape):
+    """x converted inside the kernel (fz=1) and by the pre-pass (fz=0) give the
+    same bits, including the zero-filled tail past the end of the image."""
+    torch = torch_cuda()
+    from paper_0911_3456_gb300.api import Plan
+    wl = inputs.random_case(1800, *shape)
+    p = Plan(wl.x.shape, wl.w.shape, mode)
+    x, w = dev(wl.x, torch), dev(wl.w, torch)
+    outs = {}
+    for fz in (0, 1):
+        p.set_variant(f"tcgen05:na=2,nb=2,nt=256,bt=1,lf=0,fz={fz}")
+        outs[fz] = host(p.forward(x, w))
+    assert np.array_equal(outs[0], outs[1])
+    assert_within_bound(outs[1], wl.x, wl.w, mode)
