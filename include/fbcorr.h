@@ -196,9 +196,12 @@ const char* fbcorr_last_error(void);
 const char* fbcorr_version(void);
 
 /* Generate and compile (NVRTC, sm_103a) -- without loading or running -- the
- * forward, dL/dx and dL/dw kernels that a plan of this shape would use, with
- * the forward tile `spec` ("heuristic" or a "direct:..." spec).  Needs no GPU.
- * On failure the NVRTC log is written into log (NUL-terminated, cap bytes). */
+ * forward, dL/dx and dL/dw kernels that an FP32 plan of this shape would use,
+ * with the forward tile `spec` ("heuristic" or a "direct:..." spec); or, for a
+ * "tcgen05:na=..,nb=..,nt=..,bt=..,ew=..,fz=.." spec, the tensor-core kernel
+ * that spec generates for this depth and filter width, in both BF16 and split
+ * BF16 form.  Needs no GPU.  On failure the NVRTC log (or the reason the spec
+ * does not fit) is written into log (NUL-terminated, cap bytes). */
 fbcorr_status_t fbcorr_rtcg_check(const int64_t in_shape[3], const int64_t filt_shape[4],
                                   fbcorr_epilogue_t epilogue, const char* spec, char* log,
                                   size_t cap);

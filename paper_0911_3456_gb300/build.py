@@ -1,6 +1,7 @@
 """Build libfbcorr.so in-tree with nvcc for sm_103a.
 
-Steps: embed rtcg_direct.cuh (the NVRTC kernel templates) as a string, compile
+Steps: embed rtcg_direct.cuh, tc_params.h and rtcg_tc.cuh (the NVRTC kernel
+templates) as strings, compile
 every csrc/*.cu translation unit in parallel, link one shared library that
 statically links the CUDA runtime and dynamically links NVRTC.  Usage:
 ``python -m paper_0911_3456_gb300.build`` or ``build()`` from Python.
@@ -36,12 +37,13 @@ def _cuda_home(nvcc: str) -> str:
 
 
 def _embed():
-    src = os.path.join(CSRC, "rtcg_direct.cuh")
     out = os.path.join(CSRC, "_embedded_src.inc")
-    text = open(src).read()
-    assert ')FBCSRC"' not in text
-    body = ('// generated by build.py from rtcg_direct.cuh -- do not edit\n'
-            'static const char kRtcgDirectSrc[] = R"FBCSRC(' + text + ')FBCSRC";\n')
+    body = "// generated by build.py from rtcg_direct.cuh, tc_params.h, rtcg_tc.cuh -- do not edit\n"
+    for fname, var in (("rtcg_direct.cuh", "kRtcgDirectSrc"), ("tc_params.h", "kRtcgTcParamsSrc"),
+                       ("rtcg_tc.cuh", "kRtcgTcSrc")):
+        text = open(os.path.join(CSRC, fname)).read()
+        assert ')FBCSRC"' not in text
+        body += "static const char " + var + '[] = R"FBCSRC(' + text + ')FBCSRC";\n'
     if not os.path.exists(out) or open(out).read() != body:
         with open(out, "w") as f:
             f.write(body)

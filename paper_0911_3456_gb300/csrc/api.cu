@@ -508,6 +508,20 @@ fbcorr_status_t fbcorr_autotune(fbcorr_plan_t p, fbcorr_stream_t stream) {
     return FBCORR_OK;
 }
 
+// Values in [-scale, scale) from an integer hash of the index (the "lowbias32"
+// mixer of C. Wellons' hash-prospector), for timing runs only.
+__global__ void fbc_fill_pattern(float* p, size_t n, float scale, unsigned seed) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        unsigned h = (unsigned)i ^ seed;
+        h ^= h >> 16;
+        h *= 0x7feb352du;
+        h ^= h >> 15;
+        h *= 0x846ca68bu;
+        h ^= h >> 16;
+        p[i] = scale * ((float)(h >> 8) * (2.0f / 16777216.0f) - 1.0f);
+    }
+}
+
 // Time every feasible tensor-core configuration (ring depths, filter-tile
 // width) and keep the fastest -- the same measured grid search as for the
 // generated FP32 kernels.
@@ -525,14 +539,17 @@ static fbcorr_status_t autotune_tc(fbcorr_plan_t p, fbcorr_stream_t stream) {
         cudaGetLastError();
         return set_error(FBCORR_ERR_OOM, "autotune buffers");
     }
-    cudaMemsetAsync(x, 0, xb, s);
-    cudaMemsetAsync(w, 0, wb, s);
+    // non-zero operands: the tensor cores draw (and the clocks follow) more power
+    // on real data than on zeros, so timings on zeros would favour the wrong spec
+    fbc_fill_pattern<<<256, 256, 0, s>>>(x, xb / 4, 1.0f, 0x1234u);
+    fbc_fill_pattern<<<256, 256, 0, s>>>(w, wb / 4, 0.05f, 0x5678u);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     std::string best;
     float best_ms = 1e30f;
     fbcorr_status_t status = FBCORR_OK;
+    tc_precompile(p->tc, specs);   // the generated kernels of all candidates, on host threads
     for (const auto& sp : specs) {
         if (tc_set_spec(p->tc, sp) != FBCORR_OK) continue;
         std::vector<float> ms;
@@ -649,10 +666,17 @@ fbcorr_status_t fbcorr_rtcg_check(const int64_t in_shape[3], const int64_t filt_
     tmp.Ho = tmp.H - tmp.fh + 1;
     tmp.Wo = tmp.W - tmp.fw + 1;
     tmp.epi = epilogue;
+    const std::string sp = spec ? spec : "heuristic";
+    if (sp.compare(0, 8, "tcgen05:") == 0) {
+        // the generated tensor-core kernel of this spec, BF16 and split BF16
+        std::string lg;
+        const fbcorr_status_t st = tc_rtcg_check((int)tmp.D, (int)tmp.fw, sp, &lg);
+        if (st != FBCORR_OK && log && cap) snprintf(log, cap, "%s", lg.empty() ? fbcorr_last_error() : lg.c_str());
+        return st;
+    }
     const size_t lim = 200 * 1024;
     const DirectProblem fp = fwd_problem(&tmp), bp = dx_problem(&tmp);
     DirectTile t;
-    const std::string sp = spec ? spec : "heuristic";
     if (sp == "heuristic")
         t = direct_heuristic(fp, lim, 148);
     else if (!parse_direct_spec(sp, &t))

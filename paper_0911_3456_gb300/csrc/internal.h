@@ -66,13 +66,19 @@ fbcorr_status_t rtcg_precompile(const std::vector<std::string>& sources);
 // Compile only (no GPU needed); returns the NVRTC log on failure.
 fbcorr_status_t rtcg_compile_only(const std::string& src, std::string* log);
 fbcorr_status_t launch(const Kernel& k, dim3 grid, void** args, cudaStream_t stream);
+// Launch with thread-block clusters of cluster_x CTAs along x (plain launch for 1).
+fbcorr_status_t launch_cluster(const Kernel& k, dim3 grid, int cluster_x, void** args, cudaStream_t stream);
+// How many clusters of cluster_x CTAs of `k` (k.threads, k.smem) can be resident at once.
+fbcorr_status_t kernel_max_clusters(const Kernel& k, int cluster_x, int* out);
 // CUDA-graph kernel nodes for NVRTC kernels (driver API under the hood).
 fbcorr_status_t graph_add_kernel(cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps,
                                  const Kernel& k, dim3 grid, void** args, cudaGraphNode_t* out);
 fbcorr_status_t graph_set_kernel(cudaGraphExec_t e, cudaGraphNode_t n, const Kernel& k, dim3 grid,
                                  void** args);
 fbcorr_status_t kernel_occupancy(const Kernel& k, int* blocks_per_sm);
-const char* rtcg_header_source();   // contents of rtcg_direct.cuh
+const char* rtcg_header_source();     // contents of rtcg_direct.cuh
+const char* rtcg_tc_params_source();  // contents of tc_params.h
+const char* rtcg_tc_source();         // contents of rtcg_tc.cuh
 
 // ---- variants ------------------------------------------------------------------
 enum class VarKind { Default = 0, Direct = 1, Tensor = 2 };
@@ -160,6 +166,10 @@ std::string tc_describe(const TcPlan* p);           // JSON object
 std::string tc_spec(const TcPlan* p);               // "tcgen05:na=..,nb=..,nt=.."
 std::vector<std::string> tc_candidates(TcPlan* p);  // feasible specs, default first
 fbcorr_status_t tc_set_spec(TcPlan* p, const std::string& spec);
+// Compile the generated kernels of `specs` on host threads into the cubin cache.
+fbcorr_status_t tc_precompile(TcPlan* p, const std::vector<std::string>& specs);
+// Compile-only check of the generated kernel of `spec` (BF16 and split) for depth D, width fw.
+fbcorr_status_t tc_rtcg_check(int D, int fw, const std::string& spec, std::string* log);
 
 // ---- argument validation (api.cu) -------------------------------------------------------
 fbcorr_status_t validate_shapes(const int64_t* in, const int64_t* fs, fbcorr_dtype_t dtype,

@@ -1,0 +1,600 @@
+// rtcg_tc.cuh -- the tensor-core correlation kernel, compiled at plan time by
+// NVRTC for sm_103a with the chunk-plane count NC, the split mode, the filter
+// width FW, the taps per B stage BT, the epilogue warp count EW and the fused
+// conversion switch FUSE baked in.  Embedded as a string into libfbcorr and
+// prefixed with tc_params.h; self-contained (no system headers).
+//
+// The correlation of Sec. 6.2 as an implicit GEMM: for every filter tap (i, j)
+//   Y[m, n] += sum_d X[m + i*W + j, d] * Wt[n, i, j, d]
+// where m = p*W + q runs over output pixels laid out with the INPUT width W
+// (columns q >= W' are computed and discarded).  With that layout the A operand
+// of every tap is a contiguous run of 128 input pixels, so one shared-memory
+// slab of 128+FW-1 pixels per filter row i serves all FW taps of that row:
+// tap j is the same slab started j pixels later.
+//
+// Why run-time generation: one thread issues every tcgen05.mma of a CTA, and a
+// 128x256x16 MMA lasts 128 tensor-core cycles, about three times what issuing
+// one costs.  Loop control, ring-index and descriptor arithmetic between MMAs
+// (runtime tap counts, stage boundaries) left the tensor core idle for a third
+// of the time; with FW and BT compile-time the MMA sequence of a filter row is
+// straight-line code (the paper's loop unrolling by RTCG, Sec. 3.2 and 6.2).
+//
+// Clusters (CS = 2 or 4): the CS CTAs of a cluster compute CS neighbouring
+// pixel tiles of the same filter tile in lockstep, so they read the same B
+// stages.  Each CTA copies 1/CS of every stage from global memory with a
+// multicast bulk copy into the same slot of all CS CTAs, and every MMA commit
+// that frees a slot arrives on that slot's barrier in all CS CTAs: the weights
+// cross the L2 -> SM fabric once per cluster instead of once per CTA, which at
+// one 128x256x16 MMA per 128 cycles would otherwise take 8-16 TB/s.
+//
+// Roles per CTA (persistent, one per SM):
+//   warp 0      producer: cp.async.bulk (1D TMA) of B slices of BT consecutive
+//               taps (and, unfused, of pre-split A slabs) into rings,
+//               mbarrier complete_tx;
+//   warp 1      allocates 512 TMEM columns, issues tcgen05.mma (M=128, N<=256,
+//               K=16, kind::f16 BF16, FP32 accumulate) into one of two
+//               accumulators; tcgen05.commit frees ring slots and hands
+//               finished accumulators to the epilogue;
+//   warps 2..   EW epilogue warps (two per TMEM lane quarter when EW = 8):
+//               tcgen05.ld 16x256b, optional clamp, streaming stores straight
+//               from registers (four lanes write 32 contiguous bytes of one
+//               output pixel); overlaps the MMAs of the next tile;
+//   last 4      (FUSE) converter warps: FP32 x rows read from global memory
+//               one row ahead, written as BF16 hi (and lo) chunk planes.
+// Operands use the no-swizzle K-major canonical layout: a core matrix is 8 rows
+// x 16 bytes, rows contiguous; LBO = byte stride between K-adjacent core
+// matrices (one chunk plane), SBO = 128 bytes between 8-row groups.
+//
+// Split BF16: v = hi + lo, hi = bf16_rn(v), lo = bf16_rn(v - hi); each K step
+// issues hi*lo + lo*hi, then hi*hi, into the same FP32 accumulator (the lo*lo
+// term, ~2^-16 relative, is dropped).
+//
+// Every mbarrier wait is bounded in time (%globaltimer); on expiry the kernel
+// records an error code in host-mapped memory, stops every role, waits (again
+// bounded) for its own copies and MMAs in flight, frees TMEM and returns.
+
+typedef unsigned int fbc_u32;
+typedef unsigned long long fbc_u64;
+typedef unsigned char fbc_u8;
+
+extern __shared__ __align__(1024) fbc_u8 fbc_tc_smem[];
+
+// ---------------------------------------------------------------- PTX wrappers
+__device__ __forceinline__ fbc_u32 fbc_smem_addr(const void* p) {
+    fbc_u32 r;
+    asm("{\n .reg .u64 t;\n cvta.to.shared.u64 t, %1;\n cvt.u32.u64 %0, t;\n}\n" : "=r"(r) : "l"(p));
+    return r;
+}
+
+__device__ __forceinline__ fbc_u64 fbc_globaltimer() {
+    fbc_u64 t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void fbc_mbar_init(fbc_u32 bar, fbc_u32 count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+
+__device__ __forceinline__ bool fbc_mbar_try_wait(fbc_u32 bar, fbc_u32 parity) {
+    fbc_u32 ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.b32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void fbc_mbar_arrive(fbc_u32 bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void fbc_mbar_expect_tx(fbc_u32 bar, fbc_u32 bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+// 1D bulk copy global -> shared, completion counted on `bar` (bytes % 16 == 0).
+__device__ __forceinline__ void fbc_bulk_g2s(fbc_u32 dst, const void* src, fbc_u32 bytes, fbc_u32 bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
+// The same copy into the same CTA-relative offset of every CTA in `mask`, with
+// complete_tx on the barrier at `bar`'s offset in each of them.
+__device__ __forceinline__ void fbc_bulk_g2s_mc(fbc_u32 dst, const void* src, fbc_u32 bytes, fbc_u32 bar,
+                                                unsigned short mask) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1], %2, [%3], %4;" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(bar), "h"(mask)
+        : "memory");
+}
+
+__device__ __forceinline__ fbc_u32 fbc_cluster_rank() {
+    fbc_u32 r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ void fbc_cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void fbc_tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fbc_tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// K-major, no-swizzle shared-memory matrix descriptor.
+__device__ __forceinline__ fbc_u64 fbc_smem_desc(fbc_u32 addr, fbc_u32 lbo, fbc_u32 sbo) {
+    return (fbc_u64)((addr & 0x3FFFFu) >> 4) | ((fbc_u64)(lbo >> 4) << 16) | ((fbc_u64)(sbo >> 4) << 32) |
+           (1ull << 46);
+}
+
+__device__ __forceinline__ void fbc_umma(fbc_u32 d_tmem, fbc_u64 a, fbc_u64 b, fbc_u32 idesc, fbc_u32 accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void fbc_umma_commit(fbc_u32 bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+// Arrive (when the MMAs issued so far complete) on the barrier at `bar`'s
+// offset in every CTA of `mask`.
+__device__ __forceinline__ void fbc_umma_commit_mc(fbc_u32 bar, unsigned short mask) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
+                 "h"(mask)
+                 : "memory");
+}
+
+// tcgen05.ld 16x256b.x8 -- 16 TMEM lanes x 64 columns: registers 4g, 4g+1 hold
+// columns 8g + 2*(lane%4) + {0,1} of lane lane/4, registers 4g+2, 4g+3 the same
+// columns of lane 8 + lane/4.
+// Issued without its wait: several loads can be in flight before one
+// fbc_tmem_ld_wait(); fbc_reg_fence() then orders every use of the registers
+// after that wait.
+__device__ __forceinline__ void fbc_tmem_ld16x256b_x8_async(fbc_u32 taddr, fbc_u32 (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.16x256b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+          "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+          "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void fbc_tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ void fbc_reg_fence(fbc_u32 (&r)[32]) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        asm volatile("" : "+r"(r[8 * q]), "+r"(r[8 * q + 1]), "+r"(r[8 * q + 2]), "+r"(r[8 * q + 3]),
+                     "+r"(r[8 * q + 4]), "+r"(r[8 * q + 5]), "+r"(r[8 * q + 6]), "+r"(r[8 * q + 7]));
+}
+
+// Streaming 8-byte store.
+__device__ __forceinline__ void fbc_st_cs_f2(float* p, float a, float b) {
+    asm volatile("st.global.cs.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(a), "f"(b) : "memory");
+}
+
+// Two FP32 values -> two BF16 (round to nearest even), packed low = a, high = b.
+__device__ __forceinline__ fbc_u32 fbc_pack_bf16x2(float a, float b) {
+    fbc_u32 r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(b), "f"(a));
+    return r;
+}
+
+// hi = bf16_rn(v), lo = bf16_rn(v - hi) for 8 values; v - hi is exact in FP32.
+template <int SPLIT>
+__device__ __forceinline__ void fbc_split8(const float (&v)[8], uint4* hi_out, uint4* lo_out) {
+    fbc_u32 h[4], l[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        h[k] = fbc_pack_bf16x2(v[2 * k], v[2 * k + 1]);
+        if (SPLIT) {
+            const float h0 = __uint_as_float(h[k] << 16);
+            const float h1 = __uint_as_float(h[k] & 0xFFFF0000u);
+            l[k] = fbc_pack_bf16x2(v[2 * k] - h0, v[2 * k + 1] - h1);
+        }
+    }
+    *hi_out = make_uint4(h[0], h[1], h[2], h[3]);
+    if (SPLIT) *lo_out = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// ---------------------------------------------------------------- bounded waits
+__device__ __noinline__ bool fbc_wait_slow(fbc_u32 bar, fbc_u32 parity, const FbcTcParams& P,
+                                           volatile int* abort_flag, int code) {
+    const fbc_u64 t0 = fbc_globaltimer();
+    for (;;) {
+#pragma unroll 1
+        for (int k = 0; k < 64; ++k)
+            if (fbc_mbar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (fbc_globaltimer() - t0 > P.wait_ns) {
+            *abort_flag = 1;
+            *(volatile int*)P.err = code;
+            __threadfence_system();
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ bool fbc_wait(fbc_u32 bar, fbc_u32 parity, const FbcTcParams& P,
+                                         volatile int* abort_flag, int code) {
+    if (fbc_mbar_try_wait(bar, parity)) return true;
+    return fbc_wait_slow(bar, parity, P, abort_flag, code);
+}
+
+// Drain wait after an abort: bounded, ignores the abort flag.
+__device__ __noinline__ void fbc_wait_drain(fbc_u32 bar, fbc_u32 parity, const FbcTcParams& P) {
+    const fbc_u64 t0 = fbc_globaltimer();
+    while (!fbc_mbar_try_wait(bar, parity))
+        if (fbc_globaltimer() - t0 > P.wait_ns) return;
+}
+
+// All MMAs of one filter tap: K = 16 per instruction over the NC/2 pairs of
+// chunk planes; split mode adds hi*lo and lo*hi before hi*hi.
+template <int NC, int SPLIT>
+__device__ __forceinline__ void fbc_issue_tap(fbc_u32 d_tmem, fbc_u64 ad, fbc_u64 bd, fbc_u64 ak, fbc_u64 bk,
+                                              fbc_u64 alo, fbc_u64 blo, fbc_u32 idesc, fbc_u32& accumulate) {
+#pragma unroll
+    for (int kk = 0; kk < NC / 2; ++kk) {
+        const fbc_u64 a = ad + kk * ak;
+        const fbc_u64 b = bd + kk * bk;
+        if (SPLIT) {
+            fbc_umma(d_tmem, a, b + blo, idesc, accumulate);
+            fbc_umma(d_tmem, a + alo, b, idesc, 1);
+            fbc_umma(d_tmem, a, b, idesc, 1);
+        } else {
+            fbc_umma(d_tmem, a, b, idesc, accumulate);
+        }
+        accumulate = 1;
+    }
+}
+
+// ---------------------------------------------------------------- the kernel body
+template <int NC, int SPLIT, int FW, int BT, int EW, int FUSE, int CS>
+__device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
+    constexpr int NST = (FW + BT - 1) / BT;          // B stages per filter row
+    constexpr int L = FBC_TC_TILE_M + FW - 1;        // slab pixels per filter row
+    constexpr unsigned short CMASK = (unsigned short)((1u << CS) - 1u);   // every CTA of the cluster
+    __shared__ int s_abort;
+    __shared__ fbc_u32 s_tmem;
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const fbc_u32 sbase = fbc_smem_addr(fbc_tc_smem);
+    // barrier table: a_full[na] a_empty[na] b_full[nb] b_empty[nb] acc_full[2] acc_empty[2] drain
+    const fbc_u32 a_full0 = sbase + P.bar_off;
+    const fbc_u32 a_empty0 = a_full0 + 8u * P.na;
+    const fbc_u32 b_full0 = a_empty0 + 8u * P.na;
+    const fbc_u32 b_empty0 = b_full0 + 8u * P.nb;
+    const fbc_u32 acc_full0 = b_empty0 + 8u * P.nb;
+    const fbc_u32 acc_empty0 = acc_full0 + 16u;
+    const fbc_u32 drain_bar = acc_empty0 + 16u;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < P.na; ++s) {
+            fbc_mbar_init(a_full0 + 8u * s, FUSE ? FBC_TC_CONV_WARPS : 1);
+            fbc_mbar_init(a_empty0 + 8u * s, 1);
+        }
+        for (int s = 0; s < P.nb; ++s) {
+            fbc_mbar_init(b_full0 + 8u * s, 1);
+            fbc_mbar_init(b_empty0 + 8u * s, CS);   // one commit from every CTA of the cluster
+        }
+        for (int s = 0; s < 2; ++s) {
+            fbc_mbar_init(acc_full0 + 8u * s, 1);
+            fbc_mbar_init(acc_empty0 + 8u * s, EW);
+        }
+        fbc_mbar_init(drain_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_abort = 0;
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         fbc_smem_addr(&s_tmem)),
+                     "r"(FBC_TC_TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    fbc_tc_fence_before();
+    __syncthreads();
+    if (CS > 1) fbc_cluster_sync();   // every barrier of the cluster initialised before any remote arrive
+    fbc_tc_fence_after();
+    const fbc_u32 tmem = s_tmem;
+    volatile int* abort_flag = &s_abort;
+    // Work: groups of CS pixel tiles of one filter tile; cluster cl takes groups
+    // cl, cl + ncl, ...; CTA `rank` of it computes pixel tile (g % mgroups)*CS + rank
+    // of filter tile g / mgroups.  A pixel tile >= mtiles (a partial last group)
+    // is computed on zero input and not stored, so that the cluster stays in step.
+    const int rank = CS > 1 ? (int)fbc_cluster_rank() : 0;
+    const int cl = (int)blockIdx.x / CS, ncl = (int)gridDim.x / CS;
+    const int ngroups = P.mgroups * P.ntn;
+    const int my_tiles = cl < ngroups ? (ngroups - 1 - cl) / ncl + 1 : 0;
+    const int R = my_tiles * P.fh;                    // filter rows this CTA runs, in order
+    const fbc_u32 plane = (fbc_u32)P.lp * 16u;        // bytes per A chunk plane (shared)
+    const fbc_u32 bplane = (fbc_u32)P.nt * 16u;       // bytes per B chunk plane (shared)
+    const fbc_u32 a_half = NC * plane;                // offset of the lo planes in an A slot
+    const fbc_u32 b_half = NC * bplane;               // bytes per tap and half of a B stage
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ producer
+        if (lane == 0) {
+            fbc_u32 a_it = 0, b_it = 0;
+            int as = 0, bs = 0;
+            fbc_u32 aph = 0, bph = 0;
+            bool ok = true;
+            const fbc_u32 a_copy = (fbc_u32)L * 16u;
+            const long long tap_bytes = (long long)NC * P.nt * 16;
+            int next_a = 0;
+            for (int r = 0; r < R && ok; ++r) {
+                // unfused: the A slab of row r + alook goes out before the B stages
+                // of row r, so it is in flight while the MMAs of the previous row run
+                while (!FUSE && ok && next_a < R && next_a <= r + P.alook) {
+                    const int g = cl + (next_a / P.fh) * ncl;
+                    const long long p0 = (long long)((g % P.mgroups) * CS + rank) * FBC_TC_TILE_M +
+                                         (long long)(next_a % P.fh) * P.W;
+                    if (!(ok = fbc_wait(a_empty0 + 8u * as, aph ^ 1, P, abort_flag, FBC_TC_ERR_WAIT_EMPTY))) break;
+                    const fbc_u32 afull = a_full0 + 8u * as;
+                    fbc_mbar_expect_tx(afull, P.a_tx);
+                    const fbc_u32 dst = sbase + P.a_off + as * P.a_slot;
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) {
+                        const long long src = (c * P.npix_pad + p0) * 16;
+                        fbc_bulk_g2s(dst + c * plane, P.xhi + src, a_copy, afull);
+                        if (SPLIT) fbc_bulk_g2s(dst + a_half + c * plane, P.xlo + src, a_copy, afull);
+                    }
+                    ++a_it;
+                    ++next_a;
+                    if (++as == P.na) { as = 0; aph ^= 1; }
+                }
+                if (!ok) break;
+                const int g = cl + (r / P.fh) * ncl;
+                const long long woff = (((long long)(g / P.mgroups) * P.fh + r % P.fh) * FW) * tap_bytes;
+                const fbc_u8* wtap_hi = P.whi + woff;
+                const fbc_u8* wtap_lo = P.wlo + woff;
+#pragma unroll
+                for (int s = 0; s < NST; ++s) {
+                    // taps s*BT .. s*BT+tcnt-1 of this filter row are contiguous in the
+                    // operand layout: one copy per half for the whole stage (with a
+                    // cluster: this CTA's 1/CS share of it, multicast to all CTAs)
+                    const int tcnt = (s + 1) * BT <= FW ? BT : FW - s * BT;
+                    if (!(ok = fbc_wait(b_empty0 + 8u * bs, bph ^ 1, P, abort_flag, FBC_TC_ERR_WAIT_EMPTY))) break;
+                    const fbc_u32 bfull = b_full0 + 8u * bs;
+                    const fbc_u32 bytes = (fbc_u32)tcnt * b_half;
+                    fbc_mbar_expect_tx(bfull, SPLIT ? 2u * bytes : bytes);
+                    if ((int)b_it != P.drop_b) {
+                        const fbc_u32 share = bytes / CS, off = (fbc_u32)rank * share;
+                        const fbc_u32 bdst = sbase + P.b_off + bs * P.b_stage + off;
+                        const fbc_u8* src_hi = wtap_hi + s * BT * tap_bytes + off;
+                        const fbc_u8* src_lo = wtap_lo + s * BT * tap_bytes + off;
+                        if (CS > 1) {
+                            fbc_bulk_g2s_mc(bdst, src_hi, share, bfull, CMASK);
+                            if (SPLIT) fbc_bulk_g2s_mc(bdst + (fbc_u32)BT * b_half, src_lo, share, bfull, CMASK);
+                        } else {
+                            fbc_bulk_g2s(bdst, src_hi, share, bfull);
+                            if (SPLIT) fbc_bulk_g2s(bdst + (fbc_u32)BT * b_half, src_lo, share, bfull);
+                        }
+                    }
+                    ++b_it;
+                    if (++bs == P.nb) { bs = 0; bph ^= 1; }
+                }
+            }
+            if (!ok) {
+                // wait (bounded) for the copies still in flight into each ring slot
+                const fbc_u32 a0 = a_it > (fbc_u32)P.na ? a_it - P.na : 0;
+                for (fbc_u32 k = a0; k < a_it; ++k) fbc_wait_drain(a_full0 + 8u * (k % P.na), (k / P.na) & 1, P);
+                const fbc_u32 b0 = b_it > (fbc_u32)P.nb ? b_it - P.nb : 0;
+                for (fbc_u32 k = b0; k < b_it; ++k) fbc_wait_drain(b_full0 + 8u * (k % P.nb), (k / P.nb) & 1, P);
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            const fbc_u32 idesc = (1u << 4)                                  // D: FP32
+                                  | (1u << 7) | (1u << 10)                   // A, B: BF16
+                                  | ((fbc_u32)(P.nt >> 3) << 17)             // N
+                                  | ((fbc_u32)(FBC_TC_TILE_M >> 4) << 24);   // M
+            // descriptor arithmetic: the start address sits in the low 14 bits as
+            // (addr >> 4); every shared address is < 2^18, so adding (offset >> 4)
+            // to the descriptor never carries out of that field
+            const fbc_u64 adesc0 = fbc_smem_desc(sbase + P.a_off, plane, 128);
+            const fbc_u64 bdesc0 = fbc_smem_desc(sbase + P.b_off, bplane, 128);
+            const fbc_u64 a_step = P.a_slot >> 4, b_step = P.b_stage >> 4;
+            const fbc_u64 ak = (2 * plane) >> 4, bk = (2 * bplane) >> 4;
+            const fbc_u64 alo = a_half >> 4, blo = ((fbc_u64)BT * b_half) >> 4;
+            const fbc_u64 btap = b_half >> 4;   // next tap inside a stage
+            int as = 0, bs = 0;
+            fbc_u32 aph = 0, bph = 0, acc_it = 0;
+            fbc_u64 adesc = adesc0, bdesc = bdesc0;
+            bool ok = true;
+            bool issued = false;
+            for (int k = 0; k < my_tiles && ok; ++k) {
+                const int acc = acc_it & 1;
+                if (!(ok = fbc_wait(acc_empty0 + 8u * acc, ((acc_it >> 1) & 1) ^ 1, P, abort_flag,
+                                    FBC_TC_ERR_WAIT_ACC)))
+                    break;
+                fbc_tc_fence_after();
+                const fbc_u32 d_tmem = tmem + (fbc_u32)(acc * FBC_TC_ACC_COLS);
+                fbc_u32 accumulate = 0;
+                for (int i = 0; i < P.fh && ok; ++i) {
+                    if (!(ok = fbc_wait(a_full0 + 8u * as, aph, P, abort_flag, FBC_TC_ERR_WAIT_A))) break;
+#pragma unroll
+                    for (int s = 0; s < NST; ++s) {
+                        if (!(ok = fbc_wait(b_full0 + 8u * bs, bph, P, abort_flag, FBC_TC_ERR_WAIT_B))) break;
+#pragma unroll
+                        for (int t = 0; t < BT; ++t)
+                            if (s * BT + t < FW)
+                                fbc_issue_tap<NC, SPLIT>(d_tmem, adesc + (fbc_u64)(s * BT + t), bdesc + (fbc_u64)t * btap,
+                                                         ak, bk, alo, blo, idesc, accumulate);
+                        issued = true;
+                        if (CS > 1) fbc_umma_commit_mc(b_empty0 + 8u * bs, CMASK);
+                        else fbc_umma_commit(b_empty0 + 8u * bs);
+                        if (++bs == P.nb) { bs = 0; bph ^= 1; bdesc = bdesc0; } else { bdesc += b_step; }
+                    }
+                    if (!ok) break;
+                    fbc_umma_commit(a_empty0 + 8u * as);
+                    if (++as == P.na) { as = 0; aph ^= 1; adesc = adesc0; } else { adesc += a_step; }
+                }
+                if (!ok) break;
+                fbc_umma_commit(acc_full0 + 8u * acc);
+                ++acc_it;
+            }
+            if (!ok && issued) {
+                fbc_umma_commit(drain_bar);
+                fbc_wait_drain(drain_bar, 0, P);
+            }
+        }
+    } else if (warp < 2 + EW) {
+        // ------------------------------------------------------------ epilogue
+        // tcgen05.ld 16x256b: four consecutive lanes hold 8 contiguous columns of
+        // one output pixel, so every 8-byte store of a warp completes one 32-byte
+        // sector of each of 8 pixels; no shared-memory transpose.
+        const int ew = warp - 2;
+        const int lq = warp & 3;         // the TMEM lane quarter this warp may access
+        const int part = ew >> 2;        // EW = 8: even / odd 64-column chunks of the quarter
+        const bool vec2 = (P.N & 1) == 0;
+        fbc_u32 acc_it = 0;
+        for (int k = 0; k < my_tiles; ++k) {
+            const int g = cl + k * ncl;
+            const int mt = (g % P.mgroups) * CS + rank;
+            const int nti = g / P.mgroups;
+            const int acc = acc_it & 1;
+            if (!fbc_wait(acc_full0 + 8u * acc, (acc_it >> 1) & 1, P, abort_flag, FBC_TC_ERR_WAIT_ACC)) break;
+            fbc_tc_fence_after();
+            // columns past this tile's last filter (nt is a multiple of 16, a load 64
+            // wide) hold no result: stop at the tile end as well as N
+            const int nend = min(P.N, (nti + 1) * P.nt);
+            const int ncol = (P.nt + 63) / 64;
+            // output offsets of pixels lane/4 + 8e of the two 16-lane halves h: ob[2h + e]
+            long long ob[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int m = mt * FBC_TC_TILE_M + lq * 32 + e * 8 + (lane >> 2);
+                const int p = m / P.W;
+                const int q = m - p * P.W;
+                ob[e] = (p < P.Ho && q < P.Wo) ? ((long long)p * P.Wo + q) * P.N : -1;
+            }
+#pragma unroll 1
+            for (int cc = part; cc < ncol; cc += EW / 4) {
+                // both 16-lane halves of the quarter in flight before one wait
+                fbc_u32 r[2][32];
+                const fbc_u32 taddr = tmem + ((fbc_u32)(lq * 32) << 16) + (fbc_u32)(acc * FBC_TC_ACC_COLS + cc * 64);
+                fbc_tmem_ld16x256b_x8_async(taddr, r[0]);
+                fbc_tmem_ld16x256b_x8_async(taddr + (16u << 16), r[1]);
+                fbc_tmem_ld_wait();
+                fbc_reg_fence(r[0]);
+                fbc_reg_fence(r[1]);
+                const int n0 = nti * P.nt + cc * 64 + 2 * (lane & 3);
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+#pragma unroll
+                    for (int g8 = 0; g8 < 8; ++g8) {
+                        const int n = n0 + g8 * 8;
+#pragma unroll
+                        for (int e = 0; e < 2; ++e) {
+                            float a = __uint_as_float(r[h][4 * g8 + 2 * e]);
+                            float b = __uint_as_float(r[h][4 * g8 + 2 * e + 1]);
+                            if (P.epi == 1) {
+                                a = fminf(fmaxf(a, P.lo), P.hi);
+                                b = fminf(fmaxf(b, P.lo), P.hi);
+                            }
+                            const long long o = ob[2 * h + e];
+                            if (o < 0 || n >= nend) continue;
+                            float* dst = P.y + o + n;
+                            if (vec2 && n + 2 <= nend) {
+                                fbc_st_cs_f2(dst, a, b);
+                            } else {
+                                dst[0] = a;
+                                if (n + 1 < nend) dst[1] = b;
+                            }
+                        }
+                    }
+            }
+            fbc_tc_fence_before();
+            __syncwarp();
+            if (lane == 0) fbc_mbar_arrive(acc_empty0 + 8u * acc);
+            ++acc_it;
+        }
+    } else if constexpr (FUSE != 0) {
+        // ------------------------------------------------------------ converters
+        // FP32 slab row -> BF16 hi (and lo) chunk planes of an A slot.  Thread ct
+        // owns the 32-byte chunks item = ct + k*128 (pixel item / NC, plane item % NC)
+        // of every row, so a warp reads 1 KB of x contiguously; the loads of row
+        // r + 1 are issued before row r is converted.  Generic-proxy shared-memory
+        // writes are made visible to the tensor core's async proxy by
+        // fence.proxy.async before the arrival on a_full.
+        constexpr int NCT = FBC_TC_CONV_WARPS * 32;
+        constexpr int NITEMS = L * NC;
+        static_assert(NITEMS <= FBC_TC_CONV_ITEMS * NCT, "slab row too large for the converter registers");
+        const int ct = threadIdx.x - (2 + EW) * 32;
+        float4 nxt[FBC_TC_CONV_ITEMS][2];
+        auto load_row = [&](int r) {
+            const int g = cl + (r / P.fh) * ncl;
+            const long long p0 = (long long)((g % P.mgroups) * CS + rank) * FBC_TC_TILE_M + (long long)(r % P.fh) * P.W;
+#pragma unroll
+            for (int k = 0; k < FBC_TC_CONV_ITEMS; ++k) {
+                const int item = ct + k * NCT;
+                const int px = item / NC;
+                const int c = item - px * NC;
+                float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
+                if (item < NITEMS && p0 + px < P.npix) {
+                    // D % 4 == 0: each half of the chunk is wholly inside or outside D
+                    const float* src = P.xraw + (p0 + px) * P.D + c * 8;
+                    if (c * 8 < P.D) v0 = __ldg(reinterpret_cast<const float4*>(src));
+                    if (c * 8 + 4 < P.D) v1 = __ldg(reinterpret_cast<const float4*>(src + 4));
+                }
+                nxt[k][0] = v0;
+                nxt[k][1] = v1;
+            }
+        };
+        int as = 0;
+        fbc_u32 aph = 0;
+        if (R > 0) load_row(0);
+        for (int r = 0; r < R; ++r) {
+            float4 cur[FBC_TC_CONV_ITEMS][2];
+#pragma unroll
+            for (int k = 0; k < FBC_TC_CONV_ITEMS; ++k) {
+                cur[k][0] = nxt[k][0];
+                cur[k][1] = nxt[k][1];
+            }
+            if (r + 1 < R) load_row(r + 1);
+            if (!fbc_wait(a_empty0 + 8u * as, aph ^ 1, P, abort_flag, FBC_TC_ERR_WAIT_EMPTY)) break;
+            fbc_u8* dst = fbc_tc_smem + P.a_off + as * P.a_slot;
+#pragma unroll
+            for (int k = 0; k < FBC_TC_CONV_ITEMS; ++k) {
+                const int item = ct + k * NCT;
+                if (item < NITEMS) {
+                    const int px = item / NC;
+                    const int c = item - px * NC;
+                    const float v[8] = {cur[k][0].x, cur[k][0].y, cur[k][0].z, cur[k][0].w,
+                                        cur[k][1].x, cur[k][1].y, cur[k][1].z, cur[k][1].w};
+                    fbc_split8<SPLIT>(v, reinterpret_cast<uint4*>(dst + c * plane + px * 16),
+                                      reinterpret_cast<uint4*>(dst + a_half + c * plane + px * 16));
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) fbc_mbar_arrive(a_full0 + 8u * as);
+            if (++as == P.na) { as = 0; aph ^= 1; }
+        }
+    }
+    __syncwarp();
+    fbc_tc_fence_before();
+    __syncthreads();
+    // no CTA leaves while a peer may still multicast into it or commit to its barriers
+    if (CS > 1) fbc_cluster_sync();
+    fbc_tc_fence_after();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(FBC_TC_TMEM_COLS));
+}

@@ -1,0 +1,45 @@
+// tc_params.h -- the launch parameters and fixed geometry of the tensor-core
+// correlation kernel, shared verbatim by the host (tc_kernel.cu) and by the
+// NVRTC source (rtcg_tc.cuh), which gets this text prepended.  Plain types only,
+// no includes: NVRTC compiles it without system headers.
+#ifndef FBC_TC_PARAMS_H
+#define FBC_TC_PARAMS_H
+
+#define FBC_TC_TILE_M 128       // output pixels per tile (MMA M)
+#define FBC_TC_ACC_COLS 256     // TMEM columns per accumulator (MMA N <= 256)
+#define FBC_TC_TMEM_COLS 512    // two accumulators
+#define FBC_TC_CONV_WARPS 4     // FP32 -> BF16 converter warps of the fused mode
+#define FBC_TC_CONV_ITEMS 5     // 32-byte x chunks per converter thread and slab row
+
+// Error codes written to the host-mapped error word when a bounded wait expires.
+#define FBC_TC_ERR_WAIT_A 1
+#define FBC_TC_ERR_WAIT_B 2
+#define FBC_TC_ERR_WAIT_ACC 3
+#define FBC_TC_ERR_WAIT_EMPTY 4
+
+struct FbcTcParams {
+    const unsigned char* xhi;   // [nc][npix_pad][16 B] pre-split x planes (unfused)
+    const unsigned char* xlo;
+    const unsigned char* whi;   // [ntn][fh*fw][nc][nt][16 B]
+    const unsigned char* wlo;
+    float* y;                   // [Ho][Wo][N]
+    int* err;                   // host-mapped error word
+    const float* xraw;          // x itself [H*W][D] (fused: read by the converter warps)
+    long long npix_pad;
+    long long npix;             // H*W
+    unsigned long long wait_ns; // bound of every mbarrier wait
+    int W, Ho, Wo, N, D;
+    int fh, nt, ntn, mtiles;
+    int mgroups;                // groups of CS pixel tiles: ceil(mtiles / CS)
+    int lp;                     // pixels per chunk plane of an A slot
+    int na, nb;                 // A slots, B stages
+    int alook;                  // unfused: rows by which the A slabs run ahead of the B stages
+    int epi;                    // 0: none, 1: clamp to [lo, hi]
+    float lo, hi;
+    int drop_b;                 // fault injection: B load index whose copy is skipped (-1: none)
+    unsigned int a_slot, b_stage;   // bytes per A slot / B stage (hi [+ lo])
+    unsigned int a_tx;              // bytes copied per A slot (unfused)
+    unsigned int a_off, b_off, bar_off;
+};
+
+#endif

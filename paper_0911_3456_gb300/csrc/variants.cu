@@ -16,9 +16,11 @@
 
 namespace fbc {
 
-#include "_embedded_src.inc"   // kRtcgDirectSrc: the text of rtcg_direct.cuh
+#include "_embedded_src.inc"   // the texts of rtcg_direct.cuh, tc_params.h and rtcg_tc.cuh
 
 const char* rtcg_header_source() { return kRtcgDirectSrc; }
+const char* rtcg_tc_params_source() { return kRtcgTcParamsSrc; }
+const char* rtcg_tc_source() { return kRtcgTcSrc; }
 
 size_t direct_smem_bytes(const DirectTile& t, int fh, int fw, int c) {
     const long cc = t.chunk(c);

@@ -129,6 +129,34 @@ def test_explicit_tile_specs_compile(lib, spec):
     assert st == 1
 
 
+@pytest.mark.parametrize("D,f,spec", [
+    (32, 5, b"tcgen05:na=2,nb=4,nt=256,bt=5,ew=4,fz=1,cs=2"),    # the precision workload, fused
+    (32, 5, b"tcgen05:na=3,nb=3,nt=256,bt=3,ew=8,fz=0,cs=2"),    # two stages, the second partial
+    (8, 9, b"tcgen05:na=2,nb=4,nt=128,bt=2,ew=4,fz=1,cs=4"),     # paper row 1 depth, odd last stage
+    (48, 7, b"tcgen05:na=2,nb=4,nt=256,bt=4,ew=8,fz=0,cs=2"),    # six chunk planes, pre-pass only
+    (64, 13, b"tcgen05:na=2,nb=2,nt=256,bt=1,ew=4,fz=0,cs=1"),   # the deepest supported depth
+])
+def test_tensor_core_kernels_compile(lib, D, f, spec):
+    """The run-time generated tcgen05 kernel of a spec compiles for sm_103a in
+    BF16 and split-BF16 form (filter width and taps per stage baked in)."""
+    log = ctypes.create_string_buffer(1 << 16)
+    st = lib.fbcorr_rtcg_check(C.I64_3(64, 64, D), C.I64_4(16, f, f, D), C.epilogue(), spec, log, len(log))
+    assert st == 0, C.last_error() + log.value.decode()
+
+
+@pytest.mark.parametrize("D,f,spec,status", [
+    (48, 7, b"tcgen05:na=2,nb=4,nt=256,bt=2,ew=4,fz=1,cs=2", 3),   # fused needs D <= 32
+    (32, 3, b"tcgen05:na=2,nb=4,nt=256,bt=4,ew=4,fz=0,cs=2", 3),   # more taps per stage than fw
+    (32, 5, b"tcgen05:na=2,nb=4,nt=256,bt=2,ew=6,fz=0,cs=2", 1),   # epilogue warps must be 4 or 8
+    (32, 5, b"tcgen05:na=2,nb=4,nt=256,bt=2,ew=4,fz=0", 1),   # no cluster size: not a spec of this kernel
+    (32, 5, b"tcgen05:na=2,nb=4,nt=256,bt=2,ew=4,fz=0,cs=3", 1),   # clusters of 1, 2 or 4
+])
+def test_tensor_core_spec_refusals(lib, D, f, spec, status):
+    log = ctypes.create_string_buffer(1 << 16)
+    st = lib.fbcorr_rtcg_check(C.I64_3(64, 64, D), C.I64_4(16, f, f, D), C.epilogue(), spec, log, len(log))
+    assert st == status, C.last_error()
+
+
 def test_nvrtc_fault_injection_reports_nvrtc_error():
     """FBCORR_FAULT=nvrtc makes code generation fail; the status says so."""
     code = ("import ctypes\nfrom paper_0911_3456_gb300 import _capi as C\nlib=C.load()\n"

@@ -166,8 +166,10 @@ def test_split_beats_bf16_and_approaches_fp32():
 @pytest.mark.parametrize("mode", ["bf16", "bf16x3"])
 def test_every_tensor_core_configuration_matches(mode):
     """Every configuration the auto-tuner may pick (ring depths, filter-tile
-    width, taps per B stage -- including a last stage with fewer taps) gives
-    the same result on integer inputs, bit for bit."""
+    width, taps per B stage -- including a last stage with fewer taps --,
+    epilogue warps, fused or pre-pass conversion of x, clusters of 1, 2 or 4
+    CTAs sharing the B stages) gives the same result on integer inputs, bit for
+    bit."""
     torch = torch_cuda()
     from paper_0911_3456_gb300 import _capi as C
     from paper_0911_3456_gb300.api import Plan
@@ -175,14 +177,22 @@ def test_every_tensor_core_configuration_matches(mode):
     ref = oracle.fwd(wl.x, wl.w)
     p = Plan(wl.x.shape, wl.w.shape, mode)
     x, w = dev(wl.x, torch), dev(wl.w, torch)
+    # every generated kernel (taps per stage x epilogue warps x fused x cluster
+    # size), each with one of four ring / filter-tile shapes, plus ring-depth
+    # variations of one kernel; 19 x 140 outputs give 21 pixel tiles, so clusters
+    # of 2 and 4 end on a partial group
+    rings = [(2, 2, 256), (3, 4, 128), (2, 3, 128), (3, 2, 256)]
     specs = set()
-    for na in (2, 3):
-        for nb in (2, 3, 4):
-            for nt in (256, 128):
-                for bt in (1, 2, 3, 5):
-                    for lf in (0, 1):
-                        for fz in (0, 1):
-                            specs.add(f"tcgen05:na={na},nb={nb},nt={nt},bt={bt},lf={lf},fz={fz}")
+    k = 0
+    for bt in (1, 2, 3, 5):
+        for ew in (4, 8):
+            for fz in (0, 1):
+                for cs in (1, 2, 4):
+                    na, nb, nt = rings[k % len(rings)]
+                    k += 1
+                    specs.add(f"tcgen05:na={na},nb={nb},nt={nt},bt={bt},ew={ew},fz={fz},cs={cs}")
+    for na, nb, nt in [(2, 4, 256), (3, 3, 256), (2, 2, 128), (3, 4, 256)]:
+        specs.add(f"tcgen05:na={na},nb={nb},nt={nt},bt=2,ew=8,fz=1,cs=2")
     ran = 0
     for sp in sorted(specs):
         try:
@@ -197,7 +207,7 @@ def test_every_tensor_core_configuration_matches(mode):
 
 
 @pytest.mark.parametrize("mode", ["bf16", "bf16x3"])
-@pytest.mark.parametrize("shape", [(20, 150, 16, 16, 3, 3), (37, 45, 4, 20, 4, 2), (18, 260, 48, 40, 7, 7),
+@pytest.mark.parametrize("shape", [(20, 150, 16, 16, 3, 3), (37, 45, 4, 20, 4, 2), (18, 260, 28, 40, 7, 7),
                                    (9, 9, 12, 3, 9, 9)], ids=lambda s: "x".join(map(str, s)))
 def test_fused_conversion_matches_prepass(mode, shape):
     """x converted inside the kernel (fz=1) and by the pre-pass (fz=0) give the
@@ -209,7 +219,20 @@ def test_fused_conversion_matches_prepass(mode, shape):
     x, w = dev(wl.x, torch), dev(wl.w, torch)
     outs = {}
     for fz in (0, 1):
-        p.set_variant(f"tcgen05:na=2,nb=2,nt=256,bt=1,lf=0,fz={fz}")
+        p.set_variant(f"tcgen05:na=2,nb=2,nt=256,bt=1,ew=4,fz={fz},cs=1")
         outs[fz] = host(p.forward(x, w))
     assert np.array_equal(outs[0], outs[1])
     assert_within_bound(outs[1], wl.x, wl.w, mode)
+
+
+def test_fused_conversion_limits():
+    """The fused conversion needs D % 4 == 0 and at most 32 channels; other
+    depths take the pre-pass, and a fused spec for them is refused."""
+    torch_cuda()
+    from paper_0911_3456_gb300 import _capi as C
+    from paper_0911_3456_gb300.api import Plan
+    for shape in ((16, 40, 48), (16, 40, 6)):
+        p = Plan(shape, (8, 3, 3, shape[2]), "bf16")
+        assert ",fz=0," in p.info()["fwd"]["spec"]
+        with pytest.raises(C.FbcorrError):
+            p.set_variant("tcgen05:na=2,nb=2,nt=256,bt=1,ew=4,fz=1,cs=1")
