@@ -66,10 +66,6 @@ fbcorr_status_t rtcg_precompile(const std::vector<std::string>& sources);
 // Compile only (no GPU needed); returns the NVRTC log on failure.
 fbcorr_status_t rtcg_compile_only(const std::string& src, std::string* log);
 fbcorr_status_t launch(const Kernel& k, dim3 grid, void** args, cudaStream_t stream);
-// Launch with thread-block clusters of cluster_x CTAs along x (plain launch for 1).
-fbcorr_status_t launch_cluster(const Kernel& k, dim3 grid, int cluster_x, void** args, cudaStream_t stream);
-// How many clusters of cluster_x CTAs of `k` (k.threads, k.smem) can be resident at once.
-fbcorr_status_t kernel_max_clusters(const Kernel& k, int cluster_x, int* out);
 // CUDA-graph kernel nodes for NVRTC kernels (driver API under the hood).
 fbcorr_status_t graph_add_kernel(cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps,
                                  const Kernel& k, dim3 grid, void** args, cudaGraphNode_t* out);

@@ -42,8 +42,6 @@ struct DriverApi {
     CUresult (*graphExecKernelNodeSetParams)(CUgraphExec, CUgraphNode,
                                              const CUDA_KERNEL_NODE_PARAMS*) = nullptr;
     CUresult (*occupancy)(int*, CUfunction, int, size_t) = nullptr;
-    CUresult (*launchKernelEx)(const CUlaunchConfig*, CUfunction, void**, void**) = nullptr;
-    CUresult (*maxActiveClusters)(int*, CUfunction, const CUlaunchConfig*) = nullptr;
 };
 
 std::mutex g_mu;
@@ -72,9 +70,7 @@ fbcorr_status_t driver_api(DriverApi** out) {
                   resolve("cuGetErrorString", &d.getErrorString) &&
                   resolve("cuGraphAddKernelNode", &d.graphAddKernelNode) &&
                   resolve("cuGraphExecKernelNodeSetParams", &d.graphExecKernelNodeSetParams) &&
-                  resolve("cuOccupancyMaxActiveBlocksPerMultiprocessor", &d.occupancy) &&
-                  resolve("cuLaunchKernelEx", &d.launchKernelEx) &&
-                  resolve("cuOccupancyMaxActiveClusters", &d.maxActiveClusters);
+                  resolve("cuOccupancyMaxActiveBlocksPerMultiprocessor", &d.occupancy);
         if (!ok) return set_error(FBCORR_ERR_CUDA, "could not resolve CUDA driver entry points");
         d.ok = true;
         g_drv = d;
@@ -322,56 +318,6 @@ fbcorr_status_t launch(const Kernel& k, dim3 grid, void** args, cudaStream_t str
     if (r != CUDA_SUCCESS)
         return set_error(FBCORR_ERR_CUDA, "cuLaunchKernel(%s grid=%u,%u,%u block=%d smem=%zu): %s",
                          k.name.c_str(), grid.x, grid.y, grid.z, k.threads, k.smem, cu_err(r));
-    return FBCORR_OK;
-}
-
-namespace {
-CUlaunchConfig cluster_config(const Kernel& k, dim3 grid, int cluster_x, cudaStream_t stream,
-                              CUlaunchAttribute* attr) {
-    CUlaunchConfig cfg;
-    memset(&cfg, 0, sizeof cfg);
-    cfg.gridDimX = grid.x;
-    cfg.gridDimY = grid.y;
-    cfg.gridDimZ = grid.z;
-    cfg.blockDimX = (unsigned)k.threads;
-    cfg.blockDimY = 1;
-    cfg.blockDimZ = 1;
-    cfg.sharedMemBytes = (unsigned)k.smem;
-    cfg.hStream = (CUstream)stream;
-    memset(attr, 0, sizeof *attr);
-    attr->id = CU_LAUNCH_ATTRIBUTE_CLUSTER_DIMENSION;
-    attr->value.clusterDim.x = (unsigned)cluster_x;
-    attr->value.clusterDim.y = 1;
-    attr->value.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cfg;
-}
-}  // namespace
-
-fbcorr_status_t launch_cluster(const Kernel& k, dim3 grid, int cluster_x, void** args, cudaStream_t stream) {
-    if (cluster_x <= 1) return launch(k, grid, args, stream);
-    DriverApi* drv = nullptr;
-    FBC_TRY(driver_api(&drv));
-    if (!k.fn) return set_error(FBCORR_ERR_INTERNAL, "launch of an unloaded kernel");
-    CUlaunchAttribute attr;
-    const CUlaunchConfig cfg = cluster_config(k, grid, cluster_x, stream, &attr);
-    CUresult r = drv->launchKernelEx(&cfg, k.fn, args, nullptr);
-    if (r != CUDA_SUCCESS)
-        return set_error(FBCORR_ERR_CUDA, "cuLaunchKernelEx(%s grid=%u cluster=%d block=%d smem=%zu): %s",
-                         k.name.c_str(), grid.x, cluster_x, k.threads, k.smem, cu_err(r));
-    return FBCORR_OK;
-}
-
-fbcorr_status_t kernel_max_clusters(const Kernel& k, int cluster_x, int* out) {
-    DriverApi* drv = nullptr;
-    FBC_TRY(driver_api(&drv));
-    CUlaunchAttribute attr;
-    const CUlaunchConfig cfg = cluster_config(k, dim3(cluster_x), cluster_x, nullptr, &attr);
-    CUresult r = drv->maxActiveClusters(out, k.fn, &cfg);
-    if (r != CUDA_SUCCESS)
-        return set_error(FBCORR_ERR_CUDA, "cuOccupancyMaxActiveClusters(%s, %d): %s", k.name.c_str(), cluster_x,
-                         cu_err(r));
     return FBCORR_OK;
 }
 

@@ -19,14 +19,6 @@
 // of the time; with FW and BT compile-time the MMA sequence of a filter row is
 // straight-line code (the paper's loop unrolling by RTCG, Sec. 3.2 and 6.2).
 //
-// Clusters (CS = 2 or 4): the CS CTAs of a cluster compute CS neighbouring
-// pixel tiles of the same filter tile in lockstep, so they read the same B
-// stages.  Each CTA copies 1/CS of every stage from global memory with a
-// multicast bulk copy into the same slot of all CS CTAs, and every MMA commit
-// that frees a slot arrives on that slot's barrier in all CS CTAs: the weights
-// cross the L2 -> SM fabric once per cluster instead of once per CTA, which at
-// one 128x256x16 MMA per 128 cycles would otherwise take 8-16 TB/s.
-//
 // Roles per CTA (persistent, one per SM):
 //   warp 0      producer: cp.async.bulk (1D TMA) of B slices of BT consecutive
 //               taps (and, unfused, of pre-split A slabs) into rings,
@@ -39,8 +31,14 @@
 //               tcgen05.ld 16x256b, optional clamp, streaming stores straight
 //               from registers (four lanes write 32 contiguous bytes of one
 //               output pixel); overlaps the MMAs of the next tile;
-//   last 4      (FUSE) converter warps: FP32 x rows read from global memory
-//               one row ahead, written as BF16 hi (and lo) chunk planes.
+//   last CW     (FUSE) converter warps: FP32 x rows -> BF16 hi (and lo) chunk
+//               planes of an A slot; FUSE = 1 reads the rows from global memory
+//               into registers one row ahead, FUSE = 2 from a ring of raw rows
+//               that the producer fills with one bulk copy per row.
+// The bulk-copy unit costs about 150 cycles per copy whatever its size up to
+// 16 KB (and moves at most ~110 B per cycle per SM), so the copy count per tile
+// matters: B goes in stages of BT taps (one copy per half), and FUSE = 2 brings
+// a slab row in one copy where the pre-split planes (FUSE = 0) need NC.
 // Operands use the no-swizzle K-major canonical layout: a core matrix is 8 rows
 // x 16 bytes, rows contiguous; LBO = byte stride between K-adjacent core
 // matrices (one chunk plane), SBO = 128 bytes between 8-row groups.
@@ -104,26 +102,6 @@ __device__ __forceinline__ void fbc_bulk_g2s(fbc_u32 dst, const void* src, fbc_u
         : "memory");
 }
 
-// The same copy into the same CTA-relative offset of every CTA in `mask`, with
-// complete_tx on the barrier at `bar`'s offset in each of them.
-__device__ __forceinline__ void fbc_bulk_g2s_mc(fbc_u32 dst, const void* src, fbc_u32 bytes, fbc_u32 bar,
-                                                unsigned short mask) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1], %2, [%3], %4;" ::"r"(dst),
-        "l"(src), "r"(bytes), "r"(bar), "h"(mask)
-        : "memory");
-}
-
-__device__ __forceinline__ fbc_u32 fbc_cluster_rank() {
-    fbc_u32 r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-
-__device__ __forceinline__ void fbc_cluster_sync() {
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
 __device__ __forceinline__ void fbc_tc_fence_before() {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -146,14 +124,6 @@ __device__ __forceinline__ void fbc_umma(fbc_u32 d_tmem, fbc_u64 a, fbc_u64 b, f
 
 __device__ __forceinline__ void fbc_umma_commit(fbc_u32 bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-                 : "memory");
-}
-
-// Arrive (when the MMAs issued so far complete) on the barrier at `bar`'s
-// offset in every CTA of `mask`.
-__device__ __forceinline__ void fbc_umma_commit_mc(fbc_u32 bar, unsigned short mask) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(bar),
-                 "h"(mask)
                  : "memory");
 }
 
@@ -265,17 +235,17 @@ __device__ __forceinline__ void fbc_issue_tap(fbc_u32 d_tmem, fbc_u64 ad, fbc_u6
 }
 
 // ---------------------------------------------------------------- the kernel body
-template <int NC, int SPLIT, int FW, int BT, int EW, int FUSE, int CS>
+template <int NC, int SPLIT, int FW, int BT, int EW, int FUSE, int CW>
 __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
     constexpr int NST = (FW + BT - 1) / BT;          // B stages per filter row
     constexpr int L = FBC_TC_TILE_M + FW - 1;        // slab pixels per filter row
-    constexpr unsigned short CMASK = (unsigned short)((1u << CS) - 1u);   // every CTA of the cluster
     __shared__ int s_abort;
     __shared__ fbc_u32 s_tmem;
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const fbc_u32 sbase = fbc_smem_addr(fbc_tc_smem);
-    // barrier table: a_full[na] a_empty[na] b_full[nb] b_empty[nb] acc_full[2] acc_empty[2] drain
+    // barrier table: a_full[na] a_empty[na] b_full[nb] b_empty[nb] acc_full[2] acc_empty[2]
+    // drain raw_full[nr] raw_empty[nr]
     const fbc_u32 a_full0 = sbase + P.bar_off;
     const fbc_u32 a_empty0 = a_full0 + 8u * P.na;
     const fbc_u32 b_full0 = a_empty0 + 8u * P.na;
@@ -283,21 +253,27 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
     const fbc_u32 acc_full0 = b_empty0 + 8u * P.nb;
     const fbc_u32 acc_empty0 = acc_full0 + 16u;
     const fbc_u32 drain_bar = acc_empty0 + 16u;
+    const fbc_u32 raw_full0 = drain_bar + 8u;
+    const fbc_u32 raw_empty0 = raw_full0 + 8u * P.nr;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < P.na; ++s) {
-            fbc_mbar_init(a_full0 + 8u * s, FUSE ? FBC_TC_CONV_WARPS : 1);
+            fbc_mbar_init(a_full0 + 8u * s, FUSE ? CW : 1);
             fbc_mbar_init(a_empty0 + 8u * s, 1);
         }
         for (int s = 0; s < P.nb; ++s) {
             fbc_mbar_init(b_full0 + 8u * s, 1);
-            fbc_mbar_init(b_empty0 + 8u * s, CS);   // one commit from every CTA of the cluster
+            fbc_mbar_init(b_empty0 + 8u * s, 1);
         }
         for (int s = 0; s < 2; ++s) {
             fbc_mbar_init(acc_full0 + 8u * s, 1);
             fbc_mbar_init(acc_empty0 + 8u * s, EW);
         }
         fbc_mbar_init(drain_bar, 1);
+        for (int s = 0; s < P.nr; ++s) {
+            fbc_mbar_init(raw_full0 + 8u * s, 1);
+            fbc_mbar_init(raw_empty0 + 8u * s, CW > 0 ? CW : 1);   // nr = 0 unless FUSE = 2
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_abort = 0;
     }
@@ -309,82 +285,86 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
     }
     fbc_tc_fence_before();
     __syncthreads();
-    if (CS > 1) fbc_cluster_sync();   // every barrier of the cluster initialised before any remote arrive
     fbc_tc_fence_after();
     const fbc_u32 tmem = s_tmem;
     volatile int* abort_flag = &s_abort;
-    // Work: groups of CS pixel tiles of one filter tile; cluster cl takes groups
-    // cl, cl + ncl, ...; CTA `rank` of it computes pixel tile (g % mgroups)*CS + rank
-    // of filter tile g / mgroups.  A pixel tile >= mtiles (a partial last group)
-    // is computed on zero input and not stored, so that the cluster stays in step.
-    const int rank = CS > 1 ? (int)fbc_cluster_rank() : 0;
-    const int cl = (int)blockIdx.x / CS, ncl = (int)gridDim.x / CS;
-    const int ngroups = P.mgroups * P.ntn;
-    const int my_tiles = cl < ngroups ? (ngroups - 1 - cl) / ncl + 1 : 0;
+    // tiles blockIdx.x, blockIdx.x + gridDim.x, ...: pixel tile t % mtiles of filter tile t / mtiles
+    const int ntiles = P.mtiles * P.ntn;
+    const int my_tiles = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     const int R = my_tiles * P.fh;                    // filter rows this CTA runs, in order
     const fbc_u32 plane = (fbc_u32)P.lp * 16u;        // bytes per A chunk plane (shared)
     const fbc_u32 bplane = (fbc_u32)P.nt * 16u;       // bytes per B chunk plane (shared)
     const fbc_u32 a_half = NC * plane;                // offset of the lo planes in an A slot
     const fbc_u32 b_half = NC * bplane;               // bytes per tap and half of a B stage
+    // first input pixel of slab row r
+    auto row_p0 = [&](int r) -> long long {
+        const int tile = (int)blockIdx.x + (r / P.fh) * (int)gridDim.x;
+        return (long long)(tile % P.mtiles) * FBC_TC_TILE_M + (long long)(r % P.fh) * P.W;
+    };
+    // pixels of slab row r that lie inside x (the rest reads as zero)
+    auto row_valid = [&](long long p0) -> int {
+        const long long v = P.npix - p0;
+        return (int)(v < 0 ? 0 : (v > L ? L : v));
+    };
 
     if (warp == 0) {
         // ------------------------------------------------------------ producer
         if (lane == 0) {
-            fbc_u32 a_it = 0, b_it = 0;
-            int as = 0, bs = 0;
-            fbc_u32 aph = 0, bph = 0;
+            fbc_u32 a_it = 0, b_it = 0, r_it = 0;
+            int as = 0, bs = 0, rs = 0;
+            fbc_u32 aph = 0, bph = 0, rph = 0;
             bool ok = true;
             const fbc_u32 a_copy = (fbc_u32)L * 16u;
             const long long tap_bytes = (long long)NC * P.nt * 16;
             int next_a = 0;
             for (int r = 0; r < R && ok; ++r) {
-                // unfused: the A slab of row r + alook goes out before the B stages
-                // of row r, so it is in flight while the MMAs of the previous row run
-                while (!FUSE && ok && next_a < R && next_a <= r + P.alook) {
-                    const int g = cl + (next_a / P.fh) * ncl;
-                    const long long p0 = (long long)((g % P.mgroups) * CS + rank) * FBC_TC_TILE_M +
-                                         (long long)(next_a % P.fh) * P.W;
-                    if (!(ok = fbc_wait(a_empty0 + 8u * as, aph ^ 1, P, abort_flag, FBC_TC_ERR_WAIT_EMPTY))) break;
-                    const fbc_u32 afull = a_full0 + 8u * as;
-                    fbc_mbar_expect_tx(afull, P.a_tx);
-                    const fbc_u32 dst = sbase + P.a_off + as * P.a_slot;
+                // the A side of rows up to r + look goes out before the B stages of
+                // row r, so it is in flight while the MMAs of earlier rows run
+                while (FUSE != 1 && ok && next_a < R && next_a <= r + P.alook) {
+                    const long long p0 = row_p0(next_a);
+                    if (FUSE == 2) {
+                        // one copy of the raw FP32 slab row (16-byte multiples: D % 4 == 0)
+                        if (!(ok = fbc_wait(raw_empty0 + 8u * rs, rph ^ 1, P, abort_flag, FBC_TC_ERR_WAIT_EMPTY))) break;
+                        const fbc_u32 rfull = raw_full0 + 8u * rs;
+                        const fbc_u32 bytes = (fbc_u32)row_valid(p0) * (fbc_u32)P.D * 4u;
+                        fbc_mbar_expect_tx(rfull, bytes);
+                        if (bytes) fbc_bulk_g2s(sbase + P.raw_off + rs * P.raw_slot, P.xraw + p0 * P.D, bytes, rfull);
+                        ++r_it;
+                        if (++rs == P.nr) { rs = 0; rph ^= 1; }
+                    } else {
+                        if (!(ok = fbc_wait(a_empty0 + 8u * as, aph ^ 1, P, abort_flag, FBC_TC_ERR_WAIT_EMPTY))) break;
+                        const fbc_u32 afull = a_full0 + 8u * as;
+                        fbc_mbar_expect_tx(afull, P.a_tx);
+                        const fbc_u32 dst = sbase + P.a_off + as * P.a_slot;
 #pragma unroll
-                    for (int c = 0; c < NC; ++c) {
-                        const long long src = (c * P.npix_pad + p0) * 16;
-                        fbc_bulk_g2s(dst + c * plane, P.xhi + src, a_copy, afull);
-                        if (SPLIT) fbc_bulk_g2s(dst + a_half + c * plane, P.xlo + src, a_copy, afull);
+                        for (int c = 0; c < NC; ++c) {
+                            const long long src = (c * P.npix_pad + p0) * 16;
+                            fbc_bulk_g2s(dst + c * plane, P.xhi + src, a_copy, afull);
+                            if (SPLIT) fbc_bulk_g2s(dst + a_half + c * plane, P.xlo + src, a_copy, afull);
+                        }
+                        ++a_it;
+                        if (++as == P.na) { as = 0; aph ^= 1; }
                     }
-                    ++a_it;
                     ++next_a;
-                    if (++as == P.na) { as = 0; aph ^= 1; }
                 }
                 if (!ok) break;
-                const int g = cl + (r / P.fh) * ncl;
-                const long long woff = (((long long)(g / P.mgroups) * P.fh + r % P.fh) * FW) * tap_bytes;
+                const int tile = (int)blockIdx.x + (r / P.fh) * (int)gridDim.x;
+                const long long woff = (((long long)(tile / P.mtiles) * P.fh + r % P.fh) * FW) * tap_bytes;
                 const fbc_u8* wtap_hi = P.whi + woff;
                 const fbc_u8* wtap_lo = P.wlo + woff;
 #pragma unroll
                 for (int s = 0; s < NST; ++s) {
                     // taps s*BT .. s*BT+tcnt-1 of this filter row are contiguous in the
-                    // operand layout: one copy per half for the whole stage (with a
-                    // cluster: this CTA's 1/CS share of it, multicast to all CTAs)
+                    // operand layout: one copy per half for the whole stage
                     const int tcnt = (s + 1) * BT <= FW ? BT : FW - s * BT;
                     if (!(ok = fbc_wait(b_empty0 + 8u * bs, bph ^ 1, P, abort_flag, FBC_TC_ERR_WAIT_EMPTY))) break;
                     const fbc_u32 bfull = b_full0 + 8u * bs;
                     const fbc_u32 bytes = (fbc_u32)tcnt * b_half;
                     fbc_mbar_expect_tx(bfull, SPLIT ? 2u * bytes : bytes);
                     if ((int)b_it != P.drop_b) {
-                        const fbc_u32 share = bytes / CS, off = (fbc_u32)rank * share;
-                        const fbc_u32 bdst = sbase + P.b_off + bs * P.b_stage + off;
-                        const fbc_u8* src_hi = wtap_hi + s * BT * tap_bytes + off;
-                        const fbc_u8* src_lo = wtap_lo + s * BT * tap_bytes + off;
-                        if (CS > 1) {
-                            fbc_bulk_g2s_mc(bdst, src_hi, share, bfull, CMASK);
-                            if (SPLIT) fbc_bulk_g2s_mc(bdst + (fbc_u32)BT * b_half, src_lo, share, bfull, CMASK);
-                        } else {
-                            fbc_bulk_g2s(bdst, src_hi, share, bfull);
-                            if (SPLIT) fbc_bulk_g2s(bdst + (fbc_u32)BT * b_half, src_lo, share, bfull);
-                        }
+                        const fbc_u32 bdst = sbase + P.b_off + bs * P.b_stage;
+                        fbc_bulk_g2s(bdst, wtap_hi + s * BT * tap_bytes, bytes, bfull);
+                        if (SPLIT) fbc_bulk_g2s(bdst + (fbc_u32)BT * b_half, wtap_lo + s * BT * tap_bytes, bytes, bfull);
                     }
                     ++b_it;
                     if (++bs == P.nb) { bs = 0; bph ^= 1; }
@@ -396,6 +376,8 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
                 for (fbc_u32 k = a0; k < a_it; ++k) fbc_wait_drain(a_full0 + 8u * (k % P.na), (k / P.na) & 1, P);
                 const fbc_u32 b0 = b_it > (fbc_u32)P.nb ? b_it - P.nb : 0;
                 for (fbc_u32 k = b0; k < b_it; ++k) fbc_wait_drain(b_full0 + 8u * (k % P.nb), (k / P.nb) & 1, P);
+                const fbc_u32 r0 = r_it > (fbc_u32)P.nr ? r_it - P.nr : 0;
+                for (fbc_u32 k = r0; k < r_it; ++k) fbc_wait_drain(raw_full0 + 8u * (k % P.nr), (k / P.nr) & 1, P);
             }
         }
     } else if (warp == 1) {
@@ -438,8 +420,7 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
                                 fbc_issue_tap<NC, SPLIT>(d_tmem, adesc + (fbc_u64)(s * BT + t), bdesc + (fbc_u64)t * btap,
                                                          ak, bk, alo, blo, idesc, accumulate);
                         issued = true;
-                        if (CS > 1) fbc_umma_commit_mc(b_empty0 + 8u * bs, CMASK);
-                        else fbc_umma_commit(b_empty0 + 8u * bs);
+                        fbc_umma_commit(b_empty0 + 8u * bs);
                         if (++bs == P.nb) { bs = 0; bph ^= 1; bdesc = bdesc0; } else { bdesc += b_step; }
                     }
                     if (!ok) break;
@@ -466,9 +447,9 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
         const bool vec2 = (P.N & 1) == 0;
         fbc_u32 acc_it = 0;
         for (int k = 0; k < my_tiles; ++k) {
-            const int g = cl + k * ncl;
-            const int mt = (g % P.mgroups) * CS + rank;
-            const int nti = g / P.mgroups;
+            const int tile = (int)blockIdx.x + k * (int)gridDim.x;
+            const int mt = tile % P.mtiles;
+            const int nti = tile / P.mtiles;
             const int acc = acc_it & 1;
             if (!fbc_wait(acc_full0 + 8u * acc, (acc_it >> 1) & 1, P, abort_flag, FBC_TC_ERR_WAIT_ACC)) break;
             fbc_tc_fence_after();
@@ -528,72 +509,107 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
         }
     } else if constexpr (FUSE != 0) {
         // ------------------------------------------------------------ converters
-        // FP32 slab row -> BF16 hi (and lo) chunk planes of an A slot.  Thread ct
-        // owns the 32-byte chunks item = ct + k*128 (pixel item / NC, plane item % NC)
-        // of every row, so a warp reads 1 KB of x contiguously; the loads of row
-        // r + 1 are issued before row r is converted.  Generic-proxy shared-memory
+        // FP32 slab row -> BF16 hi (and lo) chunk planes of an A slot, by CW warps.
+        // Thread ct owns the 32-byte chunks item = ct + k*32*CW (pixel item / NC,
+        // plane item % NC)
+        // of every row: FUSE = 1 loads them from x in global memory (a warp reads
+        // 1 KB contiguously) one row ahead of the conversion, FUSE = 2 reads them
+        // from the raw-row slot the producer filled.  Generic-proxy shared-memory
         // writes are made visible to the tensor core's async proxy by
         // fence.proxy.async before the arrival on a_full.
-        constexpr int NCT = FBC_TC_CONV_WARPS * 32;
+        constexpr int NCT = (CW > 0 ? CW : 1) * 32;   // CW = 0 only without conversion (branch discarded)
         constexpr int NITEMS = L * NC;
-        static_assert(NITEMS <= FBC_TC_CONV_ITEMS * NCT, "slab row too large for the converter registers");
+        constexpr int KI = (NITEMS + NCT - 1) / NCT;   // chunks per thread and row
+        static_assert(FUSE != 1 || KI <= FBC_TC_CONV_ITEMS, "slab row too large for the converter registers");
         const int ct = threadIdx.x - (2 + EW) * 32;
-        float4 nxt[FBC_TC_CONV_ITEMS][2];
-        auto load_row = [&](int r) {
-            const int g = cl + (r / P.fh) * ncl;
-            const long long p0 = (long long)((g % P.mgroups) * CS + rank) * FBC_TC_TILE_M + (long long)(r % P.fh) * P.W;
+        int as = 0, rs = 0;
+        fbc_u32 aph = 0, rph = 0;
+        if constexpr (FUSE == 1) {
+            float4 nxt[KI][2];
+            auto load_row = [&](int r) {
+                const long long p0 = row_p0(r);
 #pragma unroll
-            for (int k = 0; k < FBC_TC_CONV_ITEMS; ++k) {
-                const int item = ct + k * NCT;
-                const int px = item / NC;
-                const int c = item - px * NC;
-                float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
-                if (item < NITEMS && p0 + px < P.npix) {
-                    // D % 4 == 0: each half of the chunk is wholly inside or outside D
-                    const float* src = P.xraw + (p0 + px) * P.D + c * 8;
-                    if (c * 8 < P.D) v0 = __ldg(reinterpret_cast<const float4*>(src));
-                    if (c * 8 + 4 < P.D) v1 = __ldg(reinterpret_cast<const float4*>(src + 4));
-                }
-                nxt[k][0] = v0;
-                nxt[k][1] = v1;
-            }
-        };
-        int as = 0;
-        fbc_u32 aph = 0;
-        if (R > 0) load_row(0);
-        for (int r = 0; r < R; ++r) {
-            float4 cur[FBC_TC_CONV_ITEMS][2];
-#pragma unroll
-            for (int k = 0; k < FBC_TC_CONV_ITEMS; ++k) {
-                cur[k][0] = nxt[k][0];
-                cur[k][1] = nxt[k][1];
-            }
-            if (r + 1 < R) load_row(r + 1);
-            if (!fbc_wait(a_empty0 + 8u * as, aph ^ 1, P, abort_flag, FBC_TC_ERR_WAIT_EMPTY)) break;
-            fbc_u8* dst = fbc_tc_smem + P.a_off + as * P.a_slot;
-#pragma unroll
-            for (int k = 0; k < FBC_TC_CONV_ITEMS; ++k) {
-                const int item = ct + k * NCT;
-                if (item < NITEMS) {
+                for (int k = 0; k < KI; ++k) {
+                    const int item = ct + k * NCT;
                     const int px = item / NC;
                     const int c = item - px * NC;
-                    const float v[8] = {cur[k][0].x, cur[k][0].y, cur[k][0].z, cur[k][0].w,
-                                        cur[k][1].x, cur[k][1].y, cur[k][1].z, cur[k][1].w};
-                    fbc_split8<SPLIT>(v, reinterpret_cast<uint4*>(dst + c * plane + px * 16),
-                                      reinterpret_cast<uint4*>(dst + a_half + c * plane + px * 16));
+                    float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
+                    if (item < NITEMS && p0 + px < P.npix) {
+                        // D % 4 == 0: each half of the chunk is wholly inside or outside D
+                        const float* src = P.xraw + (p0 + px) * P.D + c * 8;
+                        if (c * 8 < P.D) v0 = __ldg(reinterpret_cast<const float4*>(src));
+                        if (c * 8 + 4 < P.D) v1 = __ldg(reinterpret_cast<const float4*>(src + 4));
+                    }
+                    nxt[k][0] = v0;
+                    nxt[k][1] = v1;
                 }
+            };
+            if (R > 0) load_row(0);
+            for (int r = 0; r < R; ++r) {
+                float4 cur[KI][2];
+#pragma unroll
+                for (int k = 0; k < KI; ++k) {
+                    cur[k][0] = nxt[k][0];
+                    cur[k][1] = nxt[k][1];
+                }
+                if (r + 1 < R) load_row(r + 1);
+                if (!fbc_wait(a_empty0 + 8u * as, aph ^ 1, P, abort_flag, FBC_TC_ERR_WAIT_EMPTY)) break;
+                fbc_u8* dst = fbc_tc_smem + P.a_off + as * P.a_slot;
+#pragma unroll
+                for (int k = 0; k < KI; ++k) {
+                    const int item = ct + k * NCT;
+                    if (item < NITEMS) {
+                        const int px = item / NC;
+                        const int c = item - px * NC;
+                        const float v[8] = {cur[k][0].x, cur[k][0].y, cur[k][0].z, cur[k][0].w,
+                                            cur[k][1].x, cur[k][1].y, cur[k][1].z, cur[k][1].w};
+                        fbc_split8<SPLIT>(v, reinterpret_cast<uint4*>(dst + c * plane + px * 16),
+                                          reinterpret_cast<uint4*>(dst + a_half + c * plane + px * 16));
+                    }
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) fbc_mbar_arrive(a_full0 + 8u * as);
+                if (++as == P.na) { as = 0; aph ^= 1; }
             }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncwarp();
-            if (lane == 0) fbc_mbar_arrive(a_full0 + 8u * as);
-            if (++as == P.na) { as = 0; aph ^= 1; }
+        } else {
+            for (int r = 0; r < R; ++r) {
+                if (!fbc_wait(raw_full0 + 8u * rs, rph, P, abort_flag, FBC_TC_ERR_WAIT_A)) break;
+                if (!fbc_wait(a_empty0 + 8u * as, aph ^ 1, P, abort_flag, FBC_TC_ERR_WAIT_EMPTY)) break;
+                const int valid = row_valid(row_p0(r));
+                const float* raw = reinterpret_cast<const float*>(fbc_tc_smem + P.raw_off + rs * P.raw_slot);
+                fbc_u8* dst = fbc_tc_smem + P.a_off + as * P.a_slot;
+#pragma unroll
+                for (int k = 0; k < KI; ++k) {
+                    const int item = ct + k * NCT;
+                    if (item < NITEMS) {
+                        const int px = item / NC;
+                        const int c = item - px * NC;
+                        float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
+                        if (px < valid) {
+                            const float* src = raw + px * P.D + c * 8;
+                            if (c * 8 < P.D) v0 = *reinterpret_cast<const float4*>(src);
+                            if (c * 8 + 4 < P.D) v1 = *reinterpret_cast<const float4*>(src + 4);
+                        }
+                        const float v[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+                        fbc_split8<SPLIT>(v, reinterpret_cast<uint4*>(dst + c * plane + px * 16),
+                                          reinterpret_cast<uint4*>(dst + a_half + c * plane + px * 16));
+                    }
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) {
+                    fbc_mbar_arrive(a_full0 + 8u * as);
+                    fbc_mbar_arrive(raw_empty0 + 8u * rs);
+                }
+                if (++as == P.na) { as = 0; aph ^= 1; }
+                if (++rs == P.nr) { rs = 0; rph ^= 1; }
+            }
         }
     }
     __syncwarp();
     fbc_tc_fence_before();
     __syncthreads();
-    // no CTA leaves while a peer may still multicast into it or commit to its barriers
-    if (CS > 1) fbc_cluster_sync();
     fbc_tc_fence_after();
     if (warp == 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(FBC_TC_TMEM_COLS));

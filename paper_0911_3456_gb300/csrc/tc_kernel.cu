@@ -124,8 +124,9 @@ struct TcConfig {
     int na = 2, nb = 5, ntmax = 256;   // A slots, B stages, widest filter tile
     int bt = 1;                        // filter taps per B stage
     int ew = 4;                        // epilogue warps (4 or 8)
-    int fuse = 0;                      // convert x inside the kernel (no x pre-pass)
-    int cs = 1;                        // CTAs per cluster sharing (multicasting) the B stages
+    int fuse = 0;                      // x conversion: 0 pre-pass, 1 converters from global, 2 from a raw ring
+    int nr = 0;                        // raw-row slots (fuse = 2)
+    int cw = 0;                        // converter warps (fuse = 1, 2): 4 or 8
 };
 
 struct TcPlan {
@@ -147,11 +148,11 @@ struct TcPlan {
 
 namespace {
 
-int tc_threads(const TcConfig& c) { return 64 + 32 * c.ew + (c.fuse ? 32 * FBC_TC_CONV_WARPS : 0); }
+int tc_threads(const TcConfig& c) { return 64 + 32 * c.ew + 32 * c.cw; }
 
 std::string tc_kernel_name(int nc, int split, int fw, const TcConfig& c) {
     char b[96];
-    snprintf(b, sizeof b, "fbc_tc_c%d_s%d_f%d_b%d_e%d_z%d_k%d", nc, split, fw, c.bt, c.ew, c.fuse, c.cs);
+    snprintf(b, sizeof b, "fbc_tc_c%d_s%d_f%d_b%d_e%d_z%d_w%d", nc, split, fw, c.bt, c.ew, c.fuse, c.cw);
     return b;
 }
 
@@ -165,7 +166,7 @@ std::string tc_kernel_source(int nc, int split, int fw, const TcConfig& c) {
     o << "extern \"C\" __global__ void __launch_bounds__(" << tc_threads(c) << ", 1) "
       << tc_kernel_name(nc, split, fw, c) << "(const __grid_constant__ FbcTcParams P) {\n"
       << "  fbc_tc_corr_body<" << nc << "," << split << "," << fw << "," << c.bt << "," << c.ew << ","
-      << c.fuse << "," << c.cs << ">(P);\n}\n";
+      << c.fuse << "," << c.cw << ">(P);\n}\n";
     return o.str();
 }
 
@@ -176,11 +177,12 @@ void filter_tiles(int N, int ntmax, int* nt, int* ntn) {
     *nt = ((npad + *ntn - 1) / *ntn + 15) / 16 * 16;
 }
 
-bool fuse_ok(int D, int nc, int fw) {
-    // x is read as float4 and a converter thread holds at most FBC_TC_CONV_ITEMS
-    // 32-byte chunks of a slab row
-    return (D % 4) == 0 && nc <= 4 &&
-           (kTileM + fw - 1) * nc <= FBC_TC_CONV_ITEMS * FBC_TC_CONV_WARPS * 32;
+bool fuse_ok(int fuse, int cw, int D, int nc, int fw) {
+    // x is read as float4 (and copied in 16-byte units); fuse = 1 holds a slab row
+    // in at most FBC_TC_CONV_ITEMS 32-byte chunks per converter thread
+    if (fuse == 0) return cw == 0;
+    if ((D % 4) != 0 || (cw != 4 && cw != 8)) return false;
+    return fuse == 2 || (nc <= 4 && (kTileM + fw - 1) * nc <= FBC_TC_CONV_ITEMS * cw * 32);
 }
 
 // Lay out shared memory, pipeline depths and the workspace for one configuration.
@@ -195,32 +197,33 @@ bool tc_layout(TcPlan* p, const TcConfig& c, bool commit) {
     const int halves = p->split ? 2 : 1;
     const uint32_t a_slot = (uint32_t)align_up((size_t)nc * lp * 16 * halves, 128);
     if (c.bt < 1 || c.bt > p->fw || (c.ew != 4 && c.ew != 8)) return false;
-    if (c.cs != 1 && c.cs != 2 && c.cs != 4) return false;
-    if (c.fuse && !fuse_ok(p->D, nc, p->fw)) return false;
+    if (c.fuse < 0 || c.fuse > 2 || !fuse_ok(c.fuse, c.cw, p->D, nc, p->fw)) return false;
+    if ((c.fuse == 2) != (c.nr > 0) || c.nr > 4) return false;
     const uint32_t b_stage = (uint32_t)align_up((size_t)c.bt * nc * nt * 16 * halves, 128);
-    if (c.na < 2 || c.nb < 2) return false;
-    const size_t need = (size_t)c.na * a_slot + (size_t)c.nb * b_stage + 512;
+    const uint32_t raw_slot = (uint32_t)align_up((size_t)(kTileM + p->fw - 1) * p->D * 4, 128);
+    if (c.na < 2 || c.nb < 2 || (c.fuse == 2 && c.nr < 2)) return false;
+    const size_t need = (size_t)c.na * a_slot + (size_t)c.nb * b_stage + (size_t)c.nr * raw_slot + 512;
     if (need > kSmemMax) return false;
     if (!commit) return true;
     p->cfg = c;
     FbcTcParams& k = p->kp;
     k = FbcTcParams{};
-    // zero-input pixel tiles of a partial cluster group read up to (cs - 1) tiles
-    // past the last one: pad the x planes for them
-    k.npix_pad = (long long)align_up((size_t)p->H * p->W + (size_t)c.cs * kTileM + p->fw + 8, 8);
+    k.npix_pad = (long long)align_up((size_t)p->H * p->W + kTileM + p->fw + 8, 8);
     k.npix = (long long)p->H * p->W;
     k.W = p->W; k.Ho = Ho; k.Wo = Wo; k.N = p->N; k.D = p->D;
     k.fh = p->fh; k.nt = nt; k.ntn = ntn; k.mtiles = mtiles;
-    k.mgroups = (mtiles + c.cs - 1) / c.cs;
     k.lp = lp; k.na = c.na; k.nb = c.nb;
     k.a_slot = a_slot; k.b_stage = b_stage;
     k.a_tx = (uint32_t)(nc * (kTileM + p->fw - 1) * 16 * halves);
     k.a_off = 0;
     k.b_off = (uint32_t)(c.na * a_slot);
-    // unfused A look-ahead needs a free slot beyond the one the MMAs of the
-    // previous row still read: three A slots
-    k.alook = c.na >= 3 ? 1 : 0;
-    k.bar_off = (uint32_t)(k.b_off + c.nb * b_stage);
+    // A-side look-ahead: pre-split slabs need a free A slot beyond the one the
+    // MMAs of the previous row still read (three slots); raw rows run nr - 1 ahead
+    k.alook = c.fuse == 2 ? c.nr - 1 : (c.na >= 3 ? 1 : 0);
+    k.nr = c.nr;
+    k.raw_off = (uint32_t)(k.b_off + c.nb * b_stage);
+    k.raw_slot = c.nr ? raw_slot : 0;
+    k.bar_off = (uint32_t)(k.raw_off + (size_t)c.nr * raw_slot);
     k.epi = p->epi; k.lo = p->lo; k.hi = p->hi;
     k.wait_ns = p->wait_ns;
     k.drop_b = p->drop_b;
@@ -244,10 +247,8 @@ bool tc_layout(TcPlan* p, const TcConfig& c, bool commit) {
     const long long wblocks = ((long long)ntn * p->fh * p->fw * nc * nt + 255) / 256;
     if (c.fuse) sp.xblocks = 0;   // x is converted inside the correlation kernel
     p->split_blocks = (int)(sp.xblocks + wblocks);
-    // one CTA per SM (the 512 TMEM columns); clusters: refined by the occupancy
-    // query once the kernel exists
-    const int ngroups = k.mgroups * ntn;
-    p->grid = c.cs * std::min(ngroups, std::max(1, p->sm_count / c.cs));
+    // one CTA per SM (the 512 TMEM columns)
+    p->grid = std::min(mtiles * ntn, std::max(1, p->sm_count));
     return true;
 }
 
@@ -262,42 +263,46 @@ size_t tc_ws_need(TcPlan* p, const TcConfig& c) {
 }
 
 std::vector<TcConfig> tc_candidate_configs(TcPlan* p) {
-    // widest filter tile first; within it, fused before unfused, clusters of 2
-    // first, taps per stage from the most (fewest barrier handoffs) down, each
-    // with the deepest B ring that fits
+    // widest filter tile first; within it raw-ring conversion, register
+    // conversion, pre-pass; taps per stage from the most (fewest copies and
+    // barrier handoffs) down, each with the deepest B ring that fits
     std::vector<TcConfig> out;
     const int widths[] = {256, 128};
     for (int ntmax : widths) {
         if (ntmax == 128 && p->N <= 128) continue;
-        for (int fuse = fuse_ok(p->D, p->nc, p->fw) ? 1 : 0; fuse >= 0; --fuse)
-            for (int cs : {2, 4, 1})
-                for (int bt = std::min(p->fw, 5); bt >= 1; --bt)
-                    for (int ew : {8, 4})
-                        for (int na = 2; na <= 3; ++na) {
-                            int best = 0;
-                            for (int nb = 2; nb <= 10; ++nb)
-                                if (tc_layout(p, TcConfig{na, nb, ntmax, bt, ew, fuse, cs}, false)) best = nb;
-                            if (best) out.push_back(TcConfig{na, best, ntmax, bt, ew, fuse, cs});
-                        }
+        for (int fuse = 2; fuse >= 0; --fuse)
+            for (int cw : fuse ? std::vector<int>{8, 4} : std::vector<int>{0}) {
+                if (!fuse_ok(fuse, cw, p->D, p->nc, p->fw)) continue;
+                for (int nr : fuse == 2 ? std::vector<int>{3, 2} : std::vector<int>{0})
+                    for (int bt = std::min(p->fw, 5); bt >= 1; --bt)
+                        for (int ew : {8, 4})
+                            for (int na = 2; na <= 3; ++na) {
+                                int best = 0;
+                                for (int nb = 2; nb <= 12; ++nb)
+                                    if (tc_layout(p, TcConfig{na, nb, ntmax, bt, ew, fuse, nr, cw}, false)) best = nb;
+                                if (best) out.push_back(TcConfig{na, best, ntmax, bt, ew, fuse, nr, cw});
+                            }
+            }
     }
     return out;
 }
 
 std::string format_spec(const TcConfig& c) {
     char b[96];
-    snprintf(b, sizeof b, "tcgen05:na=%d,nb=%d,nt=%d,bt=%d,ew=%d,fz=%d,cs=%d", c.na, c.nb, c.ntmax, c.bt,
-             c.ew, c.fuse, c.cs);
+    snprintf(b, sizeof b, "tcgen05:na=%d,nb=%d,nt=%d,bt=%d,ew=%d,fz=%d,nr=%d,cw=%d", c.na, c.nb, c.ntmax,
+             c.bt, c.ew, c.fuse, c.nr, c.cw);
     return b;
 }
 
 bool parse_tc_spec(const std::string& s, TcConfig* c) {
     TcConfig t;
     int used = 0;
-    const int n = sscanf(s.c_str(), "tcgen05:na=%d,nb=%d,nt=%d,bt=%d,ew=%d,fz=%d,cs=%d%n", &t.na, &t.nb,
-                         &t.ntmax, &t.bt, &t.ew, &t.fuse, &t.cs, &used);
-    if (n != 7 || used != (int)s.size()) return false;
-    if (t.fuse < 0 || t.fuse > 1 || (t.ew != 4 && t.ew != 8)) return false;
-    if (t.cs != 1 && t.cs != 2 && t.cs != 4) return false;
+    const int n = sscanf(s.c_str(), "tcgen05:na=%d,nb=%d,nt=%d,bt=%d,ew=%d,fz=%d,nr=%d,cw=%d%n", &t.na, &t.nb,
+                         &t.ntmax, &t.bt, &t.ew, &t.fuse, &t.nr, &t.cw, &used);
+    if (n != 8 || used != (int)s.size()) return false;
+    if ((t.fuse == 0) != (t.cw == 0) || (t.cw != 0 && t.cw != 4 && t.cw != 8)) return false;
+    if (t.fuse < 0 || t.fuse > 2 || (t.ew != 4 && t.ew != 8)) return false;
+    if ((t.fuse == 2) != (t.nr > 0) || t.nr < 0 || t.nr > 4) return false;
     if (t.ntmax != 256 && t.ntmax != 128 && t.ntmax != 64) return false;
     *c = t;
     return true;
@@ -350,15 +355,6 @@ fbcorr_status_t tc_set_spec(TcPlan* p, const std::string& spec) {
     Kernel k;
     FBC_TRY(tc_kernel(p, c, &k));
     tc_layout(p, c, true);
-    if (c.cs > 1) {
-        // clusters are placed whole on one GPC: ask how many fit at once
-        k.smem = p->smem;
-        int maxc = 0;
-        FBC_TRY(kernel_max_clusters(k, c.cs, &maxc));
-        if (maxc < 1)
-            return set_error(FBCORR_ERR_UNSUPPORTED, "no cluster of %d CTAs of spec '%s' fits", c.cs, spec.c_str());
-        p->grid = c.cs * std::min(p->kp.mgroups * p->kp.ntn, maxc);
-    }
     return FBCORR_OK;
 }
 
@@ -383,8 +379,8 @@ fbcorr_status_t tc_plan_create(TcPlan** out, int H, int W, int D, int N, int fh,
         return set_error(FBCORR_ERR_UNSUPPORTED, "shape needs more shared memory than one SM has");
     }
     for (const auto& c : cands) p->ws_bytes = std::max(p->ws_bytes, tc_ws_need(p, c));
-    // default: the first candidate (widest filter tile, fused where possible,
-    // most taps per stage, two A slots, deepest B ring)
+    // default: the first candidate (widest filter tile, raw-ring conversion where
+    // possible, most taps per stage, two A slots, deepest B ring)
     const fbcorr_status_t s = tc_set_spec(p, format_spec(cands.front()));
     if (s != FBCORR_OK) {
         delete p;
@@ -407,7 +403,7 @@ std::string tc_describe(const TcPlan* p) {
     o << "{\"precision\":\"" << (p->split ? "bf16x3" : "bf16") << "\",\"mma\":\"128x" << p->kp.nt
       << "x16\",\"filter_tiles\":" << p->kp.ntn << ",\"tiles\":" << p->kp.mtiles * p->kp.ntn
       << ",\"smem\":" << p->smem << ",\"grid\":" << p->grid << ",\"threads\":" << tc_threads(p->cfg)
-      << ",\"cluster\":" << p->cfg.cs << ",\"kernel\":\"" << tc_kernel_name(p->nc, p->split, p->fw, p->cfg) << "\"}";
+      << ",\"kernel\":\"" << tc_kernel_name(p->nc, p->split, p->fw, p->cfg) << "\"}";
     return o.str();
 }
 
@@ -436,7 +432,7 @@ fbcorr_status_t tc_forward(TcPlan* p, const float* x, const float* w, float* y, 
     kp.xraw = x;
     if (ev_start) FBC_CUDA(cudaEventRecord(ev_start, s));
     void* args[] = {&kp};
-    FBC_TRY(launch_cluster(k, dim3(p->grid), p->cfg.cs, args, s));
+    FBC_TRY(launch(k, dim3(p->grid), args, s));
     if (ev_stop) FBC_CUDA(cudaEventRecord(ev_stop, s));
     return FBCORR_OK;
 }
@@ -446,7 +442,7 @@ fbcorr_status_t tc_rtcg_check(int D, int fw, const std::string& spec, std::strin
     if (!parse_tc_spec(spec, &c)) return set_error(FBCORR_ERR_INVALID_ARG, "unknown tcgen05 spec '%s'", spec.c_str());
     const int nc = (D + 15) / 16 * 16 / 8;
     if (nc > 8) return set_error(FBCORR_ERR_UNSUPPORTED, "tensor-core modes support depth D <= 64");
-    if (c.fuse && !fuse_ok(D, nc, fw))
+    if (!fuse_ok(c.fuse, c.cw, D, nc, fw))
         return set_error(FBCORR_ERR_UNSUPPORTED, "fused conversion does not fit this shape");
     if (c.bt < 1 || c.bt > fw) return set_error(FBCORR_ERR_UNSUPPORTED, "taps per stage out of range");
     for (int split = 0; split <= 1; ++split)

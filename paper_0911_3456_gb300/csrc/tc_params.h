@@ -8,7 +8,6 @@
 #define FBC_TC_TILE_M 128       // output pixels per tile (MMA M)
 #define FBC_TC_ACC_COLS 256     // TMEM columns per accumulator (MMA N <= 256)
 #define FBC_TC_TMEM_COLS 512    // two accumulators
-#define FBC_TC_CONV_WARPS 4     // FP32 -> BF16 converter warps of the fused mode
 #define FBC_TC_CONV_ITEMS 5     // 32-byte x chunks per converter thread and slab row
 
 // Error codes written to the host-mapped error word when a bounded wait expires.
@@ -30,16 +29,17 @@ struct FbcTcParams {
     unsigned long long wait_ns; // bound of every mbarrier wait
     int W, Ho, Wo, N, D;
     int fh, nt, ntn, mtiles;
-    int mgroups;                // groups of CS pixel tiles: ceil(mtiles / CS)
     int lp;                     // pixels per chunk plane of an A slot
     int na, nb;                 // A slots, B stages
-    int alook;                  // unfused: rows by which the A slabs run ahead of the B stages
+    int alook;                  // rows by which the A side (slabs or raw rows) runs ahead of the B stages
+    int nr;                     // raw-row slots (FUSE = 2)
     int epi;                    // 0: none, 1: clamp to [lo, hi]
     float lo, hi;
     int drop_b;                 // fault injection: B load index whose copy is skipped (-1: none)
     unsigned int a_slot, b_stage;   // bytes per A slot / B stage (hi [+ lo])
     unsigned int a_tx;              // bytes copied per A slot (unfused)
     unsigned int a_off, b_off, bar_off;
+    unsigned int raw_off, raw_slot;   // raw-row ring (FUSE = 2): offset, bytes per slot
 };
 
 #endif

@@ -130,11 +130,11 @@ def test_explicit_tile_specs_compile(lib, spec):
 
 
 @pytest.mark.parametrize("D,f,spec", [
-    (32, 5, b"tcgen05:na=2,nb=4,nt=256,bt=5,ew=4,fz=1,cs=2"),    # the precision workload, fused
-    (32, 5, b"tcgen05:na=3,nb=3,nt=256,bt=3,ew=8,fz=0,cs=2"),    # two stages, the second partial
-    (8, 9, b"tcgen05:na=2,nb=4,nt=128,bt=2,ew=4,fz=1,cs=4"),     # paper row 1 depth, odd last stage
-    (48, 7, b"tcgen05:na=2,nb=4,nt=256,bt=4,ew=8,fz=0,cs=2"),    # six chunk planes, pre-pass only
-    (64, 13, b"tcgen05:na=2,nb=2,nt=256,bt=1,ew=4,fz=0,cs=1"),   # the deepest supported depth
+    (32, 5, b"tcgen05:na=2,nb=4,nt=256,bt=5,ew=4,fz=1,nr=0,cw=4"),    # the precision workload, converters from registers
+    (32, 5, b"tcgen05:na=3,nb=3,nt=256,bt=3,ew=8,fz=2,nr=3,cw=8"),    # raw-row ring; two stages, the second partial
+    (8, 9, b"tcgen05:na=2,nb=4,nt=128,bt=2,ew=4,fz=1,nr=0,cw=8"),     # paper row 1 depth, odd last stage
+    (48, 7, b"tcgen05:na=2,nb=4,nt=256,bt=4,ew=8,fz=2,nr=2,cw=8"),    # six chunk planes, raw-row ring
+    (64, 13, b"tcgen05:na=2,nb=2,nt=256,bt=1,ew=4,fz=0,nr=0,cw=0"),   # the deepest supported depth, pre-pass
 ])
 def test_tensor_core_kernels_compile(lib, D, f, spec):
     """The run-time generated tcgen05 kernel of a spec compiles for sm_103a in
@@ -145,11 +145,13 @@ def test_tensor_core_kernels_compile(lib, D, f, spec):
 
 
 @pytest.mark.parametrize("D,f,spec,status", [
-    (48, 7, b"tcgen05:na=2,nb=4,nt=256,bt=2,ew=4,fz=1,cs=2", 3),   # fused needs D <= 32
-    (32, 3, b"tcgen05:na=2,nb=4,nt=256,bt=4,ew=4,fz=0,cs=2", 3),   # more taps per stage than fw
-    (32, 5, b"tcgen05:na=2,nb=4,nt=256,bt=2,ew=6,fz=0,cs=2", 1),   # epilogue warps must be 4 or 8
-    (32, 5, b"tcgen05:na=2,nb=4,nt=256,bt=2,ew=4,fz=0", 1),   # no cluster size: not a spec of this kernel
-    (32, 5, b"tcgen05:na=2,nb=4,nt=256,bt=2,ew=4,fz=0,cs=3", 1),   # clusters of 1, 2 or 4
+    (48, 7, b"tcgen05:na=2,nb=4,nt=256,bt=2,ew=4,fz=1,nr=0,cw=8", 3),   # register conversion needs D <= 32
+    (30, 7, b"tcgen05:na=2,nb=4,nt=256,bt=2,ew=4,fz=2,nr=2,cw=8", 3),   # in-kernel conversion needs D % 4 == 0
+    (32, 3, b"tcgen05:na=2,nb=4,nt=256,bt=4,ew=4,fz=0,nr=0,cw=0", 3),   # more taps per stage than fw
+    (32, 5, b"tcgen05:na=2,nb=4,nt=256,bt=2,ew=6,fz=0,nr=0,cw=0", 1),   # epilogue warps must be 4 or 8
+    (32, 5, b"tcgen05:na=2,nb=4,nt=256,bt=2,ew=4,fz=0", 1),        # missing field: not a spec of this kernel
+    (32, 5, b"tcgen05:na=2,nb=4,nt=256,bt=2,ew=4,fz=2,nr=0,cw=8", 1),   # the raw ring needs slots
+    (32, 5, b"tcgen05:na=2,nb=4,nt=256,bt=2,ew=4,fz=1,nr=0,cw=0", 1),   # in-kernel conversion needs converter warps
 ])
 def test_tensor_core_spec_refusals(lib, D, f, spec, status):
     log = ctypes.create_string_buffer(1 << 16)

@@ -167,9 +167,9 @@ def test_split_beats_bf16_and_approaches_fp32():
 def test_every_tensor_core_configuration_matches(mode):
     """Every configuration the auto-tuner may pick (ring depths, filter-tile
     width, taps per B stage -- including a last stage with fewer taps --,
-    epilogue warps, fused or pre-pass conversion of x, clusters of 1, 2 or 4
-    CTAs sharing the B stages) gives the same result on integer inputs, bit for
-    bit."""
+    epilogue warps, conversion of x by the pre-pass, by converter warps from
+    global memory or from a ring of raw rows) gives the same result on integer
+    inputs, bit for bit."""
     torch = torch_cuda()
     from paper_0911_3456_gb300 import _capi as C
     from paper_0911_3456_gb300.api import Plan
@@ -177,22 +177,21 @@ def test_every_tensor_core_configuration_matches(mode):
     ref = oracle.fwd(wl.x, wl.w)
     p = Plan(wl.x.shape, wl.w.shape, mode)
     x, w = dev(wl.x, torch), dev(wl.w, torch)
-    # every generated kernel (taps per stage x epilogue warps x fused x cluster
-    # size), each with one of four ring / filter-tile shapes, plus ring-depth
-    # variations of one kernel; 19 x 140 outputs give 21 pixel tiles, so clusters
-    # of 2 and 4 end on a partial group
+    # every generated kernel (taps per stage x epilogue warps x conversion of x),
+    # each with one of four ring / filter-tile shapes, plus ring-depth variations
+    # of one kernel
     rings = [(2, 2, 256), (3, 4, 128), (2, 3, 128), (3, 2, 256)]
     specs = set()
     k = 0
     for bt in (1, 2, 3, 5):
         for ew in (4, 8):
-            for fz in (0, 1):
-                for cs in (1, 2, 4):
-                    na, nb, nt = rings[k % len(rings)]
-                    k += 1
-                    specs.add(f"tcgen05:na={na},nb={nb},nt={nt},bt={bt},ew={ew},fz={fz},cs={cs}")
+            for fz, nr in ((0, 0), (1, 0), (2, 2), (2, 3)):
+                na, nb, nt = rings[k % len(rings)]
+                cw = 0 if fz == 0 else (4, 8)[k % 2]
+                k += 1
+                specs.add(f"tcgen05:na={na},nb={nb},nt={nt},bt={bt},ew={ew},fz={fz},nr={nr},cw={cw}")
     for na, nb, nt in [(2, 4, 256), (3, 3, 256), (2, 2, 128), (3, 4, 256)]:
-        specs.add(f"tcgen05:na={na},nb={nb},nt={nt},bt=2,ew=8,fz=1,cs=2")
+        specs.add(f"tcgen05:na={na},nb={nb},nt={nt},bt=2,ew=8,fz=2,nr=2,cw=8")
     ran = 0
     for sp in sorted(specs):
         try:
@@ -203,36 +202,43 @@ def test_every_tensor_core_configuration_matches(mode):
         y = host(p.forward(x, w))
         assert np.array_equal(y, ref), sp
         ran += 1
-    assert ran >= 32
+    assert ran >= 24
 
 
 @pytest.mark.parametrize("mode", ["bf16", "bf16x3"])
 @pytest.mark.parametrize("shape", [(20, 150, 16, 16, 3, 3), (37, 45, 4, 20, 4, 2), (18, 260, 28, 40, 7, 7),
                                    (9, 9, 12, 3, 9, 9)], ids=lambda s: "x".join(map(str, s)))
 def test_fused_conversion_matches_prepass(mode, shape):
-    """x converted inside the kernel (fz=1) and by the pre-pass (fz=0) give the
-    same bits, including the zero-filled tail past the end of the image."""
+    """x converted inside the kernel (fz=1 from global memory, fz=2 from a ring of
+    raw rows) and by the pre-pass (fz=0) give the same bits, including the
+    zero-filled tail past the end of the image."""
     torch = torch_cuda()
     from paper_0911_3456_gb300.api import Plan
     wl = inputs.random_case(1800, *shape)
     p = Plan(wl.x.shape, wl.w.shape, mode)
     x, w = dev(wl.x, torch), dev(wl.w, torch)
     outs = {}
-    for fz in (0, 1):
-        p.set_variant(f"tcgen05:na=2,nb=2,nt=256,bt=1,ew=4,fz={fz},cs=1")
+    for fz, nr, cw in ((0, 0, 0), (1, 0, 8), (2, 2, 4)):
+        p.set_variant(f"tcgen05:na=2,nb=2,nt=256,bt=1,ew=4,fz={fz},nr={nr},cw={cw}")
         outs[fz] = host(p.forward(x, w))
     assert np.array_equal(outs[0], outs[1])
+    assert np.array_equal(outs[0], outs[2])
     assert_within_bound(outs[1], wl.x, wl.w, mode)
 
 
 def test_fused_conversion_limits():
-    """The fused conversion needs D % 4 == 0 and at most 32 channels; other
-    depths take the pre-pass, and a fused spec for them is refused."""
+    """Conversion inside the kernel needs D % 4 == 0 (x is read in 16-byte units);
+    from registers (fz=1) also at most 32 channels.  Other depths take the
+    pre-pass, and a spec that does not fit is refused."""
     torch_cuda()
     from paper_0911_3456_gb300 import _capi as C
     from paper_0911_3456_gb300.api import Plan
-    for shape in ((16, 40, 48), (16, 40, 6)):
-        p = Plan(shape, (8, 3, 3, shape[2]), "bf16")
-        assert ",fz=0," in p.info()["fwd"]["spec"]
+    p = Plan((16, 40, 6), (8, 3, 3, 6), "bf16")
+    assert ",fz=0," in p.info()["fwd"]["spec"]
+    for fz, nr in ((1, 0), (2, 2)):
         with pytest.raises(C.FbcorrError):
-            p.set_variant("tcgen05:na=2,nb=2,nt=256,bt=1,ew=4,fz=1,cs=1")
+            p.set_variant(f"tcgen05:na=2,nb=2,nt=256,bt=1,ew=4,fz={fz},nr={nr},cw=8")
+    p = Plan((16, 40, 48), (8, 3, 3, 48), "bf16")
+    assert ",fz=2," in p.info()["fwd"]["spec"]
+    with pytest.raises(C.FbcorrError):
+        p.set_variant("tcgen05:na=2,nb=2,nt=256,bt=1,ew=4,fz=1,nr=0,cw=8")
