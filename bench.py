@@ -302,6 +302,23 @@ def sampled_error(y_gpu_rows, ref_rows, scale=None):
     return float(d / s)
 
 
+def measured_traffic(info, workload):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of the
+    plan's correlation kernel, from profiles/traffic.json: entries are keyed by the
+    hash of the generated kernel source, so a kernel changed since its capture
+    (or a different tuned variant) finds none and reports null."""
+    fwd = info.get("fwd", {})
+    h = fwd.get("source_hash") or fwd.get("detail", {}).get("source_hash")
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles", "traffic.json")
+    if not h or not os.path.exists(path):
+        return None, None
+    with open(path) as f:
+        entry = json.load(f).get(h)
+    if not entry or entry.get("workload") != workload:
+        return None, None
+    return int(entry["dram_bytes_per_launch"]), entry.get("profile")
+
+
 def run_ours(args):
     import torch
     from paper_0911_3456_gb300 import inputs
@@ -322,7 +339,9 @@ def run_ours(args):
             continue
         try:
             p = Plan(wl.x.shape, wl.w.shape, m, wl.clamp)
-            if not args.no_tune:
+            if args.spec and m == mode:
+                p.set_variant(args.spec)
+            elif not args.no_tune:
                 p.autotune()
             plans[m] = p
         except Exception as e:   # a mode this build cannot run is reported, not hidden
@@ -356,9 +375,12 @@ def run_ours(args):
                 "peak_note": f"cuBLAS bf16 {'sustained' if args.steps * ms > 1000 else 'burst'}, "
                              f"{peaks['source']}"}
     achieved = flops / (kern_avg * 1e-3) / 1e12 if kern_avg else None
+    traffic, traffic_src = measured_traffic(info, wl.name)
     roof.update({"achieved": achieved, "frac": (achieved / peak) if achieved else None,
-                 "traffic": None, "kernel_ms": kern_avg,
+                 "traffic": traffic, "kernel_ms": kern_avg,
                  "algorithmic_flops_per_launch": flops})
+    if traffic_src:
+        roof["traffic_profile"] = traffic_src
     if mode == "bf16x3" and achieved:
         roof["tensor_issued_tflops"] = 3 * achieved
 
@@ -542,6 +564,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle leg")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--spec", default=None,
+                    help="forward variant of the headline plan instead of auto-tuning (profiling runs)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--workload", choices=["precision", "precision384", "paper_row1"],
                     default="precision")

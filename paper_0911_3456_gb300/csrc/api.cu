@@ -599,7 +599,8 @@ fbcorr_status_t fbcorr_plan_info(fbcorr_plan_t p, char* buf, size_t cap) {
       << kind_name(p->fwd_kind) << "\",\"source\":\"" << p->fwd_source << "\"";
     if (p->fwd_kind == VarKind::Direct) {
         o << ",\"spec\":\"" << direct_tile_spec(p->fwd_tile) << "\",\"smem\":" << p->fwd_kernel.smem
-          << ",\"threads\":" << p->fwd_kernel.threads << ",\"kernel\":\"" << p->fwd_kernel.name << "\"";
+          << ",\"threads\":" << p->fwd_kernel.threads << ",\"kernel\":\"" << p->fwd_kernel.name
+          << "\",\"source_hash\":\"" << hex64(p->fwd_kernel.src_hash) << "\"";
     } else if (p->fwd_kind == VarKind::Default) {
         o << ",\"spec\":\"default\"";
     } else if (p->tc) {

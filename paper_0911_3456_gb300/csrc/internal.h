@@ -55,7 +55,9 @@ struct Kernel {
     int threads = 0;
     size_t smem = 0;
     std::string name;
+    unsigned long long src_hash = 0;   // of the generated source and compile options (the cubin cache key)
 };
+std::string hex64(unsigned long long v);
 
 // Compile `src` (with `name` as the extern "C" kernel) for sm_103a, using the
 // on-disk cubin cache, load it into the current context and return a handle.

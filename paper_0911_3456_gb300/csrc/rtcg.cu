@@ -306,7 +306,14 @@ fbcorr_status_t rtcg_kernel(const std::string& src, const std::string& name, siz
     out->threads = threads;
     out->smem = smem;
     out->name = name;
+    out->src_hash = h;
     return FBCORR_OK;
+}
+
+std::string hex64(unsigned long long v) {
+    char b[32];
+    snprintf(b, sizeof b, "%016llx", v);
+    return b;
 }
 
 fbcorr_status_t launch(const Kernel& k, dim3 grid, void** args, cudaStream_t stream) {

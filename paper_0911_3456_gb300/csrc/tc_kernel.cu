@@ -403,7 +403,10 @@ std::string tc_describe(const TcPlan* p) {
     o << "{\"precision\":\"" << (p->split ? "bf16x3" : "bf16") << "\",\"mma\":\"128x" << p->kp.nt
       << "x16\",\"filter_tiles\":" << p->kp.ntn << ",\"tiles\":" << p->kp.mtiles * p->kp.ntn
       << ",\"smem\":" << p->smem << ",\"grid\":" << p->grid << ",\"threads\":" << tc_threads(p->cfg)
-      << ",\"kernel\":\"" << tc_kernel_name(p->nc, p->split, p->fw, p->cfg) << "\"}";
+      << ",\"kernel\":\"" << tc_kernel_name(p->nc, p->split, p->fw, p->cfg) << "\"";
+    auto it = p->kernels.find(tc_kernel_name(p->nc, p->split, p->fw, p->cfg));
+    if (it != p->kernels.end()) o << ",\"source_hash\":\"" << hex64(it->second.src_hash) << "\"";
+    o << "}";
     return o.str();
 }
 
