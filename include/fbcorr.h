@@ -109,6 +109,24 @@ fbcorr_status_t fbcorr_plan_workspace_size(fbcorr_plan_t plan, size_t* fwd_bytes
 fbcorr_status_t fbcorr_forward(fbcorr_plan_t plan, const float* x, const float* w, float* y,
                                void* ws, size_t ws_bytes, fbcorr_stream_t stream);
 
+/* The forward from HOST buffers, with the host<->device transfers overlapped
+ * (end-to-end use: inputs and result in host memory).  x_host [H][W][D],
+ * w_host [N][fh][fw][D] and y_host [H'][W'][N] are host pointers; page-locked
+ * memory (cudaHostAlloc / cudaHostRegister) lets the copies run asynchronously,
+ * pageable memory works but serialises them.  The output rows are split into
+ * `bands` bands of a multiple of 4 rows (0: automatic, 8): band b's new input
+ * rows are copied in on an internal stream, the band is correlated on `stream`
+ * by a plan of the band's shape (tuned when this plan is tuned), and its output
+ * rows are copied back on a second internal stream while the next band runs.
+ * Stream-ordered: returns once everything is enqueued; y_host is complete when
+ * `stream` reaches the point of the call.  The first call (and a call with a
+ * different band count) allocates the plan-owned device copies of x, w and y,
+ * the band plans and their workspace; later calls allocate nothing.  Not
+ * capturable (internal streams).  Errors as fbcorr_forward; a bounded-wait
+ * timeout of a band kernel is reported by fbcorr_plan_device_status. */
+fbcorr_status_t fbcorr_forward_host(fbcorr_plan_t plan, const float* x_host, const float* w_host,
+                                    float* y_host, int bands, fbcorr_stream_t stream);
+
 /* Gradients of L from g = dL/dy (shape of y):
  *   dx[p][q][d]    = sum_{n,i,j} g~[p-i][q-j][n] * w[n][i][j][d]   (zero outside the output)
  *   dw[n][i][j][d] = sum_{p,q}   g~[p][q][n]     * x[p+i][q+j][d]

@@ -54,6 +54,7 @@ PROTOTYPES = {
     "fbcorr_plan_out_shape": (_st, [_vp, I64_3]),
     "fbcorr_plan_workspace_size": (_st, [_vp, ctypes.POINTER(_sz), ctypes.POINTER(_sz)]),
     "fbcorr_forward": (_st, [_vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "fbcorr_forward_host": (_st, [_vp, _vp, _vp, _vp, ctypes.c_int, _vp]),
     "fbcorr_backward": (_st, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "fbcorr_autotune": (_st, [_vp, _vp]),
     "fbcorr_plan_set_variant": (_st, [_vp, ctypes.c_char_p]),

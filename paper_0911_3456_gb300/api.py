@@ -33,6 +33,15 @@ def _check_tensor(t: torch.Tensor, name: str, shape=None) -> None:
         raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
 
 
+def _check_host_tensor(t: torch.Tensor, name: str, shape) -> None:
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise ValueError(f"{name} must be a CPU torch.Tensor")
+    if t.dtype != torch.float32 or not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous float32")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+
+
 def _vp(t: Optional[torch.Tensor]) -> ctypes.c_void_p:
     return ctypes.c_void_p(t.data_ptr() if t is not None else 0)
 
@@ -105,6 +114,20 @@ class Plan:
         nbytes = ws.numel() * ws.element_size() if ws is not None else 0
         C.call("fbcorr_forward", self._h, _vp(x), _vp(w), _vp(y), _vp(ws), nbytes,
                _stream_handle(stream))
+        return y
+
+    def forward_host(self, x: torch.Tensor, w: torch.Tensor, y: Optional[torch.Tensor] = None,
+                     bands: int = 0, stream=None) -> torch.Tensor:
+        """The forward from host (CPU) tensors with overlapped transfers
+        (fbcorr_forward_host).  Page-locked tensors (``pin_memory()``) let the
+        copies overlap the compute; the result is complete once ``stream``
+        (default: the current stream) reaches this call."""
+        for t, name, shape in ((x, "x", self.in_shape), (w, "w", self.filt_shape)):
+            _check_host_tensor(t, name, shape)
+        if y is None:
+            y = torch.empty(self.out_shape, dtype=torch.float32).pin_memory()
+        _check_host_tensor(y, "y", self.out_shape)
+        C.call("fbcorr_forward_host", self._h, _vp(x), _vp(w), _vp(y), int(bands), _stream_handle(stream))
         return y
 
     def backward(self, x: torch.Tensor, w: torch.Tensor, g: torch.Tensor,

@@ -353,6 +353,7 @@ fbcorr_status_t fbcorr_plan_destroy(fbcorr_plan_t p) {
     if (!p) return FBCORR_OK;
     for (auto e : p->prof_start) cudaEventDestroy(e);
     for (auto e : p->prof_stop) cudaEventDestroy(e);
+    hostpipe_destroy(p->hostpipe);
     if (p->tc) tc_plan_destroy(p->tc);
     if (p->err_host) cudaFreeHost(p->err_host);
     delete p;
@@ -626,7 +627,9 @@ fbcorr_status_t fbcorr_plan_device_status(fbcorr_plan_t p, int clear) {
     if (!p) return set_error(FBCORR_ERR_INVALID_ARG, "NULL plan");
     const int v = p->err_host ? *(volatile int*)p->err_host : 0;
     if (clear && p->err_host) *(volatile int*)p->err_host = 0;
+    const fbcorr_status_t bands = hostpipe_device_status(p->hostpipe, clear);
     if (v != 0) return set_error(FBCORR_ERR_TIMEOUT, "a kernel gave up a bounded wait (code %d)", v);
+    if (bands != FBCORR_OK) return set_error(FBCORR_ERR_TIMEOUT, "a band kernel of fbcorr_forward_host gave up a bounded wait");
     return FBCORR_OK;
 }
 

@@ -150,6 +150,11 @@ cudaError_t launch_default_dw(const float* x, const float* g, const float* m, fl
                               cudaStream_t s);
 cudaError_t launch_dw_reduce(const float* part, float* dw, int S, long long E, cudaStream_t s);
 
+// ---- forward from host buffers (host_pipeline.cu) ----------------------------------
+struct HostPipe;
+void hostpipe_destroy(HostPipe* hp);
+fbcorr_status_t hostpipe_device_status(HostPipe* hp, int clear);   // of the band plans
+
 // ---- tensor-core path (tc_kernel.cu) -----------------------------------------------
 struct TcPlan;   // opaque
 fbcorr_status_t tc_plan_create(TcPlan** out, int H, int W, int D, int N, int fh, int fw,
@@ -213,4 +218,7 @@ struct fbcorr_plan {
     // timing service: events around the main forward kernel
     std::vector<cudaEvent_t> prof_start, prof_stop;
     int prof_count = 0;
+
+    // fbcorr_forward_host: device buffers, band plans and streams (first call)
+    fbc::HostPipe* hostpipe = nullptr;
 };
