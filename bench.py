@@ -527,6 +527,24 @@ def secondary(torch, args, world, peaks):
         "ms_fwd": ms_f, "ms_dx": ms_dx, "ms_dw": ms_dw, "ms_fwd_bwd": ms_fb,
         "fwd_bwd_frac_of_fp32_peak": 3 * wl.flops / ms_fb / 1e9 / fp,
         "plan": p.info()}
+    # three-layer cascade: bank -> fused non-linearity (snippet epilogue) -> next bank
+    from paper_0911_3456_gb300.cascade import Cascade, Layer
+    cx, cbanks = inputs.workload_cascade()
+    xd = torch.from_numpy(cx).cuda()
+    wds = [torch.from_numpy(b).cuda() for b in cbanks]
+    nl = ["y > 0.f ? y : 0.f", "fminf(fmaxf(y, 0.f), 1.f)", None]   # threshold, saturation, linear
+    casc = {}
+    for mode in ("f32", "bf16x3"):
+        cas = Cascade(cx.shape, [Layer(b.shape[0], b.shape[1], b.shape[2], e) for b, e in zip(cbanks, nl)], mode)
+        cas.autotune()
+        outs = [torch.empty(pl.out_shape, device="cuda") for pl in cas.plans]
+        ms_c = time_loop(torch, lambda: cas.forward(xd, wds, outs), 30, 3, world, flush)
+        casc[mode] = {"gflops": cas.flops / ms_c / 1e6, "ms": ms_c,
+                      "specs": [pl.info()["fwd"].get("spec") for pl in cas.plans]}
+    out["cascade_3layer_256x256x8"] = {"layers": [list(b.shape) for b in cbanks],
+                                       "nonlinearities": nl, "flops": cas.flops, **casc}
+    del xd, wds, outs
+
     # the 64-image uneven batch: one persistent launch replayed from a CUDA graph
     from paper_0911_3456_gb300.api import BatchPlan
     bw = inputs.workload_batch()

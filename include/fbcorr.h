@@ -71,11 +71,13 @@ typedef enum {
  * The backward pass always runs in F32. */
 typedef enum { FBCORR_F32 = 0, FBCORR_BF16 = 1, FBCORR_BF16X3 = 2 } fbcorr_dtype_t;
 
-typedef enum { FBCORR_EPI_NONE = 0, FBCORR_EPI_CLAMP = 1 } fbcorr_epilogue_kind_t;
+typedef enum { FBCORR_EPI_NONE = 0, FBCORR_EPI_CLAMP = 1, FBCORR_EPI_SNIPPET = 2 } fbcorr_epilogue_kind_t;
 
 /* Fused epilogue applied to the FP32 accumulator before the store.
  * CLAMP: y = fminf(fmaxf(acc, lo), hi), lo <= hi.  Its gradient passes g only
- * where lo < y < hi strictly. */
+ * where lo < y < hi strictly.
+ * SNIPPET: a user expression compiled into the kernels (fbcorr_plan_create_snippet);
+ * lo and hi are then two free parameters of the expression. */
 typedef struct {
     int kind;   /* fbcorr_epilogue_kind_t */
     float lo, hi;
@@ -94,6 +96,23 @@ fbcorr_status_t fbcorr_plan_create(fbcorr_plan_t* out, const int64_t in_shape[3]
                                    const int64_t filt_shape[4], fbcorr_dtype_t dtype,
                                    fbcorr_epilogue_t epilogue);
 fbcorr_status_t fbcorr_plan_destroy(fbcorr_plan_t plan);
+
+/* A plan whose epilogue is a user C expression compiled into the forward
+ * kernels at plan time: the run-time generated element-wise operation of the
+ * paper (Sec. 4, the ElementwiseKernel of Fig. 4) fused into the store of the
+ * correlation.  `expr` is an expression of float y (the FP32 accumulator of
+ * one output), int n (its filter index) and float lo, hi (epilogue.lo / .hi),
+ * evaluating to the float that is stored, e.g. "y > 0.f ? y : lo * y" or
+ * "tanhf(y)".  CUDA device math functions may be used; ';', braces, '#',
+ * quotes and backslashes may not (FBCORR_ERR_INVALID_ARG), and at most 1024
+ * characters.  epilogue.kind must be FBCORR_EPI_SNIPPET.  A snippet that does
+ * not compile gives FBCORR_ERR_NVRTC with the compiler log in
+ * fbcorr_last_error().  Forward only: fbcorr_backward on such a plan returns
+ * FBCORR_ERR_UNSUPPORTED (the expression has no known derivative).  Every
+ * forward variant is generated (there is no prebuilt fallback for it). */
+fbcorr_status_t fbcorr_plan_create_snippet(fbcorr_plan_t* out, const int64_t in_shape[3],
+                                           const int64_t filt_shape[4], fbcorr_dtype_t dtype,
+                                           fbcorr_epilogue_t epilogue, const char* expr);
 
 /* out = {H', W', N}. */
 fbcorr_status_t fbcorr_plan_out_shape(fbcorr_plan_t plan, int64_t out[3]);
@@ -223,6 +242,13 @@ const char* fbcorr_version(void);
 fbcorr_status_t fbcorr_rtcg_check(const int64_t in_shape[3], const int64_t filt_shape[4],
                                   fbcorr_epilogue_t epilogue, const char* spec, char* log,
                                   size_t cap);
+
+/* Offline check of a snippet epilogue (no GPU): generate and compile the
+ * forward kernel that fbcorr_plan_create_snippet would build for this shape and
+ * dtype (the heuristic FP32 tile, or the default tcgen05 configuration).
+ * Status and log as fbcorr_rtcg_check. */
+fbcorr_status_t fbcorr_snippet_check(const int64_t in_shape[3], const int64_t filt_shape[4],
+                                     fbcorr_dtype_t dtype, const char* expr, char* log, size_t cap);
 
 /* The same offline check for a batch plan: generate and compile (without
  * loading) the single persistent kernel that fbcorr_batch_plan_create would

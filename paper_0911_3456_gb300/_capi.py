@@ -20,7 +20,7 @@ STATUS_NAMES = {
     10: "FBCORR_ERR_INTERNAL",
 }
 DTYPES = {"f32": 0, "bf16": 1, "bf16x3": 2}
-EPI_NONE, EPI_CLAMP = 0, 1
+EPI_NONE, EPI_CLAMP, EPI_SNIPPET = 0, 1, 2
 
 
 class FbcorrError(RuntimeError):
@@ -55,6 +55,8 @@ PROTOTYPES = {
     "fbcorr_plan_workspace_size": (_st, [_vp, ctypes.POINTER(_sz), ctypes.POINTER(_sz)]),
     "fbcorr_forward": (_st, [_vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "fbcorr_forward_host": (_st, [_vp, _vp, _vp, _vp, ctypes.c_int, _vp]),
+    "fbcorr_plan_create_snippet": (_st, [ctypes.POINTER(_vp), I64_3, I64_4, ctypes.c_int, Epilogue, ctypes.c_char_p]),
+    "fbcorr_snippet_check": (_st, [I64_3, I64_4, ctypes.c_int, ctypes.c_char_p, ctypes.c_char_p, _sz]),
     "fbcorr_backward": (_st, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "fbcorr_autotune": (_st, [_vp, _vp]),
     "fbcorr_plan_set_variant": (_st, [_vp, ctypes.c_char_p]),

@@ -55,16 +55,30 @@ class Plan:
     """A single-image correlation plan (``fbcorr_plan_create``)."""
 
     def __init__(self, in_shape: Sequence[int], filt_shape: Sequence[int], dtype: str = "f32",
-                 clamp: Clamp = None):
+                 clamp: Clamp = None, snippet: Optional[str] = None,
+                 snippet_params: Tuple[float, float] = (0.0, 0.0)):
+        """``snippet``: a C expression of float y (the accumulator), int n (the
+        filter index) and float lo, hi (= ``snippet_params``) compiled into the
+        forward kernels as the epilogue (fbcorr_plan_create_snippet); forward
+        only.  Excludes ``clamp``."""
         if dtype not in C.DTYPES:
             raise ValueError(f"dtype must be one of {sorted(C.DTYPES)}")
+        if snippet is not None and clamp is not None:
+            raise ValueError("a plan has one epilogue: clamp or snippet")
         self.in_shape = tuple(int(v) for v in in_shape)
         self.filt_shape = tuple(int(v) for v in filt_shape)
         self.dtype = dtype
         self.clamp = None if clamp is None else (float(clamp[0]), float(clamp[1]))
+        self.snippet = snippet
         h = ctypes.c_void_p()
-        C.call("fbcorr_plan_create", ctypes.byref(h), C.I64_3(*self.in_shape),
-               C.I64_4(*self.filt_shape), C.DTYPES[dtype], C.epilogue(self.clamp))
+        if snippet is None:
+            C.call("fbcorr_plan_create", ctypes.byref(h), C.I64_3(*self.in_shape),
+                   C.I64_4(*self.filt_shape), C.DTYPES[dtype], C.epilogue(self.clamp))
+        else:
+            lo, hi = snippet_params
+            C.call("fbcorr_plan_create_snippet", ctypes.byref(h), C.I64_3(*self.in_shape),
+                   C.I64_4(*self.filt_shape), C.DTYPES[dtype], C.Epilogue(C.EPI_SNIPPET, float(lo), float(hi)),
+                   snippet.encode())
         self._h = h
         out = C.I64_3()
         C.call("fbcorr_plan_out_shape", h, out)

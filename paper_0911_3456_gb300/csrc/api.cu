@@ -51,8 +51,9 @@ DirectProblem fwd_problem(const fbcorr_plan* p) {
     pr.pad_y = 0;
     pr.pad_x = 0;
     pr.flip = 0;
-    pr.epi = p->epi.kind == FBCORR_EPI_CLAMP ? 1 : 0;
+    pr.epi = p->epi.kind == FBCORR_EPI_CLAMP ? 1 : (p->epi.kind == FBCORR_EPI_SNIPPET ? 2 : 0);
     pr.mask = 0;
+    pr.snippet = p->snippet;
     return pr;
 }
 
@@ -92,6 +93,8 @@ std::string shape_key(const fbcorr_plan* p, const char* what) {
 
 // Select the forward variant of an F32 plan from a spec string.
 fbcorr_status_t set_fwd_spec(fbcorr_plan* p, const std::string& spec, const char* source) {
+    if (spec == "default" && !p->snippet.empty())
+        return set_error(FBCORR_ERR_UNSUPPORTED, "the prebuilt default kernel has no snippet epilogue");
     if (spec == "default") {
         p->fwd_kind = VarKind::Default;
         p->fwd_kernel = Kernel{};
@@ -129,7 +132,7 @@ fbcorr_status_t choose_fwd_f32(fbcorr_plan* p) {
     const DirectProblem pr = fwd_problem(p);
     const DirectTile t = direct_heuristic(pr, smem_limit(p->dev), p->dev.sm_count);
     fbcorr_status_t s = set_fwd_spec(p, direct_tile_spec(t), "heuristic");
-    if (s == FBCORR_ERR_NVRTC) {
+    if (s == FBCORR_ERR_NVRTC && p->snippet.empty()) {
         logf("code generation failed, falling back to the prebuilt default kernel: %s",
              last_error_message());
         return set_fwd_spec(p, "default", "fallback");
@@ -207,7 +210,7 @@ fbcorr_status_t fbc::validate_shapes(const int64_t* in, const int64_t* fs, fbcor
     if (!in || !fs) return set_error(FBCORR_ERR_INVALID_ARG, "null shape array");
     if (dtype != FBCORR_F32 && dtype != FBCORR_BF16 && dtype != FBCORR_BF16X3)
         return set_error(FBCORR_ERR_INVALID_ARG, "unknown dtype %d", (int)dtype);
-    if (epi.kind != FBCORR_EPI_NONE && epi.kind != FBCORR_EPI_CLAMP)
+    if (epi.kind != FBCORR_EPI_NONE && epi.kind != FBCORR_EPI_CLAMP && epi.kind != FBCORR_EPI_SNIPPET)
         return set_error(FBCORR_ERR_INVALID_ARG, "unknown epilogue kind %d", epi.kind);
     if (epi.kind == FBCORR_EPI_CLAMP && !(epi.lo <= epi.hi))
         return set_error(FBCORR_ERR_INVALID_ARG, "clamp needs lo <= hi (got %g, %g)", epi.lo, epi.hi);
@@ -231,11 +234,27 @@ namespace {
 
 extern "C" {
 
-fbcorr_status_t fbcorr_plan_create(fbcorr_plan_t* out, const int64_t in_shape[3],
-                                   const int64_t filt_shape[4], fbcorr_dtype_t dtype,
-                                   fbcorr_epilogue_t epilogue) {
-    clear_error();
-    if (!out) return set_error(FBCORR_ERR_INVALID_ARG, "out is NULL");
+}  // extern "C"
+
+namespace {
+
+// A snippet is kept a single C expression: no statements, blocks, directives or literals.
+fbcorr_status_t validate_snippet(const char* expr) {
+    if (!expr || !*expr) return set_error(FBCORR_ERR_INVALID_ARG, "empty snippet");
+    const size_t n = strlen(expr);
+    if (n > 1024) return set_error(FBCORR_ERR_INVALID_ARG, "snippet longer than 1024 characters");
+    for (size_t i = 0; i < n; ++i) {
+        const char c = expr[i];
+        if (c == ';' || c == '{' || c == '}' || c == '#' || c == '"' || c == '\\' || c == '\'' ||
+            (unsigned char)c < 0x20)
+            return set_error(FBCORR_ERR_INVALID_ARG, "snippet must be one expression (character '%c' at %zu)",
+                             c >= 0x20 ? c : '?', i);
+    }
+    return FBCORR_OK;
+}
+
+fbcorr_status_t plan_create(fbcorr_plan_t* out, const int64_t in_shape[3], const int64_t filt_shape[4],
+                            fbcorr_dtype_t dtype, fbcorr_epilogue_t epilogue, const std::string& snippet) {
     *out = nullptr;
     FBC_TRY(validate_shapes(in_shape, filt_shape, dtype, epilogue));
     DeviceInfo dev;
@@ -257,6 +276,7 @@ fbcorr_status_t fbcorr_plan_create(fbcorr_plan_t* out, const int64_t in_shape[3]
     p->dtype = dtype;
     p->epi = epilogue;
     if (p->epi.kind == FBCORR_EPI_NONE) p->epi.lo = p->epi.hi = 0.f;
+    p->snippet = snippet;
     p->dev = dev;
 
     fbcorr_status_t s = FBCORR_OK;
@@ -275,7 +295,7 @@ fbcorr_status_t fbcorr_plan_create(fbcorr_plan_t* out, const int64_t in_shape[3]
             p->fwd_source = "fixed";
             s = tc_plan_create(&p->tc, (int)p->H, (int)p->W, (int)p->D, (int)p->N, (int)p->fh,
                                (int)p->fw, dtype == FBCORR_BF16X3 ? 1 : 0,
-                               p->epi.kind == FBCORR_EPI_CLAMP ? 1 : 0, p->epi.lo, p->epi.hi, dev);
+                               p->epi.kind == FBCORR_EPI_CLAMP ? 1 : 0, p->epi.lo, p->epi.hi, p->snippet, dev);
             if (s == FBCORR_OK) {
                 p->ws_fwd = tc_workspace_bytes(p->tc);
                 p->fwd_source = "heuristic";
@@ -308,6 +328,59 @@ fbcorr_status_t fbcorr_plan_create(fbcorr_plan_t* out, const int64_t in_shape[3]
          (long long)p->D, (int)dtype, kind_name(p->fwd_kind), p->fwd_source.c_str());
     *out = p;
     return FBCORR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fbcorr_status_t fbcorr_plan_create(fbcorr_plan_t* out, const int64_t in_shape[3],
+                                   const int64_t filt_shape[4], fbcorr_dtype_t dtype,
+                                   fbcorr_epilogue_t epilogue) {
+    clear_error();
+    if (!out) return set_error(FBCORR_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (epilogue.kind == FBCORR_EPI_SNIPPET)
+        return set_error(FBCORR_ERR_INVALID_ARG, "a snippet epilogue needs fbcorr_plan_create_snippet");
+    return plan_create(out, in_shape, filt_shape, dtype, epilogue, "");
+}
+
+fbcorr_status_t fbcorr_plan_create_snippet(fbcorr_plan_t* out, const int64_t in_shape[3],
+                                           const int64_t filt_shape[4], fbcorr_dtype_t dtype,
+                                           fbcorr_epilogue_t epilogue, const char* expr) {
+    clear_error();
+    if (!out) return set_error(FBCORR_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (epilogue.kind != FBCORR_EPI_SNIPPET)
+        return set_error(FBCORR_ERR_INVALID_ARG, "epilogue.kind must be FBCORR_EPI_SNIPPET");
+    FBC_TRY(validate_snippet(expr));
+    return plan_create(out, in_shape, filt_shape, dtype, epilogue, expr);
+}
+
+fbcorr_status_t fbcorr_snippet_check(const int64_t in_shape[3], const int64_t filt_shape[4],
+                                     fbcorr_dtype_t dtype, const char* expr, char* log, size_t cap) {
+    clear_error();
+    if (log && cap) log[0] = '\0';
+    const fbcorr_epilogue_t epi{FBCORR_EPI_SNIPPET, 0.f, 0.f};
+    FBC_TRY(validate_shapes(in_shape, filt_shape, dtype, epi));
+    FBC_TRY(validate_snippet(expr));
+    std::string lg;
+    fbcorr_status_t st;
+    if (dtype == FBCORR_F32) {
+        fbcorr_plan tmp;
+        tmp.H = in_shape[0]; tmp.W = in_shape[1]; tmp.D = in_shape[2];
+        tmp.N = filt_shape[0]; tmp.fh = filt_shape[1]; tmp.fw = filt_shape[2];
+        tmp.Ho = tmp.H - tmp.fh + 1; tmp.Wo = tmp.W - tmp.fw + 1;
+        tmp.epi = epi;
+        tmp.snippet = expr;
+        const DirectProblem fp = fwd_problem(&tmp);
+        const DirectTile t = direct_heuristic(fp, 200 * 1024, 148);
+        st = rtcg_compile_only(direct_kernel_source(fp, t, kname_for("fbc_direct", fp, t)), &lg);
+    } else {
+        st = tc_snippet_check((int)in_shape[2], (int)filt_shape[2], dtype == FBCORR_BF16X3 ? 1 : 0, expr, &lg);
+    }
+    if (st != FBCORR_OK && log && cap) snprintf(log, cap, "%s", lg.empty() ? fbcorr_last_error() : lg.c_str());
+    return st;
 }
 
 fbcorr_status_t fbcorr_plan_profile(fbcorr_plan_t p, int capacity) {
@@ -417,6 +490,8 @@ fbcorr_status_t fbcorr_backward(fbcorr_plan_t p, const float* x, const float* w,
                                 fbcorr_stream_t stream) {
     clear_error();
     if (!p || !g) return set_error(FBCORR_ERR_INVALID_ARG, "NULL plan or gradient");
+    if (p->epi.kind == FBCORR_EPI_SNIPPET)
+        return set_error(FBCORR_ERR_UNSUPPORTED, "a snippet epilogue is forward-only (no derivative)");
     if (dw && !x) return set_error(FBCORR_ERR_INVALID_ARG, "dw needs x");
     if (dx && !w) return set_error(FBCORR_ERR_INVALID_ARG, "dx needs w");
     const bool clamp = p->epi.kind == FBCORR_EPI_CLAMP;
@@ -484,8 +559,8 @@ static fbcorr_status_t autotune_tc(fbcorr_plan_t p, fbcorr_stream_t stream);
 static fbcorr_status_t tune_direct(fbcorr_plan_t p, const DirectProblem& pr, cudaStream_t s,
                                    const char* what, std::string* best_spec, float* best_ms_out) {
     int topk = atoi(env_str("FBCORR_TUNE_TOPK", "12").c_str());
-    return tune_direct_problem(p->dev, pr, s, 0, 64, smem_limit(p->dev), std::max(1, topk), true, what,
-                               best_spec, best_ms_out);
+    return tune_direct_problem(p->dev, pr, s, 0, 64, smem_limit(p->dev), std::max(1, topk), p->snippet.empty(),
+                               what, best_spec, best_ms_out);
 }
 
 fbcorr_status_t fbcorr_autotune(fbcorr_plan_t p, fbcorr_stream_t stream) {
@@ -660,6 +735,8 @@ fbcorr_status_t fbcorr_rtcg_check(const int64_t in_shape[3], const int64_t filt_
     clear_error();
     if (log && cap) log[0] = '\0';
     FBC_TRY(validate_shapes(in_shape, filt_shape, FBCORR_F32, epilogue));
+    if (epilogue.kind == FBCORR_EPI_SNIPPET)
+        return set_error(FBCORR_ERR_INVALID_ARG, "snippet epilogues are checked by fbcorr_snippet_check");
     fbcorr_plan tmp;
     tmp.H = in_shape[0];
     tmp.W = in_shape[1];

@@ -318,6 +318,8 @@ fbcorr_status_t fbcorr_batch_plan_create(fbcorr_batch_plan_t* out, int n, const 
         return set_error(FBCORR_ERR_INVALID_ARG, "a batch holds 1..%d images (got %d)", kBatchMaxImages, n);
     if (!in_shapes || !filt_shapes) return set_error(FBCORR_ERR_INVALID_ARG, "NULL shape arrays");
     for (int k = 0; k < n; ++k) {
+        if (epilogue.kind == FBCORR_EPI_SNIPPET)
+            return set_error(FBCORR_ERR_UNSUPPORTED, "batch plans have no snippet epilogue");
         fbcorr_status_t s = validate_shapes(in_shapes[k], filt_shapes[k], dtype, epilogue);
         if (s != FBCORR_OK) return set_error(s, "image %d: %s", k, fbcorr_last_error());
     }
@@ -353,6 +355,8 @@ fbcorr_status_t fbcorr_batch_rtcg_check(int n, const int64_t (*in_shapes)[3],
     if (log && cap) log[0] = '\0';
     if (n < 1 || n > kBatchMaxImages || !in_shapes || !filt_shapes)
         return set_error(FBCORR_ERR_INVALID_ARG, "bad batch description");
+    if (epilogue.kind == FBCORR_EPI_SNIPPET)
+        return set_error(FBCORR_ERR_UNSUPPORTED, "batch plans have no snippet epilogue");
     for (int k = 0; k < n; ++k) FBC_TRY(validate_shapes(in_shapes[k], filt_shapes[k], FBCORR_F32, epilogue));
     fbcorr_batch_plan tmp;
     tmp.n = n;

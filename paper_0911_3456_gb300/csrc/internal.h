@@ -99,8 +99,13 @@ struct DirectProblem {
     int out_h, out_w, nf;     // output extents and channels
     int fh, fw;
     int pad_y, pad_x;
-    int flip, epi, mask;
+    int flip, epi, mask;      // epi: 0 none, 1 clamp, 2 user snippet
+    std::string snippet;      // the expression of epi = 2
 };
+// The generated definition of the snippet epilogue function (empty for no snippet).
+std::string snippet_definition(const std::string& expr);
+// 8 hex digits of a hash of the expression, for kernel names.
+std::string snippet_tag(const std::string& expr);
 std::string direct_kernel_source(const DirectProblem& pr, const DirectTile& t,
                                  const std::string& kname);
 // threads > 0 restricts the candidates to one CTA size (the batched kernel).
@@ -158,7 +163,8 @@ fbcorr_status_t hostpipe_device_status(HostPipe* hp, int clear);   // of the ban
 // ---- tensor-core path (tc_kernel.cu) -----------------------------------------------
 struct TcPlan;   // opaque
 fbcorr_status_t tc_plan_create(TcPlan** out, int H, int W, int D, int N, int fh, int fw,
-                               int split, int epi, float lo, float hi, const DeviceInfo& dev);
+                               int split, int epi, float lo, float hi, const std::string& snippet,
+                               const DeviceInfo& dev);
 void tc_plan_destroy(TcPlan* p);
 size_t tc_workspace_bytes(const TcPlan* p);
 // ev_start / ev_stop (may be null): recorded around the main GEMM kernel.
@@ -173,6 +179,8 @@ fbcorr_status_t tc_set_spec(TcPlan* p, const std::string& spec);
 fbcorr_status_t tc_precompile(TcPlan* p, const std::vector<std::string>& specs);
 // Compile-only check of the generated kernel of `spec` (BF16 and split) for depth D, width fw.
 fbcorr_status_t tc_rtcg_check(int D, int fw, const std::string& spec, std::string* log);
+// Compile-only check of the generated kernel with a snippet epilogue (default configuration).
+fbcorr_status_t tc_snippet_check(int D, int fw, int split, const std::string& snippet, std::string* log);
 
 // ---- argument validation (api.cu) -------------------------------------------------------
 fbcorr_status_t validate_shapes(const int64_t* in, const int64_t* fs, fbcorr_dtype_t dtype,
@@ -198,6 +206,7 @@ struct fbcorr_plan {
     fbc::Kernel fwd_kernel;
     std::string fwd_source;        // "heuristic", "tuned", "cache", "env", "forced"
     fbc::TcPlan* tc = nullptr;
+    std::string snippet;           // user epilogue expression (epi.kind == FBCORR_EPI_SNIPPET)
 
     // backward (F32 always)
     bool bwd_ready = false;

@@ -19,6 +19,9 @@
 
 typedef unsigned int fbc_u32;
 
+// Snippet epilogue (EPI = 2): defined by the generated source after this file.
+__device__ float fbc_user_epi(float y, int n, float lo, float hi);
+
 struct FbcDirectArgs {
     const float* __restrict__ x;   // input  [in_h][in_w][C]
     const float* __restrict__ m;   // clamp-mask source, same shape as x (FLIP with MASK only)
@@ -218,6 +221,7 @@ struct FbcDirect {
 #pragma unroll
             for (int f = 0; f < TF; ++f) {
                 v[f] = acc[r][f];
+                if constexpr (EPI == 2) v[f] = fbc_user_epi(v[f], nb + f, a.lo, a.hi);
                 if (EPI == 1) v[f] = fminf(fmaxf(v[f], a.lo), a.hi);
             }
             if (vec) {

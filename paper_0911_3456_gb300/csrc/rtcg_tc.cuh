@@ -57,6 +57,9 @@ typedef unsigned char fbc_u8;
 
 extern __shared__ __align__(1024) fbc_u8 fbc_tc_smem[];
 
+// Snippet epilogue (USER = 1): defined by the generated source after this file.
+__device__ float fbc_user_epi(float y, int n, float lo, float hi);
+
 // ---------------------------------------------------------------- PTX wrappers
 __device__ __forceinline__ fbc_u32 fbc_smem_addr(const void* p) {
     fbc_u32 r;
@@ -235,7 +238,7 @@ __device__ __forceinline__ void fbc_issue_tap(fbc_u32 d_tmem, fbc_u64 ad, fbc_u6
 }
 
 // ---------------------------------------------------------------- the kernel body
-template <int NC, int SPLIT, int FW, int BT, int EW, int FUSE, int CW>
+template <int NC, int SPLIT, int FW, int BT, int EW, int FUSE, int CW, int USER>
 __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
     constexpr int NST = (FW + BT - 1) / BT;          // B stages per filter row
     constexpr int L = FBC_TC_TILE_M + FW - 1;        // slab pixels per filter row
@@ -486,7 +489,10 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
                         for (int e = 0; e < 2; ++e) {
                             float a = __uint_as_float(r[h][4 * g8 + 2 * e]);
                             float b = __uint_as_float(r[h][4 * g8 + 2 * e + 1]);
-                            if (P.epi == 1) {
+                            if constexpr (USER != 0) {
+                                a = fbc_user_epi(a, n, P.lo, P.hi);
+                                b = fbc_user_epi(b, n + 1, P.lo, P.hi);
+                            } else if (P.epi == 1) {
                                 a = fminf(fmaxf(a, P.lo), P.hi);
                                 b = fminf(fmaxf(b, P.lo), P.hi);
                             }

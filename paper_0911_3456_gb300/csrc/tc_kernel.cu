@@ -140,6 +140,7 @@ struct TcPlan {
     int split_blocks = 0;
     int H = 0, W = 0, D = 0, N = 0, fh = 0, fw = 0, nc = 0, split = 0, epi = 0;
     float lo = 0.f, hi = 0.f;
+    std::string snippet;   // user epilogue expression ("" for none)
     int sm_count = 1;
     unsigned long long wait_ns = 0;
     int drop_b = -1;
@@ -150,23 +151,23 @@ namespace {
 
 int tc_threads(const TcConfig& c) { return 64 + 32 * c.ew + 32 * c.cw; }
 
-std::string tc_kernel_name(int nc, int split, int fw, const TcConfig& c) {
+std::string tc_kernel_name(int nc, int split, int fw, const TcConfig& c, const std::string& snippet) {
     char b[96];
     snprintf(b, sizeof b, "fbc_tc_c%d_s%d_f%d_b%d_e%d_z%d_w%d", nc, split, fw, c.bt, c.ew, c.fuse, c.cw);
-    return b;
+    return snippet.empty() ? std::string(b) : std::string(b) + "_u" + snippet_tag(snippet);
 }
 
 // The NVRTC source of one kernel: parameter block, kernel templates, and an
 // extern "C" entry point with this configuration's template arguments.
-std::string tc_kernel_source(int nc, int split, int fw, const TcConfig& c) {
+std::string tc_kernel_source(int nc, int split, int fw, const TcConfig& c, const std::string& snippet) {
     std::ostringstream o;
-    o << rtcg_tc_params_source() << "\n" << rtcg_tc_source() << "\n";
+    o << rtcg_tc_params_source() << "\n" << rtcg_tc_source() << "\n" << snippet_definition(snippet);
     o << "static_assert(sizeof(FbcTcParams) == " << sizeof(FbcTcParams)
       << ", \"host and device disagree on the parameter block\");\n";
     o << "extern \"C\" __global__ void __launch_bounds__(" << tc_threads(c) << ", 1) "
-      << tc_kernel_name(nc, split, fw, c) << "(const __grid_constant__ FbcTcParams P) {\n"
+      << tc_kernel_name(nc, split, fw, c, snippet) << "(const __grid_constant__ FbcTcParams P) {\n"
       << "  fbc_tc_corr_body<" << nc << "," << split << "," << fw << "," << c.bt << "," << c.ew << ","
-      << c.fuse << "," << c.cw << ">(P);\n}\n";
+      << c.fuse << "," << c.cw << "," << (snippet.empty() ? 0 : 1) << ">(P);\n}\n";
     return o.str();
 }
 
@@ -310,14 +311,14 @@ bool parse_tc_spec(const std::string& s, TcConfig* c) {
 
 // The generated kernel of configuration `c` (compiled or taken from the caches).
 fbcorr_status_t tc_kernel(TcPlan* p, const TcConfig& c, Kernel* out) {
-    const std::string name = tc_kernel_name(p->nc, p->split, p->fw, c);
+    const std::string name = tc_kernel_name(p->nc, p->split, p->fw, c, p->snippet);
     auto it = p->kernels.find(name);
     if (it != p->kernels.end()) {
         *out = it->second;
         return FBCORR_OK;
     }
     Kernel k;
-    FBC_TRY(rtcg_kernel(tc_kernel_source(p->nc, p->split, p->fw, c), name, kSmemMax, tc_threads(c), &k));
+    FBC_TRY(rtcg_kernel(tc_kernel_source(p->nc, p->split, p->fw, c, p->snippet), name, kSmemMax, tc_threads(c), &k));
     p->kernels[name] = k;
     *out = k;
     return FBCORR_OK;
@@ -339,10 +340,10 @@ fbcorr_status_t tc_precompile(TcPlan* p, const std::vector<std::string>& specs) 
     for (const auto& s : specs) {
         TcConfig c;
         if (!parse_tc_spec(s, &c)) continue;
-        const std::string name = tc_kernel_name(p->nc, p->split, p->fw, c);
+        const std::string name = tc_kernel_name(p->nc, p->split, p->fw, c, p->snippet);
         if (seen[name]) continue;
         seen[name] = true;
-        srcs.push_back(tc_kernel_source(p->nc, p->split, p->fw, c));
+        srcs.push_back(tc_kernel_source(p->nc, p->split, p->fw, c, p->snippet));
     }
     return rtcg_precompile(srcs);
 }
@@ -359,7 +360,7 @@ fbcorr_status_t tc_set_spec(TcPlan* p, const std::string& spec) {
 }
 
 fbcorr_status_t tc_plan_create(TcPlan** out, int H, int W, int D, int N, int fh, int fw, int split,
-                               int epi, float lo, float hi, const DeviceInfo& dev) {
+                               int epi, float lo, float hi, const std::string& snippet, const DeviceInfo& dev) {
     *out = nullptr;
     if ((D + 15) / 16 * 16 / 8 > 8)
         return set_error(FBCORR_ERR_UNSUPPORTED,
@@ -369,6 +370,7 @@ fbcorr_status_t tc_plan_create(TcPlan** out, int H, int W, int D, int N, int fh,
     p->H = H; p->W = W; p->D = D; p->N = N; p->fh = fh; p->fw = fw;
     p->nc = (D + 15) / 16 * 16 / 8;
     p->split = split; p->epi = epi; p->lo = lo; p->hi = hi;
+    p->snippet = snippet;
     p->sm_count = dev.sm_count;
     const long long wait_ms = atoll(env_str("FBCORR_WAIT_MS", "4000").c_str());
     p->wait_ns = (unsigned long long)std::max(1LL, wait_ms) * 1000000ull;
@@ -403,8 +405,8 @@ std::string tc_describe(const TcPlan* p) {
     o << "{\"precision\":\"" << (p->split ? "bf16x3" : "bf16") << "\",\"mma\":\"128x" << p->kp.nt
       << "x16\",\"filter_tiles\":" << p->kp.ntn << ",\"tiles\":" << p->kp.mtiles * p->kp.ntn
       << ",\"smem\":" << p->smem << ",\"grid\":" << p->grid << ",\"threads\":" << tc_threads(p->cfg)
-      << ",\"kernel\":\"" << tc_kernel_name(p->nc, p->split, p->fw, p->cfg) << "\"";
-    auto it = p->kernels.find(tc_kernel_name(p->nc, p->split, p->fw, p->cfg));
+      << ",\"kernel\":\"" << tc_kernel_name(p->nc, p->split, p->fw, p->cfg, p->snippet) << "\"";
+    auto it = p->kernels.find(tc_kernel_name(p->nc, p->split, p->fw, p->cfg, p->snippet));
     if (it != p->kernels.end()) o << ",\"source_hash\":\"" << hex64(it->second.src_hash) << "\"";
     o << "}";
     return o.str();
@@ -449,8 +451,16 @@ fbcorr_status_t tc_rtcg_check(int D, int fw, const std::string& spec, std::strin
         return set_error(FBCORR_ERR_UNSUPPORTED, "fused conversion does not fit this shape");
     if (c.bt < 1 || c.bt > fw) return set_error(FBCORR_ERR_UNSUPPORTED, "taps per stage out of range");
     for (int split = 0; split <= 1; ++split)
-        FBC_TRY(rtcg_compile_only(tc_kernel_source(nc, split, fw, c), log));
+        FBC_TRY(rtcg_compile_only(tc_kernel_source(nc, split, fw, c, ""), log));
     return FBCORR_OK;
+}
+
+fbcorr_status_t tc_snippet_check(int D, int fw, int split, const std::string& snippet, std::string* log) {
+    const int nc = (D + 15) / 16 * 16 / 8;
+    if (nc > 8) return set_error(FBCORR_ERR_UNSUPPORTED, "tensor-core modes support depth D <= 64");
+    TcConfig c;   // the pre-pass configuration: valid for every shape
+    c.na = 2; c.nb = 2; c.ntmax = 256; c.bt = 1; c.ew = 4; c.fuse = 0; c.nr = 0; c.cw = 0;
+    return rtcg_compile_only(tc_kernel_source(nc, split, fw, c, snippet), log);
 }
 
 }  // namespace fbc

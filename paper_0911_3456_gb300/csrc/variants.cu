@@ -52,10 +52,28 @@ bool parse_direct_spec(const std::string& s, DirectTile* t) {
     return true;
 }
 
+std::string snippet_definition(const std::string& expr) {
+    if (expr.empty()) return "";
+    return "__device__ float fbc_user_epi(float y, int n, float lo, float hi) {\n"
+           "  (void)y; (void)n; (void)lo; (void)hi;\n  return (float)(" + expr + ");\n}\n";
+}
+
+std::string snippet_tag(const std::string& expr) {
+    uint32_t h = 2166136261u;   // FNV-1a
+    for (unsigned char c : expr) {
+        h ^= c;
+        h *= 16777619u;
+    }
+    char b[16];
+    snprintf(b, sizeof b, "%08x", h);
+    return b;
+}
+
 std::string direct_kernel_source(const DirectProblem& pr, const DirectTile& t,
                                  const std::string& kname) {
     std::ostringstream o;
     o << rtcg_header_source() << "\n";
+    if (pr.epi == 2) o << snippet_definition(pr.snippet);
     o << "typedef FbcDirect<" << pr.fh << "," << pr.fw << "," << pr.c << "," << t.tr << ","
       << t.tf << "," << t.wr << "," << t.wf << "," << pr.flip << "," << pr.epi << "," << pr.mask
       << "," << t.chunk(pr.c) << "> FbcThis;\n";
@@ -200,7 +218,7 @@ std::string kname_for(const char* base, const DirectProblem& pr, const DirectTil
     char b[160];
     snprintf(b, sizeof b, "%s_f%dx%d_c%d_t%d_%d_%d_%d_cc%d_fl%d_e%d_m%d", base, pr.fh, pr.fw, pr.c,
              t.tr, t.tf, t.wr, t.wf, t.chunk(pr.c), pr.flip, pr.epi, pr.mask);
-    return b;
+    return pr.epi == 2 ? std::string(b) + "_u" + snippet_tag(pr.snippet) : std::string(b);
 }
 
 size_t smem_limit(const DeviceInfo& dev) {

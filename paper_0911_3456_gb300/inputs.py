@@ -126,6 +126,26 @@ def workload_finite_difference(seed: int = 55) -> Workload:
     return Workload("fd_12x12x2_3x3x3x2", x, w, g=g)
 
 
+# A three-layer cascade with the paper's first-layer shape: 256x256x8 input, then
+# 64 filters 9x9x8 -> 32 filters 5x5x64 -> 16 filters 3x3x32, each bank drawn
+# like the small workloads (N(0,1), per-filter zero mean and unit L2 norm).
+CASCADE_IN = (256, 256, 8)
+CASCADE_BANKS = ((64, 9, 9), (32, 5, 5), (16, 3, 3))
+
+
+def workload_cascade(seed: int = 6):
+    """(x, [w1, w2, w3]): x U[0,1) 256x256x8; bank k of CASCADE_BANKS has the
+    depth of the previous layer's output.  Draw order: x, then the banks."""
+    rng = np.random.default_rng(seed)
+    x = uniform(rng, CASCADE_IN)
+    banks = []
+    depth = CASCADE_IN[2]
+    for (N, fh, fw) in CASCADE_BANKS:
+        banks.append(zero_mean_unit_norm_bank(rng, N, fh, fw, depth))
+        depth = N
+    return x, banks
+
+
 BATCH_HW = tuple(range(64, 513, 32))
 BATCH_D = (4, 8, 16, 32)
 BATCH_N = (16, 32, 64, 128)

@@ -180,3 +180,39 @@ def test_batch_kernel_source_compiles(lib):
     log = ctypes.create_string_buffer(1 << 16)
     st = lib.fbcorr_batch_rtcg_check(n, ins, fls, C.epilogue((0.0, 1.0)), log, len(log))
     assert st == 0, C.last_error() + log.value.decode()
+
+
+@pytest.mark.parametrize("dtype", [0, 1, 2])
+@pytest.mark.parametrize("expr", [b"y > 0.f ? y : lo * y", b"tanhf(y) * hi + 0.5f * (float)(n % 3)",
+                                  b"fminf(fmaxf(y, lo), hi)"])
+def test_snippet_epilogue_compiles(lib, dtype, expr):
+    """A user expression becomes the store epilogue of the generated forward
+    kernel (FP32 direct tile or tcgen05), compiled by NVRTC without a GPU."""
+    log = ctypes.create_string_buffer(1 << 16)
+    st = lib.fbcorr_snippet_check(C.I64_3(40, 52, 16), C.I64_4(12, 5, 3, 16), dtype, expr, log, len(log))
+    assert st == 0, C.last_error() + log.value.decode()
+
+
+@pytest.mark.parametrize("expr,status", [
+    (b"y +", 7),                  # does not compile: NVRTC error, with the log
+    (b"y; y = 0.f", 1),           # statements are refused before compiling
+    (b"{ return y; }", 1),
+    (b"", 1),
+    (b"y * \"1\"", 1),
+])
+def test_snippet_epilogue_refusals(lib, expr, status):
+    log = ctypes.create_string_buffer(1 << 16)
+    st = lib.fbcorr_snippet_check(C.I64_3(40, 52, 16), C.I64_4(12, 5, 3, 16), 0, expr, log, len(log))
+    assert st == status, C.last_error()
+    if status == 7:
+        assert b"error" in log.value
+
+
+def test_snippet_kind_needs_its_own_entry_points(lib):
+    """A SNIPPET epilogue kind is refused by the clamp-style checks and by batch plans."""
+    log = ctypes.create_string_buffer(1 << 12)
+    epi = C.Epilogue(C.EPI_SNIPPET, 0.0, 0.0)
+    assert lib.fbcorr_rtcg_check(C.I64_3(16, 16, 4), C.I64_4(2, 3, 3, 4), epi, b"heuristic", log, len(log)) == 1
+    ins = (ctypes.c_int64 * 3)(16, 16, 4)
+    fls = (ctypes.c_int64 * 4)(2, 3, 3, 4)
+    assert lib.fbcorr_batch_rtcg_check(1, ins, fls, epi, log, len(log)) == 3
