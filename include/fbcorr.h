@@ -167,6 +167,11 @@ fbcorr_status_t fbcorr_autotune(fbcorr_plan_t plan, fbcorr_stream_t stream);
  * "heuristic", "tuned", or an explicit spec as printed by fbcorr_plan_info. */
 fbcorr_status_t fbcorr_plan_set_variant(fbcorr_plan_t plan, const char* spec);
 
+/* The forward variants fbcorr_autotune would time for this plan, one spec per
+ * line (each accepted by fbcorr_plan_set_variant), NUL-terminated into buf;
+ * FBCORR_ERR_INVALID_ARG when cap is too small.  No GPU work. */
+fbcorr_status_t fbcorr_plan_candidates(fbcorr_plan_t plan, char* buf, size_t cap);
+
 /* A one-line JSON description of the plan and its chosen variants, written
  * into buf (NUL-terminated, truncated to cap bytes). */
 fbcorr_status_t fbcorr_plan_info(fbcorr_plan_t plan, char* buf, size_t cap);

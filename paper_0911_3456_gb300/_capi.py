@@ -57,6 +57,7 @@ PROTOTYPES = {
     "fbcorr_forward_host": (_st, [_vp, _vp, _vp, _vp, ctypes.c_int, _vp]),
     "fbcorr_plan_create_snippet": (_st, [ctypes.POINTER(_vp), I64_3, I64_4, ctypes.c_int, Epilogue, ctypes.c_char_p]),
     "fbcorr_snippet_check": (_st, [I64_3, I64_4, ctypes.c_int, ctypes.c_char_p, ctypes.c_char_p, _sz]),
+    "fbcorr_plan_candidates": (_st, [_vp, ctypes.c_char_p, _sz]),
     "fbcorr_backward": (_st, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "fbcorr_autotune": (_st, [_vp, _vp]),
     "fbcorr_plan_set_variant": (_st, [_vp, ctypes.c_char_p]),

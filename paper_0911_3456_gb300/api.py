@@ -167,6 +167,12 @@ class Plan:
     def autotune(self, stream=None) -> None:
         C.call("fbcorr_autotune", self._h, _stream_handle(stream))
 
+    def candidates(self):
+        """The forward variants the auto-tuner times for this plan (spec strings)."""
+        buf = ctypes.create_string_buffer(1 << 16)
+        C.call("fbcorr_plan_candidates", self._h, buf, len(buf))
+        return [s for s in buf.value.decode().split("\n") if s]
+
     def set_variant(self, spec: str) -> None:
         C.call("fbcorr_plan_set_variant", self._h, spec.encode())
 

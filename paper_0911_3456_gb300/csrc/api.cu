@@ -584,6 +584,8 @@ fbcorr_status_t fbcorr_autotune(fbcorr_plan_t p, fbcorr_stream_t stream) {
     return FBCORR_OK;
 }
 
+}  // extern "C"
+
 // Values in [-scale, scale) from an integer hash of the index (the "lowbias32"
 // mixer of C. Wellons' hash-prospector), for timing runs only.
 __global__ void fbc_fill_pattern(float* p, size_t n, float scale, unsigned seed) {
@@ -597,6 +599,13 @@ __global__ void fbc_fill_pattern(float* p, size_t n, float scale, unsigned seed)
         p[i] = scale * ((float)(h >> 8) * (2.0f / 16777216.0f) - 1.0f);
     }
 }
+
+cudaError_t fbc::launch_fill_pattern(float* p, size_t n, float scale, unsigned seed, cudaStream_t s) {
+    fbc_fill_pattern<<<256, 256, 0, s>>>(p, n, scale, seed);
+    return cudaGetLastError();
+}
+
+extern "C" {
 
 // Time every feasible tensor-core configuration (ring depths, filter-tile
 // width) and keep the fastest -- the same measured grid search as for the
@@ -617,8 +626,8 @@ static fbcorr_status_t autotune_tc(fbcorr_plan_t p, fbcorr_stream_t stream) {
     }
     // non-zero operands: the tensor cores draw (and the clocks follow) more power
     // on real data than on zeros, so timings on zeros would favour the wrong spec
-    fbc_fill_pattern<<<256, 256, 0, s>>>(x, xb / 4, 1.0f, 0x1234u);
-    fbc_fill_pattern<<<256, 256, 0, s>>>(w, wb / 4, 0.05f, 0x5678u);
+    launch_fill_pattern(x, xb / 4, 1.0f, 0x1234u, s);
+    launch_fill_pattern(w, wb / 4, 0.05f, 0x5678u, s);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -694,6 +703,27 @@ fbcorr_status_t fbcorr_plan_info(fbcorr_plan_t p, char* buf, size_t cap) {
       << p->dev.sm_count << "}";
     const std::string s = o.str();
     snprintf(buf, cap, "%s", s.c_str());
+    return FBCORR_OK;
+}
+
+fbcorr_status_t fbcorr_plan_candidates(fbcorr_plan_t p, char* buf, size_t cap) {
+    clear_error();
+    if (!p || !buf || cap == 0) return set_error(FBCORR_ERR_INVALID_ARG, "NULL argument");
+    std::vector<std::string> specs;
+    if (p->dtype == FBCORR_F32) {
+        const int topk = std::max(1, atoi(env_str("FBCORR_TUNE_TOPK", "12").c_str()));
+        for (const auto& t : direct_ranked(fwd_problem(p), smem_limit(p->dev), p->dev.sm_count, 0, 64)) {
+            if ((int)specs.size() >= topk) break;
+            specs.push_back(direct_tile_spec(t));
+        }
+        if (p->snippet.empty()) specs.push_back("default");
+    } else {
+        specs = tc_candidates(p->tc);
+    }
+    std::string s;
+    for (const auto& sp : specs) s += sp + "\n";
+    if (s.size() + 1 > cap) return set_error(FBCORR_ERR_INVALID_ARG, "buffer too small (%zu bytes needed)", s.size() + 1);
+    memcpy(buf, s.c_str(), s.size() + 1);
     return FBCORR_OK;
 }
 

@@ -155,6 +155,9 @@ cudaError_t launch_default_dw(const float* x, const float* g, const float* m, fl
                               cudaStream_t s);
 cudaError_t launch_dw_reduce(const float* part, float* dw, int S, long long E, cudaStream_t s);
 
+// Fill p[0..n) with values in [-scale, scale) from an integer hash (timing runs only).
+cudaError_t launch_fill_pattern(float* p, size_t n, float scale, unsigned seed, cudaStream_t s);
+
 // ---- forward from host buffers (host_pipeline.cu) ----------------------------------
 struct HostPipe;
 void hostpipe_destroy(HostPipe* hp);

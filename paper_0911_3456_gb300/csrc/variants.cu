@@ -258,7 +258,7 @@ fbcorr_status_t tune_direct_problem(const DeviceInfo& dev, const DirectProblem& 
                                     bool include_default, const char* what, std::string* best_spec,
                                     float* best_ms_out) {
     // Time the top candidates of one direct-correlation problem (and, when asked,
-    // the prebuilt default kernel) on zero-filled buffers; keep the fastest.
+    // the prebuilt default kernel) on patterned buffers; keep the fastest.
     std::vector<DirectTile> ranked = direct_ranked(pr, smem_cap, dev.sm_count, threads, max_block);
     std::vector<std::string> specs;
     for (auto& t : ranked) {
@@ -287,9 +287,10 @@ fbcorr_status_t tune_direct_problem(const DeviceInfo& dev, const DirectProblem& 
         cudaGetLastError();
         return set_error(FBCORR_ERR_OOM, "autotune buffers");
     }
-    cudaMemsetAsync(x, 0, xb, s);
-    cudaMemsetAsync(w, 0, wb, s);
-    if (m) cudaMemsetAsync(m, 0, xb, s);
+    // patterned, non-zero operands, as for the tensor-core candidates
+    launch_fill_pattern(x, xb / 4, 1.0f, 0x1234u, s);
+    launch_fill_pattern(w, wb / 4, 0.05f, 0x5678u, s);
+    if (m) launch_fill_pattern(m, xb / 4, 1.0f, 0x9abcu, s);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
