@@ -10,9 +10,12 @@ H x W x D input correlated 'valid' against N filters of fh x fw x D,
 
     y[p, q, n] = sum_{i, j, d} x[p+i, q+j, d] * w[n, i, j, d],
 
-optionally clamped, plus the two gradients of <y, g>.  The arithmetic lives in
-``fbcorr_oracle.c`` as FP64 nested loops; this module only widens the inputs to
-FP64 (exactly) and marshals arrays through ctypes.
+optionally clamped, plus the two gradients of <y, g>; and the exact
+nearest-neighbour search of the paper's second case study (Sec. 6.3): for every
+target vector the index and squared Euclidean distance of its nearest neighbour
+(lowest index on ties) and the runner-up distance.  The arithmetic lives in
+``fbcorr_oracle.c`` and ``nn_oracle.c`` as FP64 loops; this module only widens
+the inputs to FP64 (exactly) and marshals arrays through ctypes.
 """
 from __future__ import annotations
 
@@ -23,6 +26,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "fbcorr_oracle.c")
+_SRCS = (_SRC, os.path.join(_HERE, "nn_oracle.c"))
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 EPI_NONE = 0
@@ -33,10 +37,10 @@ _lib = None
 
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (FP64, no fast-math, no FMA contraction)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(map(os.path.getmtime, _SRCS)):
         tmp = _LIB + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
-               "-fPIC", "-shared", "-o", tmp, _SRC]
+               "-fPIC", "-shared", "-o", tmp, *_SRCS, "-lm"]
         subprocess.check_call(cmd)
         os.replace(tmp, _LIB)
     return _LIB
@@ -65,6 +69,8 @@ def _load():
         for f in ("oracle_fbcorr_fwd", "oracle_fbcorr_fwd_points", "oracle_fbcorr_bwd_input",
                   "oracle_fbcorr_bwd_input_points", "oracle_fbcorr_bwd_filt"):
             getattr(lib, f).restype = ctypes.c_int
+        lib.oracle_nn.argtypes = [dp, i64, dp, i64, i64, lp, dp, dp]
+        lib.oracle_nn.restype = ctypes.c_int
         lib.oracle_set_threads.argtypes = [ctypes.c_int]
         lib.oracle_max_threads.restype = ctypes.c_int
         _lib = lib
@@ -181,3 +187,22 @@ def bwd_filt(x, g, filt_shape, y=None, epilogue=None) -> np.ndarray:
     _check(_load().oracle_fbcorr_bwd_filt(_ptr(x), _ptr(g), yp, H, W, D, N, fh, fw,
                                           kind, lo, hi, _ptr(dw)), "bwd_filt")
     return dw
+
+
+def nn(targets, neighbors):
+    """Exact nearest neighbours (Sec. 6.3): for targets [nt, dim] and neighbors
+    [nn, dim], returns (idx [nt] int64, dist [nt], dist2 [nt]) -- the index of the
+    nearest neighbour (lowest on ties), its squared Euclidean distance and the
+    runner-up squared distance, all in FP64."""
+    t = _f64(targets)
+    n = _f64(neighbors)
+    if t.ndim != 2 or n.ndim != 2 or t.shape[1] != n.shape[1]:
+        raise ValueError("targets [nt, dim] and neighbors [nn, dim] must share dim")
+    nt, dim = t.shape
+    idx = np.empty(nt, dtype=np.int64)
+    dist = np.empty(nt, dtype=np.float64)
+    dist2 = np.empty(nt, dtype=np.float64)
+    _check(_load().oracle_nn(_ptr(t), nt, _ptr(n), n.shape[0], dim,
+                             idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _ptr(dist), _ptr(dist2)),
+           "nn")
+    return idx, dist, dist2

@@ -217,6 +217,57 @@ def pin_points(orc):
     assert np.array_equal(orc.bwd_input_points(g, w, x.shape, idx), dx[tuple(idx.T)])
 
 
-ALL_PINS = [pin_golden_hand, pin_scipy_forward, pin_scipy_backward, pin_torch_conv2d,
+# --- exact nearest-neighbour search (Sec. 6.3) ---------------------------------
+
+def pin_nn_golden_hand(orc):
+    G = read_golden("nn_hand_case.txt")
+    dim = int(G["dim"][0])
+    t = _arr(G["targets"], (-1, dim))
+    n = _arr(G["neighbors"], (-1, dim))
+    idx, d, d2 = orc.nn(t, n)
+    assert idx.tolist() == [int(v) for v in G["idx"]]
+    assert d.tolist() == G["dist"] and d2.tolist() == G["dist2"]
+
+
+def pin_nn_scipy(orc):
+    """scipy's pairwise squared distances + argmin (first minimum) on random data."""
+    from scipy.spatial.distance import cdist
+    rng = np.random.default_rng(60)
+    t = rng.standard_normal((40, 16))
+    n = rng.standard_normal((700, 16))
+    idx, d, d2 = orc.nn(t, n)
+    D = cdist(t, n, "sqeuclidean")
+    assert np.array_equal(idx, D.argmin(axis=1))
+    assert np.allclose(d, D.min(axis=1), rtol=1e-12, atol=0)
+    D[np.arange(len(t)), idx] = np.inf
+    assert np.allclose(d2, D.min(axis=1), rtol=1e-12, atol=0)
+
+
+def pin_nn_invariants(orc):
+    """Exact cases on integer data: a target that is also a neighbour is at
+    distance 0; duplicates resolve to the lower index with a zero gap; a
+    permutation of the neighbours permutes the answer; a common translation
+    changes nothing."""
+    rng = np.random.default_rng(61)
+    n = rng.integers(-20, 21, size=(300, 8)).astype(np.float64)
+    t = rng.integers(-20, 21, size=(25, 8)).astype(np.float64)
+    t[3] = n[123]
+    n[250] = n[40]
+    t[7] = n[40] + np.array([1, 0, 0, 0, 0, 0, 0, 0])
+    idx, d, d2 = orc.nn(t, n)
+    assert idx[3] == 123 and d[3] == 0.0
+    assert idx[7] == 40 and d[7] == 1.0 and d2[7] == 1.0
+    perm = rng.permutation(len(n))
+    idx_p, d_p, _ = orc.nn(t, n[perm])
+    assert np.array_equal(d_p, d)
+    gap = d2 > d                      # unique nearest neighbour: the index is well defined
+    assert np.array_equal(perm[idx_p][gap], idx[gap])
+    c = rng.integers(-50, 51, size=8).astype(np.float64)
+    idx_c, d_c, d2_c = orc.nn(t + c, n + c)
+    assert np.array_equal(idx_c, idx) and np.array_equal(d_c, d) and np.array_equal(d2_c, d2)
+
+
+ALL_PINS = [pin_nn_golden_hand, pin_nn_scipy, pin_nn_invariants,
+            pin_golden_hand, pin_scipy_forward, pin_scipy_backward, pin_torch_conv2d,
             pin_delta_filters, pin_constant_and_affine, pin_linearity, pin_adjoint,
             pin_finite_differences, pin_clamp, pin_points]

@@ -100,6 +100,15 @@ MUTANTS = {
                              "const int64_t i = (e / D) % fh;\n        const int64_t j = (e / (D * fh)) % fw;"),
 }
 
+# planted mistakes in the nearest-neighbour oracle (nn_oracle.c)
+NN_MUTANTS = {
+    "nn_ties_to_highest_index": ("            if (d < best) {", "            if (d <= best) {"),
+    "nn_absolute_not_squared": ("                d += e * e;", "                d += fabs(e);"),
+    "nn_dropped_last_dimension": ("for (int64_t k = 0; k < dim; ++k) {", "for (int64_t k = 0; k < dim - 1; ++k) {"),
+    "nn_runner_up_misses_later": ("            } else if (d < second) {\n                second = d;\n            }",
+                                  "            }"),
+}
+
 _RUNNER = textwrap.dedent("""
     import importlib.util, sys, json
     sys.path.insert(0, {tests!r})
@@ -118,18 +127,20 @@ _RUNNER = textwrap.dedent("""
 """)
 
 
-@pytest.mark.parametrize("name", sorted(MUTANTS))
+@pytest.mark.parametrize("name", sorted(MUTANTS) + sorted(NN_MUTANTS))
 def test_pins_catch_mutant(name, tmp_path):
     """A copy of the oracle with one planted mistake must fail at least one pin."""
     src_dir = os.path.join(ROOT, "oracle")
     dst = tmp_path / "oracle_mutant"
     dst.mkdir()
-    shutil.copy(os.path.join(src_dir, "__init__.py"), dst / "__init__.py")
-    with open(os.path.join(src_dir, "fbcorr_oracle.c")) as f:
+    for f in ("__init__.py", "fbcorr_oracle.c", "nn_oracle.c"):
+        shutil.copy(os.path.join(src_dir, f), dst / f)
+    target = "fbcorr_oracle.c" if name in MUTANTS else "nn_oracle.c"
+    with open(os.path.join(src_dir, target)) as f:
         src = f.read()
-    old, new = MUTANTS[name]
+    old, new = MUTANTS[name] if name in MUTANTS else NN_MUTANTS[name]
     assert src.count(old) == 1, f"mutation anchor for {name} not unique/found"
-    (dst / "fbcorr_oracle.c").write_text(src.replace(old, new))
+    (dst / target).write_text(src.replace(old, new))
     script = _RUNNER.format(tests=os.path.join(ROOT, "tests"), init=str(dst / "__init__.py"))
     r = subprocess.run([sys.executable, "-c", script], capture_output=True, text=True, timeout=600,
                        cwd=str(tmp_path))
