@@ -545,6 +545,27 @@ def secondary(torch, args, world, peaks):
                                        "nonlinearities": nl, "flops": cas.flops, **casc}
     del xd, wds, outs
 
+    # exact nearest-neighbour search (Sec. 6.3): 4096 8x8 patches against the
+    # paper's neighbour counts; the paper's GTX 295 seconds are context only
+    from paper_0911_3456_gb300.api import NNPlan
+    paper_gtx295_s = {4096: 0.089, 16384: 0.299, 65536: 1.146, 262144: 4.508, 1048576: 17.989}
+    nn_rows = []
+    for m in inputs.NN_NEIGHBORS:
+        tq, nq = inputs.nn_patches(n_neighbors=m)
+        td, nd = torch.from_numpy(tq).cuda(), torch.from_numpy(nq).cuda()
+        plan_nn = NNPlan(tq.shape[0], m, tq.shape[1])
+        res = {}
+
+        def nn_step():
+            res["out"] = plan_nn.search(td, nd)
+        ms_nn = time_loop(torch, nn_step, 10, 3, world)
+        row = {"targets": tq.shape[0], "neighbors": m, "dim": tq.shape[1], "ms": ms_nn,
+               "pairs_per_s": tq.shape[0] * m / (ms_nn * 1e-3), "gflops_3_per_coord": plan_nn.flops / ms_nn / 1e6,
+               "paper_gtx295_s": paper_gtx295_s.get(m), "status": plan_nn.device_status()}
+        nn_rows.append(row)
+        del td, nd, plan_nn, res
+    out["nn_search_4096_patches_8x8"] = nn_rows
+
     # the 64-image uneven batch: one persistent launch replayed from a CUDA graph
     from paper_0911_3456_gb300.api import BatchPlan
     bw = inputs.workload_batch()

@@ -45,6 +45,7 @@ typedef struct CUstream_st* fbcorr_stream_t;
 
 typedef struct fbcorr_plan* fbcorr_plan_t;
 typedef struct fbcorr_batch_plan* fbcorr_batch_plan_t;
+typedef struct fbcorr_nn_plan* fbcorr_nn_plan_t;
 
 typedef enum {
     FBCORR_OK = 0,
@@ -229,6 +230,37 @@ fbcorr_status_t fbcorr_batch_plan_info(fbcorr_batch_plan_t plan, char* buf, size
 fbcorr_status_t fbcorr_forward_batched(fbcorr_batch_plan_t plan, const float* const* x,
                                        const float* const* w, float* const* y, void* ws,
                                        size_t ws_bytes, fbcorr_stream_t stream);
+
+/* ---- exact nearest-neighbour search -------------------------------------- */
+
+/* The paper's second case study (Sec. 6.3, Table "NN-speedup"): for each of
+ * n_targets vectors, its nearest neighbour in Euclidean distance among
+ * n_neighbors vectors of the same dimension, by exhaustive comparison.
+ * targets [n_targets][dim], neighbors [n_neighbors][dim]: FP32, row-major, DEVICE
+ * memory, 16-byte aligned.  Results: idx_out[i] (int64, device) = the index of
+ * the nearest neighbour, dist_out[i] (FP32, device) = its squared distance
+ * sum_k (t_k - n_k)^2 computed exactly in FP32.
+ * Method: every (target, neighbour) pair is screened on the tensor cores by
+ * d' = |n|^2 - 2 t.n (dtype BF16X3: split-BF16 products, error about 2^-16
+ * sum_k |t_k||n_k|; BF16: plain, about 2^-8), the best candidates of each target
+ * are kept, and the best 4 are re-ranked by their exact FP32 distance (ties: the
+ * lowest index).  The result is the exact nearest neighbour (up to FP32 distance
+ * rounding) whenever fewer than 4 neighbours are within twice the screening error
+ * of it.  dim <= 64, n_targets and n_neighbors < 2^31.  The plan compiles its
+ * kernel (NVRTC) at creation; the search allocates nothing, performs no host
+ * synchronisation and is stream-ordered. */
+fbcorr_status_t fbcorr_nn_plan_create(fbcorr_nn_plan_t* out, int64_t n_targets, int64_t n_neighbors,
+                                      int64_t dim, fbcorr_dtype_t dtype);
+fbcorr_status_t fbcorr_nn_plan_destroy(fbcorr_nn_plan_t plan);
+/* Device workspace the search needs (BF16 copies of both sets, norms, candidates). */
+fbcorr_status_t fbcorr_nn_workspace_size(fbcorr_nn_plan_t plan, size_t* bytes);
+fbcorr_status_t fbcorr_nn_search(fbcorr_nn_plan_t plan, const float* targets, const float* neighbors,
+                                 int64_t* idx_out, float* dist_out, void* ws, size_t ws_bytes,
+                                 fbcorr_stream_t stream);
+/* As fbcorr_plan_device_status, for the nearest-neighbour kernel. */
+fbcorr_status_t fbcorr_nn_plan_device_status(fbcorr_nn_plan_t plan, int clear);
+/* Offline check (no GPU): generate and compile the screening kernel for dim. */
+fbcorr_status_t fbcorr_nn_rtcg_check(int64_t dim, fbcorr_dtype_t dtype, char* log, size_t cap);
 
 /* ---- diagnostics -------------------------------------------------------- */
 

@@ -58,6 +58,12 @@ PROTOTYPES = {
     "fbcorr_plan_create_snippet": (_st, [ctypes.POINTER(_vp), I64_3, I64_4, ctypes.c_int, Epilogue, ctypes.c_char_p]),
     "fbcorr_snippet_check": (_st, [I64_3, I64_4, ctypes.c_int, ctypes.c_char_p, ctypes.c_char_p, _sz]),
     "fbcorr_plan_candidates": (_st, [_vp, ctypes.c_char_p, _sz]),
+    "fbcorr_nn_plan_create": (_st, [ctypes.POINTER(_vp), ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int]),
+    "fbcorr_nn_plan_destroy": (_st, [_vp]),
+    "fbcorr_nn_workspace_size": (_st, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
+    "fbcorr_nn_search": (_st, [_vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
+    "fbcorr_nn_plan_device_status": (_st, [_vp, ctypes.c_int]),
+    "fbcorr_nn_rtcg_check": (_st, [ctypes.c_int64, ctypes.c_int, ctypes.c_char_p, _sz]),
     "fbcorr_backward": (_st, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "fbcorr_autotune": (_st, [_vp, _vp]),
     "fbcorr_plan_set_variant": (_st, [_vp, ctypes.c_char_p]),

@@ -272,6 +272,54 @@ _plans = {}
 _plans_lock = threading.Lock()
 
 
+class NNPlan:
+    """Exact brute-force nearest-neighbour search (fbcorr_nn_*): for each target
+    row the index and exact FP32 squared distance of its nearest neighbour row."""
+
+    def __init__(self, n_targets: int, n_neighbors: int, dim: int, dtype: str = "bf16x3"):
+        if dtype not in ("bf16x3", "bf16"):
+            raise ValueError("dtype must be bf16x3 or bf16")
+        self.n_targets, self.n_neighbors, self.dim, self.dtype = int(n_targets), int(n_neighbors), int(dim), dtype
+        h = ctypes.c_void_p()
+        C.call("fbcorr_nn_plan_create", ctypes.byref(h), self.n_targets, self.n_neighbors, self.dim, C.DTYPES[dtype])
+        self._h = h
+        n = ctypes.c_size_t()
+        C.call("fbcorr_nn_workspace_size", h, ctypes.byref(n))
+        self.ws_bytes = n.value
+        self._ws = None
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            C.load().fbcorr_nn_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def device_status(self, clear: bool = False) -> int:
+        return int(C.load().fbcorr_nn_plan_device_status(self._h, 1 if clear else 0))
+
+    def search(self, targets: torch.Tensor, neighbors: torch.Tensor, stream=None):
+        _check_tensor(targets, "targets", (self.n_targets, self.dim))
+        _check_tensor(neighbors, "neighbors", (self.n_neighbors, self.dim))
+        dev = targets.device
+        if self._ws is None or self._ws.device != dev:
+            self._ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=dev)
+        idx = torch.empty(self.n_targets, dtype=torch.int64, device=dev)
+        dist = torch.empty(self.n_targets, dtype=torch.float32, device=dev)
+        C.call("fbcorr_nn_search", self._h, _vp(targets), _vp(neighbors), _vp(idx), _vp(dist), _vp(self._ws),
+               self.ws_bytes, _stream_handle(stream))
+        return idx, dist
+
+    @property
+    def flops(self) -> int:
+        """3 FLOPs (difference, multiply, add) per coordinate of every target-neighbour pair."""
+        return 3 * self.n_targets * self.n_neighbors * self.dim
+
+
 def get_plan(in_shape, filt_shape, dtype="f32", clamp: Clamp = None, device=None) -> Plan:
     """A process-wide cache of plans keyed by device, shapes, dtype and epilogue."""
     dev = torch.cuda.current_device() if device is None else torch.device(device).index

@@ -1,7 +1,7 @@
 """Build libfbcorr.so in-tree with nvcc for sm_103a.
 
-Steps: embed rtcg_direct.cuh, tc_params.h and rtcg_tc.cuh (the NVRTC kernel
-templates) as strings, compile
+Steps: embed the NVRTC kernel templates (rtcg_direct.cuh, rtcg_ptx.cuh,
+rtcg_tc.cuh, rtcg_nn.cuh and their parameter headers) as strings, compile
 every csrc/*.cu translation unit in parallel, link one shared library that
 statically links the CUDA runtime and dynamically links NVRTC.  Usage:
 ``python -m paper_0911_3456_gb300.build`` or ``build()`` from Python.
@@ -38,9 +38,10 @@ def _cuda_home(nvcc: str) -> str:
 
 def _embed():
     out = os.path.join(CSRC, "_embedded_src.inc")
-    body = "// generated by build.py from rtcg_direct.cuh, tc_params.h, rtcg_tc.cuh -- do not edit\n"
+    body = "// generated by build.py from the NVRTC kernel sources -- do not edit\n"
     for fname, var in (("rtcg_direct.cuh", "kRtcgDirectSrc"), ("tc_params.h", "kRtcgTcParamsSrc"),
-                       ("rtcg_tc.cuh", "kRtcgTcSrc")):
+                       ("rtcg_ptx.cuh", "kRtcgPtxSrc"), ("rtcg_tc.cuh", "kRtcgTcSrc"),
+                       ("nn_params.h", "kRtcgNnParamsSrc"), ("rtcg_nn.cuh", "kRtcgNnSrc")):
         text = open(os.path.join(CSRC, fname)).read()
         assert ')FBCSRC"' not in text
         body += "static const char " + var + '[] = R"FBCSRC(' + text + ')FBCSRC";\n'

@@ -76,7 +76,10 @@ fbcorr_status_t graph_set_kernel(cudaGraphExec_t e, cudaGraphNode_t n, const Ker
 fbcorr_status_t kernel_occupancy(const Kernel& k, int* blocks_per_sm);
 const char* rtcg_header_source();     // contents of rtcg_direct.cuh
 const char* rtcg_tc_params_source();  // contents of tc_params.h
+const char* rtcg_ptx_source();        // contents of rtcg_ptx.cuh
 const char* rtcg_tc_source();         // contents of rtcg_tc.cuh
+const char* rtcg_nn_params_source();  // contents of nn_params.h
+const char* rtcg_nn_source();         // contents of rtcg_nn.cuh
 
 // ---- variants ------------------------------------------------------------------
 enum class VarKind { Default = 0, Direct = 1, Tensor = 2 };

@@ -1,0 +1,26 @@
+// nn_params.h -- launch parameters of the nearest-neighbour distance kernel,
+// shared verbatim by the host (nn.cu) and the NVRTC source (rtcg_nn.cuh).
+// Plain types only, no includes.
+#ifndef FBC_NN_PARAMS_H
+#define FBC_NN_PARAMS_H
+
+#define FBC_NN_TILE_T 128     // targets per tile (MMA M)
+#define FBC_NN_TILE_N 256     // neighbours per tile (MMA N)
+
+struct FbcNnParams {
+    const unsigned char* thi;     // targets, tile-major [t_tiles][nc][128][16 B] BF16 hi
+    const unsigned char* tlo;     //   and lo
+    const unsigned char* nhi;     // neighbours, tile-major [n_tiles][nc][256][16 B] BF16 hi
+    const unsigned char* nlo;     //   and lo
+    const float* n2;              // |n_j|^2 (FP32), +inf for the padding neighbours
+    unsigned long long* part;     // [chunks][parts][t_tiles*128][2] best two keys per target
+    int* err;                     // host-mapped error word
+    unsigned long long wait_ns;   // bound of every mbarrier wait
+    int t_tiles, n_tiles;         // 128-target and 256-neighbour tiles
+    int chunk_tiles, chunks;      // neighbour tiles per work item; items = chunks * t_tiles
+    int nb;                       // B stages (neighbour tiles in flight)
+    unsigned int a_bytes, b_bytes;          // bytes of one half (hi or lo) of an A tile / B tile
+    unsigned int a_off, b_off, bar_off;     // shared-memory layout
+};
+
+#endif

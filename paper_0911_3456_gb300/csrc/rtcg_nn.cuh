@@ -1,0 +1,258 @@
+// rtcg_nn.cuh -- exact brute-force nearest-neighbour search (the paper's second
+// case study, Sec. 6.3): the screening kernel, compiled at plan time by NVRTC
+// with the chunk-plane count NC (dimension / 8), the split mode and the
+// epilogue warp count EW baked in.  Prefixed with nn_params.h and rtcg_ptx.cuh.
+//
+// For target t and neighbour n, |t - n|^2 = |t|^2 + |n|^2 - 2 t.n, and |t|^2 is
+// the same for every neighbour of t, so the nearest neighbours of t are those
+// with the smallest d'(t, n) = |n|^2 - 2 t.n.  The dot products of a tile of 128
+// targets and 256 neighbours are one 128x256xdim GEMM on the tensor cores
+// (tcgen05.mma, BF16 in, FP32 accumulate in TMEM; split BF16 by default, three
+// products per K step like the correlation kernel), and the epilogue keeps, per
+// target, the two smallest keys (d' as order-preserving bits, neighbour index)
+// over the tiles of a work item.  A work item is one target tile against one
+// chunk of neighbour tiles; items run chunk-major, so the target tiles that share
+// a chunk run at the same time and read its neighbours from HBM once.  The host
+// merges the per-item candidates and re-ranks the best few by their exact FP32
+// distance (nn.cu).
+//
+// Roles (persistent CTA, one per SM, 64 + 32*EW threads): warp 0 bulk-copies the
+// item's target tile (one copy per half) and streams its neighbour tiles through
+// a ring of `nb` stages; warp 1 issues the MMAs into two alternating
+// accumulators; EW epilogue warps read the accumulators (tcgen05.ld 16x256b),
+// form the keys and keep the running best two per target row.
+
+__device__ __forceinline__ fbc_u64 fbc_nn_key(float d, unsigned j) {
+    // order-preserving map of the float onto unsigned bits, index in the low word:
+    // the smallest key is the smallest distance, then the lowest index
+    unsigned u = __float_as_uint(d);
+    u = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+    return ((fbc_u64)u << 32) | j;
+}
+
+__device__ __forceinline__ void fbc_nn_keep2(fbc_u64& k1, fbc_u64& k2, fbc_u64 k) {
+    if (k < k1) {
+        k2 = k1;
+        k1 = k;
+    } else if (k < k2) {
+        k2 = k;
+    }
+}
+
+__device__ __forceinline__ fbc_u64 fbc_shfl_xor_u64(fbc_u64 v, int m) {
+    const unsigned lo = __shfl_xor_sync(0xffffffffu, (unsigned)v, m);
+    const unsigned hi = __shfl_xor_sync(0xffffffffu, (unsigned)(v >> 32), m);
+    return ((fbc_u64)hi << 32) | lo;
+}
+
+template <int NC, int SPLIT, int EW>
+__device__ __forceinline__ void fbc_nn_body(const FbcNnParams& P) {
+    __shared__ int s_abort;
+    __shared__ fbc_u32 s_tmem;
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const fbc_u32 sbase = fbc_smem_addr(fbc_tc_smem);
+    // barrier table: a_full[2] a_empty[2] b_full[nb] b_empty[nb] acc_full[2] acc_empty[2] drain
+    const fbc_u32 a_full0 = sbase + P.bar_off;
+    const fbc_u32 a_empty0 = a_full0 + 16u;
+    const fbc_u32 b_full0 = a_empty0 + 16u;
+    const fbc_u32 b_empty0 = b_full0 + 8u * P.nb;
+    const fbc_u32 acc_full0 = b_empty0 + 8u * P.nb;
+    const fbc_u32 acc_empty0 = acc_full0 + 16u;
+    const fbc_u32 drain_bar = acc_empty0 + 16u;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < 2; ++s) {
+            fbc_mbar_init(a_full0 + 8u * s, 1);
+            fbc_mbar_init(a_empty0 + 8u * s, 1);
+            fbc_mbar_init(acc_full0 + 8u * s, 1);
+            fbc_mbar_init(acc_empty0 + 8u * s, EW);
+        }
+        for (int s = 0; s < P.nb; ++s) {
+            fbc_mbar_init(b_full0 + 8u * s, 1);
+            fbc_mbar_init(b_empty0 + 8u * s, 1);
+        }
+        fbc_mbar_init(drain_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_abort = 0;
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(fbc_smem_addr(&s_tmem)),
+                     "r"(512));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    fbc_tc_fence_before();
+    __syncthreads();
+    fbc_tc_fence_after();
+    const fbc_u32 tmem = s_tmem;
+    volatile int* abort_flag = &s_abort;
+    const int items = P.chunks * P.t_tiles;
+    constexpr fbc_u32 halves = SPLIT ? 2u : 1u;
+    const fbc_u32 a_slot = halves * P.a_bytes, b_stage = halves * P.b_bytes;
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ producer
+        if (lane == 0) {
+            fbc_u32 a_it = 0, b_it = 0;
+            int as = 0, bs = 0;
+            fbc_u32 aph = 0, bph = 0;
+            bool ok = true;
+            for (int k = blockIdx.x; k < items && ok; k += gridDim.x) {
+                const int c = k / P.t_tiles, t = k - c * P.t_tiles;
+                if (!(ok = fbc_wait(a_empty0 + 8u * as, aph ^ 1, P, abort_flag, 4))) break;
+                const fbc_u32 afull = a_full0 + 8u * as;
+                fbc_mbar_expect_tx(afull, a_slot);
+                const fbc_u32 adst = sbase + P.a_off + as * a_slot;
+                fbc_bulk_g2s(adst, P.thi + (long long)t * P.a_bytes, P.a_bytes, afull);
+                if (SPLIT) fbc_bulk_g2s(adst + P.a_bytes, P.tlo + (long long)t * P.a_bytes, P.a_bytes, afull);
+                ++a_it;
+                if (++as == 2) { as = 0; aph ^= 1; }
+                const int j1 = min(P.n_tiles, (c + 1) * P.chunk_tiles);
+                for (int jt = c * P.chunk_tiles; jt < j1 && ok; ++jt) {
+                    if (!(ok = fbc_wait(b_empty0 + 8u * bs, bph ^ 1, P, abort_flag, 4))) break;
+                    const fbc_u32 bfull = b_full0 + 8u * bs;
+                    fbc_mbar_expect_tx(bfull, b_stage);
+                    const fbc_u32 bdst = sbase + P.b_off + bs * b_stage;
+                    fbc_bulk_g2s(bdst, P.nhi + (long long)jt * P.b_bytes, P.b_bytes, bfull);
+                    if (SPLIT) fbc_bulk_g2s(bdst + P.b_bytes, P.nlo + (long long)jt * P.b_bytes, P.b_bytes, bfull);
+                    ++b_it;
+                    if (++bs == P.nb) { bs = 0; bph ^= 1; }
+                }
+            }
+            if (!ok) {
+                const fbc_u32 a0 = a_it > 2u ? a_it - 2u : 0u;
+                for (fbc_u32 q = a0; q < a_it; ++q) fbc_wait_drain(a_full0 + 8u * (q % 2), (q / 2) & 1, P);
+                const fbc_u32 b0 = b_it > (fbc_u32)P.nb ? b_it - P.nb : 0u;
+                for (fbc_u32 q = b0; q < b_it; ++q) fbc_wait_drain(b_full0 + 8u * (q % P.nb), (q / P.nb) & 1, P);
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            const fbc_u32 idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((fbc_u32)(FBC_NN_TILE_N >> 3) << 17) |
+                                  ((fbc_u32)(FBC_NN_TILE_T >> 4) << 24);
+            constexpr fbc_u32 aplane = FBC_NN_TILE_T * 16, bplane = FBC_NN_TILE_N * 16;
+            const fbc_u64 adesc0 = fbc_smem_desc(sbase + P.a_off, aplane, 128);
+            const fbc_u64 bdesc0 = fbc_smem_desc(sbase + P.b_off, bplane, 128);
+            constexpr fbc_u64 ak = (2 * aplane) >> 4, bk = (2 * bplane) >> 4;
+            const fbc_u64 alo = P.a_bytes >> 4, blo = P.b_bytes >> 4;
+            int as = 0, bs = 0;
+            fbc_u32 aph = 0, bph = 0, acc_it = 0;
+            bool ok = true, issued = false;
+            for (int k = blockIdx.x; k < items && ok; k += gridDim.x) {
+                const int c = k / P.t_tiles;
+                if (!(ok = fbc_wait(a_full0 + 8u * as, aph, P, abort_flag, 1))) break;
+                const fbc_u64 ad = adesc0 + (fbc_u64)((as * a_slot) >> 4);
+                const int j1 = min(P.n_tiles, (c + 1) * P.chunk_tiles);
+                for (int jt = c * P.chunk_tiles; jt < j1 && ok; ++jt) {
+                    const int acc = acc_it & 1;
+                    if (!(ok = fbc_wait(acc_empty0 + 8u * acc, ((acc_it >> 1) & 1) ^ 1, P, abort_flag, 3))) break;
+                    if (!(ok = fbc_wait(b_full0 + 8u * bs, bph, P, abort_flag, 2))) break;
+                    fbc_tc_fence_after();
+                    const fbc_u32 d_tmem = tmem + (fbc_u32)(acc * 256);
+                    const fbc_u64 bd = bdesc0 + (fbc_u64)((bs * b_stage) >> 4);
+#pragma unroll
+                    for (int kk = 0; kk < NC / 2; ++kk) {
+                        const fbc_u64 a = ad + kk * ak, b = bd + kk * bk;
+                        if (SPLIT) {
+                            fbc_umma(d_tmem, a, b + blo, idesc, kk > 0 ? 1u : 0u);
+                            fbc_umma(d_tmem, a + alo, b, idesc, 1u);
+                            fbc_umma(d_tmem, a, b, idesc, 1u);
+                        } else {
+                            fbc_umma(d_tmem, a, b, idesc, kk > 0 ? 1u : 0u);
+                        }
+                    }
+                    issued = true;
+                    fbc_umma_commit(b_empty0 + 8u * bs);
+                    fbc_umma_commit(acc_full0 + 8u * acc);
+                    ++acc_it;
+                    if (++bs == P.nb) { bs = 0; bph ^= 1; }
+                }
+                if (!ok) break;
+                fbc_umma_commit(a_empty0 + 8u * as);
+                if (++as == 2) { as = 0; aph ^= 1; }
+            }
+            if (!ok && issued) {
+                fbc_umma_commit(drain_bar);
+                fbc_wait_drain(drain_bar, 0, P);
+            }
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue
+        // 16x256b loads: lanes 4r..4r+3 hold 8 columns of TMEM lane r (and r + 8);
+        // this thread sees rows lq*32 + 16h + 8e + lane/4 (h, e in {0,1}).
+        const int ew = warp - 2;
+        const int lq = warp & 3;
+        const int part = ew >> 2;
+        const int rows_total = P.t_tiles * FBC_NN_TILE_T;
+        fbc_u32 acc_it = 0;
+        bool ok = true;
+        for (int k = blockIdx.x; k < items && ok; k += gridDim.x) {
+            const int c = k / P.t_tiles, t = k - c * P.t_tiles;
+            fbc_u64 best[4][2];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) best[r][0] = best[r][1] = ~0ull;
+            const int j1 = min(P.n_tiles, (c + 1) * P.chunk_tiles);
+            for (int jt = c * P.chunk_tiles; jt < j1; ++jt) {
+                const int acc = acc_it & 1;
+                if (!(ok = fbc_wait(acc_full0 + 8u * acc, (acc_it >> 1) & 1, P, abort_flag, 3))) break;
+                fbc_tc_fence_after();
+#pragma unroll 1
+                for (int cc = part; cc < 4; cc += EW / 4) {
+                    fbc_u32 r[2][32];
+                    const fbc_u32 taddr = tmem + ((fbc_u32)(lq * 32) << 16) + (fbc_u32)(acc * 256 + cc * 64);
+                    fbc_tmem_ld16x256b_x8_async(taddr, r[0]);
+                    fbc_tmem_ld16x256b_x8_async(taddr + (16u << 16), r[1]);
+                    fbc_tmem_ld_wait();
+                    fbc_reg_fence(r[0]);
+                    fbc_reg_fence(r[1]);
+                    const unsigned n0 = (unsigned)(jt * FBC_NN_TILE_N + cc * 64 + 2 * (lane & 3));
+#pragma unroll
+                    for (int g8 = 0; g8 < 8; ++g8) {
+                        const unsigned n = n0 + 8u * g8;
+                        const float na = __ldg(P.n2 + n), nb2 = __ldg(P.n2 + n + 1);
+#pragma unroll
+                        for (int h = 0; h < 2; ++h)
+#pragma unroll
+                            for (int e = 0; e < 2; ++e) {
+                                const float da = fmaf(-2.f, __uint_as_float(r[h][4 * g8 + 2 * e]), na);
+                                const float db = fmaf(-2.f, __uint_as_float(r[h][4 * g8 + 2 * e + 1]), nb2);
+                                fbc_nn_keep2(best[2 * h + e][0], best[2 * h + e][1], fbc_nn_key(da, n));
+                                fbc_nn_keep2(best[2 * h + e][0], best[2 * h + e][1], fbc_nn_key(db, n + 1));
+                            }
+                    }
+                }
+                fbc_tc_fence_before();
+                __syncwarp();
+                if (lane == 0) fbc_mbar_arrive(acc_empty0 + 8u * acc);
+                ++acc_it;
+            }
+            if (!ok) break;
+            // the four lanes of a row hold disjoint columns: merge their best two
+#pragma unroll
+            for (int m = 1; m <= 2; m <<= 1)
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const fbc_u64 p1 = fbc_shfl_xor_u64(best[r][0], m), p2 = fbc_shfl_xor_u64(best[r][1], m);
+                    const fbc_u64 lo1 = best[r][0] < p1 ? best[r][0] : p1;
+                    const fbc_u64 hi1 = best[r][0] < p1 ? p1 : best[r][0];
+                    const fbc_u64 lo2 = best[r][1] < p2 ? best[r][1] : p2;
+                    best[r][0] = lo1;
+                    best[r][1] = hi1 < lo2 ? hi1 : lo2;
+                }
+            if ((lane & 3) == 0) {
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const int row = t * FBC_NN_TILE_T + lq * 32 + (r >> 1) * 16 + (r & 1) * 8 + (lane >> 2);
+                    fbc_u64* dst = P.part + (((long long)c * (EW / 4) + part) * rows_total + row) * 2;
+                    dst[0] = best[r][0];
+                    dst[1] = best[r][1];
+                }
+            }
+        }
+    }
+    __syncwarp();
+    fbc_tc_fence_before();
+    __syncthreads();
+    fbc_tc_fence_after();
+    if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}

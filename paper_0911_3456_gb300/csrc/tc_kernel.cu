@@ -161,7 +161,8 @@ std::string tc_kernel_name(int nc, int split, int fw, const TcConfig& c, const s
 // extern "C" entry point with this configuration's template arguments.
 std::string tc_kernel_source(int nc, int split, int fw, const TcConfig& c, const std::string& snippet) {
     std::ostringstream o;
-    o << rtcg_tc_params_source() << "\n" << rtcg_tc_source() << "\n" << snippet_definition(snippet);
+    o << rtcg_tc_params_source() << "\n" << rtcg_ptx_source() << "\n" << rtcg_tc_source() << "\n"
+      << snippet_definition(snippet);
     o << "static_assert(sizeof(FbcTcParams) == " << sizeof(FbcTcParams)
       << ", \"host and device disagree on the parameter block\");\n";
     o << "extern \"C\" __global__ void __launch_bounds__(" << tc_threads(c) << ", 1) "

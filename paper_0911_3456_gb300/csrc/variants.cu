@@ -16,11 +16,14 @@
 
 namespace fbc {
 
-#include "_embedded_src.inc"   // the texts of rtcg_direct.cuh, tc_params.h and rtcg_tc.cuh
+#include "_embedded_src.inc"   // the texts of the NVRTC kernel sources
 
 const char* rtcg_header_source() { return kRtcgDirectSrc; }
 const char* rtcg_tc_params_source() { return kRtcgTcParamsSrc; }
+const char* rtcg_ptx_source() { return kRtcgPtxSrc; }
 const char* rtcg_tc_source() { return kRtcgTcSrc; }
+const char* rtcg_nn_params_source() { return kRtcgNnParamsSrc; }
+const char* rtcg_nn_source() { return kRtcgNnSrc; }
 
 size_t direct_smem_bytes(const DirectTile& t, int fh, int fw, int c) {
     const long cc = t.chunk(c);

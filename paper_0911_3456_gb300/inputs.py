@@ -146,6 +146,50 @@ def workload_cascade(seed: int = 6):
     return x, banks
 
 
+# Exact nearest-neighbour search (Sec. 6.3): 8x8 patches, 4096 targets and
+# 4096 ... 1048576 neighbours (the paper's Table "NN-speedup").  The paper's
+# patches come from the van Hateren natural-image database, which is not here;
+# synthetic images with the 1/f amplitude spectrum of natural scenes stand in.
+NN_TARGETS = 4096
+NN_NEIGHBORS = (4096, 16384, 65536, 262144, 1048576)
+
+
+def synthetic_natural_image(rng, size: int = 512, alpha: float = 1.0) -> np.ndarray:
+    """A size x size image with a 1/f^alpha amplitude spectrum and uniform random
+    phases, scaled to [0, 1] (FP64)."""
+    fy = np.fft.fftfreq(size)[:, None]
+    fx = np.fft.rfftfreq(size)[None, :]
+    f = np.sqrt(fx * fx + fy * fy)
+    f[0, 0] = 1.0
+    spec = f ** (-alpha) * np.exp(2j * np.pi * rng.uniform(size=f.shape))
+    spec[0, 0] = 0.0
+    img = np.fft.irfft2(spec, s=(size, size))
+    img -= img.min()
+    return img / img.max()
+
+
+def nn_patches(seed: int = 7, n_targets: int = NN_TARGETS, n_neighbors: int = 4096, side: int = 8,
+               images: int = 8, size: int = 512):
+    """(targets [n_targets, side*side], neighbors [n_neighbors, side*side]) FP32:
+    row-major side x side patches at uniform random positions; targets come from
+    the first image, neighbours from the other images (``images`` in all)."""
+    rng = np.random.default_rng(seed)
+    imgs = [synthetic_natural_image(rng, size) for _ in range(images)]
+    span = size - side + 1
+
+    def cut(img, count):
+        ys = rng.integers(0, span, size=count)
+        xs = rng.integers(0, span, size=count)
+        win = np.lib.stride_tricks.sliding_window_view(img, (side, side))
+        return win[ys, xs].reshape(count, side * side).astype(np.float32)
+
+    targets = cut(imgs[0], n_targets)
+    per = [n_neighbors // (images - 1)] * (images - 1)
+    per[-1] += n_neighbors - sum(per)
+    neighbors = np.concatenate([cut(im, c) for im, c in zip(imgs[1:], per)])
+    return targets, neighbors
+
+
 BATCH_HW = tuple(range(64, 513, 32))
 BATCH_D = (4, 8, 16, 32)
 BATCH_N = (16, 32, 64, 128)
