@@ -30,12 +30,20 @@ __device__ __forceinline__ fbc_u64 fbc_nn_key(float d, unsigned j) {
     return ((fbc_u64)u << 32) | j;
 }
 
-__device__ __forceinline__ void fbc_nn_keep2(fbc_u64& k1, fbc_u64& k2, fbc_u64 k) {
-    if (k < k1) {
-        k2 = k1;
-        k1 = k;
-    } else if (k < k2) {
-        k2 = k;
+// Running best two (distance, index) of one target row; the columns of a thread
+// arrive in increasing index order, so strict '<' keeps the lowest index on ties.
+// Almost every candidate fails the first comparison.
+__device__ __forceinline__ void fbc_nn_keep2(float& d1, unsigned& i1, float& d2, unsigned& i2, float d, unsigned j) {
+    if (d < d2) {
+        if (d < d1) {
+            d2 = d1;
+            i2 = i1;
+            d1 = d;
+            i1 = j;
+        } else {
+            d2 = d;
+            i2 = j;
+        }
     }
 }
 
@@ -188,9 +196,13 @@ __device__ __forceinline__ void fbc_nn_body(const FbcNnParams& P) {
         bool ok = true;
         for (int k = blockIdx.x; k < items && ok; k += gridDim.x) {
             const int c = k / P.t_tiles, t = k - c * P.t_tiles;
-            fbc_u64 best[4][2];
+            float bd1[4], bd2[4];
+            unsigned bi1[4], bi2[4];
 #pragma unroll
-            for (int r = 0; r < 4; ++r) best[r][0] = best[r][1] = ~0ull;
+            for (int r = 0; r < 4; ++r) {
+                bd1[r] = bd2[r] = __int_as_float(0x7f800000);
+                bi1[r] = bi2[r] = 0xffffffffu;
+            }
             const int j1 = min(P.n_tiles, (c + 1) * P.chunk_tiles);
             for (int jt = c * P.chunk_tiles; jt < j1; ++jt) {
                 const int acc = acc_it & 1;
@@ -198,6 +210,12 @@ __device__ __forceinline__ void fbc_nn_body(const FbcNnParams& P) {
                 fbc_tc_fence_after();
 #pragma unroll 1
                 for (int cc = part; cc < 4; cc += EW / 4) {
+                    // the norms of this chunk's 16 columns first: their latency overlaps
+                    // the tensor-memory loads
+                    const unsigned n0 = (unsigned)(jt * FBC_NN_TILE_N + cc * 64 + 2 * (lane & 3));
+                    float2 nrm[8];
+#pragma unroll
+                    for (int g8 = 0; g8 < 8; ++g8) nrm[g8] = __ldg(reinterpret_cast<const float2*>(P.n2 + n0 + 8u * g8));
                     fbc_u32 r[2][32];
                     const fbc_u32 taddr = tmem + ((fbc_u32)(lq * 32) << 16) + (fbc_u32)(acc * 256 + cc * 64);
                     fbc_tmem_ld16x256b_x8_async(taddr, r[0]);
@@ -205,19 +223,21 @@ __device__ __forceinline__ void fbc_nn_body(const FbcNnParams& P) {
                     fbc_tmem_ld_wait();
                     fbc_reg_fence(r[0]);
                     fbc_reg_fence(r[1]);
-                    const unsigned n0 = (unsigned)(jt * FBC_NN_TILE_N + cc * 64 + 2 * (lane & 3));
 #pragma unroll
                     for (int g8 = 0; g8 < 8; ++g8) {
                         const unsigned n = n0 + 8u * g8;
-                        const float na = __ldg(P.n2 + n), nb2 = __ldg(P.n2 + n + 1);
+                        const float na = nrm[g8].x, nb2 = nrm[g8].y;
 #pragma unroll
                         for (int h = 0; h < 2; ++h)
 #pragma unroll
                             for (int e = 0; e < 2; ++e) {
                                 const float da = fmaf(-2.f, __uint_as_float(r[h][4 * g8 + 2 * e]), na);
                                 const float db = fmaf(-2.f, __uint_as_float(r[h][4 * g8 + 2 * e + 1]), nb2);
-                                fbc_nn_keep2(best[2 * h + e][0], best[2 * h + e][1], fbc_nn_key(da, n));
-                                fbc_nn_keep2(best[2 * h + e][0], best[2 * h + e][1], fbc_nn_key(db, n + 1));
+                                const int q = 2 * h + e;
+                                if (fminf(da, db) < bd2[q]) {
+                                    fbc_nn_keep2(bd1[q], bi1[q], bd2[q], bi2[q], da, n);
+                                    fbc_nn_keep2(bd1[q], bi1[q], bd2[q], bi2[q], db, n + 1);
+                                }
                             }
                     }
                 }
@@ -228,6 +248,13 @@ __device__ __forceinline__ void fbc_nn_body(const FbcNnParams& P) {
             }
             if (!ok) break;
             // the four lanes of a row hold disjoint columns: merge their best two
+            // as keys (order-preserving distance bits, index)
+            fbc_u64 best[4][2];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                best[r][0] = bi1[r] == 0xffffffffu ? ~0ull : fbc_nn_key(bd1[r], bi1[r]);
+                best[r][1] = bi2[r] == 0xffffffffu ? ~0ull : fbc_nn_key(bd2[r], bi2[r]);
+            }
 #pragma unroll
             for (int m = 1; m <= 2; m <<= 1)
 #pragma unroll
