@@ -593,6 +593,28 @@ def secondary(torch, args, world, peaks):
     return out
 
 
+def nn_only(args):
+    """The nearest-neighbour search alone: 4096 8x8 patches against args.nn
+    neighbours (split BF16 screening, exact FP32 re-ranking), W warm-up and K
+    timed searches; one JSON line."""
+    import torch
+    from paper_0911_3456_gb300 import inputs
+    from paper_0911_3456_gb300.api import NNPlan
+    world, rank, local = dist_setup()
+    t, n = inputs.nn_patches(n_neighbors=args.nn)
+    td, nd = torch.from_numpy(t).cuda(), torch.from_numpy(n).cuda()
+    p = NNPlan(t.shape[0], args.nn, t.shape[1])
+    steps = min(args.steps, 50)
+    ms = time_loop(torch, lambda: p.search(td, nd), steps, args.warmup, world)
+    if rank == 0:
+        print(json.dumps({"metric": "exact nearest-neighbour search time", "value": ms, "unit": "ms",
+                          "higher_is_better": False, "steps": steps, "warmup": args.warmup,
+                          "pairs_per_s": t.shape[0] * args.nn / (ms * 1e-3), "status": p.device_status(),
+                          "config": {"workload": f"nn_{t.shape[0]}x{args.nn}x{t.shape[1]}",
+                                     "data": "synthetic 1/f-image 8x8 patches"}}), flush=True)
+    return 0
+
+
 def traffic_sweep(args):
     """One forward per tensor-core candidate of the headline workload (modes
     bf16x3 and bf16), printing each candidate's generated kernel and source hash
@@ -634,11 +656,17 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--workload", choices=["precision", "precision384", "paper_row1"],
                     default="precision")
+    ap.add_argument("--nn", type=int, default=0,
+                    help="time only the nearest-neighbour search against this many neighbours")
     ap.add_argument("--traffic-sweep", action="store_true",
                     help="one forward per tensor-core candidate, for an ncu DRAM-traffic capture")
     args = ap.parse_args()
     if args.traffic_sweep:
         return traffic_sweep(args)
+    if args.nn:
+        if args.warmup < 3:
+            args.warmup = 3
+        return nn_only(args)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
