@@ -382,7 +382,11 @@ def run_ours(args):
     if traffic_src:
         roof["traffic_profile"] = traffic_src
     if mode == "bf16x3" and achieved:
+        # split BF16 spends three BF16 products per algorithmic multiply-add, so its
+        # own ceiling in algorithmic FLOPs is a third of the BF16 peak
         roof["tensor_issued_tflops"] = 3 * achieved
+        roof["peak_split_bf16x3"] = peak / 3
+        roof["frac_of_split_peak"] = 3 * achieved / peak
 
     # ---- e2e through the C ABI from page-locked host buffers: fbcorr_forward_host
     # copies x and w in and y out every step, banded so that the transfers

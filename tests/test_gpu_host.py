@@ -81,3 +81,19 @@ def test_forward_host_rejects_device_tensors():
     p = Plan(wl.x.shape, wl.w.shape, "f32")
     with pytest.raises(ValueError):
         p.forward_host(dev(wl.x, torch), dev(wl.w, torch))
+
+
+@pytest.mark.parametrize("shape", [(5, 40, 4, 3, 5, 3), (3, 17, 8, 2, 3, 3), (64, 20, 8, 5, 1, 1)],
+                         ids=lambda s: "x".join(map(str, s)))
+def test_forward_host_small_outputs(shape):
+    """Outputs of 1, 1 and 64 rows: automatic banding never makes a band of no
+    rows, and a single output row still goes through the band plans."""
+    torch = torch_cuda()
+    from paper_0911_3456_gb300.api import Plan
+    wl = inputs.random_case(2450, *shape)
+    p = Plan(wl.x.shape, wl.w.shape, "f32")
+    x, w = _host_tensors(torch, wl, pinned=True)
+    for bands in (0, 1, 7):
+        y = p.forward_host(x, w, bands=bands)
+        torch.cuda.synchronize()
+        assert normwise_rel(y.numpy(), oracle.fwd(wl.x, wl.w)) <= 1e-5

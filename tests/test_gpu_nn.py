@@ -93,3 +93,30 @@ def test_plain_bf16_screening_is_reranked_exactly():
     ref_idx, ref_d, _ = oracle.nn(t, n)
     assert np.array_equal(idx, ref_idx)
     assert np.allclose(dist, ref_d, rtol=1e-5, atol=1e-7)
+
+
+@pytest.mark.parametrize("nt,nn,dim", [(1, 1, 1), (5, 2, 64), (200, 700, 8), (130, 1000, 48)])
+def test_edge_sizes(nt, nn, dim):
+    """One neighbour, two neighbours, dimensions that are not a multiple of 16,
+    partial target and neighbour tiles."""
+    torch = torch_cuda()
+    rng = np.random.default_rng(3300 + nt + nn + dim)
+    t = rng.standard_normal((nt, dim)).astype(np.float32)
+    n = rng.standard_normal((nn, dim)).astype(np.float32)
+    idx, dist = _run(torch, t, n)
+    ref_idx, ref_d, ref_d2 = oracle.nn(t, n)
+    sep = ref_d2 > ref_d * (1 + 1e-3) + 1e-6
+    assert np.array_equal(idx[sep], ref_idx[sep])
+    assert np.all((idx >= 0) & (idx < nn))
+    chosen = ((t.astype(np.float64) - n.astype(np.float64)[idx]) ** 2).sum(axis=1)
+    assert np.allclose(dist, chosen, rtol=64 * 2.0 ** -23, atol=1e-6)
+
+
+def test_plan_refusals():
+    torch_cuda()
+    from paper_0911_3456_gb300 import _capi as C
+    from paper_0911_3456_gb300.api import NNPlan
+    with pytest.raises(C.FbcorrError):
+        NNPlan(10, 10, 65)              # more than 64 dimensions
+    with pytest.raises(ValueError):
+        NNPlan(10, 10, 8, "f32")        # screening runs on the tensor cores

@@ -80,3 +80,17 @@ def test_snippet_plan_is_forward_only_and_reports_compile_errors():
     with pytest.raises(C.FbcorrError) as e:
         _plan("f32", wl, "y + undefined_symbol", (0.0, 0.0))
     assert e.value.status_name == "FBCORR_ERR_NVRTC"
+
+
+def test_snippet_plan_autotunes_on_the_tensor_cores():
+    """Tuning a split-BF16 snippet plan times generated tcgen05 variants that all
+    carry the snippet; the tuned plan still matches the oracle."""
+    torch = torch_cuda()
+    wl = inputs.random_case(2900, *SHAPE)
+    p = _plan("bf16x3", wl, "y > 0.f ? y : lo * y", (0.2, 0.0))
+    p.autotune()
+    assert p.info()["fwd"]["detail"]["kernel"].split("_u")[-1] != p.info()["fwd"]["detail"]["kernel"]
+    y = host(p.forward(dev(wl.x, torch), dev(wl.w, torch)))
+    z = oracle.fwd(wl.x, wl.w)
+    ref = np.where(z > 0, z, 0.2 * z)
+    assert np.abs(y - ref).max() <= 1e-5 * np.abs(z).max()
