@@ -68,6 +68,14 @@ fbcorr_status_t rtcg_precompile(const std::vector<std::string>& sources);
 // Compile only (no GPU needed); returns the NVRTC log on failure.
 fbcorr_status_t rtcg_compile_only(const std::string& src, std::string* log);
 fbcorr_status_t launch(const Kernel& k, dim3 grid, void** args, cudaStream_t stream);
+// Largest number of co-resident clusters of `cluster` CTAs of kernel `k` (its
+// compile-time cluster shape, block size and dynamic shared memory).
+fbcorr_status_t cluster_occupancy(const Kernel& k, int cluster, int* clusters);
+// A 3D FP32 tensor map for tiled bulk stores (128-byte swizzle, dims innermost
+// first, strides in bytes of dims 1 and 2) written into the 128-byte `map`;
+// false when the driver offers no tensor maps or rejects the arguments.
+bool encode_f32_store_map(void* map, const float* base, const unsigned long long dims[3],
+                          const unsigned long long strides[2], const unsigned box[3]);
 // CUDA-graph kernel nodes for NVRTC kernels (driver API under the hood).
 fbcorr_status_t graph_add_kernel(cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps,
                                  const Kernel& k, dim3 grid, void** args, cudaGraphNode_t* out);

@@ -42,6 +42,7 @@ struct DriverApi {
     CUresult (*graphExecKernelNodeSetParams)(CUgraphExec, CUgraphNode,
                                              const CUDA_KERNEL_NODE_PARAMS*) = nullptr;
     CUresult (*occupancy)(int*, CUfunction, int, size_t) = nullptr;
+    CUresult (*clusterOccupancy)(int*, CUfunction, const CUlaunchConfig*) = nullptr;   // optional
 };
 
 std::mutex g_mu;
@@ -72,6 +73,7 @@ fbcorr_status_t driver_api(DriverApi** out) {
                   resolve("cuGraphExecKernelNodeSetParams", &d.graphExecKernelNodeSetParams) &&
                   resolve("cuOccupancyMaxActiveBlocksPerMultiprocessor", &d.occupancy);
         if (!ok) return set_error(FBCORR_ERR_CUDA, "could not resolve CUDA driver entry points");
+        if (!resolve("cuOccupancyMaxActiveClusters", &d.clusterOccupancy)) d.clusterOccupancy = nullptr;
         d.ok = true;
         g_drv = d;
     }
@@ -314,6 +316,53 @@ std::string hex64(unsigned long long v) {
     char b[32];
     snprintf(b, sizeof b, "%016llx", v);
     return b;
+}
+
+fbcorr_status_t cluster_occupancy(const Kernel& k, int cluster, int* clusters) {
+    DriverApi* drv = nullptr;
+    FBC_TRY(driver_api(&drv));
+    *clusters = 0;
+    if (!drv->clusterOccupancy)
+        return set_error(FBCORR_ERR_UNSUPPORTED, "the driver offers no cluster occupancy query");
+    CUlaunchConfig cfg;
+    memset(&cfg, 0, sizeof cfg);
+    cfg.gridDimX = (unsigned)cluster;
+    cfg.gridDimY = 1;
+    cfg.gridDimZ = 1;
+    cfg.blockDimX = (unsigned)k.threads;
+    cfg.blockDimY = 1;
+    cfg.blockDimZ = 1;
+    cfg.sharedMemBytes = (unsigned)k.smem;
+    const CUresult r = drv->clusterOccupancy(clusters, k.fn, &cfg);
+    if (r != CUDA_SUCCESS)
+        return set_error(FBCORR_ERR_CUDA, "cuOccupancyMaxActiveClusters(%s): %s", k.name.c_str(), cu_err(r));
+    return FBCORR_OK;
+}
+
+bool encode_f32_store_map(void* map, const float* base, const unsigned long long dims[3],
+                          const unsigned long long strides[2], const unsigned box[3]) {
+    // resolved on first use and kept out of driver_api(): a driver without tensor
+    // maps leaves the caller on its direct-store path
+    using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static EncodeFn fn = nullptr;
+    static bool tried = false;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (!tried) {
+            tried = true;
+            if (!resolve("cuTensorMapEncodeTiled", &fn)) fn = nullptr;
+        }
+    }
+    if (!fn) return false;
+    const cuuint64_t gdim[3] = {dims[0], dims[1], dims[2]};
+    const cuuint64_t gstride[2] = {strides[0], strides[1]};
+    const cuuint32_t bdim[3] = {box[0], box[1], box[2]};
+    const cuuint32_t estride[3] = {1, 1, 1};
+    return fn(reinterpret_cast<CUtensorMap*>(map), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), gdim,
+              gstride, bdim, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 fbcorr_status_t launch(const Kernel& k, dim3 grid, void** args, cudaStream_t stream) {

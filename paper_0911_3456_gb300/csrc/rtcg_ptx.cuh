@@ -1,7 +1,8 @@
 // rtcg_ptx.cuh -- PTX wrappers shared by the run-time generated tcgen05 kernels
 // (the filter-bank correlation of rtcg_tc.cuh and the nearest-neighbour distance
 // kernel of rtcg_nn.cuh): shared-memory addresses, mbarriers with time-bounded
-// waits, 1D bulk copies, tcgen05.mma / commit / ld, BF16 packing.  Embedded as a
+// waits, 1D bulk copies (with cluster multicast), tiled bulk stores, cluster
+// barriers, tcgen05.mma / commit / ld, BF16 packing.  Embedded as a
 // string and placed after the kernel's parameter block in every generated
 // source; self-contained (no system headers).  A bounded wait takes any
 // parameter block with `wait_ns` (the bound) and `err` (the host-mapped error
@@ -59,6 +60,22 @@ __device__ __forceinline__ void fbc_bulk_g2s(fbc_u32 dst, const void* src, fbc_u
         : "memory");
 }
 
+// 1D bulk copy global -> the same shared-memory offset in every CTA of `mask`
+// (cluster multicast); completion counted on the mbarrier at `bar`'s offset in each.
+__device__ __forceinline__ void fbc_bulk_g2s_mc(fbc_u32 dst, const void* src, fbc_u32 bytes, fbc_u32 bar,
+                                                unsigned short mask) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1], %2, [%3], "
+        "%4;" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(bar), "h"(mask)
+        : "memory");
+}
+
+// Every thread of every CTA of the cluster (release / acquire).
+__device__ __forceinline__ void fbc_cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void fbc_tc_fence_before() {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -84,6 +101,15 @@ __device__ __forceinline__ void fbc_umma_commit(fbc_u32 bar) {
                  : "memory");
 }
 
+// Commit whose arrival goes to the mbarrier at `bar`'s offset in every CTA of `mask`.
+__device__ __forceinline__ void fbc_umma_commit_mc(fbc_u32 bar, unsigned short mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            bar),
+        "h"(mask)
+        : "memory");
+}
+
 // tcgen05.ld 16x256b.x8 -- 16 TMEM lanes x 64 columns: registers 4g, 4g+1 hold
 // columns 8g + 2*(lane%4) + {0,1} of lane lane/4, registers 4g+2, 4g+3 the same
 // columns of lane 8 + lane/4.
@@ -93,6 +119,20 @@ __device__ __forceinline__ void fbc_umma_commit(fbc_u32 bar) {
 __device__ __forceinline__ void fbc_tmem_ld16x256b_x8_async(fbc_u32 taddr, fbc_u32 (&r)[32]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.16x256b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+          "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+          "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+
+// tcgen05.ld 32x32b.x32 -- 32 TMEM lanes x 32 columns: register j holds column
+// j of lane `lane` (one accumulator row per thread).  Issued without its wait.
+__device__ __forceinline__ void fbc_tmem_ld32x32b_x32_async(fbc_u32 taddr, fbc_u32 (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
         "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
@@ -115,6 +155,50 @@ __device__ __forceinline__ void fbc_reg_fence(fbc_u32 (&r)[32]) {
 __device__ __forceinline__ void fbc_st_cs_f2(float* p, float a, float b) {
     asm volatile("st.global.cs.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(a), "f"(b) : "memory");
 }
+
+// 16-byte shared store.
+__device__ __forceinline__ void fbc_st_shared_v4(fbc_u32 addr, fbc_u32 a, fbc_u32 b, fbc_u32 c, fbc_u32 d) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d)
+                 : "memory");
+}
+
+__device__ __forceinline__ uint4 fbc_ld_shared_v4(fbc_u32 addr) {
+    uint4 v;
+    asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(addr)
+                 : "memory");
+    return v;
+}
+
+// Streaming 16-byte store.
+__device__ __forceinline__ void fbc_st_cs_v4(float* p, uint4 v) {
+    asm volatile("st.global.cs.v4.b32 [%0], {%1, %2, %3, %4};" ::"l"(p), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+                 : "memory");
+}
+
+// Make this thread's shared-memory writes visible to the bulk-copy (async) proxy.
+__device__ __forceinline__ void fbc_fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Tiled bulk store shared -> global of one box of a 3D tensor map (coordinates
+// innermost first, all >= 0; elements outside the tensor are not written),
+// tracked in this thread's bulk async-group.
+__device__ __forceinline__ void fbc_tma_store_3d(const void* tmap, fbc_u32 src, int c0, int c1, int c2) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(tmap),
+                 "r"(src), "r"(c0), "r"(c1), "r"(c2)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fbc_bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+
+// Wait until at most N of this thread's bulk groups still read shared memory.
+template <int N>
+__device__ __forceinline__ void fbc_bulk_wait_read() {
+    asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+
+// Wait until every bulk group of this thread has completed its writes.
+__device__ __forceinline__ void fbc_bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // Two FP32 values -> two BF16 (round to nearest even), packed low = a, high = b.
 __device__ __forceinline__ fbc_u32 fbc_pack_bf16x2(float a, float b) {

@@ -30,7 +30,10 @@
 //   warps 2..   EW epilogue warps (two per TMEM lane quarter when EW = 8):
 //               tcgen05.ld 16x256b, optional clamp, streaming stores straight
 //               from registers (four lanes write 32 contiguous bytes of one
-//               output pixel); overlaps the MMAs of the next tile;
+//               output pixel), or (TS = 32) tcgen05.ld 32x32b into SB swizzled
+//               shared-memory slots per warp, each written out as one tiled
+//               bulk store of 32 pixels x 32 filters; overlaps the MMAs of the
+//               next tile;
 //   last CW     (FUSE) converter warps: FP32 x rows -> BF16 hi (and lo) chunk
 //               planes of an A slot; FUSE = 1 reads the rows from global memory
 //               into registers one row ahead, FUSE = 2 from a ring of raw rows
@@ -46,6 +49,13 @@
 // Split BF16: v = hi + lo, hi = bf16_rn(v), lo = bf16_rn(v - hi); each K step
 // issues hi*lo + lo*hi, then hi*hi, into the same FP32 accumulator (the lo*lo
 // term, ~2^-16 relative, is dropped).
+//
+// Pairs (MC = 1): a tile needs the whole filter bank from L2 (400 KB in BF16 for
+// 256 filters of 5x5x32), more than the bulk-copy path delivers per SM in one
+// tile's MMA time.  The kernel then runs as clusters of two CTAs that process
+// two pixel tiles against the same B sequence: each producer copies half of
+// every B stage and multicasts it into both CTAs, each CTA's MMA commit
+// releases the stage in both, so L2 serves every B byte once per pair.
 //
 // Every mbarrier wait is bounded in time (%globaltimer); on expiry the kernel
 // records an error code in host-mapped memory, stops every role, waits (again
@@ -77,7 +87,7 @@ __device__ __forceinline__ void fbc_issue_tap(fbc_u32 d_tmem, fbc_u64 ad, fbc_u6
 }
 
 // ---------------------------------------------------------------- the kernel body
-template <int NC, int SPLIT, int FW, int BT, int EW, int FUSE, int CW, int USER>
+template <int NC, int SPLIT, int FW, int BT, int EW, int FUSE, int CW, int USER, int TS, int SB, int MC>
 __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
     constexpr int NST = (FW + BT - 1) / BT;          // B stages per filter row
     constexpr int L = FBC_TC_TILE_M + FW - 1;        // slab pixels per filter row
@@ -105,7 +115,7 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
         }
         for (int s = 0; s < P.nb; ++s) {
             fbc_mbar_init(b_full0 + 8u * s, 1);
-            fbc_mbar_init(b_empty0 + 8u * s, 1);
+            fbc_mbar_init(b_empty0 + 8u * s, MC ? 2 : 1);   // MC: both CTAs' MMAs release a stage
         }
         for (int s = 0; s < 2; ++s) {
             fbc_mbar_init(acc_full0 + 8u * s, 1);
@@ -127,12 +137,26 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
     }
     fbc_tc_fence_before();
     __syncthreads();
+    if constexpr (MC) fbc_cluster_sync();   // the peer's barriers are initialised before any multicast
     fbc_tc_fence_after();
     const fbc_u32 tmem = s_tmem;
     volatile int* abort_flag = &s_abort;
-    // tiles blockIdx.x, blockIdx.x + gridDim.x, ...: pixel tile t % mtiles of filter tile t / mtiles
-    const int ntiles = P.mtiles * P.ntn;
-    const int my_tiles = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    // Schedule: tile t is pixel tile t % mtiles_s of filter tile t / mtiles_s.
+    // MC = 0: tiles blockIdx.x, blockIdx.x + gridDim.x, ...
+    // MC = 1: cluster c = blockIdx.x / 2 takes the tile pairs (2j, 2j + 1), j = c,
+    // c + clusters, ...; its CTA of rank r runs tile 2j + r, so both CTAs run the
+    // same filter tiles in the same order (mtiles_s is even) and share every B
+    // stage.  A pixel tile >= mtiles (odd mtiles) is a phantom: its slab rows lie
+    // past the output and its results are never stored.
+    const int nsched = P.mtiles_s * P.ntn;
+    const int unit = MC ? (int)blockIdx.x >> 1 : (int)blockIdx.x;
+    const int nunits = MC ? (int)gridDim.x >> 1 : (int)gridDim.x;
+    const int nwork = MC ? nsched >> 1 : nsched;
+    const int my_tiles = unit < nwork ? (nwork - 1 - unit) / nunits + 1 : 0;
+    auto tile_of = [&](int k) -> int {
+        const int w = unit + k * nunits;
+        return MC ? 2 * w + ((int)blockIdx.x & 1) : w;
+    };
     const int R = my_tiles * P.fh;                    // filter rows this CTA runs, in order
     const fbc_u32 plane = (fbc_u32)P.lp * 16u;        // bytes per A chunk plane (shared)
     const fbc_u32 bplane = (fbc_u32)P.nt * 16u;       // bytes per B chunk plane (shared)
@@ -140,8 +164,8 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
     const fbc_u32 b_half = NC * bplane;               // bytes per tap and half of a B stage
     // first input pixel of slab row r
     auto row_p0 = [&](int r) -> long long {
-        const int tile = (int)blockIdx.x + (r / P.fh) * (int)gridDim.x;
-        return (long long)(tile % P.mtiles) * FBC_TC_TILE_M + (long long)(r % P.fh) * P.W;
+        const int tile = tile_of(r / P.fh);
+        return (long long)(tile % P.mtiles_s) * FBC_TC_TILE_M + (long long)(r % P.fh) * P.W;
     };
     // pixels of slab row r that lie inside x (the rest reads as zero)
     auto row_valid = [&](long long p0) -> int {
@@ -190,8 +214,8 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
                     ++next_a;
                 }
                 if (!ok) break;
-                const int tile = (int)blockIdx.x + (r / P.fh) * (int)gridDim.x;
-                const long long woff = (((long long)(tile / P.mtiles) * P.fh + r % P.fh) * FW) * tap_bytes;
+                const int tile = tile_of(r / P.fh);
+                const long long woff = (((long long)(tile / P.mtiles_s) * P.fh + r % P.fh) * FW) * tap_bytes;
                 const fbc_u8* wtap_hi = P.whi + woff;
                 const fbc_u8* wtap_lo = P.wlo + woff;
 #pragma unroll
@@ -205,8 +229,20 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
                     fbc_mbar_expect_tx(bfull, SPLIT ? 2u * bytes : bytes);
                     if ((int)b_it != P.drop_b) {
                         const fbc_u32 bdst = sbase + P.b_off + bs * P.b_stage;
-                        fbc_bulk_g2s(bdst, wtap_hi + s * BT * tap_bytes, bytes, bfull);
-                        if (SPLIT) fbc_bulk_g2s(bdst + (fbc_u32)BT * b_half, wtap_lo + s * BT * tap_bytes, bytes, bfull);
+                        if constexpr (MC) {
+                            // this CTA's half of the stage into both CTAs of the pair; the
+                            // peer's copy brings the other half (each b_full expects both)
+                            const fbc_u32 hb = bytes >> 1;
+                            const fbc_u32 ho = ((fbc_u32)blockIdx.x & 1u) * hb;
+                            fbc_bulk_g2s_mc(bdst + ho, wtap_hi + s * BT * tap_bytes + ho, hb, bfull, 3);
+                            if (SPLIT)
+                                fbc_bulk_g2s_mc(bdst + (fbc_u32)BT * b_half + ho, wtap_lo + s * BT * tap_bytes + ho, hb,
+                                                bfull, 3);
+                        } else {
+                            fbc_bulk_g2s(bdst, wtap_hi + s * BT * tap_bytes, bytes, bfull);
+                            if (SPLIT)
+                                fbc_bulk_g2s(bdst + (fbc_u32)BT * b_half, wtap_lo + s * BT * tap_bytes, bytes, bfull);
+                        }
                     }
                     ++b_it;
                     if (++bs == P.nb) { bs = 0; bph ^= 1; }
@@ -262,7 +298,10 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
                                 fbc_issue_tap<NC, SPLIT>(d_tmem, adesc + (fbc_u64)(s * BT + t), bdesc + (fbc_u64)t * btap,
                                                          ak, bk, alo, blo, idesc, accumulate);
                         issued = true;
-                        fbc_umma_commit(b_empty0 + 8u * bs);
+                        if constexpr (MC)
+                            fbc_umma_commit_mc(b_empty0 + 8u * bs, 3);   // the stage is free once both CTAs are done
+                        else
+                            fbc_umma_commit(b_empty0 + 8u * bs);
                         if (++bs == P.nb) { bs = 0; bph ^= 1; bdesc = bdesc0; } else { bdesc += b_step; }
                     }
                     if (!ok) break;
@@ -287,17 +326,140 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
         const int lq = warp & 3;         // the TMEM lane quarter this warp may access
         const int part = ew >> 2;        // EW = 8: even / odd 64-column chunks of the quarter
         const bool vec2 = (P.N & 1) == 0;
+        // TS: staging slots of this warp (1024-byte aligned for the 128-byte swizzle)
+        const fbc_u32 st_base = ((sbase + P.st_off + 1023u) & ~1023u) + (fbc_u32)(ew * SB * FBC_TC_ST_BOX);
+        int st_slot = 0;
         fbc_u32 acc_it = 0;
         for (int k = 0; k < my_tiles; ++k) {
-            const int tile = (int)blockIdx.x + k * (int)gridDim.x;
-            const int mt = tile % P.mtiles;
-            const int nti = tile / P.mtiles;
+            const int tile = tile_of(k);
+            const int mt = tile % P.mtiles_s;
+            const int nti = tile / P.mtiles_s;
             const int acc = acc_it & 1;
             if (!fbc_wait(acc_full0 + 8u * acc, (acc_it >> 1) & 1, P, abort_flag, FBC_TC_ERR_WAIT_ACC)) break;
             fbc_tc_fence_after();
-            // columns past this tile's last filter (nt is a multiple of 16, a load 64
-            // wide) hold no result: stop at the tile end as well as N
+            // columns past this tile's last filter hold no result: stop at the tile end as well as N
             const int nend = min(P.N, (nti + 1) * P.nt);
+            if constexpr (TS == 1) {
+                // tcgen05.ld 32x32b (lane l: 32 consecutive columns of pixel m0 + l)
+                // into this warp's swizzled staging slot, read back transposed so
+                // that eight lanes hold the 128 contiguous bytes of one pixel's
+                // chunk: every 16-byte store instruction writes four full lines.
+                const int m0 = mt * FBC_TC_TILE_M + lq * 32;
+                long long orow[8];    // output offsets of pixels m0 + 4i + lane / 8 (-1: outside)
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int m = m0 + 4 * i + (lane >> 3);
+                    const int p = m / P.W;
+                    const int q = m - p * P.W;
+                    orow[i] = (p < P.Ho && q < P.Wo) ? ((long long)p * P.Wo + q) * P.N : -1;
+                }
+                const fbc_u32 wbuf = st_base + (fbc_u32)lane * 128u;
+                const fbc_u32 sw = (fbc_u32)(lane & 7);
+                const int ch = lane & 7;     // 16-byte chunk this lane reads back and stores
+                const bool vec4 = (P.N & 3) == 0 && (reinterpret_cast<unsigned long long>(P.y) & 15) == 0;
+                const fbc_u32 trow = tmem + ((fbc_u32)(lq * 32) << 16) + (fbc_u32)(acc * FBC_TC_ACC_COLS);
+#pragma unroll 1
+                for (int cc = part; cc < (P.nt + 31) >> 5; cc += EW / 4) {
+                    fbc_u32 r[32];
+                    fbc_tmem_ld32x32b_x32_async(trow + (fbc_u32)(cc * 32), r);
+                    fbc_tmem_ld_wait();
+                    fbc_reg_fence(r);
+                    const int n0 = nti * P.nt + cc * 32;
+                    if (n0 >= nend) continue;   // warp-uniform
+                    if constexpr (USER != 0) {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            r[j] = __float_as_uint(fbc_user_epi(__uint_as_float(r[j]), n0 + j, P.lo, P.hi));
+                    } else if (P.epi == 1) {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j)
+                            r[j] = __float_as_uint(fminf(fmaxf(__uint_as_float(r[j]), P.lo), P.hi));
+                    }
+                    __syncwarp();   // the previous chunk's read-back is done
+#pragma unroll
+                    for (int c = 0; c < 8; ++c)
+                        fbc_st_shared_v4(wbuf + ((((fbc_u32)c) ^ sw) << 4), r[4 * c], r[4 * c + 1], r[4 * c + 2],
+                                         r[4 * c + 3]);
+                    __syncwarp();
+                    const int n = n0 + 4 * ch;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int row = 4 * i + (lane >> 3);
+                        const uint4 v = fbc_ld_shared_v4(st_base + (fbc_u32)row * 128u +
+                                                         ((((fbc_u32)ch) ^ (fbc_u32)(row & 7)) << 4));
+                        if (orow[i] < 0 || n >= nend) continue;
+                        float* dst = P.y + orow[i] + n;
+                        if (vec4 && n + 4 <= nend) {
+                            fbc_st_cs_v4(dst, v);
+                        } else {
+                            dst[0] = __uint_as_float(v.x);
+                            if (n + 1 < nend) dst[1] = __uint_as_float(v.y);
+                            if (n + 2 < nend) dst[2] = __uint_as_float(v.z);
+                            if (n + 3 < nend) dst[3] = __uint_as_float(v.w);
+                        }
+                    }
+                }
+                fbc_tc_fence_before();
+                __syncwarp();
+                if (lane == 0) fbc_mbar_arrive(acc_empty0 + 8u * acc);
+                ++acc_it;
+                continue;
+            }
+            if constexpr (TS > 1) {
+                if (P.tma_y) {
+                    // tcgen05.ld 32x32b: lane l holds 32 consecutive columns of the
+                    // accumulator row of pixel m0 + l.  W % 32 == 0, so the warp's 32
+                    // pixels lie in one output row; columns ending past the last
+                    // filter, and pixels q >= W', fall outside the tensor map and are
+                    // not written.  Each 32x32 block is written into a staging slot
+                    // in the 128-byte swizzled layout (16-byte chunk c of row l at
+                    // chunk c ^ (l % 8): conflict-free) and leaves as one tiled store.
+                    const int m0 = mt * FBC_TC_TILE_M + lq * 32;
+                    const int p = m0 / P.W;
+                    const int q0 = m0 - p * P.W;
+                    const bool inside = p < P.Ho && q0 < P.Wo;
+                    const fbc_u32 sw = (fbc_u32)(lane & 7);
+                    const fbc_u32 trow = tmem + ((fbc_u32)(lq * 32) << 16) + (fbc_u32)(acc * FBC_TC_ACC_COLS);
+#pragma unroll 1
+                    for (int cc = part; cc < (P.nt >> 5); cc += EW / 4) {
+                        fbc_u32 r[32];
+                        fbc_tmem_ld32x32b_x32_async(trow + (fbc_u32)(cc * 32), r);
+                        fbc_tmem_ld_wait();
+                        fbc_reg_fence(r);
+                        const int n0 = nti * P.nt + cc * 32;
+                        if (!inside || n0 >= P.N) continue;   // warp-uniform
+                        if constexpr (USER != 0) {
+#pragma unroll
+                            for (int j = 0; j < 32; ++j)
+                                r[j] = __float_as_uint(fbc_user_epi(__uint_as_float(r[j]), n0 + j, P.lo, P.hi));
+                        } else if (P.epi == 1) {
+#pragma unroll
+                            for (int j = 0; j < 32; ++j)
+                                r[j] = __float_as_uint(fminf(fmaxf(__uint_as_float(r[j]), P.lo), P.hi));
+                        }
+                        const fbc_u32 buf = st_base + (fbc_u32)(st_slot * FBC_TC_ST_BOX) + (fbc_u32)lane * 128u;
+                        if (lane == 0) fbc_bulk_wait_read<SB - 1>();   // the slot's previous store has read it
+                        __syncwarp();
+#pragma unroll
+                        for (int c = 0; c < 8; ++c)
+                            fbc_st_shared_v4(buf + ((((fbc_u32)c) ^ sw) << 4), r[4 * c], r[4 * c + 1], r[4 * c + 2],
+                                             r[4 * c + 3]);
+                        fbc_fence_proxy_async_smem();
+                        __syncwarp();
+                        if (lane == 0) {
+                            fbc_tma_store_3d(P.ymap, st_base + (fbc_u32)(st_slot * FBC_TC_ST_BOX), n0, q0, p);
+                            fbc_bulk_commit();
+                        }
+                        if (++st_slot == SB) st_slot = 0;
+                    }
+                    fbc_tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) fbc_mbar_arrive(acc_empty0 + 8u * acc);
+                    ++acc_it;
+                    continue;
+                }
+            }
+            // 16x256b loads of 64 columns (nt is a multiple of 16)
             const int ncol = (P.nt + 63) / 64;
             // output offsets of pixels lane/4 + 8e of the two 16-lane halves h: ob[2h + e]
             long long ob[4];
@@ -352,6 +514,9 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
             if (lane == 0) fbc_mbar_arrive(acc_empty0 + 8u * acc);
             ++acc_it;
         }
+        // tiled stores still in flight read this CTA's shared memory: finish them
+        if constexpr (TS > 1)
+            if (lane == 0) fbc_bulk_wait_all();
     } else if constexpr (FUSE != 0) {
         // ------------------------------------------------------------ converters
         // FP32 slab row -> BF16 hi (and lo) chunk planes of an A slot, by CW warps.
@@ -432,9 +597,17 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
                         const int c = item - px * NC;
                         float4 v0 = make_float4(0.f, 0.f, 0.f, 0.f), v1 = v0;
                         if (px < valid) {
+                            // the two 16-byte halves in an order that spreads the eight
+                            // threads of a phase over distinct bank groups (D = 16, 32, 64)
                             const float* src = raw + px * P.D + c * 8;
-                            if (c * 8 < P.D) v0 = *reinterpret_cast<const float4*>(src);
-                            if (c * 8 + 4 < P.D) v1 = *reinterpret_cast<const float4*>(src + 4);
+                            const bool swap = NC == 4 ? (px & 1) : NC == 2 ? ((px >> 1) & 1) : NC == 8 ? ((c >> 2) & 1) : 0;
+                            if (swap) {
+                                if (c * 8 + 4 < P.D) v1 = *reinterpret_cast<const float4*>(src + 4);
+                                if (c * 8 < P.D) v0 = *reinterpret_cast<const float4*>(src);
+                            } else {
+                                if (c * 8 < P.D) v0 = *reinterpret_cast<const float4*>(src);
+                                if (c * 8 + 4 < P.D) v1 = *reinterpret_cast<const float4*>(src + 4);
+                            }
                         }
                         const float v[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
                         fbc_split8<SPLIT>(v, reinterpret_cast<uint4*>(dst + c * plane + px * 16),
@@ -455,6 +628,9 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
     __syncwarp();
     fbc_tc_fence_before();
     __syncthreads();
+    // MC: the peer may still multicast into this CTA's shared memory or arrive on
+    // its barriers until it has finished too
+    if constexpr (MC) fbc_cluster_sync();
     fbc_tc_fence_after();
     if (warp == 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(FBC_TC_TMEM_COLS));

@@ -10,8 +10,10 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
 #include <map>
 #include <new>
 #include <sstream>
@@ -127,6 +129,9 @@ struct TcConfig {
     int fuse = 0;                      // x conversion: 0 pre-pass, 1 converters from global, 2 from a raw ring
     int nr = 0;                        // raw-row slots (fuse = 2)
     int cw = 0;                        // converter warps (fuse = 1, 2): 4 or 8
+    int ts = 0;                        // epilogue stores: 0 direct, 32 tiled (32-pixel boxes)
+    int sb = 0;                        // staging slots per epilogue warp (ts = 32): 1..3
+    int mc = 0;                        // 1: clusters of two CTAs sharing every B stage (multicast)
 };
 
 struct TcPlan {
@@ -142,9 +147,14 @@ struct TcPlan {
     float lo = 0.f, hi = 0.f;
     std::string snippet;   // user epilogue expression ("" for none)
     int sm_count = 1;
+    int pair_slots = 0;   // co-resident two-CTA clusters of the current pair kernel
     unsigned long long wait_ns = 0;
     int drop_b = -1;
     std::map<std::string, Kernel> kernels;   // generated kernels of this plan, by name
+    // tensor map of the last output pointer (tiled-store epilogue)
+    const float* map_y = nullptr;
+    bool map_ok = false;
+    alignas(64) unsigned long long map[16] = {};
 };
 
 namespace {
@@ -154,7 +164,10 @@ int tc_threads(const TcConfig& c) { return 64 + 32 * c.ew + 32 * c.cw; }
 std::string tc_kernel_name(int nc, int split, int fw, const TcConfig& c, const std::string& snippet) {
     char b[96];
     snprintf(b, sizeof b, "fbc_tc_c%d_s%d_f%d_b%d_e%d_z%d_w%d", nc, split, fw, c.bt, c.ew, c.fuse, c.cw);
-    return snippet.empty() ? std::string(b) : std::string(b) + "_u" + snippet_tag(snippet);
+    std::string name = b;
+    if (c.ts) name += "_t" + std::to_string(c.ts) + "s" + std::to_string(c.sb);
+    if (c.mc) name += "_m";
+    return snippet.empty() ? name : name + "_u" + snippet_tag(snippet);
 }
 
 // The NVRTC source of one kernel: parameter block, kernel templates, and an
@@ -165,10 +178,12 @@ std::string tc_kernel_source(int nc, int split, int fw, const TcConfig& c, const
       << snippet_definition(snippet);
     o << "static_assert(sizeof(FbcTcParams) == " << sizeof(FbcTcParams)
       << ", \"host and device disagree on the parameter block\");\n";
-    o << "extern \"C\" __global__ void __launch_bounds__(" << tc_threads(c) << ", 1) "
+    o << "extern \"C\" __global__ void " << (c.mc ? "__cluster_dims__(2, 1, 1) " : "") << "__launch_bounds__("
+      << tc_threads(c) << ", 1) "
       << tc_kernel_name(nc, split, fw, c, snippet) << "(const __grid_constant__ FbcTcParams P) {\n"
       << "  fbc_tc_corr_body<" << nc << "," << split << "," << fw << "," << c.bt << "," << c.ew << ","
-      << c.fuse << "," << c.cw << "," << (snippet.empty() ? 0 : 1) << ">(P);\n}\n";
+      << c.fuse << "," << c.cw << "," << (snippet.empty() ? 0 : 1) << "," << c.ts << "," << (c.ts ? c.sb : 1) << ","
+      << c.mc << ">(P);\n}\n";
     return o.str();
 }
 
@@ -187,6 +202,39 @@ bool fuse_ok(int fuse, int cw, int D, int nc, int fw) {
     return fuse == 2 || (nc <= 4 && (kTileM + fw - 1) * nc <= FBC_TC_CONV_ITEMS * cw * 32);
 }
 
+// Tiled stores of 32 pixels x 32 filters: every 32-pixel group of a tile in one
+// output row (W % 32 == 0), a row stride of y in 16-byte units (N % 4 == 0), and
+// 32-column chunks that never cross into the next filter tile (nt % 32 == 0).
+bool ts_ok(int ts, int sb, int W, int N, int nt) {
+    if (ts == 0) return sb == 0;
+    if (ts == 1) return sb == 1;   // staged transpose: any shape
+    return ts == 32 && sb >= 1 && sb <= 3 && W % 32 == 0 && N % 4 == 0 && nt % 32 == 0;
+}
+
+// Pixels per A chunk plane: at least the slab (128 + fw - 1), padded so that the
+// converters' 16-byte writes are spread over the eight 16-byte bank groups.  A
+// converter thread writes the chunk (pixel item / nc, plane item % nc) at
+// plane * lp * 16 + pixel * 16; eight consecutive items form one shared-memory
+// phase, so the padding e (lp = base + e) is the one that minimises the
+// largest number of those eight writes landing in one bank group.
+int a_plane_pixels(int slab, int nc) {
+    const int base = (slab + 7) / 8 * 8;
+    int best_e = 0, best = 1 << 30;
+    for (int e = 0; e < 8; ++e) {
+        int worst = 0;
+        for (int p0 = 0; p0 < 8 * nc; p0 += 8) {   // the phase pattern repeats after 8 nc items
+            int hits[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            for (int i = p0; i < p0 + 8; ++i) {
+                const int px = i / nc, c = i % nc;
+                ++hits[((c * (base + e)) + px) & 7];
+            }
+            for (int h : hits) worst = std::max(worst, h);
+        }
+        if (worst < best) { best = worst; best_e = e; }
+    }
+    return base + best_e;
+}
+
 // Lay out shared memory, pipeline depths and the workspace for one configuration.
 bool tc_layout(TcPlan* p, const TcConfig& c, bool commit) {
     const int nc = p->nc;
@@ -195,7 +243,7 @@ bool tc_layout(TcPlan* p, const TcConfig& c, bool commit) {
     filter_tiles(p->N, c.ntmax, &nt, &ntn);
     const long long mvirt = (long long)Ho * p->W;
     const int mtiles = (int)((mvirt + kTileM - 1) / kTileM);
-    const int lp = (kTileM + p->fw - 1 + 7) / 8 * 8;
+    const int lp = a_plane_pixels(kTileM + p->fw - 1, nc);
     const int halves = p->split ? 2 : 1;
     const uint32_t a_slot = (uint32_t)align_up((size_t)nc * lp * 16 * halves, 128);
     if (c.bt < 1 || c.bt > p->fw || (c.ew != 4 && c.ew != 8)) return false;
@@ -204,7 +252,13 @@ bool tc_layout(TcPlan* p, const TcConfig& c, bool commit) {
     const uint32_t b_stage = (uint32_t)align_up((size_t)c.bt * nc * nt * 16 * halves, 128);
     const uint32_t raw_slot = (uint32_t)align_up((size_t)(kTileM + p->fw - 1) * p->D * 4, 128);
     if (c.na < 2 || c.nb < 2 || (c.fuse == 2 && c.nr < 2)) return false;
-    const size_t need = (size_t)c.na * a_slot + (size_t)c.nb * b_stage + (size_t)c.nr * raw_slot + 512;
+    if (!ts_ok(c.ts, c.sb, p->W, p->N, nt)) return false;
+    // pairs: in-kernel conversion only (a phantom tile's slab rows are read with
+    // bounds checks), and at least one pair of tiles
+    if (c.mc != 0 && (c.mc != 1 || c.fuse == 0 || mtiles * ntn < 2)) return false;
+    // staging: a 1024-byte aligned run of ew * sb boxes placed after the barriers
+    const size_t staging = c.ts ? (size_t)c.ew * c.sb * FBC_TC_ST_BOX + 1024 : 0;
+    const size_t need = (size_t)c.na * a_slot + (size_t)c.nb * b_stage + (size_t)c.nr * raw_slot + 512 + staging;
     if (need > kSmemMax) return false;
     if (!commit) return true;
     p->cfg = c;
@@ -214,6 +268,7 @@ bool tc_layout(TcPlan* p, const TcConfig& c, bool commit) {
     k.npix = (long long)p->H * p->W;
     k.W = p->W; k.Ho = Ho; k.Wo = Wo; k.N = p->N; k.D = p->D;
     k.fh = p->fh; k.nt = nt; k.ntn = ntn; k.mtiles = mtiles;
+    k.mtiles_s = c.mc ? (mtiles + 1) / 2 * 2 : mtiles;
     k.lp = lp; k.na = c.na; k.nb = c.nb;
     k.a_slot = a_slot; k.b_stage = b_stage;
     k.a_tx = (uint32_t)(nc * (kTileM + p->fw - 1) * 16 * halves);
@@ -229,7 +284,9 @@ bool tc_layout(TcPlan* p, const TcConfig& c, bool commit) {
     k.epi = p->epi; k.lo = p->lo; k.hi = p->hi;
     k.wait_ns = p->wait_ns;
     k.drop_b = p->drop_b;
-    p->smem = k.bar_off + 512;
+    k.st_off = k.bar_off + 512;
+    p->smem = k.st_off + staging;
+    p->map_y = nullptr;   // re-encode for the next call
 
     const size_t xplanes = (size_t)nc * k.npix_pad * 16;
     const size_t wplanes = (size_t)ntn * p->fh * p->fw * nc * nt * 16;
@@ -249,8 +306,12 @@ bool tc_layout(TcPlan* p, const TcConfig& c, bool commit) {
     const long long wblocks = ((long long)ntn * p->fh * p->fw * nc * nt + 255) / 256;
     if (c.fuse) sp.xblocks = 0;   // x is converted inside the correlation kernel
     p->split_blocks = (int)(sp.xblocks + wblocks);
-    // one CTA per SM (the 512 TMEM columns)
-    p->grid = std::min(mtiles * ntn, std::max(1, p->sm_count));
+    // one CTA per SM (the 512 TMEM columns); pairs: two CTAs per pair of tiles, as
+    // many pairs as can be resident at once (set from the occupancy query)
+    if (c.mc)
+        p->grid = 2 * std::min(k.mtiles_s * ntn / 2, std::max(1, p->pair_slots));
+    else
+        p->grid = std::min(mtiles * ntn, std::max(1, p->sm_count));
     return true;
 }
 
@@ -267,8 +328,20 @@ size_t tc_ws_need(TcPlan* p, const TcConfig& c) {
 std::vector<TcConfig> tc_candidate_configs(TcPlan* p) {
     // widest filter tile first; within it raw-ring conversion, register
     // conversion, pre-pass; taps per stage from the most (fewest copies and
-    // barrier handoffs) down, each with the deepest B ring that fits
+    // barrier handoffs) down, each with the deepest B ring that fits.  Every
+    // configuration with eight epilogue warps is also offered with the staged
+    // (ts = 1) and the tiled-store (ts = 32) epilogue, again with the deepest
+    // ring beside their staging slots.  Pairs (mc = 1) are selectable by spec
+    // only: on the workloads measured they were never faster.
     std::vector<TcConfig> out;
+    auto deepest = [&](TcConfig c) -> int {
+        int best = 0;
+        for (int nb = 2; nb <= 12; ++nb) {
+            c.nb = nb;
+            if (tc_layout(p, c, false)) best = nb;
+        }
+        return best;
+    };
     const int widths[] = {256, 128};
     for (int ntmax : widths) {
         if (ntmax == 128 && p->N <= 128) continue;
@@ -279,10 +352,15 @@ std::vector<TcConfig> tc_candidate_configs(TcPlan* p) {
                     for (int bt = std::min(p->fw, 5); bt >= 1; --bt)
                         for (int ew : {8, 4})
                             for (int na = 2; na <= 3; ++na) {
-                                int best = 0;
-                                for (int nb = 2; nb <= 12; ++nb)
-                                    if (tc_layout(p, TcConfig{na, nb, ntmax, bt, ew, fuse, nr, cw}, false)) best = nb;
-                                if (best) out.push_back(TcConfig{na, best, ntmax, bt, ew, fuse, nr, cw});
+                                TcConfig c{na, 0, ntmax, bt, ew, fuse, nr, cw};
+                                if ((c.nb = deepest(c))) out.push_back(c);
+                                if (ew != 8) continue;
+                                for (int ts : {1, 32}) {
+                                    TcConfig t = c;
+                                    t.ts = ts;
+                                    t.sb = 1;
+                                    if ((t.nb = deepest(t))) out.push_back(t);
+                                }
                             }
             }
     }
@@ -290,10 +368,13 @@ std::vector<TcConfig> tc_candidate_configs(TcPlan* p) {
 }
 
 std::string format_spec(const TcConfig& c) {
-    char b[96];
+    char b[128];
     snprintf(b, sizeof b, "tcgen05:na=%d,nb=%d,nt=%d,bt=%d,ew=%d,fz=%d,nr=%d,cw=%d", c.na, c.nb, c.ntmax,
              c.bt, c.ew, c.fuse, c.nr, c.cw);
-    return b;
+    std::string out = b;
+    if (c.ts) out += ",ts=" + std::to_string(c.ts) + ",sb=" + std::to_string(c.sb);
+    if (c.mc) out += ",mc=1";
+    return out;
 }
 
 bool parse_tc_spec(const std::string& s, TcConfig* c) {
@@ -301,7 +382,19 @@ bool parse_tc_spec(const std::string& s, TcConfig* c) {
     int used = 0;
     const int n = sscanf(s.c_str(), "tcgen05:na=%d,nb=%d,nt=%d,bt=%d,ew=%d,fz=%d,nr=%d,cw=%d%n", &t.na, &t.nb,
                          &t.ntmax, &t.bt, &t.ew, &t.fuse, &t.nr, &t.cw, &used);
-    if (n != 8 || used != (int)s.size()) return false;
+    if (n != 8) return false;
+    // optional suffixes: staged / tiled stores, pairs
+    int used2 = 0;
+    if (sscanf(s.c_str() + used, ",ts=%d,sb=%d%n", &t.ts, &t.sb, &used2) == 2) {
+        if ((t.ts != 32 && t.ts != 1) || t.sb < 1 || t.sb > 3 || (t.ts == 1 && t.sb != 1)) return false;
+        used += used2;
+    }
+    used2 = 0;
+    if (s.compare(used, std::string::npos, ",mc=1") == 0) {
+        t.mc = 1;
+        used += 5;
+    }
+    if (used != (int)s.size()) return false;
     if ((t.fuse == 0) != (t.cw == 0) || (t.cw != 0 && t.cw != 4 && t.cw != 8)) return false;
     if (t.fuse < 0 || t.fuse > 2 || (t.ew != 4 && t.ew != 8)) return false;
     if ((t.fuse == 2) != (t.nr > 0) || t.nr < 0 || t.nr > 4) return false;
@@ -357,6 +450,16 @@ fbcorr_status_t tc_set_spec(TcPlan* p, const std::string& spec) {
     Kernel k;
     FBC_TRY(tc_kernel(p, c, &k));
     tc_layout(p, c, true);
+    if (c.mc) {
+        // as many pairs as the device keeps resident at this shared-memory size
+        k.smem = p->smem;
+        int slots = 0;
+        FBC_TRY(cluster_occupancy(k, 2, &slots));
+        if (slots < 1)
+            return set_error(FBCORR_ERR_UNSUPPORTED, "tcgen05 spec '%s': no two-CTA cluster fits", spec.c_str());
+        p->pair_slots = slots;
+        tc_layout(p, c, true);
+    }
     return FBCORR_OK;
 }
 
@@ -436,6 +539,25 @@ fbcorr_status_t tc_forward(TcPlan* p, const float* x, const float* w, float* y, 
     kp.y = y;
     kp.err = err_word;
     kp.xraw = x;
+    kp.tma_y = 0;
+    if (p->cfg.ts > 1) {
+        // y as {N, W', H'}: pixels q >= W' and filters n >= N of a box are clipped;
+        // a y that is not 16-byte aligned keeps the direct stores
+        if (p->map_y != y) {
+            const unsigned long long dims[3] = {(unsigned long long)p->N, (unsigned long long)p->kp.Wo,
+                                                (unsigned long long)p->kp.Ho};
+            const unsigned long long strides[2] = {(unsigned long long)p->N * 4,
+                                                   (unsigned long long)p->N * p->kp.Wo * 4};
+            const unsigned box[3] = {32, (unsigned)p->cfg.ts, 1};
+            p->map_ok = (reinterpret_cast<uintptr_t>(y) & 15) == 0 &&
+                        encode_f32_store_map(p->map, y, dims, strides, box);
+            p->map_y = y;
+        }
+        if (p->map_ok) {
+            memcpy(kp.ymap, p->map, sizeof kp.ymap);
+            kp.tma_y = 1;
+        }
+    }
     if (ev_start) FBC_CUDA(cudaEventRecord(ev_start, s));
     void* args[] = {&kp};
     FBC_TRY(launch(k, dim3(p->grid), args, s));

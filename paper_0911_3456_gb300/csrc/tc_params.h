@@ -9,6 +9,7 @@
 #define FBC_TC_ACC_COLS 256     // TMEM columns per accumulator (MMA N <= 256)
 #define FBC_TC_TMEM_COLS 512    // two accumulators
 #define FBC_TC_CONV_ITEMS 5     // 32-byte x chunks per converter thread and slab row
+#define FBC_TC_ST_BOX 4096      // bytes of one staged store box: 32 pixels x 32 FP32 columns
 
 // Error codes written to the host-mapped error word when a bounded wait expires.
 #define FBC_TC_ERR_WAIT_A 1
@@ -17,6 +18,9 @@
 #define FBC_TC_ERR_WAIT_EMPTY 4
 
 struct FbcTcParams {
+    // CUtensorMap of y as {N, Wo, Ho} FP32, 128-byte swizzle, box {32, 32, 1}:
+    // the target of the tiled-store epilogue (TS > 0 and tma_y != 0)
+    alignas(64) unsigned long long ymap[16];
     const unsigned char* xhi;   // [nc][npix_pad][16 B] pre-split x planes (unfused)
     const unsigned char* xlo;
     const unsigned char* whi;   // [ntn][fh*fw][nc][nt][16 B]
@@ -29,6 +33,7 @@ struct FbcTcParams {
     unsigned long long wait_ns; // bound of every mbarrier wait
     int W, Ho, Wo, N, D;
     int fh, nt, ntn, mtiles;
+    int mtiles_s;               // pixel tiles per filter tile in the schedule (MC: mtiles rounded up to even)
     int lp;                     // pixels per chunk plane of an A slot
     int na, nb;                 // A slots, B stages
     int alook;                  // rows by which the A side (slabs or raw rows) runs ahead of the B stages
@@ -40,6 +45,8 @@ struct FbcTcParams {
     unsigned int a_tx;              // bytes copied per A slot (unfused)
     unsigned int a_off, b_off, bar_off;
     unsigned int raw_off, raw_slot;   // raw-row ring (FUSE = 2): offset, bytes per slot
+    unsigned int st_off;              // store staging (TS > 0): offset, 1024-byte aligned at run time
+    int tma_y;                        // 1: ymap describes y, epilogue stores go through it
 };
 
 #endif

@@ -135,6 +135,9 @@ def test_explicit_tile_specs_compile(lib, spec):
     (8, 9, b"tcgen05:na=2,nb=4,nt=128,bt=2,ew=4,fz=1,nr=0,cw=8"),     # paper row 1 depth, odd last stage
     (48, 7, b"tcgen05:na=2,nb=4,nt=256,bt=4,ew=8,fz=2,nr=2,cw=8"),    # six chunk planes, raw-row ring
     (64, 13, b"tcgen05:na=2,nb=2,nt=256,bt=1,ew=4,fz=0,nr=0,cw=0"),   # the deepest supported depth, pre-pass
+    (32, 5, b"tcgen05:na=3,nb=2,nt=256,bt=5,ew=8,fz=1,nr=0,cw=8,ts=32,sb=1"),       # tiled bulk stores
+    (16, 3, b"tcgen05:na=3,nb=4,nt=256,bt=2,ew=8,fz=2,nr=2,cw=8,ts=1,sb=1,mc=1"),   # staged stores, tile pairs
+    (32, 5, b"tcgen05:na=2,nb=3,nt=256,bt=1,ew=4,fz=1,nr=0,cw=4,ts=32,sb=3,mc=1"),  # three staging slots, pairs
 ])
 def test_tensor_core_kernels_compile(lib, D, f, spec):
     """The run-time generated tcgen05 kernel of a spec compiles for sm_103a in
@@ -152,6 +155,11 @@ def test_tensor_core_kernels_compile(lib, D, f, spec):
     (32, 5, b"tcgen05:na=2,nb=4,nt=256,bt=2,ew=4,fz=0", 1),        # missing field: not a spec of this kernel
     (32, 5, b"tcgen05:na=2,nb=4,nt=256,bt=2,ew=4,fz=2,nr=0,cw=8", 1),   # the raw ring needs slots
     (32, 5, b"tcgen05:na=2,nb=4,nt=256,bt=2,ew=4,fz=1,nr=0,cw=0", 1),   # in-kernel conversion needs converter warps
+    (32, 5, b"tcgen05:na=2,nb=4,nt=256,bt=2,ew=8,fz=1,nr=0,cw=8,ts=2,sb=1", 1),    # store modes: 1 or 32
+    (32, 5, b"tcgen05:na=2,nb=4,nt=256,bt=2,ew=8,fz=1,nr=0,cw=8,ts=32,sb=4", 1),   # at most three staging slots
+    (32, 5, b"tcgen05:na=2,nb=4,nt=256,bt=2,ew=8,fz=1,nr=0,cw=8,ts=1,sb=2", 1),    # the staged path has one slot
+    (32, 5, b"tcgen05:na=2,nb=4,nt=256,bt=2,ew=8,fz=1,nr=0,cw=8,mc=2", 1),         # pairs: mc=1 only
+    (32, 5, b"tcgen05:na=2,nb=4,nt=256,bt=2,ew=8,fz=1,nr=0,cw=8,mc=1,ts=1,sb=1", 1),   # suffix order is fixed
 ])
 def test_tensor_core_spec_refusals(lib, D, f, spec, status):
     log = ctypes.create_string_buffer(1 << 16)

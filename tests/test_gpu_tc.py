@@ -206,6 +206,45 @@ def test_every_tensor_core_configuration_matches(mode):
 
 
 @pytest.mark.parametrize("mode", ["bf16", "bf16x3"])
+@pytest.mark.parametrize("shape", [(37, 96, 16, 96, 3, 3), (37, 128, 32, 320, 5, 5), (21, 140, 32, 40, 3, 5)],
+                         ids=lambda s: "x".join(map(str, s)))
+def test_store_modes_and_pairs_bit_exact(mode, shape):
+    """Direct stores, the staged transpose (ts=1), tiled bulk stores through a
+    tensor map (ts=32: needs W % 32 == 0, N % 4 == 0 and a filter tile that is a
+    multiple of 32, else refused) and tile pairs sharing multicast B stages
+    (mc=1; an odd pixel-tile count -- 27 and 33 tiles here -- runs a phantom
+    tile) give the oracle's bits on integer inputs, with and without the clamp;
+    an output that is not 16-byte aligned is refused before any launch."""
+    torch = torch_cuda()
+    from paper_0911_3456_gb300 import _capi as C
+    from paper_0911_3456_gb300.api import Plan
+    H, W, D, N, fh, fw = shape
+    wl = inputs.random_case(1750, *shape, kind="int")
+    x, w = dev(wl.x, torch), dev(wl.w, torch)
+    tiled_ok = W % 32 == 0 and N % 4 == 0
+    base = "tcgen05:na=2,nb=2,nt=256,bt=1,ew=8,fz=1,nr=0,cw=8"
+    suffixes = ("", ",ts=1,sb=1", ",ts=32,sb=1", ",ts=32,sb=2", ",mc=1", ",ts=1,sb=1,mc=1", ",ts=32,sb=1,mc=1")
+    for clamp in (None, (-40.0, 40.0)):
+        ref = oracle.fwd(wl.x, wl.w, epilogue=clamp)
+        p = Plan(wl.x.shape, wl.w.shape, mode, clamp)
+        ran = 0
+        for suffix in suffixes:
+            try:
+                p.set_variant(base + suffix)
+            except C.FbcorrError as e:
+                assert "ts=32" in suffix and not tiled_ok, (suffix, str(e))
+                continue
+            assert np.array_equal(host(p.forward(x, w)), ref), suffix
+            if "ts=32" in suffix:
+                buf = torch.empty(ref.size + 1, device="cuda")
+                with pytest.raises(C.FbcorrError) as e:
+                    p.forward(x, w, buf[1:].view(ref.shape))   # 4 bytes past a 16-byte boundary
+                assert e.value.status_name == "FBCORR_ERR_ALIGNMENT"
+            ran += 1
+        assert ran == (7 if tiled_ok else 4)
+
+
+@pytest.mark.parametrize("mode", ["bf16", "bf16x3"])
 @pytest.mark.parametrize("shape", [(20, 150, 16, 16, 3, 3), (37, 45, 4, 20, 4, 2), (18, 260, 28, 40, 7, 7),
                                    (9, 9, 12, 3, 9, 9)], ids=lambda s: "x".join(map(str, s)))
 def test_fused_conversion_matches_prepass(mode, shape):
