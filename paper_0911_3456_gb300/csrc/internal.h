@@ -68,6 +68,11 @@ fbcorr_status_t rtcg_precompile(const std::vector<std::string>& sources);
 // Compile only (no GPU needed); returns the NVRTC log on failure.
 fbcorr_status_t rtcg_compile_only(const std::string& src, std::string* log);
 fbcorr_status_t launch(const Kernel& k, dim3 grid, void** args, cudaStream_t stream);
+// Launch allowed to begin before the previous kernel in the stream has finished
+// (programmatic dependent launch): the kernel must execute griddepcontrol.wait
+// before it reads anything that kernel writes.  Falls back to launch() on a
+// driver without cuLaunchKernelEx.
+fbcorr_status_t launch_dependent(const Kernel& k, dim3 grid, void** args, cudaStream_t stream);
 // Largest number of co-resident clusters of `cluster` CTAs of kernel `k` (its
 // compile-time cluster shape, block size and dynamic shared memory).
 fbcorr_status_t cluster_occupancy(const Kernel& k, int cluster, int* clusters);

@@ -43,6 +43,7 @@ struct DriverApi {
                                              const CUDA_KERNEL_NODE_PARAMS*) = nullptr;
     CUresult (*occupancy)(int*, CUfunction, int, size_t) = nullptr;
     CUresult (*clusterOccupancy)(int*, CUfunction, const CUlaunchConfig*) = nullptr;   // optional
+    CUresult (*launchKernelEx)(const CUlaunchConfig*, CUfunction, void**, void**) = nullptr;   // optional
 };
 
 std::mutex g_mu;
@@ -74,6 +75,7 @@ fbcorr_status_t driver_api(DriverApi** out) {
                   resolve("cuOccupancyMaxActiveBlocksPerMultiprocessor", &d.occupancy);
         if (!ok) return set_error(FBCORR_ERR_CUDA, "could not resolve CUDA driver entry points");
         if (!resolve("cuOccupancyMaxActiveClusters", &d.clusterOccupancy)) d.clusterOccupancy = nullptr;
+        if (!resolve("cuLaunchKernelEx", &d.launchKernelEx)) d.launchKernelEx = nullptr;
         d.ok = true;
         g_drv = d;
     }
@@ -374,6 +376,34 @@ fbcorr_status_t launch(const Kernel& k, dim3 grid, void** args, cudaStream_t str
     if (r != CUDA_SUCCESS)
         return set_error(FBCORR_ERR_CUDA, "cuLaunchKernel(%s grid=%u,%u,%u block=%d smem=%zu): %s",
                          k.name.c_str(), grid.x, grid.y, grid.z, k.threads, k.smem, cu_err(r));
+    return FBCORR_OK;
+}
+
+fbcorr_status_t launch_dependent(const Kernel& k, dim3 grid, void** args, cudaStream_t stream) {
+    DriverApi* drv = nullptr;
+    FBC_TRY(driver_api(&drv));
+    if (!drv->launchKernelEx) return launch(k, grid, args, stream);
+    if (!k.fn) return set_error(FBCORR_ERR_INTERNAL, "launch of an unloaded kernel");
+    CUlaunchAttribute attr;
+    memset(&attr, 0, sizeof attr);
+    attr.id = CU_LAUNCH_ATTRIBUTE_PROGRAMMATIC_STREAM_SERIALIZATION;
+    attr.value.programmaticStreamSerializationAllowed = 1;
+    CUlaunchConfig cfg;
+    memset(&cfg, 0, sizeof cfg);
+    cfg.gridDimX = grid.x;
+    cfg.gridDimY = grid.y;
+    cfg.gridDimZ = grid.z;
+    cfg.blockDimX = (unsigned)k.threads;
+    cfg.blockDimY = 1;
+    cfg.blockDimZ = 1;
+    cfg.sharedMemBytes = (unsigned)k.smem;
+    cfg.hStream = (CUstream)stream;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    CUresult r = drv->launchKernelEx(&cfg, k.fn, args, nullptr);
+    if (r != CUDA_SUCCESS)
+        return set_error(FBCORR_ERR_CUDA, "cuLaunchKernelEx(%s grid=%u block=%d smem=%zu, dependent): %s",
+                         k.name.c_str(), grid.x, k.threads, k.smem, cu_err(r));
     return FBCORR_OK;
 }
 

@@ -176,6 +176,9 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
     if (warp == 0) {
         // ------------------------------------------------------------ producer
         if (lane == 0) {
+            // launched as a dependent of the operand split: its planes (B, and the
+            // pre-split x of FUSE = 0) are complete and visible after this wait
+            asm volatile("griddepcontrol.wait;" ::: "memory");
             fbc_u32 a_it = 0, b_it = 0, r_it = 0;
             int as = 0, bs = 0, rs = 0;
             fbc_u32 aph = 0, bph = 0, rph = 0;

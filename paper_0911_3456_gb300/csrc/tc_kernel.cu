@@ -59,6 +59,9 @@ struct SplitParams {
 
 
 __global__ void __launch_bounds__(256) fbc_tc_split(const __grid_constant__ SplitParams S) {
+    // the correlation kernel that follows may start now: it waits (griddepcontrol.wait)
+    // for this grid's completion before its producer reads any operand plane
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     if ((long long)blockIdx.x < S.xblocks) {
         // one thread per pixel: contiguous reads of its D channels, and for
         // every chunk plane a 16-byte store that is contiguous across the warp
@@ -96,25 +99,39 @@ __global__ void __launch_bounds__(256) fbc_tc_split(const __grid_constant__ Spli
             }
         }
     } else {
-        const long long idx = ((long long)blockIdx.x - S.xblocks) * 256 + threadIdx.x;
+        // one thread per (filter, tap), filters fastest: it reads the tap's D
+        // contiguous channels and writes one 16-byte chunk to each of the nc
+        // planes [ntn][taps][nc][nt], contiguous across the warp in every plane
+        const long long t = ((long long)blockIdx.x - S.xblocks) * 256 + threadIdx.x;
         const int taps = S.fh * S.fw;
-        const long long total = (long long)S.ntn * taps * S.nc * S.nt;
-        if (idx >= total) return;
-        const int nl = (int)(idx % S.nt);
-        long long t = idx / S.nt;
-        const int c = (int)(t % S.nc);
-        t /= S.nc;
-        const int tap = (int)(t % taps);
-        const int nti = (int)(t / taps);
+        const long long total = (long long)S.ntn * taps * S.nt;
+        if (t >= total) return;
+        const int nl = (int)(t % S.nt);
+        const long long u = t / S.nt;
+        const int tap = (int)(u % taps);
+        const int nti = (int)(u / taps);
         const int n = nti * S.nt + nl;
         const int i = tap / S.fw, j = tap % S.fw;
-        float v[8];
+        const float* src = S.w + (((long long)n * S.fh + i) * S.fw + j) * S.D;
+        const bool inside = n < S.N;
+        const bool vec = inside && (S.D & 3) == 0;
+        for (int c = 0; c < S.nc; ++c) {
+            float v[8];
+            if (vec && c * 8 + 8 <= S.D) {
+                const float4 a = __ldg(reinterpret_cast<const float4*>(src + c * 8));
+                const float4 b = __ldg(reinterpret_cast<const float4*>(src + c * 8 + 4));
+                v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+                v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+            } else {
 #pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            const int d = c * 8 + k;
-            v[k] = (n < S.N && d < S.D) ? __ldg(S.w + (((long long)n * S.fh + i) * S.fw + j) * S.D + d) : 0.f;
+                for (int k = 0; k < 8; ++k) {
+                    const int d = c * 8 + k;
+                    v[k] = (inside && d < S.D) ? __ldg(src + d) : 0.f;
+                }
+            }
+            const long long idx = (u * S.nc + c) * S.nt + nl;
+            split8(v, reinterpret_cast<uint4*>(S.whi) + idx, reinterpret_cast<uint4*>(S.wlo) + idx, S.split);
         }
-        split8(v, reinterpret_cast<uint4*>(S.whi) + idx, reinterpret_cast<uint4*>(S.wlo) + idx, S.split);
     }
 }
 
@@ -303,7 +320,7 @@ bool tc_layout(TcPlan* p, const TcConfig& c, bool commit) {
     sp.D = p->D; sp.nc = nc; sp.N = p->N; sp.fh = p->fh; sp.fw = p->fw; sp.nt = nt; sp.ntn = ntn;
     sp.split = p->split;
     sp.xblocks = (k.npix_pad + 255) / 256;
-    const long long wblocks = ((long long)ntn * p->fh * p->fw * nc * nt + 255) / 256;
+    const long long wblocks = ((long long)ntn * p->fh * p->fw * nt + 255) / 256;
     if (c.fuse) sp.xblocks = 0;   // x is converted inside the correlation kernel
     p->split_blocks = (int)(sp.xblocks + wblocks);
     // one CTA per SM (the 512 TMEM columns); pairs: two CTAs per pair of tiles, as
@@ -329,9 +346,9 @@ std::vector<TcConfig> tc_candidate_configs(TcPlan* p) {
     // widest filter tile first; within it raw-ring conversion, register
     // conversion, pre-pass; taps per stage from the most (fewest copies and
     // barrier handoffs) down, each with the deepest B ring that fits.  Every
-    // configuration with eight epilogue warps is also offered with the staged
-    // (ts = 1) and the tiled-store (ts = 32) epilogue, again with the deepest
-    // ring beside their staging slots.  Pairs (mc = 1) are selectable by spec
+    // configuration is also offered with the tiled-store (ts = 32) epilogue, and
+    // with eight epilogue warps with the staged (ts = 1) one, again with the
+    // deepest ring beside their staging slots.  Pairs (mc = 1) are selectable by spec
     // only: on the workloads measured they were never faster.
     std::vector<TcConfig> out;
     auto deepest = [&](TcConfig c) -> int {
@@ -354,8 +371,8 @@ std::vector<TcConfig> tc_candidate_configs(TcPlan* p) {
                             for (int na = 2; na <= 3; ++na) {
                                 TcConfig c{na, 0, ntmax, bt, ew, fuse, nr, cw};
                                 if ((c.nb = deepest(c))) out.push_back(c);
-                                if (ew != 8) continue;
                                 for (int ts : {1, 32}) {
+                                    if (ew != 8 && ts == 1) continue;
                                     TcConfig t = c;
                                     t.ts = ts;
                                     t.sb = 1;
@@ -529,6 +546,9 @@ fbcorr_status_t tc_forward(TcPlan* p, const float* x, const float* w, float* y, 
     sp.xlo = base + p->off_xlo;
     sp.whi = base + p->off_whi;
     sp.wlo = base + p->off_wlo;
+    // timing events bracket both launches of the step: an event between them
+    // would hold the correlation kernel back until the split has finished
+    if (ev_start) FBC_CUDA(cudaEventRecord(ev_start, s));
     fbc_tc_split<<<p->split_blocks, 256, 0, s>>>(sp);
     FBC_CUDA(cudaGetLastError());
     FbcTcParams kp = p->kp;
@@ -558,9 +578,10 @@ fbcorr_status_t tc_forward(TcPlan* p, const float* x, const float* w, float* y, 
             kp.tma_y = 1;
         }
     }
-    if (ev_start) FBC_CUDA(cudaEventRecord(ev_start, s));
     void* args[] = {&kp};
-    FBC_TRY(launch(k, dim3(p->grid), args, s));
+    // dependent launch: the prologue (barriers, TMEM, converters' first rows)
+    // overlaps the operand split
+    FBC_TRY(launch_dependent(k, dim3(p->grid), args, s));
     if (ev_stop) FBC_CUDA(cudaEventRecord(ev_stop, s));
     return FBCORR_OK;
 }
