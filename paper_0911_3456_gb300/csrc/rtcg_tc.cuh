@@ -50,6 +50,11 @@
 // issues hi*lo + lo*hi, then hi*hi, into the same FP32 accumulator (the lo*lo
 // term, ~2^-16 relative, is dropped).
 //
+// Tail halves: tiles t >= nfull, the last partial round of a single 256-wide
+// filter tile, run as two 128-column work items each (instruction N = 128, B
+// from half-width planes), so that round keeps twice as many SMs busy for half
+// as long.
+//
 // Pairs (MC = 1): a tile needs the whole filter bank from L2 (400 KB in BF16 for
 // 256 filters of 5x5x32), more than the bulk-copy path delivers per SM in one
 // tile's MMA time.  The kernel then runs as clusters of two CTAs that process
@@ -148,20 +153,44 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
     // same filter tiles in the same order (mtiles_s is even) and share every B
     // stage.  A pixel tile >= mtiles (odd mtiles) is a phantom: its slab rows lie
     // past the output and its results are never stored.
+    // Tail halves (MC = 0, one filter tile of 256): the tiles from nfull on, the
+    // last partial round, run as two work items each, one per 128-column half of
+    // the filter tile, so that round occupies twice as many SMs for half as long;
+    // a half takes its B operand from the half-width planes whi2 / wlo2.
     const int nsched = P.mtiles_s * P.ntn;
     const int unit = MC ? (int)blockIdx.x >> 1 : (int)blockIdx.x;
     const int nunits = MC ? (int)gridDim.x >> 1 : (int)gridDim.x;
-    const int nwork = MC ? nsched >> 1 : nsched;
-    const int my_tiles = unit < nwork ? (nwork - 1 - unit) / nunits + 1 : 0;
-    auto tile_of = [&](int k) -> int {
-        const int w = unit + k * nunits;
-        return MC ? 2 * w + ((int)blockIdx.x & 1) : w;
+    const int nwork = MC ? nsched >> 1 : P.nfull + 2 * (nsched - P.nfull);
+    const int my_tiles = unit < nwork ? (nwork - 1 - unit) / nunits + 1 : 0;   // work items
+    struct Item {
+        int tile;    // pixel tile t % mtiles_s of filter tile t / mtiles_s
+        int nt;      // filter columns of this item
+        int n0;      // first filter
+        long long wbase;   // byte offset of the item's planes in whi / wlo (half: in whi2 / wlo2)
+        bool half;
     };
+    auto item_of = [&](int k) -> Item {
+        const int w = unit + k * nunits;
+        Item it;
+        it.half = !MC && w >= P.nfull;
+        if (MC) {
+            it.tile = 2 * w + ((int)blockIdx.x & 1);
+        } else if (!it.half) {
+            it.tile = w;
+        } else {
+            it.tile = P.nfull + ((w - P.nfull) >> 1);
+        }
+        const int nti = it.tile / P.mtiles_s;
+        const int h = (w - P.nfull) & 1;
+        it.nt = it.half ? P.nt >> 1 : P.nt;
+        it.n0 = it.half ? h * it.nt : nti * P.nt;
+        it.wbase = (long long)(it.half ? h : nti) * P.fh * FW * NC * it.nt * 16;
+        return it;
+    };
+    auto tile_of = [&](int k) -> int { return item_of(k).tile; };
     const int R = my_tiles * P.fh;                    // filter rows this CTA runs, in order
     const fbc_u32 plane = (fbc_u32)P.lp * 16u;        // bytes per A chunk plane (shared)
-    const fbc_u32 bplane = (fbc_u32)P.nt * 16u;       // bytes per B chunk plane (shared)
     const fbc_u32 a_half = NC * plane;                // offset of the lo planes in an A slot
-    const fbc_u32 b_half = NC * bplane;               // bytes per tap and half of a B stage
     // first input pixel of slab row r
     auto row_p0 = [&](int r) -> long long {
         const int tile = tile_of(r / P.fh);
@@ -184,7 +213,6 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
             fbc_u32 aph = 0, bph = 0, rph = 0;
             bool ok = true;
             const fbc_u32 a_copy = (fbc_u32)L * 16u;
-            const long long tap_bytes = (long long)NC * P.nt * 16;
             int next_a = 0;
             for (int r = 0; r < R && ok; ++r) {
                 // the A side of rows up to r + look goes out before the B stages of
@@ -217,10 +245,12 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
                     ++next_a;
                 }
                 if (!ok) break;
-                const int tile = tile_of(r / P.fh);
-                const long long woff = (((long long)(tile / P.mtiles_s) * P.fh + r % P.fh) * FW) * tap_bytes;
-                const fbc_u8* wtap_hi = P.whi + woff;
-                const fbc_u8* wtap_lo = P.wlo + woff;
+                const Item it = item_of(r / P.fh);
+                const long long tap_bytes = (long long)NC * it.nt * 16;   // = the item's b_half
+                const long long woff = it.wbase + (long long)((r % P.fh) * FW) * tap_bytes;
+                const fbc_u8* wtap_hi = (it.half ? P.whi2 : P.whi) + woff;
+                const fbc_u8* wtap_lo = (it.half ? P.wlo2 : P.wlo) + woff;
+                const fbc_u32 b_half = (fbc_u32)tap_bytes;
 #pragma unroll
                 for (int s = 0; s < NST; ++s) {
                     // taps s*BT .. s*BT+tcnt-1 of this filter row are contiguous in the
@@ -264,22 +294,19 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
     } else if (warp == 1) {
         // ------------------------------------------------------------ MMA issuer
         if (lane == 0) {
-            const fbc_u32 idesc = (1u << 4)                                  // D: FP32
-                                  | (1u << 7) | (1u << 10)                   // A, B: BF16
-                                  | ((fbc_u32)(P.nt >> 3) << 17)             // N
-                                  | ((fbc_u32)(FBC_TC_TILE_M >> 4) << 24);   // M
+            const fbc_u32 idesc0 = (1u << 4)                                 // D: FP32
+                                   | (1u << 7) | (1u << 10)                  // A, B: BF16
+                                   | ((fbc_u32)(FBC_TC_TILE_M >> 4) << 24);  // M; N per work item
             // descriptor arithmetic: the start address sits in the low 14 bits as
             // (addr >> 4); every shared address is < 2^18, so adding (offset >> 4)
             // to the descriptor never carries out of that field
             const fbc_u64 adesc0 = fbc_smem_desc(sbase + P.a_off, plane, 128);
-            const fbc_u64 bdesc0 = fbc_smem_desc(sbase + P.b_off, bplane, 128);
-            const fbc_u64 a_step = P.a_slot >> 4, b_step = P.b_stage >> 4;
-            const fbc_u64 ak = (2 * plane) >> 4, bk = (2 * bplane) >> 4;
-            const fbc_u64 alo = a_half >> 4, blo = ((fbc_u64)BT * b_half) >> 4;
-            const fbc_u64 btap = b_half >> 4;   // next tap inside a stage
+            const fbc_u64 a_step = P.a_slot >> 4;
+            const fbc_u64 ak = (2 * plane) >> 4;
+            const fbc_u64 alo = a_half >> 4;
             int as = 0, bs = 0;
             fbc_u32 aph = 0, bph = 0, acc_it = 0;
-            fbc_u64 adesc = adesc0, bdesc = bdesc0;
+            fbc_u64 adesc = adesc0;
             bool ok = true;
             bool issued = false;
             for (int k = 0; k < my_tiles && ok; ++k) {
@@ -289,12 +316,19 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
                     break;
                 fbc_tc_fence_after();
                 const fbc_u32 d_tmem = tmem + (fbc_u32)(acc * FBC_TC_ACC_COLS);
+                // B operand geometry of this work item (a tail half has 128 columns)
+                const int nt_k = item_of(k).nt;
+                const fbc_u32 idesc = idesc0 | ((fbc_u32)(nt_k >> 3) << 17);
+                const fbc_u32 bplane_i = (fbc_u32)nt_k * 16u;
+                const fbc_u32 bhalf_i = NC * bplane_i;
+                const fbc_u64 bk = (2 * bplane_i) >> 4, blo = ((fbc_u64)BT * bhalf_i) >> 4, btap = bhalf_i >> 4;
                 fbc_u32 accumulate = 0;
                 for (int i = 0; i < P.fh && ok; ++i) {
                     if (!(ok = fbc_wait(a_full0 + 8u * as, aph, P, abort_flag, FBC_TC_ERR_WAIT_A))) break;
 #pragma unroll
                     for (int s = 0; s < NST; ++s) {
                         if (!(ok = fbc_wait(b_full0 + 8u * bs, bph, P, abort_flag, FBC_TC_ERR_WAIT_B))) break;
+                        const fbc_u64 bdesc = fbc_smem_desc(sbase + P.b_off + (fbc_u32)bs * P.b_stage, bplane_i, 128);
 #pragma unroll
                         for (int t = 0; t < BT; ++t)
                             if (s * BT + t < FW)
@@ -305,7 +339,7 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
                             fbc_umma_commit_mc(b_empty0 + 8u * bs, 3);   // the stage is free once both CTAs are done
                         else
                             fbc_umma_commit(b_empty0 + 8u * bs);
-                        if (++bs == P.nb) { bs = 0; bph ^= 1; bdesc = bdesc0; } else { bdesc += b_step; }
+                        if (++bs == P.nb) { bs = 0; bph ^= 1; }
                     }
                     if (!ok) break;
                     fbc_umma_commit(a_empty0 + 8u * as);
@@ -334,14 +368,15 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
         int st_slot = 0;
         fbc_u32 acc_it = 0;
         for (int k = 0; k < my_tiles; ++k) {
-            const int tile = tile_of(k);
-            const int mt = tile % P.mtiles_s;
-            const int nti = tile / P.mtiles_s;
+            const Item itm = item_of(k);
+            const int mt = itm.tile % P.mtiles_s;
+            const int nt_i = itm.nt;     // filter columns of this work item, from column 0 of the accumulator
+            const int nb0 = itm.n0;      // its first filter
             const int acc = acc_it & 1;
             if (!fbc_wait(acc_full0 + 8u * acc, (acc_it >> 1) & 1, P, abort_flag, FBC_TC_ERR_WAIT_ACC)) break;
             fbc_tc_fence_after();
             // columns past this tile's last filter hold no result: stop at the tile end as well as N
-            const int nend = min(P.N, (nti + 1) * P.nt);
+            const int nend = min(P.N, nb0 + nt_i);
             if constexpr (TS == 1) {
                 // tcgen05.ld 32x32b (lane l: 32 consecutive columns of pixel m0 + l)
                 // into this warp's swizzled staging slot, read back transposed so
@@ -362,12 +397,12 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
                 const bool vec4 = (P.N & 3) == 0 && (reinterpret_cast<unsigned long long>(P.y) & 15) == 0;
                 const fbc_u32 trow = tmem + ((fbc_u32)(lq * 32) << 16) + (fbc_u32)(acc * FBC_TC_ACC_COLS);
 #pragma unroll 1
-                for (int cc = part; cc < (P.nt + 31) >> 5; cc += EW / 4) {
+                for (int cc = part; cc < (nt_i + 31) >> 5; cc += EW / 4) {
                     fbc_u32 r[32];
                     fbc_tmem_ld32x32b_x32_async(trow + (fbc_u32)(cc * 32), r);
                     fbc_tmem_ld_wait();
                     fbc_reg_fence(r);
-                    const int n0 = nti * P.nt + cc * 32;
+                    const int n0 = nb0 + cc * 32;
                     if (n0 >= nend) continue;   // warp-uniform
                     if constexpr (USER != 0) {
 #pragma unroll
@@ -424,12 +459,12 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
                     const fbc_u32 sw = (fbc_u32)(lane & 7);
                     const fbc_u32 trow = tmem + ((fbc_u32)(lq * 32) << 16) + (fbc_u32)(acc * FBC_TC_ACC_COLS);
 #pragma unroll 1
-                    for (int cc = part; cc < (P.nt >> 5); cc += EW / 4) {
+                    for (int cc = part; cc < (nt_i >> 5); cc += EW / 4) {
                         fbc_u32 r[32];
                         fbc_tmem_ld32x32b_x32_async(trow + (fbc_u32)(cc * 32), r);
                         fbc_tmem_ld_wait();
                         fbc_reg_fence(r);
-                        const int n0 = nti * P.nt + cc * 32;
+                        const int n0 = nb0 + cc * 32;
                         if (!inside || n0 >= P.N) continue;   // warp-uniform
                         if constexpr (USER != 0) {
 #pragma unroll
@@ -463,7 +498,7 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
                 }
             }
             // 16x256b loads of 64 columns (nt is a multiple of 16)
-            const int ncol = (P.nt + 63) / 64;
+            const int ncol = (nt_i + 63) / 64;
             // output offsets of pixels lane/4 + 8e of the two 16-lane halves h: ob[2h + e]
             long long ob[4];
 #pragma unroll
@@ -483,7 +518,7 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
                 fbc_tmem_ld_wait();
                 fbc_reg_fence(r[0]);
                 fbc_reg_fence(r[1]);
-                const int n0 = nti * P.nt + cc * 64 + 2 * (lane & 3);
+                const int n0 = nb0 + cc * 64 + 2 * (lane & 3);
 #pragma unroll
                 for (int h = 0; h < 2; ++h)
 #pragma unroll

@@ -52,8 +52,10 @@ struct SplitParams {
     uint8_t* xlo;
     uint8_t* whi;
     uint8_t* wlo;
+    uint8_t* whi2;   // half-width planes of the tail halves (halves != 0)
+    uint8_t* wlo2;
     long long npix, npix_pad;
-    int D, nc, N, fh, fw, nt, ntn, split;
+    int D, nc, N, fh, fw, nt, ntn, split, halves;
     long long xblocks;
 };
 
@@ -131,6 +133,13 @@ __global__ void __launch_bounds__(256) fbc_tc_split(const __grid_constant__ Spli
             }
             const long long idx = (u * S.nc + c) * S.nt + nl;
             split8(v, reinterpret_cast<uint4*>(S.whi) + idx, reinterpret_cast<uint4*>(S.wlo) + idx, S.split);
+            if (S.halves) {
+                // the same chunk in the half-width planes [2][taps][nc][nt/2] (one filter tile)
+                const int hn = S.nt >> 1;
+                const int h = nl / hn;
+                const long long idx2 = (((long long)h * taps + tap) * S.nc + c) * hn + (nl - h * hn);
+                split8(v, reinterpret_cast<uint4*>(S.whi2) + idx2, reinterpret_cast<uint4*>(S.wlo2) + idx2, S.split);
+            }
         }
     }
 }
@@ -157,7 +166,8 @@ struct TcPlan {
     TcConfig cfg;
     size_t smem = 0;
     size_t ws_bytes = 0;  // the largest any candidate configuration needs
-    size_t off_xhi = 0, off_xlo = 0, off_whi = 0, off_wlo = 0;
+    size_t off_xhi = 0, off_xlo = 0, off_whi = 0, off_wlo = 0, off_whi2 = 0, off_wlo2 = 0;
+    size_t ws_end = 0;    // workspace bytes this configuration uses
     int grid = 0;
     int split_blocks = 0;
     int H = 0, W = 0, D = 0, N = 0, fh = 0, fw = 0, nc = 0, split = 0, epi = 0;
@@ -286,6 +296,13 @@ bool tc_layout(TcPlan* p, const TcConfig& c, bool commit) {
     k.W = p->W; k.Ho = Ho; k.Wo = Wo; k.N = p->N; k.D = p->D;
     k.fh = p->fh; k.nt = nt; k.ntn = ntn; k.mtiles = mtiles;
     k.mtiles_s = c.mc ? (mtiles + 1) / 2 * 2 : mtiles;
+    // tail halves: when the last round of whole tiles would leave at least half
+    // of the CTAs idle, its tiles run as two 128-column halves each
+    const int grid_full = std::min(mtiles * ntn, std::max(1, p->sm_count));
+    const int rem = (mtiles * ntn) % grid_full;
+    const bool tail_halves = !c.mc && ntn == 1 && nt == 256 && rem > 0 && 2 * rem <= grid_full &&
+                             env_str("FBCORR_TAIL_HALVES", "1") != "0";
+    k.nfull = tail_halves ? mtiles * ntn - rem : k.mtiles_s * ntn;
     k.lp = lp; k.na = c.na; k.nb = c.nb;
     k.a_slot = a_slot; k.b_stage = b_stage;
     k.a_tx = (uint32_t)(nc * (kTileM + p->fw - 1) * 16 * halves);
@@ -312,6 +329,9 @@ bool tc_layout(TcPlan* p, const TcConfig& c, bool commit) {
     p->off_xlo = off; if (p->split) off = align_up(off + xplanes, 256);
     p->off_whi = off; off = align_up(off + wplanes, 256);
     p->off_wlo = off; if (p->split) off = align_up(off + wplanes, 256);
+    p->off_whi2 = off; if (tail_halves) off = align_up(off + wplanes, 256);
+    p->off_wlo2 = off; if (tail_halves && p->split) off = align_up(off + wplanes, 256);
+    p->ws_end = off;
 
     SplitParams& sp = p->sp;
     sp = SplitParams{};
@@ -319,6 +339,7 @@ bool tc_layout(TcPlan* p, const TcConfig& c, bool commit) {
     sp.npix_pad = k.npix_pad;
     sp.D = p->D; sp.nc = nc; sp.N = p->N; sp.fh = p->fh; sp.fw = p->fw; sp.nt = nt; sp.ntn = ntn;
     sp.split = p->split;
+    sp.halves = tail_halves ? 1 : 0;
     sp.xblocks = (k.npix_pad + 255) / 256;
     const long long wblocks = ((long long)ntn * p->fh * p->fw * nt + 255) / 256;
     if (c.fuse) sp.xblocks = 0;   // x is converted inside the correlation kernel
@@ -338,8 +359,7 @@ size_t tc_ws_need(TcPlan* p, const TcConfig& c) {
     tmp.nc = p->nc; tmp.split = p->split; tmp.sm_count = p->sm_count;
     tmp.epi = p->epi;
     if (!tc_layout(&tmp, c, true)) return 0;
-    const size_t wplanes = (size_t)tmp.kp.ntn * p->fh * p->fw * p->nc * tmp.kp.nt * 16;
-    return align_up(tmp.off_wlo + (p->split ? wplanes : 0), 256);
+    return tmp.ws_end;
 }
 
 std::vector<TcConfig> tc_candidate_configs(TcPlan* p) {
@@ -525,6 +545,7 @@ std::string tc_describe(const TcPlan* p) {
     std::ostringstream o;
     o << "{\"precision\":\"" << (p->split ? "bf16x3" : "bf16") << "\",\"mma\":\"128x" << p->kp.nt
       << "x16\",\"filter_tiles\":" << p->kp.ntn << ",\"tiles\":" << p->kp.mtiles * p->kp.ntn
+      << ",\"tail_half_tiles\":" << (p->kp.mtiles * p->kp.ntn - std::min(p->kp.nfull, p->kp.mtiles * p->kp.ntn))
       << ",\"smem\":" << p->smem << ",\"grid\":" << p->grid << ",\"threads\":" << tc_threads(p->cfg)
       << ",\"kernel\":\"" << tc_kernel_name(p->nc, p->split, p->fw, p->cfg, p->snippet) << "\"";
     auto it = p->kernels.find(tc_kernel_name(p->nc, p->split, p->fw, p->cfg, p->snippet));
@@ -546,6 +567,8 @@ fbcorr_status_t tc_forward(TcPlan* p, const float* x, const float* w, float* y, 
     sp.xlo = base + p->off_xlo;
     sp.whi = base + p->off_whi;
     sp.wlo = base + p->off_wlo;
+    sp.whi2 = base + p->off_whi2;
+    sp.wlo2 = base + p->off_wlo2;
     // timing events bracket both launches of the step: an event between them
     // would hold the correlation kernel back until the split has finished
     if (ev_start) FBC_CUDA(cudaEventRecord(ev_start, s));
@@ -556,6 +579,8 @@ fbcorr_status_t tc_forward(TcPlan* p, const float* x, const float* w, float* y, 
     kp.xlo = sp.xlo;
     kp.whi = sp.whi;
     kp.wlo = sp.wlo;
+    kp.whi2 = sp.whi2;
+    kp.wlo2 = sp.wlo2;
     kp.y = y;
     kp.err = err_word;
     kp.xraw = x;

@@ -25,6 +25,8 @@ struct FbcTcParams {
     const unsigned char* xlo;
     const unsigned char* whi;   // [ntn][fh*fw][nc][nt][16 B]
     const unsigned char* wlo;
+    const unsigned char* whi2;  // tail halves (nt = 256, ntn = 1): [2][fh*fw][nc][128][16 B]
+    const unsigned char* wlo2;
     float* y;                   // [Ho][Wo][N]
     int* err;                   // host-mapped error word
     const float* xraw;          // x itself [H*W][D] (fused: read by the converter warps)
@@ -34,6 +36,7 @@ struct FbcTcParams {
     int W, Ho, Wo, N, D;
     int fh, nt, ntn, mtiles;
     int mtiles_s;               // pixel tiles per filter tile in the schedule (MC: mtiles rounded up to even)
+    int nfull;                  // tiles run whole; tiles nfull.. run as two halves of the filter tile
     int lp;                     // pixels per chunk plane of an A slot
     int na, nb;                 // A slots, B stages
     int alook;                  // rows by which the A side (slabs or raw rows) runs ahead of the B stages

@@ -206,6 +206,33 @@ def test_every_tensor_core_configuration_matches(mode):
 
 
 @pytest.mark.parametrize("mode", ["bf16", "bf16x3"])
+def test_tail_halves_bit_exact(mode, monkeypatch):
+    """With SM count + 8 tiles of one 256-wide filter tile, the last partial
+    round (8 tiles) runs as 16 half items of 128 filters each, with their B
+    operand from the half-width planes; every store path gives the oracle's bits
+    on integer inputs, and the same bits with the halves switched off."""
+    torch = torch_cuda()
+    from paper_0911_3456_gb300.api import Plan
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    W, fh, fw = 128, 3, 3
+    H = sms + 8 + fh - 1                      # H' * W / 128 = sms + 8 tiles
+    wl = inputs.random_case(1760, H, W, 16, 256, fh, fw, kind="int")
+    ref = oracle.fwd(wl.x, wl.w)
+    x, w = dev(wl.x, torch), dev(wl.w, torch)
+    base = "tcgen05:na=2,nb=3,nt=256,bt=3,ew=8,fz=1,nr=0,cw=8"
+    for suffix in ("", ",ts=1,sb=1", ",ts=32,sb=1"):
+        p = Plan(wl.x.shape, wl.w.shape, mode)
+        p.set_variant(base + suffix)
+        assert p.info()["fwd"]["detail"]["tail_half_tiles"] == 8
+        assert np.array_equal(host(p.forward(x, w)), ref), suffix
+    monkeypatch.setenv("FBCORR_TAIL_HALVES", "0")
+    p = Plan(wl.x.shape, wl.w.shape, mode)
+    p.set_variant(base)
+    assert p.info()["fwd"]["detail"]["tail_half_tiles"] == 0
+    assert np.array_equal(host(p.forward(x, w)), ref)
+
+
+@pytest.mark.parametrize("mode", ["bf16", "bf16x3"])
 @pytest.mark.parametrize("shape", [(37, 96, 16, 96, 3, 3), (37, 128, 32, 320, 5, 5), (21, 140, 32, 40, 3, 5)],
                          ids=lambda s: "x".join(map(str, s)))
 def test_store_modes_and_pairs_bit_exact(mode, shape):
