@@ -637,6 +637,45 @@ def nn_only(args):
     return 0
 
 
+def fwdbwd_only(args):
+    """The differentiation workload alone (256x256x16 input, 64 filters 7x7x16,
+    FP32): forward, dL/dx, dL/dw and the three together, each timed over K steps
+    with an L2 flush between steps (its 20 MB working set fits in L2); one JSON line."""
+    import torch
+    from paper_0911_3456_gb300 import inputs
+    from paper_0911_3456_gb300.api import Plan
+    world, rank, local = dist_setup()
+    peaks = load_peaks(torch.cuda.get_device_properties(0).multi_processor_count)
+    flush = make_flush(torch)
+    wl = inputs.workload_differentiation()
+    x = torch.from_numpy(wl.x).cuda()
+    w = torch.from_numpy(wl.w).cuda()
+    g = torch.from_numpy(wl.g).cuda()
+    p = Plan(wl.x.shape, wl.w.shape, "f32")
+    if not args.no_tune:
+        p.autotune()
+    y = torch.empty(p.out_shape, device="cuda")
+    steps = min(args.steps, 50)
+
+    def fb():
+        p.forward(x, w, y)
+        p.backward(x, w, g)
+    ms = {"fwd": time_loop(torch, lambda: p.forward(x, w, y), steps, args.warmup, world, flush),
+          "dx": time_loop(torch, lambda: p.backward(x, w, g, need_dw=False), steps, args.warmup, world, flush),
+          "dw": time_loop(torch, lambda: p.backward(x, w, g, need_dx=False), steps, args.warmup, world, flush),
+          "fwd_bwd": time_loop(torch, fb, steps, args.warmup, world, flush)}
+    if rank == 0:
+        fp = peaks["fp32_tflops"]
+        print(json.dumps({"metric": "FP32 forward + backward GFLOP/s", "value": 3 * wl.flops / ms["fwd_bwd"] / 1e6,
+                          "unit": "GFLOP/s", "higher_is_better": True, "steps": steps, "warmup": args.warmup,
+                          "ms": ms, "gflops": {k: (3 if k == "fwd_bwd" else 1) * wl.flops / v / 1e6
+                                                for k, v in ms.items()},
+                          "frac_of_fp32_peak": 3 * wl.flops / ms["fwd_bwd"] / 1e9 / fp,
+                          "config": {"workload": wl.name, "l2": "flushed between steps"},
+                          "plan": p.info()}), flush=True)
+    return 0
+
+
 def traffic_sweep(args):
     """One forward per tensor-core candidate of the headline workload (modes
     bf16x3 and bf16), printing each candidate's generated kernel and source hash
@@ -680,11 +719,17 @@ def main():
                     default="precision")
     ap.add_argument("--nn", type=int, default=0,
                     help="time only the nearest-neighbour search against this many neighbours")
+    ap.add_argument("--fwdbwd", action="store_true",
+                    help="the differentiation workload alone (forward, dL/dx, dL/dw)")
     ap.add_argument("--traffic-sweep", action="store_true",
                     help="one forward per tensor-core candidate, for an ncu DRAM-traffic capture")
     args = ap.parse_args()
     if args.traffic_sweep:
         return traffic_sweep(args)
+    if args.fwdbwd:
+        if args.warmup < 3:
+            args.warmup = 3
+        return fwdbwd_only(args)
     if args.nn:
         if args.warmup < 3:
             args.warmup = 3

@@ -140,6 +140,31 @@ fbcorr_status_t choose_fwd_f32(fbcorr_plan* p) {
     return s;
 }
 
+// Row chunks of the generated dL/dw kernel once its residency is known: the
+// launch runs fh x filter-block x chunk CTAs, `resident` per SM at a time, each
+// over rows_per_chunk output rows, so its length goes as (rounds of resident
+// CTAs) x rows_per_chunk.  Take the fewest rows per chunk that minimise that
+// product, never more chunks than the workspace planned at creation holds
+// (e.g. 250 rows, 7 filter rows, 3 CTAs per SM on 152 SMs: 63 chunks of 4 rows
+// in one round instead of 84 chunks of 3 rows in two).
+void replan_dw_chunks(fbcorr_plan* p, int resident) {
+    const long slots = (long)std::max(1, p->dev.sm_count) * resident;
+    const long per_chunk = (long)p->fh * p->dw_nblocks;
+    int best_rows = p->dw_rows_per_chunk;
+    long best = -1;
+    for (int rows = p->dw_rows_per_chunk; rows <= p->Ho; ++rows) {
+        const long chunks = (p->Ho + rows - 1) / rows;
+        const long rounds = (chunks * per_chunk + slots - 1) / slots;
+        const long cost = rounds * rows;
+        if (best < 0 || cost < best) {
+            best = cost;
+            best_rows = rows;
+        }
+    }
+    p->dw_rows_per_chunk = best_rows;
+    p->dw_chunks = (int)((p->Ho + best_rows - 1) / best_rows);
+}
+
 fbcorr_status_t prepare_backward(fbcorr_plan* p) {
     if (p->bwd_ready) return FBCORR_OK;
     const DirectProblem pr = dx_problem(p);
@@ -176,12 +201,16 @@ fbcorr_status_t prepare_backward(fbcorr_plan* p) {
                                          p->dw_qb, mask, name),
                         name, dw_smem_bytes((int)p->fw, (int)p->D, p->dw_tn, p->dw_ng, p->dw_qb),
                         (int)p->D * p->dw_ng, &p->dw_kernel);
-        if (s == FBCORR_OK)
+        if (s == FBCORR_OK) {
             p->dw_kind = VarKind::Direct;
-        else if (s == FBCORR_ERR_NVRTC)
+            int resident = 0;
+            if (kernel_occupancy(p->dw_kernel, &resident) == FBCORR_OK && resident > 0)
+                replan_dw_chunks(p, resident);
+        } else if (s == FBCORR_ERR_NVRTC) {
             p->dw_kind = VarKind::Default;
-        else
+        } else {
             return s;
+        }
     }
     p->bwd_ready = true;
     return FBCORR_OK;

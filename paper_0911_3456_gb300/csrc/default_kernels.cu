@@ -12,7 +12,8 @@
 //  * fbc_default_dw: generic per-chunk partial sums of dL/dw (one thread per
 //    filter element and chunk of output rows).
 //  * fbc_dw_reduce: the deterministic second stage of dL/dw: for every filter
-//    element, a fixed-order pairwise sum over the chunk partials.
+//    element, a fixed-order pairwise sum over the chunk partials (trees over
+//    groups of 8 in registers, then over the group sums in shared memory).
 #include "internal.h"
 
 namespace fbc {
@@ -120,18 +121,39 @@ __global__ void __launch_bounds__(256) fbc_default_dw(const float* __restrict__ 
     part[(long long)chunk * E + e] = tot;
 }
 
-constexpr int kMaxChunks = 256;
+constexpr int kRedElems = 128;    // filter elements per block
+constexpr int kRedSlices = 4;     // threads per element, each summing every kRedSlices-th group
+constexpr int kMaxChunks = 256;   // the plan keeps the chunk count at or below this
 
-__global__ void __launch_bounds__(256) fbc_dw_reduce(const float* __restrict__ part,
-                                                     float* __restrict__ dw, int S, long long E) {
-    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= E) return;
-    float v[kMaxChunks];
-    for (int s = 0; s < S; ++s) v[s] = __ldg(part + (long long)s * E + e);
-    // fixed-order pairwise tree: (0+1), (2+3), ... then pairs of pairs, ...
-    for (int step = 1; step < S; step *= 2)
-        for (int s = 0; s + step < S; s += 2 * step) v[s] += v[s + step];
-    dw[e] = v[0];
+// Fixed-order pairwise sum over the S chunk partials of every filter element e:
+// groups of 8 consecutive partials are summed as a balanced tree in registers
+// (8 independent loads in flight per thread; kRedSlices threads per element take
+// the groups in turn), the group sums (the last group padded with zeros) are kept
+// in shared memory, one column per element, and added by a balanced tree over
+// the groups.  No dynamically indexed register arrays.
+__global__ void __launch_bounds__(kRedElems * kRedSlices) fbc_dw_reduce(const float* __restrict__ part,
+                                                                        float* __restrict__ dw, int S,
+                                                                        long long E) {
+    extern __shared__ float gsum[];   // [ceil(S / 8)][kRedElems]
+    const int el = threadIdx.x % kRedElems;
+    const int slice = threadIdx.x / kRedElems;
+    const long long e = (long long)blockIdx.x * kRedElems + el;
+    const bool valid = e < E;
+    const int G = (S + 7) / 8;
+    for (int gi = slice; gi < G; gi += kRedSlices) {
+        float v[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int sidx = gi * 8 + k;
+            v[k] = (valid && sidx < S) ? __ldg(part + (long long)sidx * E + e) : 0.f;
+        }
+        gsum[gi * kRedElems + el] = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
+    }
+    __syncthreads();
+    if (slice != 0) return;
+    for (int step = 1; step < G; step *= 2)
+        for (int g = 0; g + step < G; g += 2 * step) gsum[g * kRedElems + el] += gsum[(g + step) * kRedElems + el];
+    if (valid) dw[e] = gsum[el];
 }
 
 }  // namespace
@@ -155,7 +177,8 @@ cudaError_t launch_default_dw(const float* x, const float* g, const float* m, fl
 
 cudaError_t launch_dw_reduce(const float* part, float* dw, int S, long long E, cudaStream_t s) {
     if (S < 1 || S > kMaxChunks) return cudaErrorInvalidValue;
-    fbc_dw_reduce<<<(unsigned)((E + 255) / 256), 256, 0, s>>>(part, dw, S, E);
+    const size_t smem = (size_t)((S + 7) / 8) * kRedElems * sizeof(float);
+    fbc_dw_reduce<<<(unsigned)((E + kRedElems - 1) / kRedElems), kRedElems * kRedSlices, smem, s>>>(part, dw, S, E);
     return cudaGetLastError();
 }
 

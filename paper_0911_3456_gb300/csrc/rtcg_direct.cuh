@@ -296,26 +296,61 @@ struct FbcDw {
             const long long xrow = (long long)(p + i) * a.W;
             for (int q0 = 0; q0 < a.Wo; q0 += QB) {
                 const int nq = min(QB, a.Wo - q0);
-                for (int e = tid; e < GS; e += NT) {
-                    const int qq = e / NBLK;
-                    const int nl = e - qq * NBLK;
-                    const int n = n0 + nl;
-                    float v = 0.f;
-                    if (qq < nq && n < a.N) {
-                        const long long off = (grow + q0 + qq) * a.N + n;
-                        v = __ldg(a.g + off);
-                        if (MASK) {
-                            const float mv = __ldg(a.m + off);
-                            v = (mv > a.lo && mv < a.hi) ? v : 0.f;
+                // g: 4 consecutive filters per 16-byte load (N % 4 == 0 keeps every
+                // row of g 16-byte aligned; NBLK is a multiple of 4)
+                if ((a.N & 3) == 0) {
+                    for (int e4 = tid; e4 < GS / 4; e4 += NT) {
+                        const int qq = e4 / (NBLK / 4);
+                        const int nl = (e4 - qq * (NBLK / 4)) * 4;
+                        const int n = n0 + nl;
+                        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (qq < nq && n < a.N) {
+                            const long long off = (grow + q0 + qq) * a.N + n;
+                            v = __ldg(reinterpret_cast<const float4*>(a.g + off));
+                            if (MASK) {
+                                const float4 mv = __ldg(reinterpret_cast<const float4*>(a.m + off));
+                                v.x = (mv.x > a.lo && mv.x < a.hi) ? v.x : 0.f;
+                                v.y = (mv.y > a.lo && mv.y < a.hi) ? v.y : 0.f;
+                                v.z = (mv.z > a.lo && mv.z < a.hi) ? v.z : 0.f;
+                                v.w = (mv.w > a.lo && mv.w < a.hi) ? v.w : 0.f;
+                            }
                         }
+                        reinterpret_cast<float4*>(gs)[e4] = v;
                     }
-                    gs[e] = v;
+                } else {
+                    for (int e = tid; e < GS; e += NT) {
+                        const int qq = e / NBLK;
+                        const int nl = e - qq * NBLK;
+                        const int n = n0 + nl;
+                        float v = 0.f;
+                        if (qq < nq && n < a.N) {
+                            const long long off = (grow + q0 + qq) * a.N + n;
+                            v = __ldg(a.g + off);
+                            if (MASK) {
+                                const float mv = __ldg(a.m + off);
+                                v = (mv > a.lo && mv < a.hi) ? v : 0.f;
+                            }
+                        }
+                        gs[e] = v;
+                    }
                 }
-                for (int e = tid; e < XS; e += NT) {
-                    const int k = e / C;
-                    const int cc = e - k * C;
-                    const int col = q0 + k;
-                    xs[e] = (k < nq + FW - 1 && col < a.W) ? __ldg(a.x + (xrow + col) * C + cc) : 0.f;
+                // x: the contiguous run of (QB + FW - 1) pixels x C channels of input row p + i
+                if constexpr ((C & 3) == 0) {
+                    for (int e4 = tid; e4 < XS / 4; e4 += NT) {
+                        const int k = (e4 * 4) / C;
+                        const int col = q0 + k;
+                        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (k < nq + FW - 1 && col < a.W)
+                            v = __ldg(reinterpret_cast<const float4*>(a.x + (xrow + q0) * C) + e4);
+                        reinterpret_cast<float4*>(xs)[e4] = v;
+                    }
+                } else {
+                    for (int e = tid; e < XS; e += NT) {
+                        const int k = e / C;
+                        const int cc = e - k * C;
+                        const int col = q0 + k;
+                        xs[e] = (k < nq + FW - 1 && col < a.W) ? __ldg(a.x + (xrow + col) * C + cc) : 0.f;
+                    }
                 }
                 __syncthreads();
                 if (ng * TN < NBLK) {
@@ -331,8 +366,17 @@ struct FbcDw {
                             if (qq < QB) {
                                 win[(s + FW - 1) % FW] = xs[(qq + FW - 1) * C + c];
                                 float gv[TN];
+                                if constexpr ((TN & 3) == 0) {
+                                    // 16-byte broadcast loads (gp is 16-byte aligned: TN, NBLK % 4 == 0)
 #pragma unroll
-                                for (int t = 0; t < TN; ++t) gv[t] = gp[qq * NBLK + t];
+                                    for (int t4 = 0; t4 < TN; t4 += 4) {
+                                        const float4 g4 = *reinterpret_cast<const float4*>(gp + qq * NBLK + t4);
+                                        gv[t4] = g4.x; gv[t4 + 1] = g4.y; gv[t4 + 2] = g4.z; gv[t4 + 3] = g4.w;
+                                    }
+                                } else {
+#pragma unroll
+                                    for (int t = 0; t < TN; ++t) gv[t] = gp[qq * NBLK + t];
+                                }
 #pragma unroll
                                 for (int t = 0; t < TN; ++t)
 #pragma unroll
