@@ -212,6 +212,20 @@ fbcorr_status_t prepare_backward(fbcorr_plan* p) {
             return s;
         }
     }
+    if (!p->bwd_side) {
+        // side stream for dL/dw when both gradients are wanted; without it the two
+        // run one after the other on the caller's stream
+        if (cudaStreamCreateWithFlags(&p->bwd_side, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&p->bwd_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&p->bwd_join, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            if (p->bwd_side) cudaStreamDestroy(p->bwd_side);
+            if (p->bwd_fork) cudaEventDestroy(p->bwd_fork);
+            if (p->bwd_join) cudaEventDestroy(p->bwd_join);
+            p->bwd_side = nullptr;
+            p->bwd_fork = p->bwd_join = nullptr;
+        }
+    }
     p->bwd_ready = true;
     return FBCORR_OK;
 }
@@ -456,6 +470,9 @@ fbcorr_status_t fbcorr_plan_destroy(fbcorr_plan_t p) {
     for (auto e : p->prof_start) cudaEventDestroy(e);
     for (auto e : p->prof_stop) cudaEventDestroy(e);
     hostpipe_destroy(p->hostpipe);
+    if (p->bwd_side) cudaStreamDestroy(p->bwd_side);
+    if (p->bwd_fork) cudaEventDestroy(p->bwd_fork);
+    if (p->bwd_join) cudaEventDestroy(p->bwd_join);
     if (p->tc) tc_plan_destroy(p->tc);
     if (p->err_host) cudaFreeHost(p->err_host);
     delete p;
@@ -535,12 +552,14 @@ fbcorr_status_t fbcorr_backward(fbcorr_plan_t p, const float* x, const float* w,
     FBC_TRY(prepare_backward(p));
     cudaStream_t s = (cudaStream_t)stream;
     const float* m = clamp ? y : nullptr;
-    if (dx) {
-        const DirectProblem pr = dx_problem(p);
-        if (p->dx_kind == VarKind::Direct)
-            FBC_TRY(run_direct(p->dx_kernel, pr, p->dx_tile, g, m, w, dx, p->epi.lo, p->epi.hi, s));
-        else
-            FBC_TRY(run_default(pr, g, m, w, dx, p->epi.lo, p->epi.hi, s));
+    // both gradients: dL/dw on the side stream, forked after the work already on
+    // `s` and joined back before anything queued on `s` after this call, so the two
+    // gradients' kernels fill each other's idle SMs
+    const bool fork = dx && dw && p->bwd_side;
+    cudaStream_t sw = fork ? p->bwd_side : s;
+    if (fork) {
+        FBC_CUDA(cudaEventRecord(p->bwd_fork, s));
+        FBC_CUDA(cudaStreamWaitEvent(sw, p->bwd_fork, 0));
     }
     if (dw) {
         float* part = (float*)ws;
@@ -549,16 +568,26 @@ fbcorr_status_t fbcorr_backward(fbcorr_plan_t p, const float* x, const float* w,
                       p->dw_rows_per_chunk, p->epi.lo, p->epi.hi};
             void* args[] = {&a};
             dim3 grid((unsigned)p->dw_chunks, (unsigned)p->fh, (unsigned)p->dw_nblocks);
-            FBC_TRY(launch(p->dw_kernel, grid, args, s));
+            FBC_TRY(launch(p->dw_kernel, grid, args, sw));
         } else {
             FBC_CUDA(launch_default_dw(x, g, m ? m : g, part, (int)p->H, (int)p->W, (int)p->D,
                                        (int)p->Ho, (int)p->Wo, (int)p->N, (int)p->fh, (int)p->fw,
                                        p->dw_chunks, p->dw_rows_per_chunk, clamp ? 1 : 0, p->epi.lo,
-                                       p->epi.hi, s));
+                                       p->epi.hi, sw));
         }
-        FBC_CUDA(launch_dw_reduce(part, dw, p->dw_chunks, (long long)p->N * p->fh * p->fw * p->D, s));
+        FBC_CUDA(launch_dw_reduce(part, dw, p->dw_chunks, (long long)p->N * p->fh * p->fw * p->D, sw));
     }
-    return FBCORR_OK;
+    if (fork) FBC_CUDA(cudaEventRecord(p->bwd_join, sw));
+    fbcorr_status_t st = FBCORR_OK;
+    if (dx) {
+        const DirectProblem pr = dx_problem(p);
+        st = p->dx_kind == VarKind::Direct
+                 ? run_direct(p->dx_kernel, pr, p->dx_tile, g, m, w, dx, p->epi.lo, p->epi.hi, s)
+                 : run_default(pr, g, m, w, dx, p->epi.lo, p->epi.hi, s);
+    }
+    // the join even when dL/dx failed to launch: nothing on `s` may overtake dL/dw
+    if (fork) FBC_CUDA(cudaStreamWaitEvent(s, p->bwd_join, 0));
+    return st;
 }
 
 fbcorr_status_t fbcorr_plan_set_variant(fbcorr_plan_t p, const char* spec) {

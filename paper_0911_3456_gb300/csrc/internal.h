@@ -239,6 +239,11 @@ struct fbcorr_plan {
 
     size_t ws_fwd = 0, ws_bwd = 0;
 
+    // backward with both gradients: dL/dw on a side stream forked from and joined
+    // back to the caller's stream (created with the backward kernels)
+    cudaStream_t bwd_side = nullptr;
+    cudaEvent_t bwd_fork = nullptr, bwd_join = nullptr;
+
     // bounded-wait failure flag in host-mapped memory
     int* err_host = nullptr;
     int* err_dev = nullptr;

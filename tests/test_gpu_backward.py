@@ -77,6 +77,36 @@ def test_backward_only_dx_or_only_dw():
     assert dx is None and normwise_rel(host(dw), oracle.bwd_filt(wl.x, wl.g, wl.w.shape)) <= TOL
 
 
+def test_concurrent_gradients_match_single_and_capture_in_a_graph():
+    """With both gradients the library runs dL/dw on the plan's side stream,
+    forked from and joined back to the caller's stream: each gradient is
+    bit-identical to the one computed alone, the call (with its fork and join)
+    is captured into a CUDA graph, and replaying the graph gives the same bits."""
+    torch = torch_cuda()
+    shape = (70, 66, 8, 24, 5, 3)
+    wl = inputs.random_case(1150, *shape, with_g=True)
+    p = _plan(shape)
+    x, w, g = dev(wl.x, torch), dev(wl.w, torch), dev(wl.g, torch)
+    dx_only, _ = p.backward(x, w, g, need_dw=False)
+    _, dw_only = p.backward(x, w, g, need_dx=False)
+    dx, dw = p.backward(x, w, g)
+    torch.cuda.synchronize()
+    assert torch.equal(dx, dx_only) and torch.equal(dw, dw_only)
+    assert normwise_rel(host(dw), oracle.bwd_filt(wl.x, wl.g, wl.w.shape)) <= TOL
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        p.backward(x, w, g)          # warm-up on the capture stream
+    torch.cuda.current_stream().wait_stream(s)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        gx, gw = p.backward(x, w, g)
+    graph.replay()
+    graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(gx, dx) and torch.equal(gw, dw)
+
+
 def test_dw_deterministic():
     torch = torch_cuda()
     shape = (64, 64, 8, 16, 5, 5)
