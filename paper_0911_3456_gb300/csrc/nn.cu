@@ -184,15 +184,25 @@ fbcorr_status_t fbcorr_nn_plan_create(fbcorr_nn_plan_t* out, int64_t n_targets, 
     k.b_bytes = (unsigned)(p->nc * FBC_NN_TILE_N * 16);
     const size_t halves = p->split ? 2 : 1;
     // as many B stages as fit next to two A slots (at least two)
-    k.nb = (int)std::min<size_t>(6, (kSmemMax - 1024 - 2 * halves * k.a_bytes) / (halves * k.b_bytes));
+    // (barriers: 512 bytes; two 1 KB slots of |n|^2).  The target tile changes once
+    // per work item, so one A slot costs a short wait per item; it is used when it
+    // makes room for one more neighbour stage (the refill latency of a stage is
+    // what the screening MMAs wait on)
+    const size_t room = kSmemMax - 512 - 2048;
+    auto stages = [&](int na) {
+        return std::min<size_t>(6, (room - (size_t)na * halves * k.a_bytes) / (halves * k.b_bytes));
+    };
+    k.na = stages(1) > stages(2) ? 1 : 2;
+    k.nb = (int)stages(k.na);
     if (k.nb < 2) {
         delete p;
         return set_error(FBCORR_ERR_UNSUPPORTED, "tiles do not fit in shared memory");
     }
     k.a_off = 0;
-    k.b_off = (unsigned)(2 * halves * k.a_bytes);
+    k.b_off = (unsigned)(k.na * halves * k.a_bytes);
     k.bar_off = (unsigned)(k.b_off + k.nb * halves * k.b_bytes);
-    p->smem = k.bar_off + 512;
+    k.nrm_off = k.bar_off + 512;
+    p->smem = k.nrm_off + 2 * FBC_NN_TILE_N * 4;
     // work items: one target tile against a chunk of neighbour tiles, about four
     // waves of items over the SMs, at most 64 tiles per chunk
     const long long want = 4LL * std::max(1, dev.sm_count);

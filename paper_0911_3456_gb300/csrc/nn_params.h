@@ -19,8 +19,10 @@ struct FbcNnParams {
     int t_tiles, n_tiles;         // 128-target and 256-neighbour tiles
     int chunk_tiles, chunks;      // neighbour tiles per work item; items = chunks * t_tiles
     int nb;                       // B stages (neighbour tiles in flight)
+    int na;                       // A slots (target tiles): 1 or 2
     unsigned int a_bytes, b_bytes;          // bytes of one half (hi or lo) of an A tile / B tile
     unsigned int a_off, b_off, bar_off;     // shared-memory layout
+    unsigned int nrm_off;                   // two 1 KB slots of |n|^2 of a neighbour tile
 };
 
 #endif

@@ -18,9 +18,12 @@
 //
 // Roles (persistent CTA, one per SM, 64 + 32*EW threads): warp 0 bulk-copies the
 // item's target tile (one copy per half) and streams its neighbour tiles through
-// a ring of `nb` stages; warp 1 issues the MMAs into two alternating
-// accumulators; EW epilogue warps read the accumulators (tcgen05.ld 16x256b),
-// form the keys and keep the running best two per target row.
+// a ring of `nb` stages, and each tile's 256 |n|^2 into one of two 1 KB slots
+// that follow the accumulators; warp 1 issues the MMAs into two alternating
+// accumulators; EW epilogue warps read the accumulators (tcgen05.ld 32x32b: one
+// target row per thread, 32 neighbours per load, the next load in flight while
+// one is processed), form d' and keep the running best two per target row in
+// registers, rejecting a 32-column chunk with one comparison of its minimum.
 
 __device__ __forceinline__ fbc_u64 fbc_nn_key(float d, unsigned j) {
     // order-preserving map of the float onto unsigned bits, index in the low word:
@@ -68,6 +71,8 @@ __device__ __forceinline__ void fbc_nn_body(const FbcNnParams& P) {
     const fbc_u32 acc_full0 = b_empty0 + 8u * P.nb;
     const fbc_u32 acc_empty0 = acc_full0 + 16u;
     const fbc_u32 drain_bar = acc_empty0 + 16u;
+    const fbc_u32 nrm_full0 = drain_bar + 8u;     // |n|^2 slots, paired with the accumulators
+    const fbc_u32 nrm_empty0 = nrm_full0 + 16u;
     if (threadIdx.x == 0) {
         for (int s = 0; s < 2; ++s) {
             fbc_mbar_init(a_full0 + 8u * s, 1);
@@ -80,6 +85,10 @@ __device__ __forceinline__ void fbc_nn_body(const FbcNnParams& P) {
             fbc_mbar_init(b_empty0 + 8u * s, 1);
         }
         fbc_mbar_init(drain_bar, 1);
+        for (int s = 0; s < 2; ++s) {
+            fbc_mbar_init(nrm_full0 + 8u * s, 1);
+            fbc_mbar_init(nrm_empty0 + 8u * s, EW);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_abort = 0;
     }
@@ -104,6 +113,7 @@ __device__ __forceinline__ void fbc_nn_body(const FbcNnParams& P) {
             int as = 0, bs = 0;
             fbc_u32 aph = 0, bph = 0;
             bool ok = true;
+            fbc_u32 n_it = 0;   // neighbour tiles so far: |n|^2 slot n_it & 1
             for (int k = blockIdx.x; k < items && ok; k += gridDim.x) {
                 const int c = k / P.t_tiles, t = k - c * P.t_tiles;
                 if (!(ok = fbc_wait(a_empty0 + 8u * as, aph ^ 1, P, abort_flag, 4))) break;
@@ -113,7 +123,7 @@ __device__ __forceinline__ void fbc_nn_body(const FbcNnParams& P) {
                 fbc_bulk_g2s(adst, P.thi + (long long)t * P.a_bytes, P.a_bytes, afull);
                 if (SPLIT) fbc_bulk_g2s(adst + P.a_bytes, P.tlo + (long long)t * P.a_bytes, P.a_bytes, afull);
                 ++a_it;
-                if (++as == 2) { as = 0; aph ^= 1; }
+                if (++as == P.na) { as = 0; aph ^= 1; }
                 const int j1 = min(P.n_tiles, (c + 1) * P.chunk_tiles);
                 for (int jt = c * P.chunk_tiles; jt < j1 && ok; ++jt) {
                     if (!(ok = fbc_wait(b_empty0 + 8u * bs, bph ^ 1, P, abort_flag, 4))) break;
@@ -124,13 +134,23 @@ __device__ __forceinline__ void fbc_nn_body(const FbcNnParams& P) {
                     if (SPLIT) fbc_bulk_g2s(bdst + P.b_bytes, P.nlo + (long long)jt * P.b_bytes, P.b_bytes, bfull);
                     ++b_it;
                     if (++bs == P.nb) { bs = 0; bph ^= 1; }
+                    // the tile's |n|^2 for the epilogue (slot freed when it has read them)
+                    const fbc_u32 ns = n_it & 1u;
+                    if (!(ok = fbc_wait(nrm_empty0 + 8u * ns, ((n_it >> 1) & 1u) ^ 1u, P, abort_flag, 4))) break;
+                    const fbc_u32 nfull = nrm_full0 + 8u * ns;
+                    fbc_mbar_expect_tx(nfull, FBC_NN_TILE_N * 4u);
+                    fbc_bulk_g2s(sbase + P.nrm_off + ns * (FBC_NN_TILE_N * 4u), P.n2 + (long long)jt * FBC_NN_TILE_N,
+                                 FBC_NN_TILE_N * 4u, nfull);
+                    ++n_it;
                 }
             }
             if (!ok) {
-                const fbc_u32 a0 = a_it > 2u ? a_it - 2u : 0u;
-                for (fbc_u32 q = a0; q < a_it; ++q) fbc_wait_drain(a_full0 + 8u * (q % 2), (q / 2) & 1, P);
+                const fbc_u32 a0 = a_it > (fbc_u32)P.na ? a_it - P.na : 0u;
+                for (fbc_u32 q = a0; q < a_it; ++q) fbc_wait_drain(a_full0 + 8u * (q % P.na), (q / P.na) & 1, P);
                 const fbc_u32 b0 = b_it > (fbc_u32)P.nb ? b_it - P.nb : 0u;
                 for (fbc_u32 q = b0; q < b_it; ++q) fbc_wait_drain(b_full0 + 8u * (q % P.nb), (q / P.nb) & 1, P);
+                const fbc_u32 n0 = n_it > 2u ? n_it - 2u : 0u;
+                for (fbc_u32 q = n0; q < n_it; ++q) fbc_wait_drain(nrm_full0 + 8u * (q & 1u), (q >> 1) & 1u, P);
             }
         }
     } else if (warp == 1) {
@@ -177,7 +197,7 @@ __device__ __forceinline__ void fbc_nn_body(const FbcNnParams& P) {
                 }
                 if (!ok) break;
                 fbc_umma_commit(a_empty0 + 8u * as);
-                if (++as == 2) { as = 0; aph ^= 1; }
+                if (++as == P.na) { as = 0; aph ^= 1; }
             }
             if (!ok && issued) {
                 fbc_umma_commit(drain_bar);
@@ -186,8 +206,11 @@ __device__ __forceinline__ void fbc_nn_body(const FbcNnParams& P) {
         }
     } else {
         // ------------------------------------------------------------ epilogue
-        // 16x256b loads: lanes 4r..4r+3 hold 8 columns of TMEM lane r (and r + 8);
-        // this thread sees rows lq*32 + 16h + 8e + lane/4 (h, e in {0,1}).
+        // tcgen05.ld 32x32b: lane l holds 32 consecutive columns of TMEM lane
+        // lq*32 + l, i.e. one target row; warp part (ew / 4) takes the 32-column
+        // chunks part, part + EW/4, ... of every tile, in increasing column order.
+        static_assert((FBC_NN_TILE_N / 32) % (EW / 4) == 0, "chunks per epilogue warp");
+        constexpr int NCH = FBC_NN_TILE_N / 32 / (EW / 4);   // chunks per warp and tile
         const int ew = warp - 2;
         const int lq = warp & 3;
         const int part = ew >> 2;
@@ -196,85 +219,63 @@ __device__ __forceinline__ void fbc_nn_body(const FbcNnParams& P) {
         bool ok = true;
         for (int k = blockIdx.x; k < items && ok; k += gridDim.x) {
             const int c = k / P.t_tiles, t = k - c * P.t_tiles;
-            float bd1[4], bd2[4];
-            unsigned bi1[4], bi2[4];
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                bd1[r] = bd2[r] = __int_as_float(0x7f800000);
-                bi1[r] = bi2[r] = 0xffffffffu;
-            }
+            float bd1 = __int_as_float(0x7f800000), bd2 = bd1;
+            unsigned bi1 = 0xffffffffu, bi2 = 0xffffffffu;
             const int j1 = min(P.n_tiles, (c + 1) * P.chunk_tiles);
             for (int jt = c * P.chunk_tiles; jt < j1; ++jt) {
                 const int acc = acc_it & 1;
-                if (!(ok = fbc_wait(acc_full0 + 8u * acc, (acc_it >> 1) & 1, P, abort_flag, 3))) break;
+                const fbc_u32 par = (acc_it >> 1) & 1;
+                if (!(ok = fbc_wait(acc_full0 + 8u * acc, par, P, abort_flag, 3))) break;
+                if (!(ok = fbc_wait(nrm_full0 + 8u * acc, par, P, abort_flag, 3))) break;
                 fbc_tc_fence_after();
-#pragma unroll 1
-                for (int cc = part; cc < 4; cc += EW / 4) {
-                    // the norms of this chunk's 16 columns first: their latency overlaps
-                    // the tensor-memory loads
-                    const unsigned n0 = (unsigned)(jt * FBC_NN_TILE_N + cc * 64 + 2 * (lane & 3));
-                    float2 nrm[8];
+                const fbc_u32 trow = tmem + ((fbc_u32)(lq * 32) << 16) + (fbc_u32)(acc * 256);
+                const fbc_u32 nrm = sbase + P.nrm_off + (fbc_u32)acc * (FBC_NN_TILE_N * 4u);
+                fbc_u32 r[2][32];
+                fbc_tmem_ld32x32b_x32_async(trow + (fbc_u32)(part * 32), r[0]);
 #pragma unroll
-                    for (int g8 = 0; g8 < 8; ++g8) nrm[g8] = __ldg(reinterpret_cast<const float2*>(P.n2 + n0 + 8u * g8));
-                    fbc_u32 r[2][32];
-                    const fbc_u32 taddr = tmem + ((fbc_u32)(lq * 32) << 16) + (fbc_u32)(acc * 256 + cc * 64);
-                    fbc_tmem_ld16x256b_x8_async(taddr, r[0]);
-                    fbc_tmem_ld16x256b_x8_async(taddr + (16u << 16), r[1]);
+                for (int i = 0; i < NCH; ++i) {
+                    const int cc = part + i * (EW / 4);
                     fbc_tmem_ld_wait();
-                    fbc_reg_fence(r[0]);
-                    fbc_reg_fence(r[1]);
+                    fbc_reg_fence(r[i & 1]);
+                    if (i + 1 < NCH)   // the next chunk's load runs while this one is processed
+                        fbc_tmem_ld32x32b_x32_async(trow + (fbc_u32)((cc + EW / 4) * 32), r[(i + 1) & 1]);
+                    float d[32];
 #pragma unroll
-                    for (int g8 = 0; g8 < 8; ++g8) {
-                        const unsigned n = n0 + 8u * g8;
-                        const float na = nrm[g8].x, nb2 = nrm[g8].y;
+                    for (int q = 0; q < 8; ++q) {
+                        const uint4 nv = fbc_ld_shared_v4(nrm + (fbc_u32)(cc * 32 + 4 * q) * 4u);
+                        d[4 * q + 0] = fmaf(-2.f, __uint_as_float(r[i & 1][4 * q + 0]), __uint_as_float(nv.x));
+                        d[4 * q + 1] = fmaf(-2.f, __uint_as_float(r[i & 1][4 * q + 1]), __uint_as_float(nv.y));
+                        d[4 * q + 2] = fmaf(-2.f, __uint_as_float(r[i & 1][4 * q + 2]), __uint_as_float(nv.z));
+                        d[4 * q + 3] = fmaf(-2.f, __uint_as_float(r[i & 1][4 * q + 3]), __uint_as_float(nv.w));
+                    }
+                    // minimum of the chunk as a balanced tree; almost every chunk fails
+                    // the comparison with the row's second best
+                    float m[16];
 #pragma unroll
-                        for (int h = 0; h < 2; ++h)
+                    for (int j = 0; j < 16; ++j) m[j] = fminf(d[2 * j], d[2 * j + 1]);
 #pragma unroll
-                            for (int e = 0; e < 2; ++e) {
-                                const float da = fmaf(-2.f, __uint_as_float(r[h][4 * g8 + 2 * e]), na);
-                                const float db = fmaf(-2.f, __uint_as_float(r[h][4 * g8 + 2 * e + 1]), nb2);
-                                const int q = 2 * h + e;
-                                if (fminf(da, db) < bd2[q]) {
-                                    fbc_nn_keep2(bd1[q], bi1[q], bd2[q], bi2[q], da, n);
-                                    fbc_nn_keep2(bd1[q], bi1[q], bd2[q], bi2[q], db, n + 1);
-                                }
-                            }
+                    for (int w2 = 8; w2 >= 1; w2 >>= 1)
+#pragma unroll
+                        for (int j = 0; j < w2; ++j) m[j] = fminf(m[j], m[j + w2]);
+                    if (m[0] < bd2) {
+                        const unsigned n0 = (unsigned)(jt * FBC_NN_TILE_N + cc * 32);
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) fbc_nn_keep2(bd1, bi1, bd2, bi2, d[j], n0 + (unsigned)j);
                     }
                 }
                 fbc_tc_fence_before();
                 __syncwarp();
-                if (lane == 0) fbc_mbar_arrive(acc_empty0 + 8u * acc);
+                if (lane == 0) {
+                    fbc_mbar_arrive(acc_empty0 + 8u * acc);
+                    fbc_mbar_arrive(nrm_empty0 + 8u * acc);
+                }
                 ++acc_it;
             }
             if (!ok) break;
-            // the four lanes of a row hold disjoint columns: merge their best two
-            // as keys (order-preserving distance bits, index)
-            fbc_u64 best[4][2];
-#pragma unroll
-            for (int r = 0; r < 4; ++r) {
-                best[r][0] = bi1[r] == 0xffffffffu ? ~0ull : fbc_nn_key(bd1[r], bi1[r]);
-                best[r][1] = bi2[r] == 0xffffffffu ? ~0ull : fbc_nn_key(bd2[r], bi2[r]);
-            }
-#pragma unroll
-            for (int m = 1; m <= 2; m <<= 1)
-#pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    const fbc_u64 p1 = fbc_shfl_xor_u64(best[r][0], m), p2 = fbc_shfl_xor_u64(best[r][1], m);
-                    const fbc_u64 lo1 = best[r][0] < p1 ? best[r][0] : p1;
-                    const fbc_u64 hi1 = best[r][0] < p1 ? p1 : best[r][0];
-                    const fbc_u64 lo2 = best[r][1] < p2 ? best[r][1] : p2;
-                    best[r][0] = lo1;
-                    best[r][1] = hi1 < lo2 ? hi1 : lo2;
-                }
-            if ((lane & 3) == 0) {
-#pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    const int row = t * FBC_NN_TILE_T + lq * 32 + (r >> 1) * 16 + (r & 1) * 8 + (lane >> 2);
-                    fbc_u64* dst = P.part + (((long long)c * (EW / 4) + part) * rows_total + row) * 2;
-                    dst[0] = best[r][0];
-                    dst[1] = best[r][1];
-                }
-            }
+            const int row = t * FBC_NN_TILE_T + lq * 32 + lane;
+            fbc_u64* dst = P.part + (((long long)c * (EW / 4) + part) * rows_total + row) * 2;
+            dst[0] = bi1 == 0xffffffffu ? ~0ull : fbc_nn_key(bd1, bi1);
+            dst[1] = bi2 == 0xffffffffu ? ~0ull : fbc_nn_key(bd2, bi2);
         }
     }
     __syncwarp();
