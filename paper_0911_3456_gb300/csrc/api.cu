@@ -616,7 +616,7 @@ static fbcorr_status_t autotune_tc(fbcorr_plan_t p, fbcorr_stream_t stream);
 
 static fbcorr_status_t tune_direct(fbcorr_plan_t p, const DirectProblem& pr, cudaStream_t s,
                                    const char* what, std::string* best_spec, float* best_ms_out) {
-    int topk = atoi(env_str("FBCORR_TUNE_TOPK", "12").c_str());
+    int topk = atoi(env_str("FBCORR_TUNE_TOPK", "48").c_str());
     return tune_direct_problem(p->dev, pr, s, 0, 64, smem_limit(p->dev), std::max(1, topk), p->snippet.empty(),
                                what, best_spec, best_ms_out);
 }
@@ -769,7 +769,7 @@ fbcorr_status_t fbcorr_plan_candidates(fbcorr_plan_t p, char* buf, size_t cap) {
     if (!p || !buf || cap == 0) return set_error(FBCORR_ERR_INVALID_ARG, "NULL argument");
     std::vector<std::string> specs;
     if (p->dtype == FBCORR_F32) {
-        const int topk = std::max(1, atoi(env_str("FBCORR_TUNE_TOPK", "12").c_str()));
+        const int topk = std::max(1, atoi(env_str("FBCORR_TUNE_TOPK", "48").c_str()));
         for (const auto& t : direct_ranked(fwd_problem(p), smem_limit(p->dev), p->dev.sm_count, 0, 64)) {
             if ((int)specs.size() >= topk) break;
             specs.push_back(direct_tile_spec(t));
