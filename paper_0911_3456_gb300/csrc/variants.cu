@@ -119,7 +119,7 @@ std::vector<DirectTile> direct_candidates(const DirectProblem& pr, size_t smem_l
     std::vector<DirectTile> out;
     const int trs[] = {2, 4, 8};
     const int tfs[] = {4, 8};
-    const int wrs[] = {1, 2, 4, 8};
+    const int wrs[] = {1, 2, 3, 4, 5, 6, 7, 8};   // any count: block heights that fit 152 SMs better
     const int wfs[] = {1, 2, 4, 8};
     const int nf4 = ((pr.nf + 3) / 4) * 4;
     // channel chunks: the whole depth, or 16 / 8 / 4 channels per stage
