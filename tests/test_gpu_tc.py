@@ -205,6 +205,34 @@ def test_every_tensor_core_configuration_matches(mode):
     assert ran >= 24
 
 
+@pytest.mark.parametrize("mode", ["f32", "bf16", "bf16x3"])
+def test_forward_captures_into_a_cuda_graph(mode):
+    """The forward is CUDA-graph capturable in every mode -- for the tensor-core
+    modes that includes the operand split and the correlation kernel launched as
+    its programmatic dependent -- and replaying the graph gives the eager bits."""
+    torch = torch_cuda()
+    from paper_0911_3456_gb300.api import Plan
+    wl = inputs.random_case(1770, 37, 96, 16, 40, 3, 3)
+    x, w = dev(wl.x, torch), dev(wl.w, torch)
+    p = Plan(wl.x.shape, wl.w.shape, mode)
+    y_eager = p.forward(x, w).clone()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        p.forward(x, w)                 # warm-up on the capture stream
+    torch.cuda.current_stream().wait_stream(s)
+    y = torch.empty(p.out_shape, device="cuda")
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        p.forward(x, w, y)
+    for _ in range(2):
+        y.zero_()
+        graph.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(y, y_eager)
+    assert p.device_status() == 0
+
+
 @pytest.mark.parametrize("mode", ["bf16", "bf16x3"])
 def test_tail_halves_bit_exact(mode, monkeypatch):
     """With SM count + 8 tiles of one 256-wide filter tile, the last partial
