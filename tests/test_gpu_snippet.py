@@ -94,3 +94,25 @@ def test_snippet_plan_autotunes_on_the_tensor_cores():
     z = oracle.fwd(wl.x, wl.w)
     ref = np.where(z > 0, z, 0.2 * z)
     assert np.abs(y - ref).max() <= 1e-5 * np.abs(z).max()
+
+
+@pytest.mark.parametrize("mode", ["bf16", "bf16x3"])
+def test_snippet_through_every_tensor_core_store_path(mode):
+    """The snippet is applied before the store in every epilogue path of the
+    tensor-core kernel -- direct stores, the staged transpose, tiled bulk stores
+    -- and in the tail halves (SM count + 8 tiles of a 256-wide filter tile):
+    all give the same bits on integer inputs, and the oracle's."""
+    torch = torch_cuda()
+    from paper_0911_3456_gb300.api import Plan
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    wl = inputs.random_case(3000, sms + 8 + 2, 128, 16, 256, 3, 3, kind="int")
+    x, w = dev(wl.x, torch), dev(wl.w, torch)
+    expr, params = "y > 0.f ? y : lo * y", (0.25, 0.0)     # exact on integers: y * 1/4
+    z = oracle.fwd(wl.x, wl.w)
+    ref = np.where(z > 0, z, 0.25 * z)
+    base = "tcgen05:na=2,nb=3,nt=256,bt=3,ew=8,fz=1,nr=0,cw=8"
+    for suffix in ("", ",ts=1,sb=1", ",ts=32,sb=1"):
+        p = _plan(mode, wl, expr, params)
+        p.set_variant(base + suffix)
+        assert p.info()["fwd"]["detail"]["tail_half_tiles"] == 8
+        assert np.array_equal(host(p.forward(x, w)), ref), suffix
