@@ -1,7 +1,9 @@
 // rtcg_tc.cuh -- the tensor-core correlation kernel, compiled at plan time by
 // NVRTC for sm_103a with the chunk-plane count NC, the split mode, the filter
-// width FW, the taps per B stage BT, the epilogue warp count EW and the fused
-// conversion switch FUSE baked in.  Embedded as a string into libfbcorr and
+// width FW, the taps per B stage BT, the epilogue warp count EW, the fused
+// conversion switch FUSE (and its converter warps CW), the snippet switch USER,
+// the epilogue store path TS (with SB staging slots) and the cluster-pair
+// switch MC baked in.  Embedded as a string into libfbcorr and
 // prefixed with tc_params.h and rtcg_ptx.cuh; self-contained (no system headers).
 //
 // The correlation of Sec. 6.2 as an implicit GEMM: for every filter tap (i, j)
@@ -22,18 +24,20 @@
 // Roles per CTA (persistent, one per SM):
 //   warp 0      producer: cp.async.bulk (1D TMA) of B slices of BT consecutive
 //               taps (and, unfused, of pre-split A slabs) into rings,
-//               mbarrier complete_tx;
+//               mbarrier complete_tx; it first waits (griddepcontrol.wait) for
+//               the operand split the kernel is launched as a dependent of;
 //   warp 1      allocates 512 TMEM columns, issues tcgen05.mma (M=128, N<=256,
 //               K=16, kind::f16 BF16, FP32 accumulate) into one of two
 //               accumulators; tcgen05.commit frees ring slots and hands
 //               finished accumulators to the epilogue;
-//   warps 2..   EW epilogue warps (two per TMEM lane quarter when EW = 8):
-//               tcgen05.ld 16x256b, optional clamp, streaming stores straight
-//               from registers (four lanes write 32 contiguous bytes of one
-//               output pixel), or (TS = 32) tcgen05.ld 32x32b into SB swizzled
-//               shared-memory slots per warp, each written out as one tiled
-//               bulk store of 32 pixels x 32 filters; overlaps the MMAs of the
-//               next tile;
+//   warps 2..   EW epilogue warps (two per TMEM lane quarter when EW = 8),
+//               overlapping the MMAs of the next tile; clamp or snippet, then
+//               TS = 0: tcgen05.ld 16x256b and streaming stores straight from
+//               registers (four lanes write 32 contiguous bytes of one pixel);
+//               TS = 1: tcgen05.ld 32x32b into a swizzled shared-memory slot,
+//               read back transposed, 16-byte stores of four full lines;
+//               TS = 32: the same swizzled 32-pixel x 32-filter blocks leave
+//               as tiled bulk stores through the tensor map of y;
 //   last CW     (FUSE) converter warps: FP32 x rows -> BF16 hi (and lo) chunk
 //               planes of an A slot; FUSE = 1 reads the rows from global memory
 //               into registers one row ahead, FUSE = 2 from a ring of raw rows
@@ -55,12 +59,14 @@
 // from half-width planes), so that round keeps twice as many SMs busy for half
 // as long.
 //
-// Pairs (MC = 1): a tile needs the whole filter bank from L2 (400 KB in BF16 for
-// 256 filters of 5x5x32), more than the bulk-copy path delivers per SM in one
-// tile's MMA time.  The kernel then runs as clusters of two CTAs that process
-// two pixel tiles against the same B sequence: each producer copies half of
-// every B stage and multicasts it into both CTAs, each CTA's MMA commit
-// releases the stage in both, so L2 serves every B byte once per pair.
+// Pairs (MC = 1): every tile reads the whole filter bank from L2 (400 KB in
+// BF16 for 256 filters of 5x5x32).  In this mode the kernel runs as clusters of
+// two CTAs that process two pixel tiles against the same B sequence: each
+// producer copies half of every B stage and multicasts it into both CTAs, each
+// CTA's MMA commit releases the stage in both, so L2 serves every B byte once
+// per pair.  (Each SM still fills its shared memory with the whole stage, and
+// that fill latency, not L2 bandwidth, is what the MMAs wait on: on the
+// workloads measured this mode is not faster, so only a spec selects it.)
 //
 // Every mbarrier wait is bounded in time (%globaltimer); on expiry the kernel
 // records an error code in host-mapped memory, stops every role, waits (again

@@ -19,7 +19,7 @@
 
 struct FbcTcParams {
     // CUtensorMap of y as {N, Wo, Ho} FP32, 128-byte swizzle, box {32, 32, 1}:
-    // the target of the tiled-store epilogue (TS > 0 and tma_y != 0)
+    // the target of the tiled-store epilogue (TS = 32 and tma_y != 0)
     alignas(64) unsigned long long ymap[16];
     const unsigned char* xhi;   // [nc][npix_pad][16 B] pre-split x planes (unfused)
     const unsigned char* xlo;
