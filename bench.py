@@ -344,7 +344,7 @@ def run_ours(args):
             elif not args.no_tune:
                 p.autotune()
             plans[m] = p
-        except Exception as e:   # a mode this build cannot run is reported, not hidden
+        except Exception as e:   # a mode the library cannot run is reported, not hidden
             if m == mode:
                 raise
             plans[m] = e

@@ -52,7 +52,7 @@ typedef enum {
     FBCORR_ERR_INVALID_ARG = 1,  /* null pointer, bad enum, bad count          */
     FBCORR_ERR_SHAPE = 2,        /* non-positive dim, fh > H, depth mismatch,  */
                                  /* index arithmetic that would overflow int32 */
-    FBCORR_ERR_UNSUPPORTED = 3,  /* valid request this build cannot run        */
+    FBCORR_ERR_UNSUPPORTED = 3,  /* valid request the library cannot run       */
     FBCORR_ERR_ALIGNMENT = 4,    /* a tensor pointer is not 16-byte aligned    */
     FBCORR_ERR_WORKSPACE = 5,    /* workspace missing or smaller than required */
     FBCORR_ERR_CUDA = 6,         /* a CUDA runtime call or a launch failed     */
