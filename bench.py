@@ -589,6 +589,15 @@ def secondary(torch, args, world, peaks):
     out["nn_search_4096_patches_8x8"] = nn_rows
 
     # the 64-image uneven batch: one persistent launch replayed from a CUDA graph
+    out["batch64_uneven"] = measure_batch(torch, world, flush, fp, 20, 3)
+    return out
+
+
+def measure_batch(torch, world, flush, fp, steps, warmup):
+    """The 64-image uneven batch (per-image tiles auto-tuned on this GPU): one
+    persistent launch per step, replayed from a CUDA graph, L2 flushed between
+    steps."""
+    from paper_0911_3456_gb300 import inputs
     from paper_0911_3456_gb300.api import BatchPlan
     bw = inputs.workload_batch()
     t0 = time.perf_counter()
@@ -605,14 +614,29 @@ def secondary(torch, args, world, peaks):
     xs = [torch.from_numpy(it.x).cuda() for it in bw.items]
     wss = [torch.from_numpy(it.w).cuda() for it in bw.items]
     ys = [torch.empty(it.out_shape, device="cuda") for it in bw.items]
-    ms_b = time_loop(torch, lambda: bp.forward(xs, wss, ys), 20, 3, world, flush)
+    ms_b = time_loop(torch, lambda: bp.forward(xs, wss, ys), steps, warmup, world, flush)
     binfo = bp.info()
-    out["batch64_uneven"] = {
+    return {
         "gflops": bw.flops / ms_b / 1e6, "ms": ms_b, "flops": bw.flops,
         "frac_of_fp32_peak": bw.flops / ms_b / 1e9 / fp, "launches_per_step": binfo["launches"],
         "work_items": binfo["work_items"], "grid": binfo["grid"], "variants": len(binfo["variants"]),
         "plan_seconds_incl_tuning": t_plan, "tiles": [v["spec"] for v in binfo["variants"]]}
-    return out
+
+
+def batch_only(args):
+    """The 64-image uneven batch alone: W warm-up and K timed steps (one
+    persistent launch each); one JSON line."""
+    import torch
+    world, rank, local = dist_setup()
+    peaks = load_peaks(torch.cuda.get_device_properties(0).multi_processor_count)
+    steps = min(args.steps, 50)
+    res = measure_batch(torch, world, make_flush(torch), peaks["fp32_tflops"], steps, args.warmup)
+    if rank == 0:
+        print(json.dumps({"metric": "batched FP32 forward GFLOP/s", "value": res["gflops"] * world,
+                          "unit": "GFLOP/s", "higher_is_better": True, "steps": steps, "warmup": args.warmup,
+                          "config": {"workload": "batch64_uneven", "l2": "flushed between steps"},
+                          "batch": res}), flush=True)
+    return 0
 
 
 def nn_only(args):
@@ -721,6 +745,8 @@ def main():
                     help="time only the nearest-neighbour search against this many neighbours")
     ap.add_argument("--fwdbwd", action="store_true",
                     help="the differentiation workload alone (forward, dL/dx, dL/dw)")
+    ap.add_argument("--batch", action="store_true",
+                    help="the 64-image uneven batch alone (one persistent launch per step)")
     ap.add_argument("--traffic-sweep", action="store_true",
                     help="one forward per tensor-core candidate, for an ncu DRAM-traffic capture")
     args = ap.parse_args()
@@ -730,6 +756,10 @@ def main():
         if args.warmup < 3:
             args.warmup = 3
         return fwdbwd_only(args)
+    if args.batch:
+        if args.warmup < 3:
+            args.warmup = 3
+        return batch_only(args)
     if args.nn:
         if args.warmup < 3:
             args.warmup = 3

@@ -770,10 +770,8 @@ fbcorr_status_t fbcorr_plan_candidates(fbcorr_plan_t p, char* buf, size_t cap) {
     std::vector<std::string> specs;
     if (p->dtype == FBCORR_F32) {
         const int topk = std::max(1, atoi(env_str("FBCORR_TUNE_TOPK", "48").c_str()));
-        for (const auto& t : direct_ranked(fwd_problem(p), smem_limit(p->dev), p->dev.sm_count, 0, 64)) {
-            if ((int)specs.size() >= topk) break;
-            specs.push_back(direct_tile_spec(t));
-        }
+        specs = direct_tuning_specs(direct_ranked(fwd_problem(p), smem_limit(p->dev), p->dev.sm_count, 0, 64),
+                                    topk);
         if (p->snippet.empty()) specs.push_back("default");
     } else {
         specs = tc_candidates(p->tc);

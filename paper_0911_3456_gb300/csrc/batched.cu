@@ -84,7 +84,7 @@ std::string batch_source(const fbcorr_batch_plan* b) {
         const BatchVariant& bv = b->variants[v];
         const DirectTile& t = bv.tile;
         o << "typedef FbcDirect<" << bv.fh << "," << bv.fw << "," << bv.d << "," << t.tr << "," << t.tf
-          << "," << t.wr << "," << t.wf << ",0," << epi << ",0," << t.chunk(bv.d) << "> FbcV" << v
+          << "," << t.wr << "," << t.wf << ",0," << epi << ",0," << t.chunk(bv.d) << "," << t.pk << "> FbcV" << v
           << ";\n";
         // one non-inlined function per variant: each gets its own register
         // allocation instead of the maximum over every variant of the switch
@@ -172,8 +172,11 @@ fbcorr_status_t select_variants(fbcorr_batch_plan* b, bool allow_tuning) {
             DirectProblem rep{(int)s[0], (int)s[1], bv.d, (int)(s[0] - s[4] + 1), (int)(s[1] - s[5] + 1),
                               (int)s[3], bv.fh, bv.fw, 0, 0, 0, epi, 0};
             auto ranked = direct_ranked(rep, kBatchSmemLimit, b->dev.sm_count, kBatchThreads, kBatchMaxBlock);
-            for (int k = 0; k < topk && k < (int)ranked.size(); ++k)
-                srcs.push_back(direct_kernel_source(rep, ranked[k], kname_for("fbc_direct", rep, ranked[k])));
+            for (const auto& sp : direct_tuning_specs(ranked, topk)) {
+                DirectTile t;
+                if (parse_direct_spec(sp, &t))
+                    srcs.push_back(direct_kernel_source(rep, t, kname_for("fbc_direct", rep, t)));
+            }
         }
         rtcg_precompile(srcs);
     }

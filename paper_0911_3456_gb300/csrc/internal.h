@@ -100,6 +100,7 @@ enum class VarKind { Default = 0, Direct = 1, Tensor = 2 };
 struct DirectTile {
     int tr = 8, tf = 8, wr = 1, wf = 2;
     int cc = 0;   // input channels staged per chunk; 0 = the whole depth
+    int pk = 0;   // 1: multiply-adds issued as packed pairs (fma.rn.f32x2), same bits
     int chunk(int c) const { return (cc > 0 && cc < c) ? cc : c; }
     int bh() const { return tr * wr; }
     int bn() const { return tf * wf; }
@@ -128,6 +129,10 @@ std::string direct_kernel_source(const DirectProblem& pr, const DirectTile& t,
 // max_block bounds the per-thread accumulator block TR*TF (register pressure).
 std::vector<DirectTile> direct_candidates(const DirectProblem& pr, size_t smem_limit,
                                           int threads = 0, int max_block = 64);
+// The specs the tuner times: the first topk tiles of a ranked list, each as
+// written and with packed-pair FMAs (pk=1); FBCORR_TUNE_PK=0 keeps only the
+// former.
+std::vector<std::string> direct_tuning_specs(const std::vector<DirectTile>& ranked, int topk);
 DirectTile direct_heuristic(const DirectProblem& pr, size_t smem_limit, int sm_count,
                             int threads = 0, int max_block = 64);
 // candidates ordered by the analytic model, best first

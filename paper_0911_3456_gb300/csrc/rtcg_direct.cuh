@@ -48,7 +48,13 @@ struct FbcOdd { static constexpr int value = (V % 2 == 1) ? V : V + 1; };
 // Chunking bounds shared memory by CC instead of the full depth C, so large
 // filters (11x11x32) and deep inputs (the 64-channel gradient of dL/dx) keep
 // several CTAs resident per SM.
-template <int FH, int FW, int C, int TR, int TF, int WR, int WF, int FLIP, int EPI, int MASK, int CC>
+// PK = 1 issues the TR x TF multiply-adds as packed pairs over adjacent filters
+// (fma.rn.f32x2, sm_100 and later): one instruction per two FMAs, each lane
+// rounded exactly like fmaf, so the results are bit-identical to PK = 0 and
+// only the issue pressure differs.  The input value is broadcast into both
+// halves once per (j, c) and reused for all FH filter rows.
+template <int FH, int FW, int C, int TR, int TF, int WR, int WF, int FLIP, int EPI, int MASK, int CC,
+          int PK = 0>
 struct FbcDirect {
     static constexpr int BW = 32;
     static constexpr int BH = TR * WR;
@@ -167,11 +173,15 @@ struct FbcDirect {
         float* xs = smem;
         float* ws = smem + XS;
 
-        float acc[TR][TF];
+        float acc[TR][TF];       // PK = 0
+        float2 acc2[TR][TF / 2]; // PK = 1: filters (2k, 2k+1) in one register pair
 #pragma unroll
-        for (int r = 0; r < TR; ++r)
+        for (int r = 0; r < TR; ++r) {
 #pragma unroll
             for (int f = 0; f < TF; ++f) acc[r][f] = 0.f;
+#pragma unroll
+            for (int f = 0; f < TF / 2; ++f) acc2[r][f] = make_float2(0.f, 0.f);
+        }
 
         const float* xb = xs + (wr * TR) * CC * COLP + lane;
         const float* wb = ws + wf * TF;
@@ -184,25 +194,50 @@ struct FbcDirect {
             for (int j = 0; j < FW; ++j) {
 #pragma unroll 2
                 for (int c = 0; c < CC; ++c) {
-                    float xv[TR + FH - 1];
+                    if constexpr (PK) {
+                        float2 xv2[TR + FH - 1];
 #pragma unroll
-                    for (int k = 0; k < TR + FH - 1; ++k) xv[k] = xb[(k * CC + c) * COLP + j];
-#pragma unroll
-                    for (int i = 0; i < FH; ++i) {
-                        float wv[TF];
-                        const float4* wp = reinterpret_cast<const float4*>(wb + ((i * FW + j) * CC + c) * BNP);
-#pragma unroll
-                        for (int f4 = 0; f4 < TF / 4; ++f4) {
-                            const float4 t4 = wp[f4];
-                            wv[4 * f4 + 0] = t4.x;
-                            wv[4 * f4 + 1] = t4.y;
-                            wv[4 * f4 + 2] = t4.z;
-                            wv[4 * f4 + 3] = t4.w;
+                        for (int k = 0; k < TR + FH - 1; ++k) {
+                            const float v = xb[(k * CC + c) * COLP + j];
+                            xv2[k] = make_float2(v, v);
                         }
 #pragma unroll
-                        for (int r = 0; r < TR; ++r)
+                        for (int i = 0; i < FH; ++i) {
+                            float2 wv2[TF / 2];
+                            const float4* wp = reinterpret_cast<const float4*>(wb + ((i * FW + j) * CC + c) * BNP);
 #pragma unroll
-                            for (int f = 0; f < TF; ++f) acc[r][f] = fmaf(xv[r + i], wv[f], acc[r][f]);
+                            for (int f4 = 0; f4 < TF / 4; ++f4) {
+                                const float4 t4 = wp[f4];
+                                wv2[2 * f4 + 0] = make_float2(t4.x, t4.y);
+                                wv2[2 * f4 + 1] = make_float2(t4.z, t4.w);
+                            }
+#pragma unroll
+                            for (int r = 0; r < TR; ++r)
+#pragma unroll
+                                for (int f = 0; f < TF / 2; ++f)
+                                    acc2[r][f] = __ffma2_rn(xv2[r + i], wv2[f], acc2[r][f]);
+                        }
+                    } else {
+                        float xv[TR + FH - 1];
+#pragma unroll
+                        for (int k = 0; k < TR + FH - 1; ++k) xv[k] = xb[(k * CC + c) * COLP + j];
+#pragma unroll
+                        for (int i = 0; i < FH; ++i) {
+                            float wv[TF];
+                            const float4* wp = reinterpret_cast<const float4*>(wb + ((i * FW + j) * CC + c) * BNP);
+#pragma unroll
+                            for (int f4 = 0; f4 < TF / 4; ++f4) {
+                                const float4 t4 = wp[f4];
+                                wv[4 * f4 + 0] = t4.x;
+                                wv[4 * f4 + 1] = t4.y;
+                                wv[4 * f4 + 2] = t4.z;
+                                wv[4 * f4 + 3] = t4.w;
+                            }
+#pragma unroll
+                            for (int r = 0; r < TR; ++r)
+#pragma unroll
+                                for (int f = 0; f < TF; ++f) acc[r][f] = fmaf(xv[r + i], wv[f], acc[r][f]);
+                        }
                     }
                 }
             }
@@ -220,7 +255,7 @@ struct FbcDirect {
             float v[TF];
 #pragma unroll
             for (int f = 0; f < TF; ++f) {
-                v[f] = acc[r][f];
+                v[f] = PK ? ((f & 1) ? acc2[r][f / 2].y : acc2[r][f / 2].x) : acc[r][f];
                 if constexpr (EPI == 2) v[f] = fbc_user_epi(v[f], nb + f, a.lo, a.hi);
                 if (EPI == 1) v[f] = fminf(fmaxf(v[f], a.lo), a.hi);
             }

@@ -118,7 +118,8 @@ def test_generated_sources_compile(lib, ins, fs, clamp):
 
 
 @pytest.mark.parametrize("spec", [b"direct:tr=8,tf=8,wr=1,wf=2", b"direct:tr=2,tf=4,wr=4,wf=1",
-                                  b"direct:tr=4,tf=8,wr=2,wf=4"])
+                                  b"direct:tr=4,tf=8,wr=2,wf=4", b"direct:tr=8,tf=8,wr=2,wf=2,cc=4,pk=1",
+                                  b"direct:tr=2,tf=4,wr=4,wf=1,cc=0,pk=1"])
 def test_explicit_tile_specs_compile(lib, spec):
     log = ctypes.create_string_buffer(1 << 16)
     st = lib.fbcorr_rtcg_check(C.I64_3(64, 80, 8), C.I64_4(24, 5, 3, 8), C.epilogue((0, 1)), spec,
@@ -126,6 +127,9 @@ def test_explicit_tile_specs_compile(lib, spec):
     assert st == 0, C.last_error() + log.value.decode()
     st = lib.fbcorr_rtcg_check(C.I64_3(64, 80, 8), C.I64_4(24, 5, 3, 8), C.epilogue(), b"direct:bogus",
                                log, len(log))
+    assert st == 1
+    st = lib.fbcorr_rtcg_check(C.I64_3(64, 80, 8), C.I64_4(24, 5, 3, 8), C.epilogue(),
+                               b"direct:tr=8,tf=8,wr=1,wf=2,cc=0,pk=2", log, len(log))
     assert st == 1
 
 

@@ -102,6 +102,25 @@ def test_every_tile_shape_matches_oracle(spec):
     assert normwise_rel(y, oracle.fwd(wl.x, wl.w)) <= TOL_F32
 
 
+@pytest.mark.parametrize("spec,clamp", [("direct:tr=8,tf=8,wr=2,wf=2,cc=4", None),
+                                        ("direct:tr=2,tf=4,wr=4,wf=1,cc=0", (-1.0, 1.0)),
+                                        ("direct:tr=4,tf=8,wr=2,wf=4,cc=4", (-0.5, 0.5)),
+                                        ("direct:tr=8,tf=4,wr=3,wf=1,cc=0", None)])
+def test_packed_pair_fma_is_bit_identical(spec, clamp):
+    """pk=1 issues the same multiply-adds as fma.rn.f32x2 pairs over adjacent
+    filters; each lane rounds like fmaf in the same order, so the output must
+    equal the scalar variant's bit for bit (27 filters: a ragged filter tile)."""
+    torch = torch_cuda()
+    wl = inputs.random_case(510, 51, 77, 8, 27, 5, 4)
+    y0, _ = _run(torch, wl.x, wl.w, clamp=clamp, spec=spec)
+    y1, p1 = _run(torch, wl.x, wl.w, clamp=clamp, spec=spec + ",pk=1")
+    assert p1.info()["fwd"]["spec"] == spec + ",pk=1"
+    assert p1.info()["fwd"]["kernel"].endswith("_pk1")
+    assert np.array_equal(y0, y1)
+    ref = oracle.fwd(wl.x, wl.w, epilogue=clamp) if clamp else oracle.fwd(wl.x, wl.w)
+    assert np.abs(y1 - ref).max() <= TOL_F32 * np.abs(oracle.fwd(wl.x, wl.w)).max()
+
+
 def test_run_to_run_bitwise_determinism():
     torch = torch_cuda()
     from paper_0911_3456_gb300.api import Plan
