@@ -237,13 +237,16 @@ def oracle_rows_sample(wl, rows, r0=None):
 
 
 def cpu_baseline(wl, target_s=12.0):
-    """Time the oracle on a sample of output rows sized for about target_s."""
+    """Time the oracle on a sample of output rows sized for about target_s
+    (at most the whole output).  The oracle spreads output rows over its
+    threads, so the per-row time is calibrated on two rows per thread."""
     import oracle
     Ho, Wo, N = wl.out_shape
     _, fh, fw, D = wl.w.shape
     row_flops = 2 * Wo * N * fh * fw * D
-    _, _, dt1, cores = oracle_rows_sample(wl, 1)
-    rows = max(1, min(Ho, int(target_s / max(dt1, 1e-6))))
+    k = max(1, min(Ho, 2 * oracle.max_threads()))
+    _, _, dtk, cores = oracle_rows_sample(wl, k)
+    rows = max(1, min(Ho, int(target_s * k / max(dtk, 1e-6))))
     r0, y, dt, cores = oracle_rows_sample(wl, rows)
     gflops = rows * row_flops / dt / 1e9
     return {"value": gflops, "unit": UNIT, "cores": cores, "kind": "oracle",
