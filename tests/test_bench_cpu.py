@@ -30,7 +30,7 @@ def test_cpu_baseline_covers_the_whole_output_when_it_fits():
     assert np.array_equal(y, oracle.fwd(wl.x, wl.w))
 
 
-def test_cpu_baseline_sample_scales_with_the_target():
+def test_cpu_baseline_partial_sample_is_a_centred_slab():
     """A short target gives a centred slab of consecutive rows (the calibration
     runs on two rows per oracle thread), and the slab is the oracle on the
     matching input rows."""
@@ -40,7 +40,7 @@ def test_cpu_baseline_sample_scales_with_the_target():
     k = max(1, min(Ho, 2 * oracle.max_threads()))
     _, _, dtk, _ = bench.oracle_rows_sample(wl, k)
     target = 3.0 * dtk
-    res, (r0, y) = bench.cpu_baseline(wl, target_s=target)
+    _, (r0, y) = bench.cpu_baseline(wl, target_s=target)
     rows = y.shape[0]
     assert 1 <= rows <= Ho
     assert r0 == (Ho - rows) // 2
