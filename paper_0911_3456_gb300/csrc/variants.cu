@@ -44,12 +44,27 @@ std::string direct_tile_spec(const DirectTile& t) {
 }
 
 bool parse_direct_spec(const std::string& s, DirectTile* t) {
+    // "direct:tr=R,tf=F,wr=WR,wf=WF" then optionally ",cc=CC" and ",pk=P", in
+    // that order; anything else left over rejects the spec
     DirectTile d;
-    const int n = sscanf(s.c_str(), "direct:tr=%d,tf=%d,wr=%d,wf=%d,cc=%d,pk=%d", &d.tr, &d.tf, &d.wr,
-                         &d.wf, &d.cc, &d.pk);
-    if (n < 4 || n > 6) return false;
-    if (n == 4) d.cc = 0;
-    if (n < 6) d.pk = 0;
+    d.cc = 0;
+    d.pk = 0;
+    int used = -1;
+    if (sscanf(s.c_str(), "direct:tr=%d,tf=%d,wr=%d,wf=%d%n", &d.tr, &d.tf, &d.wr, &d.wf, &used) != 4 ||
+        used < 0)
+        return false;
+    const char* rest = s.c_str() + used;
+    int u = -1;
+    if (strncmp(rest, ",cc=", 4) == 0) {
+        if (sscanf(rest, ",cc=%d%n", &d.cc, &u) != 1 || u < 0) return false;
+        rest += u;
+    }
+    u = -1;
+    if (strncmp(rest, ",pk=", 4) == 0) {
+        if (sscanf(rest, ",pk=%d%n", &d.pk, &u) != 1 || u < 0) return false;
+        rest += u;
+    }
+    if (*rest != '\0') return false;
     if (d.tr < 1 || d.tr > 16 || (d.tf != 4 && d.tf != 8 && d.tf != 12 && d.tf != 16) ||
         d.wr < 1 || d.wf < 1 || d.threads() > 1024 || d.cc < 0 || d.cc > 4096 || d.pk < 0 || d.pk > 1)
         return false;

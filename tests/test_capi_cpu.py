@@ -133,6 +133,21 @@ def test_explicit_tile_specs_compile(lib, spec):
     assert st == 1
 
 
+@pytest.mark.parametrize("spec,ok", [
+    (b"direct:tr=8,tf=8,wr=1,wf=2,pk=1", True),          # pk without cc
+    (b"direct:tr=8,tf=8,wr=1,wf=2,cc=4,pk=0", True),
+    (b"direct:tr=8,tf=8,wr=1,wf=2,cc=4,pk=1x", False),   # trailing text
+    (b"direct:tr=8,tf=8,wr=1,wf=2,cc=4,zz=1", False),    # unknown field
+    (b"direct:tr=8,tf=8,wr=1,wf=2,pk=1,cc=4", False),    # fields out of order
+    (b"direct:tr=8,tf=8,wr=1,wf=2 ", False),
+    (b"direct:tr=8,tf=6,wr=1,wf=2", False),              # TF not a multiple of 4
+])
+def test_direct_spec_parsing_is_strict(lib, spec, ok):
+    log = ctypes.create_string_buffer(1 << 16)
+    st = lib.fbcorr_rtcg_check(C.I64_3(64, 80, 8), C.I64_4(24, 5, 3, 8), C.epilogue(), spec, log, len(log))
+    assert (st == 0) == ok, (st, C.last_error())
+
+
 @pytest.mark.parametrize("D,f,spec", [
     (32, 5, b"tcgen05:na=2,nb=4,nt=256,bt=5,ew=4,fz=1,nr=0,cw=4"),    # the precision workload, converters from registers
     (32, 5, b"tcgen05:na=3,nb=3,nt=256,bt=3,ew=8,fz=2,nr=3,cw=8"),    # raw-row ring; two stages, the second partial
