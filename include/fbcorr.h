@@ -96,6 +96,10 @@ typedef struct {
 fbcorr_status_t fbcorr_plan_create(fbcorr_plan_t* out, const int64_t in_shape[3],
                                    const int64_t filt_shape[4], fbcorr_dtype_t dtype,
                                    fbcorr_epilogue_t epilogue);
+/* Release what the plan owns (modules, streams, events, pinned status word,
+ * tensor-core descriptors).  NULL is accepted and does nothing.  The caller
+ * makes sure no work the plan enqueued is still running (synchronise its
+ * streams first); caller-owned tensors and workspaces are not touched. */
 fbcorr_status_t fbcorr_plan_destroy(fbcorr_plan_t plan);
 
 /* A plan whose epilogue is a user C expression compiled into the forward
@@ -222,8 +226,14 @@ fbcorr_status_t fbcorr_batch_plan_create(fbcorr_batch_plan_t* out, int n,
                                          const int64_t (*in_shapes)[3],
                                          const int64_t (*filt_shapes)[4], fbcorr_dtype_t dtype,
                                          fbcorr_epilogue_t epilogue);
+/* Release the batch plan's graph, work list and counters (NULL: no-op); its
+ * launches must have finished. */
 fbcorr_status_t fbcorr_batch_plan_destroy(fbcorr_batch_plan_t plan);
+/* Device workspace fbcorr_forward_batched needs: currently always 0 (the plan
+ * owns its work list and counter). */
 fbcorr_status_t fbcorr_batch_plan_workspace_size(fbcorr_batch_plan_t plan, size_t* bytes);
+/* A JSON description of the plan (images, work items, grid, residency,
+ * variants and their tiles) into buf (NUL-terminated, cap bytes). */
 fbcorr_status_t fbcorr_batch_plan_info(fbcorr_batch_plan_t plan, char* buf, size_t cap);
 
 /* x[k], w[k], y[k]: HOST arrays of n DEVICE pointers (image k's tensors). */
@@ -251,9 +261,14 @@ fbcorr_status_t fbcorr_forward_batched(fbcorr_batch_plan_t plan, const float* co
  * synchronisation and is stream-ordered. */
 fbcorr_status_t fbcorr_nn_plan_create(fbcorr_nn_plan_t* out, int64_t n_targets, int64_t n_neighbors,
                                       int64_t dim, fbcorr_dtype_t dtype);
+/* Release the plan (NULL: no-op); its searches must have finished. */
 fbcorr_status_t fbcorr_nn_plan_destroy(fbcorr_nn_plan_t plan);
 /* Device workspace the search needs (BF16 copies of both sets, norms, candidates). */
 fbcorr_status_t fbcorr_nn_workspace_size(fbcorr_nn_plan_t plan, size_t* bytes);
+/* Run the search on `stream`: targets, neighbors, idx_out, dist_out and ws are
+ * DEVICE pointers (NULL: FBCORR_ERR_INVALID_ARG), 16-byte aligned
+ * (FBCORR_ERR_ALIGNMENT otherwise); ws must hold fbcorr_nn_workspace_size bytes
+ * (FBCORR_ERR_WORKSPACE otherwise).  All checks happen before any launch. */
 fbcorr_status_t fbcorr_nn_search(fbcorr_nn_plan_t plan, const float* targets, const float* neighbors,
                                  int64_t* idx_out, float* dist_out, void* ws, size_t ws_bytes,
                                  fbcorr_stream_t stream);
@@ -264,7 +279,10 @@ fbcorr_status_t fbcorr_nn_rtcg_check(int64_t dim, fbcorr_dtype_t dtype, char* lo
 
 /* ---- diagnostics -------------------------------------------------------- */
 
+/* The enumerator's name, e.g. "FBCORR_ERR_SHAPE" (a static string). */
 const char* fbcorr_status_string(fbcorr_status_t status);
+/* Detail of the last failing call on this thread (thread-local; every other
+ * entry point clears it when it starts, so read it before the next call). */
 const char* fbcorr_last_error(void);
 /* Library version string, e.g. "fbcorr 0.1 sm_103a". */
 const char* fbcorr_version(void);
