@@ -322,6 +322,27 @@ def measured_traffic(info, workload):
     return int(entry["dram_bytes_per_launch"]), entry.get("profile")
 
 
+def fp32_fma_probe(sm_count: int, iters: int = 5000) -> dict:
+    """The FP32 multiply-add rate the GPU sustains (the library's register-only
+    probe, scalar FMAs and packed pairs), beside the nominal FP32 peak; run
+    outside every timed region.  A failure is reported, not raised."""
+    import ctypes
+    from paper_0911_3456_gb300 import _capi as C
+    lib = C.load()
+    out = {"iters": iters}
+    for name, pk in (("scalar", 0), ("packed", 1)):
+        t, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+        st = lib.fbcorr_fp32_fma_probe(pk, iters, ctypes.byref(t), ctypes.byref(ms))
+        if st != 0:
+            return {"unavailable": f"{C.STATUS_NAMES.get(st, st)}: {C.last_error()}"}
+        out[f"{name}_tflops"] = t.value
+        out[f"{name}_ms"] = ms.value
+    best = max(out["scalar_tflops"], out["packed_tflops"])
+    # the SM clock at which 128 lanes x 2 FLOP per SM would give the best rate
+    out["implied_sm_mhz"] = best * 1e12 / (sm_count * 128 * 2) / 1e6
+    return out
+
+
 def run_ours(args):
     import torch
     from paper_0911_3456_gb300 import inputs
@@ -469,6 +490,10 @@ def run_ours(args):
         if "f32" in modes and mode in modes and "gflops" in modes.get("f32", {}):
             detail["speedup_vs_fp32_direct"] = modes[mode]["gflops"] / modes["f32"]["gflops"]
         detail.update(secondary(torch, args, world, peaks))
+        try:
+            detail["fp32_fma_probe"] = fp32_fma_probe(props.multi_processor_count)
+        except Exception as e:   # reported, never fatal to the line
+            detail["fp32_fma_probe"] = {"unavailable": str(e)}
 
     if rank == 0:
         line = {

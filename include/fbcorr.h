@@ -287,6 +287,18 @@ const char* fbcorr_last_error(void);
 /* Library version string, e.g. "fbcorr 0.1 sm_103a". */
 const char* fbcorr_version(void);
 
+/* The FP32 multiply-add rate the current device sustains, the measured
+ * counterpart of the nominal FP32 peak (SMs x 128 lanes x 2 FLOP x clock) that
+ * the FP32 kernels are rated against; the paper has no counterpart.  Runs 8
+ * independent multiply-add chains per thread in registers on 2048 threads per
+ * SM, `iters` x 128 multiply-adds per thread per launch, packed = 0 with scalar
+ * FMAs or 1 with packed pairs (fma.rn.f32x2); one warm-up and three timed
+ * launches on an internal stream.  *tflops = 2 x multiply-adds / best launch
+ * time; *best_ms (may be NULL) = that time.  Allocates and frees one small
+ * device buffer and synchronises with its own stream: a diagnostic, not for
+ * use inside a capture.  iters in [1, 2^24], else FBCORR_ERR_INVALID_ARG. */
+fbcorr_status_t fbcorr_fp32_fma_probe(int packed, int iters, double* tflops, double* best_ms);
+
 /* Generate and compile (NVRTC, sm_103a) -- without loading or running -- the
  * forward, dL/dx and dL/dw kernels that an FP32 plan of this shape would use,
  * with the forward tile `spec` ("heuristic" or a "direct:..." spec); or, for a

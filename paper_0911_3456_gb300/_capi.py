@@ -83,6 +83,8 @@ PROTOTYPES = {
     "fbcorr_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "fbcorr_last_error": (ctypes.c_char_p, []),
     "fbcorr_version": (ctypes.c_char_p, []),
+    "fbcorr_fp32_fma_probe": (_st, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(ctypes.c_double)]),
     "fbcorr_rtcg_check": (_st, [I64_3, I64_4, Epilogue, ctypes.c_char_p, ctypes.c_char_p, _sz]),
     "fbcorr_batch_rtcg_check": (_st, [ctypes.c_int, ctypes.POINTER(ctypes.c_int64),
                                       ctypes.POINTER(ctypes.c_int64), Epilogue, ctypes.c_char_p, _sz]),

@@ -243,3 +243,12 @@ def test_snippet_kind_needs_its_own_entry_points(lib):
     ins = (ctypes.c_int64 * 3)(16, 16, 4)
     fls = (ctypes.c_int64 * 4)(2, 3, 3, 4)
     assert lib.fbcorr_batch_rtcg_check(1, ins, fls, epi, log, len(log)) == 3
+
+
+def test_fma_probe_rejects_bad_arguments_before_any_launch(lib):
+    t = ctypes.c_double()
+    assert lib.fbcorr_fp32_fma_probe(0, 0, ctypes.byref(t), None) == 1
+    assert lib.fbcorr_fp32_fma_probe(2, 100, ctypes.byref(t), None) == 1
+    assert lib.fbcorr_fp32_fma_probe(0, (1 << 24) + 1, ctypes.byref(t), None) == 1
+    assert lib.fbcorr_fp32_fma_probe(1, 100, None, None) == 1
+    assert "iters" in C.last_error()
