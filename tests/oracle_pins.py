@@ -49,7 +49,10 @@ def _rand(seed, H, W, D, N, fh, fw):
     return x, w, g
 
 
-SHAPES = [(7, 9, 3, 4, 3, 2), (6, 5, 2, 3, 1, 4), (10, 8, 5, 2, 4, 3), (5, 5, 1, 1, 5, 5)]
+# (H, W, D, N, fh, fw); the last has the even square 8x8 filters and depth 4 of
+# the fourth row of the paper's filter-bank table (2048x2048x4 input, 4x8x8x4 bank)
+SHAPES = [(7, 9, 3, 4, 3, 2), (6, 5, 2, 3, 1, 4), (10, 8, 5, 2, 4, 3), (5, 5, 1, 1, 5, 5),
+          (12, 11, 4, 4, 8, 8)]
 
 
 def pin_scipy_forward(orc):
