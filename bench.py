@@ -249,10 +249,31 @@ def cpu_baseline(wl, target_s=12.0):
     rows = max(1, min(Ho, int(target_s * k / max(dtk, 1e-6))))
     r0, y, dt, cores = oracle_rows_sample(wl, rows)
     gflops = rows * row_flops / dt / 1e9
+    single = oracle_single_core(wl, dt / rows * cores, min(2.0, target_s / 4))
     return {"value": gflops, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"{rows} consecutive output rows (from row {r0}) of {Ho}: "
                       f"{rows * Wo * N} outputs, FP64 nested loops, OpenMP over rows",
-            "seconds": dt}, (r0, y)
+            "seconds": dt, "single_core": single}, (r0, y)
+
+
+def oracle_single_core(wl, row_s_guess, target_s):
+    """The oracle on one thread over a slab of consecutive output rows sized
+    for about target_s (from a per-row time guess), extrapolated linearly to the
+    whole output and labelled as extrapolated."""
+    import oracle
+    Ho, Wo, N = wl.out_shape
+    _, fh, fw, D = wl.w.shape
+    row_flops = 2 * Wo * N * fh * fw * D
+    rows = max(1, min(Ho, int(target_s / max(row_s_guess, 1e-6))))
+    oracle.set_threads(1)
+    try:
+        r0, _, dt, _ = oracle_rows_sample(wl, rows)
+    finally:
+        oracle.set_threads(0)
+    return {"value": rows * row_flops / dt / 1e9, "unit": UNIT, "cores": 1, "rows": rows, "seconds": dt,
+            "whole_output_seconds_extrapolated": dt / rows * Ho,
+            "note": f"{rows} consecutive output rows (from row {r0}) of {Ho} on one thread, "
+                    "extrapolated linearly to the whole output"}
 
 
 # ----------------------------------------------------------------------------- reference arm

@@ -48,3 +48,15 @@ def test_cpu_baseline_partial_sample_is_a_centred_slab():
     fh = wl.w.shape[1]
     ref = oracle.fwd(wl.x[r0:r0 + rows + fh - 1], wl.w)
     assert np.array_equal(y, ref)
+
+
+def test_cpu_baseline_reports_an_extrapolated_single_core_figure():
+    oracle.build()
+    wl = inputs.workload_small_f32()
+    before = oracle.max_threads()
+    res, _ = bench.cpu_baseline(wl, target_s=0.4)
+    one = res["single_core"]
+    assert one["cores"] == 1 and 1 <= one["rows"] <= wl.out_shape[0]
+    assert one["value"] > 0 and "extrapolated" in one["note"]
+    assert abs(one["whole_output_seconds_extrapolated"] - one["seconds"] / one["rows"] * wl.out_shape[0]) < 1e-9
+    assert oracle.max_threads() == before          # the oracle's thread count is restored
