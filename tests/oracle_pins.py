@@ -218,6 +218,13 @@ def pin_points(orc):
     dx = orc.bwd_input(g, w, x.shape)
     idx = np.stack([rng.integers(0, s, 50) for s in x.shape], axis=1)
     assert np.array_equal(orc.bwd_input_points(g, w, x.shape, idx), dx[tuple(idx.T)])
+    # with the clamp the gradient passes only where -1 < y < 1 (both occur here)
+    inside = (y > -1.0) & (y < 1.0)
+    assert inside.any() and (~inside).any()
+    dxc = orc.bwd_input(g, w, x.shape, y=y, epilogue=(-1.0, 1.0))
+    assert not np.array_equal(dxc, dx)
+    assert np.array_equal(orc.bwd_input_points(g, w, x.shape, idx, y=y, epilogue=(-1.0, 1.0)),
+                          dxc[tuple(idx.T)])
 
 
 # --- exact nearest-neighbour search (Sec. 6.3) ---------------------------------

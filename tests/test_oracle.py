@@ -98,6 +98,14 @@ MUTANTS = {
                             "for (int64_t p = 0; p < Ho - 1; ++p)\n            for (int64_t q = 0; q < Wo; ++q)\n                s += g_eff"),
     "dw_swapped_ij_decode": ("const int64_t j = (e / D) % fw;\n        const int64_t i = (e / (D * fw)) % fh;",
                              "const int64_t i = (e / D) % fh;\n        const int64_t j = (e / (D * fh)) % fw;"),
+    "dx_last_output_row_dropped": ("                        if (po < 0 || po >= Ho) continue;",
+                                   "                        if (po < 0 || po >= Ho - 1) continue;"),
+    "dw_clamp_mask_ignored": ("                s += g_eff(g, y, (p * Wo + q) * N + n, epi_kind, lo, hi) *",
+                              "                s += g[(p * Wo + q) * N + n] *"),
+    "dx_points_clamp_mask_ignored": ("qo >= Wo) continue;\n                    s += g_eff(g, y, (po * Wo + qo) * N + n, epi_kind, lo, hi) *",
+                                     "qo >= Wo) continue;\n                    s += g[(po * Wo + qo) * N + n] *"),
+    "fwd_points_clamp_dropped": ("        if (epi_kind == ORACLE_EPI_CLAMP) s = clamp_d(s, lo, hi);\n        out[k] = s;",
+                                 "        out[k] = s;"),
 }
 
 # planted mistakes in the nearest-neighbour oracle (nn_oracle.c)
