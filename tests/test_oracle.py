@@ -115,6 +115,9 @@ NN_MUTANTS = {
     "nn_dropped_last_dimension": ("for (int64_t k = 0; k < dim; ++k) {", "for (int64_t k = 0; k < dim - 1; ++k) {"),
     "nn_runner_up_misses_later": ("            } else if (d < second) {\n                second = d;\n            }",
                                   "            }"),
+    "nn_old_best_not_demoted": ("                second = best;\n                best = d;", "                best = d;"),
+    "nn_skips_last_neighbour": ("for (int64_t j = 0; j < nn; ++j) {", "for (int64_t j = 0; j < nn - 1; ++j) {"),
+    "nn_neighbour_row_stride": ("const double* nj = n + j * dim;", "const double* nj = n + j;"),
 }
 
 _RUNNER = textwrap.dedent("""
