@@ -73,9 +73,6 @@ fbcorr_status_t launch(const Kernel& k, dim3 grid, void** args, cudaStream_t str
 // before it reads anything that kernel writes.  Falls back to launch() on a
 // driver without cuLaunchKernelEx.
 fbcorr_status_t launch_dependent(const Kernel& k, dim3 grid, void** args, cudaStream_t stream);
-// Largest number of co-resident clusters of `cluster` CTAs of kernel `k` (its
-// compile-time cluster shape, block size and dynamic shared memory).
-fbcorr_status_t cluster_occupancy(const Kernel& k, int cluster, int* clusters);
 // A 3D FP32 tensor map for tiled bulk stores (128-byte swizzle, dims innermost
 // first, strides in bytes of dims 1 and 2) written into the 128-byte `map`;
 // false when the driver offers no tensor maps or rejects the arguments.

@@ -3,7 +3,7 @@
 //
 // The paper builds its kernels from source strings at run time and caches the
 // binaries in a "semi-permanent" compiler cache keyed on the hardware/software
-// environment, recompiling only when that changes (Sec. 4, Fig. 2).  Here the
+// environment, recompiling only when that changes (Sec. 5, Fig. 2).  Here the
 // cache key is a hash of the full source, the NVRTC options, the NVRTC
 // version and the target architecture; the file is written atomically
 // (temporary file + rename) so that concurrent processes never read a torn
@@ -42,7 +42,6 @@ struct DriverApi {
     CUresult (*graphExecKernelNodeSetParams)(CUgraphExec, CUgraphNode,
                                              const CUDA_KERNEL_NODE_PARAMS*) = nullptr;
     CUresult (*occupancy)(int*, CUfunction, int, size_t) = nullptr;
-    CUresult (*clusterOccupancy)(int*, CUfunction, const CUlaunchConfig*) = nullptr;   // optional
     CUresult (*launchKernelEx)(const CUlaunchConfig*, CUfunction, void**, void**) = nullptr;   // optional
 };
 
@@ -74,7 +73,6 @@ fbcorr_status_t driver_api(DriverApi** out) {
                   resolve("cuGraphExecKernelNodeSetParams", &d.graphExecKernelNodeSetParams) &&
                   resolve("cuOccupancyMaxActiveBlocksPerMultiprocessor", &d.occupancy);
         if (!ok) return set_error(FBCORR_ERR_CUDA, "could not resolve CUDA driver entry points");
-        if (!resolve("cuOccupancyMaxActiveClusters", &d.clusterOccupancy)) d.clusterOccupancy = nullptr;
         if (!resolve("cuLaunchKernelEx", &d.launchKernelEx)) d.launchKernelEx = nullptr;
         d.ok = true;
         g_drv = d;
@@ -318,27 +316,6 @@ std::string hex64(unsigned long long v) {
     char b[32];
     snprintf(b, sizeof b, "%016llx", v);
     return b;
-}
-
-fbcorr_status_t cluster_occupancy(const Kernel& k, int cluster, int* clusters) {
-    DriverApi* drv = nullptr;
-    FBC_TRY(driver_api(&drv));
-    *clusters = 0;
-    if (!drv->clusterOccupancy)
-        return set_error(FBCORR_ERR_UNSUPPORTED, "the driver offers no cluster occupancy query");
-    CUlaunchConfig cfg;
-    memset(&cfg, 0, sizeof cfg);
-    cfg.gridDimX = (unsigned)cluster;
-    cfg.gridDimY = 1;
-    cfg.gridDimZ = 1;
-    cfg.blockDimX = (unsigned)k.threads;
-    cfg.blockDimY = 1;
-    cfg.blockDimZ = 1;
-    cfg.sharedMemBytes = (unsigned)k.smem;
-    const CUresult r = drv->clusterOccupancy(clusters, k.fn, &cfg);
-    if (r != CUDA_SUCCESS)
-        return set_error(FBCORR_ERR_CUDA, "cuOccupancyMaxActiveClusters(%s): %s", k.name.c_str(), cu_err(r));
-    return FBCORR_OK;
 }
 
 bool encode_f32_store_map(void* map, const float* base, const unsigned long long dims[3],

@@ -1,8 +1,8 @@
 // rtcg_ptx.cuh -- PTX wrappers shared by the run-time generated tcgen05 kernels
 // (the filter-bank correlation of rtcg_tc.cuh and the nearest-neighbour distance
 // kernel of rtcg_nn.cuh): shared-memory addresses, mbarriers with time-bounded
-// waits, 1D bulk copies (with cluster multicast), tiled bulk stores, cluster
-// barriers, tcgen05.mma / commit / ld, BF16 packing.  Embedded as a
+// waits, 1D bulk copies, tiled bulk stores, tcgen05.mma / commit / ld, BF16
+// packing.  Embedded as a
 // string and placed after the kernel's parameter block in every generated
 // source; self-contained (no system headers).  A bounded wait takes any
 // parameter block with `wait_ns` (the bound) and `err` (the host-mapped error
@@ -60,22 +60,6 @@ __device__ __forceinline__ void fbc_bulk_g2s(fbc_u32 dst, const void* src, fbc_u
         : "memory");
 }
 
-// 1D bulk copy global -> the same shared-memory offset in every CTA of `mask`
-// (cluster multicast); completion counted on the mbarrier at `bar`'s offset in each.
-__device__ __forceinline__ void fbc_bulk_g2s_mc(fbc_u32 dst, const void* src, fbc_u32 bytes, fbc_u32 bar,
-                                                unsigned short mask) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1], %2, [%3], "
-        "%4;" ::"r"(dst),
-        "l"(src), "r"(bytes), "r"(bar), "h"(mask)
-        : "memory");
-}
-
-// Every thread of every CTA of the cluster (release / acquire).
-__device__ __forceinline__ void fbc_cluster_sync() {
-    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
 __device__ __forceinline__ void fbc_tc_fence_before() {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -99,15 +83,6 @@ __device__ __forceinline__ void fbc_umma(fbc_u32 d_tmem, fbc_u64 a, fbc_u64 b, f
 __device__ __forceinline__ void fbc_umma_commit(fbc_u32 bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                  : "memory");
-}
-
-// Commit whose arrival goes to the mbarrier at `bar`'s offset in every CTA of `mask`.
-__device__ __forceinline__ void fbc_umma_commit_mc(fbc_u32 bar, unsigned short mask) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-            bar),
-        "h"(mask)
-        : "memory");
 }
 
 // tcgen05.ld 16x256b.x8 -- 16 TMEM lanes x 64 columns: registers 4g, 4g+1 hold

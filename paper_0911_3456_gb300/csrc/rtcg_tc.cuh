@@ -2,9 +2,9 @@
 // NVRTC for sm_103a with the chunk-plane count NC, the split mode, the filter
 // width FW, the taps per B stage BT, the epilogue warp count EW, the fused
 // conversion switch FUSE (and its converter warps CW), the snippet switch USER,
-// the epilogue store path TS (with SB staging slots) and the cluster-pair
-// switch MC baked in.  Embedded as a string into libfbcorr and
-// prefixed with tc_params.h and rtcg_ptx.cuh; self-contained (no system headers).
+// and the epilogue store path TS (with SB staging slots) baked in.  Embedded
+// as a string into libfbcorr and prefixed with tc_params.h and rtcg_ptx.cuh;
+// self-contained (no system headers).
 //
 // The correlation of Sec. 6.2 as an implicit GEMM: for every filter tap (i, j)
 //   Y[m, n] += sum_d X[m + i*W + j, d] * Wt[n, i, j, d]
@@ -19,7 +19,7 @@
 // one costs.  Loop control, ring-index and descriptor arithmetic between MMAs
 // (runtime tap counts, stage boundaries) left the tensor core idle for a third
 // of the time; with FW and BT compile-time the MMA sequence of a filter row is
-// straight-line code (the paper's loop unrolling by RTCG, Sec. 3.2 and 6.2).
+// straight-line code (the paper's loop unrolling by RTCG, Sec. 4.2 and 6.2).
 //
 // Roles per CTA (persistent, one per SM):
 //   warp 0      producer: cp.async.bulk (1D TMA) of B slices of BT consecutive
@@ -59,15 +59,6 @@
 // from half-width planes), so that round keeps twice as many SMs busy for half
 // as long.
 //
-// Pairs (MC = 1): every tile reads the whole filter bank from L2 (400 KB in
-// BF16 for 256 filters of 5x5x32).  In this mode the kernel runs as clusters of
-// two CTAs that process two pixel tiles against the same B sequence: each
-// producer copies half of every B stage and multicasts it into both CTAs, each
-// CTA's MMA commit releases the stage in both, so L2 serves every B byte once
-// per pair.  (Each SM still fills its shared memory with the whole stage, and
-// that fill latency, not L2 bandwidth, is what the MMAs wait on: on the
-// workloads measured this mode is not faster, so only a spec selects it.)
-//
 // Every mbarrier wait is bounded in time (%globaltimer); on expiry the kernel
 // records an error code in host-mapped memory, stops every role, waits (again
 // bounded) for its own copies and MMAs in flight, frees TMEM and returns.
@@ -98,7 +89,7 @@ __device__ __forceinline__ void fbc_issue_tap(fbc_u32 d_tmem, fbc_u64 ad, fbc_u6
 }
 
 // ---------------------------------------------------------------- the kernel body
-template <int NC, int SPLIT, int FW, int BT, int EW, int FUSE, int CW, int USER, int TS, int SB, int MC>
+template <int NC, int SPLIT, int FW, int BT, int EW, int FUSE, int CW, int USER, int TS, int SB>
 __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
     constexpr int NST = (FW + BT - 1) / BT;          // B stages per filter row
     constexpr int L = FBC_TC_TILE_M + FW - 1;        // slab pixels per filter row
@@ -126,7 +117,7 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
         }
         for (int s = 0; s < P.nb; ++s) {
             fbc_mbar_init(b_full0 + 8u * s, 1);
-            fbc_mbar_init(b_empty0 + 8u * s, MC ? 2 : 1);   // MC: both CTAs' MMAs release a stage
+            fbc_mbar_init(b_empty0 + 8u * s, 1);
         }
         for (int s = 0; s < 2; ++s) {
             fbc_mbar_init(acc_full0 + 8u * s, 1);
@@ -148,28 +139,22 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
     }
     fbc_tc_fence_before();
     __syncthreads();
-    if constexpr (MC) fbc_cluster_sync();   // the peer's barriers are initialised before any multicast
     fbc_tc_fence_after();
     const fbc_u32 tmem = s_tmem;
     volatile int* abort_flag = &s_abort;
-    // Schedule: tile t is pixel tile t % mtiles_s of filter tile t / mtiles_s.
-    // MC = 0: tiles blockIdx.x, blockIdx.x + gridDim.x, ...
-    // MC = 1: cluster c = blockIdx.x / 2 takes the tile pairs (2j, 2j + 1), j = c,
-    // c + clusters, ...; its CTA of rank r runs tile 2j + r, so both CTAs run the
-    // same filter tiles in the same order (mtiles_s is even) and share every B
-    // stage.  A pixel tile >= mtiles (odd mtiles) is a phantom: its slab rows lie
-    // past the output and its results are never stored.
-    // Tail halves (MC = 0, one filter tile of 256): the tiles from nfull on, the
+    // Schedule: tile t is pixel tile t % mtiles of filter tile t / mtiles; CTA b
+    // takes the work items b, b + gridDim.x, ...
+    // Tail halves (one filter tile of 256): the tiles from nfull on, the
     // last partial round, run as two work items each, one per 128-column half of
     // the filter tile, so that round occupies twice as many SMs for half as long;
     // a half takes its B operand from the half-width planes whi2 / wlo2.
-    const int nsched = P.mtiles_s * P.ntn;
-    const int unit = MC ? (int)blockIdx.x >> 1 : (int)blockIdx.x;
-    const int nunits = MC ? (int)gridDim.x >> 1 : (int)gridDim.x;
-    const int nwork = MC ? nsched >> 1 : P.nfull + 2 * (nsched - P.nfull);
+    const int nsched = P.mtiles * P.ntn;
+    const int unit = (int)blockIdx.x;
+    const int nunits = (int)gridDim.x;
+    const int nwork = P.nfull + 2 * (nsched - P.nfull);
     const int my_tiles = unit < nwork ? (nwork - 1 - unit) / nunits + 1 : 0;   // work items
     struct Item {
-        int tile;    // pixel tile t % mtiles_s of filter tile t / mtiles_s
+        int tile;    // pixel tile t % mtiles of filter tile t / mtiles
         int nt;      // filter columns of this item
         int n0;      // first filter
         long long wbase;   // byte offset of the item's planes in whi / wlo (half: in whi2 / wlo2)
@@ -178,15 +163,13 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
     auto item_of = [&](int k) -> Item {
         const int w = unit + k * nunits;
         Item it;
-        it.half = !MC && w >= P.nfull;
-        if (MC) {
-            it.tile = 2 * w + ((int)blockIdx.x & 1);
-        } else if (!it.half) {
+        it.half = w >= P.nfull;
+        if (!it.half) {
             it.tile = w;
         } else {
             it.tile = P.nfull + ((w - P.nfull) >> 1);
         }
-        const int nti = it.tile / P.mtiles_s;
+        const int nti = it.tile / P.mtiles;
         const int h = (w - P.nfull) & 1;
         it.nt = it.half ? P.nt >> 1 : P.nt;
         it.n0 = it.half ? h * it.nt : nti * P.nt;
@@ -200,7 +183,7 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
     // first input pixel of slab row r
     auto row_p0 = [&](int r) -> long long {
         const int tile = tile_of(r / P.fh);
-        return (long long)(tile % P.mtiles_s) * FBC_TC_TILE_M + (long long)(r % P.fh) * P.W;
+        return (long long)(tile % P.mtiles) * FBC_TC_TILE_M + (long long)(r % P.fh) * P.W;
     };
     // pixels of slab row r that lie inside x (the rest reads as zero)
     auto row_valid = [&](long long p0) -> int {
@@ -268,20 +251,9 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
                     fbc_mbar_expect_tx(bfull, SPLIT ? 2u * bytes : bytes);
                     if ((int)b_it != P.drop_b) {
                         const fbc_u32 bdst = sbase + P.b_off + bs * P.b_stage;
-                        if constexpr (MC) {
-                            // this CTA's half of the stage into both CTAs of the pair; the
-                            // peer's copy brings the other half (each b_full expects both)
-                            const fbc_u32 hb = bytes >> 1;
-                            const fbc_u32 ho = ((fbc_u32)blockIdx.x & 1u) * hb;
-                            fbc_bulk_g2s_mc(bdst + ho, wtap_hi + s * BT * tap_bytes + ho, hb, bfull, 3);
-                            if (SPLIT)
-                                fbc_bulk_g2s_mc(bdst + (fbc_u32)BT * b_half + ho, wtap_lo + s * BT * tap_bytes + ho, hb,
-                                                bfull, 3);
-                        } else {
-                            fbc_bulk_g2s(bdst, wtap_hi + s * BT * tap_bytes, bytes, bfull);
-                            if (SPLIT)
-                                fbc_bulk_g2s(bdst + (fbc_u32)BT * b_half, wtap_lo + s * BT * tap_bytes, bytes, bfull);
-                        }
+                        fbc_bulk_g2s(bdst, wtap_hi + s * BT * tap_bytes, bytes, bfull);
+                        if (SPLIT)
+                            fbc_bulk_g2s(bdst + (fbc_u32)BT * b_half, wtap_lo + s * BT * tap_bytes, bytes, bfull);
                     }
                     ++b_it;
                     if (++bs == P.nb) { bs = 0; bph ^= 1; }
@@ -341,10 +313,7 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
                                 fbc_issue_tap<NC, SPLIT>(d_tmem, adesc + (fbc_u64)(s * BT + t), bdesc + (fbc_u64)t * btap,
                                                          ak, bk, alo, blo, idesc, accumulate);
                         issued = true;
-                        if constexpr (MC)
-                            fbc_umma_commit_mc(b_empty0 + 8u * bs, 3);   // the stage is free once both CTAs are done
-                        else
-                            fbc_umma_commit(b_empty0 + 8u * bs);
+                        fbc_umma_commit(b_empty0 + 8u * bs);
                         if (++bs == P.nb) { bs = 0; bph ^= 1; }
                     }
                     if (!ok) break;
@@ -375,7 +344,7 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
         fbc_u32 acc_it = 0;
         for (int k = 0; k < my_tiles; ++k) {
             const Item itm = item_of(k);
-            const int mt = itm.tile % P.mtiles_s;
+            const int mt = itm.tile % P.mtiles;
             const int nt_i = itm.nt;     // filter columns of this work item, from column 0 of the accumulator
             const int nb0 = itm.n0;      // its first filter
             const int acc = acc_it & 1;
@@ -672,9 +641,6 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
     __syncwarp();
     fbc_tc_fence_before();
     __syncthreads();
-    // MC: the peer may still multicast into this CTA's shared memory or arrive on
-    // its barriers until it has finished too
-    if constexpr (MC) fbc_cluster_sync();
     fbc_tc_fence_after();
     if (warp == 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(FBC_TC_TMEM_COLS));

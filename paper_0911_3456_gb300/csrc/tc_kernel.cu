@@ -157,7 +157,6 @@ struct TcConfig {
     int cw = 0;                        // converter warps (fuse = 1, 2): 4 or 8
     int ts = 0;                        // epilogue stores: 0 direct, 32 tiled (32-pixel boxes)
     int sb = 0;                        // staging slots per epilogue warp (ts = 32): 1..3
-    int mc = 0;                        // 1: clusters of two CTAs sharing every B stage (multicast)
 };
 
 struct TcPlan {
@@ -174,7 +173,6 @@ struct TcPlan {
     float lo = 0.f, hi = 0.f;
     std::string snippet;   // user epilogue expression ("" for none)
     int sm_count = 1;
-    int pair_slots = 0;   // co-resident two-CTA clusters of the current pair kernel
     unsigned long long wait_ns = 0;
     int drop_b = -1;
     std::map<std::string, Kernel> kernels;   // generated kernels of this plan, by name
@@ -193,7 +191,6 @@ std::string tc_kernel_name(int nc, int split, int fw, const TcConfig& c, const s
     snprintf(b, sizeof b, "fbc_tc_c%d_s%d_f%d_b%d_e%d_z%d_w%d", nc, split, fw, c.bt, c.ew, c.fuse, c.cw);
     std::string name = b;
     if (c.ts) name += "_t" + std::to_string(c.ts) + "s" + std::to_string(c.sb);
-    if (c.mc) name += "_m";
     return snippet.empty() ? name : name + "_u" + snippet_tag(snippet);
 }
 
@@ -205,12 +202,12 @@ std::string tc_kernel_source(int nc, int split, int fw, const TcConfig& c, const
       << snippet_definition(snippet);
     o << "static_assert(sizeof(FbcTcParams) == " << sizeof(FbcTcParams)
       << ", \"host and device disagree on the parameter block\");\n";
-    o << "extern \"C\" __global__ void " << (c.mc ? "__cluster_dims__(2, 1, 1) " : "") << "__launch_bounds__("
+    o << "extern \"C\" __global__ void __launch_bounds__("
       << tc_threads(c) << ", 1) "
       << tc_kernel_name(nc, split, fw, c, snippet) << "(const __grid_constant__ FbcTcParams P) {\n"
       << "  fbc_tc_corr_body<" << nc << "," << split << "," << fw << "," << c.bt << "," << c.ew << ","
-      << c.fuse << "," << c.cw << "," << (snippet.empty() ? 0 : 1) << "," << c.ts << "," << (c.ts ? c.sb : 1) << ","
-      << c.mc << ">(P);\n}\n";
+      << c.fuse << "," << c.cw << "," << (snippet.empty() ? 0 : 1) << "," << c.ts << "," << (c.ts ? c.sb : 1)
+      << ">(P);\n}\n";
     return o.str();
 }
 
@@ -280,9 +277,6 @@ bool tc_layout(TcPlan* p, const TcConfig& c, bool commit) {
     const uint32_t raw_slot = (uint32_t)align_up((size_t)(kTileM + p->fw - 1) * p->D * 4, 128);
     if (c.na < 2 || c.nb < 2 || (c.fuse == 2 && c.nr < 2)) return false;
     if (!ts_ok(c.ts, c.sb, p->W, p->N, nt)) return false;
-    // pairs: in-kernel conversion only (a phantom tile's slab rows are read with
-    // bounds checks), and at least one pair of tiles
-    if (c.mc != 0 && (c.mc != 1 || c.fuse == 0 || mtiles * ntn < 2)) return false;
     // staging: a 1024-byte aligned run of ew * sb boxes placed after the barriers
     const size_t staging = c.ts ? (size_t)c.ew * c.sb * FBC_TC_ST_BOX + 1024 : 0;
     const size_t need = (size_t)c.na * a_slot + (size_t)c.nb * b_stage + (size_t)c.nr * raw_slot + 512 + staging;
@@ -295,14 +289,13 @@ bool tc_layout(TcPlan* p, const TcConfig& c, bool commit) {
     k.npix = (long long)p->H * p->W;
     k.W = p->W; k.Ho = Ho; k.Wo = Wo; k.N = p->N; k.D = p->D;
     k.fh = p->fh; k.nt = nt; k.ntn = ntn; k.mtiles = mtiles;
-    k.mtiles_s = c.mc ? (mtiles + 1) / 2 * 2 : mtiles;
     // tail halves: when the last round of whole tiles would leave at least half
     // of the CTAs idle, its tiles run as two 128-column halves each
     const int grid_full = std::min(mtiles * ntn, std::max(1, p->sm_count));
     const int rem = (mtiles * ntn) % grid_full;
-    const bool tail_halves = !c.mc && ntn == 1 && nt == 256 && rem > 0 && 2 * rem <= grid_full &&
+    const bool tail_halves = ntn == 1 && nt == 256 && rem > 0 && 2 * rem <= grid_full &&
                              env_str("FBCORR_TAIL_HALVES", "1") != "0";
-    k.nfull = tail_halves ? mtiles * ntn - rem : k.mtiles_s * ntn;
+    k.nfull = tail_halves ? mtiles * ntn - rem : mtiles * ntn;
     k.lp = lp; k.na = c.na; k.nb = c.nb;
     k.a_slot = a_slot; k.b_stage = b_stage;
     k.a_tx = (uint32_t)(nc * (kTileM + p->fw - 1) * 16 * halves);
@@ -344,12 +337,8 @@ bool tc_layout(TcPlan* p, const TcConfig& c, bool commit) {
     const long long wblocks = ((long long)ntn * p->fh * p->fw * nt + 255) / 256;
     if (c.fuse) sp.xblocks = 0;   // x is converted inside the correlation kernel
     p->split_blocks = (int)(sp.xblocks + wblocks);
-    // one CTA per SM (the 512 TMEM columns); pairs: two CTAs per pair of tiles, as
-    // many pairs as can be resident at once (set from the occupancy query)
-    if (c.mc)
-        p->grid = 2 * std::min(k.mtiles_s * ntn / 2, std::max(1, p->pair_slots));
-    else
-        p->grid = std::min(mtiles * ntn, std::max(1, p->sm_count));
+    // one CTA per SM (the 512 TMEM columns)
+    p->grid = std::min(mtiles * ntn, std::max(1, p->sm_count));
     return true;
 }
 
@@ -368,8 +357,7 @@ std::vector<TcConfig> tc_candidate_configs(TcPlan* p) {
     // barrier handoffs) down, each with the deepest B ring that fits.  Every
     // configuration is also offered with the tiled-store (ts = 32) epilogue, and
     // with eight epilogue warps with the staged (ts = 1) one, again with the
-    // deepest ring beside their staging slots.  Pairs (mc = 1) are selectable by spec
-    // only: on the workloads measured they were never faster.
+    // deepest ring beside their staging slots.
     std::vector<TcConfig> out;
     auto deepest = [&](TcConfig c) -> int {
         int best = 0;
@@ -410,7 +398,6 @@ std::string format_spec(const TcConfig& c) {
              c.bt, c.ew, c.fuse, c.nr, c.cw);
     std::string out = b;
     if (c.ts) out += ",ts=" + std::to_string(c.ts) + ",sb=" + std::to_string(c.sb);
-    if (c.mc) out += ",mc=1";
     return out;
 }
 
@@ -420,16 +407,11 @@ bool parse_tc_spec(const std::string& s, TcConfig* c) {
     const int n = sscanf(s.c_str(), "tcgen05:na=%d,nb=%d,nt=%d,bt=%d,ew=%d,fz=%d,nr=%d,cw=%d%n", &t.na, &t.nb,
                          &t.ntmax, &t.bt, &t.ew, &t.fuse, &t.nr, &t.cw, &used);
     if (n != 8) return false;
-    // optional suffixes: staged / tiled stores, pairs
+    // optional suffix: staged / tiled stores
     int used2 = 0;
     if (sscanf(s.c_str() + used, ",ts=%d,sb=%d%n", &t.ts, &t.sb, &used2) == 2) {
         if ((t.ts != 32 && t.ts != 1) || t.sb < 1 || t.sb > 3 || (t.ts == 1 && t.sb != 1)) return false;
         used += used2;
-    }
-    used2 = 0;
-    if (s.compare(used, std::string::npos, ",mc=1") == 0) {
-        t.mc = 1;
-        used += 5;
     }
     if (used != (int)s.size()) return false;
     if ((t.fuse == 0) != (t.cw == 0) || (t.cw != 0 && t.cw != 4 && t.cw != 8)) return false;
@@ -487,16 +469,6 @@ fbcorr_status_t tc_set_spec(TcPlan* p, const std::string& spec) {
     Kernel k;
     FBC_TRY(tc_kernel(p, c, &k));
     tc_layout(p, c, true);
-    if (c.mc) {
-        // as many pairs as the device keeps resident at this shared-memory size
-        k.smem = p->smem;
-        int slots = 0;
-        FBC_TRY(cluster_occupancy(k, 2, &slots));
-        if (slots < 1)
-            return set_error(FBCORR_ERR_UNSUPPORTED, "tcgen05 spec '%s': no two-CTA cluster fits", spec.c_str());
-        p->pair_slots = slots;
-        tc_layout(p, c, true);
-    }
     return FBCORR_OK;
 }
 

@@ -35,7 +35,6 @@ struct FbcTcParams {
     unsigned long long wait_ns; // bound of every mbarrier wait
     int W, Ho, Wo, N, D;
     int fh, nt, ntn, mtiles;
-    int mtiles_s;               // pixel tiles per filter tile in the schedule (MC: mtiles rounded up to even)
     int nfull;                  // tiles run whole; tiles nfull.. run as two halves of the filter tile
     int lp;                     // pixels per chunk plane of an A slot
     int na, nb;                 // A slots, B stages

@@ -155,8 +155,8 @@ def test_direct_spec_parsing_is_strict(lib, spec, ok):
     (48, 7, b"tcgen05:na=2,nb=4,nt=256,bt=4,ew=8,fz=2,nr=2,cw=8"),    # six chunk planes, raw-row ring
     (64, 13, b"tcgen05:na=2,nb=2,nt=256,bt=1,ew=4,fz=0,nr=0,cw=0"),   # the deepest supported depth, pre-pass
     (32, 5, b"tcgen05:na=3,nb=2,nt=256,bt=5,ew=8,fz=1,nr=0,cw=8,ts=32,sb=1"),       # tiled bulk stores
-    (16, 3, b"tcgen05:na=3,nb=4,nt=256,bt=2,ew=8,fz=2,nr=2,cw=8,ts=1,sb=1,mc=1"),   # staged stores, tile pairs
-    (32, 5, b"tcgen05:na=2,nb=3,nt=256,bt=1,ew=4,fz=1,nr=0,cw=4,ts=32,sb=3,mc=1"),  # three staging slots, pairs
+    (16, 3, b"tcgen05:na=3,nb=4,nt=256,bt=2,ew=8,fz=2,nr=2,cw=8,ts=1,sb=1"),        # staged stores
+    (32, 5, b"tcgen05:na=2,nb=3,nt=256,bt=1,ew=4,fz=1,nr=0,cw=4,ts=32,sb=3"),       # three staging slots
 ])
 def test_tensor_core_kernels_compile(lib, D, f, spec):
     """The run-time generated tcgen05 kernel of a spec compiles for sm_103a in
@@ -177,8 +177,8 @@ def test_tensor_core_kernels_compile(lib, D, f, spec):
     (32, 5, b"tcgen05:na=2,nb=4,nt=256,bt=2,ew=8,fz=1,nr=0,cw=8,ts=2,sb=1", 1),    # store modes: 1 or 32
     (32, 5, b"tcgen05:na=2,nb=4,nt=256,bt=2,ew=8,fz=1,nr=0,cw=8,ts=32,sb=4", 1),   # at most three staging slots
     (32, 5, b"tcgen05:na=2,nb=4,nt=256,bt=2,ew=8,fz=1,nr=0,cw=8,ts=1,sb=2", 1),    # the staged path has one slot
-    (32, 5, b"tcgen05:na=2,nb=4,nt=256,bt=2,ew=8,fz=1,nr=0,cw=8,mc=2", 1),         # pairs: mc=1 only
-    (32, 5, b"tcgen05:na=2,nb=4,nt=256,bt=2,ew=8,fz=1,nr=0,cw=8,mc=1,ts=1,sb=1", 1),   # suffix order is fixed
+    (32, 5, b"tcgen05:na=2,nb=4,nt=256,bt=2,ew=8,fz=1,nr=0,cw=8,sb=1,ts=1", 1),    # suffix fields in order
+    (32, 5, b"tcgen05:na=2,nb=4,nt=256,bt=2,ew=8,fz=1,nr=0,cw=8,ts=1,sb=1,", 1),   # nothing after the suffix
 ])
 def test_tensor_core_spec_refusals(lib, D, f, spec, status):
     log = ctypes.create_string_buffer(1 << 16)

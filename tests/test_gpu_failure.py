@@ -31,16 +31,15 @@ class _env:
                 os.environ[k] = v
 
 
-@pytest.mark.parametrize("spec", [None, "tcgen05:na=2,nb=3,nt=256,bt=1,ew=8,fz=1,nr=0,cw=8,ts=1,sb=1,mc=1"],
-                         ids=["default", "cluster_pairs"])
+@pytest.mark.parametrize("spec", [None, "tcgen05:na=2,nb=3,nt=256,bt=1,ew=8,fz=1,nr=0,cw=8,ts=1,sb=1"],
+                         ids=["default", "staged_stores"])
 def test_dropped_copy_times_out_and_context_survives(spec):
     """FBCORR_FAULT=tcdrop makes the producer skip one copy that the MMA warp
     waits for -- an arrival that never comes.  Every wait is bounded (here
     50 ms): the kernel records FBCORR_ERR_TIMEOUT in host-mapped memory, drains
     its own copies and MMAs, frees TMEM and returns; the next plan on the same
-    context computes correct results.  With cluster pairs both CTAs of a pair
-    skip their half of the stage, time out, drain the multicast copies they
-    issued and meet at the closing cluster barrier."""
+    context computes correct results, with the default variant and with the
+    staged-store epilogue."""
     torch = torch_cuda()
     from paper_0911_3456_gb300.api import Plan
     wl = inputs.random_case(3000, 20, 150, 16, 32, 3, 3)
