@@ -616,7 +616,7 @@ def secondary(torch, args, world, peaks):
                                        "nonlinearities": nl, "flops": cas.flops, **casc}
     del xd, wds, outs
 
-    # exact nearest-neighbour search (Sec. 6.3): 4096 8x8 patches against the
+    # exact nearest-neighbour search (Sec. 6.4): 4096 8x8 patches against the
     # paper's neighbour counts; the paper's GTX 295 seconds are context only
     from paper_0911_3456_gb300.api import NNPlan
     paper_gtx295_s = {4096: 0.089, 16384: 0.299, 65536: 1.146, 262144: 4.508, 1048576: 17.989}

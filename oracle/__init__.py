@@ -11,7 +11,7 @@ H x W x D input correlated 'valid' against N filters of fh x fw x D,
     y[p, q, n] = sum_{i, j, d} x[p+i, q+j, d] * w[n, i, j, d],
 
 optionally clamped, plus the two gradients of <y, g>; and the exact
-nearest-neighbour search of the paper's second case study (Sec. 6.3): for every
+nearest-neighbour search of the paper's second case study (Sec. 6.4): for every
 target vector the index and squared Euclidean distance of its nearest neighbour
 (lowest index on ties) and the runner-up distance.  The arithmetic lives in
 ``fbcorr_oracle.c`` and ``nn_oracle.c`` as FP64 loops; this module only widens
@@ -190,7 +190,7 @@ def bwd_filt(x, g, filt_shape, y=None, epilogue=None) -> np.ndarray:
 
 
 def nn(targets, neighbors):
-    """Exact nearest neighbours (Sec. 6.3): for targets [nt, dim] and neighbors
+    """Exact nearest neighbours (Sec. 6.4): for targets [nt, dim] and neighbors
     [nn, dim], returns (idx [nt] int64, dist [nt], dist2 [nt]) -- the index of the
     nearest neighbour (lowest on ties), its squared Euclidean distance and the
     runner-up squared distance, all in FP64."""

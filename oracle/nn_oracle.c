@@ -6,7 +6,7 @@
  * calls it, and it shares no code with the GPU path.
  *
  * What it computes (the plain definition, written out as loops): the paper's
- * natural-scene-statistics case study (Sec. 6.3, Table "NN-speedup") finds, for
+ * natural-scene-statistics case study (Sec. 6.4, Table "NN-speedup") finds, for
  * every target patch (8x8 pixels, a 64-dimensional vector), its nearest
  * neighbour in Euclidean distance among a set of neighbour patches, by computing
  * the distance to every neighbour and taking the smallest (exact, exhaustive).

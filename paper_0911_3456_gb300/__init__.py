@@ -2,7 +2,7 @@
 vision case study of "PyCUDA and PyOpenCL: A Scripting-Based Approach to GPU
 Run-Time Code Generation" (Sec. 6.2), rebuilt around run-time-generated,
 auto-tuned CUDA kernels behind a C ABI (include/fbcorr.h); plus the exact
-nearest-neighbour search of its natural-scene case study (Sec. 6.3, NNPlan).
+nearest-neighbour search of its natural-scene case study (Sec. 6.4, NNPlan).
 
 Importing this package does not load the CUDA library; the first plan does.
 """

@@ -1,7 +1,7 @@
 // api.cu -- the C ABI of libfbcorr: plan creation, variant selection,
 // forward / backward dispatch and the auto-tuner.
 //
-// Control flow mirrors the paper's RTCG loop (Sec. 3.1, Sec. 6.2): a plan
+// Control flow mirrors the paper's RTCG loop (Fig. 1, Sec. 6.2): a plan
 // fixes the problem shape, code is generated and compiled for exactly that
 // shape (NVRTC, cached), candidates are timed when tuning is requested and the
 // winner is remembered per GPU and shape; the per-call path is then a single

@@ -1,4 +1,4 @@
-// nn.cu -- exact brute-force nearest-neighbour search (Sec. 6.3 of the paper):
+// nn.cu -- exact brute-force nearest-neighbour search (Sec. 6.4 of the paper):
 // plans, the split / norm pre-pass, the run-time generated tensor-core screening
 // kernel (rtcg_nn.cuh) and the exact re-ranking.
 //

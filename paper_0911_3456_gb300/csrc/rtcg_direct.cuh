@@ -3,7 +3,7 @@
 // This file is embedded as a string into libfbcorr and compiled with the
 // filter size, depth and tile of one plan baked in as template arguments --
 // the "hardcoding" specialisation that the paper obtains from run-time code
-// generation (Sec. 3.2, Sec. 6.2): fixed loop trip counts, fully unrolled
+// generation (Sec. 4.2, Sec. 6.2): fixed loop trip counts, fully unrolled
 // inner loops, register blocking chosen per shape by the auto-tuner.
 // It is self-contained: NVRTC compiles it without any system header.
 //

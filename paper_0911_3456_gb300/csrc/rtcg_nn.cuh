@@ -1,5 +1,5 @@
 // rtcg_nn.cuh -- exact brute-force nearest-neighbour search (the paper's second
-// case study, Sec. 6.3): the screening kernel, compiled at plan time by NVRTC
+// case study, Sec. 6.4): the screening kernel, compiled at plan time by NVRTC
 // with the chunk-plane count NC (dimension / 8), the split mode and the
 // epilogue warp count EW baked in.  Prefixed with nn_params.h and rtcg_ptx.cuh.
 //

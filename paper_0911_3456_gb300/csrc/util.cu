@@ -2,7 +2,7 @@
 // cache of libfbcorr.
 //
 // Errors follow the paper's requirement that failures surface as recoverable,
-// informative conditions rather than aborts (Sec. 4): every entry point returns
+// informative conditions rather than aborts (Sec. 5): every entry point returns
 // a status and leaves a thread-local message for fbcorr_last_error().
 // The tuning cache realises the paper's per-platform, per-input database of
 // optimisation configurations (Sec. 6.2): entries are keyed on the GPU name,

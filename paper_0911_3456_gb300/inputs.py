@@ -146,7 +146,7 @@ def workload_cascade(seed: int = 6):
     return x, banks
 
 
-# Exact nearest-neighbour search (Sec. 6.3): 8x8 patches, 4096 targets and
+# Exact nearest-neighbour search (Sec. 6.4): 8x8 patches, 4096 targets and
 # 4096 ... 1048576 neighbours (the paper's Table "NN-speedup").  The paper's
 # patches come from the van Hateren natural-image database, which is not here;
 # synthetic images with the 1/f amplitude spectrum of natural scenes stand in.

@@ -227,7 +227,7 @@ def pin_points(orc):
                           dxc[tuple(idx.T)])
 
 
-# --- exact nearest-neighbour search (Sec. 6.3) ---------------------------------
+# --- exact nearest-neighbour search (Sec. 6.4) ---------------------------------
 
 def pin_nn_golden_hand(orc):
     G = read_golden("nn_hand_case.txt")
