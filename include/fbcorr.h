@@ -27,7 +27,7 @@
  *    caller's workspace (size from the *_workspace_size queries).
  *  - Kernels are specialised per (fh, fw, D, tile) at plan time by run-time
  *    code generation (NVRTC, cached on disk) -- the paper's RTCG approach
- *    (Sec. 3, Sec. 6.2) -- with a prebuilt generic "default" kernel when
+ *    (Sec. 4, Sec. 6.2) -- with a prebuilt generic "default" kernel when
  *    code generation is unavailable.  There is no CPU fallback.
  */
 #ifndef FBCORR_H
@@ -104,7 +104,7 @@ fbcorr_status_t fbcorr_plan_destroy(fbcorr_plan_t plan);
 
 /* A plan whose epilogue is a user C expression compiled into the forward
  * kernels at plan time: the run-time generated element-wise operation of the
- * paper (Sec. 4, the ElementwiseKernel of Fig. 4) fused into the store of the
+ * paper (Sec. 5.2, the ElementwiseKernel of Fig. 4) fused into the store of the
  * correlation.  `expr` is an expression of float y (the FP32 accumulator of
  * one output), int n (its filter index) and float lo, hi (epilogue.lo / .hi),
  * evaluating to the float that is stored, e.g. "y > 0.f ? y : lo * y" or
@@ -187,7 +187,7 @@ fbcorr_status_t fbcorr_plan_info(fbcorr_plan_t plan, char* buf, size_t cap);
 fbcorr_status_t fbcorr_plan_device_status(fbcorr_plan_t plan, int clear);
 
 /* Timing service (the paper's auto-tuning relies on the runtime's timers,
- * Sec. 4): when capacity > 0, every later forward call of this plan records a
+ * Sec. 4.1 and 5): when capacity > 0, every later forward call of this plan records a
  * pair of CUDA events on its stream around its main kernel (the correlation
  * kernel itself, not the BF16 split pre-pass), for up to `capacity` calls.
  * capacity = 0 switches recording off. */
@@ -209,7 +209,9 @@ fbcorr_status_t fbcorr_plan_profile_read(fbcorr_plan_t plan, float* ms, int cap,
  * forward workspace (fbcorr_plan_workspace_size) exceeds 48 MiB are rejected
  * with FBCORR_ERR_WORKSPACE; FP32 plans need no scratch.  The first call on a
  * device looks up the array's device address, so make that first call before
- * any stream capture.  All calls on a device share the one array: calls whose
+ * any stream capture; the address is kept for the life of the process, so do
+ * not call this entry point after cudaDeviceReset.  The plan's device must be
+ * the current device (else FBCORR_ERR_INVALID_ARG).  All calls on a device share the one array: calls whose
  * GPU work may overlap (different streams, or different threads without
  * ordering) race on it; order them on one stream.  The array keeps the last
  * call's contents; every call rewrites all the scratch it reads first.
@@ -243,7 +245,7 @@ fbcorr_status_t fbcorr_forward_batched(fbcorr_batch_plan_t plan, const float* co
 
 /* ---- exact nearest-neighbour search -------------------------------------- */
 
-/* The paper's second case study (Sec. 6.3, Table "NN-speedup"): for each of
+/* The paper's second case study (Sec. 6.4, Table "NN-speedup"): for each of
  * n_targets vectors, its nearest neighbour in Euclidean distance among
  * n_neighbors vectors of the same dimension, by exhaustive comparison.
  * targets [n_targets][dim], neighbors [n_neighbors][dim]: FP32, row-major, DEVICE

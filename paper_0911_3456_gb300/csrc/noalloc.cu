@@ -13,7 +13,9 @@
 // The array's name is a host-side stand-in, not a device address, so host code
 // never passes it to a kernel.  Its device address is looked up once per device
 // with cudaGetSymbolAddress (with that device current) on the first call made
-// on that device, and cached.
+// on that device, and cached; the plan's device must be the current one.  The
+// cache is not refreshed after cudaDeviceReset, so the entry point must not be
+// used once the device has been reset in this process.
 #include <mutex>
 #include <vector>
 
@@ -31,9 +33,17 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 std::mutex g_scratch_mu;
 std::vector<void*> g_scratch_ptr;   // device address per device ordinal
 
-fbcorr_status_t scratch_address(void** out) {
+// The scratch address on `plan_dev`, which must be the current device: the
+// address belongs to the device current when it was looked up, and a kernel of
+// the plan given another device's address would touch that device's memory.
+fbcorr_status_t scratch_address(int plan_dev, void** out) {
     int dev = -1;
     FBC_CUDA(cudaGetDevice(&dev));
+    if (dev != plan_dev)
+        return set_error(FBCORR_ERR_INVALID_ARG,
+                         "the plan was created on device %d but device %d is current; make the plan's "
+                         "device current before calling fbcorr_forward_noalloc",
+                         plan_dev, dev);
     std::lock_guard<std::mutex> lk(g_scratch_mu);
     if ((int)g_scratch_ptr.size() <= dev) g_scratch_ptr.resize(dev + 1, nullptr);
     if (!g_scratch_ptr[dev]) {
@@ -64,6 +74,6 @@ extern "C" fbcorr_status_t fbcorr_forward_noalloc(fbcorr_plan_t plan, const floa
     // Nothing in the scratch needs clearing: the pre-pass writes every byte the
     // kernel reads (zero padding included) before the kernel runs.
     void* ws = nullptr;
-    FBC_TRY(scratch_address(&ws));
+    FBC_TRY(scratch_address(plan->dev.device, &ws));
     return fbcorr_forward(plan, x, w, y, ws, kNoAllocScratchBytes, stream);
 }
