@@ -202,11 +202,11 @@ fbcorr_status_t select_variants(fbcorr_batch_plan* b, bool allow_tuning) {
             }
         }
         if (!have && tune_lookup(key, &spec) && parse_direct_spec(spec, &t) &&
-            t.threads() == kBatchThreads && t.tr * t.tf <= kBatchMaxBlock &&
+            t.threads() == kBatchThreads && t.ks == 1 && t.tr * t.tf <= kBatchMaxBlock &&
             direct_smem_bytes(t, bv.fh, bv.fw, bv.d) <= kBatchSmemLimit)
             have = true;
         if (!have) t = direct_heuristic(rep, kBatchSmemLimit, b->dev.sm_count, kBatchThreads, kBatchMaxBlock);
-        if (t.threads() != kBatchThreads || direct_smem_bytes(t, bv.fh, bv.fw, bv.d) > kBatchSmemLimit)
+        if (t.threads() != kBatchThreads || t.ks != 1 || direct_smem_bytes(t, bv.fh, bv.fw, bv.d) > kBatchSmemLimit)
             return set_error(FBCORR_ERR_UNSUPPORTED, "no batched tile fits filter %dx%d at depth %d", bv.fh,
                              bv.fw, bv.d);
         bv.tile = t;

@@ -98,10 +98,17 @@ struct DirectTile {
     int tr = 8, tf = 8, wr = 1, wf = 2;
     int cc = 0;   // input channels staged per chunk; 0 = the whole depth
     int pk = 0;   // 1: multiply-adds issued as packed pairs (fma.rn.f32x2), same bits
-    int chunk(int c) const { return (cc > 0 && cc < c) ? cc : c; }
+    // K split (forward only): ks > 1 lanes share each output and split the depth,
+    // combined by warp shuffles; a warp then covers 32 / ks columns and the CTA
+    // wq warps side by side; sh = 1 takes the depth share from the high lane
+    // bits (the lanes of a quarter warp then read the same filter values).
+    // ks = 1: one column per lane (wq = 1, sh = 0).
+    int ks = 1, wq = 1, sh = 0;
+    int chunk(int c) const { return ks > 1 ? c : ((cc > 0 && cc < c) ? cc : c); }
     int bh() const { return tr * wr; }
     int bn() const { return tf * wf; }
-    int threads() const { return 32 * wr * wf; }
+    int bw() const { return (32 / ks) * wq; }
+    int threads() const { return 32 * wr * wf * wq; }
 };
 size_t direct_smem_bytes(const DirectTile& t, int fh, int fw, int c);
 std::string direct_tile_spec(const DirectTile& t);

@@ -273,6 +273,304 @@ struct FbcDirect {
     }
 };
 
+// ---- K-split forward tile for small fh*fw*D --------------------------------
+// When the reduction K = FH*FW*C is short (e.g. 9x9x8 = 648) and the output is
+// small, one output column per lane leaves most of the GPU idle: 120x120x16
+// outputs in 8-output register blocks are under 30 k threads for a machine of
+// 311 k.  Here the KS lanes of a lane group share the same outputs and split
+// the depth: lane (qs, s) of a warp -- qs = lane / KS, s = lane % KS -- owns
+// output column qs of the warp's LQ = 32 / KS columns and accumulates the
+// channels c = s, s + KS, ... (channels C..CPAD-1 are zero padding) over all
+// FH x FW taps of its TR x TF register block.  The KS partial blocks are then
+// combined by a reduce-scatter over the lane bits of s with __shfl_xor_sync:
+// at every step a lane keeps one half of its values, receives the partner's
+// copy of that half and adds it, so after log2(KS) steps lane s holds the
+// complete sums of its share (block entries s*n/KS .. (s+1)*n/KS - 1 of the
+// n = TR*TF entries, row-major over (row, filter)).  The summation tree is
+// fixed, so the results are deterministic run to run.
+// Shared memory keeps the natural layout of x: the halo as [row][column][CP]
+// with the pixel pitch CP = CPAD rounded up to KS modulo 32, so that the 32
+// lanes of a warp (LQ columns x KS channels) read 32 distinct banks; the bank
+// slice as [i][j][c][BNP], one float4 per 4 filters, whose KS distinct channel
+// rows fall into distinct bank quads (BNP / 4 odd).  Staging issues all of a
+// thread's 16-byte loads of a batch before storing any, so the halo and the
+// bank stream in with many loads in flight.
+// SHI = 1 takes s from the high lane bits instead (qs = lane % LQ, s = lane / LQ),
+// so that the lanes of a quarter warp read the same filter values; the tuner
+// measures both.  Forward only (no flip, no mask).  PK = 1 issues packed-pair FMAs.
+template <int FH, int FW, int C, int TR, int TF, int KS, int WQ, int WR, int WF, int EPI, int PK = 0,
+          int SHI = 0>
+struct FbcDirectKS {
+    static constexpr int LQ = 32 / KS;
+    static constexpr int BW = LQ * WQ;
+    static constexpr int BH = TR * WR;
+    static constexpr int BN = TF * WF;
+    static constexpr int NT = 32 * WQ * WR * WF;
+    static constexpr int HR = BH + FH - 1;
+    static constexpr int HC = BW + FW - 1;
+    static constexpr int CPAD = (C + KS - 1) / KS * KS;
+    static constexpr int CPL = CPAD / KS;                          // channels per lane
+    static constexpr int CP = CPAD + (((KS - CPAD) % 32) + 32) % 32;   // CP = KS (mod 32)
+    static constexpr int BNP = ((BN / 4) % 2 == 1) ? BN : BN + 4;
+    static constexpr int XS = HR * HC * CP;
+    static constexpr int WS = FH * FW * CPAD * BNP;
+    static constexpr int SMEM_BYTES = (XS + WS) * 4;
+    static constexpr int NPAIR = TR * TF / 2;                      // accumulator pairs per lane
+    static constexpr int NOWN = NPAIR / KS;                        // pairs each lane ends with
+    static constexpr int BATCH = 8;                                // 16-byte loads in flight per thread
+    static_assert(KS == 4 || KS == 8 || KS == 16 || KS == 32, "KS must be 4, 8, 16 or 32");
+    static_assert(TF % 4 == 0, "TF must be a multiple of 4");
+    static_assert(NPAIR % KS == 0, "TR*TF/2 must be a multiple of KS");
+
+    static __device__ __forceinline__ void stage(const FbcDirectArgs& a, float* xs, float* ws, int p0,
+                                                 int q0, int f0) {
+        const int tid = threadIdx.x;
+        // ---- input halo [HR][HC][CP]; channels C..CPAD-1 zero
+        if constexpr (C % 4 == 0) {
+            constexpr int C4 = C / 4;
+            constexpr int NV = HR * HC * C4;
+#pragma unroll 1
+            for (int b0 = 0; b0 < NV; b0 += NT * BATCH) {
+                float4 v[BATCH];
+#pragma unroll
+                for (int k = 0; k < BATCH; ++k) {
+                    const int e = b0 + tid + k * NT;
+                    v[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (e < NV) {
+                        const int c4 = e % C4;
+                        const int t = e / C4;
+                        const int col = t % HC;
+                        const int row = t / HC;
+                        const int gy = p0 + row, gx = q0 + col;
+                        if (gy < a.in_h && gx < a.in_w)
+                            v[k] = __ldg(reinterpret_cast<const float4*>(a.x + ((long long)gy * a.in_w + gx) * C) + c4);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < BATCH; ++k) {
+                    const int e = b0 + tid + k * NT;
+                    if (e < NV) {
+                        const int c4 = e % C4;
+                        const int t = e / C4;
+                        reinterpret_cast<float4*>(xs + t * CP)[c4] = v[k];
+                    }
+                }
+            }
+        } else {
+            constexpr int NV = HR * HC * C;
+#pragma unroll 1
+            for (int b0 = 0; b0 < NV; b0 += NT * BATCH) {
+                float v[BATCH];
+#pragma unroll
+                for (int k = 0; k < BATCH; ++k) {
+                    const int e = b0 + tid + k * NT;
+                    v[k] = 0.f;
+                    if (e < NV) {
+                        const int c = e % C;
+                        const int t = e / C;
+                        const int col = t % HC;
+                        const int row = t / HC;
+                        const int gy = p0 + row, gx = q0 + col;
+                        if (gy < a.in_h && gx < a.in_w) v[k] = __ldg(a.x + ((long long)gy * a.in_w + gx) * C + c);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < BATCH; ++k) {
+                    const int e = b0 + tid + k * NT;
+                    if (e < NV) xs[(e / C) * CP + e % C] = v[k];
+                }
+            }
+        }
+        if constexpr (CPAD > C) {
+            for (int e = tid; e < HR * HC * (CPAD - C); e += NT) {
+                const int t = e / (CPAD - C);
+                xs[t * CP + C + e % (CPAD - C)] = 0.f;
+            }
+        }
+        // ---- bank slice [FH][FW][CPAD][BNP]: w[f0 + f][i][j][c], zero for c >= C or f0 + f >= nf.
+        // Filters fastest across the threads: a warp's scalar stores of one
+        // component cover BN consecutive words per 4-channel group
+        if constexpr (C % 4 == 0) {
+            constexpr int C4 = C / 4;
+            constexpr int NV = BN * FH * FW * C4;
+#pragma unroll 1
+            for (int b0 = 0; b0 < NV; b0 += NT * BATCH) {
+                float4 v[BATCH];
+#pragma unroll
+                for (int k = 0; k < BATCH; ++k) {
+                    const int e = b0 + tid + k * NT;
+                    v[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (e < NV) {
+                        const int f = e % BN;
+                        const int r = e / BN;   // (i*FW + j)*C4 + c4
+                        if (f0 + f < a.nf)
+                            v[k] = __ldg(reinterpret_cast<const float4*>(a.w + (long long)(f0 + f) * (FH * FW * C)) + r);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < BATCH; ++k) {
+                    const int e = b0 + tid + k * NT;
+                    if (e < NV) {
+                        const int f = e % BN;
+                        const int r = e / BN;
+                        const int tap = r / C4;
+                        const int c = (r - tap * C4) * 4;
+                        float* dst = ws + (tap * CPAD + c) * BNP + f;
+                        dst[0] = v[k].x;
+                        dst[BNP] = v[k].y;
+                        dst[2 * BNP] = v[k].z;
+                        dst[3 * BNP] = v[k].w;
+                    }
+                }
+            }
+        } else {
+            for (int e = tid; e < BN * FH * FW * C; e += NT) {
+                const int f = e % BN;
+                const int r = e / BN;   // (i*FW + j)*C + c
+                const int tap = r / C;
+                const int c = r - tap * C;
+                ws[(tap * CPAD + c) * BNP + f] = (f0 + f < a.nf) ? __ldg(a.w + (long long)(f0 + f) * (FH * FW * C) + r) : 0.f;
+            }
+        }
+        if constexpr (CPAD > C) {
+            for (int e = tid; e < FH * FW * (CPAD - C) * BN; e += NT) {
+                const int f = e % BN;
+                const int t = e / BN;
+                const int tap = t / (CPAD - C);
+                const int c = C + t % (CPAD - C);
+                ws[(tap * CPAD + c) * BNP + f] = 0.f;
+            }
+        }
+    }
+
+    static __device__ __forceinline__ void run(const FbcDirectArgs& a, float* smem, int tile_x, int tile_y,
+                                               int tile_f) {
+        const int tid = threadIdx.x;
+        const int lane = tid & 31;
+        const int warp = tid >> 5;
+        const int s = SHI ? lane / LQ : lane % KS;
+        const int qs = SHI ? lane % LQ : lane / KS;
+        const int wq = warp % WQ;
+        const int wr = (warp / WQ) % WR;
+        const int wf = warp / (WQ * WR);
+        const int q0 = tile_x * BW;
+        const int p0 = tile_y * BH;
+        const int f0 = tile_f * BN;
+        float* xs = smem;
+        float* ws = smem + XS;
+
+        float2 acc[TR][TF / 2];   // filters (2k, 2k+1) of row r
+#pragma unroll
+        for (int r = 0; r < TR; ++r)
+#pragma unroll
+            for (int f = 0; f < TF / 2; ++f) acc[r][f] = make_float2(0.f, 0.f);
+
+        stage(a, xs, ws, p0, q0, f0);
+        __syncthreads();
+
+        const float* xb = xs + ((wr * TR) * HC + wq * LQ + qs) * CP + s;
+        const float* wb = ws + s * BNP + wf * TF;
+#pragma unroll
+        for (int t = 0; t < CPL; ++t) {
+#pragma unroll 1
+            for (int j = 0; j < FW; ++j) {
+                float xv[TR + FH - 1];
+#pragma unroll
+                for (int k = 0; k < TR + FH - 1; ++k) xv[k] = xb[(k * HC + j) * CP + KS * t];
+#pragma unroll
+                for (int i = 0; i < FH; ++i) {
+                    const float4* wp = reinterpret_cast<const float4*>(wb + ((i * FW + j) * CPAD + KS * t) * BNP);
+                    float2 wv[TF / 2];
+#pragma unroll
+                    for (int f4 = 0; f4 < TF / 4; ++f4) {
+                        const float4 t4 = wp[f4];
+                        wv[2 * f4 + 0] = make_float2(t4.x, t4.y);
+                        wv[2 * f4 + 1] = make_float2(t4.z, t4.w);
+                    }
+#pragma unroll
+                    for (int r = 0; r < TR; ++r) {
+                        if constexpr (PK) {
+                            const float2 xx = make_float2(xv[r + i], xv[r + i]);
+#pragma unroll
+                            for (int f = 0; f < TF / 2; ++f) acc[r][f] = __ffma2_rn(xx, wv[f], acc[r][f]);
+                        } else {
+#pragma unroll
+                            for (int f = 0; f < TF / 2; ++f) {
+                                acc[r][f].x = fmaf(xv[r + i], wv[f].x, acc[r][f].x);
+                                acc[r][f].y = fmaf(xv[r + i], wv[f].y, acc[r][f].y);
+                            }
+                        }
+                    }
+                }
+            }
+        }
+
+        // ---- reduce-scatter over the KS lanes of the group (fixed tree)
+        float2 v[NPAIR];
+#pragma unroll
+        for (int r = 0; r < TR; ++r)
+#pragma unroll
+            for (int f = 0; f < TF / 2; ++f) v[r * (TF / 2) + f] = acc[r][f];
+        reduce_step<KS / 2, NPAIR>(v, s);
+
+        // ---- epilogue: lane s owns pairs s*NOWN .. s*NOWN + NOWN - 1 of its group's block
+        const int q = q0 + wq * LQ + qs;
+        if (q >= a.out_w) return;
+        constexpr int VW = (NOWN % 2 == 0 && (TF / 2) % 2 == 0) ? 2 : 1;   // pairs per store
+#pragma unroll
+        for (int k = 0; k < NOWN; k += VW) {
+            const int o = s * NOWN + k;
+            const int r = o / (TF / 2);
+            const int n = f0 + wf * TF + 2 * (o % (TF / 2));
+            const int p = p0 + wr * TR + r;
+            if (p >= a.out_h) continue;
+            float e[2 * VW];
+#pragma unroll
+            for (int u = 0; u < VW; ++u) {
+                e[2 * u] = v[k + u].x;
+                e[2 * u + 1] = v[k + u].y;
+            }
+#pragma unroll
+            for (int u = 0; u < 2 * VW; ++u) {
+                if constexpr (EPI == 2) e[u] = fbc_user_epi(e[u], n + u, a.lo, a.hi);
+                if (EPI == 1) e[u] = fminf(fmaxf(e[u], a.lo), a.hi);
+            }
+            float* yp = a.y + ((long long)p * a.out_w + q) * a.nf + n;
+            if (VW == 2 && (a.nf & 3) == 0 && n + 4 <= a.nf) {
+                *reinterpret_cast<float4*>(yp) = make_float4(e[0], e[1], e[2 % (2 * VW)], e[3 % (2 * VW)]);
+            } else if (VW == 1 && (a.nf & 1) == 0 && n + 2 <= a.nf) {
+                *reinterpret_cast<float2*>(yp) = make_float2(e[0], e[1]);
+            } else {
+#pragma unroll
+                for (int u = 0; u < 2 * VW; ++u)
+                    if (n + u < a.nf) yp[u] = e[u];
+            }
+        }
+    }
+
+    // One step of the reduce-scatter over bit M of s, LEN pairs: the lane whose
+    // bit M is set keeps the upper half, its partner the lower; each adds the
+    // partner's copy of the half it keeps.  Then the next bit, on half as many
+    // pairs.  The partner differs in lane bit M (s in the low lane bits) or
+    // M * LQ (s in the high bits).
+    template <int M, int LEN>
+    static __device__ __forceinline__ void reduce_step(float2 (&v)[NPAIR], int s) {
+        if constexpr (M >= 1) {
+            constexpr int LM = SHI ? M * LQ : M;
+            const bool hi = (s & M) != 0;
+#pragma unroll
+            for (int k = 0; k < LEN / 2; ++k) {
+                const float2 send = hi ? v[k] : v[k + LEN / 2];
+                const float2 mine = hi ? v[k + LEN / 2] : v[k];
+                const float gx = __shfl_xor_sync(0xffffffffu, send.x, LM);
+                const float gy = __shfl_xor_sync(0xffffffffu, send.y, LM);
+                v[k] = make_float2(mine.x + gx, mine.y + gy);
+            }
+            reduce_step<M / 2, LEN / 2>(v, s);
+        }
+    }
+};
+
 // ---- dL/dw partial sums -----------------------------------------------------
 // Grid: x = chunk of output rows, y = filter row i, z = block of NBLK = TN*NG
 // filters.  Thread (ng, c) = (tid / C, tid % C) accumulates

@@ -26,6 +26,15 @@ const char* rtcg_nn_params_source() { return kRtcgNnParamsSrc; }
 const char* rtcg_nn_source() { return kRtcgNnSrc; }
 
 size_t direct_smem_bytes(const DirectTile& t, int fh, int fw, int c) {
+    if (t.ks > 1) {
+        // FbcDirectKS: halo [HR][HC][CP] + bank [fh][fw][CPAD][BNP]
+        const long cpad = (c + t.ks - 1) / t.ks * t.ks;
+        const long cp = cpad + (((t.ks - cpad) % 32) + 32) % 32;
+        const long bn = t.bn();
+        const long bnp = ((bn / 4) % 2 == 1) ? bn : bn + 4;
+        const long hr = t.bh() + fh - 1, hc = t.bw() + fw - 1;
+        return (size_t)(hr * hc * cp + (long)fh * fw * cpad * bnp) * 4;
+    }
     const long cc = t.chunk(c);
     const long bh = t.tr * t.wr, bn = t.tf * t.wf;
     const long hr = bh + fh - 1, hc = 32 + fw - 1;
@@ -37,15 +46,27 @@ size_t direct_smem_bytes(const DirectTile& t, int fh, int fw, int c) {
 }
 
 std::string direct_tile_spec(const DirectTile& t) {
-    char b[112];
+    char b[128];
     snprintf(b, sizeof b, "direct:tr=%d,tf=%d,wr=%d,wf=%d,cc=%d%s", t.tr, t.tf, t.wr, t.wf, t.cc,
              t.pk ? ",pk=1" : "");
-    return b;
+    std::string out = b;
+    if (t.ks > 1) out += ",ks=" + std::to_string(t.ks) + ",wq=" + std::to_string(t.wq);
+    if (t.sh) out += ",sh=1";
+    return out;
+}
+
+static bool ks_tile_ok(const DirectTile& t) {
+    if (t.ks == 1) return t.wq == 1 && t.sh == 0;
+    if (t.sh != 0 && t.sh != 1) return false;
+    if (t.ks != 4 && t.ks != 8 && t.ks != 16 && t.ks != 32) return false;
+    // whole depth in one stage; the register block splits evenly over the ks lanes
+    return t.cc == 0 && t.wq >= 1 && t.wq <= 32 && (t.tr * t.tf / 2) % t.ks == 0;
 }
 
 bool parse_direct_spec(const std::string& s, DirectTile* t) {
-    // "direct:tr=R,tf=F,wr=WR,wf=WF" then optionally ",cc=CC" and ",pk=P", in
-    // that order; anything else left over rejects the spec
+    // "direct:tr=R,tf=F,wr=WR,wf=WF" then optionally ",cc=CC", ",pk=P",
+    // ",ks=K,wq=Q" and ",sh=S", in that order; anything else left over rejects
+    // the spec
     DirectTile d;
     d.cc = 0;
     d.pk = 0;
@@ -64,7 +85,18 @@ bool parse_direct_spec(const std::string& s, DirectTile* t) {
         if (sscanf(rest, ",pk=%d%n", &d.pk, &u) != 1 || u < 0) return false;
         rest += u;
     }
+    u = -1;
+    if (strncmp(rest, ",ks=", 4) == 0) {
+        if (sscanf(rest, ",ks=%d,wq=%d%n", &d.ks, &d.wq, &u) != 2 || u < 0) return false;
+        rest += u;
+    }
+    u = -1;
+    if (strncmp(rest, ",sh=", 4) == 0) {
+        if (sscanf(rest, ",sh=%d%n", &d.sh, &u) != 1 || u < 0) return false;
+        rest += u;
+    }
     if (*rest != '\0') return false;
+    if (!ks_tile_ok(d)) return false;
     if (d.tr < 1 || d.tr > 16 || (d.tf != 4 && d.tf != 8 && d.tf != 12 && d.tf != 16) ||
         d.wr < 1 || d.wf < 1 || d.threads() > 1024 || d.cc < 0 || d.cc > 4096 || d.pk < 0 || d.pk > 1)
         return false;
@@ -94,9 +126,16 @@ std::string direct_kernel_source(const DirectProblem& pr, const DirectTile& t,
     std::ostringstream o;
     o << rtcg_header_source() << "\n";
     if (pr.epi == 2) o << snippet_definition(pr.snippet);
-    o << "typedef FbcDirect<" << pr.fh << "," << pr.fw << "," << pr.c << "," << t.tr << ","
-      << t.tf << "," << t.wr << "," << t.wf << "," << pr.flip << "," << pr.epi << "," << pr.mask
-      << "," << t.chunk(pr.c) << "," << t.pk << "> FbcThis;\n";
+    if (t.ks > 1) {
+        // the K-split tile (forward only: callers check flip == 0 and mask == 0)
+        o << "typedef FbcDirectKS<" << pr.fh << "," << pr.fw << "," << pr.c << "," << t.tr << "," << t.tf << ","
+          << t.ks << "," << t.wq << "," << t.wr << "," << t.wf << "," << pr.epi << "," << t.pk << "," << t.sh
+          << "> FbcThis;\n";
+    } else {
+        o << "typedef FbcDirect<" << pr.fh << "," << pr.fw << "," << pr.c << "," << t.tr << ","
+          << t.tf << "," << t.wr << "," << t.wf << "," << pr.flip << "," << pr.epi << "," << pr.mask
+          << "," << t.chunk(pr.c) << "," << t.pk << "> FbcThis;\n";
+    }
     o << "static_assert(FbcThis::SMEM_BYTES == " << direct_smem_bytes(t, pr.fh, pr.fw, pr.c)
       << ", \"host and device disagree on the shared-memory size\");\n";
     o << "extern \"C\" __global__ void __launch_bounds__(" << t.threads() << ") " << kname
@@ -159,6 +198,33 @@ std::vector<DirectTile> direct_candidates(const DirectProblem& pr, size_t smem_l
                         if (direct_smem_bytes(t, pr.fh, pr.fw, pr.c) > smem_limit) continue;
                         out.push_back(t);
                     }
+    // K-split tiles (forward only, not in the batched kernel's fixed CTA size):
+    // ks lanes per output split the depth, at most a quarter of them on zero
+    // padding channels and at most 8 channels per lane (deeper inputs keep the
+    // lane-per-column tile busy enough)
+    if (threads > 0 || pr.flip || pr.mask) return out;
+    for (int ks : {4, 8, 16, 32}) {
+        const int cpad = (pr.c + ks - 1) / ks * ks;
+        if (4 * (cpad - pr.c) > cpad || cpad / ks > 8) continue;
+        for (int tr : {2, 4, 8, 16})
+            for (int tf : {4, 8, 16})
+                for (int wq : {1, 2, 4, 8})
+                    for (int wr : {1, 2, 4, 8})
+                        for (int wf : {1, 2, 4})
+                            for (int sh : {0, 1}) {
+                                DirectTile t{tr, tf, wr, wf, 0};
+                                t.ks = ks;
+                                t.wq = wq;
+                                t.sh = sh;
+                                if ((tr * tf / 2) % ks != 0 || t.threads() > 512 || t.threads() < 64) continue;
+                                if (tf > nf4 || (t.bn() > nf4 && wf > 1)) continue;
+                                if (tr * tf > max_block || tr + pr.fh - 1 > 40) continue;
+                                if (t.bw() > ((pr.out_w + 7) / 8) * 8 + 8 && wq > 1) continue;
+                                if (t.bh() > ((pr.out_h + 1) / 2) * 2 + 8 && wr > 1) continue;
+                                if (direct_smem_bytes(t, pr.fh, pr.fw, pr.c) > smem_limit) continue;
+                                out.push_back(t);
+                            }
+    }
     return out;
 }
 
@@ -168,6 +234,43 @@ std::vector<DirectTile> direct_candidates(const DirectProblem& pr, size_t smem_l
 // orders the candidates the tuner measures first.
 static double direct_score(const DirectProblem& pr, const DirectTile& t, int sm_count) {
     const size_t smem_per_sm = 228 * 1024;
+    if (t.ks > 1) {
+        // K-split tile: the same factors, with the depth split over ks lanes (a
+        // share of them on zero padding), vectorised staging, and the shuffle
+        // reduction of the register block at the end
+        const int gx = ceil_div(pr.out_w, t.bw()), gy = ceil_div(pr.out_h, t.bh()), gz = ceil_div(pr.nf, t.bn());
+        const double useful = (double)pr.out_w * pr.out_h * pr.nf;
+        const double computed = (double)gx * t.bw() * gy * t.bh() * gz * t.bn();
+        const int cpad = (pr.c + t.ks - 1) / t.ks * t.ks;
+        const double e_tile = useful / computed * pr.c / cpad;
+        const size_t smem = direct_smem_bytes(t, pr.fh, pr.fw, pr.c) + 1024;
+        const int regs = t.tr * t.tf + t.tr + pr.fh + t.tf + 32;
+        int res = (int)(smem_per_sm / smem);
+        res = std::min(res, 2048 / t.threads());
+        res = std::min(res, 65536 / (t.threads() * std::min(255, regs)));
+        if (res < 1) return -1.0;
+        const long ctas = (long)gx * gy * gz;
+        const long slots = (long)res * sm_count;
+        const long waves = (ctas + slots - 1) / slots;
+        const double wave_eff = (double)ctas / (double)(waves * slots);
+        // inner loop per warp and (tap column, channel step), in SM cycles: the
+        // FMA pipe (128 lanes), the shared-memory pipe (one wavefront per cycle:
+        // one per input load, four per float4 filter load, whose lanes read
+        // ks different channels) and instruction issue (4 per cycle)
+        const int cpl = cpad / t.ks;
+        const double fma_cyc = t.tr * t.tf * pr.fh / 4.0;
+        const double lsu_cyc = (t.tr + pr.fh - 1) + pr.fh * t.tf;
+        const double iss_cyc = (t.tr * t.tf * pr.fh / 2.0 + (t.tr + pr.fh - 1) + pr.fh * t.tf / 4.0) / 4.0;
+        const double e_inner = fma_cyc / std::max(fma_cyc, std::max(lsu_cyc, iss_cyc));
+        const double fma_total = (double)t.tr * t.tf * pr.fh * pr.fw * cpl;
+        const double staged = ((double)(t.bh() + pr.fh - 1) * (t.bw() + pr.fw - 1) * pr.c +
+                               (double)pr.fh * pr.fw * pr.c * t.bn()) / t.threads();
+        const double reduce = 4.0 * t.tr * t.tf / 2.0;
+        const double e_issue = e_inner * fma_total / (fma_total + 2.5 * staged + reduce + 400.0);
+        const int warps = std::min<long>(res, (ctas + sm_count - 1) / sm_count) * t.threads() / 32;
+        const double occ = std::min(1.0, warps / 12.0);
+        return e_tile * wave_eff * e_issue * (0.5 + 0.5 * occ);
+    }
     const int gx = ceil_div(pr.out_w, 32), gy = ceil_div(pr.out_h, t.bh()), gz = ceil_div(pr.nf, t.bn());
     const double useful = (double)pr.out_w * pr.out_h * pr.nf;
     const double computed = (double)gx * 32 * gy * t.bh() * gz * t.bn();
@@ -214,9 +317,12 @@ std::vector<DirectTile> direct_ranked(const DirectProblem& pr, size_t smem_limit
 std::vector<std::string> direct_tuning_specs(const std::vector<DirectTile>& ranked, int topk) {
     const bool twins = env_str("FBCORR_TUNE_PK", "1") != "0";
     std::vector<std::string> specs;
-    int tiles = 0;
+    // the first topk lane-per-column tiles and, beside them, the first topk / 2
+    // K-split tiles (their model scores are not comparable enough to let one
+    // family crowd out the other)
+    int tiles = 0, ks_tiles = 0;
     for (const auto& t : ranked) {
-        if (tiles++ >= topk) break;
+        if (t.ks > 1 ? ks_tiles++ >= topk / 2 : tiles++ >= topk) continue;
         DirectTile a = t;
         a.pk = 0;
         specs.push_back(direct_tile_spec(a));
@@ -258,7 +364,9 @@ std::string kname_for(const char* base, const DirectProblem& pr, const DirectTil
     char b[160];
     snprintf(b, sizeof b, "%s_f%dx%d_c%d_t%d_%d_%d_%d_cc%d_fl%d_e%d_m%d%s", base, pr.fh, pr.fw, pr.c,
              t.tr, t.tf, t.wr, t.wf, t.chunk(pr.c), pr.flip, pr.epi, pr.mask, t.pk ? "_pk1" : "");
-    return pr.epi == 2 ? std::string(b) + "_u" + snippet_tag(pr.snippet) : std::string(b);
+    std::string name = b;
+    if (t.ks > 1) name += "_ks" + std::to_string(t.ks) + "q" + std::to_string(t.wq) + (t.sh ? "h" : "");
+    return pr.epi == 2 ? name + "_u" + snippet_tag(pr.snippet) : name;
 }
 
 size_t smem_limit(const DeviceInfo& dev) {
@@ -266,13 +374,15 @@ size_t smem_limit(const DeviceInfo& dev) {
 }
 
 fbcorr_status_t build_direct(const DirectProblem& pr, const DirectTile& t, Kernel* k) {
+    if (t.ks > 1 && (pr.flip || pr.mask))
+        return set_error(FBCORR_ERR_UNSUPPORTED, "K-split tiles compute the forward correlation only");
     const std::string name = kname_for("fbc_direct", pr, t);
     const std::string src = direct_kernel_source(pr, t, name);
     return rtcg_kernel(src, name, direct_smem_bytes(t, pr.fh, pr.fw, pr.c), t.threads(), k);
 }
 
 dim3 direct_grid(const DirectProblem& pr, const DirectTile& t) {
-    return dim3((unsigned)((pr.out_w + 31) / 32), (unsigned)((pr.out_h + t.bh() - 1) / t.bh()),
+    return dim3((unsigned)((pr.out_w + t.bw() - 1) / t.bw()), (unsigned)((pr.out_h + t.bh() - 1) / t.bh()),
                 (unsigned)((pr.nf + t.bn() - 1) / t.bn()));
 }
 

@@ -141,11 +141,38 @@ def test_explicit_tile_specs_compile(lib, spec):
     (b"direct:tr=8,tf=8,wr=1,wf=2,pk=1,cc=4", False),    # fields out of order
     (b"direct:tr=8,tf=8,wr=1,wf=2 ", False),
     (b"direct:tr=8,tf=6,wr=1,wf=2", False),              # TF not a multiple of 4
+    (b"direct:tr=4,tf=8,wr=2,wf=1,cc=0,pk=1,ks=8,wq=4", True),    # K-split tile
+    (b"direct:tr=4,tf=8,wr=2,wf=1,ks=8,wq=4", True),
+    (b"direct:tr=4,tf=8,wr=2,wf=1,cc=0,ks=8", False),             # ks needs wq
+    (b"direct:tr=4,tf=8,wr=2,wf=1,cc=0,ks=6,wq=4", False),        # ks: 4, 8, 16 or 32
+    (b"direct:tr=2,tf=4,wr=2,wf=1,cc=0,ks=8,wq=4", False),        # 4 pairs do not split over 8 lanes
+    (b"direct:tr=4,tf=8,wr=2,wf=1,cc=4,ks=8,wq=4", False),        # K split stages the whole depth
+    (b"direct:tr=4,tf=8,wr=2,wf=1,cc=0,ks=8,wq=4,pk=1", False),   # fields out of order
+    (b"direct:tr=4,tf=8,wr=2,wf=1,cc=0,ks=1,wq=2", False),        # no split: one warp per 32 columns
+    (b"direct:tr=16,tf=4,wr=1,wf=4,cc=0,pk=1,ks=8,wq=2,sh=1", True),   # share in the high lane bits
+    (b"direct:tr=4,tf=8,wr=2,wf=1,cc=0,ks=8,wq=4,sh=2", False),
+    (b"direct:tr=4,tf=8,wr=2,wf=1,cc=0,sh=1", False),              # sh only with a K split
 ])
 def test_direct_spec_parsing_is_strict(lib, spec, ok):
     log = ctypes.create_string_buffer(1 << 16)
     st = lib.fbcorr_rtcg_check(C.I64_3(64, 80, 8), C.I64_4(24, 5, 3, 8), C.epilogue(), spec, log, len(log))
     assert (st == 0) == ok, (st, C.last_error())
+
+
+@pytest.mark.parametrize("D,N,spec", [
+    (8, 16, b"direct:tr=4,tf=8,wr=2,wf=1,cc=0,pk=1,ks=8,wq=4"),    # the first configuration's depth
+    (8, 16, b"direct:tr=2,tf=16,wr=4,wf=1,cc=0,ks=16,wq=2"),       # eight padding channels per pixel
+    (3, 5, b"direct:tr=4,tf=4,wr=1,wf=2,cc=0,pk=1,ks=4,wq=8"),     # depth 3 padded to 4, scalar staging
+    (16, 12, b"direct:tr=8,tf=8,wr=1,wf=1,cc=0,ks=32,wq=2"),       # one column per warp
+    (24, 20, b"direct:tr=4,tf=8,wr=2,wf=2,cc=0,pk=1,ks=8,wq=2"),   # three channels per lane
+    (8, 16, b"direct:tr=16,tf=4,wr=1,wf=4,cc=0,pk=1,ks=8,wq=2,sh=1"),   # share in the high lane bits
+])
+def test_ksplit_tiles_compile(lib, D, N, spec):
+    """The K-split forward tile compiles for sm_103a with the clamp epilogue;
+    a backward (flipped) problem never takes it."""
+    log = ctypes.create_string_buffer(1 << 16)
+    st = lib.fbcorr_rtcg_check(C.I64_3(40, 50, D), C.I64_4(N, 5, 3, D), C.epilogue((-1, 1)), spec, log, len(log))
+    assert st == 0, C.last_error() + log.value.decode()
 
 
 @pytest.mark.parametrize("D,f,spec", [
