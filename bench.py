@@ -208,6 +208,8 @@ def workload_by_name(name):
         return inputs.Workload("precision_384x384x32_256x5x5x32", x, w)
     if name == "paper_row1":
         return inputs.workload_paper_row1_clamp()
+    if name == "small":
+        return inputs.workload_small_f32()
     raise ValueError(name)
 
 
@@ -364,6 +366,51 @@ def fp32_fma_probe(sm_count: int, iters: int = 5000) -> dict:
     return out
 
 
+def link_rate(torch, h2d_bytes, d2h_bytes, reps=5):
+    """The host link measured on the e2e byte counts: one cudaMemcpyAsync per
+    direction between page-locked host memory and the device (torch copy_),
+    timed by CUDA events; each direction alone, and both at once on two
+    streams (the link is full duplex, so that is the floor of a step that moves
+    both).  Medians of `reps` runs."""
+    hsrc = torch.empty(h2d_bytes, dtype=torch.uint8).pin_memory()
+    ddst = torch.empty(h2d_bytes, dtype=torch.uint8, device="cuda")
+    dsrc = torch.empty(d2h_bytes, dtype=torch.uint8, device="cuda")
+    hdst = torch.empty(d2h_bytes, dtype=torch.uint8).pin_memory()
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def alone(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(s1)
+        with torch.cuda.stream(s1):
+            fn()
+        e1.record(s1)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    def duplex():
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        torch.cuda.synchronize()
+        e0.record(s1)
+        s2.wait_event(e0)
+        with torch.cuda.stream(s1):
+            ddst.copy_(hsrc, non_blocking=True)
+        e1.record(s1)
+        with torch.cuda.stream(s2):
+            hdst.copy_(dsrc, non_blocking=True)
+        e2.record(s2)
+        torch.cuda.synchronize()
+        return max(e0.elapsed_time(e1), e0.elapsed_time(e2))
+
+    h2d = statistics.median(alone(lambda: ddst.copy_(hsrc, non_blocking=True)) for _ in range(reps))
+    d2h = statistics.median(alone(lambda: hdst.copy_(dsrc, non_blocking=True)) for _ in range(reps))
+    both = statistics.median(duplex() for _ in range(reps))
+    return {"h2d_gbs": h2d_bytes / (h2d * 1e-3) / 1e9, "d2h_gbs": d2h_bytes / (d2h * 1e-3) / 1e9,
+            "h2d_ms": h2d, "d2h_ms": d2h, "duplex_ms": both,
+            "how": "one cudaMemcpyAsync per direction, pinned host memory, CUDA events, median of "
+                   f"{reps}; duplex = both directions at once on two streams"}
+
+
 def run_ours(args):
     import torch
     from paper_0911_3456_gb300 import inputs
@@ -377,6 +424,11 @@ def run_ours(args):
     x = torch.from_numpy(wl.x).cuda()
     w = torch.from_numpy(wl.w).cuda()
 
+    # clocks: sampled from before the auto-tuning (which runs this plan's
+    # kernels for seconds) to the end of the timed steps, so that a short timed
+    # region still has samples under the same load
+    clocks = ClockSampler(local)
+    clocks.start()
     mode = args.mode
     plans = {}
     for m in dict.fromkeys([mode, "f32", "bf16", "bf16x3"]):
@@ -405,10 +457,9 @@ def run_ours(args):
     per_launch = mode == "f32"
     if per_launch:
         plan.profile(args.steps)
-    clocks = ClockSampler(local)
-    clocks.start()
     ms = time_loop(torch, lambda: plan.forward(x, w, y), args.steps, args.warmup, world)
     clk = clocks.stop()
+    clk["window"] = "plan auto-tuning, warm-up and the timed steps"
     if per_launch:
         kern_ms = plan.profile_read()
         plan.profile(0)
@@ -447,9 +498,27 @@ def run_ours(args):
         roof["peak_split_bf16x3"] = peak / 3
         roof["frac_of_split_peak"] = 3 * achieved / peak
 
+    # ---- the same step back to back for about --sustained-s seconds (clocks
+    # sampled during it), rated against the sustained BF16 peak
+    sustained = None
+    if args.sustained_s > 0 and not args.quick:
+        n_s = max(args.steps, int(args.sustained_s * 1e3 / max(ms, 1e-3)))
+        sc = ClockSampler(local)
+        sc.start()
+        ms_s = time_loop(torch, lambda: plan.forward(x, w, y), n_s, 3, world)
+        sclk = sc.stop()
+        sustained = {"steps": n_s, "seconds": n_s * ms_s / 1e3, "ms_per_step": ms_s,
+                     "gflops": world * flops / (ms_s * 1e-3) / 1e9, "clocks": sclk}
+        if mode != "f32":
+            pk_s = peaks["bf16_tflops_sustained"]
+            a_s = flops / (ms_s * 1e-3) / 1e12
+            sustained["frac_of_sustained_peak"] = a_s / pk_s
+            if mode == "bf16x3":
+                sustained["frac_of_split_sustained_peak"] = 3 * a_s / pk_s
+
     # ---- e2e through the C ABI from page-locked host buffers: fbcorr_forward_host
     # copies x and w in and y out every step, banded so that the transfers
-    # overlap the compute (the host link, ~0.2 TB/s each way, is the bound)
+    # overlap the compute; the same byte counts are also timed as plain copies
     e2e = None
     if not args.no_e2e:
         xh = torch.from_numpy(wl.x).pin_memory()
@@ -463,13 +532,20 @@ def run_ours(args):
         ms_e2e = time_loop(torch, e2e_step, k_e2e, max(3, args.warmup), world)
         torch.cuda.synchronize()
         e2e_diff = float((yh - y.cpu()).abs().max() / y.abs().max())
+        h2d_b, d2h_b = int(wl.x.nbytes + wl.w.nbytes), int(np.prod(plan.out_shape) * 4)
         e2e = {"value": world * flops / (ms_e2e * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms_e2e,
-               "steps": k_e2e, "h2d_bytes_per_step": int(wl.x.nbytes + wl.w.nbytes),
-               "d2h_bytes_per_step": int(np.prod(plan.out_shape) * 4),
+               "steps": k_e2e, "h2d_bytes_per_step": h2d_b, "d2h_bytes_per_step": d2h_b,
                "call": "fbcorr_forward_host", "bands": args.bands or "auto",
                "max_rel_diff_vs_device_forward": e2e_diff}
+        try:
+            link = link_rate(torch, h2d_b, d2h_b)
+            link["e2e_frac_of_duplex_copy"] = link["duplex_ms"] / ms_e2e
+            e2e["link"] = link
+        except Exception as ex:   # reported, never fatal to the line
+            e2e["link"] = {"unavailable": str(ex)}
 
     detail = {"headline_plan": info}
+    accuracy = None
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         # CPU oracle on a bounded sample; the same sample gives the error of every mode
@@ -483,12 +559,14 @@ def run_ours(args):
             yy = p.forward(x, w)
             torch.cuda.synchronize()
             errs[m] = sampled_error(yy[r0:r0 + rows].cpu().numpy(), ref)
-        detail["max_rel_err_vs_fp64_oracle"] = errs
-        detail["error_sample"] = cpu["sample"]
+        accuracy = {"max_rel_err_vs_fp64_oracle": errs,
+                    "definition": "max|y - y_oracle| / max|y_oracle| over the sample",
+                    "sample_rows": [int(r0), int(r0 + rows)], "gates": {"f32": 1e-5, "bf16x3": 1e-5, "bf16": 1e-2}}
 
     # ---- the same workload in the other modes (kernel + step times)
+    modes = {}
+    summary = None
     if not args.quick:
-        modes = {}
         for m, p in plans.items():
             if isinstance(p, Exception):
                 modes[m] = {"unavailable": str(p)}
@@ -508,13 +586,14 @@ def run_ours(args):
                         "kernel_frac_of_peak": (flops / (k_avg * 1e-3) / 1e12 / pk) if k_avg else None,
                         "peak_tflops": pk, "spec": p.info()["fwd"].get("spec")}
         detail["modes_same_workload"] = modes
-        if "f32" in modes and mode in modes and "gflops" in modes.get("f32", {}):
+        if "gflops" in modes.get("f32", {}) and "gflops" in modes.get(mode, {}):
             detail["speedup_vs_fp32_direct"] = modes[mode]["gflops"] / modes["f32"]["gflops"]
         detail.update(secondary(torch, args, world, peaks))
         try:
             detail["fp32_fma_probe"] = fp32_fma_probe(props.multi_processor_count)
         except Exception as e:   # reported, never fatal to the line
             detail["fp32_fma_probe"] = {"unavailable": str(e)}
+        summary = summarize(detail, modes, mode)
 
     if rank == 0:
         line = {
@@ -526,13 +605,64 @@ def run_ours(args):
                        "l2": l2_note(wl, plan.out_shape),
                        "parallelism": f"replicas x{world}"},
             "roofline": roof, "clocks": clk, "gpu_launches": launches_per_step * args.steps,
-            "e2e": e2e, "cpu_baseline": cpu, "peaks": peaks, "detail": detail,
+            "accuracy": accuracy, "sustained": sustained,
+            "e2e": e2e, "cpu_baseline": cpu, "peaks": peaks, "summary": summary,
         }
+        full = dict(line, detail=detail)
+        if args.detail_out:
+            with open(args.detail_out, "w") as f:
+                json.dump(full, f, indent=1)
+        print(json.dumps({"detail": detail}), file=sys.stderr, flush=True)
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def summarize(detail, modes, mode):
+    """The figures of the secondary workloads that the printed line keeps (the
+    full record goes to --detail-out and stderr)."""
+    def r3(v):
+        return None if v is None else float(f"{v:.4g}")
+
+    out = {"modes": {m: {"gflops": r3(v.get("gflops")), "kernel_frac_of_peak": r3(v.get("kernel_frac_of_peak")),
+                         "spec": v.get("spec")} for m, v in modes.items() if "gflops" in v}}
+    if "speedup_vs_fp32_direct" in detail:
+        out["modes"][f"{mode}_speedup_vs_fp32_direct"] = r3(detail["speedup_vs_fp32_direct"])
+    for key, name in (("small_128x128x8_16x9x9x8", "small_f32"), ("paper_row1_256x256x8_64x9x9x8_clamp",
+                                                                     "paper_row1_clamp_f32")):
+        v = detail.get(key)
+        if v:
+            out[name] = {k: r3(v.get(k)) if k != "tuned_spec" else v.get(k)
+                         for k in ("default_gflops", "heuristic_gflops", "tuned_gflops", "boost_percent",
+                                   "search_gain_percent", "tuned_frac_of_fp32_peak", "tuned_spec")}
+    if detail.get("paper_table_fp32"):
+        out["paper_table_fp32"] = [{"shape": f"{'x'.join(map(str, r['input']))}/{'x'.join(map(str, r['bank']))}",
+                                    "default": r3(r["default_gflops"]), "heuristic": r3(r["heuristic_gflops"]),
+                                    "tuned": r3(r["tuned_gflops"]), "boost_percent": r3(r["boost_percent"]),
+                                    "search_gain_percent": r3(r["search_gain_percent"])}
+                                   for r in detail["paper_table_fp32"]]
+    fb = detail.get("fwdbwd_256x256x16_64x7x7x16")
+    if fb:
+        out["fwdbwd_f32"] = {k: r3(fb[k]) for k in ("fwd_gflops", "dx_gflops", "dw_gflops", "fwd_bwd_gflops",
+                                                     "fwd_bwd_frac_of_fp32_peak")}
+    b = detail.get("batch64_uneven")
+    if b:
+        out["batch64_f32"] = {"gflops": r3(b["gflops"]), "frac_of_fp32_peak": r3(b["frac_of_fp32_peak"]),
+                              "launches_per_step": b["launches_per_step"]}
+    c = detail.get("cascade_3layer_256x256x8")
+    if c:
+        out["cascade_gflops"] = {m: r3(c[m]["gflops"]) for m in ("f32", "bf16x3") if m in c}
+    nn = detail.get("nn_search_4096_patches_8x8")
+    if nn:
+        last = nn[-1]
+        out["nn_search"] = {"neighbors": last["neighbors"], "ms": r3(last["ms"]),
+                            "pairs_per_s": r3(last["pairs_per_s"]), "status": last["status"]}
+    fma = detail.get("fp32_fma_probe")
+    if fma and "packed_tflops" in fma:
+        out["fp32_fma_probe_tflops"] = r3(max(fma["scalar_tflops"], fma["packed_tflops"]))
+    return out
 
 
 def secondary(torch, args, world, peaks):
@@ -549,14 +679,21 @@ def secondary(torch, args, world, peaks):
         y = torch.empty(p.out_shape, device="cuda")
         p.set_variant("default")
         ms_def = time_loop(torch, lambda: p.forward(x, w, y), 30, 3, world, flush)
+        p.set_variant("heuristic")
+        heur_spec = p.info()["fwd"].get("spec")
+        ms_heur = time_loop(torch, lambda: p.forward(x, w, y), 30, 3, world, flush)
         p.autotune()
         ms_tuned = time_loop(torch, lambda: p.forward(x, w, y), 30, 3, world, flush)
-        out[name] = {"default_gflops": wl.flops / ms_def / 1e6, "tuned_gflops": wl.flops / ms_tuned / 1e6,
+        out[name] = {"default_gflops": wl.flops / ms_def / 1e6, "heuristic_gflops": wl.flops / ms_heur / 1e6,
+                     "tuned_gflops": wl.flops / ms_tuned / 1e6,
                      "boost_percent": 100.0 * (ms_def / ms_tuned - 1.0),
+                     "search_gain_percent": 100.0 * (ms_heur / ms_tuned - 1.0),
                      "tuned_frac_of_fp32_peak": wl.flops / ms_tuned / 1e9 / peaks["fp32_tflops"],
-                     "tuned_spec": p.info()["fwd"].get("spec")}
-    # the paper's own table shapes: default (prebuilt generic) vs tuned, the
-    # table's "Default", "RTCG auto-tuned" and "Boost" columns measured here
+                     "heuristic_spec": heur_spec, "tuned_spec": p.info()["fwd"].get("spec")}
+    # the paper's own table shapes: default (prebuilt generic), heuristic (the
+    # generated kernel with the model's tile, not searched) and tuned; the
+    # table's "Default", "RTCG auto-tuned" and "Boost" columns measured here,
+    # and tuned over heuristic, the gain of the search itself
     table = []
     for row in range(len(inputs.PAPER_TABLE_SHAPES)):
         wl = inputs.workload_paper_table(row)
@@ -566,11 +703,17 @@ def secondary(torch, args, world, peaks):
         y = torch.empty(p.out_shape, device="cuda")
         p.set_variant("default")
         ms_def = time_loop(torch, lambda: p.forward(x, w, y), 20, 3, world, flush)
+        p.set_variant("heuristic")
+        heur_spec = p.info()["fwd"].get("spec")
+        ms_heur = time_loop(torch, lambda: p.forward(x, w, y), 20, 3, world, flush)
         p.autotune()
         ms_tuned = time_loop(torch, lambda: p.forward(x, w, y), 20, 3, world, flush)
         table.append({"input": list(wl.x.shape), "bank": list(wl.w.shape),
-                      "default_gflops": wl.flops / ms_def / 1e6, "tuned_gflops": wl.flops / ms_tuned / 1e6,
+                      "default_gflops": wl.flops / ms_def / 1e6, "heuristic_gflops": wl.flops / ms_heur / 1e6,
+                      "tuned_gflops": wl.flops / ms_tuned / 1e6,
                       "boost_percent": 100.0 * (ms_def / ms_tuned - 1.0),
+                      "search_gain_percent": 100.0 * (ms_heur / ms_tuned - 1.0),
+                      "heuristic_spec": heur_spec,
                       "tuned_frac_of_fp32_peak": wl.flops / ms_tuned / 1e9 / peaks["fp32_tflops"],
                       "tuned_spec": p.info()["fwd"].get("spec")})
         del x, w, y, p
@@ -788,8 +931,12 @@ def main():
     ap.add_argument("--spec", default=None,
                     help="forward variant of the headline plan instead of auto-tuning (profiling runs)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    ap.add_argument("--workload", choices=["precision", "precision384", "paper_row1"],
+    ap.add_argument("--workload", choices=["precision", "precision384", "paper_row1", "small"],
                     default="precision")
+    ap.add_argument("--detail-out", default=None,
+                    help="write the full detail record (every secondary workload, plans) to this JSON file")
+    ap.add_argument("--sustained-s", type=float, default=1.0,
+                    help="seconds of the back-to-back sustained headline loop (0: skip)")
     ap.add_argument("--nn", type=int, default=0,
                     help="time only the nearest-neighbour search against this many neighbours")
     ap.add_argument("--fwdbwd", action="store_true",
