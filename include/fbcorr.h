@@ -254,13 +254,19 @@ fbcorr_status_t fbcorr_forward_batched(fbcorr_batch_plan_t plan, const float* co
  * sum_k (t_k - n_k)^2 computed exactly in FP32.
  * Method: every (target, neighbour) pair is screened on the tensor cores by
  * d' = |n|^2 - 2 t.n (dtype BF16X3: split-BF16 products, error about 2^-16
- * sum_k |t_k||n_k|; BF16: plain, about 2^-8), the best candidates of each target
- * are kept, and the best 4 are re-ranked by their exact FP32 distance (ties: the
- * lowest index).  The result is the exact nearest neighbour (up to FP32 distance
- * rounding) whenever fewer than 4 neighbours are within twice the screening error
- * of it.  dim <= 64, n_targets and n_neighbors < 2^31.  The plan compiles its
- * kernel (NVRTC) at creation; the search allocates nothing, performs no host
- * synchronisation and is stream-ordered. */
+ * sum_k |t_k||n_k|; BF16: plain, about 2^-8), and the two best candidates of
+ * every part of the screening are kept.  A bound E on the screening error of the
+ * target's keys (from |t|, the largest |n| and the arithmetic of each step)
+ * gives the window of keys within 2E of the smallest one, which holds the true
+ * nearest neighbour; every candidate in it is re-ranked by its exact FP32
+ * distance.  Where a part may hold more candidates in the window than it kept,
+ * the target's exact FP32 distance to every neighbour of that part is taken too
+ * (to every neighbour when more than 8 of its parts are incomplete).  So the
+ * result is always the argmin of the exact FP32 distance over all neighbours
+ * (ties: the lowest index): the exact nearest neighbour up to FP32 rounding of
+ * the distances.  dim <= 64, n_targets and n_neighbors < 2^31.  The plan
+ * compiles its kernel (NVRTC) at creation; the search allocates nothing, performs
+ * no host synchronisation and is stream-ordered. */
 fbcorr_status_t fbcorr_nn_plan_create(fbcorr_nn_plan_t* out, int64_t n_targets, int64_t n_neighbors,
                                       int64_t dim, fbcorr_dtype_t dtype);
 /* Release the plan (NULL: no-op); its searches must have finished. */
@@ -276,6 +282,12 @@ fbcorr_status_t fbcorr_nn_search(fbcorr_nn_plan_t plan, const float* targets, co
                                  fbcorr_stream_t stream);
 /* As fbcorr_plan_device_status, for the nearest-neighbour kernel. */
 fbcorr_status_t fbcorr_nn_plan_device_status(fbcorr_nn_plan_t plan, int clear);
+/* How many targets of the plan's last search were re-scanned exactly (their
+ * window could not be certified from the kept candidates alone) into *count;
+ * 0 before the first search.  Waits for the last search's stream and reads its
+ * workspace, which must still hold that search's counters (diagnostics, not for
+ * a hot loop). */
+fbcorr_status_t fbcorr_nn_last_fallbacks(fbcorr_nn_plan_t plan, int64_t* count);
 /* Offline check (no GPU): generate and compile the screening kernel for dim. */
 fbcorr_status_t fbcorr_nn_rtcg_check(int64_t dim, fbcorr_dtype_t dtype, char* log, size_t cap);
 

@@ -63,6 +63,7 @@ PROTOTYPES = {
     "fbcorr_nn_workspace_size": (_st, [_vp, ctypes.POINTER(ctypes.c_size_t)]),
     "fbcorr_nn_search": (_st, [_vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "fbcorr_nn_plan_device_status": (_st, [_vp, ctypes.c_int]),
+    "fbcorr_nn_last_fallbacks": (_st, [_vp, ctypes.POINTER(ctypes.c_int64)]),
     "fbcorr_nn_rtcg_check": (_st, [ctypes.c_int64, ctypes.c_int, ctypes.c_char_p, _sz]),
     "fbcorr_backward": (_st, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _sz, _vp]),
     "fbcorr_autotune": (_st, [_vp, _vp]),

@@ -302,6 +302,13 @@ class NNPlan:
     def device_status(self, clear: bool = False) -> int:
         return int(C.load().fbcorr_nn_plan_device_status(self._h, 1 if clear else 0))
 
+    def last_fallbacks(self) -> int:
+        """Targets of the last search whose screening window could not be
+        certified and that were searched exhaustively instead (synchronises)."""
+        n = ctypes.c_int64()
+        C.call("fbcorr_nn_last_fallbacks", self._h, ctypes.byref(n))
+        return int(n.value)
+
     def search(self, targets: torch.Tensor, neighbors: torch.Tensor, stream=None):
         _check_tensor(targets, "targets", (self.n_targets, self.dim))
         _check_tensor(neighbors, "neighbors", (self.n_neighbors, self.dim))

@@ -168,6 +168,19 @@ std::string dw_kernel_source(int fh, int fw, int c, int tn, int ng, int qb, int 
 
 namespace {
 int ceil_div(long a, long b) { return (int)((a + b - 1) / b); }
+
+// How evenly `ctas` CTAs spread over the SMs, `res` resident per SM: within one
+// round the busiest SM runs ceil(ctas / sms) of them against an average of
+// ctas / sms; beyond one round, whole rounds of res * sms CTAs.
+double wave_balance(long ctas, int res, int sms) {
+    const long slots = (long)res * sms;
+    if (ctas <= slots) {
+        const long per = (ctas + sms - 1) / sms;
+        return ((double)ctas / sms) / (double)per;
+    }
+    const long waves = (ctas + slots - 1) / slots;
+    return (double)ctas / (double)(waves * slots);
+}
 }  // namespace
 
 std::vector<DirectTile> direct_candidates(const DirectProblem& pr, size_t smem_limit, int threads,
@@ -250,9 +263,7 @@ static double direct_score(const DirectProblem& pr, const DirectTile& t, int sm_
         res = std::min(res, 65536 / (t.threads() * std::min(255, regs)));
         if (res < 1) return -1.0;
         const long ctas = (long)gx * gy * gz;
-        const long slots = (long)res * sm_count;
-        const long waves = (ctas + slots - 1) / slots;
-        const double wave_eff = (double)ctas / (double)(waves * slots);
+        const double wave_eff = wave_balance(ctas, res, sm_count);
         // inner loop per warp and (tap column, channel step), in SM cycles: the
         // FMA pipe (128 lanes), the shared-memory pipe (one wavefront per cycle:
         // one per input load, four per float4 filter load, whose lanes read

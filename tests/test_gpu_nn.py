@@ -14,13 +14,20 @@ from paper_0911_3456_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 
-def _run(torch, t, n, dtype="bf16x3"):
+def _run(torch, t, n, dtype="bf16x3", fallbacks=False):
     from paper_0911_3456_gb300.api import NNPlan
     p = NNPlan(t.shape[0], n.shape[0], t.shape[1], dtype)
     idx, dist = p.search(torch.from_numpy(t).cuda(), torch.from_numpy(n).cuda())
     torch.cuda.synchronize()
     assert p.device_status() == 0
-    return idx.cpu().numpy(), dist.cpu().numpy().astype(np.float64)
+    out = idx.cpu().numpy(), dist.cpu().numpy().astype(np.float64)
+    return out + (p.last_fallbacks(),) if fallbacks else out
+
+
+def _fp32_separated(ref_d, ref_d2, dim):
+    """Targets whose nearest neighbour is unique by more than the FP32 rounding
+    of the exact distances ((dim + 3) * 2^-24 relative, twice, with margin)."""
+    return (ref_d2 - ref_d) > 4 * (dim + 3) * 2.0 ** -24 * ref_d2 + 1e-30
 
 
 def _check(t, n, idx, dist, tol_rel_pair, min_sep=0.5):
@@ -38,6 +45,11 @@ def _check(t, n, idx, dist, tol_rel_pair, min_sep=0.5):
     assert sep.mean() >= min_sep
     # the distance is the exact FP32 one for the returned neighbour
     assert np.allclose(dist, chosen, rtol=64 * 2.0 ** -23, atol=1e-7)
+    # the search returns the argmin of the exact FP32 distance over all
+    # neighbours, so wherever the oracle's nearest is unique beyond FP32
+    # rounding the index is the oracle's
+    fs = _fp32_separated(ref_d, ref_d2, t.shape[1])
+    assert np.array_equal(idx[fs], ref_idx[fs])
 
 
 @pytest.mark.parametrize("nt,nn,dim", [(300, 5000, 64), (129, 257, 3), (128, 256, 16), (1, 3000, 33)])
@@ -75,10 +87,12 @@ def test_natural_patches_against_oracle():
     t, n = inputs.nn_patches(n_neighbors=65536)
     idx, dist = _run(torch, t, n)
     _check(t, n, idx, dist, 4 * 2.0 ** -16, min_sep=0.0)
-    # the bound above is loose for smooth patches; the exact re-ranking in fact
-    # returns the oracle's neighbour almost everywhere
-    ref_idx, _, _ = oracle.nn(t, n)
-    assert (idx == ref_idx).mean() >= 0.99
+    # every target whose nearest neighbour is unique beyond FP32 rounding gets
+    # exactly the oracle's
+    ref_idx, ref_d, ref_d2 = oracle.nn(t, n)
+    fs = _fp32_separated(ref_d, ref_d2, t.shape[1])
+    assert fs.mean() >= 0.95
+    assert np.array_equal(idx[fs], ref_idx[fs])
 
 
 def test_plain_bf16_screening_is_reranked_exactly():
@@ -93,6 +107,74 @@ def test_plain_bf16_screening_is_reranked_exactly():
     ref_idx, ref_d, _ = oracle.nn(t, n)
     assert np.array_equal(idx, ref_idx)
     assert np.allclose(dist, ref_d, rtol=1e-5, atol=1e-7)
+
+
+def _planted(spread, seed=3400):
+    """Target 0 is the all-ones vector of 64 coordinates.  Twelve neighbours lie
+    around it: the true nearest n* = 1 + a (every coordinate) and eleven at
+    1 - b_k with b_k slightly larger than a.  Plain BF16 rounds every one of them
+    to the all-ones vector, so the screened key of n* is the largest of the
+    twelve by 128 (a + b) while its exact distance, 64 a^2, is the smallest: the
+    true nearest is not among the first four screened, and all twelve lie within
+    the screening error of the best.  The other neighbours are far away, so the
+    window of the one target holds exactly the twelve.
+    spread=True puts the twelve in twelve different neighbour tiles (one per
+    screening part: the window holds them all and is certified without the
+    fallback); spread=False puts them in the first 32 columns of one tile (one
+    part keeps only two of them, so the target is searched exhaustively)."""
+    rng = np.random.default_rng(seed)
+    dim, nn = 64, 5120
+    n = (1.0 + 3.0 * rng.standard_normal((nn, dim))).astype(np.float32)
+    t = np.ones((1, dim), np.float32)
+    a = 1e-3
+    slots = [256 * k + 7 for k in range(12)] if spread else [256 * 9 + k for k in range(12)]
+    star = slots[5]
+    for k, j in enumerate(slots):
+        n[j] = (1.0 + a) if j == star else (1.0 - a * (1.02 + 0.01 * k))
+    return t, n, star
+
+
+@pytest.mark.parametrize("spread", [True, False], ids=["window_certified", "exhaustive_fallback"])
+@pytest.mark.parametrize("dtype", ["bf16", "bf16x3"])
+def test_nearest_beyond_the_first_four_screened(spread, dtype):
+    """Twelve neighbours within the screening error of the true nearest, which
+    screens last of them (plain BF16): the index must be the oracle's.  Either
+    every candidate of the certified window is re-ranked exactly, or the target
+    whose window a part may have truncated is searched exhaustively."""
+    torch = torch_cuda()
+    t, n, star = _planted(spread)
+    ref_idx, ref_d, ref_d2 = oracle.nn(t, n)
+    assert ref_idx[0] == star
+    if dtype == "bf16":
+        # the construction: in plain BF16 every planted neighbour rounds to the
+        # target itself, so n* has the largest screened key of the twelve
+        n_bf = n.view(np.uint32)
+        assert np.all(((n_bf[star] + 0x8000) & 0xFFFF0000) == np.float32(1.0).view(np.uint32))
+    idx, dist, fb = _run(torch, t, n, dtype, fallbacks=True)
+    assert idx[0] == star
+    assert dist[0] == np.float32(dist[0]) and abs(dist[0] - ref_d[0]) <= 1e-3 * ref_d[0]
+    if dtype == "bf16":
+        assert fb == (0 if spread else 1)
+
+
+def test_exhaustive_fallback_many_targets():
+    """Many targets with truncated windows at once (duplicated neighbours: every
+    target has a whole tile of near-ties in plain BF16): the fallback handles
+    them all, and every answer is the argmin of the exact distance."""
+    torch = torch_cuda()
+    rng = np.random.default_rng(3500)
+    dim = 32
+    base = (rng.standard_normal((300, dim)) * 4).astype(np.float32)
+    n = np.repeat(base, 8, axis=0) + (1e-4 * rng.standard_normal((2400, dim))).astype(np.float32)
+    t = base[rng.integers(0, 300, size=500)] + (1e-4 * rng.standard_normal((500, dim))).astype(np.float32)
+    idx, dist, fb = _run(torch, t, n, "bf16", fallbacks=True)
+    assert fb > 0
+    ref_idx, ref_d, ref_d2 = oracle.nn(t, n)
+    fs = _fp32_separated(ref_d, ref_d2, dim)
+    assert fs.mean() >= 0.9
+    assert np.array_equal(idx[fs], ref_idx[fs])
+    chosen = ((t.astype(np.float64) - n.astype(np.float64)[idx]) ** 2).sum(axis=1)
+    assert np.allclose(dist, chosen, rtol=64 * 2.0 ** -23, atol=1e-9)
 
 
 @pytest.mark.parametrize("nt,nn,dim", [(1, 1, 1), (5, 2, 64), (200, 700, 8), (130, 1000, 48)])
