@@ -171,7 +171,9 @@ fbcorr_status_t prepare_backward(fbcorr_plan* p) {
     DirectTile t = direct_heuristic(pr, smem_limit(p->dev), p->dev.sm_count);
     std::string cached;
     bool use_default = false;
-    if (tune_lookup(tune_key(p->dev, shape_key(p, "dx")), &cached)) {
+    const std::string forced = env_str("FBCORR_DX_VARIANT", "");   // a dL/dx spec (tests, profiling)
+    if (!forced.empty() || tune_lookup(tune_key(p->dev, shape_key(p, "dx")), &cached)) {
+        if (!forced.empty()) cached = forced;
         DirectTile ct;
         if (cached == "default")
             use_default = true;
@@ -771,7 +773,7 @@ fbcorr_status_t fbcorr_plan_candidates(fbcorr_plan_t p, char* buf, size_t cap) {
     if (p->dtype == FBCORR_F32) {
         const int topk = std::max(1, atoi(env_str("FBCORR_TUNE_TOPK", "48").c_str()));
         specs = direct_tuning_specs(direct_ranked(fwd_problem(p), smem_limit(p->dev), p->dev.sm_count, 0, 64),
-                                    topk);
+                                    topk, (int)p->D);
         if (p->snippet.empty()) specs.push_back("default");
     } else {
         specs = tc_candidates(p->tc);

@@ -98,6 +98,7 @@ struct DirectTile {
     int tr = 8, tf = 8, wr = 1, wf = 2;
     int cc = 0;   // input channels staged per chunk; 0 = the whole depth
     int pk = 0;   // 1: multiply-adds issued as packed pairs (fma.rn.f32x2), same bits
+    int pf = 0;   // 1: the next channel chunk is loaded into registers while one is summed
     // K split (forward only): ks > 1 lanes share each output and split the depth,
     // combined by warp shuffles; a warp then covers 32 / ks columns and the CTA
     // wq warps side by side; sh = 1 takes the depth share from the high lane
@@ -134,9 +135,10 @@ std::string direct_kernel_source(const DirectProblem& pr, const DirectTile& t,
 std::vector<DirectTile> direct_candidates(const DirectProblem& pr, size_t smem_limit,
                                           int threads = 0, int max_block = 64);
 // The specs the tuner times: the first topk tiles of a ranked list, each as
-// written and with packed-pair FMAs (pk=1); FBCORR_TUNE_PK=0 keeps only the
-// former.
-std::vector<std::string> direct_tuning_specs(const std::vector<DirectTile>& ranked, int topk);
+// written and with packed-pair FMAs (pk=1; FBCORR_TUNE_PK=0 keeps only the
+// former), and, given the problem's depth, tiles of several channel chunks also
+// with the register prefetch (pf=1; FBCORR_TUNE_PF=0 leaves it out).
+std::vector<std::string> direct_tuning_specs(const std::vector<DirectTile>& ranked, int topk, int depth = 0);
 DirectTile direct_heuristic(const DirectProblem& pr, size_t smem_limit, int sm_count,
                             int threads = 0, int max_block = 64);
 // candidates ordered by the analytic model, best first

@@ -54,7 +54,7 @@ struct FbcOdd { static constexpr int value = (V % 2 == 1) ? V : V + 1; };
 // only the issue pressure differs.  The input value is broadcast into both
 // halves once per (j, c) and reused for all FH filter rows.
 template <int FH, int FW, int C, int TR, int TF, int WR, int WF, int FLIP, int EPI, int MASK, int CC,
-          int PK = 0>
+          int PK = 0, int PF = 0>
 struct FbcDirect {
     static constexpr int BW = 32;
     static constexpr int BH = TR * WR;
@@ -70,92 +70,194 @@ struct FbcDirect {
     static constexpr int SMEM_BYTES = (XS + WS) * 4;
     static_assert(TF % 4 == 0, "TF must be a multiple of 4");
 
+    // Staging elements: the halo in 4-channel groups (XV) or single channels, the
+    // forward bank in 4-channel groups (WV) or single values.  Each element is
+    // loaded from global memory (x_load / w_load) and stored transposed into
+    // shared memory (x_store / w_store).
+    static constexpr bool XV = (C % 4 == 0) && (CC % 4 == 0);
+    static constexpr bool WV = !FLIP && (C % 4 == 0) && (CC % 4 == 0);
+    static constexpr int NXE = XV ? HR * HC * (CC / 4) : HR * HC * CC;
+    static constexpr int NWE = WV ? BN * FH * FW * (CC / 4) : BN * FH * FW * CC;
+    static constexpr int PX = (NXE + NT - 1) / NT;   // elements per thread
+    static constexpr int PW = (NWE + NT - 1) / NT;
+
     static __device__ __forceinline__ float mask_val(float v, float mv, float lo, float hi) {
         return (mv > lo && mv < hi) ? v : 0.0f;
+    }
+
+    static __device__ __forceinline__ float4 x_load4(const FbcDirectArgs& a, int e, int c0, int p0, int q0) {
+        constexpr int C4 = CC / 4;
+        const int c4 = e % C4;
+        const int t = e / C4;
+        const int col = t % HC;
+        const int row = t / HC;
+        const int gy = p0 - a.pad_y + row;
+        const int gx = q0 - a.pad_x + col;
+        const int c = c0 + c4 * 4;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (gy >= 0 && gy < a.in_h && gx >= 0 && gx < a.in_w && c < C) {
+            const long long off = ((long long)gy * a.in_w + gx) * C + c;
+            v = __ldg(reinterpret_cast<const float4*>(a.x + off));
+            if (MASK) {
+                const float4 mv = __ldg(reinterpret_cast<const float4*>(a.m + off));
+                v.x = mask_val(v.x, mv.x, a.lo, a.hi);
+                v.y = mask_val(v.y, mv.y, a.lo, a.hi);
+                v.z = mask_val(v.z, mv.z, a.lo, a.hi);
+                v.w = mask_val(v.w, mv.w, a.lo, a.hi);
+            }
+        }
+        return v;
+    }
+    static __device__ __forceinline__ void x_store4(float* xs, int e, float4 v) {
+        constexpr int C4 = CC / 4;
+        const int c4 = e % C4;
+        const int t = e / C4;
+        const int col = t % HC;
+        const int row = t / HC;
+        float* dst = xs + (row * CC + c4 * 4) * COLP + col;
+        dst[0] = v.x;
+        dst[COLP] = v.y;
+        dst[2 * COLP] = v.z;
+        dst[3 * COLP] = v.w;
+    }
+    static __device__ __forceinline__ float x_load1(const FbcDirectArgs& a, int e, int c0, int p0, int q0) {
+        const int cl = e % CC;
+        const int t = e / CC;
+        const int col = t % HC;
+        const int row = t / HC;
+        const int gy = p0 - a.pad_y + row;
+        const int gx = q0 - a.pad_x + col;
+        const int c = c0 + cl;
+        float v = 0.f;
+        if (gy >= 0 && gy < a.in_h && gx >= 0 && gx < a.in_w && c < C) {
+            const long long off = ((long long)gy * a.in_w + gx) * C + c;
+            v = __ldg(a.x + off);
+            if (MASK) v = mask_val(v, __ldg(a.m + off), a.lo, a.hi);
+        }
+        return v;
+    }
+    static __device__ __forceinline__ void x_store1(float* xs, int e, float v) {
+        const int cl = e % CC;
+        const int t = e / CC;
+        const int col = t % HC;
+        const int row = t / HC;
+        xs[(row * CC + cl) * COLP + col] = v;
+    }
+    // forward, 4-channel groups: ws[i][j][cl][f] = w[f0+f][i][j][c0+cl]; filters
+    // fastest across the threads, each reading 4 channels of one tap with a
+    // 16-byte load and storing them down 4 rows of ws, so that a warp's stores of
+    // one component cover consecutive filters
+    static __device__ __forceinline__ float4 w_load4(const FbcDirectArgs& a, int e, int c0, int f0) {
+        constexpr int C4 = CC / 4;
+        const int f = e % BN;
+        const int r = e / BN;   // (i*FW + j)*C4 + c4
+        const int tap = r / C4;
+        const int cl = (r - tap * C4) * 4;
+        const int n = f0 + f;
+        const int c = c0 + cl;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (n < a.nf && c < C) v = __ldg(reinterpret_cast<const float4*>(a.w + ((long long)n * FH * FW + tap) * C + c));
+        return v;
+    }
+    static __device__ __forceinline__ void w_store4(float* ws, int e, float4 v) {
+        constexpr int C4 = CC / 4;
+        const int f = e % BN;
+        const int r = e / BN;
+        const int tap = r / C4;
+        const int cl = (r - tap * C4) * 4;
+        float* dst = ws + (tap * CC + cl) * BNP + f;
+        dst[0] = v.x;
+        dst[BNP] = v.y;
+        dst[2 * BNP] = v.z;
+        dst[3 * BNP] = v.w;
+    }
+    // single values: forward with filters fastest (w[f0+f][i][j][c0+cl]); dL/dx
+    // with output channels fastest, reading along them: output channel f is the
+    // bank's depth index, input channel c its filter index, ws[i][j][cl][f] =
+    // w[c0+cl][FH-1-i][FW-1-j][f0+f]
+    static __device__ __forceinline__ float w_load1(const FbcDirectArgs& a, int e, int c0, int f0) {
+        const int f = e % BN;
+        const int r = e / BN;   // (i*FW + j)*CC + cl
+        const int tap = r / CC;
+        const int cl = r - tap * CC;
+        const int n = f0 + f;
+        const int c = c0 + cl;
+        if (n >= a.nf || c >= C) return 0.f;
+        if (!FLIP) return __ldg(a.w + ((long long)n * FH * FW + tap) * C + c);
+        const int i = tap / FW, j = tap - i * FW;
+        return __ldg(a.w + (((long long)c * FH + (FH - 1 - i)) * FW + (FW - 1 - j)) * a.nf + n);
+    }
+    static __device__ __forceinline__ void w_store1(float* ws, int e, float v) {
+        const int f = e % BN;
+        const int r = e / BN;
+        ws[r * BNP + f] = v;   // r = (i*FW + j)*CC + cl
     }
 
     // Stage input channels [c0, c0+CC) of the halo and the matching bank slice.
     static __device__ __forceinline__ void stage(const FbcDirectArgs& a, float* xs, float* ws, int c0,
                                                  int p0, int q0, int f0) {
         const int tid = threadIdx.x;
-        if (C % 4 == 0 && CC % 4 == 0) {
-            constexpr int C4 = CC / 4;
-            for (int e = tid; e < HR * HC * C4; e += NT) {
-                const int c4 = e % C4;
-                const int t = e / C4;
-                const int col = t % HC;
-                const int row = t / HC;
-                const int gy = p0 - a.pad_y + row;
-                const int gx = q0 - a.pad_x + col;
-                const int c = c0 + c4 * 4;
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (gy >= 0 && gy < a.in_h && gx >= 0 && gx < a.in_w && c < C) {
-                    const long long off = ((long long)gy * a.in_w + gx) * C + c;
-                    v = __ldg(reinterpret_cast<const float4*>(a.x + off));
-                    if (MASK) {
-                        const float4 mv = __ldg(reinterpret_cast<const float4*>(a.m + off));
-                        v.x = mask_val(v.x, mv.x, a.lo, a.hi);
-                        v.y = mask_val(v.y, mv.y, a.lo, a.hi);
-                        v.z = mask_val(v.z, mv.z, a.lo, a.hi);
-                        v.w = mask_val(v.w, mv.w, a.lo, a.hi);
-                    }
-                }
-                float* dst = xs + (row * CC + c4 * 4) * COLP + col;
-                dst[0] = v.x;
-                dst[COLP] = v.y;
-                dst[2 * COLP] = v.z;
-                dst[3 * COLP] = v.w;
-            }
+        if constexpr (XV) {
+            for (int e = tid; e < NXE; e += NT) x_store4(xs, e, x_load4(a, e, c0, p0, q0));
         } else {
-            for (int e = tid; e < HR * HC * CC; e += NT) {
-                const int cl = e % CC;
-                const int t = e / CC;
-                const int col = t % HC;
-                const int row = t / HC;
-                const int gy = p0 - a.pad_y + row;
-                const int gx = q0 - a.pad_x + col;
-                const int c = c0 + cl;
-                float v = 0.f;
-                if (gy >= 0 && gy < a.in_h && gx >= 0 && gx < a.in_w && c < C) {
-                    const long long off = ((long long)gy * a.in_w + gx) * C + c;
-                    v = __ldg(a.x + off);
-                    if (MASK) v = mask_val(v, __ldg(a.m + off), a.lo, a.hi);
-                }
-                xs[(row * CC + cl) * COLP + col] = v;
+            for (int e = tid; e < NXE; e += NT) x_store1(xs, e, x_load1(a, e, c0, p0, q0));
+        }
+        if constexpr (WV) {
+            for (int e = tid; e < NWE; e += NT) w_store4(ws, e, w_load4(a, e, c0, f0));
+        } else {
+            for (int e = tid; e < NWE; e += NT) w_store1(ws, e, w_load1(a, e, c0, f0));
+        }
+    }
+
+    // PF = 1: the next chunk's staging elements are loaded into registers before
+    // the current chunk is summed (their latency hides behind its FMAs) and
+    // stored into shared memory after it.
+    struct Pre {
+        float4 x4[XV ? PX : 1];
+        float x1[XV ? 1 : PX];
+        float4 w4[WV ? PW : 1];
+        float w1[WV ? 1 : PW];
+    };
+    static __device__ __forceinline__ void prefetch(const FbcDirectArgs& a, Pre& pre, int c0, int p0, int q0,
+                                                    int f0) {
+        const int tid = threadIdx.x;
+#pragma unroll
+        for (int k = 0; k < PX; ++k) {
+            const int e = tid + k * NT;
+            if constexpr (XV) {
+                if (e < NXE) pre.x4[k] = x_load4(a, e, c0, p0, q0);
+            } else {
+                if (e < NXE) pre.x1[k] = x_load1(a, e, c0, p0, q0);
             }
         }
-        if (!FLIP) {
-            // forward: ws[i][j][cl][f] = w[f0+f][i][j][c0+cl]; global reads along c
-            for (int e = tid; e < BN * FH * FW * CC; e += NT) {
-                const int cl = e % CC;
-                int t = e / CC;
-                const int j = t % FW;
-                t /= FW;
-                const int i = t % FH;
-                const int f = t / FH;
-                const int n = f0 + f;
-                const int c = c0 + cl;
-                const float v = (n < a.nf && c < C)
-                    ? __ldg(a.w + (((long long)n * FH + i) * FW + j) * C + c) : 0.f;
-                ws[((i * FW + j) * CC + cl) * BNP + f] = v;
+#pragma unroll
+        for (int k = 0; k < PW; ++k) {
+            const int e = tid + k * NT;
+            if constexpr (WV) {
+                if (e < NWE) pre.w4[k] = w_load4(a, e, c0, f0);
+            } else {
+                if (e < NWE) pre.w1[k] = w_load1(a, e, c0, f0);
             }
-        } else {
-            // dL/dx: output channel f is the bank's depth index, input channel c
-            // its filter index: ws[i][j][cl][f] = w[c0+cl][FH-1-i][FW-1-j][f0+f];
-            // global reads along f
-            for (int e = tid; e < BN * FH * FW * CC; e += NT) {
-                const int f = e % BN;
-                int t = e / BN;
-                const int j = t % FW;
-                t /= FW;
-                const int i = t % FH;
-                const int cl = t / FH;
-                const int n = f0 + f;
-                const int c = c0 + cl;
-                const float v = (n < a.nf && c < C)
-                    ? __ldg(a.w + (((long long)c * FH + (FH - 1 - i)) * FW + (FW - 1 - j)) * a.nf + n)
-                    : 0.f;
-                ws[((i * FW + j) * CC + cl) * BNP + f] = v;
+        }
+    }
+    static __device__ __forceinline__ void commit(const Pre& pre, float* xs, float* ws) {
+        const int tid = threadIdx.x;
+#pragma unroll
+        for (int k = 0; k < PX; ++k) {
+            const int e = tid + k * NT;
+            if constexpr (XV) {
+                if (e < NXE) x_store4(xs, e, pre.x4[k]);
+            } else {
+                if (e < NXE) x_store1(xs, e, pre.x1[k]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < PW; ++k) {
+            const int e = tid + k * NT;
+            if constexpr (WV) {
+                if (e < NWE) w_store4(ws, e, pre.w4[k]);
+            } else {
+                if (e < NWE) w_store1(ws, e, pre.w1[k]);
             }
         }
     }
@@ -185,11 +287,18 @@ struct FbcDirect {
 
         const float* xb = xs + (wr * TR) * CC * COLP + lane;
         const float* wb = ws + wf * TF;
+        Pre pre;
+        if constexpr (PF) stage(a, xs, ws, 0, p0, q0, f0);
 #pragma unroll 1
         for (int ch = 0; ch < NCHUNK; ++ch) {
-            if (ch > 0) __syncthreads();   // every thread is done reading the previous chunk
-            stage(a, xs, ws, ch * CC, p0, q0, f0);
-            __syncthreads();
+            if constexpr (PF) {
+                __syncthreads();   // chunk ch is staged
+                if (ch + 1 < NCHUNK) prefetch(a, pre, (ch + 1) * CC, p0, q0, f0);
+            } else {
+                if (ch > 0) __syncthreads();   // every thread is done reading the previous chunk
+                stage(a, xs, ws, ch * CC, p0, q0, f0);
+                __syncthreads();
+            }
 #pragma unroll 1
             for (int j = 0; j < FW; ++j) {
 #pragma unroll 2
@@ -239,6 +348,12 @@ struct FbcDirect {
                                 for (int f = 0; f < TF; ++f) acc[r][f] = fmaf(xv[r + i], wv[f], acc[r][f]);
                         }
                     }
+                }
+            }
+            if constexpr (PF) {
+                if (ch + 1 < NCHUNK) {
+                    __syncthreads();   // every thread is done reading chunk ch
+                    commit(pre, xs, ws);
                 }
             }
         }
@@ -593,16 +708,148 @@ struct FbcDwArgs {
     float lo, hi;
 };
 
+// 16-byte asynchronous copy global -> shared (cp.async, L2 only); bytes = 0
+// fills the destination with zeros and reads nothing.
+__device__ __forceinline__ void fbc_cp_async16(float* dst, const float* src, int bytes) {
+    unsigned d;
+    asm("{\n .reg .u64 t;\n cvta.to.shared.u64 t, %1;\n cvt.u32.u64 %0, t;\n}\n" : "=r"(d) : "l"(dst));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void fbc_cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void fbc_cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Shared memory holds two (g block, x segment) buffers: with 16-byte rows of g
+// and x (N % 4 == 0, C % 4 == 0) and no clamp mask, the blocks of a chunk stream
+// through them with cp.async, the next block's copies in flight while the current
+// one is summed (the same arithmetic in the same order as the synchronous path,
+// which the other cases take).
 template <int FH, int FW, int C, int TN, int NG, int QB, int MASK>
 struct FbcDw {
     static constexpr int NT = C * NG;
     static constexpr int NBLK = TN * NG;
     static constexpr int GS = QB * NBLK;
     static constexpr int XS = (QB + FW - 1) * C;
-    static constexpr int SMEM_BYTES = (GS + XS) * 4;
+    static constexpr int SMEM_BYTES = 2 * (GS + XS) * 4;
+
+    // Issue the copies of block (p, q0) into buffer (gs, xs): g[p][q0..q0+QB)[n0..n0+NBLK)
+    // and x[p+i][q0..q0+QB+FW-1)[0..C), zero-filled past the row ends.
+    static __device__ __forceinline__ void issue(const FbcDwArgs& a, float* gs, float* xs, int p, int q0, int i,
+                                                 int n0) {
+        const int tid = threadIdx.x;
+        const int nq = min(QB, a.Wo - q0);
+        const long long grow = (long long)p * a.Wo;
+        const long long xrow = (long long)(p + i) * a.W;
+        for (int e4 = tid; e4 < GS / 4; e4 += NT) {
+            const int qq = e4 / (NBLK / 4);
+            const int n = n0 + (e4 - qq * (NBLK / 4)) * 4;
+            const bool ok = qq < nq && n < a.N;
+            fbc_cp_async16(gs + e4 * 4, ok ? a.g + (grow + q0 + qq) * a.N + n : a.g, ok ? 16 : 0);
+        }
+        for (int e4 = tid; e4 < XS / 4; e4 += NT) {
+            const int k = (e4 * 4) / C;
+            const bool ok = k < nq + FW - 1 && q0 + k < a.W;
+            fbc_cp_async16(xs + e4 * 4, ok ? a.x + (xrow + q0) * C + e4 * 4 : a.x, ok ? 16 : 0);
+        }
+    }
+
+    // TN x FW outer-product terms of one staged block into ra (the synchronous
+    // path's inner loop).
+    static __device__ __forceinline__ void sum_block(const float* gs, const float* xs, int ng, int c,
+                                                     float (&ra)[TN][FW]) {
+        if (ng * TN >= NBLK) return;
+        float win[FW];
+#pragma unroll
+        for (int k = 0; k < FW - 1; ++k) win[k] = xs[k * C + c];
+        const float* gp = gs + ng * TN;
+#pragma unroll 1
+        for (int qb = 0; qb < QB; qb += FW) {
+#pragma unroll
+            for (int s = 0; s < FW; ++s) {
+                const int qq = qb + s;
+                if (qq < QB) {
+                    win[(s + FW - 1) % FW] = xs[(qq + FW - 1) * C + c];
+                    float gv[TN];
+                    if constexpr ((TN & 3) == 0) {
+#pragma unroll
+                        for (int t4 = 0; t4 < TN; t4 += 4) {
+                            const float4 g4 = *reinterpret_cast<const float4*>(gp + qq * NBLK + t4);
+                            gv[t4] = g4.x; gv[t4 + 1] = g4.y; gv[t4 + 2] = g4.z; gv[t4 + 3] = g4.w;
+                        }
+                    } else {
+#pragma unroll
+                        for (int t = 0; t < TN; ++t) gv[t] = gp[qq * NBLK + t];
+                    }
+#pragma unroll
+                    for (int t = 0; t < TN; ++t)
+#pragma unroll
+                        for (int k = 0; k < FW; ++k) ra[t][k] = fmaf(gv[t], win[(s + k) % FW], ra[t][k]);
+                }
+            }
+        }
+    }
+
+    static __device__ __forceinline__ void run_async(const FbcDwArgs& a, float* smem, int chunk, int i,
+                                                     int nblk) {
+        const int tid = threadIdx.x;
+        const int ng = tid / C;
+        const int c = tid - ng * C;
+        const int n0 = nblk * NBLK;
+        const int pb = chunk * a.rows_per_chunk;
+        int pe = pb + a.rows_per_chunk;
+        if (pe > a.Ho) pe = a.Ho;
+        const int qblocks = (a.Wo + QB - 1) / QB;
+        const int nb = (pe - pb) * qblocks;   // blocks (row, column block) of this chunk, in order
+        float tot[TN][FW], ra[TN][FW];
+#pragma unroll
+        for (int t = 0; t < TN; ++t)
+#pragma unroll
+            for (int k = 0; k < FW; ++k) tot[t][k] = ra[t][k] = 0.f;
+        if (nb > 0) issue(a, smem, smem + GS, pb, 0, i, n0);
+        fbc_cp_async_commit();
+        for (int b = 0; b < nb; ++b) {
+            const int buf = b & 1;
+            if (b + 1 < nb) {
+                const int p1 = pb + (b + 1) / qblocks, q1 = ((b + 1) % qblocks) * QB;
+                float* nbuf = smem + (buf ^ 1) * (GS + XS);
+                issue(a, nbuf, nbuf + GS, p1, q1, i, n0);
+            }
+            fbc_cp_async_commit();
+            fbc_cp_async_wait<1>();   // block b has landed (this thread's copies)
+            __syncthreads();          // ... and every thread's
+            const float* cur = smem + buf * (GS + XS);
+            sum_block(cur, cur + GS, ng, c, ra);
+            if ((b + 1) % qblocks == 0) {
+                // the row is complete: two-level summation as in the synchronous path
+#pragma unroll
+                for (int t = 0; t < TN; ++t)
+#pragma unroll
+                    for (int k = 0; k < FW; ++k) {
+                        tot[t][k] += ra[t][k];
+                        ra[t][k] = 0.f;
+                    }
+            }
+            __syncthreads();   // every thread is done with buffer `buf` before it is refilled
+        }
+        fbc_cp_async_wait<0>();
+#pragma unroll
+        for (int t = 0; t < TN; ++t) {
+            const int n = n0 + ng * TN + t;
+            if (n >= a.N) continue;
+#pragma unroll
+            for (int k = 0; k < FW; ++k)
+                a.part[((((long long)chunk * a.N + n) * FH + i) * FW + k) * C + c] = tot[t][k];
+        }
+    }
 
     static __device__ __forceinline__ void run(const FbcDwArgs& a, float* smem, int chunk, int i,
                                                int nblk) {
+        if constexpr (!MASK && (C % 4) == 0) {
+            if ((a.N & 3) == 0) {
+                run_async(a, smem, chunk, i, nblk);
+                return;
+            }
+        }
         const int tid = threadIdx.x;
         const int ng = tid / C;
         const int c = tid - ng * C;

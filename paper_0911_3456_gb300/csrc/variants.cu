@@ -47,8 +47,8 @@ size_t direct_smem_bytes(const DirectTile& t, int fh, int fw, int c) {
 
 std::string direct_tile_spec(const DirectTile& t) {
     char b[128];
-    snprintf(b, sizeof b, "direct:tr=%d,tf=%d,wr=%d,wf=%d,cc=%d%s", t.tr, t.tf, t.wr, t.wf, t.cc,
-             t.pk ? ",pk=1" : "");
+    snprintf(b, sizeof b, "direct:tr=%d,tf=%d,wr=%d,wf=%d,cc=%d%s%s", t.tr, t.tf, t.wr, t.wf, t.cc,
+             t.pk ? ",pk=1" : "", t.pf ? ",pf=1" : "");
     std::string out = b;
     if (t.ks > 1) out += ",ks=" + std::to_string(t.ks) + ",wq=" + std::to_string(t.wq);
     if (t.sh) out += ",sh=1";
@@ -57,6 +57,7 @@ std::string direct_tile_spec(const DirectTile& t) {
 
 static bool ks_tile_ok(const DirectTile& t) {
     if (t.ks == 1) return t.wq == 1 && t.sh == 0;
+    if (t.pf) return false;   // the K-split tile stages the whole depth once
     if (t.sh != 0 && t.sh != 1) return false;
     if (t.ks != 4 && t.ks != 8 && t.ks != 16 && t.ks != 32) return false;
     // whole depth in one stage; the register block splits evenly over the ks lanes
@@ -64,7 +65,7 @@ static bool ks_tile_ok(const DirectTile& t) {
 }
 
 bool parse_direct_spec(const std::string& s, DirectTile* t) {
-    // "direct:tr=R,tf=F,wr=WR,wf=WF" then optionally ",cc=CC", ",pk=P",
+    // "direct:tr=R,tf=F,wr=WR,wf=WF" then optionally ",cc=CC", ",pk=P", ",pf=F",
     // ",ks=K,wq=Q" and ",sh=S", in that order; anything else left over rejects
     // the spec
     DirectTile d;
@@ -83,6 +84,11 @@ bool parse_direct_spec(const std::string& s, DirectTile* t) {
     u = -1;
     if (strncmp(rest, ",pk=", 4) == 0) {
         if (sscanf(rest, ",pk=%d%n", &d.pk, &u) != 1 || u < 0) return false;
+        rest += u;
+    }
+    u = -1;
+    if (strncmp(rest, ",pf=", 4) == 0) {
+        if (sscanf(rest, ",pf=%d%n", &d.pf, &u) != 1 || u < 0 || (d.pf != 0 && d.pf != 1)) return false;
         rest += u;
     }
     u = -1;
@@ -134,7 +140,7 @@ std::string direct_kernel_source(const DirectProblem& pr, const DirectTile& t,
     } else {
         o << "typedef FbcDirect<" << pr.fh << "," << pr.fw << "," << pr.c << "," << t.tr << ","
           << t.tf << "," << t.wr << "," << t.wf << "," << pr.flip << "," << pr.epi << "," << pr.mask
-          << "," << t.chunk(pr.c) << "," << t.pk << "> FbcThis;\n";
+          << "," << t.chunk(pr.c) << "," << t.pk << "," << t.pf << "> FbcThis;\n";
     }
     o << "static_assert(FbcThis::SMEM_BYTES == " << direct_smem_bytes(t, pr.fh, pr.fw, pr.c)
       << ", \"host and device disagree on the shared-memory size\");\n";
@@ -147,7 +153,7 @@ std::string direct_kernel_source(const DirectProblem& pr, const DirectTile& t,
 }
 
 size_t dw_smem_bytes(int fw, int c, int tn, int ng, int qb) {
-    return (size_t)(qb * tn * ng + (qb + fw - 1) * c) * 4;
+    return 2 * (size_t)(qb * tn * ng + (qb + fw - 1) * c) * 4;   // two (g, x) buffers
 }
 
 std::string dw_kernel_source(int fh, int fw, int c, int tn, int ng, int qb, int mask,
@@ -221,8 +227,8 @@ std::vector<DirectTile> direct_candidates(const DirectProblem& pr, size_t smem_l
         if (4 * (cpad - pr.c) > cpad || cpad / ks > 8) continue;
         for (int tr : {2, 4, 8, 16})
             for (int tf : {4, 8, 16})
-                for (int wq : {1, 2, 4, 8})
-                    for (int wr : {1, 2, 4, 8})
+                for (int wq : {1, 2, 3, 4, 8})
+                    for (int wr : {1, 2, 3, 4, 6, 8})
                         for (int wf : {1, 2, 4})
                             for (int sh : {0, 1}) {
                                 DirectTile t{tr, tf, wr, wf, 0};
@@ -325,8 +331,9 @@ std::vector<DirectTile> direct_ranked(const DirectProblem& pr, size_t smem_limit
     return out;
 }
 
-std::vector<std::string> direct_tuning_specs(const std::vector<DirectTile>& ranked, int topk) {
+std::vector<std::string> direct_tuning_specs(const std::vector<DirectTile>& ranked, int topk, int depth) {
     const bool twins = env_str("FBCORR_TUNE_PK", "1") != "0";
+    const bool pf = depth > 0 && env_str("FBCORR_TUNE_PF", "1") != "0";
     std::vector<std::string> specs;
     // the first topk lane-per-column tiles and, beside them, the first topk / 2
     // K-split tiles (their model scores are not comparable enough to let one
@@ -339,6 +346,12 @@ std::vector<std::string> direct_tuning_specs(const std::vector<DirectTile>& rank
         specs.push_back(direct_tile_spec(a));
         if (twins) {
             a.pk = 1;
+            specs.push_back(direct_tile_spec(a));
+        }
+        if (pf && a.ks == 1 && a.chunk(depth) < depth) {
+            // several channel chunks: the register-prefetch form (packed pairs)
+            a.pk = 1;
+            a.pf = 1;
             specs.push_back(direct_tile_spec(a));
         }
     }
@@ -376,6 +389,7 @@ std::string kname_for(const char* base, const DirectProblem& pr, const DirectTil
     snprintf(b, sizeof b, "%s_f%dx%d_c%d_t%d_%d_%d_%d_cc%d_fl%d_e%d_m%d%s", base, pr.fh, pr.fw, pr.c,
              t.tr, t.tf, t.wr, t.wf, t.chunk(pr.c), pr.flip, pr.epi, pr.mask, t.pk ? "_pk1" : "");
     std::string name = b;
+    if (t.pf) name += "_pf1";
     if (t.ks > 1) name += "_ks" + std::to_string(t.ks) + "q" + std::to_string(t.wq) + (t.sh ? "h" : "");
     return pr.epi == 2 ? name + "_u" + snippet_tag(pr.snippet) : name;
 }
@@ -421,7 +435,8 @@ fbcorr_status_t tune_direct_problem(const DeviceInfo& dev, const DirectProblem& 
     // Time the top candidates of one direct-correlation problem (and, when asked,
     // the prebuilt default kernel) on patterned buffers; keep the fastest.
     std::vector<DirectTile> ranked = direct_ranked(pr, smem_cap, dev.sm_count, threads, max_block);
-    std::vector<std::string> specs = direct_tuning_specs(ranked, topk);
+    // the batched kernel (fixed CTA size, two CTAs per SM) takes no prefetch variants
+    std::vector<std::string> specs = direct_tuning_specs(ranked, topk, threads > 0 ? 0 : pr.c);
     if (specs.empty() && !include_default)
         return set_error(FBCORR_ERR_UNSUPPORTED, "no %s candidate fits", what);
     {

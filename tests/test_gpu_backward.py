@@ -164,3 +164,28 @@ def test_differentiation_config_full():
     assert normwise_rel(host(y), oracle.fwd(wl.x, wl.w)) <= TOL
     assert normwise_rel(host(dx), oracle.bwd_input(wl.g, wl.w, wl.x.shape)) <= TOL
     assert normwise_rel(host(dw), oracle.bwd_filt(wl.x, wl.g, wl.w.shape)) <= TOL
+
+
+@pytest.mark.parametrize("dx_spec", ["direct:tr=4,tf=4,wr=4,wf=2,cc=8,pk=1",
+                                     "direct:tr=2,tf=4,wr=2,wf=4,cc=8,pk=1"])
+def test_dx_register_prefetch_is_bit_identical(dx_spec, monkeypatch):
+    """The dL/dx kernel (flipped bank, 24 gradient channels in 8-channel
+    chunks) with the register prefetch of the next chunk gives the plain
+    kernel's bits, with and without the clamp mask, and the oracle's gradient."""
+    torch = torch_cuda()
+    shape = (40, 52, 16, 24, 7, 7)
+    wl = inputs.random_case(1100, *shape, with_g=True)
+    for clamp in (None, (-0.5, 0.5)):
+        outs = []
+        for pf in ("", ",pf=1"):
+            monkeypatch.setenv("FBCORR_DX_VARIANT", dx_spec + pf)
+            p = _plan(shape, clamp)
+            x, w, g = dev(wl.x, torch), dev(wl.w, torch), dev(wl.g, torch)
+            y = p.forward(x, w) if clamp else None
+            dx, _ = p.backward(x, w, g, y, need_dw=False)
+            torch.cuda.synchronize()
+            assert p.info()["dx"]["spec"] == dx_spec + pf
+            outs.append(host(dx))
+        assert np.array_equal(outs[0], outs[1])
+        if clamp is None:
+            assert normwise_rel(outs[1], oracle.bwd_input(wl.g, wl.w, wl.x.shape)) <= TOL

@@ -227,3 +227,23 @@ def test_paper_table_shapes_sampled(row):
             ref = oracle.fwd(wl.x[r:r + fh], wl.w)[0]
             assert np.abs(y[r] - ref).max() <= TOL_F32 * np.abs(ref).max(), (spec, r)
         assert np.abs(y[tuple(idx.T)] - ref_pts).max() <= TOL_F32 * np.abs(ref_pts).max(), spec
+
+
+@pytest.mark.parametrize("shape,spec", [
+    ((51, 77, 8, 27, 5, 4), "direct:tr=4,tf=8,wr=2,wf=2,cc=4,pk=1"),      # two 4-channel chunks
+    ((41, 70, 10, 12, 3, 5), "direct:tr=8,tf=4,wr=3,wf=1,cc=4,pk=1"),     # depth 10: scalar staging, ragged chunk
+    ((64, 40, 32, 40, 5, 5), "direct:tr=2,tf=4,wr=4,wf=2,cc=8,pk=1"),     # four 8-channel chunks
+], ids=["c8cc4", "c10cc4", "c32cc8"])
+def test_register_prefetch_is_bit_identical(shape, spec):
+    """pf=1 loads the next channel chunk into registers while the current one is
+    summed and stores it afterwards: the same sums in the same order, so the
+    output equals the plain tile's bit for bit (with and without the clamp)."""
+    torch = torch_cuda()
+    wl = inputs.random_case(520, *shape)
+    for clamp in (None, (-0.5, 0.5)):
+        y0, _ = _run(torch, wl.x, wl.w, clamp=clamp, spec=spec)
+        y1, p1 = _run(torch, wl.x, wl.w, clamp=clamp, spec=spec + ",pf=1")
+        assert p1.info()["fwd"]["kernel"].endswith("_pf1")
+        assert np.array_equal(y0, y1)
+        ref = oracle.fwd(wl.x, wl.w, epilogue=clamp)
+        assert np.abs(y1 - ref).max() <= TOL_F32 * np.abs(oracle.fwd(wl.x, wl.w)).max()
