@@ -2,9 +2,9 @@
 // NVRTC for sm_103a with the chunk-plane count NC, the split mode, the filter
 // width FW, the taps per B stage BT, the epilogue warp count EW, the fused
 // conversion switch FUSE (and its converter warps CW), the snippet switch USER,
-// and the epilogue store path TS (with SB staging slots) baked in.  Embedded
-// as a string into libfbcorr and prefixed with tc_params.h and rtcg_ptx.cuh;
-// self-contained (no system headers).
+// the epilogue store path TS (with SB staging slots) and the resident-bank
+// switch RES baked in.  Embedded as a string into libfbcorr and prefixed with
+// tc_params.h and rtcg_ptx.cuh; self-contained (no system headers).
 //
 // The correlation of Sec. 6.2 as an implicit GEMM: for every filter tap (i, j)
 //   Y[m, n] += sum_d X[m + i*W + j, d] * Wt[n, i, j, d]
@@ -54,6 +54,14 @@
 // issues hi*lo + lo*hi, then hi*hi, into the same FP32 accumulator (the lo*lo
 // term, ~2^-16 relative, is dropped).
 //
+// Resident bank (RES = 1): every 128-row tile otherwise streams the whole bank
+// slice of its filter tile through the B ring (400 KB for 256 filters of
+// 5x5x32 in BF16), and in plain BF16 the refills, not the tensor core, set the
+// pace.  With RES the B ring holds every tap of one filter tile (nb = fh *
+// stages per filter row), the producer loads it once, and the CTA walks pixel
+// tiles under it: CTA b keeps filter tile b % ntn and takes the pixel tiles
+// b / ntn, b / ntn + gridDim.x / ntn, ... (the grid is a multiple of ntn).
+//
 // Tail halves: tiles t >= nfull, the last partial round of a single 256-wide
 // filter tile, run as two 128-column work items each (instruction N = 128, B
 // from half-width planes), so that round keeps twice as many SMs busy for half
@@ -89,7 +97,7 @@ __device__ __forceinline__ void fbc_issue_tap(fbc_u32 d_tmem, fbc_u64 ad, fbc_u6
 }
 
 // ---------------------------------------------------------------- the kernel body
-template <int NC, int SPLIT, int FW, int BT, int EW, int FUSE, int CW, int USER, int TS, int SB>
+template <int NC, int SPLIT, int FW, int BT, int EW, int FUSE, int CW, int USER, int TS, int SB, int RES>
 __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
     constexpr int NST = (FW + BT - 1) / BT;          // B stages per filter row
     constexpr int L = FBC_TC_TILE_M + FW - 1;        // slab pixels per filter row
@@ -148,10 +156,13 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
     // last partial round, run as two work items each, one per 128-column half of
     // the filter tile, so that round occupies twice as many SMs for half as long;
     // a half takes its B operand from the half-width planes whi2 / wlo2.
+    // RES: the CTA's filter tile is blockIdx.x % ntn and its pixel tiles are
+    // unit, unit + nunits, ... with unit = blockIdx.x / ntn
     const int nsched = P.mtiles * P.ntn;
-    const int unit = (int)blockIdx.x;
-    const int nunits = (int)gridDim.x;
-    const int nwork = P.nfull + 2 * (nsched - P.nfull);
+    const int res_fi = RES ? (int)blockIdx.x % P.ntn : 0;
+    const int unit = RES ? (int)blockIdx.x / P.ntn : (int)blockIdx.x;
+    const int nunits = RES ? (int)gridDim.x / P.ntn : (int)gridDim.x;
+    const int nwork = RES ? P.mtiles : P.nfull + 2 * (nsched - P.nfull);
     const int my_tiles = unit < nwork ? (nwork - 1 - unit) / nunits + 1 : 0;   // work items
     struct Item {
         int tile;    // pixel tile t % mtiles of filter tile t / mtiles
@@ -163,8 +174,10 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
     auto item_of = [&](int k) -> Item {
         const int w = unit + k * nunits;
         Item it;
-        it.half = w >= P.nfull;
-        if (!it.half) {
+        it.half = !RES && w >= P.nfull;
+        if (RES) {
+            it.tile = res_fi * P.mtiles + w;
+        } else if (!it.half) {
             it.tile = w;
         } else {
             it.tile = P.nfull + ((w - P.nfull) >> 1);
@@ -234,6 +247,8 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
                     ++next_a;
                 }
                 if (!ok) break;
+                // RES: the B stages of the first item's filter rows fill the ring once
+                if (RES && r >= P.fh) continue;
                 const Item it = item_of(r / P.fh);
                 const long long tap_bytes = (long long)NC * it.nt * 16;   // = the item's b_half
                 const long long woff = it.wbase + (long long)((r % P.fh) * FW) * tap_bytes;
@@ -305,16 +320,24 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
                     if (!(ok = fbc_wait(a_full0 + 8u * as, aph, P, abort_flag, FBC_TC_ERR_WAIT_A))) break;
 #pragma unroll
                     for (int s = 0; s < NST; ++s) {
-                        if (!(ok = fbc_wait(b_full0 + 8u * bs, bph, P, abort_flag, FBC_TC_ERR_WAIT_B))) break;
-                        const fbc_u64 bdesc = fbc_smem_desc(sbase + P.b_off + (fbc_u32)bs * P.b_stage, bplane_i, 128);
+                        // RES: stage (filter row i, s) stays in slot i * NST + s; its
+                        // copy is waited for by the first work item only
+                        const int slot = RES ? i * NST + s : bs;
+                        if (!RES || k == 0)
+                            if (!(ok = fbc_wait(b_full0 + 8u * slot, RES ? 0u : bph, P, abort_flag, FBC_TC_ERR_WAIT_B)))
+                                break;
+                        const fbc_u64 bdesc =
+                            fbc_smem_desc(sbase + P.b_off + (fbc_u32)slot * P.b_stage, bplane_i, 128);
 #pragma unroll
                         for (int t = 0; t < BT; ++t)
                             if (s * BT + t < FW)
                                 fbc_issue_tap<NC, SPLIT>(d_tmem, adesc + (fbc_u64)(s * BT + t), bdesc + (fbc_u64)t * btap,
                                                          ak, bk, alo, blo, idesc, accumulate);
                         issued = true;
-                        fbc_umma_commit(b_empty0 + 8u * bs);
-                        if (++bs == P.nb) { bs = 0; bph ^= 1; }
+                        if constexpr (!RES) {
+                            fbc_umma_commit(b_empty0 + 8u * bs);
+                            if (++bs == P.nb) { bs = 0; bph ^= 1; }
+                        }
                     }
                     if (!ok) break;
                     fbc_umma_commit(a_empty0 + 8u * as);

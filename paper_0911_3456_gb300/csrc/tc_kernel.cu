@@ -157,6 +157,7 @@ struct TcConfig {
     int cw = 0;                        // converter warps (fuse = 1, 2): 4 or 8
     int ts = 0;                        // epilogue stores: 0 direct, 32 tiled (32-pixel boxes)
     int sb = 0;                        // staging slots per epilogue warp (ts = 32): 1..3
+    int rs = 0;                        // 1: the B ring holds the CTA's whole filter tile (resident bank)
 };
 
 struct TcPlan {
@@ -191,6 +192,7 @@ std::string tc_kernel_name(int nc, int split, int fw, const TcConfig& c, const s
     snprintf(b, sizeof b, "fbc_tc_c%d_s%d_f%d_b%d_e%d_z%d_w%d", nc, split, fw, c.bt, c.ew, c.fuse, c.cw);
     std::string name = b;
     if (c.ts) name += "_t" + std::to_string(c.ts) + "s" + std::to_string(c.sb);
+    if (c.rs) name += "_r";
     return snippet.empty() ? name : name + "_u" + snippet_tag(snippet);
 }
 
@@ -207,7 +209,7 @@ std::string tc_kernel_source(int nc, int split, int fw, const TcConfig& c, const
       << tc_kernel_name(nc, split, fw, c, snippet) << "(const __grid_constant__ FbcTcParams P) {\n"
       << "  fbc_tc_corr_body<" << nc << "," << split << "," << fw << "," << c.bt << "," << c.ew << ","
       << c.fuse << "," << c.cw << "," << (snippet.empty() ? 0 : 1) << "," << c.ts << "," << (c.ts ? c.sb : 1)
-      << ">(P);\n}\n";
+      << "," << c.rs << ">(P);\n}\n";
     return o.str();
 }
 
@@ -267,7 +269,9 @@ bool tc_layout(TcPlan* p, const TcConfig& c, bool commit) {
     filter_tiles(p->N, c.ntmax, &nt, &ntn);
     const long long mvirt = (long long)Ho * p->W;
     const int mtiles = (int)((mvirt + kTileM - 1) / kTileM);
-    const int lp = a_plane_pixels(kTileM + p->fw - 1, nc);
+    // the padding spreads the converters' writes over the bank groups; slabs the
+    // pre-pass planes fill by bulk copies (fuse = 0) need none
+    const int lp = c.fuse ? a_plane_pixels(kTileM + p->fw - 1, nc) : (kTileM + p->fw - 1 + 7) / 8 * 8;
     const int halves = p->split ? 2 : 1;
     const uint32_t a_slot = (uint32_t)align_up((size_t)nc * lp * 16 * halves, 128);
     if (c.bt < 1 || c.bt > p->fw || (c.ew != 4 && c.ew != 8)) return false;
@@ -277,6 +281,13 @@ bool tc_layout(TcPlan* p, const TcConfig& c, bool commit) {
     const uint32_t raw_slot = (uint32_t)align_up((size_t)(kTileM + p->fw - 1) * p->D * 4, 128);
     if (c.na < 2 || c.nb < 2 || (c.fuse == 2 && c.nr < 2)) return false;
     if (!ts_ok(c.ts, c.sb, p->W, p->N, nt)) return false;
+    // resident bank: the ring holds every stage of the filter tile, each CTA
+    // keeps one filter tile, and there are at least as many SMs as filter tiles
+    if (c.rs != 0 && (c.rs != 1 || c.nb != p->fh * ((p->fw + c.bt - 1) / c.bt) || ntn > std::max(1, p->sm_count)))
+        return false;
+    // the barrier table: a_full / a_empty per A slot, b_full / b_empty per B stage,
+    // two accumulator pairs, the drain barrier, raw_full / raw_empty per raw slot
+    if (8 * (2 * c.na + 2 * c.nb + 5 + 2 * c.nr) > 512) return false;
     // staging: a 1024-byte aligned run of ew * sb boxes placed after the barriers
     const size_t staging = c.ts ? (size_t)c.ew * c.sb * FBC_TC_ST_BOX + 1024 : 0;
     const size_t need = (size_t)c.na * a_slot + (size_t)c.nb * b_stage + (size_t)c.nr * raw_slot + 512 + staging;
@@ -293,7 +304,7 @@ bool tc_layout(TcPlan* p, const TcConfig& c, bool commit) {
     // of the CTAs idle, its tiles run as two 128-column halves each
     const int grid_full = std::min(mtiles * ntn, std::max(1, p->sm_count));
     const int rem = (mtiles * ntn) % grid_full;
-    const bool tail_halves = ntn == 1 && nt == 256 && rem > 0 && 2 * rem <= grid_full &&
+    const bool tail_halves = !c.rs && ntn == 1 && nt == 256 && rem > 0 && 2 * rem <= grid_full &&
                              env_str("FBCORR_TAIL_HALVES", "1") != "0";
     k.nfull = tail_halves ? mtiles * ntn - rem : mtiles * ntn;
     k.lp = lp; k.na = c.na; k.nb = c.nb;
@@ -337,8 +348,12 @@ bool tc_layout(TcPlan* p, const TcConfig& c, bool commit) {
     const long long wblocks = ((long long)ntn * p->fh * p->fw * nt + 255) / 256;
     if (c.fuse) sp.xblocks = 0;   // x is converted inside the correlation kernel
     p->split_blocks = (int)(sp.xblocks + wblocks);
-    // one CTA per SM (the 512 TMEM columns)
-    p->grid = std::min(mtiles * ntn, std::max(1, p->sm_count));
+    // one CTA per SM (the 512 TMEM columns); resident bank: a multiple of the
+    // filter-tile count, each group of ntn CTAs sharing the pixel tiles
+    if (c.rs)
+        p->grid = ntn * std::min(mtiles, std::max(1, p->sm_count / ntn));
+    else
+        p->grid = std::min(mtiles * ntn, std::max(1, p->sm_count));
     return true;
 }
 
@@ -389,6 +404,28 @@ std::vector<TcConfig> tc_candidate_configs(TcPlan* p) {
                             }
             }
     }
+    // resident bank (rs = 1): the ring holds all fh * ceil(fw / bt) stages of a
+    // filter tile, loaded once per CTA; offered wherever a filter tile fits in
+    // shared memory beside the A slots (plain BF16 of the headline shape: 128
+    // filters of 5x5x32 = 200 KB)
+    for (int ntmax : widths)
+        for (int fuse = 2; fuse >= 0; --fuse)
+            for (int cw : fuse ? std::vector<int>{8, 4} : std::vector<int>{0}) {
+                if (!fuse_ok(fuse, cw, p->D, p->nc, p->fw)) continue;
+                for (int nr : fuse == 2 ? std::vector<int>{3, 2} : std::vector<int>{0})
+                    for (int bt = std::min(p->fw, 5); bt >= 1; --bt)
+                        for (int ew : {8, 4})
+                            for (int na = 2; na <= 3; ++na)
+                                for (int ts : {0, 1, 32}) {
+                                    if (ew != 8 && ts == 1) continue;
+                                    TcConfig c{na, 0, ntmax, bt, ew, fuse, nr, cw};
+                                    c.ts = ts;
+                                    c.sb = ts ? 1 : 0;
+                                    c.rs = 1;
+                                    c.nb = p->fh * ((p->fw + bt - 1) / bt);
+                                    if (tc_layout(p, c, false)) out.push_back(c);
+                                }
+            }
     return out;
 }
 
@@ -398,6 +435,7 @@ std::string format_spec(const TcConfig& c) {
              c.bt, c.ew, c.fuse, c.nr, c.cw);
     std::string out = b;
     if (c.ts) out += ",ts=" + std::to_string(c.ts) + ",sb=" + std::to_string(c.sb);
+    if (c.rs) out += ",rs=1";
     return out;
 }
 
@@ -407,11 +445,15 @@ bool parse_tc_spec(const std::string& s, TcConfig* c) {
     const int n = sscanf(s.c_str(), "tcgen05:na=%d,nb=%d,nt=%d,bt=%d,ew=%d,fz=%d,nr=%d,cw=%d%n", &t.na, &t.nb,
                          &t.ntmax, &t.bt, &t.ew, &t.fuse, &t.nr, &t.cw, &used);
     if (n != 8) return false;
-    // optional suffix: staged / tiled stores
+    // optional suffixes, in this order: staged / tiled stores, resident bank
     int used2 = 0;
     if (sscanf(s.c_str() + used, ",ts=%d,sb=%d%n", &t.ts, &t.sb, &used2) == 2) {
         if ((t.ts != 32 && t.ts != 1) || t.sb < 1 || t.sb > 3 || (t.ts == 1 && t.sb != 1)) return false;
         used += used2;
+    }
+    if (s.compare(used, std::string::npos, ",rs=1") == 0) {
+        t.rs = 1;
+        used += 5;
     }
     if (used != (int)s.size()) return false;
     if ((t.fuse == 0) != (t.cw == 0) || (t.cw != 0 && t.cw != 4 && t.cw != 8)) return false;

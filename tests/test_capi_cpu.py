@@ -184,6 +184,8 @@ def test_ksplit_tiles_compile(lib, D, N, spec):
     (32, 5, b"tcgen05:na=3,nb=2,nt=256,bt=5,ew=8,fz=1,nr=0,cw=8,ts=32,sb=1"),       # tiled bulk stores
     (16, 3, b"tcgen05:na=3,nb=4,nt=256,bt=2,ew=8,fz=2,nr=2,cw=8,ts=1,sb=1"),        # staged stores
     (32, 5, b"tcgen05:na=2,nb=3,nt=256,bt=1,ew=4,fz=1,nr=0,cw=4,ts=32,sb=3"),       # three staging slots
+    (32, 5, b"tcgen05:na=2,nb=5,nt=128,bt=5,ew=4,fz=1,nr=0,cw=8,rs=1"),             # resident bank
+    (16, 3, b"tcgen05:na=3,nb=3,nt=256,bt=3,ew=8,fz=2,nr=2,cw=8,ts=1,sb=1,rs=1"),   # resident, staged stores
 ])
 def test_tensor_core_kernels_compile(lib, D, f, spec):
     """The run-time generated tcgen05 kernel of a spec compiles for sm_103a in
@@ -206,6 +208,8 @@ def test_tensor_core_kernels_compile(lib, D, f, spec):
     (32, 5, b"tcgen05:na=2,nb=4,nt=256,bt=2,ew=8,fz=1,nr=0,cw=8,ts=1,sb=2", 1),    # the staged path has one slot
     (32, 5, b"tcgen05:na=2,nb=4,nt=256,bt=2,ew=8,fz=1,nr=0,cw=8,sb=1,ts=1", 1),    # suffix fields in order
     (32, 5, b"tcgen05:na=2,nb=4,nt=256,bt=2,ew=8,fz=1,nr=0,cw=8,ts=1,sb=1,", 1),   # nothing after the suffix
+    (32, 5, b"tcgen05:na=2,nb=5,nt=128,bt=5,ew=4,fz=1,nr=0,cw=8,rs=2", 1),          # rs=1 only
+    (32, 5, b"tcgen05:na=2,nb=5,nt=128,bt=5,ew=8,fz=1,nr=0,cw=8,rs=1,ts=1,sb=1", 1),   # stores before rs
 ])
 def test_tensor_core_spec_refusals(lib, D, f, spec, status):
     log = ctypes.create_string_buffer(1 << 16)

@@ -335,3 +335,45 @@ def test_fused_conversion_limits():
     assert ",fz=2," in p.info()["fwd"]["spec"]
     with pytest.raises(C.FbcorrError):
         p.set_variant("tcgen05:na=2,nb=2,nt=256,bt=1,ew=4,fz=1,nr=0,cw=8")
+
+
+@pytest.mark.parametrize("mode", ["bf16", "bf16x3"])
+@pytest.mark.parametrize("shape", [(37, 96, 16, 160, 3, 3), (21, 140, 32, 40, 3, 5), (40, 64, 32, 256, 5, 5),
+                                   (9, 9, 12, 3, 9, 9)], ids=lambda s: "x".join(map(str, s)))
+def test_resident_bank_bit_exact(mode, shape):
+    """rs=1 loads the B ring once with every tap of the CTA's filter tile and
+    walks pixel tiles under it (two filter tiles: the CTAs split into two
+    groups): the same MMAs in the same order as the streamed ring, so the same
+    bits; on integer inputs the oracle's.  Shapes whose filter tile does not
+    fit in shared memory are refused."""
+    torch = torch_cuda()
+    from paper_0911_3456_gb300 import _capi as C
+    from paper_0911_3456_gb300.api import Plan
+    H, W, D, N, fh, fw = shape
+    p = Plan((H, W, D), (N, fh, fw, D), mode)
+    res = [s for s in p.candidates() if s.endswith(",rs=1")]
+    ran = 0
+    for nt in (256, 128):
+        specs = [s for s in res if f",nt={nt}," in s]
+        if not specs:
+            continue
+        spec = specs[0]
+        streamed = spec.split(",nb=")[0] + ",nb=2," + spec.split(",nb=")[1].split(",", 1)[1]
+        streamed = streamed.replace(",rs=1", "")
+        for kind in ("int", "real"):
+            wl = inputs.random_case(1900, *shape, kind=kind)
+            x, w = dev(wl.x, torch), dev(wl.w, torch)
+            p.set_variant(spec)
+            y_res = host(p.forward(x, w))
+            assert p.device_status() == 0
+            try:
+                p.set_variant(streamed)
+            except C.FbcorrError:
+                continue
+            y_str = host(p.forward(x, w))
+            assert np.array_equal(y_res, y_str), (spec, streamed)
+            if kind == "int":
+                assert np.array_equal(y_res, oracle.fwd(wl.x, wl.w)), spec
+        ran += 1
+    if mode == "bf16" and shape[2] <= 32 and shape[3] <= 256:
+        assert ran >= 1
