@@ -892,6 +892,34 @@ def fwdbwd_only(args):
     return 0
 
 
+def cascade_only(args):
+    """The synthetic three-layer cascade alone (bank -> fused non-linearity
+    snippet -> next bank across the previous output), in --mode f32 or
+    bf16x3, K steps with an L2 flush between steps; one JSON line."""
+    import torch
+    from paper_0911_3456_gb300 import inputs
+    from paper_0911_3456_gb300.cascade import Cascade, Layer
+    world, rank, local = dist_setup()
+    cx, cbanks = inputs.workload_cascade()
+    xd = torch.from_numpy(cx).cuda()
+    wds = [torch.from_numpy(b).cuda() for b in cbanks]
+    nl = ["y > 0.f ? y : 0.f", "fminf(fmaxf(y, 0.f), 1.f)", None]   # threshold, saturation, linear
+    mode = args.mode if args.mode in ("f32", "bf16x3", "bf16") else "f32"
+    cas = Cascade(cx.shape, [Layer(b.shape[0], b.shape[1], b.shape[2], e) for b, e in zip(cbanks, nl)], mode)
+    if not args.no_tune:
+        cas.autotune()
+    outs = [torch.empty(pl.out_shape, device="cuda") for pl in cas.plans]
+    steps = min(args.steps, 50)
+    ms = time_loop(torch, lambda: cas.forward(xd, wds, outs), steps, args.warmup, world, make_flush(torch))
+    if rank == 0:
+        print(json.dumps({"metric": "three-layer cascade GFLOP/s", "value": cas.flops / ms / 1e6, "unit": "GFLOP/s",
+                          "higher_is_better": True, "steps": steps, "warmup": args.warmup, "ms": ms, "mode": mode,
+                          "config": {"workload": "cascade_256x256x8", "layers": [list(b.shape) for b in cbanks],
+                                     "nonlinearities": nl, "l2": "flushed between steps"},
+                          "specs": [pl.info()["fwd"].get("spec") for pl in cas.plans]}), flush=True)
+    return 0
+
+
 def traffic_sweep(args):
     """One forward per tensor-core candidate of the headline workload (modes
     bf16x3 and bf16), printing each candidate's generated kernel and source hash
@@ -943,11 +971,17 @@ def main():
                     help="the differentiation workload alone (forward, dL/dx, dL/dw)")
     ap.add_argument("--batch", action="store_true",
                     help="the 64-image uneven batch alone (one persistent launch per step)")
+    ap.add_argument("--cascade", action="store_true",
+                    help="the three-layer cascade alone (--mode f32 or bf16x3)")
     ap.add_argument("--traffic-sweep", action="store_true",
                     help="one forward per tensor-core candidate, for an ncu DRAM-traffic capture")
     args = ap.parse_args()
     if args.traffic_sweep:
         return traffic_sweep(args)
+    if args.cascade:
+        if args.warmup < 3:
+            args.warmup = 3
+        return cascade_only(args)
     if args.fwdbwd:
         if args.warmup < 3:
             args.warmup = 3
