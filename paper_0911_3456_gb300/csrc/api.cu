@@ -197,10 +197,14 @@ fbcorr_status_t prepare_backward(fbcorr_plan* p) {
         p->dw_kind = VarKind::Default;   // one thread per channel does not fit a CTA
     } else {
         char name[160];
-        snprintf(name, sizeof name, "fbc_dw_f%dx%d_c%d_n%d_g%d_q%d_m%d", (int)p->fh, (int)p->fw,
-                 (int)p->D, p->dw_tn, p->dw_ng, p->dw_qb, mask);
+        // packed pairs need 120 registers (2 CTAs per SM instead of 3): measured
+        // slower on the differentiation workload (30.2 against 41.3 TFLOP/s), so off
+        // unless FBCORR_DW_PK=1
+        p->dw_pk = env_str("FBCORR_DW_PK", "0") == "1" ? 1 : 0;
+        snprintf(name, sizeof name, "fbc_dw_f%dx%d_c%d_n%d_g%d_q%d_m%d%s", (int)p->fh, (int)p->fw,
+                 (int)p->D, p->dw_tn, p->dw_ng, p->dw_qb, mask, p->dw_pk ? "_pk1" : "");
         s = rtcg_kernel(dw_kernel_source((int)p->fh, (int)p->fw, (int)p->D, p->dw_tn, p->dw_ng,
-                                         p->dw_qb, mask, name),
+                                         p->dw_qb, mask, p->dw_pk, name),
                         name, dw_smem_bytes((int)p->fw, (int)p->D, p->dw_tn, p->dw_ng, p->dw_qb),
                         (int)p->D * p->dw_ng, &p->dw_kernel);
         if (s == FBCORR_OK) {
@@ -756,7 +760,8 @@ fbcorr_status_t fbcorr_plan_info(fbcorr_plan_t p, char* buf, size_t cap) {
         o << ",\"dx\":{\"kind\":\"" << kind_name(p->dx_kind) << "\"";
         if (p->dx_kind == VarKind::Direct) o << ",\"spec\":\"" << direct_tile_spec(p->dx_tile) << "\"";
         o << "},\"dw\":{\"kind\":\"" << kind_name(p->dw_kind) << "\",\"threads\":" << p->D * p->dw_ng
-          << ",\"filters_per_cta\":" << p->dw_tn * p->dw_ng << ",\"chunks\":" << p->dw_chunks
+          << ",\"filters_per_cta\":" << p->dw_tn * p->dw_ng << ",\"packed_pairs\":" << p->dw_pk
+          << ",\"chunks\":" << p->dw_chunks
           << ",\"rows_per_chunk\":" << p->dw_rows_per_chunk << "}";
     }
     o << ",\"ws_fwd\":" << p->ws_fwd << ",\"ws_bwd\":" << p->ws_bwd << ",\"sm_count\":"
@@ -857,7 +862,7 @@ fbcorr_status_t fbcorr_rtcg_check(const int64_t in_shape[3], const int64_t filt_
         direct_kernel_source(bp, tb, kname_for("fbc_direct", bp, tb)),
         dw_kernel_source((int)tmp.fh, (int)tmp.fw, (int)tmp.D, 4,
                          (int)std::max<int64_t>(1, std::min<int64_t>(256 / tmp.D, (tmp.N + 3) / 4)), 64,
-                         mask, "fbc_dw_check")};
+                         mask, 1, "fbc_dw_check")};
     for (const auto& src : srcs) {
         std::string lg;
         fbcorr_status_t s = rtcg_compile_only(src, &lg);

@@ -163,7 +163,8 @@ fbcorr_status_t tune_direct_problem(const DeviceInfo& dev, const DirectProblem& 
 // dL/dw partial-sum kernel: TN filters x fw taps per thread, NG filter groups of
 // C threads per CTA, rows walked in blocks of QB columns staged in shared memory.
 size_t dw_smem_bytes(int fw, int c, int tn, int ng, int qb);
-std::string dw_kernel_source(int fh, int fw, int c, int tn, int ng, int qb, int mask,
+// pk = 1: packed-pair FMAs in the double-buffered path (bit-identical).
+std::string dw_kernel_source(int fh, int fw, int c, int tn, int ng, int qb, int mask, int pk,
                              const std::string& kname);
 
 // prebuilt (nvcc) kernels, launchers defined in default_kernels.cu
@@ -246,6 +247,7 @@ struct fbcorr_plan {
     fbc::VarKind dw_kind = fbc::VarKind::Direct;
     fbc::Kernel dw_kernel;
     int dw_tn = 4, dw_ng = 1, dw_qb = 64, dw_nblocks = 1;
+    int dw_pk = 0;                 // packed-pair FMAs in the dL/dw kernel (FBCORR_DW_PK=1; off by default)
     int dw_chunks = 1, dw_rows_per_chunk = 1;
 
     size_t ws_fwd = 0, ws_bwd = 0;

@@ -724,7 +724,7 @@ __device__ __forceinline__ void fbc_cp_async_wait() { asm volatile("cp.async.wai
 // through them with cp.async, the next block's copies in flight while the current
 // one is summed (the same arithmetic in the same order as the synchronous path,
 // which the other cases take).
-template <int FH, int FW, int C, int TN, int NG, int QB, int MASK>
+template <int FH, int FW, int C, int TN, int NG, int QB, int MASK, int PK = 0>
 struct FbcDw {
     static constexpr int NT = C * NG;
     static constexpr int NBLK = TN * NG;
@@ -789,6 +789,98 @@ struct FbcDw {
         }
     }
 
+    // PK = 1: the same TN x FW terms as packed pairs over adjacent filters
+    // (fma.rn.f32x2 on (g[t], g[t+1]) x (x, x)): each lane rounds like fmaf in
+    // the same order, so the sums are bit-identical and half as many
+    // instructions are issued.
+    static __device__ __forceinline__ void sum_block_pk(const float* gs, const float* xs, int ng, int c,
+                                                        float2 (&ra)[TN / 2][FW]) {
+        if (ng * TN >= NBLK) return;
+        float2 win[FW];
+#pragma unroll
+        for (int k = 0; k < FW - 1; ++k) {
+            const float v = xs[k * C + c];
+            win[k] = make_float2(v, v);
+        }
+        const float* gp = gs + ng * TN;
+#pragma unroll 1
+        for (int qb = 0; qb < QB; qb += FW) {
+#pragma unroll
+            for (int s = 0; s < FW; ++s) {
+                const int qq = qb + s;
+                if (qq < QB) {
+                    const float v = xs[(qq + FW - 1) * C + c];
+                    win[(s + FW - 1) % FW] = make_float2(v, v);
+                    float2 gv[TN / 2];
+#pragma unroll
+                    for (int t4 = 0; t4 < TN; t4 += 4) {
+                        const float4 g4 = *reinterpret_cast<const float4*>(gp + qq * NBLK + t4);
+                        gv[t4 / 2] = make_float2(g4.x, g4.y);
+                        gv[t4 / 2 + 1] = make_float2(g4.z, g4.w);
+                    }
+#pragma unroll
+                    for (int u = 0; u < TN / 2; ++u)
+#pragma unroll
+                        for (int k = 0; k < FW; ++k) ra[u][k] = __ffma2_rn(gv[u], win[(s + k) % FW], ra[u][k]);
+                }
+            }
+        }
+    }
+
+    static __device__ __forceinline__ void run_async_pk(const FbcDwArgs& a, float* smem, int chunk, int i,
+                                                        int nblk) {
+        const int tid = threadIdx.x;
+        const int ng = tid / C;
+        const int c = tid - ng * C;
+        const int n0 = nblk * NBLK;
+        const int pb = chunk * a.rows_per_chunk;
+        int pe = pb + a.rows_per_chunk;
+        if (pe > a.Ho) pe = a.Ho;
+        const int qblocks = (a.Wo + QB - 1) / QB;
+        const int nb = (pe - pb) * qblocks;
+        float2 tot[TN / 2][FW], ra[TN / 2][FW];
+#pragma unroll
+        for (int u = 0; u < TN / 2; ++u)
+#pragma unroll
+            for (int k = 0; k < FW; ++k) tot[u][k] = ra[u][k] = make_float2(0.f, 0.f);
+        if (nb > 0) issue(a, smem, smem + GS, pb, 0, i, n0);
+        fbc_cp_async_commit();
+        for (int b = 0; b < nb; ++b) {
+            const int buf = b & 1;
+            if (b + 1 < nb) {
+                const int p1 = pb + (b + 1) / qblocks, q1 = ((b + 1) % qblocks) * QB;
+                float* nbuf = smem + (buf ^ 1) * (GS + XS);
+                issue(a, nbuf, nbuf + GS, p1, q1, i, n0);
+            }
+            fbc_cp_async_commit();
+            fbc_cp_async_wait<1>();
+            __syncthreads();
+            const float* cur = smem + buf * (GS + XS);
+            sum_block_pk(cur, cur + GS, ng, c, ra);
+            if ((b + 1) % qblocks == 0) {
+#pragma unroll
+                for (int u = 0; u < TN / 2; ++u)
+#pragma unroll
+                    for (int k = 0; k < FW; ++k) {
+                        tot[u][k].x += ra[u][k].x;
+                        tot[u][k].y += ra[u][k].y;
+                        ra[u][k] = make_float2(0.f, 0.f);
+                    }
+            }
+            __syncthreads();
+        }
+        fbc_cp_async_wait<0>();
+#pragma unroll
+        for (int t = 0; t < TN; ++t) {
+            const int n = n0 + ng * TN + t;
+            if (n >= a.N) continue;
+#pragma unroll
+            for (int k = 0; k < FW; ++k)
+                a.part[((((long long)chunk * a.N + n) * FH + i) * FW + k) * C + c] =
+                    (t & 1) ? tot[t / 2][k].y : tot[t / 2][k].x;
+        }
+    }
+
     static __device__ __forceinline__ void run_async(const FbcDwArgs& a, float* smem, int chunk, int i,
                                                      int nblk) {
         const int tid = threadIdx.x;
@@ -846,7 +938,10 @@ struct FbcDw {
                                                int nblk) {
         if constexpr (!MASK && (C % 4) == 0) {
             if ((a.N & 3) == 0) {
-                run_async(a, smem, chunk, i, nblk);
+                if constexpr (PK && (TN & 3) == 0)
+                    run_async_pk(a, smem, chunk, i, nblk);
+                else
+                    run_async(a, smem, chunk, i, nblk);
                 return;
             }
         }

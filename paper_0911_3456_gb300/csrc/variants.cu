@@ -156,12 +156,12 @@ size_t dw_smem_bytes(int fw, int c, int tn, int ng, int qb) {
     return 2 * (size_t)(qb * tn * ng + (qb + fw - 1) * c) * 4;   // two (g, x) buffers
 }
 
-std::string dw_kernel_source(int fh, int fw, int c, int tn, int ng, int qb, int mask,
+std::string dw_kernel_source(int fh, int fw, int c, int tn, int ng, int qb, int mask, int pk,
                              const std::string& kname) {
     std::ostringstream o;
     o << rtcg_header_source() << "\n";
     o << "typedef FbcDw<" << fh << "," << fw << "," << c << "," << tn << "," << ng << "," << qb << ","
-      << mask << "> FbcDwThis;\n";
+      << mask << "," << pk << "> FbcDwThis;\n";
     o << "static_assert(FbcDwThis::SMEM_BYTES == " << dw_smem_bytes(fw, c, tn, ng, qb)
       << ", \"host and device disagree on the shared-memory size\");\n";
     o << "extern \"C\" __global__ void __launch_bounds__(" << c * ng << ") " << kname
@@ -299,9 +299,7 @@ static double direct_score(const DirectProblem& pr, const DirectTile& t, int sm_
     res = std::min(res, 65536 / (t.threads() * std::min(255, regs)));
     if (res < 1) return -1.0;
     const long ctas = (long)gx * gy * gz;
-    const long slots = (long)res * sm_count;
-    const long waves = (ctas + slots - 1) / slots;
-    const double wave_eff = (double)ctas / (double)(waves * slots);
+    const double wave_eff = wave_balance(ctas, res, sm_count);
     const double loads = (t.tr + pr.fh - 1) + pr.fh * t.tf / 4.0 + 2.0;
     const double fmas = (double)t.tr * t.tf * pr.fh;
     const int cc = t.chunk(pr.c);
