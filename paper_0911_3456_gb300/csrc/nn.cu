@@ -7,14 +7,14 @@
 // the same pass (or fbc_nn_norms for 48-dimension planes), the neighbour norms
 // |n|^2 in FP32 and their maximum; (2) the
 // generated kernel screens every (target, neighbour) pair on the tensor cores
-// and keeps, per work item part and target, the two smallest keys of
+// and keeps, per work item part and target, the FBC_NN_KEEP smallest keys of
 // d' = |n|^2 - 2 t.n; (3) fbc_nn_finalize certifies the screening per target:
 // with E the bound on the screening error of any d' of that target (below), the
 // true nearest neighbour j* satisfies d'(j*) <= m + 2E, m the smallest screened
 // key, so every neighbour screened at most m + 2E (the window) is re-ranked by
 // its exact FP32 squared distance sum_k (t_k - n_k)^2 (ties: lowest index).  The
-// window is known to be complete when no part's second key lies inside it (a part
-// keeps only two keys, so a second key inside the window may hide a third);
+// window is known to be complete when no part's last kept key lies inside it (a
+// part keeps FBC_NN_KEEP keys, so a last key inside the window may hide another);
 // otherwise (4) fbc_nn_part_scan takes the target's exact FP32 distance to every
 // neighbour of each such part (up to kPartCap parts per target; beyond that
 // fbc_nn_exact_scan takes all neighbours), and fbc_nn_exact_write stores the
@@ -163,11 +163,11 @@ __device__ __forceinline__ float fbc_nn_exact_dist(const float* __restrict__ ti,
 
 // One thread per target: the smallest screened key m, the window m + 2E (+ the
 // rounding of the exact distances), every candidate inside it re-ranked by its
-// exact FP32 distance; a part whose second key lies inside the window may hold
+// exact FP32 distance; a part whose last kept key lies inside the window may hold
 // more candidates in it than it kept, and is listed for an exact re-scan.
 struct NnFinalizeArgs {
     const unsigned long long* part;
-    int cands;                  // keys per target: parts x 2
+    int cands;                  // keys per target: parts x FBC_NN_KEEP
     long long rows_total;
     const float* t;
     const float* n;
@@ -201,10 +201,10 @@ __global__ void __launch_bounds__(128) fbc_nn_finalize(const NnFinalizeArgs A) {
     for (int k = 0; k < A.dim; ++k) t2 = fmaf(__ldg(ti + k), __ldg(ti + k), t2);
     const float tn = sqrtf(t2);
     const float nmax = sqrtf(__uint_as_float(A.stats->nmax2_bits));
-    const int nparts = A.cands / 2;
+    const int nparts = A.cands / FBC_NN_KEEP;
     float m = __int_as_float(0x7f800000);
     for (int pq = lane; pq < nparts; pq += 32) {
-        const unsigned long long k0 = __ldg(A.part + ((long long)pq * A.rows_total + i) * 2);
+        const unsigned long long k0 = __ldg(A.part + ((long long)pq * A.rows_total + i) * FBC_NN_KEEP);
         if (k0 != ~0ull) m = fminf(m, fbc_nn_key_dist(k0));   // a part's first key is its smallest
     }
 #pragma unroll
@@ -221,17 +221,19 @@ __global__ void __launch_bounds__(128) fbc_nn_finalize(const NnFinalizeArgs A) {
         const int pq = pq0 + lane;
         bool over = false;
         if (pq < nparts) {
-            const unsigned long long* pk = A.part + ((long long)pq * A.rows_total + i) * 2;
-            const unsigned long long k0 = __ldg(pk), k1 = __ldg(pk + 1);
-            over = k1 != ~0ull && fbc_nn_key_dist(k1) <= win;
+            const unsigned long long* pk = A.part + ((long long)pq * A.rows_total + i) * FBC_NN_KEEP;
+            unsigned long long kk[FBC_NN_KEEP];
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const unsigned long long key = h ? k1 : k0;
+            for (int h = 0; h < FBC_NN_KEEP; ++h) kk[h] = __ldg(pk + h);
+            over = kk[FBC_NN_KEEP - 1] != ~0ull && fbc_nn_key_dist(kk[FBC_NN_KEEP - 1]) <= win;
+#pragma unroll
+            for (int h = 0; h < FBC_NN_KEEP; ++h) {
+                const unsigned long long key = kk[h];
                 if (key == ~0ull || fbc_nn_key_dist(key) > win) continue;
                 const long long j = (long long)(key & 0xffffffffull);
                 const float d = fbc_nn_exact_dist(ti, A.n + j * A.dim, A.dim);
-                const unsigned long long kk = ((unsigned long long)__float_as_uint(d) << 32) | (unsigned long long)j;
-                best = kk < best ? kk : best;
+                const unsigned long long ek = ((unsigned long long)__float_as_uint(d) << 32) | (unsigned long long)j;
+                best = ek < best ? ek : best;
             }
         }
         // incomplete parts, in part order, up to kPartCap of them
@@ -506,7 +508,7 @@ fbcorr_status_t fbcorr_nn_plan_create(fbcorr_nn_plan_t* out, int64_t n_targets, 
     p->off_nhi = off; off = align_up(off + (size_t)k.n_tiles * k.b_bytes, 256);
     p->off_nlo = off; if (p->split) off = align_up(off + (size_t)k.n_tiles * k.b_bytes, 256);
     p->off_n2 = off; off = align_up(off + (size_t)k.n_tiles * FBC_NN_TILE_N * 4, 256);
-    p->off_part = off; off = align_up(off + (size_t)k.chunks * (kEW / 4) * rows_total * 2 * 8, 256);
+    p->off_part = off; off = align_up(off + (size_t)k.chunks * (kEW / 4) * rows_total * FBC_NN_KEEP * 8, 256);
     p->off_stats = off; off = align_up(off + sizeof(NnStats), 256);
     p->off_flag = off; off = align_up(off + (size_t)n_targets * 4, 256);
     p->off_best = off; off = align_up(off + (size_t)n_targets * 8, 256);
@@ -625,7 +627,7 @@ fbcorr_status_t fbcorr_nn_search(fbcorr_nn_plan_t p, const float* targets, const
     FBC_TRY(launch(p->k, dim3(p->grid), args, s));
     NnFinalizeArgs fa;
     fa.part = reinterpret_cast<const unsigned long long*>(base + p->off_part);
-    fa.cands = kp.chunks * (kEW / 4) * 2;
+    fa.cands = kp.chunks * (kEW / 4) * FBC_NN_KEEP;
     fa.rows_total = t_rows;
     fa.t = targets;
     fa.n = neighbors;

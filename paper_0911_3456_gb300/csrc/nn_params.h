@@ -6,6 +6,7 @@
 
 #define FBC_NN_TILE_T 128     // targets per tile (MMA M)
 #define FBC_NN_TILE_N 256     // neighbours per tile (MMA N)
+#define FBC_NN_KEEP 2         // smallest keys kept per target and screening part
 
 struct FbcNnParams {
     const unsigned char* thi;     // targets, tile-major [t_tiles][nc][128][16 B] BF16 hi
@@ -13,7 +14,7 @@ struct FbcNnParams {
     const unsigned char* nhi;     // neighbours, tile-major [n_tiles][nc][256][16 B] BF16 hi
     const unsigned char* nlo;     //   and lo
     const float* n2;              // |n_j|^2 (FP32), +inf for the padding neighbours
-    unsigned long long* part;     // [chunks][parts][t_tiles*128][2] best two keys per target
+    unsigned long long* part;     // [chunks][parts][t_tiles*128][FBC_NN_KEEP] smallest keys per target
     int* err;                     // host-mapped error word
     unsigned long long wait_ns;   // bound of every mbarrier wait
     int t_tiles, n_tiles;         // 128-target and 256-neighbour tiles

@@ -9,7 +9,7 @@
 // targets and 256 neighbours are one 128x256xdim GEMM on the tensor cores
 // (tcgen05.mma, BF16 in, FP32 accumulate in TMEM; split BF16 by default, three
 // products per K step like the correlation kernel), and the epilogue keeps, per
-// target, the two smallest keys (d' as order-preserving bits, neighbour index)
+// target, the FBC_NN_KEEP smallest keys (d' as order-preserving bits, neighbour index)
 // over the tiles of a work item.  A work item is one target tile against one
 // chunk of neighbour tiles; items run chunk-major, so the target tiles that share
 // a chunk run at the same time and read its neighbours from HBM once.  The host
@@ -22,7 +22,7 @@
 // that follow the accumulators; warp 1 issues the MMAs into two alternating
 // accumulators; EW epilogue warps read the accumulators (tcgen05.ld 32x32b: one
 // target row per thread, 32 neighbours per load, the next load in flight while
-// one is processed), form d' and keep the running best two per target row in
+// one is processed), form d' and keep the running best keys per target row in
 // registers, rejecting a 32-column chunk with one comparison of its minimum.
 
 __device__ __forceinline__ fbc_u64 fbc_nn_key(float d, unsigned j) {
@@ -33,19 +33,39 @@ __device__ __forceinline__ fbc_u64 fbc_nn_key(float d, unsigned j) {
     return ((fbc_u64)u << 32) | j;
 }
 
-// Running best two (distance, index) of one target row; the columns of a thread
-// arrive in increasing index order, so strict '<' keeps the lowest index on ties.
-// Almost every candidate fails the first comparison.
-__device__ __forceinline__ void fbc_nn_keep2(float& d1, unsigned& i1, float& d2, unsigned& i2, float d, unsigned j) {
-    if (d < d2) {
-        if (d < d1) {
-            d2 = d1;
-            i2 = i1;
-            d1 = d;
-            i1 = j;
-        } else {
-            d2 = d;
-            i2 = j;
+// Running FBC_NN_KEEP smallest (distance, index) of one target row, sorted; the
+// columns of a thread arrive in increasing index order, so strict '<' keeps the
+// lowest index on ties.  Almost every candidate fails the first comparison.
+// (Four keys per part were measured: no target needed a re-scan on the 1/f patch
+// sets, but the insertions made the screening of 4096 x 1M three times slower.)
+__device__ __forceinline__ void fbc_nn_keep(float (&bd)[FBC_NN_KEEP], unsigned (&bi)[FBC_NN_KEEP], float d,
+                                            unsigned j) {
+    if constexpr (FBC_NN_KEEP == 2) {
+        if (d < bd[1]) {
+            if (d < bd[0]) {
+                bd[1] = bd[0];
+                bi[1] = bi[0];
+                bd[0] = d;
+                bi[0] = j;
+            } else {
+                bd[1] = d;
+                bi[1] = j;
+            }
+        }
+        return;
+    }
+    if (d < bd[FBC_NN_KEEP - 1]) {
+#pragma unroll
+        for (int k = FBC_NN_KEEP - 1; k > 0; --k) {
+            // slot k takes slot k-1's entry if d goes before it, else d if d goes here
+            const bool shift = d < bd[k - 1];
+            const bool here = !shift && d < bd[k];
+            bd[k] = shift ? bd[k - 1] : (here ? d : bd[k]);
+            bi[k] = shift ? bi[k - 1] : (here ? j : bi[k]);
+        }
+        if (d < bd[0]) {
+            bd[0] = d;
+            bi[0] = j;
         }
     }
 }
@@ -219,8 +239,13 @@ __device__ __forceinline__ void fbc_nn_body(const FbcNnParams& P) {
         bool ok = true;
         for (int k = blockIdx.x; k < items && ok; k += gridDim.x) {
             const int c = k / P.t_tiles, t = k - c * P.t_tiles;
-            float bd1 = __int_as_float(0x7f800000), bd2 = bd1;
-            unsigned bi1 = 0xffffffffu, bi2 = 0xffffffffu;
+            float bd[FBC_NN_KEEP];
+            unsigned bi[FBC_NN_KEEP];
+#pragma unroll
+            for (int k = 0; k < FBC_NN_KEEP; ++k) {
+                bd[k] = __int_as_float(0x7f800000);
+                bi[k] = 0xffffffffu;
+            }
             const int j1 = min(P.n_tiles, (c + 1) * P.chunk_tiles);
             for (int jt = c * P.chunk_tiles; jt < j1; ++jt) {
                 const int acc = acc_it & 1;
@@ -249,7 +274,7 @@ __device__ __forceinline__ void fbc_nn_body(const FbcNnParams& P) {
                         d[4 * q + 3] = fmaf(-2.f, __uint_as_float(r[i & 1][4 * q + 3]), __uint_as_float(nv.w));
                     }
                     // minimum of the chunk as a balanced tree; almost every chunk fails
-                    // the comparison with the row's second best
+                    // the comparison with the row's last kept key
                     float m[16];
 #pragma unroll
                     for (int j = 0; j < 16; ++j) m[j] = fminf(d[2 * j], d[2 * j + 1]);
@@ -257,10 +282,10 @@ __device__ __forceinline__ void fbc_nn_body(const FbcNnParams& P) {
                     for (int w2 = 8; w2 >= 1; w2 >>= 1)
 #pragma unroll
                         for (int j = 0; j < w2; ++j) m[j] = fminf(m[j], m[j + w2]);
-                    if (m[0] < bd2) {
+                    if (m[0] < bd[FBC_NN_KEEP - 1]) {
                         const unsigned n0 = (unsigned)(jt * FBC_NN_TILE_N + cc * 32);
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) fbc_nn_keep2(bd1, bi1, bd2, bi2, d[j], n0 + (unsigned)j);
+                        for (int j = 0; j < 32; ++j) fbc_nn_keep(bd, bi, d[j], n0 + (unsigned)j);
                     }
                 }
                 fbc_tc_fence_before();
@@ -273,9 +298,9 @@ __device__ __forceinline__ void fbc_nn_body(const FbcNnParams& P) {
             }
             if (!ok) break;
             const int row = t * FBC_NN_TILE_T + lq * 32 + lane;
-            fbc_u64* dst = P.part + (((long long)c * (EW / 4) + part) * rows_total + row) * 2;
-            dst[0] = bi1 == 0xffffffffu ? ~0ull : fbc_nn_key(bd1, bi1);
-            dst[1] = bi2 == 0xffffffffu ? ~0ull : fbc_nn_key(bd2, bi2);
+            fbc_u64* dst = P.part + (((long long)c * (EW / 4) + part) * rows_total + row) * FBC_NN_KEEP;
+#pragma unroll
+            for (int k = 0; k < FBC_NN_KEEP; ++k) dst[k] = bi[k] == 0xffffffffu ? ~0ull : fbc_nn_key(bd[k], bi[k]);
         }
     }
     __syncwarp();

@@ -192,7 +192,9 @@ double wave_balance(long ctas, int res, int sms) {
 std::vector<DirectTile> direct_candidates(const DirectProblem& pr, size_t smem_limit, int threads,
                                           int max_block) {
     std::vector<DirectTile> out;
-    const int trs[] = {2, 4, 8};
+    // row blocks of 6 and 7 give grids that fill 152 SMs on 248- and 256-row
+    // outputs (e.g. dL/dx of the differentiation workload: 8 x 19 = 152 CTAs)
+    const int trs[] = {2, 4, 6, 7, 8};
     const int tfs[] = {4, 8};
     const int wrs[] = {1, 2, 3, 4, 5, 6, 7, 8};   // any count: block heights that fit 152 SMs better
     const int wfs[] = {1, 2, 4, 8};
