@@ -698,6 +698,7 @@ static fbcorr_status_t autotune_tc(fbcorr_plan_t p, fbcorr_stream_t stream) {
     std::string best;
     float best_ms = 1e30f;
     fbcorr_status_t status = FBCORR_OK;
+    std::vector<std::pair<float, std::string>> timed;   // (median single-step ms, spec)
     tc_precompile(p->tc, specs);   // the generated kernels of all candidates, on host threads
     for (const auto& sp : specs) {
         if (tc_set_spec(p->tc, sp) != FBCORR_OK) continue;
@@ -719,9 +720,37 @@ static fbcorr_status_t autotune_tc(fbcorr_plan_t p, fbcorr_stream_t stream) {
         }
         std::sort(ms.begin(), ms.end());
         logf("autotune %s: %.4f ms", sp.c_str(), ms[ms.size() / 2]);
-        if (ms[ms.size() / 2] < best_ms) {
-            best_ms = ms[ms.size() / 2];
-            best = sp;
+        timed.push_back({ms[ms.size() / 2], sp});
+    }
+    // Finalists: single steps separate candidates within about 1 %, and the clock
+    // drifts as the GPU warms up over the sweep, so the six fastest are timed
+    // again, round-robin over three rounds, as runs of 20 back-to-back steps
+    // (the way the forward is used); the best round of each decides.
+    if (status == FBCORR_OK && !timed.empty()) {
+        std::sort(timed.begin(), timed.end());
+        const size_t nf = std::min<size_t>(timed.size(), 6);
+        std::vector<float> fin(nf, 1e30f);
+        for (int round = 0; round < 3 && status == FBCORR_OK; ++round)
+            for (size_t f = 0; f < nf && status == FBCORR_OK; ++f) {
+                if (tc_set_spec(p->tc, timed[f].second) != FBCORR_OK) continue;
+                bool ok = fbcorr_forward(p, x, w, y, ws, p->ws_fwd, stream) == FBCORR_OK;
+                cudaEventRecord(e0, s);
+                for (int r = 0; r < 20 && ok; ++r) ok = fbcorr_forward(p, x, w, y, ws, p->ws_fwd, stream) == FBCORR_OK;
+                cudaEventRecord(e1, s);
+                if (!ok || cudaEventSynchronize(e1) != cudaSuccess || fbcorr_plan_device_status(p, 0) != FBCORR_OK) {
+                    status = set_error(FBCORR_ERR_CUDA, "autotune run of %s failed", timed[f].second.c_str());
+                    break;
+                }
+                float t = 0.f;
+                cudaEventElapsedTime(&t, e0, e1);
+                fin[f] = std::min(fin[f], t / 20.f);
+            }
+        for (size_t f = 0; f < nf; ++f) {
+            logf("autotune finalist %s: %.4f ms", timed[f].second.c_str(), fin[f]);
+            if (fin[f] < best_ms) {
+                best_ms = fin[f];
+                best = timed[f].second;
+            }
         }
     }
     cudaEventDestroy(e0);

@@ -469,6 +469,7 @@ fbcorr_status_t tune_direct_problem(const DeviceInfo& dev, const DirectProblem& 
     float best_ms = 1e30f;
     best_spec->clear();
     fbcorr_status_t status = FBCORR_OK;
+    std::vector<std::pair<float, std::string>> timed;   // (median single-launch ms, spec)
     for (const auto& sp : specs) {
         Kernel k;
         DirectTile t;
@@ -497,9 +498,49 @@ fbcorr_status_t tune_direct_problem(const DeviceInfo& dev, const DirectProblem& 
         std::sort(ms_list.begin(), ms_list.end());
         const float med = ms_list[ms_list.size() / 2];
         logf("autotune %s %s: %.4f ms", what, sp.c_str(), med);
-        if (med < best_ms) {
-            best_ms = med;
-            *best_spec = sp;
+        timed.push_back({med, sp});
+    }
+    // Finalists: the six fastest timed again, round-robin over three rounds, as
+    // runs of 10 back-to-back launches (single launches separate them within
+    // their noise); the best round of each decides.
+    if (status == FBCORR_OK && !timed.empty()) {
+        std::sort(timed.begin(), timed.end());
+        const size_t nf = std::min<size_t>(timed.size(), 6);
+        std::vector<float> fin(nf, 1e30f);
+        std::vector<Kernel> fk(nf);
+        std::vector<DirectTile> ft(nf);
+        std::vector<bool> fdef(nf, false);
+        for (size_t f = 0; f < nf; ++f) {
+            fdef[f] = timed[f].second == "default";
+            if (!fdef[f] && (!parse_direct_spec(timed[f].second, &ft[f]) || build_direct(pr, ft[f], &fk[f]) != FBCORR_OK))
+                fin[f] = 2e30f;   // not re-timed
+        }
+        for (int round = 0; round < 3 && status == FBCORR_OK; ++round)
+            for (size_t f = 0; f < nf; ++f) {
+                if (fin[f] > 1.5e30f) continue;
+                auto run = [&]() {
+                    return fdef[f] ? run_default(pr, x, m, w, y, 0.f, 1.f, s)
+                                   : run_direct(fk[f], pr, ft[f], x, m, w, y, 0.f, 1.f, s);
+                };
+                bool ok = run() == FBCORR_OK;
+                cudaEventRecord(e0, s);
+                for (int r = 0; r < 10 && ok; ++r) ok = run() == FBCORR_OK;
+                cudaEventRecord(e1, s);
+                if (!ok || cudaEventSynchronize(e1) != cudaSuccess) {
+                    status = set_error(FBCORR_ERR_CUDA, "autotune run of %s (%s) failed", timed[f].second.c_str(), what);
+                    break;
+                }
+                float t = 0.f;
+                cudaEventElapsedTime(&t, e0, e1);
+                fin[f] = std::min(fin[f], t / 10.f);
+            }
+        for (size_t f = 0; f < nf; ++f) {
+            if (fin[f] > 1.5e30f) continue;
+            logf("autotune %s finalist %s: %.4f ms", what, timed[f].second.c_str(), fin[f]);
+            if (fin[f] < best_ms) {
+                best_ms = fin[f];
+                *best_spec = timed[f].second;
+            }
         }
     }
     cudaEventDestroy(e0);
