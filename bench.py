@@ -920,30 +920,6 @@ def cascade_only(args):
     return 0
 
 
-def traffic_sweep(args):
-    """One forward per tensor-core candidate of the headline workload (modes
-    bf16x3 and bf16), printing each candidate's generated kernel and source hash
-    as a JSON line, in launch order: run under ncu with
-    -k regex:^fbc_tc_c --metrics dram__bytes_read.sum,dram__bytes_write.sum to
-    measure the DRAM traffic of every variant the auto-tuner can pick."""
-    import torch
-    from paper_0911_3456_gb300.api import Plan
-    wl = workload_by_name(args.workload)
-    x = torch.from_numpy(wl.x).cuda()
-    w = torch.from_numpy(wl.w).cuda()
-    for mode in ("bf16x3", "bf16"):
-        p = Plan(wl.x.shape, wl.w.shape, mode, wl.clamp)
-        y = torch.empty(p.out_shape, device="cuda")
-        for spec in p.candidates():
-            p.set_variant(spec)
-            p.forward(x, w, y)
-            torch.cuda.synchronize()
-            det = p.info()["fwd"]["detail"]
-            print(json.dumps({"mode": mode, "workload": wl.name, "spec": spec, "kernel": det["kernel"],
-                              "source_hash": det["source_hash"]}), flush=True)
-    return 0
-
-
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -973,11 +949,7 @@ def main():
                     help="the 64-image uneven batch alone (one persistent launch per step)")
     ap.add_argument("--cascade", action="store_true",
                     help="the three-layer cascade alone (--mode f32 or bf16x3)")
-    ap.add_argument("--traffic-sweep", action="store_true",
-                    help="one forward per tensor-core candidate, for an ncu DRAM-traffic capture")
     args = ap.parse_args()
-    if args.traffic_sweep:
-        return traffic_sweep(args)
     if args.cascade:
         if args.warmup < 3:
             args.warmup = 3
