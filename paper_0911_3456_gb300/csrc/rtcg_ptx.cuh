@@ -1,7 +1,8 @@
 // rtcg_ptx.cuh -- PTX wrappers shared by the run-time generated tcgen05 kernels
 // (the filter-bank correlation of rtcg_tc.cuh and the nearest-neighbour distance
 // kernel of rtcg_nn.cuh): shared-memory addresses, mbarriers with time-bounded
-// waits, 1D bulk copies, tiled bulk stores, tcgen05.mma / commit / ld, BF16
+// waits, 1D bulk copies, tiled bulk stores, tcgen05.mma / commit / ld (one CTA,
+// or a CTA pair with cta_group::2), cluster barriers and remote arrivals, BF16
 // packing.  Embedded as a
 // string and placed after the kernel's parameter block in every generated
 // source; self-contained (no system headers).  A bounded wait takes any
@@ -73,16 +74,63 @@ __device__ __forceinline__ fbc_u64 fbc_smem_desc(fbc_u32 addr, fbc_u32 lbo, fbc_
            (1ull << 46);
 }
 
+// CG = 1: one CTA, M = 128.  CG = 2: issued by the even CTA of a pair for both
+// (M = 256: rows 0..127 from the even CTA's A, 128..255 from the odd CTA's, at the
+// same shared-memory offsets; B columns 0..N/2-1 from the even CTA, the rest
+// from the odd one; each CTA's TMEM receives its own 128 rows).  Every tcgen05
+// instruction of a kernel uses the same CG.
+template <int CG = 1>
 __device__ __forceinline__ void fbc_umma(fbc_u32 d_tmem, fbc_u64 a, fbc_u64 b, fbc_u32 idesc, fbc_u32 accumulate) {
-    asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+    if constexpr (CG == 2)
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+    else
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
 }
 
+// Arrive on the mbarrier at shared::cluster address `bar` (this CTA's, or with
+// CG = 2 one of the peer's, from fbc_mapa) once the MMAs issued so far are done.
+template <int CG = 1>
 __device__ __forceinline__ void fbc_umma_commit(fbc_u32 bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-                 : "memory");
+    if constexpr (CG == 2)
+        asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                     : "memory");
+    else
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                     : "memory");
+}
+
+// ---------------------------------------------------------------- clusters
+__device__ __forceinline__ fbc_u32 fbc_cluster_rank() {
+    fbc_u32 r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// All threads of every CTA of the cluster (release / acquire at cluster scope).
+__device__ __forceinline__ void fbc_cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// The shared::cluster address of shared-memory address `addr` in CTA `rank` of the cluster.
+__device__ __forceinline__ fbc_u32 fbc_mapa(fbc_u32 addr, fbc_u32 rank) {
+    fbc_u32 r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+
+// Arrive on an mbarrier of another CTA of the cluster.  The default (CTA-scope)
+// release: what the arrival publishes lives in shared memory and TMEM, which
+// the peer reaches directly; a cluster-scope release, which also orders global
+// memory across SMs, cost about 1000 cycles per arrival and set the pace of a
+// relay that forwards every ring fill.
+__device__ __forceinline__ void fbc_mbar_arrive_remote(fbc_u32 cluster_addr) {
+    asm volatile("mbarrier.arrive.shared::cluster.b64 _, [%0];" ::"r"(cluster_addr) : "memory");
 }
 
 // tcgen05.ld 16x256b.x8 -- 16 TMEM lanes x 64 columns: registers 4g, 4g+1 hold

@@ -2,8 +2,8 @@
 // NVRTC for sm_103a with the chunk-plane count NC, the split mode, the filter
 // width FW, the taps per B stage BT, the epilogue warp count EW, the fused
 // conversion switch FUSE (and its converter warps CW), the snippet switch USER,
-// the epilogue store path TS (with SB staging slots) and the resident-bank
-// switch RES baked in.  Embedded as a string into libfbcorr and prefixed with
+// the epilogue store path TS (with SB staging slots), the resident-bank
+// switch RES and the CTA-pair switch PAIR baked in.  Embedded as a string into libfbcorr and prefixed with
 // tc_params.h and rtcg_ptx.cuh; self-contained (no system headers).
 //
 // The correlation of Sec. 6.2 as an implicit GEMM: for every filter tap (i, j)
@@ -29,7 +29,9 @@
 //   warp 1      allocates 512 TMEM columns, issues tcgen05.mma (M=128, N<=256,
 //               K=16, kind::f16 BF16, FP32 accumulate) into one of two
 //               accumulators; tcgen05.commit frees ring slots and hands
-//               finished accumulators to the epilogue;
+//               finished accumulators to the epilogue (PAIR: the even CTA's
+//               warp 1 issues M=256 cta_group::2 MMAs for both CTAs, the odd
+//               CTA's relays its filled rows);
 //   warps 2..   EW epilogue warps (two per TMEM lane quarter when EW = 8),
 //               overlapping the MMAs of the next tile; clamp or snippet, then
 //               TS = 0: tcgen05.ld 16x256b and streaming stores straight from
@@ -40,7 +42,7 @@
 //               as tiled bulk stores through the tensor map of y;
 //   last CW     (FUSE) converter warps: FP32 x rows -> BF16 hi (and lo) chunk
 //               planes of an A slot; FUSE = 1 reads the rows from global memory
-//               into registers one row ahead, FUSE = 2 from a ring of raw rows
+//               into registers two rows ahead, FUSE = 2 from a ring of raw rows
 //               that the producer fills with one bulk copy per row.
 // The bulk-copy unit costs about 150 cycles per copy whatever its size up to
 // 16 KB (and moves at most ~110 B per cycle per SM), so the copy count per tile
@@ -62,6 +64,20 @@
 // tiles under it: CTA b keeps filter tile b % ntn and takes the pixel tiles
 // b / ntn, b / ntn + gridDim.x / ntn, ... (the grid is a multiple of ntn).
 //
+// CTA pairs (PAIR = 1, launched as clusters of two): with one CTA per tile, a
+// 128-row tile of plain BF16 needs 256 B of bank per 256 tensor-core cycles of
+// each SM from L2, and the bank refills, not the tensor core, set the pace.  A
+// pair shares one M = 256 tile (its two 128-pixel tiles) under cta_group::2
+// MMAs: each CTA stages its own A rows and HALF of the bank slice (filters
+// 0..127 in the even CTA, 128..255 in the odd one, from the half-width planes),
+// so every SM moves half the bank bytes per tile.  The even CTA's MMA thread
+// issues for both; the odd CTA's MMA warp relays each filter row it has filled
+// (A slot and B stages) to the even CTA's pa_full barriers with one remote
+// arrival per row; the MMA commits
+// arrive on the ring and accumulator barriers of both CTAs; the odd CTA's
+// epilogue warps release an accumulator with remote arrivals on the even CTA's
+// acc_empty.  Each CTA stores its own 128 accumulator rows.
+//
 // Tail halves: tiles t >= nfull, the last partial round of a single 256-wide
 // filter tile, run as two 128-column work items each (instruction N = 128, B
 // from half-width planes), so that round keeps twice as many SMs busy for half
@@ -78,7 +94,7 @@ __device__ float fbc_user_epi(float y, int n, float lo, float hi);
 
 // All MMAs of one filter tap: K = 16 per instruction over the NC/2 pairs of
 // chunk planes; split mode adds hi*lo and lo*hi before hi*hi.
-template <int NC, int SPLIT>
+template <int NC, int SPLIT, int CG>
 __device__ __forceinline__ void fbc_issue_tap(fbc_u32 d_tmem, fbc_u64 ad, fbc_u64 bd, fbc_u64 ak, fbc_u64 bk,
                                               fbc_u64 alo, fbc_u64 blo, fbc_u32 idesc, fbc_u32& accumulate) {
 #pragma unroll
@@ -86,19 +102,22 @@ __device__ __forceinline__ void fbc_issue_tap(fbc_u32 d_tmem, fbc_u64 ad, fbc_u6
         const fbc_u64 a = ad + kk * ak;
         const fbc_u64 b = bd + kk * bk;
         if (SPLIT) {
-            fbc_umma(d_tmem, a, b + blo, idesc, accumulate);
-            fbc_umma(d_tmem, a + alo, b, idesc, 1);
-            fbc_umma(d_tmem, a, b, idesc, 1);
+            fbc_umma<CG>(d_tmem, a, b + blo, idesc, accumulate);
+            fbc_umma<CG>(d_tmem, a + alo, b, idesc, 1);
+            fbc_umma<CG>(d_tmem, a, b, idesc, 1);
         } else {
-            fbc_umma(d_tmem, a, b, idesc, accumulate);
+            fbc_umma<CG>(d_tmem, a, b, idesc, accumulate);
         }
         accumulate = 1;
     }
 }
 
 // ---------------------------------------------------------------- the kernel body
-template <int NC, int SPLIT, int FW, int BT, int EW, int FUSE, int CW, int USER, int TS, int SB, int RES>
+template <int NC, int SPLIT, int FW, int BT, int EW, int FUSE, int CW, int USER, int TS, int SB, int RES,
+          int PAIR>
 __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
+    static_assert(!(PAIR && RES), "a CTA pair streams the bank");
+    constexpr int CG = PAIR ? 2 : 1;                 // cta_group of every tcgen05 instruction
     constexpr int NST = (FW + BT - 1) / BT;          // B stages per filter row
     constexpr int L = FBC_TC_TILE_M + FW - 1;        // slab pixels per filter row
     __shared__ int s_abort;
@@ -107,7 +126,8 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
     const int lane = threadIdx.x & 31;
     const fbc_u32 sbase = fbc_smem_addr(fbc_tc_smem);
     // barrier table: a_full[na] a_empty[na] b_full[nb] b_empty[nb] acc_full[2] acc_empty[2]
-    // drain raw_full[nr] raw_empty[nr]
+    // drain raw_full[nr] raw_empty[nr], and for a pair pa_full[na] (the odd CTA's
+    // filter rows, A slot and B stages, relayed to the even CTA)
     const fbc_u32 a_full0 = sbase + P.bar_off;
     const fbc_u32 a_empty0 = a_full0 + 8u * P.na;
     const fbc_u32 b_full0 = a_empty0 + 8u * P.na;
@@ -117,6 +137,9 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
     const fbc_u32 drain_bar = acc_empty0 + 16u;
     const fbc_u32 raw_full0 = drain_bar + 8u;
     const fbc_u32 raw_empty0 = raw_full0 + 8u * P.nr;
+    const fbc_u32 pa_full0 = raw_empty0 + 8u * P.nr;
+    // PAIR: this CTA's rank in the pair; rank 0 issues the MMAs of both
+    const fbc_u32 rank = PAIR ? fbc_cluster_rank() : 0u;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < P.na; ++s) {
@@ -129,8 +152,10 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
         }
         for (int s = 0; s < 2; ++s) {
             fbc_mbar_init(acc_full0 + 8u * s, 1);
-            fbc_mbar_init(acc_empty0 + 8u * s, EW);
+            fbc_mbar_init(acc_empty0 + 8u * s, PAIR ? 2 * EW : EW);   // pair: both CTAs' epilogue warps
         }
+        if (PAIR)
+            for (int s = 0; s < P.na; ++s) fbc_mbar_init(pa_full0 + 8u * s, 1);
         fbc_mbar_init(drain_bar, 1);
         for (int s = 0; s < P.nr; ++s) {
             fbc_mbar_init(raw_full0 + 8u * s, 1);
@@ -140,13 +165,25 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
         s_abort = 0;
     }
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                         fbc_smem_addr(&s_tmem)),
-                     "r"(FBC_TC_TMEM_COLS));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+        // a pair allocates collectively: one warp of each CTA, the same columns in both
+        if constexpr (PAIR) {
+            asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             fbc_smem_addr(&s_tmem)),
+                         "r"(FBC_TC_TMEM_COLS));
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
+        } else {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             fbc_smem_addr(&s_tmem)),
+                         "r"(FBC_TC_TMEM_COLS));
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+        }
     }
     fbc_tc_fence_before();
-    __syncthreads();
+    // a pair: the peer's barriers are initialised before any remote arrival
+    if constexpr (PAIR)
+        fbc_cluster_sync();
+    else
+        __syncthreads();
     fbc_tc_fence_after();
     const fbc_u32 tmem = s_tmem;
     volatile int* abort_flag = &s_abort;
@@ -158,22 +195,35 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
     // a half takes its B operand from the half-width planes whi2 / wlo2.
     // RES: the CTA's filter tile is blockIdx.x % ntn and its pixel tiles are
     // unit, unit + nunits, ... with unit = blockIdx.x / ntn
+    // PAIR (one filter tile of 256): pair u = blockIdx.x / 2 takes the pixel-tile
+    // pairs u, u + gridDim.x / 2, ...; pair w is tiles 2w (even CTA) and 2w + 1
+    // (odd CTA; tile mtiles, past the image when mtiles is odd, stores nothing)
     const int nsched = P.mtiles * P.ntn;
     const int res_fi = RES ? (int)blockIdx.x % P.ntn : 0;
-    const int unit = RES ? (int)blockIdx.x / P.ntn : (int)blockIdx.x;
-    const int nunits = RES ? (int)gridDim.x / P.ntn : (int)gridDim.x;
-    const int nwork = RES ? P.mtiles : P.nfull + 2 * (nsched - P.nfull);
+    const int unit = RES ? (int)blockIdx.x / P.ntn : PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+    const int nunits = RES ? (int)gridDim.x / P.ntn : PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
+    const int nwork = RES ? P.mtiles : PAIR ? (P.mtiles + 1) >> 1 : P.nfull + 2 * (nsched - P.nfull);
     const int my_tiles = unit < nwork ? (nwork - 1 - unit) / nunits + 1 : 0;   // work items
     struct Item {
         int tile;    // pixel tile t % mtiles of filter tile t / mtiles
-        int nt;      // filter columns of this item
+        int nt;      // filter columns of this item (the MMA's N)
+        int bn;      // filter rows of B this CTA stages (a pair: nt / 2)
         int n0;      // first filter
         long long wbase;   // byte offset of the item's planes in whi / wlo (half: in whi2 / wlo2)
-        bool half;
+        bool half;   // B from the half-width planes
     };
     auto item_of = [&](int k) -> Item {
         const int w = unit + k * nunits;
         Item it;
+        if (PAIR) {
+            it.half = true;
+            it.tile = 2 * w + (int)rank;
+            it.nt = P.nt;
+            it.bn = P.nt >> 1;
+            it.n0 = 0;
+            it.wbase = (long long)rank * P.fh * FW * NC * it.bn * 16;
+            return it;
+        }
         it.half = !RES && w >= P.nfull;
         if (RES) {
             it.tile = res_fi * P.mtiles + w;
@@ -185,6 +235,7 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
         const int nti = it.tile / P.mtiles;
         const int h = (w - P.nfull) & 1;
         it.nt = it.half ? P.nt >> 1 : P.nt;
+        it.bn = it.nt;
         it.n0 = it.half ? h * it.nt : nti * P.nt;
         it.wbase = (long long)(it.half ? h : nti) * P.fh * FW * NC * it.nt * 16;
         return it;
@@ -250,7 +301,7 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
                 // RES: the B stages of the first item's filter rows fill the ring once
                 if (RES && r >= P.fh) continue;
                 const Item it = item_of(r / P.fh);
-                const long long tap_bytes = (long long)NC * it.nt * 16;   // = the item's b_half
+                const long long tap_bytes = (long long)NC * it.bn * 16;   // = the item's b_half
                 const long long woff = it.wbase + (long long)((r % P.fh) * FW) * tap_bytes;
                 const fbc_u8* wtap_hi = (it.half ? P.whi2 : P.whi) + woff;
                 const fbc_u8* wtap_lo = (it.half ? P.wlo2 : P.wlo) + woff;
@@ -285,11 +336,32 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
             }
         }
     } else if (warp == 1) {
-        // ------------------------------------------------------------ MMA issuer
-        if (lane == 0) {
+        if (PAIR && rank != 0) {
+            // -------------------------------------------------------- relay (odd CTA of a pair)
+            // once this CTA's A slot and all B stages of a filter row are filled,
+            // one arrival on the even CTA's pa_full of that slot (rows in the
+            // order its MMA thread consumes them; the ring holds a whole row)
+            if (lane == 0) {
+                int as = 0, bs = 0;
+                fbc_u32 aph = 0, bph = 0;
+                bool ok = true;
+                for (int k = 0; k < my_tiles && ok; ++k)
+                    for (int i = 0; i < P.fh && ok; ++i) {
+                        if (!(ok = fbc_wait(a_full0 + 8u * as, aph, P, abort_flag, FBC_TC_ERR_WAIT_A))) break;
+                        for (int s = 0; s < NST && ok; ++s) {
+                            ok = fbc_wait(b_full0 + 8u * bs, bph, P, abort_flag, FBC_TC_ERR_WAIT_B);
+                            if (++bs == P.nb) { bs = 0; bph ^= 1; }
+                        }
+                        if (!ok) break;
+                        fbc_mbar_arrive_remote(fbc_mapa(pa_full0 + 8u * as, 0u));
+                        if (++as == P.na) { as = 0; aph ^= 1; }
+                    }
+            }
+        } else if (lane == 0) {
+            // ------------------------------------------------------------ MMA issuer
             const fbc_u32 idesc0 = (1u << 4)                                 // D: FP32
                                    | (1u << 7) | (1u << 10)                  // A, B: BF16
-                                   | ((fbc_u32)(FBC_TC_TILE_M >> 4) << 24);  // M; N per work item
+                                   | ((fbc_u32)((PAIR ? 2 : 1) * FBC_TC_TILE_M >> 4) << 24);  // M; N per item
             // descriptor arithmetic: the start address sits in the low 14 bits as
             // (addr >> 4); every shared address is < 2^18, so adding (offset >> 4)
             // to the descriptor never carries out of that field
@@ -305,50 +377,58 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
             for (int k = 0; k < my_tiles && ok; ++k) {
                 const int acc = acc_it & 1;
                 if (!(ok = fbc_wait(acc_empty0 + 8u * acc, ((acc_it >> 1) & 1) ^ 1, P, abort_flag,
-                                    FBC_TC_ERR_WAIT_ACC)))
+                                        FBC_TC_ERR_WAIT_ACC)))
                     break;
                 fbc_tc_fence_after();
                 const fbc_u32 d_tmem = tmem + (fbc_u32)(acc * FBC_TC_ACC_COLS);
-                // B operand geometry of this work item (a tail half has 128 columns)
-                const int nt_k = item_of(k).nt;
+                // B operand geometry of this work item (a tail half has 128 columns;
+                // a pair's N = 256 takes 128 B rows from each CTA)
+                const Item itk = item_of(k);
+                const int nt_k = itk.nt;
                 const fbc_u32 idesc = idesc0 | ((fbc_u32)(nt_k >> 3) << 17);
-                const fbc_u32 bplane_i = (fbc_u32)nt_k * 16u;
+                const fbc_u32 bplane_i = (fbc_u32)itk.bn * 16u;
                 const fbc_u32 bhalf_i = NC * bplane_i;
                 const fbc_u64 bk = (2 * bplane_i) >> 4, blo = ((fbc_u64)BT * bhalf_i) >> 4, btap = bhalf_i >> 4;
                 fbc_u32 accumulate = 0;
                 for (int i = 0; i < P.fh && ok; ++i) {
                     if (!(ok = fbc_wait(a_full0 + 8u * as, aph, P, abort_flag, FBC_TC_ERR_WAIT_A))) break;
+                    if (PAIR && !(ok = fbc_wait(pa_full0 + 8u * as, aph, P, abort_flag, FBC_TC_ERR_WAIT_A))) break;
 #pragma unroll
                     for (int s = 0; s < NST; ++s) {
                         // RES: stage (filter row i, s) stays in slot i * NST + s; its
                         // copy is waited for by the first work item only
                         const int slot = RES ? i * NST + s : bs;
                         if (!RES || k == 0)
-                            if (!(ok = fbc_wait(b_full0 + 8u * slot, RES ? 0u : bph, P, abort_flag, FBC_TC_ERR_WAIT_B)))
+                            if (!(ok = fbc_wait(b_full0 + 8u * slot, RES ? 0u : bph, P, abort_flag,
+                                                    FBC_TC_ERR_WAIT_B)))
                                 break;
                         const fbc_u64 bdesc =
                             fbc_smem_desc(sbase + P.b_off + (fbc_u32)slot * P.b_stage, bplane_i, 128);
 #pragma unroll
                         for (int t = 0; t < BT; ++t)
                             if (s * BT + t < FW)
-                                fbc_issue_tap<NC, SPLIT>(d_tmem, adesc + (fbc_u64)(s * BT + t), bdesc + (fbc_u64)t * btap,
-                                                         ak, bk, alo, blo, idesc, accumulate);
+                                fbc_issue_tap<NC, SPLIT, CG>(d_tmem, adesc + (fbc_u64)(s * BT + t),
+                                                             bdesc + (fbc_u64)t * btap, ak, bk, alo, blo, idesc,
+                                                             accumulate);
                         issued = true;
                         if constexpr (!RES) {
-                            fbc_umma_commit(b_empty0 + 8u * bs);
+                            fbc_umma_commit<CG>(b_empty0 + 8u * bs);
+                            if (PAIR) fbc_umma_commit<CG>(fbc_mapa(b_empty0 + 8u * bs, 1u));
                             if (++bs == P.nb) { bs = 0; bph ^= 1; }
                         }
                     }
                     if (!ok) break;
-                    fbc_umma_commit(a_empty0 + 8u * as);
+                    fbc_umma_commit<CG>(a_empty0 + 8u * as);
+                    if (PAIR) fbc_umma_commit<CG>(fbc_mapa(a_empty0 + 8u * as, 1u));
                     if (++as == P.na) { as = 0; aph ^= 1; adesc = adesc0; } else { adesc += a_step; }
                 }
                 if (!ok) break;
-                fbc_umma_commit(acc_full0 + 8u * acc);
+                fbc_umma_commit<CG>(acc_full0 + 8u * acc);
+                if (PAIR) fbc_umma_commit<CG>(fbc_mapa(acc_full0 + 8u * acc, 1u));
                 ++acc_it;
             }
             if (!ok && issued) {
-                fbc_umma_commit(drain_bar);
+                fbc_umma_commit<CG>(drain_bar);
                 fbc_wait_drain(drain_bar, 0, P);
             }
         }
@@ -365,9 +445,19 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
         const fbc_u32 st_base = ((sbase + P.st_off + 1023u) & ~1023u) + (fbc_u32)(ew * SB * FBC_TC_ST_BOX);
         int st_slot = 0;
         fbc_u32 acc_it = 0;
+        // the accumulator is free again: this CTA's arrival, or for the odd CTA of
+        // a pair a remote arrival on the even CTA's barrier (count 2 EW there)
+        const fbc_u32 acc_release0 = (PAIR && rank != 0) ? fbc_mapa(acc_empty0, 0u) : acc_empty0;
+        auto release_acc = [&](int acc) {
+            if (PAIR && rank != 0)
+                fbc_mbar_arrive_remote(acc_release0 + 8u * acc);
+            else
+                fbc_mbar_arrive(acc_empty0 + 8u * acc);
+        };
         for (int k = 0; k < my_tiles; ++k) {
             const Item itm = item_of(k);
-            const int mt = itm.tile % P.mtiles;
+            // a pair's odd CTA may hold tile mtiles (past the image): no wrap-around
+            const int mt = PAIR ? itm.tile : itm.tile % P.mtiles;
             const int nt_i = itm.nt;     // filter columns of this work item, from column 0 of the accumulator
             const int nb0 = itm.n0;      // its first filter
             const int acc = acc_it & 1;
@@ -437,7 +527,7 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
                 }
                 fbc_tc_fence_before();
                 __syncwarp();
-                if (lane == 0) fbc_mbar_arrive(acc_empty0 + 8u * acc);
+                if (lane == 0) release_acc(acc);
                 ++acc_it;
                 continue;
             }
@@ -490,7 +580,7 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
                     }
                     fbc_tc_fence_before();
                     __syncwarp();
-                    if (lane == 0) fbc_mbar_arrive(acc_empty0 + 8u * acc);
+                    if (lane == 0) release_acc(acc);
                     ++acc_it;
                     continue;
                 }
@@ -547,7 +637,7 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
             }
             fbc_tc_fence_before();
             __syncwarp();
-            if (lane == 0) fbc_mbar_arrive(acc_empty0 + 8u * acc);
+            if (lane == 0) release_acc(acc);
             ++acc_it;
         }
         // tiled stores still in flight read this CTA's shared memory: finish them
@@ -559,7 +649,7 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
         // Thread ct owns the 32-byte chunks item = ct + k*32*CW (pixel item / NC,
         // plane item % NC)
         // of every row: FUSE = 1 loads them from x in global memory (a warp reads
-        // 1 KB contiguously) one row ahead of the conversion, FUSE = 2 reads them
+        // 1 KB contiguously) two rows ahead of the conversion, FUSE = 2 reads them
         // from the raw-row slot the producer filled.  Generic-proxy shared-memory
         // writes are made visible to the tensor core's async proxy by
         // fence.proxy.async before the arrival on a_full.
@@ -571,8 +661,12 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
         int as = 0, rs = 0;
         fbc_u32 aph = 0, rph = 0;
         if constexpr (FUSE == 1) {
-            float4 nxt[KI][2];
-            auto load_row = [&](int r) {
+            // two register buffers, even and odd rows: row r + 2 is loaded into the
+            // buffer of row r as soon as row r is converted, so a load has about two
+            // rows of MMAs to arrive (one row of plain-BF16 MMAs is shorter than a
+            // load under load); the same 2 x KI x 32 bytes as a row held while the
+            // next one loads
+            auto load_row = [&](int r, float4 (&buf)[KI][2]) {
                 const long long p0 = row_p0(r);
 #pragma unroll
                 for (int k = 0; k < KI; ++k) {
@@ -586,20 +680,12 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
                         if (c * 8 < P.D) v0 = __ldg(reinterpret_cast<const float4*>(src));
                         if (c * 8 + 4 < P.D) v1 = __ldg(reinterpret_cast<const float4*>(src + 4));
                     }
-                    nxt[k][0] = v0;
-                    nxt[k][1] = v1;
+                    buf[k][0] = v0;
+                    buf[k][1] = v1;
                 }
             };
-            if (R > 0) load_row(0);
-            for (int r = 0; r < R; ++r) {
-                float4 cur[KI][2];
-#pragma unroll
-                for (int k = 0; k < KI; ++k) {
-                    cur[k][0] = nxt[k][0];
-                    cur[k][1] = nxt[k][1];
-                }
-                if (r + 1 < R) load_row(r + 1);
-                if (!fbc_wait(a_empty0 + 8u * as, aph ^ 1, P, abort_flag, FBC_TC_ERR_WAIT_EMPTY)) break;
+            auto convert_row = [&](const float4 (&buf)[KI][2]) -> bool {
+                if (!fbc_wait(a_empty0 + 8u * as, aph ^ 1, P, abort_flag, FBC_TC_ERR_WAIT_EMPTY)) return false;
                 fbc_u8* dst = fbc_tc_smem + P.a_off + as * P.a_slot;
 #pragma unroll
                 for (int k = 0; k < KI; ++k) {
@@ -607,8 +693,8 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
                     if (item < NITEMS) {
                         const int px = item / NC;
                         const int c = item - px * NC;
-                        const float v[8] = {cur[k][0].x, cur[k][0].y, cur[k][0].z, cur[k][0].w,
-                                            cur[k][1].x, cur[k][1].y, cur[k][1].z, cur[k][1].w};
+                        const float v[8] = {buf[k][0].x, buf[k][0].y, buf[k][0].z, buf[k][0].w,
+                                            buf[k][1].x, buf[k][1].y, buf[k][1].z, buf[k][1].w};
                         fbc_split8<SPLIT>(v, reinterpret_cast<uint4*>(dst + c * plane + px * 16),
                                           reinterpret_cast<uint4*>(dst + a_half + c * plane + px * 16));
                     }
@@ -617,6 +703,16 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
                 __syncwarp();
                 if (lane == 0) fbc_mbar_arrive(a_full0 + 8u * as);
                 if (++as == P.na) { as = 0; aph ^= 1; }
+                return true;
+            };
+            float4 even[KI][2], odd[KI][2];
+            if (R > 0) load_row(0, even);
+            if (R > 1) load_row(1, odd);
+            for (int r = 0; r < R; r += 2) {
+                if (!convert_row(even)) break;
+                if (r + 2 < R) load_row(r + 2, even);
+                if (r + 1 >= R || !convert_row(odd)) break;
+                if (r + 3 < R) load_row(r + 3, odd);
             }
         } else {
             for (int r = 0; r < R; ++r) {
@@ -663,8 +759,17 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
     }
     __syncwarp();
     fbc_tc_fence_before();
-    __syncthreads();
+    // a pair: neither CTA leaves (or frees TMEM) while the other may still reach
+    // its shared memory or TMEM, or arrive on its barriers
+    if constexpr (PAIR)
+        fbc_cluster_sync();
+    else
+        __syncthreads();
     fbc_tc_fence_after();
-    if (warp == 1)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(FBC_TC_TMEM_COLS));
+    if (warp == 1) {
+        if constexpr (PAIR)
+            asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(FBC_TC_TMEM_COLS));
+        else
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(FBC_TC_TMEM_COLS));
+    }
 }

@@ -158,6 +158,7 @@ struct TcConfig {
     int ts = 0;                        // epilogue stores: 0 direct, 32 tiled (32-pixel boxes)
     int sb = 0;                        // staging slots per epilogue warp (ts = 32): 1..3
     int rs = 0;                        // 1: the B ring holds the CTA's whole filter tile (resident bank)
+    int cg = 0;                        // 2: CTA pairs (clusters of two, cta_group::2 MMAs, M = 256)
 };
 
 struct TcPlan {
@@ -193,6 +194,7 @@ std::string tc_kernel_name(int nc, int split, int fw, const TcConfig& c, const s
     std::string name = b;
     if (c.ts) name += "_t" + std::to_string(c.ts) + "s" + std::to_string(c.sb);
     if (c.rs) name += "_r";
+    if (c.cg) name += "_p";
     return snippet.empty() ? name : name + "_u" + snippet_tag(snippet);
 }
 
@@ -204,12 +206,12 @@ std::string tc_kernel_source(int nc, int split, int fw, const TcConfig& c, const
       << snippet_definition(snippet);
     o << "static_assert(sizeof(FbcTcParams) == " << sizeof(FbcTcParams)
       << ", \"host and device disagree on the parameter block\");\n";
-    o << "extern \"C\" __global__ void __launch_bounds__("
+    o << "extern \"C\" __global__ void " << (c.cg ? "__cluster_dims__(2, 1, 1) " : "") << "__launch_bounds__("
       << tc_threads(c) << ", 1) "
       << tc_kernel_name(nc, split, fw, c, snippet) << "(const __grid_constant__ FbcTcParams P) {\n"
       << "  fbc_tc_corr_body<" << nc << "," << split << "," << fw << "," << c.bt << "," << c.ew << ","
       << c.fuse << "," << c.cw << "," << (snippet.empty() ? 0 : 1) << "," << c.ts << "," << (c.ts ? c.sb : 1)
-      << "," << c.rs << ">(P);\n}\n";
+      << "," << c.rs << "," << (c.cg ? 1 : 0) << ">(P);\n}\n";
     return o.str();
 }
 
@@ -277,7 +279,13 @@ bool tc_layout(TcPlan* p, const TcConfig& c, bool commit) {
     if (c.bt < 1 || c.bt > p->fw || (c.ew != 4 && c.ew != 8)) return false;
     if (c.fuse < 0 || c.fuse > 2 || !fuse_ok(c.fuse, c.cw, p->D, nc, p->fw)) return false;
     if ((c.fuse == 2) != (c.nr > 0) || c.nr > 4) return false;
-    const uint32_t b_stage = (uint32_t)align_up((size_t)c.bt * nc * nt * 16 * halves, 128);
+    // CTA pairs: one filter tile of 256 (each CTA stages half of it from the
+    // half-width planes), streamed (not resident), at least one pair of SMs
+    if (c.cg != 0 && (c.cg != 2 || ntn != 1 || nt != 256 || c.rs != 0 || p->sm_count < 2)) return false;
+    // a pair relays whole filter rows: the B ring holds at least one row's stages
+    if (c.cg && c.nb < (p->fw + c.bt - 1) / c.bt) return false;
+    const int bn = c.cg ? nt / 2 : nt;   // B rows this CTA stages
+    const uint32_t b_stage = (uint32_t)align_up((size_t)c.bt * nc * bn * 16 * halves, 128);
     const uint32_t raw_slot = (uint32_t)align_up((size_t)(kTileM + p->fw - 1) * p->D * 4, 128);
     if (c.na < 2 || c.nb < 2 || (c.fuse == 2 && c.nr < 2)) return false;
     if (!ts_ok(c.ts, c.sb, p->W, p->N, nt)) return false;
@@ -286,8 +294,9 @@ bool tc_layout(TcPlan* p, const TcConfig& c, bool commit) {
     if (c.rs != 0 && (c.rs != 1 || c.nb != p->fh * ((p->fw + c.bt - 1) / c.bt) || ntn > std::max(1, p->sm_count)))
         return false;
     // the barrier table: a_full / a_empty per A slot, b_full / b_empty per B stage,
-    // two accumulator pairs, the drain barrier, raw_full / raw_empty per raw slot
-    if (8 * (2 * c.na + 2 * c.nb + 5 + 2 * c.nr) > 512) return false;
+    // two accumulator pairs, the drain barrier, raw_full / raw_empty per raw slot,
+    // and for a pair pa_full per A slot
+    if (8 * (2 * c.na + 2 * c.nb + 5 + 2 * c.nr + (c.cg ? c.na : 0)) > 512) return false;
     // staging: a 1024-byte aligned run of ew * sb boxes placed after the barriers
     const size_t staging = c.ts ? (size_t)c.ew * c.sb * FBC_TC_ST_BOX + 1024 : 0;
     const size_t need = (size_t)c.na * a_slot + (size_t)c.nb * b_stage + (size_t)c.nr * raw_slot + 512 + staging;
@@ -304,8 +313,9 @@ bool tc_layout(TcPlan* p, const TcConfig& c, bool commit) {
     // of the CTAs idle, its tiles run as two 128-column halves each
     const int grid_full = std::min(mtiles * ntn, std::max(1, p->sm_count));
     const int rem = (mtiles * ntn) % grid_full;
-    const bool tail_halves = !c.rs && ntn == 1 && nt == 256 && rem > 0 && 2 * rem <= grid_full &&
+    const bool tail_halves = !c.rs && !c.cg && ntn == 1 && nt == 256 && rem > 0 && 2 * rem <= grid_full &&
                              env_str("FBCORR_TAIL_HALVES", "1") != "0";
+    const bool half_planes = tail_halves || c.cg;   // B from the half-width planes
     k.nfull = tail_halves ? mtiles * ntn - rem : mtiles * ntn;
     k.lp = lp; k.na = c.na; k.nb = c.nb;
     k.a_slot = a_slot; k.b_stage = b_stage;
@@ -324,6 +334,10 @@ bool tc_layout(TcPlan* p, const TcConfig& c, bool commit) {
     k.drop_b = p->drop_b;
     k.st_off = k.bar_off + 512;
     p->smem = k.st_off + staging;
+    // a pair's CTAs must sit on two SMs, one CTA per SM: with room for two CTAs
+    // in one SM's shared memory two CTAs of different pairs could share an SM,
+    // and pairs waiting for each other's TMEM could deadlock
+    if (c.cg) p->smem = std::max(p->smem, kSmemMax / 2 + 4096);
     p->map_y = nullptr;   // re-encode for the next call
 
     const size_t xplanes = (size_t)nc * k.npix_pad * 16;
@@ -333,8 +347,8 @@ bool tc_layout(TcPlan* p, const TcConfig& c, bool commit) {
     p->off_xlo = off; if (p->split) off = align_up(off + xplanes, 256);
     p->off_whi = off; off = align_up(off + wplanes, 256);
     p->off_wlo = off; if (p->split) off = align_up(off + wplanes, 256);
-    p->off_whi2 = off; if (tail_halves) off = align_up(off + wplanes, 256);
-    p->off_wlo2 = off; if (tail_halves && p->split) off = align_up(off + wplanes, 256);
+    p->off_whi2 = off; if (half_planes) off = align_up(off + wplanes, 256);
+    p->off_wlo2 = off; if (half_planes && p->split) off = align_up(off + wplanes, 256);
     p->ws_end = off;
 
     SplitParams& sp = p->sp;
@@ -343,7 +357,7 @@ bool tc_layout(TcPlan* p, const TcConfig& c, bool commit) {
     sp.npix_pad = k.npix_pad;
     sp.D = p->D; sp.nc = nc; sp.N = p->N; sp.fh = p->fh; sp.fw = p->fw; sp.nt = nt; sp.ntn = ntn;
     sp.split = p->split;
-    sp.halves = tail_halves ? 1 : 0;
+    sp.halves = half_planes ? 1 : 0;
     sp.xblocks = (k.npix_pad + 255) / 256;
     const long long wblocks = ((long long)ntn * p->fh * p->fw * nt + 255) / 256;
     if (c.fuse) sp.xblocks = 0;   // x is converted inside the correlation kernel
@@ -352,6 +366,8 @@ bool tc_layout(TcPlan* p, const TcConfig& c, bool commit) {
     // filter-tile count, each group of ntn CTAs sharing the pixel tiles
     if (c.rs)
         p->grid = ntn * std::min(mtiles, std::max(1, p->sm_count / ntn));
+    else if (c.cg)   // pairs of tiles, one pair of CTAs per pair of SMs
+        p->grid = 2 * std::min((mtiles + 1) / 2, std::max(1, p->sm_count / 2));
     else
         p->grid = std::min(mtiles * ntn, std::max(1, p->sm_count));
     return true;
@@ -366,7 +382,7 @@ size_t tc_ws_need(TcPlan* p, const TcConfig& c) {
     return tmp.ws_end;
 }
 
-std::vector<TcConfig> tc_candidate_configs(TcPlan* p) {
+std::vector<TcConfig> tc_candidate_configs(TcPlan* p, bool pairs) {
     // widest filter tile first; within it raw-ring conversion, register
     // conversion, pre-pass; taps per stage from the most (fewest copies and
     // barrier handoffs) down, each with the deepest B ring that fits.  Every
@@ -404,6 +420,25 @@ std::vector<TcConfig> tc_candidate_configs(TcPlan* p) {
                             }
             }
     }
+    // CTA pairs (cg = 2): the same family over one 256-wide filter tile, each
+    // CTA's B stages half as large (deeper rings in the same shared memory)
+    if (pairs)
+        for (int fuse = 2; fuse >= 0; --fuse)
+            for (int cw : fuse ? std::vector<int>{8, 4} : std::vector<int>{0}) {
+                if (!fuse_ok(fuse, cw, p->D, p->nc, p->fw)) continue;
+                for (int nr : fuse == 2 ? std::vector<int>{3, 2} : std::vector<int>{0})
+                    for (int bt = std::min(p->fw, 5); bt >= 1; --bt)
+                        for (int ew : {8, 4})
+                            for (int na = 2; na <= 3; ++na)
+                                for (int ts : {0, 1, 32}) {
+                                    if (ew != 8 && ts == 1) continue;
+                                    TcConfig c{na, 0, 256, bt, ew, fuse, nr, cw};
+                                    c.ts = ts;
+                                    c.sb = ts ? 1 : 0;
+                                    c.cg = 2;
+                                    if ((c.nb = deepest(c))) out.push_back(c);
+                                }
+            }
     // resident bank (rs = 1): the ring holds all fh * ceil(fw / bt) stages of a
     // filter tile, loaded once per CTA; offered wherever a filter tile fits in
     // shared memory beside the A slots (plain BF16 of the headline shape: 128
@@ -429,6 +464,10 @@ std::vector<TcConfig> tc_candidate_configs(TcPlan* p) {
     return out;
 }
 
+// CTA-pair configurations among the tuning candidates (FBCORR_TC_PAIR=0 leaves
+// them out; a pair spec can still be set explicitly).
+bool pairs_offered() { return env_str("FBCORR_TC_PAIR", "1") != "0"; }
+
 std::string format_spec(const TcConfig& c) {
     char b[128];
     snprintf(b, sizeof b, "tcgen05:na=%d,nb=%d,nt=%d,bt=%d,ew=%d,fz=%d,nr=%d,cw=%d", c.na, c.nb, c.ntmax,
@@ -436,6 +475,7 @@ std::string format_spec(const TcConfig& c) {
     std::string out = b;
     if (c.ts) out += ",ts=" + std::to_string(c.ts) + ",sb=" + std::to_string(c.sb);
     if (c.rs) out += ",rs=1";
+    if (c.cg) out += ",cg=2";
     return out;
 }
 
@@ -445,16 +485,21 @@ bool parse_tc_spec(const std::string& s, TcConfig* c) {
     const int n = sscanf(s.c_str(), "tcgen05:na=%d,nb=%d,nt=%d,bt=%d,ew=%d,fz=%d,nr=%d,cw=%d%n", &t.na, &t.nb,
                          &t.ntmax, &t.bt, &t.ew, &t.fuse, &t.nr, &t.cw, &used);
     if (n != 8) return false;
-    // optional suffixes, in this order: staged / tiled stores, resident bank
+    // optional suffixes, in this order: staged / tiled stores, resident bank, CTA pairs
     int used2 = 0;
     if (sscanf(s.c_str() + used, ",ts=%d,sb=%d%n", &t.ts, &t.sb, &used2) == 2) {
         if ((t.ts != 32 && t.ts != 1) || t.sb < 1 || t.sb > 3 || (t.ts == 1 && t.sb != 1)) return false;
         used += used2;
     }
-    if (s.compare(used, std::string::npos, ",rs=1") == 0) {
+    if (s.compare(used, 5, ",rs=1") == 0) {
         t.rs = 1;
         used += 5;
     }
+    if (s.compare(used, 5, ",cg=2") == 0) {
+        t.cg = 2;
+        used += 5;
+    }
+    if (t.rs && t.cg) return false;
     if (used != (int)s.size()) return false;
     if ((t.fuse == 0) != (t.cw == 0) || (t.cw != 0 && t.cw != 4 && t.cw != 8)) return false;
     if (t.fuse < 0 || t.fuse > 2 || (t.ew != 4 && t.ew != 8)) return false;
@@ -485,7 +530,7 @@ std::string tc_spec(const TcPlan* p) { return format_spec(p->cfg); }
 
 std::vector<std::string> tc_candidates(TcPlan* p) {
     std::vector<std::string> out;
-    for (const auto& c : tc_candidate_configs(p)) out.push_back(format_spec(c));
+    for (const auto& c : tc_candidate_configs(p, pairs_offered())) out.push_back(format_spec(c));
     return out;
 }
 
@@ -530,7 +575,8 @@ fbcorr_status_t tc_plan_create(TcPlan** out, int H, int W, int D, int N, int fh,
     const long long wait_ms = atoll(env_str("FBCORR_WAIT_MS", "4000").c_str());
     p->wait_ns = (unsigned long long)std::max(1LL, wait_ms) * 1000000ull;
     p->drop_b = fault_injected("tcdrop") ? 0 : -1;   // the first B stage: every CTA has one
-    const std::vector<TcConfig> cands = tc_candidate_configs(p);
+    // the workspace covers every configuration, CTA pairs included
+    const std::vector<TcConfig> cands = tc_candidate_configs(p, true);
     if (cands.empty()) {
         delete p;
         return set_error(FBCORR_ERR_UNSUPPORTED, "shape needs more shared memory than one SM has");
@@ -557,8 +603,9 @@ int tc_launches(const TcPlan*) { return 2; }
 
 std::string tc_describe(const TcPlan* p) {
     std::ostringstream o;
-    o << "{\"precision\":\"" << (p->split ? "bf16x3" : "bf16") << "\",\"mma\":\"128x" << p->kp.nt
-      << "x16\",\"filter_tiles\":" << p->kp.ntn << ",\"tiles\":" << p->kp.mtiles * p->kp.ntn
+    o << "{\"precision\":\"" << (p->split ? "bf16x3" : "bf16") << "\",\"mma\":\""
+      << (p->cfg.cg ? "256x" : "128x") << p->kp.nt << "x16" << (p->cfg.cg ? " (CTA pair)" : "")
+      << "\",\"filter_tiles\":" << p->kp.ntn << ",\"tiles\":" << p->kp.mtiles * p->kp.ntn
       << ",\"tail_half_tiles\":" << (p->kp.mtiles * p->kp.ntn - std::min(p->kp.nfull, p->kp.mtiles * p->kp.ntn))
       << ",\"smem\":" << p->smem << ",\"grid\":" << p->grid << ",\"threads\":" << tc_threads(p->cfg)
       << ",\"kernel\":\"" << tc_kernel_name(p->nc, p->split, p->fw, p->cfg, p->snippet) << "\"";

@@ -186,6 +186,9 @@ def test_ksplit_tiles_compile(lib, D, N, spec):
     (32, 5, b"tcgen05:na=2,nb=3,nt=256,bt=1,ew=4,fz=1,nr=0,cw=4,ts=32,sb=3"),       # three staging slots
     (32, 5, b"tcgen05:na=2,nb=5,nt=128,bt=5,ew=4,fz=1,nr=0,cw=8,rs=1"),             # resident bank
     (16, 3, b"tcgen05:na=3,nb=3,nt=256,bt=3,ew=8,fz=2,nr=2,cw=8,ts=1,sb=1,rs=1"),   # resident, staged stores
+    (32, 5, b"tcgen05:na=2,nb=8,nt=256,bt=1,ew=4,fz=1,nr=0,cw=8,ts=32,sb=1,cg=2"),  # CTA pair, tiled stores
+    (32, 5, b"tcgen05:na=3,nb=6,nt=256,bt=3,ew=8,fz=2,nr=3,cw=8,cg=2"),             # CTA pair, raw-row ring
+    (16, 3, b"tcgen05:na=3,nb=4,nt=256,bt=2,ew=8,fz=0,nr=0,cw=0,ts=1,sb=1,cg=2"),   # CTA pair, pre-pass, staged
 ])
 def test_tensor_core_kernels_compile(lib, D, f, spec):
     """The run-time generated tcgen05 kernel of a spec compiles for sm_103a in
@@ -210,6 +213,9 @@ def test_tensor_core_kernels_compile(lib, D, f, spec):
     (32, 5, b"tcgen05:na=2,nb=4,nt=256,bt=2,ew=8,fz=1,nr=0,cw=8,ts=1,sb=1,", 1),   # nothing after the suffix
     (32, 5, b"tcgen05:na=2,nb=5,nt=128,bt=5,ew=4,fz=1,nr=0,cw=8,rs=2", 1),          # rs=1 only
     (32, 5, b"tcgen05:na=2,nb=5,nt=128,bt=5,ew=8,fz=1,nr=0,cw=8,rs=1,ts=1,sb=1", 1),   # stores before rs
+    (32, 5, b"tcgen05:na=2,nb=5,nt=256,bt=5,ew=4,fz=1,nr=0,cw=8,cg=1", 1),          # cg=2 only
+    (32, 5, b"tcgen05:na=2,nb=5,nt=256,bt=5,ew=4,fz=1,nr=0,cw=8,cg=2,rs=1", 1),     # rs before cg
+    (32, 5, b"tcgen05:na=2,nb=5,nt=256,bt=5,ew=4,fz=1,nr=0,cw=8,rs=1,cg=2", 1),     # a pair streams the bank
 ])
 def test_tensor_core_spec_refusals(lib, D, f, spec, status):
     log = ctypes.create_string_buffer(1 << 16)

@@ -377,3 +377,68 @@ def test_resident_bank_bit_exact(mode, shape):
         ran += 1
     if mode == "bf16" and shape[2] <= 32 and shape[3] <= 256:
         assert ran >= 1
+
+
+PAIR_SHAPES = [
+    # one 256-wide filter tile: an odd pixel-tile count (the odd CTA of the last
+    # pair holds a tile past the image), W not a multiple of 32, six and eight
+    # chunk planes, 1x1 filters, N padded to 256
+    (41, 64, 32, 256, 5, 5),
+    (40, 200, 32, 256, 5, 5),
+    (18, 128, 48, 256, 7, 7),
+    (30, 131, 64, 256, 1, 1),
+    (12, 96, 8, 250, 3, 3),
+]
+
+
+def _single_cta(spec, p, C):
+    """A single-CTA kernel: the same configuration (with a two-stage ring when
+    the pair's ring does not fit), else the first single-CTA candidate -- every
+    tensor-core variant sums the same products in the same order."""
+    base = spec.replace(",cg=2", "")
+    cands = [base, base.split(",nb=")[0] + ",nb=2," + base.split(",nb=")[1].split(",", 1)[1]]
+    cands += [s for s in p.candidates() if ",cg=2" not in s][:1]
+    for cand in cands:
+        try:
+            p.set_variant(cand)
+            return cand
+        except C.FbcorrError:
+            continue
+    return None
+
+
+@pytest.mark.parametrize("mode", ["bf16", "bf16x3"])
+@pytest.mark.parametrize("shape", PAIR_SHAPES, ids=lambda s: "x".join(map(str, s)))
+def test_cta_pair_bit_exact(mode, shape):
+    """cg=2 runs each pair of 128-pixel tiles as one M = 256 tile on two SMs
+    (cta_group::2 MMAs, half of the bank staged in each CTA): the same products
+    summed in the same order as the single-CTA kernel, so the same bits, with
+    every conversion path (pre-pass, converters, raw-row ring) and store path;
+    on integer inputs the oracle's."""
+    torch = torch_cuda()
+    from paper_0911_3456_gb300 import _capi as C
+    from paper_0911_3456_gb300.api import Plan
+    H, W, D, N, fh, fw = shape
+    clamp = (-0.5, 0.75) if shape[0] == 12 else None
+    p = Plan((H, W, D), (N, fh, fw, D), mode, clamp)
+    pairs = [s for s in p.candidates() if s.endswith(",cg=2")]
+    assert pairs, "a single 256-wide filter tile offers CTA pairs"
+    # one configuration per (conversion, store path)
+    picked = {}
+    for s in pairs:
+        key = (s.split(",fz=")[1][0], s.split(",ts=")[1].split(",")[0] if ",ts=" in s else "0")
+        picked.setdefault(key, s)
+    for spec in picked.values():
+        for kind in ("int", "real"):
+            wl = inputs.random_case(2200, *shape, kind=kind)
+            x, w = dev(wl.x, torch), dev(wl.w, torch)
+            p.set_variant(spec)
+            assert p.info()["fwd"]["detail"]["mma"].startswith("256x256x16")
+            y_pair = host(p.forward(x, w))
+            assert p.device_status() == 0, spec
+            single = _single_cta(spec, p, C)
+            assert single is not None, spec
+            y_one = host(p.forward(x, w))
+            assert np.array_equal(y_pair, y_one), (spec, single)
+            if kind == "int":
+                assert np.array_equal(y_pair, oracle.fwd(wl.x, wl.w, epilogue=clamp)), spec
