@@ -31,18 +31,20 @@ class _env:
                 os.environ[k] = v
 
 
-@pytest.mark.parametrize("spec", [None, "tcgen05:na=2,nb=3,nt=256,bt=1,ew=8,fz=1,nr=0,cw=8,ts=1,sb=1"],
-                         ids=["default", "staged_stores"])
-def test_dropped_copy_times_out_and_context_survives(spec):
+@pytest.mark.parametrize("spec,N", [(None, 32), ("tcgen05:na=2,nb=3,nt=256,bt=1,ew=8,fz=1,nr=0,cw=8,ts=1,sb=1", 32),
+                                    ("tcgen05:na=2,nb=4,nt=256,bt=1,ew=4,fz=1,nr=0,cw=8,cg=2", 256)],
+                         ids=["default", "staged_stores", "cta_pair"])
+def test_dropped_copy_times_out_and_context_survives(spec, N):
     """FBCORR_FAULT=tcdrop makes the producer skip one copy that the MMA warp
     waits for -- an arrival that never comes.  Every wait is bounded (here
     50 ms): the kernel records FBCORR_ERR_TIMEOUT in host-mapped memory, drains
     its own copies and MMAs, frees TMEM and returns; the next plan on the same
-    context computes correct results, with the default variant and with the
-    staged-store epilogue."""
+    context computes correct results, with the default variant, with the
+    staged-store epilogue, and with CTA pairs (both CTAs of a pair give up on
+    their own bounded waits and meet at the closing cluster barrier)."""
     torch = torch_cuda()
     from paper_0911_3456_gb300.api import Plan
-    wl = inputs.random_case(3000, 20, 150, 16, 32, 3, 3)
+    wl = inputs.random_case(3000, 20, 150, 16, N, 3, 3)
     x, w = dev(wl.x, torch), dev(wl.w, torch)
     with _env(FBCORR_FAULT="tcdrop", FBCORR_WAIT_MS="50"):
         bad = Plan(wl.x.shape, wl.w.shape, "bf16x3")
