@@ -267,11 +267,14 @@ __global__ void __launch_bounds__(128) fbc_nn_finalize(const NnFinalizeArgs A) {
     }
 }
 
-// Exact re-scan of one incomplete part per block (grid-stride over the listed
-// entries): the part's neighbours are the 32-column chunks part, part + parts,
-// ... of the tiles of its chunk; each thread takes the exact FP32 distance of
-// its neighbours (the target in shared memory), and the smallest key of each
-// warp goes to the target's best_key by atomicMin.
+// Exact re-scan of the incomplete parts.  A part's neighbours are the 32-column
+// chunks part, part + parts, ... of the tiles of its chunk; the work units are
+// (listed part, step of kScanRows of its neighbours), spread over the grid so
+// that a few hundred parts keep every SM busy.  A unit stages its rows in shared
+// memory (16-byte loads when the rows allow), each thread takes the exact FP32
+// distance of one neighbour (the target in shared memory, the same sequential
+// fmaf order as everywhere), and the smallest key of each warp goes to the
+// target's best_key by atomicMin.
 struct NnPartScanArgs {
     const NnStats* stats;
     const int2* entries;
@@ -293,7 +296,14 @@ __global__ void __launch_bounds__(kScanRows) fbc_nn_part_scan(const NnPartScanAr
     const int tid = threadIdx.x;
     const int cols = (256 / 32) / A.parts;                  // 32-column chunks per tile in one part
     const int per_part = A.chunk_tiles * cols * 32;
-    for (int e = blockIdx.x; e < cnt; e += gridDim.x) {
+    const int steps = (per_part + kScanRows - 1) / kScanRows;
+    const long long units = (long long)cnt * steps;
+    const bool vec = (A.dim & 3) == 0 && (reinterpret_cast<unsigned long long>(A.n) & 15) == 0;
+    const float inv_dim = 1.f / (float)A.dim;
+    int cur = -1;                                           // entry whose target is in tv
+    for (long long w = blockIdx.x; w < units; w += gridDim.x) {
+        const int e = (int)(w / steps);
+        const int u0 = (int)(w - (long long)e * steps) * kScanRows;
         const int2 en = A.entries[A.entry_list[e]];
         const int c = en.y / A.parts, p = en.y - c * A.parts;
         // neighbour index of the part's u-th row: runs of 32 consecutive rows
@@ -302,37 +312,52 @@ __global__ void __launch_bounds__(kScanRows) fbc_nn_part_scan(const NnPartScanAr
             const int r = u % (cols * 32);
             return (long long)jt * 256 + (p + (r >> 5) * A.parts) * 32 + (r & 31);
         };
-        __syncthreads();   // the previous entry's readers are done
-        for (int k = tid; k < A.dim; k += kScanRows) tv[k] = __ldg(A.t + (long long)en.x * A.dim + k);
-        unsigned long long key = ~0ull;
-        const float inv_dim = 1.f / (float)A.dim;
-        for (int u0 = 0; u0 < per_part; u0 += kScanRows) {
-            __syncthreads();   // the previous step's readers are done (and tv is written)
-            // kScanRows / 32 runs of 32 consecutive neighbours, each contiguous in memory
-            for (int q = 0; q < kScanRows / 32; ++q) {
-                const int u = u0 + 32 * q;
-                if (u >= per_part) break;
-                const long long j0 = row_of(u);
-                const int nrow = (int)min(32LL, A.nn - j0);
-                if (nrow <= 0) continue;
-                const float* src = A.n + j0 * A.dim;
+        __syncthreads();   // the previous unit's readers are done
+        if (e != cur) {    // block-uniform: w is
+            for (int k = tid; k < A.dim; k += kScanRows) tv[k] = __ldg(A.t + (long long)en.x * A.dim + k);
+            cur = e;
+        }
+        // kScanRows / 32 runs of 32 consecutive neighbours, each contiguous in memory
+        for (int q = 0; q < kScanRows / 32; ++q) {
+            const int u = u0 + 32 * q;
+            if (u >= per_part) break;
+            const long long j0 = row_of(u);
+            const int nrow = (int)min(32LL, A.nn - j0);
+            if (nrow <= 0) continue;
+            const float* src = A.n + j0 * A.dim;
+            float* dst = fbc_nn_prows + 32 * q * (A.dim + 1);
+            if (vec) {
+                const float4* src4 = reinterpret_cast<const float4*>(src);
+                for (int f = tid; f < nrow * A.dim / 4; f += kScanRows) {
+                    const int el = 4 * f;
+                    // el / dim: exact, since el < 32 dim puts the quotient below 32 and at
+                    // least 0.5 / dim from an integer, far above the product's rounding
+                    const int r = (int)(((float)el + 0.5f) * inv_dim);
+                    const float4 v = __ldg(src4 + f);
+                    float* o = dst + r * (A.dim + 1) + (el - r * A.dim);
+                    o[0] = v.x;
+                    o[1] = v.y;
+                    o[2] = v.z;
+                    o[3] = v.w;
+                }
+            } else {
                 for (int el = tid; el < nrow * A.dim; el += kScanRows) {
-                    const int r = (int)(((float)el + 0.5f) * inv_dim);   // el / dim, exact (el < 2^11)
-                    fbc_nn_prows[(32 * q + r) * (A.dim + 1) + (el - r * A.dim)] = __ldg(src + el);
+                    const int r = (int)(((float)el + 0.5f) * inv_dim);
+                    dst[r * (A.dim + 1) + (el - r * A.dim)] = __ldg(src + el);
                 }
             }
-            __syncthreads();
-            const long long j = row_of(u0 + tid);
-            if (u0 + tid < per_part && j < A.nn) {
-                const float* nr = fbc_nn_prows + tid * (A.dim + 1);
-                float d = 0.f;
-                for (int k = 0; k < A.dim; ++k) {
-                    const float df = tv[k] - nr[k];
-                    d = fmaf(df, df, d);
-                }
-                const unsigned long long kk = ((unsigned long long)__float_as_uint(d) << 32) | (unsigned long long)j;
-                key = kk < key ? kk : key;
+        }
+        __syncthreads();
+        unsigned long long key = ~0ull;
+        const long long j = row_of(u0 + tid);
+        if (u0 + tid < per_part && j < A.nn) {
+            const float* nr = fbc_nn_prows + tid * (A.dim + 1);
+            float d = 0.f;
+            for (int k = 0; k < A.dim; ++k) {
+                const float df = tv[k] - nr[k];
+                d = fmaf(df, df, d);
             }
+            key = ((unsigned long long)__float_as_uint(d) << 32) | (unsigned long long)j;
         }
 #pragma unroll
         for (int m2 = 16; m2 >= 1; m2 >>= 1) {

@@ -265,13 +265,20 @@ __device__ __forceinline__ void fbc_nn_body(const FbcNnParams& P) {
                     if (i + 1 < NCH)   // the next chunk's load runs while this one is processed
                         fbc_tmem_ld32x32b_x32_async(trow + (fbc_u32)((cc + EW / 4) * 32), r[(i + 1) & 1]);
                     float d[32];
+                    const float2 neg2 = make_float2(-2.f, -2.f);
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
                         const uint4 nv = fbc_ld_shared_v4(nrm + (fbc_u32)(cc * 32 + 4 * q) * 4u);
-                        d[4 * q + 0] = fmaf(-2.f, __uint_as_float(r[i & 1][4 * q + 0]), __uint_as_float(nv.x));
-                        d[4 * q + 1] = fmaf(-2.f, __uint_as_float(r[i & 1][4 * q + 1]), __uint_as_float(nv.y));
-                        d[4 * q + 2] = fmaf(-2.f, __uint_as_float(r[i & 1][4 * q + 2]), __uint_as_float(nv.z));
-                        d[4 * q + 3] = fmaf(-2.f, __uint_as_float(r[i & 1][4 * q + 3]), __uint_as_float(nv.w));
+                        const float2 p0 = __ffma2_rn(neg2, make_float2(__uint_as_float(r[i & 1][4 * q + 0]),
+                                                                       __uint_as_float(r[i & 1][4 * q + 1])),
+                                                     make_float2(__uint_as_float(nv.x), __uint_as_float(nv.y)));
+                        const float2 p1 = __ffma2_rn(neg2, make_float2(__uint_as_float(r[i & 1][4 * q + 2]),
+                                                                       __uint_as_float(r[i & 1][4 * q + 3])),
+                                                     make_float2(__uint_as_float(nv.z), __uint_as_float(nv.w)));
+                        d[4 * q + 0] = p0.x;
+                        d[4 * q + 1] = p0.y;
+                        d[4 * q + 2] = p1.x;
+                        d[4 * q + 3] = p1.y;
                     }
                     // minimum of the chunk as a balanced tree; almost every chunk fails
                     // the comparison with the row's last kept key
