@@ -35,6 +35,20 @@
 // and the true nearest j* both lie within sqrt(|t|^2 + m + E(Nmax)) of t, so
 // |n_j| <= |t| + sqrt(|t|^2 + m + E(Nmax)) for both, and E is taken with the
 // smaller of that and Nmax.
+//
+// Key threshold (FBCORR_NN_PRESCREEN, default 16): the same screening kernel
+// first runs over the first 1/16 of the neighbour tiles (at least two); U, the
+// smallest key it finds for a target, is a screened key of some neighbour, and
+// the full screening computes that neighbour's key bit for bit the same, so
+// m <= U.  The window m + 2E(+ rounding) grows with m (every step of its FP32
+// formula is monotone), so it lies below T = the window formula at U, moved up
+// by one ulp.  The full screening keeps, per part, only keys below T: a part
+// with fewer than FBC_NN_KEEP of them stores the empty key (complete, its other
+// neighbours are at or above T, outside the window), the smallest key m is
+// unchanged (it is at most U < T), and every neighbour inside the window is
+// still kept or its part listed.  With T known from the first tile on, a chunk
+// rarely beats a row's last key, and the insertions that dominated the
+// epilogue's work almost vanish.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -191,6 +205,46 @@ __device__ __forceinline__ float fbc_nn_bound(const NnFinalizeArgs& A, float tn,
     return 1.25f * (A.c_dot * tn * nb + A.c_nrm * nb * nb + A.c_key * 2.f * tn * nb);
 }
 
+// The certificate window of a target whose smallest screened key is m: m + 2E,
+// E with the norm bound lowered by m (file header), widened by the rounding of
+// the exact distances.  Every operation is monotone in m.
+__device__ __forceinline__ float fbc_nn_window(const NnFinalizeArgs& A, float t2, float tn, float nmax, float m) {
+    const float e_max = fbc_nn_bound(A, tn, nmax);
+    const float nb = fminf(nmax, (tn + sqrtf(fmaxf(t2 + m + e_max, 0.f))) * 1.0001f);
+    const float e = fbc_nn_bound(A, tn, nb);
+    // the exact distances carry a relative FP32 rounding; the best is at most t2 + m + e
+    return m + 2.f * e + A.c_rr * 2.f * fmaxf(t2 + m + e, 0.f);
+}
+
+// The key threshold of every target row (file header): U = the smallest first
+// key of the sample screening's parts, T = the window at U plus one ulp; padding
+// rows and targets with no sampled key get +inf.  One warp per row (the same
+// |t|^2 loop as fbc_nn_finalize, so the same bits), lanes over the parts.
+__global__ void __launch_bounds__(128) fbc_nn_threshold(const NnFinalizeArgs A, float* thr) {
+    const long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= A.rows_total) return;   // warp-uniform
+    float T = __int_as_float(0x7f800000);
+    if (i < A.nt) {
+        const int nparts = A.cands / FBC_NN_KEEP;
+        float u = __int_as_float(0x7f800000);
+        for (int pq = lane; pq < nparts; pq += 32) {
+            const unsigned long long k0 = __ldg(A.part + ((long long)pq * A.rows_total + i) * FBC_NN_KEEP);
+            if (k0 != ~0ull) u = fminf(u, fbc_nn_key_dist(k0));
+        }
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) u = fminf(u, __shfl_xor_sync(0xffffffffu, u, o));
+        if (u < __int_as_float(0x7f800000)) {
+            const float* ti = A.t + i * A.dim;
+            float t2 = 0.f;
+            for (int k = 0; k < A.dim; ++k) t2 = fmaf(__ldg(ti + k), __ldg(ti + k), t2);
+            const float nmax = sqrtf(__uint_as_float(A.stats->nmax2_bits));
+            T = nextafterf(fbc_nn_window(A, t2, sqrtf(t2), nmax, u), __int_as_float(0x7f800000));
+        }
+    }
+    if (lane == 0) thr[i] = T;
+}
+
 // One warp per target; lane l takes the parts l, l + 32, ...
 __global__ void __launch_bounds__(128) fbc_nn_finalize(const NnFinalizeArgs A) {
     const long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -209,12 +263,7 @@ __global__ void __launch_bounds__(128) fbc_nn_finalize(const NnFinalizeArgs A) {
     }
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    // the norm bound of the two neighbours the argument needs (file header)
-    const float e_max = fbc_nn_bound(A, tn, nmax);
-    const float nb = fminf(nmax, (tn + sqrtf(fmaxf(t2 + m + e_max, 0.f))) * 1.0001f);
-    const float e = fbc_nn_bound(A, tn, nb);
-    // the exact distances carry a relative FP32 rounding; the best is at most t2 + m + e
-    const float win = m + 2.f * e + A.c_rr * 2.f * fmaxf(t2 + m + e, 0.f);
+    const float win = fbc_nn_window(A, t2, tn, nmax, m);
     unsigned long long best = ~0ull;   // (exact distance bits, index): distances are >= 0
     int n_over = 0;
     for (int pq0 = 0; pq0 < nparts; pq0 += 32) {
@@ -454,8 +503,11 @@ struct fbcorr_nn_plan {
     int nc = 0, split = 1;
     FbcNnParams kp{};
     int grid = 0;
+    FbcNnParams kpre{};   // the sample screening (key thresholds); kpre.n_tiles == 0: none
+    int pre_grid = 0;
     size_t smem = 0, ws = 0;
     size_t off_thi = 0, off_tlo = 0, off_nhi = 0, off_nlo = 0, off_n2 = 0, off_part = 0;
+    size_t off_pre_part = 0, off_thr = 0;
     size_t off_stats = 0, off_flag = 0, off_best = 0, off_entries = 0, off_elist = 0, off_full = 0;
     float c_dot = 0.f, c_nrm = 0.f, c_key = 0.f, c_rr = 0.f;   // screening error bound (nn.cu header)
     int scan_grid = 1;
@@ -526,6 +578,21 @@ fbcorr_status_t fbcorr_nn_plan_create(fbcorr_nn_plan_t* out, int64_t n_targets, 
     k.chunk_tiles = (int)chunk;
     k.chunks = (int)((k.n_tiles + chunk - 1) / chunk);
     p->grid = (int)std::min<long long>((long long)k.chunks * k.t_tiles, dev.sm_count);
+    // the sample screening for the key thresholds (file header): the first
+    // 1/FBCORR_NN_PRESCREEN of the neighbour tiles (default 16; 0: none), when
+    // that is at least two tiles
+    p->kpre = k;
+    p->kpre.n_tiles = 0;
+    const int pre_div = atoi(env_str("FBCORR_NN_PRESCREEN", "16").c_str());
+    if (pre_div > 0 && k.n_tiles / pre_div >= 2) {
+        FbcNnParams& q = p->kpre;
+        q.n_tiles = k.n_tiles / pre_div;
+        long long qc = ((long long)q.n_tiles * k.t_tiles + want - 1) / want;
+        qc = std::max(1LL, std::min(64LL, qc));
+        q.chunk_tiles = (int)qc;
+        q.chunks = (int)((q.n_tiles + qc - 1) / qc);
+        p->pre_grid = (int)std::min<long long>((long long)q.chunks * k.t_tiles, dev.sm_count);
+    }
     const long long rows_total = (long long)k.t_tiles * FBC_NN_TILE_T;
     size_t off = 0;
     p->off_thi = off; off = align_up(off + (size_t)k.t_tiles * k.a_bytes, 256);
@@ -534,6 +601,9 @@ fbcorr_status_t fbcorr_nn_plan_create(fbcorr_nn_plan_t* out, int64_t n_targets, 
     p->off_nlo = off; if (p->split) off = align_up(off + (size_t)k.n_tiles * k.b_bytes, 256);
     p->off_n2 = off; off = align_up(off + (size_t)k.n_tiles * FBC_NN_TILE_N * 4, 256);
     p->off_part = off; off = align_up(off + (size_t)k.chunks * (kEW / 4) * rows_total * FBC_NN_KEEP * 8, 256);
+    p->off_pre_part = off;
+    off = align_up(off + (size_t)p->kpre.chunks * (kEW / 4) * rows_total * FBC_NN_KEEP * 8 * (p->kpre.n_tiles > 0), 256);
+    p->off_thr = off; off = align_up(off + (size_t)rows_total * 4, 256);
     p->off_stats = off; off = align_up(off + sizeof(NnStats), 256);
     p->off_flag = off; off = align_up(off + (size_t)n_targets * 4, 256);
     p->off_best = off; off = align_up(off + (size_t)n_targets * 8, 256);
@@ -648,8 +718,6 @@ fbcorr_status_t fbcorr_nn_search(fbcorr_nn_plan_t p, const float* targets, const
         fbc_nn_norms<<<(unsigned)((n_rows + kNormRows - 1) / kNormRows), kNormRows,
                        (size_t)kNormRows * (p->dim + 1) * 4, s>>>(neighbors, p->nn, (int)p->dim, n_rows, n2, stats);
     FBC_CUDA(cudaGetLastError());
-    void* args[] = {&kp};
-    FBC_TRY(launch(p->k, dim3(p->grid), args, s));
     NnFinalizeArgs fa;
     fa.part = reinterpret_cast<const unsigned long long*>(base + p->off_part);
     fa.cands = kp.chunks * (kEW / 4) * FBC_NN_KEEP;
@@ -670,6 +738,30 @@ fbcorr_status_t fbcorr_nn_search(fbcorr_nn_plan_t p, const float* targets, const
     fa.best_key = reinterpret_cast<unsigned long long*>(base + p->off_best);
     fa.idx_out = reinterpret_cast<long long*>(idx_out);
     fa.dist_out = dist_out;
+    kp.thr = nullptr;
+    if (p->kpre.n_tiles > 0) {
+        // the sample screening, then the per-row key thresholds of the full one
+        FbcNnParams kq = p->kpre;
+        kq.thi = kp.thi;
+        kq.tlo = kp.tlo;
+        kq.nhi = kp.nhi;
+        kq.nlo = kp.nlo;
+        kq.n2 = kp.n2;
+        kq.err = kp.err;
+        kq.thr = nullptr;
+        kq.part = reinterpret_cast<unsigned long long*>(base + p->off_pre_part);
+        void* qargs[] = {&kq};
+        FBC_TRY(launch(p->k, dim3(p->pre_grid), qargs, s));
+        NnFinalizeArgs qa = fa;
+        qa.part = kq.part;
+        qa.cands = kq.chunks * (kEW / 4) * FBC_NN_KEEP;
+        float* thr = reinterpret_cast<float*>(base + p->off_thr);
+        fbc_nn_threshold<<<(unsigned)((t_rows + 3) / 4), 128, 0, s>>>(qa, thr);
+        FBC_CUDA(cudaGetLastError());
+        kp.thr = thr;
+    }
+    void* args[] = {&kp};
+    FBC_TRY(launch(p->k, dim3(p->grid), args, s));
     fbc_nn_finalize<<<(unsigned)((p->nt + 3) / 4), 128, 0, s>>>(fa);
     // the exact re-scans: each kernel returns at once when nothing is listed
     NnPartScanArgs pa;

@@ -15,6 +15,7 @@ struct FbcNnParams {
     const unsigned char* nlo;     //   and lo
     const float* n2;              // |n_j|^2 (FP32), +inf for the padding neighbours
     unsigned long long* part;     // [chunks][parts][t_tiles*128][FBC_NN_KEEP] smallest keys per target
+    const float* thr;             // per target row: keys at or above it are not kept (null: none)
     int* err;                     // host-mapped error word
     unsigned long long wait_ns;   // bound of every mbarrier wait
     int t_tiles, n_tiles;         // 128-target and 256-neighbour tiles

@@ -10,7 +10,8 @@
 // (tcgen05.mma, BF16 in, FP32 accumulate in TMEM; split BF16 by default, three
 // products per K step like the correlation kernel), and the epilogue keeps, per
 // target, the FBC_NN_KEEP smallest keys (d' as order-preserving bits, neighbour index)
-// over the tiles of a work item.  A work item is one target tile against one
+// over the tiles of a work item (only keys below the row's threshold, when the
+// plan screens a sample of the neighbours first).  A work item is one target tile against one
 // chunk of neighbour tiles; items run chunk-major, so the target tiles that share
 // a chunk run at the same time and read its neighbours from HBM once.  The host
 // merges the per-item candidates and re-ranks the best few by their exact FP32
@@ -239,11 +240,16 @@ __device__ __forceinline__ void fbc_nn_body(const FbcNnParams& P) {
         bool ok = true;
         for (int k = blockIdx.x; k < items && ok; k += gridDim.x) {
             const int c = k / P.t_tiles, t = k - c * P.t_tiles;
+            // keys at or above the row's threshold (from a screening of a sample of
+            // the neighbours) cannot enter the certificate window: none is kept,
+            // so the insertions are rare from the first tile on
+            const int row = t * FBC_NN_TILE_T + lq * 32 + lane;
+            const float thr0 = P.thr ? P.thr[row] : __int_as_float(0x7f800000);
             float bd[FBC_NN_KEEP];
             unsigned bi[FBC_NN_KEEP];
 #pragma unroll
             for (int k = 0; k < FBC_NN_KEEP; ++k) {
-                bd[k] = __int_as_float(0x7f800000);
+                bd[k] = thr0;
                 bi[k] = 0xffffffffu;
             }
             const int j1 = min(P.n_tiles, (c + 1) * P.chunk_tiles);
@@ -304,7 +310,6 @@ __device__ __forceinline__ void fbc_nn_body(const FbcNnParams& P) {
                 ++acc_it;
             }
             if (!ok) break;
-            const int row = t * FBC_NN_TILE_T + lq * 32 + lane;
             fbc_u64* dst = P.part + (((long long)c * (EW / 4) + part) * rows_total + row) * FBC_NN_KEEP;
 #pragma unroll
             for (int k = 0; k < FBC_NN_KEEP; ++k) dst[k] = bi[k] == 0xffffffffu ? ~0ull : fbc_nn_key(bd[k], bi[k]);

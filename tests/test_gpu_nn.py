@@ -109,7 +109,7 @@ def test_plain_bf16_screening_is_reranked_exactly():
     assert np.allclose(dist, ref_d, rtol=1e-5, atol=1e-7)
 
 
-def _planted(spread, seed=3400):
+def _planted(spread, seed=3400, nn=5120):
     """Target 0 is the all-ones vector of 64 coordinates.  Twelve neighbours lie
     around it: the true nearest n* = 1 + a (every coordinate) and eleven at
     1 - b_k with b_k slightly larger than a.  Plain BF16 rounds every one of them
@@ -121,9 +121,11 @@ def _planted(spread, seed=3400):
     spread=True puts the twelve in twelve different neighbour tiles (one per
     screening part: the window holds them all and is certified without the
     fallback); spread=False puts them in the first 32 columns of one tile (one
-    part keeps only two of them, so the target is searched exhaustively)."""
+    part keeps only two of them, so the target is searched exhaustively).
+    nn=16384 (64 neighbour tiles) makes the plan screen the first four tiles
+    first for the key thresholds: spread, that sample holds four of the twelve."""
     rng = np.random.default_rng(seed)
-    dim, nn = 64, 5120
+    dim = 64
     n = (1.0 + 3.0 * rng.standard_normal((nn, dim))).astype(np.float32)
     t = np.ones((1, dim), np.float32)
     a = 1e-3
@@ -134,15 +136,17 @@ def _planted(spread, seed=3400):
     return t, n, star
 
 
+@pytest.mark.parametrize("nn", [5120, 16384], ids=["no_threshold", "sampled_threshold"])
 @pytest.mark.parametrize("spread", [True, False], ids=["window_certified", "exhaustive_fallback"])
 @pytest.mark.parametrize("dtype", ["bf16", "bf16x3"])
-def test_nearest_beyond_the_first_four_screened(spread, dtype):
+def test_nearest_beyond_the_first_four_screened(spread, dtype, nn):
     """Twelve neighbours within the screening error of the true nearest, which
     screens last of them (plain BF16): the index must be the oracle's.  Either
     every candidate of the certified window is re-ranked exactly, or the target
-    whose window a part may have truncated is searched exhaustively."""
+    whose window a part may have truncated is searched exhaustively -- also when
+    the key threshold comes from a sample that holds some of the twelve."""
     torch = torch_cuda()
-    t, n, star = _planted(spread)
+    t, n, star = _planted(spread, nn=nn)
     ref_idx, ref_d, ref_d2 = oracle.nn(t, n)
     assert ref_idx[0] == star
     if dtype == "bf16":
@@ -202,3 +206,26 @@ def test_plan_refusals():
         NNPlan(10, 10, 65)              # more than 64 dimensions
     with pytest.raises(ValueError):
         NNPlan(10, 10, 8, "f32")        # screening runs on the tensor cores
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "bf16x3"])
+def test_sampled_key_threshold_changes_no_answer(dtype):
+    """The key threshold from the sample screening (FBCORR_NN_PRESCREEN, on by
+    default from 32 neighbour tiles) only drops keys that cannot enter a window:
+    indices and distances are bit-identical with and without it."""
+    import os
+    torch = torch_cuda()
+    t, n = inputs.nn_patches(n_neighbors=65536)
+    t = t[:1024]
+    with_thr = _run(torch, t, n, dtype, fallbacks=True)
+    old = os.environ.get("FBCORR_NN_PRESCREEN")
+    os.environ["FBCORR_NN_PRESCREEN"] = "0"
+    try:
+        without = _run(torch, t, n, dtype, fallbacks=True)
+    finally:
+        if old is None:
+            os.environ.pop("FBCORR_NN_PRESCREEN")
+        else:
+            os.environ["FBCORR_NN_PRESCREEN"] = old
+    assert np.array_equal(with_thr[0], without[0])
+    assert np.array_equal(with_thr[1], without[1])
