@@ -261,7 +261,11 @@ fbcorr_status_t fbcorr_forward_batched(fbcorr_batch_plan_t plan, const float* co
  * nearest neighbour; every candidate in it is re-ranked by its exact FP32
  * distance.  Where a part may hold more candidates in the window than it kept,
  * the target's exact FP32 distance to every neighbour of that part is taken too
- * (to every neighbour when more than 8 of its parts are incomplete).  So the
+ * (to every neighbour when more than 8 of its parts are incomplete).  With 32
+ * or more neighbour tiles of 256, the first 1/16 of them are screened first
+ * (FBCORR_NN_PRESCREEN=k: 1/k, 0: none) and the window at a target's best key
+ * there bounds the window of the full screening from above, so keys at or
+ * above it are not kept; this changes no result.  So the
  * result is always the argmin of the exact FP32 distance over all neighbours
  * (ties: the lowest index): the exact nearest neighbour up to FP32 rounding of
  * the distances.  dim <= 64, n_targets and n_neighbors < 2^31.  The plan
