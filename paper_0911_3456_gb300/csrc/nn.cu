@@ -94,10 +94,21 @@ __global__ void fbc_nn_split(const float* __restrict__ src, long long rows, int 
     float sq = 0.f;
     if (active) {
         __nv_bfloat16 h[8], l[8];
+        // the row's 8 values: two 16-byte loads when rows are whole 32-byte chunks
+        float vv[8];
+        const bool inside = row < rows && c * 8 < dim;
+        if (inside && (dim & 7) == 0 && (reinterpret_cast<unsigned long long>(src) & 15) == 0) {
+            const float4* s4 = reinterpret_cast<const float4*>(src + row * dim + c * 8);
+            const float4 a = __ldg(s4), b = __ldg(s4 + 1);
+            vv[0] = a.x; vv[1] = a.y; vv[2] = a.z; vv[3] = a.w;
+            vv[4] = b.x; vv[5] = b.y; vv[6] = b.z; vv[7] = b.w;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) vv[k] = (inside && c * 8 + k < dim) ? __ldg(src + row * dim + c * 8 + k) : 0.f;
+        }
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-            const int d = c * 8 + k;
-            const float v = (row < rows && d < dim) ? __ldg(src + row * dim + d) : 0.f;
+            const float v = vv[k];
             sq = fmaf(v, v, sq);
             h[k] = __float2bfloat16_rn(v);
             l[k] = __float2bfloat16_rn(v - __bfloat162float(h[k]));
@@ -332,7 +343,11 @@ struct NnPartScanArgs {
     const float* n;
     long long nn;
     int dim;
-    int chunk_tiles;            // neighbour tiles per chunk
+    int pre_chunks;             // chunks 0 .. pre_chunks - 1: the sample screening's,
+    int pre_chunk_tiles;        //   pre_chunk_tiles tiles each from tile 0, up to sample_tiles
+    int sample_tiles;
+    int chunk_tiles;            // then chunk_tiles tiles each from sample_tiles, up to n_tiles
+    int n_tiles;
     int parts;                  // parts per chunk (epilogue warps / 4)
     unsigned long long* best_key;
 };
@@ -344,8 +359,8 @@ __global__ void __launch_bounds__(kScanRows) fbc_nn_part_scan(const NnPartScanAr
     float* tv = fbc_nn_prows + kScanRows * (A.dim + 1);
     const int tid = threadIdx.x;
     const int cols = (256 / 32) / A.parts;                  // 32-column chunks per tile in one part
-    const int per_part = A.chunk_tiles * cols * 32;
-    const int steps = (per_part + kScanRows - 1) / kScanRows;
+    const int most = max(A.pre_chunks > 0 ? A.pre_chunk_tiles : 0, A.chunk_tiles) * cols * 32;
+    const int steps = (most + kScanRows - 1) / kScanRows;   // of the largest part
     const long long units = (long long)cnt * steps;
     const bool vec = (A.dim & 3) == 0 && (reinterpret_cast<unsigned long long>(A.n) & 15) == 0;
     const float inv_dim = 1.f / (float)A.dim;
@@ -355,9 +370,20 @@ __global__ void __launch_bounds__(kScanRows) fbc_nn_part_scan(const NnPartScanAr
         const int u0 = (int)(w - (long long)e * steps) * kScanRows;
         const int2 en = A.entries[A.entry_list[e]];
         const int c = en.y / A.parts, p = en.y - c * A.parts;
+        // the tiles of chunk c
+        int t0, tn;
+        if (c < A.pre_chunks) {
+            t0 = c * A.pre_chunk_tiles;
+            tn = min(A.sample_tiles, t0 + A.pre_chunk_tiles) - t0;
+        } else {
+            t0 = A.sample_tiles + (c - A.pre_chunks) * A.chunk_tiles;
+            tn = min(A.n_tiles, t0 + A.chunk_tiles) - t0;
+        }
+        const int per_part = tn * cols * 32;
+        if (u0 >= per_part) continue;   // block-uniform: a step past this part's end
         // neighbour index of the part's u-th row: runs of 32 consecutive rows
         auto row_of = [&](int u) -> long long {
-            const int jt = c * A.chunk_tiles + u / (cols * 32);
+            const int jt = t0 + u / (cols * 32);
             const int r = u % (cols * 32);
             return (long long)jt * 256 + (p + (r >> 5) * A.parts) * 32 + (r & 31);
         };
@@ -507,7 +533,7 @@ struct fbcorr_nn_plan {
     int pre_grid = 0;
     size_t smem = 0, ws = 0;
     size_t off_thi = 0, off_tlo = 0, off_nhi = 0, off_nlo = 0, off_n2 = 0, off_part = 0;
-    size_t off_pre_part = 0, off_thr = 0;
+    size_t off_thr = 0;
     size_t off_stats = 0, off_flag = 0, off_best = 0, off_entries = 0, off_elist = 0, off_full = 0;
     float c_dot = 0.f, c_nrm = 0.f, c_key = 0.f, c_rr = 0.f;   // screening error bound (nn.cu header)
     int scan_grid = 1;
@@ -573,36 +599,42 @@ fbcorr_status_t fbcorr_nn_plan_create(fbcorr_nn_plan_t* out, int64_t n_targets, 
     // work items: one target tile against a chunk of neighbour tiles, about four
     // waves of items over the SMs, at most 64 tiles per chunk
     const long long want = 4LL * std::max(1, dev.sm_count);
-    long long chunk = ((long long)k.n_tiles * k.t_tiles + want - 1) / want;
-    chunk = std::max(1LL, std::min(64LL, chunk));
-    k.chunk_tiles = (int)chunk;
-    k.chunks = (int)((k.n_tiles + chunk - 1) / chunk);
-    p->grid = (int)std::min<long long>((long long)k.chunks * k.t_tiles, dev.sm_count);
+    auto chunking = [&](FbcNnParams& q, int first, int end) {
+        long long c = ((long long)(end - first) * k.t_tiles + want - 1) / want;
+        c = std::max(1LL, std::min(64LL, c));
+        q.tile0 = first;
+        q.n_tiles = end;
+        q.chunk_tiles = (int)c;
+        q.chunks = (int)((end - first + c - 1) / c);
+    };
     // the sample screening for the key thresholds (file header): the first
     // 1/FBCORR_NN_PRESCREEN of the neighbour tiles (default 16; 0: none), when
-    // that is at least two tiles
+    // that is at least two tiles; the full screening then covers the other tiles,
+    // and the sample's parts (kept without a threshold) join its parts
+    const int n_tiles_all = k.n_tiles;
+    const int pre_div = atoi(env_str("FBCORR_NN_PRESCREEN", "16").c_str());
+    const int sample = (pre_div > 0 && n_tiles_all / pre_div >= 2) ? n_tiles_all / pre_div : 0;
     p->kpre = k;
     p->kpre.n_tiles = 0;
-    const int pre_div = atoi(env_str("FBCORR_NN_PRESCREEN", "16").c_str());
-    if (pre_div > 0 && k.n_tiles / pre_div >= 2) {
-        FbcNnParams& q = p->kpre;
-        q.n_tiles = k.n_tiles / pre_div;
-        long long qc = ((long long)q.n_tiles * k.t_tiles + want - 1) / want;
-        qc = std::max(1LL, std::min(64LL, qc));
-        q.chunk_tiles = (int)qc;
-        q.chunks = (int)((q.n_tiles + qc - 1) / qc);
-        p->pre_grid = (int)std::min<long long>((long long)q.chunks * k.t_tiles, dev.sm_count);
+    p->kpre.chunks = 0;
+    if (sample > 0) {
+        chunking(p->kpre, 0, sample);
+        p->kpre.chunk_base = 0;
+        p->pre_grid = (int)std::min<long long>((long long)p->kpre.chunks * k.t_tiles, dev.sm_count);
     }
+    chunking(k, sample, n_tiles_all);
+    k.chunk_base = p->kpre.chunks;
+    p->grid = (int)std::min<long long>((long long)k.chunks * k.t_tiles, dev.sm_count);
     const long long rows_total = (long long)k.t_tiles * FBC_NN_TILE_T;
     size_t off = 0;
     p->off_thi = off; off = align_up(off + (size_t)k.t_tiles * k.a_bytes, 256);
     p->off_tlo = off; if (p->split) off = align_up(off + (size_t)k.t_tiles * k.a_bytes, 256);
-    p->off_nhi = off; off = align_up(off + (size_t)k.n_tiles * k.b_bytes, 256);
-    p->off_nlo = off; if (p->split) off = align_up(off + (size_t)k.n_tiles * k.b_bytes, 256);
-    p->off_n2 = off; off = align_up(off + (size_t)k.n_tiles * FBC_NN_TILE_N * 4, 256);
-    p->off_part = off; off = align_up(off + (size_t)k.chunks * (kEW / 4) * rows_total * FBC_NN_KEEP * 8, 256);
-    p->off_pre_part = off;
-    off = align_up(off + (size_t)p->kpre.chunks * (kEW / 4) * rows_total * FBC_NN_KEEP * 8 * (p->kpre.n_tiles > 0), 256);
+    p->off_nhi = off; off = align_up(off + (size_t)n_tiles_all * k.b_bytes, 256);
+    p->off_nlo = off; if (p->split) off = align_up(off + (size_t)n_tiles_all * k.b_bytes, 256);
+    p->off_n2 = off; off = align_up(off + (size_t)n_tiles_all * FBC_NN_TILE_N * 4, 256);
+    // parts: the sample's chunks, then the full screening's
+    const long long all_chunks = (long long)p->kpre.chunks + k.chunks;
+    p->off_part = off; off = align_up(off + (size_t)all_chunks * (kEW / 4) * rows_total * FBC_NN_KEEP * 8, 256);
     p->off_thr = off; off = align_up(off + (size_t)rows_total * 4, 256);
     p->off_stats = off; off = align_up(off + sizeof(NnStats), 256);
     p->off_flag = off; off = align_up(off + (size_t)n_targets * 4, 256);
@@ -720,7 +752,7 @@ fbcorr_status_t fbcorr_nn_search(fbcorr_nn_plan_t p, const float* targets, const
     FBC_CUDA(cudaGetLastError());
     NnFinalizeArgs fa;
     fa.part = reinterpret_cast<const unsigned long long*>(base + p->off_part);
-    fa.cands = kp.chunks * (kEW / 4) * FBC_NN_KEEP;
+    fa.cands = (p->kpre.chunks + kp.chunks) * (kEW / 4) * FBC_NN_KEEP;   // the sample's parts, then the rest
     fa.rows_total = t_rows;
     fa.t = targets;
     fa.n = neighbors;
@@ -749,7 +781,7 @@ fbcorr_status_t fbcorr_nn_search(fbcorr_nn_plan_t p, const float* targets, const
         kq.n2 = kp.n2;
         kq.err = kp.err;
         kq.thr = nullptr;
-        kq.part = reinterpret_cast<unsigned long long*>(base + p->off_pre_part);
+        kq.part = kp.part;   // chunks 0 .. kpre.chunks - 1 of the part array
         void* qargs[] = {&kq};
         FBC_TRY(launch(p->k, dim3(p->pre_grid), qargs, s));
         NnFinalizeArgs qa = fa;
@@ -772,7 +804,11 @@ fbcorr_status_t fbcorr_nn_search(fbcorr_nn_plan_t p, const float* targets, const
     pa.n = neighbors;
     pa.nn = p->nn;
     pa.dim = (int)p->dim;
+    pa.pre_chunks = p->kpre.chunks;
+    pa.pre_chunk_tiles = p->kpre.chunk_tiles;
+    pa.sample_tiles = kp.tile0;
     pa.chunk_tiles = kp.chunk_tiles;
+    pa.n_tiles = kp.n_tiles;
     pa.parts = kEW / 4;
     pa.best_key = fa.best_key;
     const size_t scan_smem = (size_t)(kScanRows * (p->dim + 1) + p->dim) * 4;

@@ -18,8 +18,10 @@ struct FbcNnParams {
     const float* thr;             // per target row: keys at or above it are not kept (null: none)
     int* err;                     // host-mapped error word
     unsigned long long wait_ns;   // bound of every mbarrier wait
-    int t_tiles, n_tiles;         // 128-target and 256-neighbour tiles
+    int t_tiles, n_tiles;         // 128-target tiles; neighbour tiles [tile0, n_tiles) screened
     int chunk_tiles, chunks;      // neighbour tiles per work item; items = chunks * t_tiles
+    int tile0;                    // first neighbour tile of chunk 0
+    int chunk_base;               // chunk c writes its parts as chunk chunk_base + c of `part`
     int nb;                       // B stages (neighbour tiles in flight)
     int na;                       // A slots (target tiles): 1 or 2
     unsigned int a_bytes, b_bytes;          // bytes of one half (hi or lo) of an A tile / B tile

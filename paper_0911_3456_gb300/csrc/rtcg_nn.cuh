@@ -145,8 +145,8 @@ __device__ __forceinline__ void fbc_nn_body(const FbcNnParams& P) {
                 if (SPLIT) fbc_bulk_g2s(adst + P.a_bytes, P.tlo + (long long)t * P.a_bytes, P.a_bytes, afull);
                 ++a_it;
                 if (++as == P.na) { as = 0; aph ^= 1; }
-                const int j1 = min(P.n_tiles, (c + 1) * P.chunk_tiles);
-                for (int jt = c * P.chunk_tiles; jt < j1 && ok; ++jt) {
+                const int j1 = min(P.n_tiles, P.tile0 + (c + 1) * P.chunk_tiles);
+                for (int jt = P.tile0 + c * P.chunk_tiles; jt < j1 && ok; ++jt) {
                     if (!(ok = fbc_wait(b_empty0 + 8u * bs, bph ^ 1, P, abort_flag, 4))) break;
                     const fbc_u32 bfull = b_full0 + 8u * bs;
                     fbc_mbar_expect_tx(bfull, b_stage);
@@ -191,8 +191,8 @@ __device__ __forceinline__ void fbc_nn_body(const FbcNnParams& P) {
                 const int c = k / P.t_tiles;
                 if (!(ok = fbc_wait(a_full0 + 8u * as, aph, P, abort_flag, 1))) break;
                 const fbc_u64 ad = adesc0 + (fbc_u64)((as * a_slot) >> 4);
-                const int j1 = min(P.n_tiles, (c + 1) * P.chunk_tiles);
-                for (int jt = c * P.chunk_tiles; jt < j1 && ok; ++jt) {
+                const int j1 = min(P.n_tiles, P.tile0 + (c + 1) * P.chunk_tiles);
+                for (int jt = P.tile0 + c * P.chunk_tiles; jt < j1 && ok; ++jt) {
                     const int acc = acc_it & 1;
                     if (!(ok = fbc_wait(acc_empty0 + 8u * acc, ((acc_it >> 1) & 1) ^ 1, P, abort_flag, 3))) break;
                     if (!(ok = fbc_wait(b_full0 + 8u * bs, bph, P, abort_flag, 2))) break;
@@ -252,8 +252,8 @@ __device__ __forceinline__ void fbc_nn_body(const FbcNnParams& P) {
                 bd[k] = thr0;
                 bi[k] = 0xffffffffu;
             }
-            const int j1 = min(P.n_tiles, (c + 1) * P.chunk_tiles);
-            for (int jt = c * P.chunk_tiles; jt < j1; ++jt) {
+            const int j1 = min(P.n_tiles, P.tile0 + (c + 1) * P.chunk_tiles);
+            for (int jt = P.tile0 + c * P.chunk_tiles; jt < j1; ++jt) {
                 const int acc = acc_it & 1;
                 const fbc_u32 par = (acc_it >> 1) & 1;
                 if (!(ok = fbc_wait(acc_full0 + 8u * acc, par, P, abort_flag, 3))) break;
@@ -310,7 +310,8 @@ __device__ __forceinline__ void fbc_nn_body(const FbcNnParams& P) {
                 ++acc_it;
             }
             if (!ok) break;
-            fbc_u64* dst = P.part + (((long long)c * (EW / 4) + part) * rows_total + row) * FBC_NN_KEEP;
+            fbc_u64* dst =
+                P.part + (((long long)(P.chunk_base + c) * (EW / 4) + part) * rows_total + row) * FBC_NN_KEEP;
 #pragma unroll
             for (int k = 0; k < FBC_NN_KEEP; ++k) dst[k] = bi[k] == 0xffffffffu ? ~0ull : fbc_nn_key(bd[k], bi[k]);
         }
