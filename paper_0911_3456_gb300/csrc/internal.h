@@ -105,6 +105,9 @@ struct DirectTile {
     // bits (the lanes of a quarter warp then read the same filter values).
     // ks = 1: one column per lane (wq = 1, sh = 0).
     int ks = 1, wq = 1, sh = 0;
+    // mb > 0: compiled with __launch_bounds__(threads, mb), so that mb CTAs fit in
+    // an SM's registers (one stages while the others compute); 0: no bound
+    int mb = 0;
     int chunk(int c) const { return ks > 1 ? c : ((cc > 0 && cc < c) ? cc : c); }
     int bh() const { return tr * wr; }
     int bn() const { return tf * wf; }

@@ -52,6 +52,7 @@ std::string direct_tile_spec(const DirectTile& t) {
     std::string out = b;
     if (t.ks > 1) out += ",ks=" + std::to_string(t.ks) + ",wq=" + std::to_string(t.wq);
     if (t.sh) out += ",sh=1";
+    if (t.mb) out += ",mb=" + std::to_string(t.mb);
     return out;
 }
 
@@ -66,8 +67,8 @@ static bool ks_tile_ok(const DirectTile& t) {
 
 bool parse_direct_spec(const std::string& s, DirectTile* t) {
     // "direct:tr=R,tf=F,wr=WR,wf=WF" then optionally ",cc=CC", ",pk=P", ",pf=F",
-    // ",ks=K,wq=Q" and ",sh=S", in that order; anything else left over rejects
-    // the spec
+    // ",ks=K,wq=Q", ",sh=S" and ",mb=M", in that order; anything else left over
+    // rejects the spec
     DirectTile d;
     d.cc = 0;
     d.pk = 0;
@@ -99,6 +100,11 @@ bool parse_direct_spec(const std::string& s, DirectTile* t) {
     u = -1;
     if (strncmp(rest, ",sh=", 4) == 0) {
         if (sscanf(rest, ",sh=%d%n", &d.sh, &u) != 1 || u < 0) return false;
+        rest += u;
+    }
+    u = -1;
+    if (strncmp(rest, ",mb=", 4) == 0) {
+        if (sscanf(rest, ",mb=%d%n", &d.mb, &u) != 1 || u < 0 || d.mb < 2 || d.mb > 4) return false;
         rest += u;
     }
     if (*rest != '\0') return false;
@@ -144,8 +150,9 @@ std::string direct_kernel_source(const DirectProblem& pr, const DirectTile& t,
     }
     o << "static_assert(FbcThis::SMEM_BYTES == " << direct_smem_bytes(t, pr.fh, pr.fw, pr.c)
       << ", \"host and device disagree on the shared-memory size\");\n";
-    o << "extern \"C\" __global__ void __launch_bounds__(" << t.threads() << ") " << kname
-      << "(FbcDirectArgs a) {\n"
+    o << "extern \"C\" __global__ void __launch_bounds__(" << t.threads();
+    if (t.mb) o << ", " << t.mb;
+    o << ") " << kname << "(FbcDirectArgs a) {\n"
       << "  extern __shared__ __align__(16) float fbc_smem[];\n"
       << "  FbcThis::run(a, fbc_smem, blockIdx.x, blockIdx.y, blockIdx.z);\n"
       << "}\n";
@@ -391,6 +398,7 @@ std::string kname_for(const char* base, const DirectProblem& pr, const DirectTil
     std::string name = b;
     if (t.pf) name += "_pf1";
     if (t.ks > 1) name += "_ks" + std::to_string(t.ks) + "q" + std::to_string(t.wq) + (t.sh ? "h" : "");
+    if (t.mb) name += "_mb" + std::to_string(t.mb);
     return pr.epi == 2 ? name + "_u" + snippet_tag(pr.snippet) : name;
 }
 
@@ -437,6 +445,25 @@ fbcorr_status_t tune_direct_problem(const DeviceInfo& dev, const DirectProblem& 
     std::vector<DirectTile> ranked = direct_ranked(pr, smem_cap, dev.sm_count, threads, max_block);
     // the batched kernel (fixed CTA size, two CTAs per SM) takes no prefetch variants
     std::vector<std::string> specs = direct_tuning_specs(ranked, topk, threads > 0 ? 0 : pr.c);
+    if (threads == 0 && env_str("FBCORR_TUNE_MB", "1") != "0") {
+        // occupancy variants: the packed-pair form of the first candidates bounded
+        // to 2 or 3 CTAs per SM (registers, where the shared memory allows it), so
+        // that one CTA stages while the others compute
+        const size_t n0 = specs.size();
+        int added = 0;
+        for (size_t i = 0; i < n0 && added < topk / 2; ++i) {
+            DirectTile t;
+            if (!parse_direct_spec(specs[i], &t) || t.pk != 1) continue;
+            const size_t sm = direct_smem_bytes(t, pr.fh, pr.fw, pr.c) + 1024;
+            for (int mb = 2; mb <= 3; ++mb)
+                if ((size_t)mb * sm <= 228 * 1024 && (size_t)mb * t.threads() <= 2048) {
+                    DirectTile u = t;
+                    u.mb = mb;
+                    specs.push_back(direct_tile_spec(u));
+                    ++added;
+                }
+        }
+    }
     if (specs.empty() && !include_default)
         return set_error(FBCORR_ERR_UNSUPPORTED, "no %s candidate fits", what);
     {

@@ -152,6 +152,11 @@ def test_explicit_tile_specs_compile(lib, spec):
     (b"direct:tr=16,tf=4,wr=1,wf=4,cc=0,pk=1,ks=8,wq=2,sh=1", True),   # share in the high lane bits
     (b"direct:tr=4,tf=8,wr=2,wf=1,cc=0,ks=8,wq=4,sh=2", False),
     (b"direct:tr=4,tf=8,wr=2,wf=1,cc=0,sh=1", False),              # sh only with a K split
+    (b"direct:tr=8,tf=8,wr=2,wf=2,cc=8,pk=1,mb=2", True),          # two CTAs per SM (launch bounds)
+    (b"direct:tr=8,tf=4,wr=3,wf=2,cc=0,pk=1,ks=8,wq=2,sh=1,mb=3", True),
+    (b"direct:tr=8,tf=8,wr=2,wf=2,cc=8,pk=1,mb=1", False),         # mb: 2, 3 or 4
+    (b"direct:tr=8,tf=8,wr=2,wf=2,cc=8,pk=1,mb=5", False),
+    (b"direct:tr=8,tf=8,wr=2,wf=2,cc=8,mb=2,pk=1", False),         # fields out of order
 ])
 def test_direct_spec_parsing_is_strict(lib, spec, ok):
     log = ctypes.create_string_buffer(1 << 16)

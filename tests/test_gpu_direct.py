@@ -247,3 +247,21 @@ def test_register_prefetch_is_bit_identical(shape, spec):
         assert np.array_equal(y0, y1)
         ref = oracle.fwd(wl.x, wl.w, epilogue=clamp)
         assert np.abs(y1 - ref).max() <= TOL_F32 * np.abs(oracle.fwd(wl.x, wl.w)).max()
+
+
+@pytest.mark.parametrize("shape,spec", [
+    ((40, 70, 32, 24, 5, 5), "direct:tr=8,tf=8,wr=2,wf=2,cc=8,pk=1"),
+    ((33, 50, 16, 20, 7, 3), "direct:tr=7,tf=4,wr=2,wf=4,cc=8,pk=1,pf=1"),
+    ((30, 45, 8, 16, 9, 9), "direct:tr=8,tf=4,wr=3,wf=2,cc=0,pk=1,ks=8,wq=2,sh=1"),
+])
+@pytest.mark.parametrize("mb", [2, 3])
+def test_occupancy_bound_is_bit_identical(shape, spec, mb):
+    """mb=M compiles the same tile with __launch_bounds__(threads, M): only the
+    register allocation changes, so the output equals the unbounded tile's bit for
+    bit."""
+    torch = torch_cuda()
+    wl = inputs.random_case(530, *shape)
+    y0, _ = _run(torch, wl.x, wl.w, spec=spec)
+    y1, p1 = _run(torch, wl.x, wl.w, spec=spec + f",mb={mb}")
+    assert p1.info()["fwd"]["kernel"].endswith(f"_mb{mb}")
+    assert np.array_equal(y0, y1)
