@@ -197,18 +197,37 @@ fbcorr_status_t prepare_backward(fbcorr_plan* p) {
         p->dw_kind = VarKind::Default;   // one thread per channel does not fit a CTA
     } else {
         char name[160];
-        // packed pairs need 120 registers (2 CTAs per SM instead of 3): measured
-        // slower on the differentiation workload (30.2 against 41.3 TFLOP/s), so off
-        // unless FBCORR_DW_PK=1
-        p->dw_pk = env_str("FBCORR_DW_PK", "0") == "1" ? 1 : 0;
-        snprintf(name, sizeof name, "fbc_dw_f%dx%d_c%d_n%d_g%d_q%d_m%d%s", (int)p->fh, (int)p->fw,
-                 (int)p->D, p->dw_tn, p->dw_ng, p->dw_qb, mask, p->dw_pk ? "_pk1" : "");
-        s = rtcg_kernel(dw_kernel_source((int)p->fh, (int)p->fw, (int)p->D, p->dw_tn, p->dw_ng,
-                                         p->dw_qb, mask, p->dw_pk, name),
-                        name, dw_smem_bytes((int)p->fw, (int)p->D, p->dw_tn, p->dw_ng, p->dw_qb),
-                        (int)p->D * p->dw_ng, &p->dw_kernel);
+        // FMA form, chosen with the tile at plan creation (FBCORR_DW_PK): 0 scalar;
+        // 1 packed pairs with register totals (about 120 registers); 2 (default)
+        // packed pairs with the chunk totals in shared memory
+        if (p->dw_pk == 2 &&
+            dw_smem_bytes((int)p->fw, (int)p->D, p->dw_tn, p->dw_ng, p->dw_qb, 2) > smem_limit(p->dev))
+            p->dw_pk = 0;   // the totals do not fit beside the buffers
+        // launch bounds: as many CTAs per SM (at most 3) as the shared memory
+        // holds, so that the register allocator keeps that residency
+        const size_t need = dw_smem_bytes((int)p->fw, (int)p->D, p->dw_tn, p->dw_ng, p->dw_qb, p->dw_pk);
+        const size_t per_sm = 228 * 1024;   // shared memory per SM (sm_100 family)
+        p->dw_mb = std::max(1, std::min(3, (int)(per_sm / (need + 1024))));
+        const int mb_env = atoi(env_str("FBCORR_DW_MB", "-1").c_str());
+        if (mb_env >= 0 && mb_env <= 4) p->dw_mb = mb_env;   // 0: no launch bound
+        auto build_dw = [&]() {
+            snprintf(name, sizeof name, "fbc_dw_f%dx%d_c%d_n%d_g%d_q%d_m%d%s_b%d", (int)p->fh, (int)p->fw,
+                     (int)p->D, p->dw_tn, p->dw_ng, p->dw_qb, mask,
+                     p->dw_pk == 1 ? "_pk1" : p->dw_pk == 2 ? "_pk2" : "", p->dw_mb);
+            return rtcg_kernel(dw_kernel_source((int)p->fh, (int)p->fw, (int)p->D, p->dw_tn, p->dw_ng,
+                                                p->dw_qb, mask, p->dw_pk, name, p->dw_mb),
+                               name, need, (int)p->D * p->dw_ng, &p->dw_kernel);
+        };
+        s = build_dw();
+        int regs = 0, local = 0;
+        if (s == FBCORR_OK && p->dw_mb > 0 && mb_env < 0 &&
+            kernel_resources(p->dw_kernel, &regs, &local) == FBCORR_OK && local > 0) {
+            p->dw_mb = 0;   // the bound made the allocator spill (wide filters): drop it
+            s = build_dw();
+        }
         if (s == FBCORR_OK) {
             p->dw_kind = VarKind::Direct;
+            if (kernel_resources(p->dw_kernel, &regs, &local) == FBCORR_OK) p->dw_regs = regs;
             int resident = 0;
             if (kernel_occupancy(p->dw_kernel, &resident) == FBCORR_OK && resident > 0)
                 replan_dw_chunks(p, resident);
@@ -237,12 +256,35 @@ fbcorr_status_t prepare_backward(fbcorr_plan* p) {
 }
 
 void plan_dw_chunks(fbcorr_plan* p) {
-    // CTA = NG filter groups x D channels (about 256 threads); enough row chunks
-    // for about 4 resident CTAs per SM over two waves; deterministic in the shape
-    p->dw_tn = 4;
+    // CTA = NG filter groups x D channels (about 256 threads with 4 filters per
+    // thread, 128 with 8); enough row chunks for about 4 resident CTAs per SM
+    // over two waves (re-planned from the built kernel's residency); deterministic
+    // in the shape
+    // FMA form (FBCORR_DW_PK, default 2): packed pairs with the chunk totals in
+    // shared memory.  Measured on the differentiation workload (256x256x16 input,
+    // 64 filters 7x7x16): scalar 0.149 ms, packed pairs with register totals (2
+    // CTAs per SM) 0.143, with shared totals 0.132 (4 filters per thread) and
+    // 0.130 (8 filters per thread, 128-thread CTAs, 3 per SM).
+    const std::string pk_env = env_str("FBCORR_DW_PK", "2");
+    p->dw_pk = pk_env == "1" ? 1 : pk_env == "0" ? 0 : 2;
+    // 8 filters per thread where the packed double-buffered path runs (16-byte
+    // rows of g and x, no clamp mask) at depths up to 64; 4 elsewhere
+    const bool async_path = p->epi.kind != FBCORR_EPI_CLAMP && p->D % 4 == 0 && p->N % 4 == 0;
+    p->dw_tn = (p->dw_pk == 2 && async_path && p->D <= 64) ? 8 : 4;
+    int tn_env = 0, ng_env = 0, qb_env = 0;   // FBCORR_DW_TILE="tn,ng,qb" (tile sweeps)
+    if (sscanf(env_str("FBCORR_DW_TILE", "").c_str(), "%d,%d,%d", &tn_env, &ng_env, &qb_env) == 3 &&
+        (tn_env == 4 || tn_env == 8) && ng_env >= 1 && ng_env * p->D <= 1024 && qb_env >= 8 && qb_env <= 256)
+        p->dw_tn = tn_env;
+    else
+        ng_env = qb_env = 0;
     const long ngroups_needed = (p->N + p->dw_tn - 1) / p->dw_tn;
-    p->dw_ng = (int)std::max(1L, std::min<long>(256 / std::max<int64_t>(1, p->D), ngroups_needed));
+    p->dw_ng = (int)std::max(1L, std::min<long>((p->dw_tn == 8 ? 128 : 256) / std::max<int64_t>(1, p->D),
+                                                ngroups_needed));
     p->dw_qb = 64;
+    if (ng_env) {
+        p->dw_ng = (int)std::min<long>(ng_env, ngroups_needed);
+        p->dw_qb = qb_env;
+    }
     p->dw_nblocks = (int)((p->N + (long)p->dw_tn * p->dw_ng - 1) / ((long)p->dw_tn * p->dw_ng));
     long want = (4L * std::max(1, p->dev.sm_count) + p->fh * p->dw_nblocks - 1) /
                 (p->fh * p->dw_nblocks);
@@ -789,7 +831,8 @@ fbcorr_status_t fbcorr_plan_info(fbcorr_plan_t p, char* buf, size_t cap) {
         o << ",\"dx\":{\"kind\":\"" << kind_name(p->dx_kind) << "\"";
         if (p->dx_kind == VarKind::Direct) o << ",\"spec\":\"" << direct_tile_spec(p->dx_tile) << "\"";
         o << "},\"dw\":{\"kind\":\"" << kind_name(p->dw_kind) << "\",\"threads\":" << p->D * p->dw_ng
-          << ",\"filters_per_cta\":" << p->dw_tn * p->dw_ng << ",\"packed_pairs\":" << p->dw_pk
+          << ",\"filters_per_cta\":" << p->dw_tn * p->dw_ng << ",\"packed_pairs\":" << p->dw_pk << ",\"min_blocks\":" << p->dw_mb
+          << ",\"registers\":" << p->dw_regs << ",\"tile\":[" << p->dw_tn << "," << p->dw_ng << "," << p->dw_qb << "]"
           << ",\"chunks\":" << p->dw_chunks
           << ",\"rows_per_chunk\":" << p->dw_rows_per_chunk << "}";
     }
@@ -891,7 +934,7 @@ fbcorr_status_t fbcorr_rtcg_check(const int64_t in_shape[3], const int64_t filt_
         direct_kernel_source(bp, tb, kname_for("fbc_direct", bp, tb)),
         dw_kernel_source((int)tmp.fh, (int)tmp.fw, (int)tmp.D, 4,
                          (int)std::max<int64_t>(1, std::min<int64_t>(256 / tmp.D, (tmp.N + 3) / 4)), 64,
-                         mask, 1, "fbc_dw_check")};
+                         mask, 2, "fbc_dw_check", 3)};
     for (const auto& src : srcs) {
         std::string lg;
         fbcorr_status_t s = rtcg_compile_only(src, &lg);

@@ -135,6 +135,9 @@ __global__ void __launch_bounds__(kRedElems * kRedSlices) fbc_dw_reduce(const fl
                                                                         float* __restrict__ dw, int S,
                                                                         long long E) {
     extern __shared__ float gsum[];   // [ceil(S / 8)][kRedElems]
+    // launched as the programmatic dependent of the partial-sum kernel: wait for
+    // that grid to complete and its partials to be visible before reading them
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const int el = threadIdx.x % kRedElems;
     const int slice = threadIdx.x / kRedElems;
     const long long e = (long long)blockIdx.x * kRedElems + el;
@@ -178,8 +181,19 @@ cudaError_t launch_default_dw(const float* x, const float* g, const float* m, fl
 cudaError_t launch_dw_reduce(const float* part, float* dw, int S, long long E, cudaStream_t s) {
     if (S < 1 || S > kMaxChunks) return cudaErrorInvalidValue;
     const size_t smem = (size_t)((S + 7) / 8) * kRedElems * sizeof(float);
-    fbc_dw_reduce<<<(unsigned)((E + kRedElems - 1) / kRedElems), kRedElems * kRedSlices, smem, s>>>(part, dw, S, E);
-    return cudaGetLastError();
+    // programmatic dependent launch: the reduction's launch and CTA set-up overlap
+    // the tail of the partial-sum kernel (which triggers it once its sums are done)
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)((E + kRedElems - 1) / kRedElems));
+    cfg.blockDim = dim3(kRedElems * kRedSlices);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, fbc_dw_reduce, part, dw, S, E);
 }
 
 }  // namespace fbc

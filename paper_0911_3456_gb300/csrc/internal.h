@@ -84,6 +84,8 @@ fbcorr_status_t graph_add_kernel(cudaGraph_t g, const cudaGraphNode_t* deps, siz
 fbcorr_status_t graph_set_kernel(cudaGraphExec_t e, cudaGraphNode_t n, const Kernel& k, dim3 grid,
                                  void** args);
 fbcorr_status_t kernel_occupancy(const Kernel& k, int* blocks_per_sm);
+// registers per thread and local (spill and stack) bytes per thread of a loaded kernel
+fbcorr_status_t kernel_resources(const Kernel& k, int* regs, int* local_bytes);
 const char* rtcg_header_source();     // contents of rtcg_direct.cuh
 const char* rtcg_tc_params_source();  // contents of tc_params.h
 const char* rtcg_ptx_source();        // contents of rtcg_ptx.cuh
@@ -165,10 +167,12 @@ fbcorr_status_t tune_direct_problem(const DeviceInfo& dev, const DirectProblem& 
 
 // dL/dw partial-sum kernel: TN filters x fw taps per thread, NG filter groups of
 // C threads per CTA, rows walked in blocks of QB columns staged in shared memory.
-size_t dw_smem_bytes(int fw, int c, int tn, int ng, int qb);
-// pk = 1: packed-pair FMAs in the double-buffered path (bit-identical).
+size_t dw_smem_bytes(int fw, int c, int tn, int ng, int qb, int pk);
+// pk = 1: packed-pair FMAs in the double-buffered path (bit-identical); pk = 2:
+// the same with each thread's chunk totals in shared memory (fewer registers).
+// min_blocks > 0: CTAs per SM asked of the register allocator (launch bounds).
 std::string dw_kernel_source(int fh, int fw, int c, int tn, int ng, int qb, int mask, int pk,
-                             const std::string& kname);
+                             const std::string& kname, int min_blocks = 0);
 
 // prebuilt (nvcc) kernels, launchers defined in default_kernels.cu
 struct DirectArgsRT {
@@ -250,7 +254,9 @@ struct fbcorr_plan {
     fbc::VarKind dw_kind = fbc::VarKind::Direct;
     fbc::Kernel dw_kernel;
     int dw_tn = 4, dw_ng = 1, dw_qb = 64, dw_nblocks = 1;
-    int dw_pk = 0;                 // packed-pair FMAs in the dL/dw kernel (FBCORR_DW_PK=1; off by default)
+    int dw_pk = 2;                 // dL/dw FMA form: 0 scalar, 1 packed pairs, 2 packed pairs + shared totals
+    int dw_mb = 0;                 // CTAs per SM in the dL/dw kernel's launch bounds (0: none)
+    int dw_regs = 0;               // registers per thread of the built dL/dw kernel
     int dw_chunks = 1, dw_rows_per_chunk = 1;
 
     size_t ws_fwd = 0, ws_bwd = 0;

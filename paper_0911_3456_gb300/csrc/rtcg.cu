@@ -43,6 +43,7 @@ struct DriverApi {
                                              const CUDA_KERNEL_NODE_PARAMS*) = nullptr;
     CUresult (*occupancy)(int*, CUfunction, int, size_t) = nullptr;
     CUresult (*launchKernelEx)(const CUlaunchConfig*, CUfunction, void**, void**) = nullptr;   // optional
+    CUresult (*funcGetAttribute)(int*, CUfunction_attribute, CUfunction) = nullptr;            // optional
 };
 
 std::mutex g_mu;
@@ -74,6 +75,7 @@ fbcorr_status_t driver_api(DriverApi** out) {
                   resolve("cuOccupancyMaxActiveBlocksPerMultiprocessor", &d.occupancy);
         if (!ok) return set_error(FBCORR_ERR_CUDA, "could not resolve CUDA driver entry points");
         if (!resolve("cuLaunchKernelEx", &d.launchKernelEx)) d.launchKernelEx = nullptr;
+        if (!resolve("cuFuncGetAttribute", &d.funcGetAttribute)) d.funcGetAttribute = nullptr;
         d.ok = true;
         g_drv = d;
     }
@@ -423,6 +425,17 @@ fbcorr_status_t graph_set_kernel(cudaGraphExec_t e, cudaGraphNode_t n, const Ker
     if (r != CUDA_SUCCESS)
         return set_error(FBCORR_ERR_CUDA, "cuGraphExecKernelNodeSetParams(%s): %s", k.name.c_str(),
                          cu_err(r));
+    return FBCORR_OK;
+}
+
+fbcorr_status_t kernel_resources(const Kernel& k, int* regs, int* local_bytes) {
+    DriverApi* drv = nullptr;
+    FBC_TRY(driver_api(&drv));
+    if (!drv->funcGetAttribute) return set_error(FBCORR_ERR_CUDA, "cuFuncGetAttribute unavailable");
+    CUresult r = drv->funcGetAttribute(regs, CU_FUNC_ATTRIBUTE_NUM_REGS, k.fn);
+    if (r == CUDA_SUCCESS) r = drv->funcGetAttribute(local_bytes, CU_FUNC_ATTRIBUTE_LOCAL_SIZE_BYTES, k.fn);
+    if (r != CUDA_SUCCESS)
+        return set_error(FBCORR_ERR_CUDA, "cuFuncGetAttribute(%s): %s", k.name.c_str(), cu_err(r));
     return FBCORR_OK;
 }
 

@@ -730,7 +730,12 @@ struct FbcDw {
     static constexpr int NBLK = TN * NG;
     static constexpr int GS = QB * NBLK;
     static constexpr int XS = (QB + FW - 1) * C;
-    static constexpr int SMEM_BYTES = 2 * (GS + XS) * 4;
+    // PK = 2 keeps each thread's chunk totals in shared memory ([TN/2][FW][NT]
+    // float2, thread-private slots, consecutive threads in consecutive words):
+    // the 2 x TN x FW accumulators of the packed form otherwise need about 120
+    // registers, which leaves 2 CTAs per SM instead of 3.
+    static constexpr int TSZ = (PK == 2) ? TN * FW * NT : 0;
+    static constexpr int SMEM_BYTES = (2 * (GS + XS) + TSZ) * 4;
 
     // Issue the copies of block (p, q0) into buffer (gs, xs): g[p][q0..q0+QB)[n0..n0+NBLK)
     // and x[p+i][q0..q0+QB+FW-1)[0..C), zero-filled past the row ends.
@@ -762,31 +767,40 @@ struct FbcDw {
 #pragma unroll
         for (int k = 0; k < FW - 1; ++k) win[k] = xs[k * C + c];
         const float* gp = gs + ng * TN;
+        // whole periods of FW columns (the window's rotation phase returns to 0
+        // after each), then the QB % FW remaining columns with compile-time
+        // indices: no per-column bound test
+        constexpr int QF = QB - QB % FW;
 #pragma unroll 1
-        for (int qb = 0; qb < QB; qb += FW) {
+        for (int qb = 0; qb < QF; qb += FW) {
 #pragma unroll
-            for (int s = 0; s < FW; ++s) {
-                const int qq = qb + s;
-                if (qq < QB) {
-                    win[(s + FW - 1) % FW] = xs[(qq + FW - 1) * C + c];
-                    float gv[TN];
-                    if constexpr ((TN & 3) == 0) {
-#pragma unroll
-                        for (int t4 = 0; t4 < TN; t4 += 4) {
-                            const float4 g4 = *reinterpret_cast<const float4*>(gp + qq * NBLK + t4);
-                            gv[t4] = g4.x; gv[t4 + 1] = g4.y; gv[t4 + 2] = g4.z; gv[t4 + 3] = g4.w;
-                        }
-                    } else {
-#pragma unroll
-                        for (int t = 0; t < TN; ++t) gv[t] = gp[qq * NBLK + t];
-                    }
-#pragma unroll
-                    for (int t = 0; t < TN; ++t)
-#pragma unroll
-                        for (int k = 0; k < FW; ++k) ra[t][k] = fmaf(gv[t], win[(s + k) % FW], ra[t][k]);
-                }
-            }
+            for (int s = 0; s < FW; ++s) column(gp, xs, c, qb + s, s, win, ra);
         }
+#pragma unroll
+        for (int s = 0; s < QB - QF; ++s) column(gp, xs, c, QF + s, s, win, ra);
+    }
+
+    // One output column qq of a staged block: the window's next x value enters
+    // slot (s + FW - 1) % FW, then TN x FW multiply-adds.
+    static __device__ __forceinline__ void column(const float* gp, const float* xs, int c, int qq, int s,
+                                                  float (&win)[FW], float (&ra)[TN][FW]) {
+        win[(s + FW - 1) % FW] = xs[(qq + FW - 1) * C + c];
+        float gv[TN];
+        if constexpr ((TN & 3) == 0) {
+            // 16-byte broadcast loads (gp is 16-byte aligned: TN, NBLK % 4 == 0)
+#pragma unroll
+            for (int t4 = 0; t4 < TN; t4 += 4) {
+                const float4 g4 = *reinterpret_cast<const float4*>(gp + qq * NBLK + t4);
+                gv[t4] = g4.x; gv[t4 + 1] = g4.y; gv[t4 + 2] = g4.z; gv[t4 + 3] = g4.w;
+            }
+        } else {
+#pragma unroll
+            for (int t = 0; t < TN; ++t) gv[t] = gp[qq * NBLK + t];
+        }
+#pragma unroll
+        for (int t = 0; t < TN; ++t)
+#pragma unroll
+            for (int k = 0; k < FW; ++k) ra[t][k] = fmaf(gv[t], win[(s + k) % FW], ra[t][k]);
     }
 
     // PK = 1: the same TN x FW terms as packed pairs over adjacent filters
@@ -803,28 +817,47 @@ struct FbcDw {
             win[k] = make_float2(v, v);
         }
         const float* gp = gs + ng * TN;
+        constexpr int QF = QB - QB % FW;
 #pragma unroll 1
-        for (int qb = 0; qb < QB; qb += FW) {
+        for (int qb = 0; qb < QF; qb += FW) {
 #pragma unroll
-            for (int s = 0; s < FW; ++s) {
-                const int qq = qb + s;
-                if (qq < QB) {
-                    const float v = xs[(qq + FW - 1) * C + c];
-                    win[(s + FW - 1) % FW] = make_float2(v, v);
-                    float2 gv[TN / 2];
-#pragma unroll
-                    for (int t4 = 0; t4 < TN; t4 += 4) {
-                        const float4 g4 = *reinterpret_cast<const float4*>(gp + qq * NBLK + t4);
-                        gv[t4 / 2] = make_float2(g4.x, g4.y);
-                        gv[t4 / 2 + 1] = make_float2(g4.z, g4.w);
-                    }
-#pragma unroll
-                    for (int u = 0; u < TN / 2; ++u)
-#pragma unroll
-                        for (int k = 0; k < FW; ++k) ra[u][k] = __ffma2_rn(gv[u], win[(s + k) % FW], ra[u][k]);
-                }
-            }
+            for (int s = 0; s < FW; ++s) column_pk(gp, xs, c, qb + s, s, win, ra);
         }
+#pragma unroll
+        for (int s = 0; s < QB - QF; ++s) column_pk(gp, xs, c, QF + s, s, win, ra);
+    }
+
+    static __device__ __forceinline__ void column_pk(const float* gp, const float* xs, int c, int qq, int s,
+                                                     float2 (&win)[FW], float2 (&ra)[TN / 2][FW]) {
+        const float v = xs[(qq + FW - 1) * C + c];
+        win[(s + FW - 1) % FW] = make_float2(v, v);
+        float2 gv[TN / 2];
+#pragma unroll
+        for (int t4 = 0; t4 < TN; t4 += 4) {
+            const float4 g4 = *reinterpret_cast<const float4*>(gp + qq * NBLK + t4);
+            gv[t4 / 2] = make_float2(g4.x, g4.y);
+            gv[t4 / 2 + 1] = make_float2(g4.z, g4.w);
+        }
+#pragma unroll
+        for (int u = 0; u < TN / 2; ++u)
+#pragma unroll
+            for (int k = 0; k < FW; ++k) ra[u][k] = __ffma2_rn(gv[u], win[(s + k) % FW], ra[u][k]);
+    }
+
+    // Top of pipeline step b: block b has landed (this thread's copies: the only
+    // group in flight), then one barrier -- every thread's copies have landed and
+    // every thread is done with block b - 1 -- after which block b + 1 is issued
+    // into the buffer block b - 1 used, to land while block b is summed.
+    static __device__ __forceinline__ void next_block(const FbcDwArgs& a, float* smem, int b, int nb, int pb,
+                                                      int qblocks, int i, int n0) {
+        fbc_cp_async_wait<0>();
+        __syncthreads();
+        if (b + 1 < nb) {
+            const int p1 = pb + (b + 1) / qblocks, q1 = ((b + 1) % qblocks) * QB;
+            float* nbuf = smem + ((b + 1) & 1) * (GS + XS);
+            issue(a, nbuf, nbuf + GS, p1, q1, i, n0);
+        }
+        fbc_cp_async_commit();
     }
 
     static __device__ __forceinline__ void run_async_pk(const FbcDwArgs& a, float* smem, int chunk, int i,
@@ -838,23 +871,24 @@ struct FbcDw {
         if (pe > a.Ho) pe = a.Ho;
         const int qblocks = (a.Wo + QB - 1) / QB;
         const int nb = (pe - pb) * qblocks;
-        float2 tot[TN / 2][FW], ra[TN / 2][FW];
+        constexpr int TOT_R = (PK == 2) ? 1 : TN / 2;   // register totals only for PK = 1
+        float2 tot[TOT_R][FW], ra[TN / 2][FW];
+        float2* tots = reinterpret_cast<float2*>(smem + 2 * (GS + XS));
 #pragma unroll
         for (int u = 0; u < TN / 2; ++u)
 #pragma unroll
-            for (int k = 0; k < FW; ++k) tot[u][k] = ra[u][k] = make_float2(0.f, 0.f);
+            for (int k = 0; k < FW; ++k) {
+                ra[u][k] = make_float2(0.f, 0.f);
+                if constexpr (PK == 2)
+                    tots[(u * FW + k) * NT + tid] = make_float2(0.f, 0.f);
+                else
+                    tot[u][k] = make_float2(0.f, 0.f);
+            }
         if (nb > 0) issue(a, smem, smem + GS, pb, 0, i, n0);
         fbc_cp_async_commit();
         for (int b = 0; b < nb; ++b) {
             const int buf = b & 1;
-            if (b + 1 < nb) {
-                const int p1 = pb + (b + 1) / qblocks, q1 = ((b + 1) % qblocks) * QB;
-                float* nbuf = smem + (buf ^ 1) * (GS + XS);
-                issue(a, nbuf, nbuf + GS, p1, q1, i, n0);
-            }
-            fbc_cp_async_commit();
-            fbc_cp_async_wait<1>();
-            __syncthreads();
+            next_block(a, smem, b, nb, pb, qblocks, i, n0);
             const float* cur = smem + buf * (GS + XS);
             sum_block_pk(cur, cur + GS, ng, c, ra);
             if ((b + 1) % qblocks == 0) {
@@ -862,22 +896,34 @@ struct FbcDw {
                 for (int u = 0; u < TN / 2; ++u)
 #pragma unroll
                     for (int k = 0; k < FW; ++k) {
-                        tot[u][k].x += ra[u][k].x;
-                        tot[u][k].y += ra[u][k].y;
+                        if constexpr (PK == 2) {
+                            float2 t2 = tots[(u * FW + k) * NT + tid];
+                            t2.x += ra[u][k].x;
+                            t2.y += ra[u][k].y;
+                            tots[(u * FW + k) * NT + tid] = t2;
+                        } else {
+                            tot[u][k].x += ra[u][k].x;
+                            tot[u][k].y += ra[u][k].y;
+                        }
                         ra[u][k] = make_float2(0.f, 0.f);
                     }
             }
-            __syncthreads();
         }
         fbc_cp_async_wait<0>();
+        asm volatile("griddepcontrol.launch_dependents;" ::: "memory");   // the reduction may start launching
 #pragma unroll
         for (int t = 0; t < TN; ++t) {
             const int n = n0 + ng * TN + t;
             if (n >= a.N) continue;
 #pragma unroll
-            for (int k = 0; k < FW; ++k)
-                a.part[((((long long)chunk * a.N + n) * FH + i) * FW + k) * C + c] =
-                    (t & 1) ? tot[t / 2][k].y : tot[t / 2][k].x;
+            for (int k = 0; k < FW; ++k) {
+                float2 t2;
+                if constexpr (PK == 2)
+                    t2 = tots[((t / 2) * FW + k) * NT + tid];
+                else
+                    t2 = tot[t / 2][k];
+                a.part[((((long long)chunk * a.N + n) * FH + i) * FW + k) * C + c] = (t & 1) ? t2.y : t2.x;
+            }
         }
     }
 
@@ -901,14 +947,7 @@ struct FbcDw {
         fbc_cp_async_commit();
         for (int b = 0; b < nb; ++b) {
             const int buf = b & 1;
-            if (b + 1 < nb) {
-                const int p1 = pb + (b + 1) / qblocks, q1 = ((b + 1) % qblocks) * QB;
-                float* nbuf = smem + (buf ^ 1) * (GS + XS);
-                issue(a, nbuf, nbuf + GS, p1, q1, i, n0);
-            }
-            fbc_cp_async_commit();
-            fbc_cp_async_wait<1>();   // block b has landed (this thread's copies)
-            __syncthreads();          // ... and every thread's
+            next_block(a, smem, b, nb, pb, qblocks, i, n0);
             const float* cur = smem + buf * (GS + XS);
             sum_block(cur, cur + GS, ng, c, ra);
             if ((b + 1) % qblocks == 0) {
@@ -921,9 +960,9 @@ struct FbcDw {
                         ra[t][k] = 0.f;
                     }
             }
-            __syncthreads();   // every thread is done with buffer `buf` before it is refilled
         }
         fbc_cp_async_wait<0>();
+        asm volatile("griddepcontrol.launch_dependents;" ::: "memory");   // the reduction may start launching
 #pragma unroll
         for (int t = 0; t < TN; ++t) {
             const int n = n0 + ng * TN + t;
@@ -1028,39 +1067,7 @@ struct FbcDw {
                     }
                 }
                 __syncthreads();
-                if (ng * TN < NBLK) {
-                    float win[FW];
-#pragma unroll
-                    for (int k = 0; k < FW - 1; ++k) win[k] = xs[k * C + c];
-                    const float* gp = gs + ng * TN;
-#pragma unroll 1
-                    for (int qb = 0; qb < QB; qb += FW) {
-#pragma unroll
-                        for (int s = 0; s < FW; ++s) {
-                            const int qq = qb + s;
-                            if (qq < QB) {
-                                win[(s + FW - 1) % FW] = xs[(qq + FW - 1) * C + c];
-                                float gv[TN];
-                                if constexpr ((TN & 3) == 0) {
-                                    // 16-byte broadcast loads (gp is 16-byte aligned: TN, NBLK % 4 == 0)
-#pragma unroll
-                                    for (int t4 = 0; t4 < TN; t4 += 4) {
-                                        const float4 g4 = *reinterpret_cast<const float4*>(gp + qq * NBLK + t4);
-                                        gv[t4] = g4.x; gv[t4 + 1] = g4.y; gv[t4 + 2] = g4.z; gv[t4 + 3] = g4.w;
-                                    }
-                                } else {
-#pragma unroll
-                                    for (int t = 0; t < TN; ++t) gv[t] = gp[qq * NBLK + t];
-                                }
-#pragma unroll
-                                for (int t = 0; t < TN; ++t)
-#pragma unroll
-                                    for (int k = 0; k < FW; ++k)
-                                        ra[t][k] = fmaf(gv[t], win[(s + k) % FW], ra[t][k]);
-                            }
-                        }
-                    }
-                }
+                sum_block(gs, xs, ng, c, ra);
                 __syncthreads();
             }
 #pragma unroll

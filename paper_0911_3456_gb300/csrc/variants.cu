@@ -159,19 +159,22 @@ std::string direct_kernel_source(const DirectProblem& pr, const DirectTile& t,
     return o.str();
 }
 
-size_t dw_smem_bytes(int fw, int c, int tn, int ng, int qb) {
-    return 2 * (size_t)(qb * tn * ng + (qb + fw - 1) * c) * 4;   // two (g, x) buffers
+size_t dw_smem_bytes(int fw, int c, int tn, int ng, int qb, int pk) {
+    // two (g, x) buffers, plus the chunk totals of every thread for pk = 2
+    return (2 * (size_t)(qb * tn * ng + (qb + fw - 1) * c) + (pk == 2 ? (size_t)tn * fw * c * ng : 0)) * 4;
 }
 
 std::string dw_kernel_source(int fh, int fw, int c, int tn, int ng, int qb, int mask, int pk,
-                             const std::string& kname) {
+                             const std::string& kname, int min_blocks) {
     std::ostringstream o;
     o << rtcg_header_source() << "\n";
     o << "typedef FbcDw<" << fh << "," << fw << "," << c << "," << tn << "," << ng << "," << qb << ","
       << mask << "," << pk << "> FbcDwThis;\n";
-    o << "static_assert(FbcDwThis::SMEM_BYTES == " << dw_smem_bytes(fw, c, tn, ng, qb)
+    o << "static_assert(FbcDwThis::SMEM_BYTES == " << dw_smem_bytes(fw, c, tn, ng, qb, pk)
       << ", \"host and device disagree on the shared-memory size\");\n";
-    o << "extern \"C\" __global__ void __launch_bounds__(" << c * ng << ") " << kname
+    o << "extern \"C\" __global__ void __launch_bounds__(" << c * ng;
+    if (min_blocks > 0) o << ", " << min_blocks;
+    o << ") " << kname
       << "(FbcDwArgs a) {\n"
       << "  extern __shared__ __align__(16) float fbc_smem[];\n"
       << "  FbcDwThis::run(a, fbc_smem, blockIdx.x, blockIdx.y, blockIdx.z);\n"

@@ -194,13 +194,14 @@ def test_dx_register_prefetch_is_bit_identical(dx_spec, monkeypatch):
 @pytest.mark.parametrize("shape", [(40, 52, 16, 24, 7, 7), (33, 97, 8, 12, 3, 5), (70, 130, 32, 40, 5, 5)],
                          ids=lambda s: "x".join(map(str, s)))
 def test_dw_packed_pairs_bit_identical(shape, monkeypatch):
-    """dL/dw with packed-pair FMAs (FBCORR_DW_PK=1; off by default, slower at
-    its lower residency) gives the scalar kernel's bits (the same per-lane
-    multiply-adds in the same order) and the oracle's gradient."""
+    """dL/dw with packed-pair FMAs, chunk totals in registers (FBCORR_DW_PK=1)
+    or in shared memory (FBCORR_DW_PK=2), gives the scalar kernel's bits (the
+    same per-lane multiply-adds and the same additions in the same order) and
+    the oracle's gradient."""
     torch = torch_cuda()
     wl = inputs.random_case(1200, *shape, with_g=True)
     outs = []
-    for pk in ("0", "1"):
+    for pk in ("0", "1", "2"):
         monkeypatch.setenv("FBCORR_DW_PK", pk)
         p = _plan(shape)
         _, dw = p.backward(dev(wl.x, torch), dev(wl.w, torch), dev(wl.g, torch), need_dx=False)
@@ -208,4 +209,5 @@ def test_dw_packed_pairs_bit_identical(shape, monkeypatch):
         assert p.info()["dw"]["packed_pairs"] == int(pk)
         outs.append(host(dw))
     assert np.array_equal(outs[0], outs[1])
-    assert normwise_rel(outs[1], oracle.bwd_filt(wl.x, wl.g, wl.w.shape)) <= TOL
+    assert np.array_equal(outs[0], outs[2])
+    assert normwise_rel(outs[2], oracle.bwd_filt(wl.x, wl.g, wl.w.shape)) <= TOL
