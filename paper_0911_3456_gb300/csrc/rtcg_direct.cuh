@@ -437,9 +437,64 @@ struct FbcDirectKS {
     static_assert(TF % 4 == 0, "TF must be a multiple of 4");
     static_assert(NPAIR % KS == 0, "TR*TF/2 must be a multiple of KS");
 
+    // Halo and bank together (C % 4 == 0): one index space over the halo's
+    // float4s followed by the bank's, so that a batch issues the loads of both
+    // before storing any and the whole staging costs one memory round trip when
+    // it fits one batch (first configuration: 1024 + 1296 float4s for 384
+    // threads), where staging them one after the other costs two.
+    static __device__ __forceinline__ void stage_joint(const FbcDirectArgs& a, float* xs, float* ws, int p0,
+                                                       int q0, int f0) {
+        const int tid = threadIdx.x;
+        constexpr int C4 = C / 4;
+        constexpr int NX = HR * HC * C4;
+        constexpr int NV = NX + BN * FH * FW * C4;
+#pragma unroll 1
+        for (int b0 = 0; b0 < NV; b0 += NT * BATCH) {
+            float4 v[BATCH];
+#pragma unroll
+            for (int k = 0; k < BATCH; ++k) {
+                const int e = b0 + tid + k * NT;
+                v[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (e < NX) {
+                    const int c4 = e % C4;
+                    const int t = e / C4;
+                    const int gy = p0 + t / HC, gx = q0 + t % HC;
+                    if (gy < a.in_h && gx < a.in_w)
+                        v[k] = __ldg(reinterpret_cast<const float4*>(a.x + ((long long)gy * a.in_w + gx) * C) + c4);
+                } else if (e < NV) {
+                    const int f = (e - NX) % BN;
+                    const int r = (e - NX) / BN;   // (i*FW + j)*C4 + c4
+                    if (f0 + f < a.nf)
+                        v[k] = __ldg(reinterpret_cast<const float4*>(a.w + (long long)(f0 + f) * (FH * FW * C)) + r);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < BATCH; ++k) {
+                const int e = b0 + tid + k * NT;
+                if (e < NX) {
+                    reinterpret_cast<float4*>(xs + (e / C4) * CP)[e % C4] = v[k];
+                } else if (e < NV) {
+                    const int f = (e - NX) % BN;
+                    const int r = (e - NX) / BN;
+                    const int tap = r / C4;
+                    const int c = (r - tap * C4) * 4;
+                    float* dst = ws + (tap * CPAD + c) * BNP + f;
+                    dst[0] = v[k].x;
+                    dst[BNP] = v[k].y;
+                    dst[2 * BNP] = v[k].z;
+                    dst[3 * BNP] = v[k].w;
+                }
+            }
+        }
+    }
+
     static __device__ __forceinline__ void stage(const FbcDirectArgs& a, float* xs, float* ws, int p0,
                                                  int q0, int f0) {
         const int tid = threadIdx.x;
+        if constexpr (C % 4 == 0 && CPAD == C) {
+            stage_joint(a, xs, ws, p0, q0, f0);
+            return;
+        }
         // ---- input halo [HR][HC][CP]; channels C..CPAD-1 zero
         if constexpr (C % 4 == 0) {
             constexpr int C4 = C / 4;

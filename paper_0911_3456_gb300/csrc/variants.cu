@@ -154,6 +154,11 @@ std::string direct_kernel_source(const DirectProblem& pr, const DirectTile& t,
     if (t.mb) o << ", " << t.mb;
     o << ") " << kname << "(FbcDirectArgs a) {\n"
       << "  extern __shared__ __align__(16) float fbc_smem[];\n"
+      // launched as a programmatic dependent: nothing the previous kernel of
+      // the stream may still read or write is touched before its grid has
+      // completed, and the next kernel may begin launching at once
+      << "  asm volatile(\"griddepcontrol.wait;\" ::: \"memory\");\n"
+      << "  asm volatile(\"griddepcontrol.launch_dependents;\" ::: \"memory\");\n"
       << "  FbcThis::run(a, fbc_smem, blockIdx.x, blockIdx.y, blockIdx.z);\n"
       << "}\n";
     return o.str();
@@ -427,7 +432,7 @@ fbcorr_status_t run_direct(const Kernel& k, const DirectProblem& pr, const Direc
                            float hi, cudaStream_t s) {
     DirectArgsK a{x, m, w, y, pr.in_h, pr.in_w, pr.out_h, pr.out_w, pr.nf, pr.pad_y, pr.pad_x, lo, hi};
     void* args[] = {&a};
-    return launch(k, direct_grid(pr, t), args, s);
+    return launch_dependent(k, direct_grid(pr, t), args, s);
 }
 
 fbcorr_status_t run_default(const DirectProblem& pr, const float* x, const float* m,
