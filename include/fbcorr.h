@@ -319,7 +319,10 @@ fbcorr_status_t fbcorr_fp32_fma_probe(int packed, int iters, double* tflops, dou
 
 /* Generate and compile (NVRTC, sm_103a) -- without loading or running -- the
  * forward, dL/dx and dL/dw kernels that an FP32 plan of this shape would use,
- * with the forward tile `spec` ("heuristic" or a "direct:..." spec); or, for a
+ * with the forward tile `spec` ("heuristic" or a "direct:..." spec; a chunked
+ * K-split spec -- ks with cc > 0 -- is a dL/dx tile and replaces the dL/dx
+ * heuristic instead, FBCORR_ERR_UNSUPPORTED where the shape's dL/dx cannot take
+ * it: a clamp epilogue, or a depth or filter count not a multiple of 4); or, for a
  * "tcgen05:na=..,nb=..,nt=..,bt=..,ew=..,fz=.." spec, the tensor-core kernel
  * that spec generates for this depth and filter width, in both BF16 and split
  * BF16 form.  Needs no GPU.  On failure the NVRTC log (or the reason the spec

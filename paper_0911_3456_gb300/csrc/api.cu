@@ -927,7 +927,15 @@ fbcorr_status_t fbcorr_rtcg_check(const int64_t in_shape[3], const int64_t filt_
         t = direct_heuristic(fp, lim, 148);
     else if (!parse_direct_spec(sp, &t))
         return set_error(FBCORR_ERR_INVALID_ARG, "unknown variant spec '%s'", sp.c_str());
-    const DirectTile tb = direct_heuristic(bp, lim, 148);
+    DirectTile tb = direct_heuristic(bp, lim, 148);
+    if (t.ks_chunked()) {
+        // a chunked K-split spec is a dL/dx tile: checked on the flipped problem
+        if (!ks_chunked_fits(bp))
+            return set_error(FBCORR_ERR_UNSUPPORTED, "spec '%s' is a dL/dx tile that this shape does not take",
+                             sp.c_str());
+        tb = t;
+        t = direct_heuristic(fp, lim, 148);
+    }
     const int mask = epilogue.kind == FBCORR_EPI_CLAMP ? 1 : 0;
     const std::string srcs[3] = {
         direct_kernel_source(fp, t, kname_for("fbc_direct", fp, t)),

@@ -107,10 +107,13 @@ struct DirectTile {
     // bits (the lanes of a quarter warp then read the same filter values).
     // ks = 1: one column per lane (wq = 1, sh = 0).
     int ks = 1, wq = 1, sh = 0;
+    // ks > 1 with cc > 0 (dL/dx without a clamp mask only): the chunked K-split
+    // tile, cc channels per chunk through a cp.async ring of 2 stages, 3 with pf = 1
     // mb > 0: compiled with __launch_bounds__(threads, mb), so that mb CTAs fit in
     // an SM's registers (one stages while the others compute); 0: no bound
     int mb = 0;
-    int chunk(int c) const { return ks > 1 ? c : ((cc > 0 && cc < c) ? cc : c); }
+    bool ks_chunked() const { return ks > 1 && cc > 0; }
+    int chunk(int c) const { return (ks > 1 && cc == 0) ? c : ((cc > 0 && cc < c) ? cc : c); }
     int bh() const { return tr * wr; }
     int bn() const { return tf * wf; }
     int bw() const { return (32 / ks) * wq; }
@@ -137,6 +140,8 @@ std::string direct_kernel_source(const DirectProblem& pr, const DirectTile& t,
                                  const std::string& kname);
 // threads > 0 restricts the candidates to one CTA size (the batched kernel).
 // max_block bounds the per-thread accumulator block TR*TF (register pressure).
+// dL/dx without a clamp mask, c % 4 == 0 and nf % 4 == 0: the chunked K-split tile applies.
+bool ks_chunked_fits(const DirectProblem& pr);
 std::vector<DirectTile> direct_candidates(const DirectProblem& pr, size_t smem_limit,
                                           int threads = 0, int max_block = 64);
 // The specs the tuner times: the first topk tiles of a ranked list, each as

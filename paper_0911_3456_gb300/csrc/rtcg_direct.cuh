@@ -774,6 +774,204 @@ __device__ __forceinline__ void fbc_cp_async_commit() { asm volatile("cp.async.c
 template <int N>
 __device__ __forceinline__ void fbc_cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
+// ---- K-split dL/dx tile with channel chunks in a cp.async ring --------------
+// dL/dx of the differentiation workload (Sec. 6.2's correlation run over the
+// zero-padded upstream gradient with the flipped bank) has a long reduction
+// (K = FH*FW*N = 7*7*64) but a small output (256 x 256 x 16): one output column
+// per lane with a 28-value register block is 8 warps per SM, too few to hide
+// the latencies of the inner loop, and the register prefetch of the next chunk
+// that the lane-per-column tile uses keeps it at that.  Here, as in the K-split
+// forward tile, the KS lanes of a lane group (qs = lane / KS, s = lane % KS)
+// share a TR x TF output block and split the channels: lane s sums channels
+// c0 + s + KS*t of every chunk, and a fixed reduce-scatter over the lane bits
+// of s combines the partial blocks at the end (deterministic).  Both operands
+// keep their global layouts in shared memory, so every staged element is a
+// 16-byte cp.async copy and chunks stream through an NS-stage ring while an
+// earlier one is summed, with no registers spent on staging:
+//   halo  [HR][HC][CP]: gradient pixels with channels c0 .. c0+CC-1, zero
+//         outside the gradient (the padding) -- the copy's zero fill;
+//   bank  [FH][FW][CC][BNP]: row (i, j, cl) holds the flipped bank's output
+//         channels d0 .. d0+BN-1 for gradient channel n = c0 + cl, which are the
+//         contiguous run w[n][FH-1-i][FW-1-j][d0 ..] of the bank itself: the flip
+//         turns the bank's layout into the one the tile reads.
+// The pixel pitch CP = CC + ((KS - CC) mod 32) makes the LQ x KS lanes of a
+// warp read 32 distinct banks; BNP / 4 odd puts the KS channel rows of a float4
+// filter read into distinct bank quads.  A block of NPAIR accumulator pairs is
+// reduced as NPR = NPAIR rounded up to a multiple of KS pairs (the extra pairs
+// are zero and not stored).  Requires C % 4 == 0, nf % 4 == 0, CC % KS == 0,
+// CC % 4 == 0; no clamp mask (callers check).
+template <int FH, int FW, int C, int TR, int TF, int KS, int WQ, int WR, int WF, int CC, int NS, int PK>
+struct FbcDirectKSC {
+    static constexpr int LQ = 32 / KS;
+    static constexpr int BW = LQ * WQ;
+    static constexpr int BH = TR * WR;
+    static constexpr int BN = TF * WF;
+    static constexpr int NT = 32 * WQ * WR * WF;
+    static constexpr int HR = BH + FH - 1;
+    static constexpr int HC = BW + FW - 1;
+    static constexpr int CPL = CC / KS;                            // channels per lane and chunk
+    static constexpr int CP = CC + (((KS - CC) % 32) + 32) % 32;   // CP = KS (mod 32)
+    static constexpr int BNP = ((BN / 4) % 2 == 1) ? BN : BN + 4;
+    static constexpr int XS = HR * HC * CP;
+    static constexpr int WS = FH * FW * CC * BNP;
+    static constexpr int STAGE = XS + WS;                          // floats per ring stage
+    static constexpr int SMEM_BYTES = NS * STAGE * 4;
+    static constexpr int NCH = (C + CC - 1) / CC;
+    static constexpr int NPAIR = TR * TF / 2;
+    static constexpr int NPR = (NPAIR + KS - 1) / KS * KS;
+    static constexpr int NOWN = NPR / KS;
+    static_assert(KS == 4 || KS == 8 || KS == 16 || KS == 32, "KS must be 4, 8, 16 or 32");
+    static_assert(TF % 4 == 0 && CC % 4 == 0 && CC % KS == 0 && C % 4 == 0, "16-byte staging");
+    static_assert(NS == 2 || NS == 3, "two or three ring stages");
+
+    // Issue the copies of chunk kc into ring stage sb (one commit group per chunk).
+    static __device__ __forceinline__ void issue(const FbcDirectArgs& a, float* sb, int kc, int p0, int q0,
+                                                 int f0) {
+        constexpr int C4 = CC / 4;
+        constexpr int B4 = BN / 4;
+        constexpr int NX = HR * HC * C4;
+        constexpr int NV = NX + FH * FW * CC * B4;
+        const int c0 = kc * CC;
+        float* xs = sb;
+        float* ws = sb + XS;
+#pragma unroll 4
+        for (int e = threadIdx.x; e < NV; e += NT) {
+            if (e < NX) {
+                const int c4 = e % C4;
+                const int t = e / C4;
+                const int gy = p0 - a.pad_y + t / HC, gx = q0 - a.pad_x + t % HC;
+                const int c = c0 + 4 * c4;
+                const bool ok = gy >= 0 && gy < a.in_h && gx >= 0 && gx < a.in_w && c < C;
+                fbc_cp_async16(xs + t * CP + 4 * c4, ok ? a.x + ((long long)gy * a.in_w + gx) * C + c : a.x,
+                               ok ? 16 : 0);
+            } else {
+                const int r = e - NX;
+                const int f4 = r % B4;
+                const int row = r / B4;   // (i*FW + j)*CC + cl
+                const int tap = row / CC;
+                const int cl = row - tap * CC;
+                const int i = tap / FW, j = tap - (tap / FW) * FW;
+                const int n = c0 + cl, d = f0 + 4 * f4;
+                const bool ok = n < C && d < a.nf;
+                fbc_cp_async16(ws + row * BNP + 4 * f4,
+                               ok ? a.w + (((long long)n * FH + (FH - 1 - i)) * FW + (FW - 1 - j)) * a.nf + d : a.w,
+                               ok ? 16 : 0);
+            }
+        }
+    }
+
+    static __device__ __forceinline__ void run(const FbcDirectArgs& a, float* smem, int tile_x, int tile_y,
+                                               int tile_f) {
+        const int lane = threadIdx.x & 31;
+        const int warp = threadIdx.x >> 5;
+        const int s = lane % KS;
+        const int qs = lane / KS;
+        const int wq = warp % WQ;
+        const int wr = (warp / WQ) % WR;
+        const int wf = warp / (WQ * WR);
+        const int q0 = tile_x * BW;
+        const int p0 = tile_y * BH;
+        const int f0 = tile_f * BN;
+
+        float2 acc[TR][TF / 2];
+#pragma unroll
+        for (int r = 0; r < TR; ++r)
+#pragma unroll
+            for (int f = 0; f < TF / 2; ++f) acc[r][f] = make_float2(0.f, 0.f);
+
+#pragma unroll
+        for (int k = 0; k < NS - 1; ++k) {
+            if (k < NCH) issue(a, smem + k * STAGE, k, p0, q0, f0);
+            fbc_cp_async_commit();
+        }
+#pragma unroll 1
+        for (int kc = 0; kc < NCH; ++kc) {
+            fbc_cp_async_wait<NS - 2>();   // this thread's copies of chunk kc have landed
+            __syncthreads();               // everyone's have, and chunk kc-1 is no longer read
+            const int kn = kc + NS - 1;    // refill the stage chunk kc-1 used
+            if (kn < NCH) issue(a, smem + (kn % NS) * STAGE, kn, p0, q0, f0);
+            fbc_cp_async_commit();
+            const float* xs = smem + (kc % NS) * STAGE;
+            const float* xb = xs + ((wr * TR) * HC + wq * LQ + qs) * CP + s;
+            const float* wb = xs + XS + s * BNP + wf * TF;
+#pragma unroll
+            for (int t = 0; t < CPL; ++t) {
+#pragma unroll 1
+                for (int j = 0; j < FW; ++j) {
+                    float xv[TR + FH - 1];
+#pragma unroll
+                    for (int k = 0; k < TR + FH - 1; ++k) xv[k] = xb[(k * HC + j) * CP + KS * t];
+#pragma unroll
+                    for (int i = 0; i < FH; ++i) {
+                        const float4* wp = reinterpret_cast<const float4*>(wb + ((i * FW + j) * CC + KS * t) * BNP);
+                        float2 wv[TF / 2];
+#pragma unroll
+                        for (int f4 = 0; f4 < TF / 4; ++f4) {
+                            const float4 t4 = wp[f4];
+                            wv[2 * f4 + 0] = make_float2(t4.x, t4.y);
+                            wv[2 * f4 + 1] = make_float2(t4.z, t4.w);
+                        }
+#pragma unroll
+                        for (int r = 0; r < TR; ++r) {
+                            if constexpr (PK) {
+                                const float2 xx = make_float2(xv[r + i], xv[r + i]);
+#pragma unroll
+                                for (int f = 0; f < TF / 2; ++f) acc[r][f] = __ffma2_rn(xx, wv[f], acc[r][f]);
+                            } else {
+#pragma unroll
+                                for (int f = 0; f < TF / 2; ++f) {
+                                    acc[r][f].x = fmaf(xv[r + i], wv[f].x, acc[r][f].x);
+                                    acc[r][f].y = fmaf(xv[r + i], wv[f].y, acc[r][f].y);
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        fbc_cp_async_wait<0>();   // only empty groups remain; nothing is left in flight at exit
+
+        float2 v[NPR];
+#pragma unroll
+        for (int r = 0; r < TR; ++r)
+#pragma unroll
+            for (int f = 0; f < TF / 2; ++f) v[r * (TF / 2) + f] = acc[r][f];
+#pragma unroll
+        for (int k = NPAIR; k < NPR; ++k) v[k] = make_float2(0.f, 0.f);
+        reduce_step<KS / 2, NPR>(v, s);
+
+        const int q = q0 + wq * LQ + qs;
+        if (q >= a.out_w) return;
+#pragma unroll
+        for (int k = 0; k < NOWN; ++k) {
+            const int o = s * NOWN + k;
+            if (o >= NPAIR) continue;
+            const int r = o / (TF / 2);
+            const int n = f0 + wf * TF + 2 * (o % (TF / 2));
+            const int p = p0 + wr * TR + r;
+            if (p >= a.out_h || n >= a.nf) continue;
+            // nf % 4 == 0 and n even: both values of the pair are in range
+            *reinterpret_cast<float2*>(a.y + ((long long)p * a.out_w + q) * a.nf + n) = v[k];
+        }
+    }
+
+    template <int M, int LEN>
+    static __device__ __forceinline__ void reduce_step(float2 (&v)[NPR], int s) {
+        if constexpr (M >= 1) {
+            const bool hi = (s & M) != 0;
+#pragma unroll
+            for (int k = 0; k < LEN / 2; ++k) {
+                const float2 send = hi ? v[k] : v[k + LEN / 2];
+                const float2 mine = hi ? v[k + LEN / 2] : v[k];
+                const float gx = __shfl_xor_sync(0xffffffffu, send.x, M);
+                const float gy = __shfl_xor_sync(0xffffffffu, send.y, M);
+                v[k] = make_float2(mine.x + gx, mine.y + gy);
+            }
+            reduce_step<M / 2, LEN / 2>(v, s);
+        }
+    }
+};
+
 // Shared memory holds two (g block, x segment) buffers: with 16-byte rows of g
 // and x (N % 4 == 0, C % 4 == 0) and no clamp mask, the blocks of a chunk stream
 // through them with cp.async, the next block's copies in flight while the current

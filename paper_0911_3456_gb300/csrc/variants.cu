@@ -26,6 +26,14 @@ const char* rtcg_nn_params_source() { return kRtcgNnParamsSrc; }
 const char* rtcg_nn_source() { return kRtcgNnSrc; }
 
 size_t direct_smem_bytes(const DirectTile& t, int fh, int fw, int c) {
+    if (t.ks_chunked()) {
+        // FbcDirectKSC: a ring of (halo [HR][HC][CP] + bank [fh][fw][cc][BNP]) stages
+        const long cp = t.cc + (((t.ks - t.cc) % 32) + 32) % 32;
+        const long bn = t.bn();
+        const long bnp = ((bn / 4) % 2 == 1) ? bn : bn + 4;
+        const long hr = t.bh() + fh - 1, hc = t.bw() + fw - 1;
+        return (size_t)(t.pf ? 3 : 2) * (size_t)(hr * hc * cp + (long)fh * fw * t.cc * bnp) * 4;
+    }
     if (t.ks > 1) {
         // FbcDirectKS: halo [HR][HC][CP] + bank [fh][fw][CPAD][BNP]
         const long cpad = (c + t.ks - 1) / t.ks * t.ks;
@@ -58,6 +66,9 @@ std::string direct_tile_spec(const DirectTile& t) {
 
 static bool ks_tile_ok(const DirectTile& t) {
     if (t.ks == 1) return t.wq == 1 && t.sh == 0;
+    if (t.ks_chunked())   // chunks of cc channels, cc / ks of them per lane
+        return (t.ks == 4 || t.ks == 8 || t.ks == 16) && t.sh == 0 && t.cc % t.ks == 0 && t.cc % 4 == 0 &&
+               t.cc / t.ks <= 4 && t.wq >= 1 && t.wq <= 32;
     if (t.pf) return false;   // the K-split tile stages the whole depth once
     if (t.sh != 0 && t.sh != 1) return false;
     if (t.ks != 4 && t.ks != 8 && t.ks != 16 && t.ks != 32) return false;
@@ -138,7 +149,12 @@ std::string direct_kernel_source(const DirectProblem& pr, const DirectTile& t,
     std::ostringstream o;
     o << rtcg_header_source() << "\n";
     if (pr.epi == 2) o << snippet_definition(pr.snippet);
-    if (t.ks > 1) {
+    if (t.ks_chunked()) {
+        // the chunked K-split tile (dL/dx only: callers check flip == 1, mask == 0)
+        o << "typedef FbcDirectKSC<" << pr.fh << "," << pr.fw << "," << pr.c << "," << t.tr << "," << t.tf << ","
+          << t.ks << "," << t.wq << "," << t.wr << "," << t.wf << "," << t.cc << "," << (t.pf ? 3 : 2) << ","
+          << t.pk << "> FbcThis;\n";
+    } else if (t.ks > 1) {
         // the K-split tile (forward only: callers check flip == 0 and mask == 0)
         o << "typedef FbcDirectKS<" << pr.fh << "," << pr.fw << "," << pr.c << "," << t.tr << "," << t.tf << ","
           << t.ks << "," << t.wq << "," << t.wr << "," << t.wf << "," << pr.epi << "," << t.pk << "," << t.sh
@@ -204,6 +220,13 @@ double wave_balance(long ctas, int res, int sms) {
 }
 }  // namespace
 
+// The chunked K-split tile's problem: dL/dx (flipped bank) without a clamp mask
+// or epilogue, 16-byte rows of the gradient (c % 4 == 0) and of the bank's
+// output-channel runs (nf % 4 == 0).
+bool ks_chunked_fits(const DirectProblem& pr) {
+    return pr.flip == 1 && pr.mask == 0 && pr.epi == 0 && pr.c % 4 == 0 && pr.nf % 4 == 0;
+}
+
 std::vector<DirectTile> direct_candidates(const DirectProblem& pr, size_t smem_limit, int threads,
                                           int max_block) {
     std::vector<DirectTile> out;
@@ -238,7 +261,32 @@ std::vector<DirectTile> direct_candidates(const DirectProblem& pr, size_t smem_l
     // ks lanes per output split the depth, at most a quarter of them on zero
     // padding channels and at most 8 channels per lane (deeper inputs keep the
     // lane-per-column tile busy enough)
-    if (threads > 0 || pr.flip || pr.mask) return out;
+    if (threads > 0) return out;
+    if (ks_chunked_fits(pr)) {
+        // chunked K-split tiles for dL/dx: chunks of cc = ks or 2 ks channels
+        for (int ks : {4, 8})
+            for (int cpl : {1, 2})
+                for (int tr : {4, 6, 7, 8})
+                    for (int tf : {4, 8})
+                        for (int wq : {1, 2, 4})
+                            for (int wr : {1, 2, 3, 4})
+                                for (int wf : {1, 2, 4})
+                                    for (int pf : {0, 1}) {
+                                        DirectTile t{tr, tf, wr, wf, ks * cpl};
+                                        t.ks = ks;
+                                        t.wq = wq;
+                                        t.pf = pf;
+                                        if (t.cc > pr.c || t.threads() > 512 || t.threads() < 128) continue;
+                                        if (tf > pr.nf || (t.bn() > pr.nf && wf > 1)) continue;
+                                        if (tr * tf > max_block || tr + pr.fh - 1 > 40) continue;
+                                        if (t.bw() > ((pr.out_w + 7) / 8) * 8 + 8 && wq > 1) continue;
+                                        if (t.bh() > ((pr.out_h + 1) / 2) * 2 + 8 && wr > 1) continue;
+                                        if (direct_smem_bytes(t, pr.fh, pr.fw, pr.c) > smem_limit) continue;
+                                        out.push_back(t);
+                                    }
+        return out;
+    }
+    if (pr.flip || pr.mask) return out;
     for (int ks : {4, 8, 16, 32}) {
         const int cpad = (pr.c + ks - 1) / ks * ks;
         if (4 * (cpad - pr.c) > cpad || cpad / ks > 8) continue;
@@ -270,6 +318,33 @@ std::vector<DirectTile> direct_candidates(const DirectProblem& pr, size_t smem_l
 // orders the candidates the tuner measures first.
 static double direct_score(const DirectProblem& pr, const DirectTile& t, int sm_count) {
     const size_t smem_per_sm = 228 * 1024;
+    if (t.ks_chunked()) {
+        // chunked K-split tile: tile edges and wave quantisation, the inner loop
+        // of the K-split tile, a barrier per chunk, and latency hiding, which
+        // wants about 16 warps per SM (the staging is asynchronous)
+        const int gx = ceil_div(pr.out_w, t.bw()), gy = ceil_div(pr.out_h, t.bh()), gz = ceil_div(pr.nf, t.bn());
+        const double useful = (double)pr.out_w * pr.out_h * pr.nf;
+        const double computed = (double)gx * t.bw() * gy * t.bh() * gz * t.bn();
+        const int nch = ceil_div(pr.c, t.cc);
+        const double e_tile = useful / computed * pr.c / ((double)nch * t.cc);
+        const size_t smem = direct_smem_bytes(t, pr.fh, pr.fw, pr.c) + 1024;
+        const int regs = t.tr * t.tf + t.tr + pr.fh + t.tf + 40;
+        int res = (int)(smem_per_sm / smem);
+        res = std::min(res, 2048 / t.threads());
+        res = std::min(res, 65536 / (t.threads() * std::min(255, regs)));
+        if (res < 1) return -1.0;
+        const long ctas = (long)gx * gy * gz;
+        const double wave_eff = wave_balance(ctas, res, sm_count);
+        const double fma_cyc = t.tr * t.tf * pr.fh / 4.0;
+        const double lsu_cyc = (t.tr + pr.fh - 1) + pr.fh * t.tf;
+        const double iss_cyc = (t.tr * t.tf * pr.fh / 2.0 + (t.tr + pr.fh - 1) + pr.fh * t.tf / 4.0) / 4.0;
+        const double e_inner = fma_cyc / std::max(fma_cyc, std::max(lsu_cyc, iss_cyc));
+        const double fma_chunk = (double)t.tr * t.tf * pr.fh * pr.fw * (t.cc / t.ks);
+        const double e_issue = e_inner * fma_chunk / (fma_chunk + 300.0 + 4.0 * t.tr * t.tf / nch);
+        const int warps = std::min<long>(res, (ctas + sm_count - 1) / sm_count) * t.threads() / 32;
+        const double occ = std::min(1.0, warps / 16.0);
+        return e_tile * wave_eff * e_issue * (0.4 + 0.6 * occ);
+    }
     if (t.ks > 1) {
         // K-split tile: the same factors, with the depth split over ks lanes (a
         // share of them on zero padding), vectorised staging, and the shuffle
@@ -376,6 +451,9 @@ std::vector<std::string> direct_tuning_specs(const std::vector<DirectTile>& rank
 DirectTile direct_heuristic(const DirectProblem& pr, size_t smem_limit, int sm_count, int threads,
                             int max_block) {
     auto r = direct_ranked(pr, smem_limit, sm_count, threads, max_block);
+    // the model does not rate the chunked K-split tile against the others (its
+    // score is on another scale): only the tuner's measurements choose it
+    r.erase(std::remove_if(r.begin(), r.end(), [](const DirectTile& c) { return c.ks_chunked(); }), r.end());
     DirectTile t = !r.empty() ? r.front() : (threads == 256 ? DirectTile{4, 4, 2, 4, 4} : DirectTile{4, 4, 1, 1, 4});
     // packed-pair FMAs: the same bits, and faster on most tiles measured on a
     // GB300 (median 0.91-0.93 of the scalar time across the top 48 tiles)
@@ -415,7 +493,11 @@ size_t smem_limit(const DeviceInfo& dev) {
 }
 
 fbcorr_status_t build_direct(const DirectProblem& pr, const DirectTile& t, Kernel* k) {
-    if (t.ks > 1 && (pr.flip || pr.mask))
+    if (t.ks_chunked() && !ks_chunked_fits(pr))
+        return set_error(FBCORR_ERR_UNSUPPORTED,
+                         "chunked K-split tiles compute dL/dx without a clamp mask, with depth and filter count "
+                         "multiples of 4");
+    if (t.ks > 1 && !t.ks_chunked() && (pr.flip || pr.mask))
         return set_error(FBCORR_ERR_UNSUPPORTED, "K-split tiles compute the forward correlation only");
     const std::string name = kname_for("fbc_direct", pr, t);
     const std::string src = direct_kernel_source(pr, t, name);

@@ -180,6 +180,27 @@ def test_ksplit_tiles_compile(lib, D, N, spec):
     assert st == 0, C.last_error() + log.value.decode()
 
 
+@pytest.mark.parametrize("shape,clamp,spec,expect", [
+    ((256, 256, 16, 64, 7, 7), None, b"direct:tr=7,tf=4,wr=2,wf=4,cc=4,pk=1,ks=4,wq=2", 0),
+    ((256, 256, 16, 64, 7, 7), None, b"direct:tr=8,tf=4,wr=2,wf=4,cc=8,pk=1,pf=1,ks=4,wq=2", 0),
+    ((40, 52, 16, 24, 7, 7), None, b"direct:tr=6,tf=8,wr=2,wf=2,cc=16,ks=8,wq=1", 0),
+    ((61, 45, 4, 8, 5, 4), None, b"direct:tr=7,tf=4,wr=2,wf=4,cc=8,pk=1,ks=8,wq=2", 0),
+    ((40, 52, 16, 24, 7, 7), (0, 1), b"direct:tr=7,tf=4,wr=2,wf=4,cc=4,pk=1,ks=4,wq=2", 3),   # clamp mask
+    ((40, 52, 6, 24, 7, 7), None, b"direct:tr=7,tf=4,wr=2,wf=4,cc=4,pk=1,ks=4,wq=2", 3),      # D % 4
+    ((40, 52, 16, 22, 7, 7), None, b"direct:tr=7,tf=4,wr=2,wf=4,cc=4,pk=1,ks=4,wq=2", 3),     # N % 4
+    ((40, 52, 16, 24, 7, 7), None, b"direct:tr=7,tf=4,wr=2,wf=4,cc=6,pk=1,ks=4,wq=2", 1),     # cc % ks
+    ((40, 52, 16, 24, 7, 7), None, b"direct:tr=7,tf=4,wr=2,wf=4,cc=40,pk=1,ks=8,wq=2", 1),    # 5 per lane
+    ((40, 52, 16, 24, 7, 7), None, b"direct:tr=7,tf=4,wr=2,wf=4,cc=8,pk=1,ks=8,wq=2,sh=1", 1),
+])
+def test_chunked_ksplit_dx_tiles_compile(lib, shape, clamp, spec, expect):
+    """The chunked K-split dL/dx tile compiles for sm_103a on the flipped
+    problem; shapes whose dL/dx it cannot take and malformed specs are refused."""
+    H, W, D, N, fh, fw = shape
+    log = ctypes.create_string_buffer(1 << 16)
+    st = lib.fbcorr_rtcg_check(C.I64_3(H, W, D), C.I64_4(N, fh, fw, D), C.epilogue(clamp), spec, log, len(log))
+    assert st == expect, C.last_error() + log.value.decode()
+
+
 @pytest.mark.parametrize("D,f,spec", [
     (32, 5, b"tcgen05:na=2,nb=4,nt=256,bt=5,ew=4,fz=1,nr=0,cw=4"),    # the precision workload, converters from registers
     (32, 5, b"tcgen05:na=3,nb=3,nt=256,bt=3,ew=8,fz=2,nr=3,cw=8"),    # raw-row ring; two stages, the second partial
