@@ -3,7 +3,7 @@
 // width FW, the taps per B stage BT, the epilogue warp count EW, the fused
 // conversion switch FUSE (and its converter warps CW), the snippet switch USER,
 // the epilogue store path TS (with SB staging slots), the resident-bank
-// switch RES and the CTA-pair switch PAIR baked in.  Embedded as a string into libfbcorr and prefixed with
+// switch RES, the CTA-pair switch PAIR and the sliding-window switch SW baked in.  Embedded as a string into libfbcorr and prefixed with
 // tc_params.h and rtcg_ptx.cuh; self-contained (no system headers).
 //
 // The correlation of Sec. 6.2 as an implicit GEMM: for every filter tap (i, j)
@@ -78,6 +78,17 @@
 // epilogue warps release an accumulator with remote arrivals on the even CTA's
 // acc_empty.  Each CTA stores its own 128 accumulator rows.
 //
+// Sliding window (SW = 1; one filter tile, W a multiple of 128, single CTAs):
+// the slab of filter row i of the tile at output row p, columns c .. c+127, is
+// input row p + i, which is also the slab of filter row i - 1 of the tile one
+// output row down.  A CTA takes a run of consecutive output rows of one
+// 128-pixel column block, and its A ring holds slabs, not (tile, filter row)
+// pairs: tile k of the run reads slabs k .. k + fh - 1, so the run of n tiles
+// brings in and converts n + fh - 1 slab rows instead of n * fh.  Slab j sits in
+// slot j % na (na >= fh), is waited for by every tile that reads it (its slot's
+// barrier cannot move on before the slab is released) and is released by its
+// last reader: tile j as its filter row 0, or the run's last tile.
+//
 // Tail halves: tiles t >= nfull, the last partial round of a single 256-wide
 // filter tile, run as two 128-column work items each (instruction N = 128, B
 // from half-width planes), so that round keeps twice as many SMs busy for half
@@ -114,9 +125,10 @@ __device__ __forceinline__ void fbc_issue_tap(fbc_u32 d_tmem, fbc_u64 ad, fbc_u6
 
 // ---------------------------------------------------------------- the kernel body
 template <int NC, int SPLIT, int FW, int BT, int EW, int FUSE, int CW, int USER, int TS, int SB, int RES,
-          int PAIR>
+          int PAIR, int SW>
 __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
     static_assert(!(PAIR && RES), "a CTA pair streams the bank");
+    static_assert(!(SW && (PAIR || RES)), "the sliding window runs single CTAs over a streamed bank");
     constexpr int CG = PAIR ? 2 : 1;                 // cta_group of every tcgen05 instruction
     constexpr int NST = (FW + BT - 1) / BT;          // B stages per filter row
     constexpr int L = FBC_TC_TILE_M + FW - 1;        // slab pixels per filter row
@@ -198,12 +210,19 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
     // PAIR (one filter tile of 256): pair u = blockIdx.x / 2 takes the pixel-tile
     // pairs u, u + gridDim.x / 2, ...; pair w is tiles 2w (even CTA) and 2w + 1
     // (odd CTA; tile mtiles, past the image when mtiles is odd, stores nothing)
+    // SW: column block blockIdx.x % sw_delta, output rows [sw_r0, sw_r1) of the
+    // gridDim.x / sw_delta equal runs of that block
     const int nsched = P.mtiles * P.ntn;
     const int res_fi = RES ? (int)blockIdx.x % P.ntn : 0;
     const int unit = RES ? (int)blockIdx.x / P.ntn : PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
     const int nunits = RES ? (int)gridDim.x / P.ntn : PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
     const int nwork = RES ? P.mtiles : PAIR ? (P.mtiles + 1) >> 1 : P.nfull + 2 * (nsched - P.nfull);
-    const int my_tiles = unit < nwork ? (nwork - 1 - unit) / nunits + 1 : 0;   // work items
+    const int sw_runs = SW ? (int)gridDim.x / P.sw_delta : 1;
+    const int sw_u = SW ? (int)blockIdx.x / P.sw_delta : 0;
+    const int sw_t0 = SW ? (int)((long long)sw_u * P.Ho / sw_runs) * P.sw_delta + (int)blockIdx.x % P.sw_delta : 0;
+    const int sw_n = SW ? (int)((long long)(sw_u + 1) * P.Ho / sw_runs - (long long)sw_u * P.Ho / sw_runs) : 0;
+    const int my_tiles = SW ? (sw_u < sw_runs ? sw_n : 0)
+                            : unit < nwork ? (nwork - 1 - unit) / nunits + 1 : 0;   // work items
     struct Item {
         int tile;    // pixel tile t % mtiles of filter tile t / mtiles
         int nt;      // filter columns of this item (the MMA's N)
@@ -215,6 +234,15 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
     auto item_of = [&](int k) -> Item {
         const int w = unit + k * nunits;
         Item it;
+        if (SW) {
+            it.half = false;
+            it.tile = sw_t0 + k * P.sw_delta;
+            it.nt = P.nt;
+            it.bn = P.nt;
+            it.n0 = 0;
+            it.wbase = 0;
+            return it;
+        }
         if (PAIR) {
             it.half = true;
             it.tile = 2 * w + (int)rank;
@@ -242,10 +270,15 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
     };
     auto tile_of = [&](int k) -> int { return item_of(k).tile; };
     const int R = my_tiles * P.fh;                    // filter rows this CTA runs, in order
+    // slab rows this CTA brings in: one per filter row, or (SW) the run's
+    // distinct input rows; filter row r reads slab slab_of(r)
+    const int RA = SW ? (my_tiles > 0 ? my_tiles + P.fh - 1 : 0) : R;
+    auto slab_of = [&](int r) -> int { return SW ? r / P.fh + r % P.fh : r; };
     const fbc_u32 plane = (fbc_u32)P.lp * 16u;        // bytes per A chunk plane (shared)
     const fbc_u32 a_half = NC * plane;                // offset of the lo planes in an A slot
     // first input pixel of slab row r
     auto row_p0 = [&](int r) -> long long {
+        if (SW) return (long long)sw_t0 * FBC_TC_TILE_M + (long long)r * P.W;
         const int tile = tile_of(r / P.fh);
         return (long long)(tile % P.mtiles) * FBC_TC_TILE_M + (long long)(r % P.fh) * P.W;
     };
@@ -270,7 +303,7 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
             for (int r = 0; r < R && ok; ++r) {
                 // the A side of rows up to r + look goes out before the B stages of
                 // row r, so it is in flight while the MMAs of earlier rows run
-                while (FUSE != 1 && ok && next_a < R && next_a <= r + P.alook) {
+                while (FUSE != 1 && ok && next_a < RA && next_a <= slab_of(r) + P.alook) {
                     const long long p0 = row_p0(next_a);
                     if (FUSE == 2) {
                         // one copy of the raw FP32 slab row (16-byte multiples: D % 4 == 0)
@@ -391,6 +424,13 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
                 const fbc_u64 bk = (2 * bplane_i) >> 4, blo = ((fbc_u64)BT * bhalf_i) >> 4, btap = bhalf_i >> 4;
                 fbc_u32 accumulate = 0;
                 for (int i = 0; i < P.fh && ok; ++i) {
+                    if (SW) {
+                        // slab k + i: its slot and the parity of its fill
+                        const int j = k + i;
+                        as = j % P.na;
+                        aph = (fbc_u32)(j / P.na) & 1u;
+                        adesc = adesc0 + (fbc_u64)as * a_step;
+                    }
                     if (!(ok = fbc_wait(a_full0 + 8u * as, aph, P, abort_flag, FBC_TC_ERR_WAIT_A))) break;
                     if (PAIR && !(ok = fbc_wait(pa_full0 + 8u * as, aph, P, abort_flag, FBC_TC_ERR_WAIT_A))) break;
 #pragma unroll
@@ -418,6 +458,11 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
                         }
                     }
                     if (!ok) break;
+                    if (SW) {
+                        // the slab's last reader releases it
+                        if (i == 0 || k == my_tiles - 1) fbc_umma_commit<CG>(a_empty0 + 8u * as);
+                        continue;
+                    }
                     fbc_umma_commit<CG>(a_empty0 + 8u * as);
                     if (PAIR) fbc_umma_commit<CG>(fbc_mapa(a_empty0 + 8u * as, 1u));
                     if (++as == P.na) { as = 0; aph ^= 1; adesc = adesc0; } else { adesc += a_step; }
@@ -706,16 +751,16 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
                 return true;
             };
             float4 even[KI][2], odd[KI][2];
-            if (R > 0) load_row(0, even);
-            if (R > 1) load_row(1, odd);
-            for (int r = 0; r < R; r += 2) {
+            if (RA > 0) load_row(0, even);
+            if (RA > 1) load_row(1, odd);
+            for (int r = 0; r < RA; r += 2) {
                 if (!convert_row(even)) break;
-                if (r + 2 < R) load_row(r + 2, even);
-                if (r + 1 >= R || !convert_row(odd)) break;
-                if (r + 3 < R) load_row(r + 3, odd);
+                if (r + 2 < RA) load_row(r + 2, even);
+                if (r + 1 >= RA || !convert_row(odd)) break;
+                if (r + 3 < RA) load_row(r + 3, odd);
             }
         } else {
-            for (int r = 0; r < R; ++r) {
+            for (int r = 0; r < RA; ++r) {
                 if (!fbc_wait(raw_full0 + 8u * rs, rph, P, abort_flag, FBC_TC_ERR_WAIT_A)) break;
                 if (!fbc_wait(a_empty0 + 8u * as, aph ^ 1, P, abort_flag, FBC_TC_ERR_WAIT_EMPTY)) break;
                 const int valid = row_valid(row_p0(r));

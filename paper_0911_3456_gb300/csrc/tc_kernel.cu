@@ -159,6 +159,7 @@ struct TcConfig {
     int sb = 0;                        // staging slots per epilogue warp (ts = 32): 1..3
     int rs = 0;                        // 1: the B ring holds the CTA's whole filter tile (resident bank)
     int cg = 0;                        // 2: CTA pairs (clusters of two, cta_group::2 MMAs, M = 256)
+    int sw = 0;                        // 1: sliding window (runs of output rows share their slab rows)
 };
 
 struct TcPlan {
@@ -195,6 +196,7 @@ std::string tc_kernel_name(int nc, int split, int fw, const TcConfig& c, const s
     if (c.ts) name += "_t" + std::to_string(c.ts) + "s" + std::to_string(c.sb);
     if (c.rs) name += "_r";
     if (c.cg) name += "_p";
+    if (c.sw) name += "_sw";
     return snippet.empty() ? name : name + "_u" + snippet_tag(snippet);
 }
 
@@ -211,7 +213,7 @@ std::string tc_kernel_source(int nc, int split, int fw, const TcConfig& c, const
       << tc_kernel_name(nc, split, fw, c, snippet) << "(const __grid_constant__ FbcTcParams P) {\n"
       << "  fbc_tc_corr_body<" << nc << "," << split << "," << fw << "," << c.bt << "," << c.ew << ","
       << c.fuse << "," << c.cw << "," << (snippet.empty() ? 0 : 1) << "," << c.ts << "," << (c.ts ? c.sb : 1)
-      << "," << c.rs << "," << (c.cg ? 1 : 0) << ">(P);\n}\n";
+      << "," << c.rs << "," << (c.cg ? 1 : 0) << "," << c.sw << ">(P);\n}\n";
     return o.str();
 }
 
@@ -293,6 +295,13 @@ bool tc_layout(TcPlan* p, const TcConfig& c, bool commit) {
     // keeps one filter tile, and there are at least as many SMs as filter tiles
     if (c.rs != 0 && (c.rs != 1 || c.nb != p->fh * ((p->fw + c.bt - 1) / c.bt) || ntn > std::max(1, p->sm_count)))
         return false;
+    // sliding window: one filter tile, whole 128-pixel column blocks per input
+    // row, single CTAs over a streamed bank, the A ring holding fh slabs, and a
+    // run of at least one output row for every CTA
+    const int sw_delta = p->W / kTileM;
+    if (c.sw != 0 && (c.sw != 1 || c.cg || c.rs || ntn != 1 || p->W % kTileM != 0 || c.na < p->fh ||
+                      p->sm_count < sw_delta))
+        return false;
     // the barrier table: a_full / a_empty per A slot, b_full / b_empty per B stage,
     // two accumulator pairs, the drain barrier, raw_full / raw_empty per raw slot,
     // and for a pair pa_full per A slot
@@ -313,7 +322,7 @@ bool tc_layout(TcPlan* p, const TcConfig& c, bool commit) {
     // of the CTAs idle, its tiles run as two 128-column halves each
     const int grid_full = std::min(mtiles * ntn, std::max(1, p->sm_count));
     const int rem = (mtiles * ntn) % grid_full;
-    const bool tail_halves = !c.rs && !c.cg && ntn == 1 && nt == 256 && rem > 0 && 2 * rem <= grid_full &&
+    const bool tail_halves = !c.rs && !c.cg && !c.sw && ntn == 1 && nt == 256 && rem > 0 && 2 * rem <= grid_full &&
                              env_str("FBCORR_TAIL_HALVES", "1") != "0";
     const bool half_planes = tail_halves || c.cg;   // B from the half-width planes
     k.nfull = tail_halves ? mtiles * ntn - rem : mtiles * ntn;
@@ -333,6 +342,7 @@ bool tc_layout(TcPlan* p, const TcConfig& c, bool commit) {
     k.wait_ns = p->wait_ns;
     k.drop_b = p->drop_b;
     k.st_off = k.bar_off + 512;
+    k.sw_delta = c.sw ? sw_delta : 0;
     p->smem = k.st_off + staging;
     // a pair's CTAs must sit on two SMs, one CTA per SM: with room for two CTAs
     // in one SM's shared memory two CTAs of different pairs could share an SM,
@@ -364,7 +374,9 @@ bool tc_layout(TcPlan* p, const TcConfig& c, bool commit) {
     p->split_blocks = (int)(sp.xblocks + wblocks);
     // one CTA per SM (the 512 TMEM columns); resident bank: a multiple of the
     // filter-tile count, each group of ntn CTAs sharing the pixel tiles
-    if (c.rs)
+    if (c.sw)   // runs of output rows: the same number of runs in every column block
+        p->grid = sw_delta * std::min(Ho, p->sm_count / sw_delta);
+    else if (c.rs)
         p->grid = ntn * std::min(mtiles, std::max(1, p->sm_count / ntn));
     else if (c.cg)   // pairs of tiles, one pair of CTAs per pair of SMs
         p->grid = 2 * std::min((mtiles + 1) / 2, std::max(1, p->sm_count / 2));
@@ -439,6 +451,23 @@ std::vector<TcConfig> tc_candidate_configs(TcPlan* p, bool pairs) {
                                     if ((c.nb = deepest(c))) out.push_back(c);
                                 }
             }
+    // sliding window (sw = 1): one 256-wide filter tile over runs of output rows,
+    // the A ring fh or fh + 1 slabs deep, raw-ring or register conversion
+    for (int fuse = 2; fuse >= 1; --fuse)
+        for (int cw : {8, 4}) {
+            if (!fuse_ok(fuse, cw, p->D, p->nc, p->fw)) continue;
+            for (int nr : fuse == 2 ? std::vector<int>{3, 2} : std::vector<int>{0})
+                for (int bt = std::min(p->fw, 5); bt >= 1; --bt)
+                    for (int ew : {8, 4})
+                        for (int na = p->fh; na <= p->fh + 1; ++na)
+                            for (int ts : {0, 32}) {
+                                TcConfig c{na, 0, 256, bt, ew, fuse, nr, cw};
+                                c.ts = ts;
+                                c.sb = ts ? 1 : 0;
+                                c.sw = 1;
+                                if ((c.nb = deepest(c))) out.push_back(c);
+                            }
+        }
     // resident bank (rs = 1): the ring holds all fh * ceil(fw / bt) stages of a
     // filter tile, loaded once per CTA; offered wherever a filter tile fits in
     // shared memory beside the A slots (plain BF16 of the headline shape: 128
@@ -476,6 +505,7 @@ std::string format_spec(const TcConfig& c) {
     if (c.ts) out += ",ts=" + std::to_string(c.ts) + ",sb=" + std::to_string(c.sb);
     if (c.rs) out += ",rs=1";
     if (c.cg) out += ",cg=2";
+    if (c.sw) out += ",sw=1";
     return out;
 }
 
@@ -499,7 +529,12 @@ bool parse_tc_spec(const std::string& s, TcConfig* c) {
         t.cg = 2;
         used += 5;
     }
+    if (s.compare(used, 5, ",sw=1") == 0) {
+        t.sw = 1;
+        used += 5;
+    }
     if (t.rs && t.cg) return false;
+    if (t.sw && (t.rs || t.cg)) return false;
     if (used != (int)s.size()) return false;
     if ((t.fuse == 0) != (t.cw == 0) || (t.cw != 0 && t.cw != 4 && t.cw != 8)) return false;
     if (t.fuse < 0 || t.fuse > 2 || (t.ew != 4 && t.ew != 8)) return false;

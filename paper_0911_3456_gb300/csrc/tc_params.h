@@ -49,6 +49,7 @@ struct FbcTcParams {
     unsigned int raw_off, raw_slot;   // raw-row ring (FUSE = 2): offset, bytes per slot
     unsigned int st_off;              // store staging (TS > 0): offset, 1024-byte aligned at run time
     int tma_y;                        // 1: ymap describes y, epilogue stores go through it
+    int sw_delta;                     // sliding window (SW = 1): pixel tiles per input row, W / 128
 };
 
 #endif

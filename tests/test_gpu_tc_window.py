@@ -1,0 +1,87 @@
+"""GPU checks of the sliding-window tensor-core kernel (spec suffix sw=1): a
+CTA walks a run of output rows of one 128-pixel column block and keeps the
+converted input rows its next tiles read, so a run of n tiles converts
+n + fh - 1 slab rows instead of n * fh.  Every tile still sums the same
+products in the same order, so the bits equal those of the single-CTA kernel
+without the window; on integer inputs they equal the oracle's."""
+import numpy as np
+import pytest
+
+import oracle
+from helpers import dev, host, torch_cuda
+from paper_0911_3456_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+WINDOW_SHAPES = [
+    # W a multiple of 128, one filter tile: runs of one row (W = 128, 37 output
+    # rows), runs of 1-2 rows over two column blocks, runs of 7-8 rows over four,
+    # 7x7 filters over three column blocks (a ring of 7 or 8 slabs), 1x1 filters
+    (41, 128, 32, 256, 5, 5),
+    (100, 256, 16, 96, 3, 3),
+    (300, 512, 32, 256, 5, 5),
+    (200, 384, 8, 250, 7, 7),
+    (64, 128, 64, 128, 1, 1),
+]
+
+
+def _plain_variant(spec, p, C):
+    """The same configuration without the window (two A slots where its ring
+    does not fit), else the first candidate without it."""
+    base = spec.replace(",sw=1", "")
+    na = base.split("na=")[1].split(",")[0]
+    cands = [base, base.replace("na=" + na + ",", "na=2,", 1)]
+    cands += [s for s in p.candidates() if ",sw=1" not in s and ",cg=2" not in s][:1]
+    for cand in cands:
+        try:
+            p.set_variant(cand)
+            return cand
+        except C.FbcorrError:
+            continue
+    return None
+
+
+@pytest.mark.parametrize("mode", ["bf16", "bf16x3"])
+@pytest.mark.parametrize("shape", WINDOW_SHAPES, ids=lambda s: "x".join(map(str, s)))
+def test_sliding_window_bit_exact(mode, shape):
+    torch = torch_cuda()
+    from paper_0911_3456_gb300 import _capi as C
+    from paper_0911_3456_gb300.api import Plan
+    H, W, D, N, fh, fw = shape
+    clamp = (-0.5, 0.75) if fh == 3 else None
+    p = Plan((H, W, D), (N, fh, fw, D), mode, clamp)
+    windows = [s for s in p.candidates() if s.endswith(",sw=1")]
+    assert windows, "a single filter tile over whole 128-pixel column blocks offers the window"
+    # one configuration per (conversion, store path, ring depth)
+    picked = {}
+    for s in windows:
+        key = (s.split(",fz=")[1][0], ",ts=" in s, s.split("na=")[1].split(",")[0])
+        picked.setdefault(key, s)
+    for spec in picked.values():
+        for kind in ("int", "real"):
+            wl = inputs.random_case(2300, *shape, kind=kind)
+            x, w = dev(wl.x, torch), dev(wl.w, torch)
+            p.set_variant(spec)
+            y_win = host(p.forward(x, w))
+            assert p.device_status() == 0, spec
+            plain = _plain_variant(spec, p, C)
+            assert plain is not None, spec
+            y_plain = host(p.forward(x, w))
+            assert np.array_equal(y_win, y_plain), (spec, plain)
+            if kind == "int":
+                assert np.array_equal(y_win, oracle.fwd(wl.x, wl.w, epilogue=clamp)), spec
+
+
+def test_sliding_window_refused_where_it_does_not_apply():
+    """Widths that are not whole 128-pixel column blocks, and banks of more
+    than one filter tile, offer no window and refuse a window spec."""
+    torch_cuda()
+    from paper_0911_3456_gb300 import _capi as C
+    from paper_0911_3456_gb300.api import Plan
+    spec = "tcgen05:na=6,nb=3,nt=256,bt=2,ew=4,fz=2,nr=3,cw=8,ts=32,sb=1,sw=1"
+    for shape in [(40, 200, 32, 256, 5, 5), (40, 256, 32, 300, 5, 5)]:
+        H, W, D, N, fh, fw = shape
+        p = Plan((H, W, D), (N, fh, fw, D), "bf16")
+        assert not any(s.endswith(",sw=1") for s in p.candidates())
+        with pytest.raises(C.FbcorrError):
+            p.set_variant(spec)
