@@ -169,7 +169,7 @@ class Plan:
 
     def candidates(self):
         """The forward variants the auto-tuner times for this plan (spec strings)."""
-        buf = ctypes.create_string_buffer(1 << 16)
+        buf = ctypes.create_string_buffer(1 << 18)
         C.call("fbcorr_plan_candidates", self._h, buf, len(buf))
         return [s for s in buf.value.decode().split("\n") if s]
 

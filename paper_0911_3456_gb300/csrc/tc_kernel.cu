@@ -452,22 +452,25 @@ std::vector<TcConfig> tc_candidate_configs(TcPlan* p, bool pairs) {
                                 }
             }
     // sliding window (sw = 1): one 256-wide filter tile over runs of output rows,
-    // the A ring fh or fh + 1 slabs deep, raw-ring or register conversion
-    for (int fuse = 2; fuse >= 1; --fuse)
-        for (int cw : {8, 4}) {
-            if (!fuse_ok(fuse, cw, p->D, p->nc, p->fw)) continue;
-            for (int nr : fuse == 2 ? std::vector<int>{3, 2} : std::vector<int>{0})
-                for (int bt = std::min(p->fw, 5); bt >= 1; --bt)
-                    for (int ew : {8, 4})
-                        for (int na = p->fh; na <= p->fh + 1; ++na)
-                            for (int ts : {0, 32}) {
-                                TcConfig c{na, 0, 256, bt, ew, fuse, nr, cw};
-                                c.ts = ts;
-                                c.sb = ts ? 1 : 0;
-                                c.sw = 1;
-                                if ((c.nb = deepest(c))) out.push_back(c);
-                            }
+    // the A ring fh or fh + 1 slabs deep, raw-ring or register conversion by 8
+    // warps, tiled stores where they apply (direct stores otherwise)
+    {
+        const int ts = ts_ok(32, 1, p->W, p->N, 256) ? 32 : 0;
+        for (int fuse = 2; fuse >= 1; --fuse) {
+            if (!fuse_ok(fuse, 8, p->D, p->nc, p->fw)) continue;
+            for (int bt : {5, 3, 2, 1}) {
+                if (bt > p->fw) continue;
+                for (int ew : {4, 8})
+                    for (int na = p->fh; na <= p->fh + 1; ++na) {
+                        TcConfig c{na, 0, 256, bt, ew, fuse, fuse == 2 ? 3 : 0, 8};
+                        c.ts = ts;
+                        c.sb = ts ? 1 : 0;
+                        c.sw = 1;
+                        if ((c.nb = deepest(c))) out.push_back(c);
+                    }
+            }
         }
+    }
     // resident bank (rs = 1): the ring holds all fh * ceil(fw / bt) stages of a
     // filter tile, loaded once per CTA; offered wherever a filter tile fits in
     // shared memory beside the A slots (plain BF16 of the headline shape: 128

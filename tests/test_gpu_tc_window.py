@@ -51,6 +51,11 @@ def test_sliding_window_bit_exact(mode, shape):
     clamp = (-0.5, 0.75) if fh == 3 else None
     p = Plan((H, W, D), (N, fh, fw, D), mode, clamp)
     windows = [s for s in p.candidates() if s.endswith(",sw=1")]
+    if not windows and mode == "bf16x3" and D == 64:
+        # split slabs of 8 chunk planes (35 KB each) plus a raw-row ring and two
+        # B stages exceed an SM's shared memory, and register conversion takes
+        # at most 4 planes
+        pytest.skip("no window configuration fits in shared memory")
     assert windows, "a single filter tile over whole 128-pixel column blocks offers the window"
     # one configuration per (conversion, store path, ring depth)
     picked = {}
