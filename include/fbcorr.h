@@ -25,6 +25,13 @@
  *  - forward / backward / forward_batched are stream-ordered, never
  *    synchronise the host, and allocate no memory: scratch space is the
  *    caller's workspace (size from the *_workspace_size queries).
+ *  - The generated FP32 kernels (forward and dL/dx) are launched as
+ *    programmatic dependents: each waits (griddepcontrol.wait) for the
+ *    previous kernel of the stream to complete before touching memory, then
+ *    lets the next kernel begin launching.  A kernel the caller launches after
+ *    them with programmatic stream serialization must likewise wait
+ *    (cudaGridDependencySynchronize) before it reads their outputs; kernels
+ *    launched without that attribute see ordinary stream order.
  *  - Kernels are specialised per (fh, fw, D, tile) at plan time by run-time
  *    code generation (NVRTC, cached on disk) -- the paper's RTCG approach
  *    (Sec. 4, Sec. 6.2) -- with a prebuilt generic "default" kernel when
