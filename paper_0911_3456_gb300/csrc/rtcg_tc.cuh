@@ -92,7 +92,9 @@
 // Tail halves: tiles t >= nfull, the last partial round of a single 256-wide
 // filter tile, run as two 128-column work items each (instruction N = 128, B
 // from half-width planes), so that round keeps twice as many SMs busy for half
-// as long.
+// as long.  A pair does the same with its pairs of tiles w >= nfull: M = 256,
+// N = 128, each CTA staging a quarter of the bank (64 filters) from the
+// quarter-width planes.
 //
 // Every mbarrier wait is bounded in time (%globaltimer); on expiry the kernel
 // records an error code in host-mapped memory, stops every role, waits (again
@@ -216,7 +218,8 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
     const int res_fi = RES ? (int)blockIdx.x % P.ntn : 0;
     const int unit = RES ? (int)blockIdx.x / P.ntn : PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
     const int nunits = RES ? (int)gridDim.x / P.ntn : PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
-    const int nwork = RES ? P.mtiles : PAIR ? (P.mtiles + 1) >> 1 : P.nfull + 2 * (nsched - P.nfull);
+    const int npairs = (P.mtiles + 1) >> 1;
+    const int nwork = RES ? P.mtiles : PAIR ? P.nfull + 2 * (npairs - P.nfull) : P.nfull + 2 * (nsched - P.nfull);
     const int sw_runs = SW ? (int)gridDim.x / P.sw_delta : 1;
     const int sw_u = SW ? (int)blockIdx.x / P.sw_delta : 0;
     const int sw_t0 = SW ? (int)((long long)sw_u * P.Ho / sw_runs) * P.sw_delta + (int)blockIdx.x % P.sw_delta : 0;
@@ -228,12 +231,14 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
         int nt;      // filter columns of this item (the MMA's N)
         int bn;      // filter rows of B this CTA stages (a pair: nt / 2)
         int n0;      // first filter
-        long long wbase;   // byte offset of the item's planes in whi / wlo (half: in whi2 / wlo2)
+        long long wbase;   // byte offset of the item's planes in whi / wlo (half: whi2 / wlo2; quarter: whi4 / wlo4)
         bool half;   // B from the half-width planes
+        bool quarter;   // B from the quarter-width planes (a pair's tail half)
     };
     auto item_of = [&](int k) -> Item {
         const int w = unit + k * nunits;
         Item it;
+        it.quarter = false;
         if (SW) {
             it.half = false;
             it.tile = sw_t0 + k * P.sw_delta;
@@ -245,11 +250,22 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
         }
         if (PAIR) {
             it.half = true;
-            it.tile = 2 * w + (int)rank;
-            it.nt = P.nt;
-            it.bn = P.nt >> 1;
-            it.n0 = 0;
-            it.wbase = (long long)rank * P.fh * FW * NC * it.bn * 16;
+            if (w < P.nfull) {
+                it.tile = 2 * w + (int)rank;
+                it.nt = P.nt;
+                it.bn = P.nt >> 1;
+                it.n0 = 0;
+                it.wbase = (long long)rank * P.fh * FW * NC * it.bn * 16;
+            } else {
+                // tail half h of pair pw: filters h * 128 .., this CTA's quarter 2h + rank
+                const int h = (w - P.nfull) & 1;
+                it.quarter = true;
+                it.tile = 2 * (P.nfull + ((w - P.nfull) >> 1)) + (int)rank;
+                it.nt = P.nt >> 1;
+                it.bn = P.nt >> 2;
+                it.n0 = h * it.nt;
+                it.wbase = (long long)(2 * h + (int)rank) * P.fh * FW * NC * it.bn * 16;
+            }
             return it;
         }
         it.half = !RES && w >= P.nfull;
@@ -336,8 +352,8 @@ __device__ __forceinline__ void fbc_tc_corr_body(const FbcTcParams& P) {
                 const Item it = item_of(r / P.fh);
                 const long long tap_bytes = (long long)NC * it.bn * 16;   // = the item's b_half
                 const long long woff = it.wbase + (long long)((r % P.fh) * FW) * tap_bytes;
-                const fbc_u8* wtap_hi = (it.half ? P.whi2 : P.whi) + woff;
-                const fbc_u8* wtap_lo = (it.half ? P.wlo2 : P.wlo) + woff;
+                const fbc_u8* wtap_hi = (it.quarter ? P.whi4 : it.half ? P.whi2 : P.whi) + woff;
+                const fbc_u8* wtap_lo = (it.quarter ? P.wlo4 : it.half ? P.wlo2 : P.wlo) + woff;
                 const fbc_u32 b_half = (fbc_u32)tap_bytes;
 #pragma unroll
                 for (int s = 0; s < NST; ++s) {

@@ -54,8 +54,10 @@ struct SplitParams {
     uint8_t* wlo;
     uint8_t* whi2;   // half-width planes of the tail halves (halves != 0)
     uint8_t* wlo2;
+    uint8_t* whi4;   // quarter-width planes of a pair's tail halves (quarters != 0)
+    uint8_t* wlo4;
     long long npix, npix_pad;
-    int D, nc, N, fh, fw, nt, ntn, split, halves;
+    int D, nc, N, fh, fw, nt, ntn, split, halves, quarters;
     long long xblocks;
 };
 
@@ -140,6 +142,13 @@ __global__ void __launch_bounds__(256) fbc_tc_split(const __grid_constant__ Spli
                 const long long idx2 = (((long long)h * taps + tap) * S.nc + c) * hn + (nl - h * hn);
                 split8(v, reinterpret_cast<uint4*>(S.whi2) + idx2, reinterpret_cast<uint4*>(S.wlo2) + idx2, S.split);
             }
+            if (S.quarters) {
+                // and in the quarter-width planes [4][taps][nc][nt/4] (a pair's tail halves)
+                const int qn = S.nt >> 2;
+                const int q = nl / qn;
+                const long long idx4 = (((long long)q * taps + tap) * S.nc + c) * qn + (nl - q * qn);
+                split8(v, reinterpret_cast<uint4*>(S.whi4) + idx4, reinterpret_cast<uint4*>(S.wlo4) + idx4, S.split);
+            }
         }
     }
 }
@@ -168,7 +177,7 @@ struct TcPlan {
     TcConfig cfg;
     size_t smem = 0;
     size_t ws_bytes = 0;  // the largest any candidate configuration needs
-    size_t off_xhi = 0, off_xlo = 0, off_whi = 0, off_wlo = 0, off_whi2 = 0, off_wlo2 = 0;
+    size_t off_xhi = 0, off_xlo = 0, off_whi = 0, off_wlo = 0, off_whi2 = 0, off_wlo2 = 0, off_whi4 = 0, off_wlo4 = 0;
     size_t ws_end = 0;    // workspace bytes this configuration uses
     int grid = 0;
     int split_blocks = 0;
@@ -326,6 +335,13 @@ bool tc_layout(TcPlan* p, const TcConfig& c, bool commit) {
                              env_str("FBCORR_TAIL_HALVES", "1") != "0";
     const bool half_planes = tail_halves || c.cg;   // B from the half-width planes
     k.nfull = tail_halves ? mtiles * ntn - rem : mtiles * ntn;
+    // a pair's tail halves: the same rule over pairs of tiles and pairs of SMs;
+    // nfull then counts pairs run whole
+    const int npairs = (mtiles + 1) / 2;
+    const int grid_pairs = std::min(npairs, std::max(1, p->sm_count / 2));
+    const int prem = npairs % grid_pairs;
+    const bool pair_tail = c.cg && prem > 0 && 2 * prem <= grid_pairs && env_str("FBCORR_TAIL_HALVES", "1") != "0";
+    if (c.cg) k.nfull = pair_tail ? npairs - prem : npairs;
     k.lp = lp; k.na = c.na; k.nb = c.nb;
     k.a_slot = a_slot; k.b_stage = b_stage;
     k.a_tx = (uint32_t)(nc * (kTileM + p->fw - 1) * 16 * halves);
@@ -359,6 +375,8 @@ bool tc_layout(TcPlan* p, const TcConfig& c, bool commit) {
     p->off_wlo = off; if (p->split) off = align_up(off + wplanes, 256);
     p->off_whi2 = off; if (half_planes) off = align_up(off + wplanes, 256);
     p->off_wlo2 = off; if (half_planes && p->split) off = align_up(off + wplanes, 256);
+    p->off_whi4 = off; if (pair_tail) off = align_up(off + wplanes, 256);
+    p->off_wlo4 = off; if (pair_tail && p->split) off = align_up(off + wplanes, 256);
     p->ws_end = off;
 
     SplitParams& sp = p->sp;
@@ -368,6 +386,7 @@ bool tc_layout(TcPlan* p, const TcConfig& c, bool commit) {
     sp.D = p->D; sp.nc = nc; sp.N = p->N; sp.fh = p->fh; sp.fw = p->fw; sp.nt = nt; sp.ntn = ntn;
     sp.split = p->split;
     sp.halves = half_planes ? 1 : 0;
+    sp.quarters = pair_tail ? 1 : 0;
     sp.xblocks = (k.npix_pad + 255) / 256;
     const long long wblocks = ((long long)ntn * p->fh * p->fw * nt + 255) / 256;
     if (c.fuse) sp.xblocks = 0;   // x is converted inside the correlation kernel
@@ -644,7 +663,9 @@ std::string tc_describe(const TcPlan* p) {
     o << "{\"precision\":\"" << (p->split ? "bf16x3" : "bf16") << "\",\"mma\":\""
       << (p->cfg.cg ? "256x" : "128x") << p->kp.nt << "x16" << (p->cfg.cg ? " (CTA pair)" : "")
       << "\",\"filter_tiles\":" << p->kp.ntn << ",\"tiles\":" << p->kp.mtiles * p->kp.ntn
-      << ",\"tail_half_tiles\":" << (p->kp.mtiles * p->kp.ntn - std::min(p->kp.nfull, p->kp.mtiles * p->kp.ntn))
+      << ",\"tail_half_tiles\":"
+      << (p->cfg.cg ? 2 * ((p->kp.mtiles + 1) / 2 - p->kp.nfull)
+                    : p->kp.mtiles * p->kp.ntn - std::min(p->kp.nfull, p->kp.mtiles * p->kp.ntn))
       << ",\"smem\":" << p->smem << ",\"grid\":" << p->grid << ",\"threads\":" << tc_threads(p->cfg)
       << ",\"kernel\":\"" << tc_kernel_name(p->nc, p->split, p->fw, p->cfg, p->snippet) << "\"";
     auto it = p->kernels.find(tc_kernel_name(p->nc, p->split, p->fw, p->cfg, p->snippet));
@@ -668,6 +689,8 @@ fbcorr_status_t tc_forward(TcPlan* p, const float* x, const float* w, float* y, 
     sp.wlo = base + p->off_wlo;
     sp.whi2 = base + p->off_whi2;
     sp.wlo2 = base + p->off_wlo2;
+    sp.whi4 = base + p->off_whi4;
+    sp.wlo4 = base + p->off_wlo4;
     // timing events bracket both launches of the step: an event between them
     // would hold the correlation kernel back until the split has finished
     if (ev_start) FBC_CUDA(cudaEventRecord(ev_start, s));
@@ -680,6 +703,8 @@ fbcorr_status_t tc_forward(TcPlan* p, const float* x, const float* w, float* y, 
     kp.wlo = sp.wlo;
     kp.whi2 = sp.whi2;
     kp.wlo2 = sp.wlo2;
+    kp.whi4 = sp.whi4;
+    kp.wlo4 = sp.wlo4;
     kp.y = y;
     kp.err = err_word;
     kp.xraw = x;

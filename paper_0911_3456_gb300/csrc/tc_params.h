@@ -27,6 +27,8 @@ struct FbcTcParams {
     const unsigned char* wlo;
     const unsigned char* whi2;  // tail halves (nt = 256, ntn = 1): [2][fh*fw][nc][128][16 B]
     const unsigned char* wlo2;
+    const unsigned char* whi4;  // a pair's tail halves: quarter-width planes [4][fh*fw][nc][64][16 B]
+    const unsigned char* wlo4;
     float* y;                   // [Ho][Wo][N]
     int* err;                   // host-mapped error word
     const float* xraw;          // x itself [H*W][D] (fused: read by the converter warps)
@@ -35,7 +37,8 @@ struct FbcTcParams {
     unsigned long long wait_ns; // bound of every mbarrier wait
     int W, Ho, Wo, N, D;
     int fh, nt, ntn, mtiles;
-    int nfull;                  // tiles run whole; tiles nfull.. run as two halves of the filter tile
+    int nfull;                  // tiles (a pair: pairs of tiles) run whole; the rest run as two
+                                // halves of the filter tile
     int lp;                     // pixels per chunk plane of an A slot
     int na, nb;                 // A slots, B stages
     int alook;                  // rows by which the A side (slabs or raw rows) runs ahead of the B stages

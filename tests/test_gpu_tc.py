@@ -442,3 +442,48 @@ def test_cta_pair_bit_exact(mode, shape):
             assert np.array_equal(y_pair, y_one), (spec, single)
             if kind == "int":
                 assert np.array_equal(y_pair, oracle.fwd(wl.x, wl.w, epilogue=clamp)), spec
+
+
+@pytest.mark.parametrize("mode", ["bf16", "bf16x3"])
+@pytest.mark.parametrize("shape", [(196, 128, 32, 256, 5, 5), (195, 128, 16, 250, 3, 3)],
+                         ids=lambda s: "x".join(map(str, s)))
+def test_cta_pair_tail_halves_bit_exact(mode, shape, monkeypatch):
+    """96 pairs of tiles on 76 pairs of SMs: the last 20 pairs run as two
+    M = 256, N = 128 work items each, every CTA staging a quarter of the bank
+    from the quarter-width planes.  Per output the same products in the same
+    order: the bits of the pair kernel without tail halves and of the
+    single-CTA kernel, and on integer inputs the oracle's.  The second shape
+    has an odd tile count, so the odd CTA of the last (split) pair holds a
+    tile past the image."""
+    torch = torch_cuda()
+    from paper_0911_3456_gb300 import _capi as C
+    from paper_0911_3456_gb300.api import Plan
+    H, W, D, N, fh, fw = shape
+    p = Plan((H, W, D), (N, fh, fw, D), mode)
+    pairs = [s for s in p.candidates() if s.endswith(",cg=2")]
+    assert pairs
+    spec = pairs[0]
+    for kind in ("int", "real"):
+        wl = inputs.random_case(2400, *shape, kind=kind)
+        x, w = dev(wl.x, torch), dev(wl.w, torch)
+        monkeypatch.setenv("FBCORR_TAIL_HALVES", "1")
+        p.set_variant(spec)
+        det = p.info()["fwd"]["detail"]
+        sms = p.info().get("sm_count", 152)
+        npairs = (det["tiles"] + 1) // 2
+        rem = npairs % (sms // 2)
+        expect_tail = npairs > sms // 2 and 0 < rem and 2 * rem <= sms // 2
+        assert det["tail_half_tiles"] == (2 * rem if expect_tail else 0), det
+        y_tail = host(p.forward(x, w))
+        assert p.device_status() == 0, spec
+        monkeypatch.setenv("FBCORR_TAIL_HALVES", "0")
+        p.set_variant(spec)
+        assert p.info()["fwd"]["detail"]["tail_half_tiles"] == 0
+        y_whole = host(p.forward(x, w))
+        assert np.array_equal(y_tail, y_whole), spec
+        single = _single_cta(spec, p, C)
+        assert single is not None, spec
+        y_one = host(p.forward(x, w))
+        assert np.array_equal(y_tail, y_one), (spec, single)
+        if kind == "int":
+            assert np.array_equal(y_tail, oracle.fwd(wl.x, wl.w)), spec
