@@ -88,9 +88,14 @@ std::string batch_source(const fbcorr_batch_plan* b) {
     for (size_t v = 0; v < b->variants.size(); ++v) {
         const BatchVariant& bv = b->variants[v];
         const DirectTile& t = bv.tile;
-        o << "typedef FbcDirect<" << bv.fh << "," << bv.fw << "," << bv.d << "," << t.tr << "," << t.tf
-          << "," << t.wr << "," << t.wf << ",0," << epi << ",0," << t.chunk(bv.d) << "," << t.pk << "> FbcV" << v
-          << ";\n";
+        if (t.ks > 1)   // the K-split tile (short reductions: lanes split the depth)
+            o << "typedef FbcDirectKS<" << bv.fh << "," << bv.fw << "," << bv.d << "," << t.tr << "," << t.tf << ","
+              << t.ks << "," << t.wq << "," << t.wr << "," << t.wf << "," << epi << "," << t.pk << "," << t.sh
+              << "> FbcV" << v << ";\n";
+        else
+            o << "typedef FbcDirect<" << bv.fh << "," << bv.fw << "," << bv.d << "," << t.tr << "," << t.tf
+              << "," << t.wr << "," << t.wf << ",0," << epi << ",0," << t.chunk(bv.d) << "," << t.pk << "> FbcV"
+              << v << ";\n";
         // one non-inlined function per variant: each gets its own register
         // allocation instead of the maximum over every variant of the switch
         o << "__device__ __noinline__ void fbc_run_v" << v
@@ -197,7 +202,18 @@ fbcorr_status_t select_variants(fbcorr_batch_plan* b, bool allow_tuning) {
         std::string spec;
         DirectTile t;
         bool have = false;
-        if (tune && (at == "force" || !tune_lookup(key, &spec))) {
+        if (env_str("FBCORR_BATCH_KS", "0") == "1") {
+            // tests and profiling: the model's first K-split tile wherever one fits
+            // (the tuner itself is offered them only with FBCORR_TUNE_KS_BATCH=1)
+            for (const auto& c : direct_ranked(rep, kBatchSmemLimit, b->dev.sm_count, kBatchThreads, kBatchMaxBlock))
+                if (c.ks > 1 && !c.ks_chunked()) {
+                    t = c;
+                    t.pk = 1;
+                    have = true;
+                    break;
+                }
+        }
+        if (!have && tune && (at == "force" || !tune_lookup(key, &spec))) {
             float ms = 0.f;
             if (tune_direct_problem(b->dev, rep, nullptr, kBatchThreads, kBatchMaxBlock, kBatchSmemLimit,
                                     topk, false, "batch", &spec, &ms) == FBCORR_OK &&
@@ -207,11 +223,11 @@ fbcorr_status_t select_variants(fbcorr_batch_plan* b, bool allow_tuning) {
             }
         }
         if (!have && tune_lookup(key, &spec) && parse_direct_spec(spec, &t) &&
-            t.threads() == kBatchThreads && t.ks == 1 && t.tr * t.tf <= kBatchMaxBlock &&
+            t.threads() == kBatchThreads && !t.ks_chunked() && t.tr * t.tf <= kBatchMaxBlock &&
             direct_smem_bytes(t, bv.fh, bv.fw, bv.d) <= kBatchSmemLimit)
             have = true;
         if (!have) t = direct_heuristic(rep, kBatchSmemLimit, b->dev.sm_count, kBatchThreads, kBatchMaxBlock);
-        if (t.threads() != kBatchThreads || t.ks != 1 || direct_smem_bytes(t, bv.fh, bv.fw, bv.d) > kBatchSmemLimit)
+        if (t.threads() != kBatchThreads || t.ks_chunked() || direct_smem_bytes(t, bv.fh, bv.fw, bv.d) > kBatchSmemLimit)
             return set_error(FBCORR_ERR_UNSUPPORTED, "no batched tile fits filter %dx%d at depth %d", bv.fh,
                              bv.fw, bv.d);
         bv.tile = t;
@@ -249,8 +265,8 @@ fbcorr_status_t build(fbcorr_batch_plan* b) {
         const int Ho = (int)(s[0] - s[4] + 1), Wo = (int)(s[1] - s[5] + 1), N = (int)s[3];
         const BatchVariant& bv = b->variants[b->var_of[k]];
         const DirectTile& t = bv.tile;
-        const int gx = (Wo + 31) / 32, gy = (Ho + t.bh() - 1) / t.bh(), gz = (N + t.bn() - 1) / t.bn();
-        const long long cost = (long long)t.bh() * 32 * t.bn() * bv.fh * bv.fw * bv.d;
+        const int gx = (Wo + t.bw() - 1) / t.bw(), gy = (Ho + t.bh() - 1) / t.bh(), gz = (N + t.bn() - 1) / t.bn();
+        const long long cost = (long long)t.bh() * t.bw() * t.bn() * bv.fh * bv.fw * bv.d;
         for (int z = 0; z < gz; ++z)
             for (int y = 0; y < gy; ++y)
                 for (int x = 0; x < gx; ++x) items.push_back(Item{cost, make_int4(k, x, y, z)});

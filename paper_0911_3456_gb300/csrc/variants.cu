@@ -261,8 +261,8 @@ std::vector<DirectTile> direct_candidates(const DirectProblem& pr, size_t smem_l
     // ks lanes per output split the depth, at most a quarter of them on zero
     // padding channels and at most 8 channels per lane (deeper inputs keep the
     // lane-per-column tile busy enough)
-    if (threads > 0) return out;
-    if (ks_chunked_fits(pr)) {
+    if (threads > 0 && (pr.flip || pr.mask)) return out;
+    if (threads == 0 && ks_chunked_fits(pr)) {
         // chunked K-split tiles for dL/dx: chunks of cc = ks or 2 ks channels
         for (int ks : {4, 8})
             for (int cpl : {1, 2})
@@ -287,6 +287,12 @@ std::vector<DirectTile> direct_candidates(const DirectProblem& pr, size_t smem_l
         return out;
     }
     if (pr.flip || pr.mask) return out;
+    // K-split tiles inside the batched kernel: offered to its tuner only with
+    // FBCORR_TUNE_KS_BATCH=1 (measured on the 64-image batch: picked for 6 of 37
+    // variants by their single-image timings, the batch 7.98 against 7.95 ms;
+    // FBCORR_BATCH_KS=1, for tests and profiling, forces them)
+    if (threads > 0 && env_str("FBCORR_TUNE_KS_BATCH", "0") != "1" && env_str("FBCORR_BATCH_KS", "0") != "1")
+        return out;
     for (int ks : {4, 8, 16, 32}) {
         const int cpad = (pr.c + ks - 1) / ks * ks;
         if (4 * (cpad - pr.c) > cpad || cpad / ks > 8) continue;
@@ -301,6 +307,7 @@ std::vector<DirectTile> direct_candidates(const DirectProblem& pr, size_t smem_l
                                 t.wq = wq;
                                 t.sh = sh;
                                 if ((tr * tf / 2) % ks != 0 || t.threads() > 512 || t.threads() < 64) continue;
+                                if (threads > 0 && t.threads() != threads) continue;   // the batch's CTA size
                                 if (tf > nf4 || (t.bn() > nf4 && wf > 1)) continue;
                                 if (tr * tf > max_block || tr + pr.fh - 1 > 40) continue;
                                 if (t.bw() > ((pr.out_w + 7) / 8) * 8 + 8 && wq > 1) continue;
@@ -452,8 +459,11 @@ DirectTile direct_heuristic(const DirectProblem& pr, size_t smem_limit, int sm_c
                             int max_block) {
     auto r = direct_ranked(pr, smem_limit, sm_count, threads, max_block);
     // the model does not rate the chunked K-split tile against the others (its
-    // score is on another scale): only the tuner's measurements choose it
-    r.erase(std::remove_if(r.begin(), r.end(), [](const DirectTile& c) { return c.ks_chunked(); }), r.end());
+    // score is on another scale): only the tuner's measurements choose it;
+    // likewise the K-split tile inside the batched kernel
+    r.erase(std::remove_if(r.begin(), r.end(),
+                           [threads](const DirectTile& c) { return c.ks_chunked() || (threads > 0 && c.ks > 1); }),
+            r.end());
     DirectTile t = !r.empty() ? r.front() : (threads == 256 ? DirectTile{4, 4, 2, 4, 4} : DirectTile{4, 4, 1, 1, 4});
     // packed-pair FMAs: the same bits, and faster on most tiles measured on a
     // GB300 (median 0.91-0.93 of the scalar time across the top 48 tiles)

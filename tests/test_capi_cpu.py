@@ -259,9 +259,12 @@ def test_nvrtc_fault_injection_reports_nvrtc_error():
     assert r.stdout.strip().splitlines()[-1] == "7", r.stderr
 
 
-def test_batch_kernel_source_compiles(lib):
+@pytest.mark.parametrize("ks", ["0", "1"])
+def test_batch_kernel_source_compiles(lib, ks, monkeypatch):
     """The single persistent kernel of a batch plan (several filter sizes and
-    depths in one switch) compiles for sm_103a."""
+    depths in one switch) compiles for sm_103a, also with K-split tiles in the
+    variants that take one (FBCORR_BATCH_KS=1)."""
+    monkeypatch.setenv("FBCORR_BATCH_KS", ks)
     shapes = [(40, 70, 8, 16, 3, 3), (33, 45, 4, 32, 5, 5), (20, 150, 32, 64, 11, 11),
               (17, 19, 3, 5, 2, 4)]
     n = len(shapes)

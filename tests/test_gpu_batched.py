@@ -115,3 +115,32 @@ def test_batched_bad_arguments():
     fls = (ctypes.c_int64 * 4)(1, 3, 3, 2)
     assert lib.fbcorr_batch_plan_create(ctypes.byref(h), 0, ins, fls, 0, C.epilogue()) == 1
     assert lib.fbcorr_batch_plan_create(ctypes.byref(h), 1, ins, fls, 1, C.epilogue()) == 3  # BF16
+
+
+@pytest.mark.parametrize("clamp", [None, (0.0, 1.5)])
+def test_batched_ksplit_variants(clamp, monkeypatch):
+    """Batch variants may run the K-split tile (lanes of a group split the
+    depth of a short reduction and combine their sums by warp shuffles) inside
+    the persistent kernel; FBCORR_BATCH_KS=1 gives every variant that takes one
+    its first K-split tile.  Every image against the oracle (integer data:
+    exactly), including 4- and 3-channel images, ragged columns and the clamp."""
+    torch = torch_cuda()
+    from paper_0911_3456_gb300.api import BatchPlan
+    monkeypatch.setenv("FBCORR_BATCH_KS", "1")
+    shapes = [(40, 70, 8, 16, 3, 3), (33, 45, 4, 32, 5, 5), (64, 64, 16, 20, 7, 7), (12, 12, 8, 16, 3, 3),
+              (37, 29, 4, 16, 9, 9), (17, 19, 3, 5, 2, 4), (70, 90, 8, 64, 5, 5)]
+    for kind in ("int", "real"):
+        items = _batch(2500, shapes, kind=kind)
+        bp = BatchPlan([it.x.shape for it in items], [it.w.shape for it in items], clamp=clamp)
+        specs = [v["spec"] for v in bp.info()["variants"]]
+        assert sum(",ks=" in s for s in specs) >= 3, specs
+        xs = [dev(it.x, torch) for it in items]
+        ws = [dev(it.w, torch) for it in items]
+        ys = bp.forward(xs, ws)
+        torch.cuda.synchronize()
+        for it, y in zip(items, ys):
+            ref = oracle.fwd(it.x, it.w, epilogue=clamp)
+            if kind == "int":
+                assert np.array_equal(host(y), ref), it.name
+            else:
+                assert normwise_rel(host(y), ref) <= 1e-5, it.name
