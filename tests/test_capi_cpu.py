@@ -214,6 +214,8 @@ def test_chunked_ksplit_dx_tiles_compile(lib, shape, clamp, spec, expect):
     (16, 3, b"tcgen05:na=3,nb=3,nt=256,bt=3,ew=8,fz=2,nr=2,cw=8,ts=1,sb=1,rs=1"),   # resident, staged stores
     (32, 5, b"tcgen05:na=2,nb=8,nt=256,bt=1,ew=4,fz=1,nr=0,cw=8,ts=32,sb=1,cg=2"),  # CTA pair, tiled stores
     (32, 5, b"tcgen05:na=3,nb=6,nt=256,bt=3,ew=8,fz=2,nr=3,cw=8,cg=2"),             # CTA pair, raw-row ring
+    (32, 5, b"tcgen05:na=6,nb=3,nt=256,bt=2,ew=4,fz=2,nr=3,cw=8,ts=32,sb=1,sw=1"),  # sliding window, raw ring
+    (16, 7, b"tcgen05:na=7,nb=3,nt=256,bt=3,ew=8,fz=1,nr=0,cw=8,sw=1"),             # sliding window, registers
     (16, 3, b"tcgen05:na=3,nb=4,nt=256,bt=2,ew=8,fz=0,nr=0,cw=0,ts=1,sb=1,cg=2"),   # CTA pair, pre-pass, staged
 ])
 def test_tensor_core_kernels_compile(lib, D, f, spec):
@@ -242,6 +244,10 @@ def test_tensor_core_kernels_compile(lib, D, f, spec):
     (32, 5, b"tcgen05:na=2,nb=5,nt=256,bt=5,ew=4,fz=1,nr=0,cw=8,cg=1", 1),          # cg=2 only
     (32, 5, b"tcgen05:na=2,nb=5,nt=256,bt=5,ew=4,fz=1,nr=0,cw=8,cg=2,rs=1", 1),     # rs before cg
     (32, 5, b"tcgen05:na=2,nb=5,nt=256,bt=5,ew=4,fz=1,nr=0,cw=8,rs=1,cg=2", 1),     # a pair streams the bank
+    (32, 5, b"tcgen05:na=6,nb=3,nt=256,bt=2,ew=4,fz=1,nr=0,cw=8,sw=2", 1),          # sw=1 only
+    (32, 5, b"tcgen05:na=6,nb=3,nt=256,bt=2,ew=4,fz=1,nr=0,cw=8,cg=2,sw=1", 1),     # the window runs single CTAs
+    (32, 5, b"tcgen05:na=6,nb=3,nt=128,bt=2,ew=4,fz=1,nr=0,cw=8,rs=1,sw=1", 1),     # and a streamed bank
+    (32, 5, b"tcgen05:na=6,nb=3,nt=256,bt=2,ew=4,fz=1,nr=0,cw=8,sw=1,ts=1,sb=1", 1),   # stores before sw
 ])
 def test_tensor_core_spec_refusals(lib, D, f, spec, status):
     log = ctypes.create_string_buffer(1 << 16)
