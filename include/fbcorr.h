@@ -163,8 +163,10 @@ fbcorr_status_t fbcorr_forward_host(fbcorr_plan_t plan, const float* x_host, con
  *   dw[n][i][j][d] = sum_{p,q}   g~[p][q][n]     * x[p+i][q+j][d]
  * with g~ = g, or g masked to lo < y < hi when the plan's epilogue is CLAMP
  * (then y_or_null must be the forward output; otherwise it is ignored).
- * Either dx_or_null or dw_or_null may be NULL to skip that gradient.  The
- * dw reduction is deterministic (fixed order, no atomics).  Always F32. */
+ * Either dx_or_null or dw_or_null may be NULL to skip that gradient.  Both
+ * are deterministic run to run: the dw reduction sums fixed chunks in a fixed
+ * order (no atomics), and a dL/dx tile that splits the gradient channels over
+ * lanes combines their partial sums by a fixed shuffle tree.  Always F32. */
 fbcorr_status_t fbcorr_backward(fbcorr_plan_t plan, const float* x, const float* w,
                                 const float* g, const float* y_or_null, float* dx_or_null,
                                 float* dw_or_null, void* ws, size_t ws_bytes,
