@@ -103,15 +103,18 @@ __global__ void __launch_bounds__(256) fbc_tc_split(const __grid_constant__ Spli
             }
         }
     } else {
-        // one thread per (filter, tap), filters fastest: it reads the tap's D
-        // contiguous channels and writes one 16-byte chunk to each of the nc
-        // planes [ntn][taps][nc][nt], contiguous across the warp in every plane
+        // one thread per (filter, tap, chunk plane), filters fastest: it reads
+        // the 8 channels of its chunk and writes one 16-byte chunk to the planes
+        // [ntn][taps][nc][nt] (and the half- and quarter-width copies), contiguous
+        // across the warp in every plane
         const long long t = ((long long)blockIdx.x - S.xblocks) * 256 + threadIdx.x;
         const int taps = S.fh * S.fw;
-        const long long total = (long long)S.ntn * taps * S.nt;
+        const long long total = (long long)S.ntn * taps * S.nc * S.nt;
         if (t >= total) return;
         const int nl = (int)(t % S.nt);
-        const long long u = t / S.nt;
+        const long long uc = t / S.nt;   // u * nc + c
+        const int c = (int)(uc % S.nc);
+        const long long u = uc / S.nc;
         const int tap = (int)(u % taps);
         const int nti = (int)(u / taps);
         const int n = nti * S.nt + nl;
@@ -119,36 +122,33 @@ __global__ void __launch_bounds__(256) fbc_tc_split(const __grid_constant__ Spli
         const float* src = S.w + (((long long)n * S.fh + i) * S.fw + j) * S.D;
         const bool inside = n < S.N;
         const bool vec = inside && (S.D & 3) == 0;
-        for (int c = 0; c < S.nc; ++c) {
-            float v[8];
-            if (vec && c * 8 + 8 <= S.D) {
-                const float4 a = __ldg(reinterpret_cast<const float4*>(src + c * 8));
-                const float4 b = __ldg(reinterpret_cast<const float4*>(src + c * 8 + 4));
-                v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-                v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
-            } else {
+        float v[8];
+        if (vec && c * 8 + 8 <= S.D) {
+            const float4 a = __ldg(reinterpret_cast<const float4*>(src + c * 8));
+            const float4 b = __ldg(reinterpret_cast<const float4*>(src + c * 8 + 4));
+            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+            v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+        } else {
 #pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const int d = c * 8 + k;
-                    v[k] = (inside && d < S.D) ? __ldg(src + d) : 0.f;
-                }
+            for (int k = 0; k < 8; ++k) {
+                const int d = c * 8 + k;
+                v[k] = (inside && d < S.D) ? __ldg(src + d) : 0.f;
             }
-            const long long idx = (u * S.nc + c) * S.nt + nl;
-            split8(v, reinterpret_cast<uint4*>(S.whi) + idx, reinterpret_cast<uint4*>(S.wlo) + idx, S.split);
-            if (S.halves) {
-                // the same chunk in the half-width planes [2][taps][nc][nt/2] (one filter tile)
-                const int hn = S.nt >> 1;
-                const int h = nl / hn;
-                const long long idx2 = (((long long)h * taps + tap) * S.nc + c) * hn + (nl - h * hn);
-                split8(v, reinterpret_cast<uint4*>(S.whi2) + idx2, reinterpret_cast<uint4*>(S.wlo2) + idx2, S.split);
-            }
-            if (S.quarters) {
-                // and in the quarter-width planes [4][taps][nc][nt/4] (a pair's tail halves)
-                const int qn = S.nt >> 2;
-                const int q = nl / qn;
-                const long long idx4 = (((long long)q * taps + tap) * S.nc + c) * qn + (nl - q * qn);
-                split8(v, reinterpret_cast<uint4*>(S.whi4) + idx4, reinterpret_cast<uint4*>(S.wlo4) + idx4, S.split);
-            }
+        }
+        split8(v, reinterpret_cast<uint4*>(S.whi) + t, reinterpret_cast<uint4*>(S.wlo) + t, S.split);
+        if (S.halves) {
+            // the same chunk in the half-width planes [2][taps][nc][nt/2] (one filter tile)
+            const int hn = S.nt >> 1;
+            const int h = nl / hn;
+            const long long idx2 = (((long long)h * taps + tap) * S.nc + c) * hn + (nl - h * hn);
+            split8(v, reinterpret_cast<uint4*>(S.whi2) + idx2, reinterpret_cast<uint4*>(S.wlo2) + idx2, S.split);
+        }
+        if (S.quarters) {
+            // and in the quarter-width planes [4][taps][nc][nt/4] (a pair's tail halves)
+            const int qn = S.nt >> 2;
+            const int q = nl / qn;
+            const long long idx4 = (((long long)q * taps + tap) * S.nc + c) * qn + (nl - q * qn);
+            split8(v, reinterpret_cast<uint4*>(S.whi4) + idx4, reinterpret_cast<uint4*>(S.wlo4) + idx4, S.split);
         }
     }
 }
@@ -388,7 +388,7 @@ bool tc_layout(TcPlan* p, const TcConfig& c, bool commit) {
     sp.halves = half_planes ? 1 : 0;
     sp.quarters = pair_tail ? 1 : 0;
     sp.xblocks = (k.npix_pad + 255) / 256;
-    const long long wblocks = ((long long)ntn * p->fh * p->fw * nt + 255) / 256;
+    const long long wblocks = ((long long)ntn * p->fh * p->fw * nc * nt + 255) / 256;
     if (c.fuse) sp.xblocks = 0;   // x is converted inside the correlation kernel
     p->split_blocks = (int)(sp.xblocks + wblocks);
     // one CTA per SM (the 512 TMEM columns); resident bank: a multiple of the
